@@ -1,0 +1,209 @@
+/*
+ * gw.h -- C ABI of the GB300 GW screening library (libgw.so).
+ *
+ * The library computes, on one GPU, the frequency-resolved screening
+ * pipeline of Foerster, Koval and Sanchez-Portal, "An O(N^3) implementation
+ * of Hedin's GW approximation for molecules" (arXiv:1101.2065):
+ *
+ *   gw_build_chi0  spectral function of chi0 in the dominant-product basis
+ *                  (Eq. chi_by_spectra, closed form of Sec. 6.1), compressed
+ *                  (Eqs. subsetof_vef, projector0, subspace, subspace_chi0),
+ *                  and its Cauchy (Kramers-Kronig) transform by FFT.
+ *   gw_screen_W    chi^RPA = (1 - chi0)^-1 chi0 per frequency (Eq. chi_RPA),
+ *                  W = v + Zup chi^RPA Zup^T.
+ *   gw_sigma_diag  diagonal GW self-energy from the spectral convolution of
+ *                  Eq. spectral_3 and the Cauchy integral of Eq. Cauchy1;
+ *                  exchange part by Eq. instantaneous.
+ *   gw_qp_solve    diagonal quasiparticle equation E = E_KS + Sigma(E) - vxc.
+ *
+ * Conventions (all readings are stated here so that a caller needs nothing
+ * else):
+ *  - Units: Hartree, bohr.  All floating point arguments are IEEE binary64.
+ *  - Grid: s_j = j*d_omega, j = 0..n_omega-1 (non-negative half; spectral
+ *    functions are odd, a(-s) = -a(s)); eta = broadening (1.5*d_omega in the
+ *    paper, Sec. 4.2).  Transitions are deposited with tent weights:
+ *    x = Delta/d_omega, j = floor(x), f = x - j, weight 1-f on bin j and f on
+ *    bin j+1.
+ *  - chi0_k = sum_j A_j [1/(w_k - s_j + i eta) - 1/(w_k + s_j + i eta)],
+ *    w_k = k*d_omega, A_j = sum_p 2 w_j(Delta_p) u_p u_p^T (spin factor 2).
+ *  - Pairs (E occupied, F virtual) are ordered by (Delta = eps_F - eps_E,
+ *    E, F).  Compression keeps the top n_sub eigenvectors of
+ *    g = X_r^T v X_r over the first N_rank = min(N_pair, max(5 n_orb, n_sub))
+ *    pairs; n_sub == n_prod selects the uncompressed basis Zup = L (v = L L^T).
+ *  - gamma_k = -(1/pi) Im chi^RPA_k for k >= 1, gamma_0 = 0.
+ *  - Matrices are row-major.  Complex numbers are interleaved (re, im)
+ *    binary64 pairs.
+ *
+ * Ownership: host arrays passed in belong to the caller and are copied (or
+ * fully consumed) before the call returns.  Opaque handles own device memory
+ * until their gw_*_free or gw_ctx_destroy.  Every call is synchronous with
+ * respect to the calling host thread: it enqueues its kernels on the
+ * context stream and returns after they finished and their status word was
+ * checked.  Functions are thread-compatible per context (one host thread at
+ * a time per context), not thread-safe.
+ *
+ * Errors: every function returns a gw_status (0 = GW_OK, negative = error)
+ * and records a message readable with gw_last_error().  No C++ exception
+ * crosses this interface.  On error the output handle is set to NULL and
+ * nothing is leaked.
+ */
+#ifndef GW_GB300_GW_H
+#define GW_GB300_GW_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gw_status;
+#define GW_OK                  0
+#define GW_ERR_INVALID_ARG    -1   /* bad size, NULL pointer, inconsistent layout */
+#define GW_ERR_NOT_SPD        -2   /* Coulomb metric v not positive definite */
+#define GW_ERR_GRID           -3   /* a transition falls outside the frequency window */
+#define GW_ERR_RANK           -4   /* compression subspace rank below n_sub */
+#define GW_ERR_SINGULAR       -5   /* zero or non-finite pivot of 1 - chi0 */
+#define GW_ERR_NO_CONVERGENCE -6   /* eigensolver did not converge */
+#define GW_ERR_OOM            -7   /* device allocation failed */
+#define GW_ERR_ADMISSION      -8   /* request exceeds the context's HBM budget */
+#define GW_ERR_TIMEOUT        -9   /* a bounded device wait gave up */
+#define GW_ERR_CUDA          -10   /* CUDA runtime error (message has details) */
+
+typedef enum {
+    GW_FP64 = 0,      /* every step in binary64 */
+    GW_MIXED = 1      /* binary32 contractions, FFTs and factorisations, binary64 setup
+                         and quasiparticle root; error stated against GW_FP64 */
+} gw_precision;
+
+typedef struct gw_ctx gw_ctx;       /* device, stream, HBM accounting */
+typedef struct gw_mol gw_mol;       /* device-resident molecule */
+typedef struct gw_chi0 gw_chi0;     /* pair table, basis, chi0(w_k) for all k */
+typedef struct gw_W gw_W;           /* factorised 1 - chi0(w_k) for all k */
+typedef struct gw_sigma gw_sigma;   /* Sigma forms, sigma(s), Sigma_c grid, Sigma_x */
+
+/* Molecule description, host pointers, read during gw_mol_upload only.
+ * Orbitals and products are atom-major: atom A owns orbitals
+ * [sum_{B<A} atom_norb[B], ... + atom_norb[A]) and likewise products.
+ * L(A) = orbitals of the atoms {A} u N(A) in ascending atom order; the
+ * vertex block of product mu (on atom A) is a dense symmetric row-major
+ * |L(A)| x |L(A)| matrix at vertex + vertex_off[mu] (Eq. VertexDefinition;
+ * entries outside L(A) x L(A) are zero by locality). */
+typedef struct {
+    int n_atoms, n_orb, n_occ, n_prod, n_sub;
+    const int* atom_norb;          /* [n_atoms] */
+    const int* atom_nprod;         /* [n_atoms] */
+    const int* nbr_ptr;            /* [n_atoms+1] CSR neighbour lists, no self loops */
+    const int* nbr_idx;            /* [nbr_ptr[n_atoms]] */
+    const double* eps;             /* [n_orb] ascending; first n_occ occupied */
+    const double* X;               /* [n_orb*n_orb] X[a*n_orb + E], column E = state E */
+    const double* vertex;          /* concatenated blocks */
+    const long long* vertex_off;   /* [n_prod+1] */
+    const double* v;               /* [n_prod*n_prod] symmetric positive definite */
+    const double* Z;               /* optional [n_prod*n_sub] basis Z[mu*n_sub + m] with
+                                      Z^T v Z = I; NULL => built by the library */
+} gw_molecule_desc;
+
+typedef struct { int n_omega; double d_omega; double eta; } gw_grid;
+
+typedef struct {
+    int n_orb, n_occ, n_prod, n_sub, n_pair, n_rank;  /* n_rank = 0: uncompressed */
+    int n_omega, j_lo, j_hi;       /* bins j_lo..j_hi carry all spectral weight */
+    int precision;
+    double min_pivot_ratio;        /* min_k min_i |d_i(k)| / max|1 - chi0_k| (after screen_W) */
+} gw_info;
+
+/* ---------------------------------------------------------------- context */
+const char* gw_version(void);
+/* device: CUDA ordinal; hbm_budget_bytes: 0 = unlimited, else allocations
+ * beyond it fail with GW_ERR_ADMISSION; cuda_stream: a cudaStream_t to
+ * enqueue on (e.g. a PyTorch stream), or NULL for a stream owned by the
+ * context. */
+gw_status gw_ctx_create(gw_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
+void      gw_ctx_destroy(gw_ctx* ctx);
+const char* gw_last_error(const gw_ctx* ctx);
+size_t    gw_ctx_bytes_in_use(const gw_ctx* ctx);
+/* Number of this library's kernel launches issued on the context so far. */
+long long gw_ctx_launch_count(const gw_ctx* ctx);
+
+/* ---------------------------------------------------------------- molecule */
+/* Validates the description (sizes, CSR, offsets) and copies it to the
+ * device.  GW_ERR_INVALID_ARG on inconsistent input. */
+gw_status gw_mol_upload(gw_ctx* ctx, const gw_molecule_desc* desc, gw_mol** out);
+void      gw_mol_free(gw_mol* mol);
+
+/* ---------------------------------------------------------------- pipeline */
+/* a0-a4: pair table, vertex products V^{EF}_mu = X_aE V^mu_ab X_bF
+ * (Sec. 6.1), compression basis (Eqs. projector0, subspace,
+ * global-basis-orthogonality) unless desc->Z was given, u_p = Zup^T V^p
+ * (Eq. subspace_chi0), tent deposit of A_j and chi0_k by the FFT form of the
+ * Cauchy integral (Eq. chi_by_spectra).  Errors: GW_ERR_GRID if
+ * max Delta/d_omega + 1 > n_omega - 1; GW_ERR_NOT_SPD; GW_ERR_RANK if
+ * lambda_{n_sub} < 1e-12 lambda_max; GW_ERR_NO_CONVERGENCE. */
+gw_status gw_build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid,
+                        gw_precision prec, gw_chi0** out);
+/* a5: factorises 1 - chi0_k = L_k D_k L_k^T (complex symmetric) for every
+ * k (Eq. chi_RPA).  chi0 stays valid.  GW_ERR_SINGULAR on a zero or
+ * non-finite pivot. */
+gw_status gw_screen_W(gw_ctx* ctx, const gw_chi0* chi0, gw_W** out);
+/* a6-a7 for the host list of states (each in [0, n_orb)):
+ * q_nk = Zup^T V^{nk}, c_nk(s_j) = q_nk^T gamma_j q_nk, sigma_n(s) by the
+ * tent shift of Eq. spectral_3 (virtual k: s = E_k + s2; occupied k:
+ * s = E_k - s2), Sigma_c on w_k = k d_omega, |k| < n_omega, by Eq. Cauchy1
+ * with time ordering sgn(s_j) (sgn 0 = +1), and
+ * Sigma_x_n = -sum_{k occ} V^{nk} v V^{nk} (Eq. instantaneous). */
+gw_status gw_sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n_states,
+                        gw_sigma** out);
+/* a8: E solves E - E_KS - Sigma_x + vxc - Re Sigma_c(E) = 0 per state:
+ * linearised start, Newton to |step| < 1e-11 Ha (100 steps, confined to
+ * +-0.5 Ha of the start), else bracket scan at step d_omega over +-0.5 Ha
+ * and bisection.  vxc: host [n_states] or NULL for vxc = Sigma_x (the
+ * mean field is taken to contain exchange).  Outputs are host arrays
+ * [n_states]; root_status 0 = Newton, 1 = bisection, 2 = no root found
+ * (the linearised value is returned). */
+gw_status gw_qp_solve(gw_ctx* ctx, const gw_sigma* sigma, const double* vxc,
+                      double* e_qp, double* z_factor, int* root_status);
+
+/* End to end through host memory: upload, a0-a8, QP results to host,
+ * device state released.  sigma_x: host [n_states] or NULL. */
+gw_status gw_solve_host(gw_ctx* ctx, const gw_molecule_desc* desc, const gw_grid* grid,
+                        gw_precision prec, const int* states, int n_states,
+                        const double* vxc, double* e_qp, double* z_factor,
+                        int* root_status, double* sigma_x);
+
+void gw_chi0_free(gw_chi0* chi0);
+void gw_W_free(gw_W* W);
+void gw_sigma_free(gw_sigma* sigma);
+
+/* ---------------------------------------------------------------- read-back
+ * Blocking copies into caller-owned host buffers (used by tests). */
+gw_status gw_chi0_info(const gw_chi0* chi0, gw_info* out);
+gw_status gw_W_info(const gw_W* W, gw_info* out);
+/* pair table in sorted order: E, F [n_pair] int, delta, frac [n_pair] double,
+ * bin [n_pair] int; any pointer may be NULL */
+gw_status gw_chi0_copy_pairs(gw_ctx* ctx, const gw_chi0* chi0, int* E, int* F,
+                             double* delta, int* bin, double* frac);
+/* Z and Zup: [n_prod*n_sub] row-major; either may be NULL */
+gw_status gw_chi0_copy_basis(gw_ctx* ctx, const gw_chi0* chi0, double* Z, double* Zup);
+/* U: [n_pair*n_sub] row-major, u_p = Zup^T V^p for sorted pair p */
+gw_status gw_chi0_copy_U(gw_ctx* ctx, const gw_chi0* chi0, double* U);
+/* A_j for j in [j0, j0+nj): [nj*n_sub*n_sub] real, recomputed on the device */
+gw_status gw_chi0_copy_spectral(gw_ctx* ctx, const gw_chi0* chi0, int j0, int nj, double* A);
+/* chi0_k for k in [k0, k0+nk): [nk*n_sub*n_sub] complex (full symmetric) */
+gw_status gw_chi0_copy(gw_ctx* ctx, const gw_chi0* chi0, int k0, int nk, double* out);
+/* chi^RPA_k (compressed, complex [nf*n_sub*n_sub]) for the host list freqs */
+gw_status gw_W_copy_chi_rpa(gw_ctx* ctx, const gw_W* W, const int* freqs, int nf, double* out);
+/* W_k = v + Zup chi^RPA_k Zup^T (complex [nf*n_prod*n_prod]) for the host list freqs */
+gw_status gw_W_copy_full(gw_ctx* ctx, const gw_W* W, const int* freqs, int nf, double* out);
+/* sigma read-back; every pointer may be NULL.
+ *   c      [n_states*n_orb*n_omega] real   c_nk(s_j)
+ *   sigma  [n_states*n_sig] real           sigma_n(s_j), s_j = (j0 + i) d_omega
+ *   sigc   [n_states*(2 n_omega - 1)] complex  Sigma_c(w_k), k = -(n_omega-1)..n_omega-1
+ *   sigma_x [n_states] */
+gw_status gw_sigma_copy(gw_ctx* ctx, const gw_sigma* s, double* c, double* sigma,
+                        double* sigc, double* sigma_x);
+gw_status gw_sigma_grid(const gw_sigma* s, int* j0, int* n_sig);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

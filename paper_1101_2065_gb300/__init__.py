@@ -1,0 +1,13 @@
+"""GB300-native GW screening pipeline (arXiv:1101.2065, Foerster, Koval,
+Sanchez-Portal): chi0 -> W -> Sigma -> diagonal quasiparticle equation on one
+GPU, behind the C ABI of libgw.so (include/gw.h).
+
+The Python layer is a ctypes binding (``gw``) and the in-tree build
+(``build``); all computation runs in the CUDA library.
+"""
+from . import build
+from .gw import (GW_FP64, GW_MIXED, Context, GWError, gw_build_chi0, gw_mol_upload, gw_qp_solve,
+                 gw_screen_W, gw_sigma_diag, gw_solve_host, load, solve)
+
+__all__ = ["build", "GW_FP64", "GW_MIXED", "Context", "GWError", "gw_build_chi0", "gw_mol_upload",
+           "gw_qp_solve", "gw_screen_W", "gw_sigma_diag", "gw_solve_host", "load", "solve"]

@@ -1,0 +1,742 @@
+// C ABI of the GW library: argument validation, device memory accounting,
+// orchestration of the kernels of steps a0-a8, read-back for tests.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+// ======================================================================
+// runtime helpers
+// ======================================================================
+void gw_throw(gw_status code, const std::string& msg) { throw GwError{code, msg}; }
+
+void cuda_check(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        gw_throw(e == cudaErrorMemoryAllocation ? GW_ERR_OOM : GW_ERR_CUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+
+void* ctx_alloc(gw_ctx* ctx, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+        gw_throw(GW_ERR_ADMISSION, "allocation of " + std::to_string(bytes) +
+                                       " bytes exceeds the HBM budget of the context");
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        gw_throw(GW_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
+                                 cudaGetErrorString(e));
+    }
+    ctx->blocks[p] = bytes;
+    ctx->in_use += bytes;
+    ctx->peak = std::max(ctx->peak, ctx->in_use);
+    return p;
+}
+
+void ctx_free(gw_ctx* ctx, void* p) {
+    if (!p || !ctx) return;
+    auto it = ctx->blocks.find(p);
+    if (it == ctx->blocks.end()) return;
+    ctx->in_use -= it->second;
+    ctx->blocks.erase(it);
+    cudaFreeAsync(p, ctx->stream);
+}
+
+void after_launch(gw_ctx* ctx, const char* name) {
+    ctx->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) gw_throw(GW_ERR_CUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e));
+}
+
+void ctx_finish(gw_ctx* ctx, const char* where) {
+    CUDA_CHECK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    int st = *ctx->h_status;
+    if (st) {
+        CUDA_CHECK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        std::string w(where);
+        if (st & ST_TIMEOUT) gw_throw(GW_ERR_TIMEOUT, w + ": a bounded device wait gave up");
+        if (st & ST_NOT_SPD) gw_throw(GW_ERR_NOT_SPD, w + ": Coulomb metric is not positive definite");
+        if (st & ST_RANK) gw_throw(GW_ERR_RANK, w + ": compression rank below n_sub (lambda_nsub < 1e-12 lambda_max)");
+        if (st & ST_SINGULAR) gw_throw(GW_ERR_SINGULAR, w + ": zero or non-finite pivot of 1 - chi0");
+        if (st & ST_NONFINITE) gw_throw(GW_ERR_SINGULAR, w + ": non-finite value");
+        if (st & ST_BOUNDS) gw_throw(GW_ERR_INVALID_ARG, w + ": index out of bounds detected on the device");
+        gw_throw(GW_ERR_CUDA, w + ": unknown device status");
+    }
+}
+
+#define API_BEGIN(ctxp) gw_ctx* _api_ctx = (ctxp); try {
+#define API_END                                                                  \
+    }                                                                            \
+    catch (const GwError& e) {                                                   \
+        if (_api_ctx) _api_ctx->err = e.msg;                                     \
+        return e.code;                                                           \
+    }                                                                            \
+    catch (const std::bad_alloc&) {                                              \
+        if (_api_ctx) _api_ctx->err = "host allocation failed";                  \
+        return GW_ERR_OOM;                                                       \
+    }                                                                            \
+    catch (...) {                                                                \
+        if (_api_ctx) _api_ctx->err = "unexpected internal error";               \
+        return GW_ERR_CUDA;                                                      \
+    }                                                                            \
+    return GW_OK;
+
+#define REQUIRE(cond, msg) do { if (!(cond)) gw_throw(GW_ERR_INVALID_ARG, msg); } while (0)
+
+template <class T>
+static T* upload(gw_ctx* ctx, const T* h, size_t n) {
+    T* d = dalloc<T>(ctx, n);
+    CUDA_CHECK(cudaMemcpyAsync(d, h, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return d;
+}
+
+template <class T>
+static void download(gw_ctx* ctx, T* h, const T* d, size_t n) {
+    CUDA_CHECK(cudaMemcpyAsync(h, d, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+}
+
+// ======================================================================
+// context
+// ======================================================================
+extern "C" const char* gw_version(void) { return "gw-gb300 0.1 (sm_103a)"; }
+
+extern "C" gw_status gw_ctx_create(gw_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
+    if (!out) return GW_ERR_INVALID_ARG;
+    *out = nullptr;
+    gw_ctx* ctx = new (std::nothrow) gw_ctx();
+    if (!ctx) return GW_ERR_OOM;
+    try {
+        int ndev = 0;
+        CUDA_CHECK(cudaGetDeviceCount(&ndev));
+        REQUIRE(device >= 0 && device < ndev, "device ordinal out of range");
+        CUDA_CHECK(cudaSetDevice(device));
+        ctx->device = device;
+        ctx->budget = hbm_budget_bytes;
+        if (cuda_stream) {
+            ctx->stream = (cudaStream_t)cuda_stream;
+        } else {
+            CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+            ctx->own_stream = true;
+        }
+        CUDA_CHECK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
+        cudaMemPool_t pool;
+        CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, device));
+        uint64_t thr = UINT64_MAX;
+        CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        CUDA_CHECK(cudaMalloc(&ctx->d_status, sizeof(int)));
+        CUDA_CHECK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+        CUDA_CHECK(cudaMallocHost(&ctx->h_status, sizeof(int)));
+    } catch (const GwError& e) {
+        gw_status code = e.code;
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->h_status) cudaFreeHost(ctx->h_status);
+        if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return code;
+    }
+    *out = ctx;
+    return GW_OK;
+}
+
+extern "C" void gw_ctx_destroy(gw_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    for (auto& kv : ctx->blocks) cudaFreeAsync(kv.first, ctx->stream);
+    ctx->blocks.clear();
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->d_status);
+    cudaFreeHost(ctx->h_status);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+extern "C" const char* gw_last_error(const gw_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+extern "C" size_t gw_ctx_bytes_in_use(const gw_ctx* ctx) { return ctx ? ctx->in_use : 0; }
+extern "C" long long gw_ctx_launch_count(const gw_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+// ======================================================================
+// molecule
+// ======================================================================
+static void mol_release(gw_mol* m) {
+    if (!m) return;
+    gw_ctx* c = m->ctx;
+    ctx_free(c, m->eps); ctx_free(c, m->X); ctx_free(c, m->vertex); ctx_free(c, m->voff);
+    ctx_free(c, m->v); ctx_free(c, m->Z); ctx_free(c, m->prod_atom); ctx_free(c, m->loc_ptr);
+    ctx_free(c, m->loc_idx);
+    delete m;
+}
+
+static gw_mol* mol_upload(gw_ctx* ctx, const gw_molecule_desc* d) {
+    REQUIRE(d, "NULL molecule description");
+    REQUIRE(d->n_atoms > 0 && d->n_orb > 1 && d->n_prod > 0, "empty molecule");
+    REQUIRE(d->n_occ > 0 && d->n_occ < d->n_orb, "need at least one occupied and one virtual state");
+    REQUIRE(d->n_sub > 0 && d->n_sub <= d->n_prod, "n_sub must be in [1, n_prod]");
+    REQUIRE(d->atom_norb && d->atom_nprod && d->nbr_ptr && d->eps && d->X && d->vertex &&
+                d->vertex_off && d->v,
+            "NULL array in molecule description");
+    const int na = d->n_atoms;
+    std::vector<int> optr(na + 1, 0), pptr(na + 1, 0);
+    for (int a = 0; a < na; ++a) {
+        REQUIRE(d->atom_norb[a] >= 0 && d->atom_nprod[a] >= 0, "negative per-atom count");
+        optr[a + 1] = optr[a] + d->atom_norb[a];
+        pptr[a + 1] = pptr[a] + d->atom_nprod[a];
+    }
+    REQUIRE(optr[na] == d->n_orb, "sum of atom_norb differs from n_orb");
+    REQUIRE(pptr[na] == d->n_prod, "sum of atom_nprod differs from n_prod");
+    REQUIRE(d->nbr_ptr[0] == 0, "nbr_ptr[0] must be 0");
+    for (int a = 0; a < na; ++a) REQUIRE(d->nbr_ptr[a + 1] >= d->nbr_ptr[a], "nbr_ptr not monotone");
+    const int nnz = d->nbr_ptr[na];
+    REQUIRE(nnz == 0 || d->nbr_idx, "NULL nbr_idx");
+    for (int a = 0; a < na; ++a)
+        for (int q = d->nbr_ptr[a]; q < d->nbr_ptr[a + 1]; ++q)
+            REQUIRE(d->nbr_idx[q] >= 0 && d->nbr_idx[q] < na && d->nbr_idx[q] != a,
+                    "neighbour index out of range or self loop");
+    for (int i = 1; i < d->n_orb; ++i) REQUIRE(d->eps[i] >= d->eps[i - 1], "eps must be ascending");
+    for (int i = 0; i < d->n_orb; ++i) REQUIRE(std::isfinite(d->eps[i]), "non-finite eps");
+
+    // local orbital lists L(A)
+    std::vector<int> loc_ptr(na + 1, 0), loc_idx;
+    int max_nloc = 0;
+    for (int a = 0; a < na; ++a) {
+        std::vector<int> atoms{a};
+        for (int q = d->nbr_ptr[a]; q < d->nbr_ptr[a + 1]; ++q) atoms.push_back(d->nbr_idx[q]);
+        std::sort(atoms.begin(), atoms.end());
+        atoms.erase(std::unique(atoms.begin(), atoms.end()), atoms.end());
+        for (int b : atoms)
+            for (int o = optr[b]; o < optr[b + 1]; ++o) loc_idx.push_back(o);
+        loc_ptr[a + 1] = (int)loc_idx.size();
+        max_nloc = std::max(max_nloc, loc_ptr[a + 1] - loc_ptr[a]);
+    }
+    REQUIRE(max_nloc <= 112, "a local orbital set L(A) larger than 112 orbitals is not supported");
+    std::vector<int> prod_atom(d->n_prod);
+    REQUIRE(d->vertex_off[0] == 0, "vertex_off[0] must be 0");
+    for (int a = 0; a < na; ++a)
+        for (int mu = pptr[a]; mu < pptr[a + 1]; ++mu) {
+            prod_atom[mu] = a;
+            long long nl = loc_ptr[a + 1] - loc_ptr[a];
+            REQUIRE(d->vertex_off[mu + 1] - d->vertex_off[mu] == nl * nl,
+                    "vertex block size differs from |L(A)|^2");
+        }
+    gw_mol* m = new gw_mol();
+    m->ctx = ctx;
+    m->n_atoms = na; m->n_orb = d->n_orb; m->n_occ = d->n_occ; m->n_prod = d->n_prod; m->n_sub = d->n_sub;
+    m->max_nloc = max_nloc;
+    m->h_eps.assign(d->eps, d->eps + d->n_orb);
+    m->vertex_len = (size_t)d->vertex_off[d->n_prod];
+    try {
+        m->eps = upload(ctx, d->eps, d->n_orb);
+        m->X = upload(ctx, d->X, (size_t)d->n_orb * d->n_orb);
+        m->vertex = upload(ctx, d->vertex, m->vertex_len);
+        m->voff = upload(ctx, d->vertex_off, d->n_prod + 1);
+        m->v = upload(ctx, d->v, (size_t)d->n_prod * d->n_prod);
+        if (d->Z) m->Z = upload(ctx, d->Z, (size_t)d->n_prod * d->n_sub);
+        m->prod_atom = upload(ctx, prod_atom.data(), prod_atom.size());
+        m->loc_ptr = upload(ctx, loc_ptr.data(), loc_ptr.size());
+        m->loc_idx = upload(ctx, loc_idx.data(), std::max<size_t>(loc_idx.size(), 1));
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    } catch (...) {
+        mol_release(m);
+        throw;
+    }
+    return m;
+}
+
+extern "C" gw_status gw_mol_upload(gw_ctx* ctx, const gw_molecule_desc* desc, gw_mol** out) {
+    if (!ctx || !out) return GW_ERR_INVALID_ARG;
+    *out = nullptr;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    *out = mol_upload(ctx, desc);
+    API_END
+}
+
+extern "C" void gw_mol_free(gw_mol* mol) { mol_release(mol); }
+
+// ======================================================================
+// a0-a4: chi0
+// ======================================================================
+static void chi0_release(gw_chi0* c) {
+    if (!c) return;
+    gw_ctx* x = c->ctx;
+    ctx_free(x, c->pE); ctx_free(x, c->pF); ctx_free(x, c->pBin); ctx_free(x, c->pDelta);
+    ctx_free(x, c->pFrac); ctx_free(x, c->seg); ctx_free(x, c->Z); ctx_free(x, c->Zup);
+    ctx_free(x, c->Ut); ctx_free(x, c->tw); ctx_free(x, c->C1); ctx_free(x, c->C2);
+    ctx_free(x, c->chi0); ctx_free(x, c->Ut32); ctx_free(x, c->tw32); ctx_free(x, c->C1_32);
+    ctx_free(x, c->C2_32); ctx_free(x, c->chi0_32);
+    delete c;
+}
+
+static void check_grid(const gw_grid* g) {
+    REQUIRE(g, "NULL grid");
+    REQUIRE(g->n_omega >= 4 && (g->n_omega & (g->n_omega - 1)) == 0 && g->n_omega <= (1 << 15),
+            "n_omega must be a power of two in [4, 32768]");
+    REQUIRE(g->d_omega > 0 && std::isfinite(g->d_omega), "d_omega must be positive");
+    REQUIRE(g->eta > 0 && std::isfinite(g->eta), "eta must be positive");
+}
+
+static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, gw_precision prec) {
+    REQUIRE(mol && mol->ctx == ctx, "molecule belongs to another context");
+    check_grid(grid);
+    REQUIRE(prec == GW_FP64 || prec == GW_MIXED, "unknown precision");
+    const int n_occ = mol->n_occ, n_orb = mol->n_orb, n_virt = n_orb - n_occ;
+    const int N = grid->n_omega;
+    // band of the tent bins, from the same binary64 operations as the device
+    const std::vector<double>& e = mol->h_eps;
+    double dmin = e[n_occ] - e[n_occ - 1], dmax = e[n_orb - 1] - e[0];
+    double xlo = std::floor(dmin / grid->d_omega), xhi = std::floor(dmax / grid->d_omega);
+    if (!(xlo >= 0) || !(xhi + 1 <= N - 1))
+        gw_throw(GW_ERR_GRID, "a transition lies outside the frequency window (need floor(Delta/d_omega)+1 <= n_omega-1)");
+    gw_chi0* c = new gw_chi0();
+    c->ctx = ctx; c->mol = mol; c->grid = *grid; c->prec = prec;
+    c->n_pair = n_occ * n_virt;
+    c->n_sub = mol->n_sub;
+    c->j_lo = (int)xlo;
+    c->nb_bins = (int)xhi - (int)xlo + 1;
+    c->j_hi = (int)xhi + 1;
+    c->L = 2 * N;
+    c->logL = 0;
+    while ((1 << c->logL) < c->L) c->logL++;
+    const int n_prod = mol->n_prod, n_sub = mol->n_sub, n_pair = c->n_pair;
+    double* VEFt = nullptr;
+    double *T1 = nullptr, *g = nullptr, *evals = nullptr, *evecs = nullptr, *Bsel = nullptr;
+    int* occ = nullptr; int* virt = nullptr; int* rank_of = nullptr;
+    try {
+        // a0: pair table
+        launch_pair_table(ctx, mol, c);
+        // a1: vertex products for every pair, product-major [n_prod][n_pair] in sorted order
+        std::vector<int> ho(n_occ), hv(n_virt);
+        for (int i = 0; i < n_occ; ++i) ho[i] = i;
+        for (int i = 0; i < n_virt; ++i) hv[i] = n_occ + i;
+        occ = upload(ctx, ho.data(), ho.size());
+        virt = upload(ctx, hv.data(), hv.size());
+        rank_of = dalloc<int>(ctx, n_pair);
+        // inverse permutation: natural pair index -> sorted position
+        launch_invert_perm(ctx, c, rank_of);
+        VEFt = dalloc<double>(ctx, (size_t)n_prod * n_pair);
+        launch_vertex_contract(ctx, mol, occ, n_occ, virt, n_virt, rank_of, VEFt, n_pair);
+        // a0: basis
+        c->Zup = dalloc<double>(ctx, (size_t)n_prod * n_sub);
+        if (mol->Z) {
+            c->Z = dalloc<double>(ctx, (size_t)n_prod * n_sub);
+            CUDA_CHECK(cudaMemcpyAsync(c->Z, mol->Z, sizeof(double) * n_prod * n_sub, cudaMemcpyDeviceToDevice, ctx->stream));
+            gemm_f64(ctx, false, false, n_prod, n_sub, n_prod, 1.0, mol->v, n_prod, c->Z, n_sub, 0.0, c->Zup, n_sub);
+        } else if (n_sub == n_prod) {
+            CUDA_CHECK(cudaMemcpyAsync(c->Zup, mol->v, sizeof(double) * n_prod * n_prod, cudaMemcpyDeviceToDevice, ctx->stream));
+            cholesky_lower(ctx, c->Zup, n_prod);
+        } else {
+            const int nr = std::min(n_pair, std::max(5 * n_orb, n_sub));
+            c->n_rank = nr;
+            T1 = dalloc<double>(ctx, (size_t)n_prod * nr);
+            g = dalloc<double>(ctx, (size_t)nr * nr);
+            // T1 = v X_r, g = X_r^T v X_r  (X_r = first nr columns of VEFt)
+            gemm_f64(ctx, false, false, n_prod, nr, n_prod, 1.0, mol->v, n_prod, VEFt, n_pair, 0.0, T1, nr);
+            gemm_f64(ctx, true, false, nr, nr, n_prod, 1.0, VEFt, n_pair, T1, nr, 0.0, g, nr);
+            int np = nr + (nr & 1);
+            evals = dalloc<double>(ctx, np);
+            evecs = dalloc<double>(ctx, (size_t)np * np);
+            jacobi_eigh(ctx, g, nr, evals, evecs);
+            Bsel = dalloc<double>(ctx, (size_t)nr * n_sub);
+            select_top_scaled(ctx, evals, evecs, nr, n_sub, Bsel);
+            c->Z = dalloc<double>(ctx, (size_t)n_prod * n_sub);
+            gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, VEFt, n_pair, Bsel, n_sub, 0.0, c->Z, n_sub);
+            gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, T1, nr, Bsel, n_sub, 0.0, c->Zup, n_sub);
+        }
+        // a2: U^T = Zup^T V^EF  -> [n_sub][n_pair]
+        c->Ut = dalloc<double>(ctx, (size_t)n_sub * n_pair);
+        gemm_f64(ctx, true, false, n_sub, n_pair, n_prod, 1.0, c->Zup, n_sub, VEFt, n_pair, 0.0, c->Ut, n_pair);
+        ctx_free(ctx, VEFt); VEFt = nullptr;
+        ctx_free(ctx, T1); T1 = nullptr; ctx_free(ctx, g); g = nullptr;
+        ctx_free(ctx, evals); evals = nullptr; ctx_free(ctx, evecs); evecs = nullptr;
+        ctx_free(ctx, Bsel); Bsel = nullptr;
+        ctx_free(ctx, occ); occ = nullptr; ctx_free(ctx, virt); virt = nullptr;
+        ctx_free(ctx, rank_of); rank_of = nullptr;
+        // a3 + a4: deposit and Cauchy transform by FFT
+        launch_fft_tables(ctx, c);
+        launch_chi0_fft(ctx, c);
+        ctx_finish(ctx, "gw_build_chi0");
+    } catch (...) {
+        ctx_free(ctx, VEFt); ctx_free(ctx, T1); ctx_free(ctx, g); ctx_free(ctx, evals);
+        ctx_free(ctx, evecs); ctx_free(ctx, Bsel); ctx_free(ctx, occ); ctx_free(ctx, virt);
+        ctx_free(ctx, rank_of);
+        chi0_release(c);
+        throw;
+    }
+    return c;
+}
+
+extern "C" gw_status gw_build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid,
+                                   gw_precision prec, gw_chi0** out) {
+    if (!ctx || !out) return GW_ERR_INVALID_ARG;
+    *out = nullptr;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    *out = build_chi0(ctx, mol, grid, prec);
+    API_END
+}
+
+extern "C" void gw_chi0_free(gw_chi0* c) { chi0_release(c); }
+
+// ======================================================================
+// a5: screening
+// ======================================================================
+static void W_release(gw_W* w) {
+    if (!w) return;
+    ctx_free(w->ctx, w->fac); ctx_free(w->ctx, w->fac32); ctx_free(w->ctx, w->piv);
+    delete w;
+}
+
+static gw_W* screen_W(gw_ctx* ctx, const gw_chi0* c) {
+    REQUIRE(c && c->ctx == ctx, "chi0 belongs to another context");
+    gw_W* w = new gw_W();
+    w->ctx = ctx; w->chi0 = c;
+    const size_t n = c->n_sub, N = c->grid.n_omega;
+    try {
+        w->fac = dalloc<double2>(ctx, N * n * n);
+        w->piv = dalloc<double>(ctx, N);
+        launch_ldlt(ctx, w);
+        std::vector<double> piv(N);
+        download(ctx, piv.data(), w->piv, N);
+        ctx_finish(ctx, "gw_screen_W");
+        w->min_pivot_ratio = *std::min_element(piv.begin(), piv.end());
+    } catch (...) {
+        W_release(w);
+        throw;
+    }
+    return w;
+}
+
+extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_chi0* chi0, gw_W** out) {
+    if (!ctx || !out) return GW_ERR_INVALID_ARG;
+    *out = nullptr;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    *out = screen_W(ctx, chi0);
+    API_END
+}
+
+extern "C" void gw_W_free(gw_W* W) { W_release(W); }
+
+// ======================================================================
+// a6-a7: self-energy
+// ======================================================================
+static void sigma_release(gw_sigma* s) {
+    if (!s) return;
+    gw_ctx* x = s->ctx;
+    ctx_free(x, s->c); ctx_free(x, s->sig); ctx_free(x, s->sigc); ctx_free(x, s->sx); ctx_free(x, s->eks);
+    delete s;
+}
+
+static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n_states) {
+    REQUIRE(W && W->ctx == ctx, "W belongs to another context");
+    REQUIRE(states && n_states > 0, "empty state list");
+    const gw_chi0* c = W->chi0;
+    const gw_mol* mol = c->mol;
+    for (int i = 0; i < n_states; ++i) REQUIRE(states[i] >= 0 && states[i] < mol->n_orb, "state index out of range");
+    gw_sigma* s = new gw_sigma();
+    s->ctx = ctx; s->W = W; s->n_states = n_states; s->states.assign(states, states + n_states);
+    const int n_orb = mol->n_orb, n_prod = mol->n_prod, n_sub = c->n_sub, N = c->grid.n_omega;
+    const int R = n_states * n_orb;
+    s->R = R;
+    // sigma grid range: floor(E/d_omega) - (N-1) .. floor(E/d_omega) + N over all states
+    const double dw = c->grid.d_omega;
+    double imin = std::floor(mol->h_eps.front() / dw), imax = std::floor(mol->h_eps.back() / dw);
+    s->j0 = (int)imin - (N - 1);
+    s->n_sig = ((int)imax + N) - s->j0 + 1;
+    int *Es = nullptr, *Fs = nullptr;
+    double *Vnk = nullptr, *Q = nullptr, *T = nullptr;
+    try {
+        std::vector<int> all(n_orb);
+        for (int i = 0; i < n_orb; ++i) all[i] = i;
+        Es = upload(ctx, states, n_states);
+        Fs = upload(ctx, all.data(), n_orb);
+        std::vector<double> eks(n_states);
+        for (int i = 0; i < n_states; ++i) eks[i] = mol->h_eps[states[i]];
+        s->eks = upload(ctx, eks.data(), n_states);
+        // V^{nk}_mu, columns r = i*n_orb + k
+        Vnk = dalloc<double>(ctx, (size_t)n_prod * R);
+        launch_vertex_contract(ctx, mol, Es, n_states, Fs, n_orb, nullptr, Vnk, R);
+        // q_nk = Zup^T V^{nk}: Q [n_sub][R]
+        Q = dalloc<double>(ctx, (size_t)n_sub * R);
+        gemm_f64(ctx, true, false, n_sub, R, n_prod, 1.0, c->Zup, n_sub, Vnk, R, 0.0, Q, R);
+        // c_nk(s_j)
+        s->c = dalloc<double>(ctx, (size_t)R * N);
+        launch_forms(ctx, W, Q, R, s->c);
+        // sigma_n(s), Sigma_c grid
+        s->sig = dalloc<double>(ctx, (size_t)n_states * s->n_sig);
+        launch_sigma_grid(ctx, s);
+        s->sigc = dalloc<double2>(ctx, (size_t)n_states * (2 * N - 1));
+        launch_sigma_c(ctx, s);
+        // Sigma_x = -sum_{k occ} V^{nk} v V^{nk}
+        T = dalloc<double>(ctx, (size_t)n_prod * R);
+        gemm_f64(ctx, false, false, n_prod, R, n_prod, 1.0, mol->v, n_prod, Vnk, R, 0.0, T, R);
+        s->sx = dalloc<double>(ctx, n_states);
+        launch_sigma_x(ctx, s, Vnk, T, R);
+        ctx_finish(ctx, "gw_sigma_diag");
+        ctx_free(ctx, Es); ctx_free(ctx, Fs); ctx_free(ctx, Vnk); ctx_free(ctx, Q); ctx_free(ctx, T);
+    } catch (...) {
+        ctx_free(ctx, Es); ctx_free(ctx, Fs); ctx_free(ctx, Vnk); ctx_free(ctx, Q); ctx_free(ctx, T);
+        sigma_release(s);
+        throw;
+    }
+    return s;
+}
+
+extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n_states,
+                                   gw_sigma** out) {
+    if (!ctx || !out) return GW_ERR_INVALID_ARG;
+    *out = nullptr;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    *out = sigma_diag(ctx, W, states, n_states);
+    API_END
+}
+
+extern "C" void gw_sigma_free(gw_sigma* s) { sigma_release(s); }
+
+// ======================================================================
+// a8: quasiparticle equation
+// ======================================================================
+static void qp_solve(gw_ctx* ctx, const gw_sigma* s, const double* vxc, double* e, double* z, int* st) {
+    REQUIRE(s && s->ctx == ctx, "sigma belongs to another context");
+    REQUIRE(e && z && st, "NULL output array");
+    const int ns = s->n_states;
+    double* dv = nullptr; double* de = nullptr; double* dz = nullptr; int* ds = nullptr;
+    try {
+        if (vxc) dv = upload(ctx, vxc, ns);
+        de = dalloc<double>(ctx, ns); dz = dalloc<double>(ctx, ns); ds = dalloc<int>(ctx, ns);
+        launch_qp(ctx, s, dv, de, dz, ds);
+        download(ctx, e, de, ns); download(ctx, z, dz, ns); download(ctx, st, ds, ns);
+        ctx_finish(ctx, "gw_qp_solve");
+    } catch (...) {
+        ctx_free(ctx, dv); ctx_free(ctx, de); ctx_free(ctx, dz); ctx_free(ctx, ds);
+        throw;
+    }
+    ctx_free(ctx, dv); ctx_free(ctx, de); ctx_free(ctx, dz); ctx_free(ctx, ds);
+}
+
+extern "C" gw_status gw_qp_solve(gw_ctx* ctx, const gw_sigma* sigma, const double* vxc,
+                                 double* e_qp, double* z_factor, int* root_status) {
+    if (!ctx) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    qp_solve(ctx, sigma, vxc, e_qp, z_factor, root_status);
+    API_END
+}
+
+extern "C" gw_status gw_solve_host(gw_ctx* ctx, const gw_molecule_desc* desc, const gw_grid* grid,
+                                   gw_precision prec, const int* states, int n_states,
+                                   const double* vxc, double* e_qp, double* z_factor,
+                                   int* root_status, double* sigma_x) {
+    if (!ctx) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    gw_mol* m = nullptr; gw_chi0* c = nullptr; gw_W* w = nullptr; gw_sigma* s = nullptr;
+    try {
+        m = mol_upload(ctx, desc);
+        c = build_chi0(ctx, m, grid, prec);
+        w = screen_W(ctx, c);
+        s = sigma_diag(ctx, w, states, n_states);
+        qp_solve(ctx, s, vxc, e_qp, z_factor, root_status);
+        if (sigma_x) {
+            download(ctx, sigma_x, s->sx, n_states);
+            CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        }
+    } catch (...) {
+        sigma_release(s); W_release(w); chi0_release(c); mol_release(m);
+        throw;
+    }
+    sigma_release(s); W_release(w); chi0_release(c); mol_release(m);
+    API_END
+}
+
+// ======================================================================
+// read-back
+// ======================================================================
+extern "C" gw_status gw_chi0_info(const gw_chi0* c, gw_info* out) {
+    if (!c || !out) return GW_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->n_orb = c->mol->n_orb; out->n_occ = c->mol->n_occ; out->n_prod = c->mol->n_prod;
+    out->n_sub = c->n_sub; out->n_pair = c->n_pair; out->n_rank = c->n_rank;
+    out->n_omega = c->grid.n_omega; out->j_lo = c->j_lo; out->j_hi = c->j_hi;
+    out->precision = (int)c->prec;
+    return GW_OK;
+}
+
+extern "C" gw_status gw_W_info(const gw_W* W, gw_info* out) {
+    if (!W || !out) return GW_ERR_INVALID_ARG;
+    gw_status s = gw_chi0_info(W->chi0, out);
+    out->min_pivot_ratio = W->min_pivot_ratio;
+    return s;
+}
+
+extern "C" gw_status gw_chi0_copy_pairs(gw_ctx* ctx, const gw_chi0* c, int* E, int* F,
+                                        double* delta, int* bin, double* frac) {
+    if (!ctx || !c) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    if (E) download(ctx, E, c->pE, c->n_pair);
+    if (F) download(ctx, F, c->pF, c->n_pair);
+    if (delta) download(ctx, delta, c->pDelta, c->n_pair);
+    if (bin) download(ctx, bin, c->pBin, c->n_pair);
+    if (frac) download(ctx, frac, c->pFrac, c->n_pair);
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    API_END
+}
+
+extern "C" gw_status gw_chi0_copy_basis(gw_ctx* ctx, const gw_chi0* c, double* Z, double* Zup) {
+    if (!ctx || !c) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    size_t n = (size_t)c->mol->n_prod * c->n_sub;
+    if (Z) {
+        REQUIRE(c->Z, "Z is not formed for the Cholesky (uncompressed) basis; read Zup");
+        download(ctx, Z, c->Z, n);
+    }
+    if (Zup) download(ctx, Zup, c->Zup, n);
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    API_END
+}
+
+extern "C" gw_status gw_chi0_copy_U(gw_ctx* ctx, const gw_chi0* c, double* U) {
+    if (!ctx || !c || !U) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    std::vector<double> t((size_t)c->n_sub * c->n_pair);
+    download(ctx, t.data(), c->Ut, t.size());
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    for (int m = 0; m < c->n_sub; ++m)
+        for (int p = 0; p < c->n_pair; ++p) U[(size_t)p * c->n_sub + m] = t[(size_t)m * c->n_pair + p];
+    API_END
+}
+
+extern "C" gw_status gw_chi0_copy_spectral(gw_ctx* ctx, const gw_chi0* c, int j0, int nj, double* A) {
+    if (!ctx || !c || !A) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    REQUIRE(nj >= 0 && j0 >= 0 && j0 + nj <= c->grid.n_omega, "bin range outside the grid");
+    size_t n = (size_t)nj * c->n_sub * c->n_sub;
+    double* d = dalloc<double>(ctx, std::max<size_t>(n, 1));
+    try {
+        launch_spectral_readback(ctx, c, j0, nj, d);
+        download(ctx, A, d, n);
+        ctx_finish(ctx, "gw_chi0_copy_spectral");
+    } catch (...) { ctx_free(ctx, d); throw; }
+    ctx_free(ctx, d);
+    API_END
+}
+
+extern "C" gw_status gw_chi0_copy(gw_ctx* ctx, const gw_chi0* c, int k0, int nk, double* out) {
+    if (!ctx || !c || !out) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    REQUIRE(nk >= 0 && k0 >= 0 && k0 + nk <= c->grid.n_omega, "frequency range outside the grid");
+    const size_t n = c->n_sub;
+    std::vector<double2> t(nk * n * n);
+    if (c->prec == GW_MIXED && c->chi0_32) {
+        std::vector<float2> t32(t.size());
+        download(ctx, t32.data(), c->chi0_32 + (size_t)k0 * n * n, t32.size());
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        for (size_t i = 0; i < t.size(); ++i) t[i] = make_double2(t32[i].x, t32[i].y);
+    } else {
+        download(ctx, t.data(), c->chi0 + (size_t)k0 * n * n, t.size());
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    }
+    double2* o = reinterpret_cast<double2*>(out);
+    for (int k = 0; k < nk; ++k)
+        for (size_t i = 0; i < n; ++i)
+            for (size_t j = 0; j < n; ++j) {
+                size_t a = std::max(i, j), b = std::min(i, j);
+                o[(k * n + i) * n + j] = t[(k * n + a) * n + b];
+            }
+    API_END
+}
+
+extern "C" gw_status gw_W_copy_chi_rpa(gw_ctx* ctx, const gw_W* W, const int* freqs, int nf, double* out) {
+    if (!ctx || !W || !out || (nf > 0 && !freqs)) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    const gw_chi0* c = W->chi0;
+    const size_t n = c->n_sub;
+    for (int i = 0; i < nf; ++i) REQUIRE(freqs[i] >= 0 && freqs[i] < c->grid.n_omega, "frequency out of range");
+    double2* d = dalloc<double2>(ctx, n * n);
+    double2* work = dalloc<double2>(ctx, n * n);
+    try {
+        for (int i = 0; i < nf; ++i) {
+            launch_ldlt_inverse(ctx, W, freqs[i], d, work);   // chi^RPA = M^-1 - I
+            download(ctx, reinterpret_cast<double2*>(out) + i * n * n, d, n * n);
+        }
+        ctx_finish(ctx, "gw_W_copy_chi_rpa");
+    } catch (...) { ctx_free(ctx, d); ctx_free(ctx, work); throw; }
+    ctx_free(ctx, d); ctx_free(ctx, work);
+    API_END
+}
+
+extern "C" gw_status gw_W_copy_full(gw_ctx* ctx, const gw_W* W, const int* freqs, int nf, double* out) {
+    if (!ctx || !W || !out || (nf > 0 && !freqs)) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    const gw_chi0* c = W->chi0;
+    const int n = c->n_sub, np = c->mol->n_prod;
+    for (int i = 0; i < nf; ++i) REQUIRE(freqs[i] >= 0 && freqs[i] < c->grid.n_omega, "frequency out of range");
+    double2* d = dalloc<double2>(ctx, (size_t)n * n);
+    double2* work = dalloc<double2>(ctx, (size_t)n * n);
+    double* re = dalloc<double>(ctx, (size_t)n * n);
+    double* im = dalloc<double>(ctx, (size_t)n * n);
+    double* T = dalloc<double>(ctx, (size_t)np * n);
+    double* Wre = dalloc<double>(ctx, (size_t)np * np);
+    double* Wim = dalloc<double>(ctx, (size_t)np * np);
+    try {
+        std::vector<double> hre((size_t)np * np), him((size_t)np * np);
+        for (int i = 0; i < nf; ++i) {
+            launch_ldlt_inverse(ctx, W, freqs[i], d, work);
+            launch_split_complex(ctx, d, re, im, (size_t)n * n);
+            CUDA_CHECK(cudaMemcpyAsync(Wre, c->mol->v, sizeof(double) * np * np, cudaMemcpyDeviceToDevice, ctx->stream));
+            gemm_f64(ctx, false, false, np, n, n, 1.0, c->Zup, n, re, n, 0.0, T, n);
+            gemm_f64(ctx, false, true, np, np, n, 1.0, T, n, c->Zup, n, 1.0, Wre, np);
+            gemm_f64(ctx, false, false, np, n, n, 1.0, c->Zup, n, im, n, 0.0, T, n);
+            gemm_f64(ctx, false, true, np, np, n, 1.0, T, n, c->Zup, n, 0.0, Wim, np);
+            download(ctx, hre.data(), Wre, hre.size());
+            download(ctx, him.data(), Wim, him.size());
+            CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+            double2* o = reinterpret_cast<double2*>(out) + (size_t)i * np * np;
+            for (size_t q = 0; q < hre.size(); ++q) o[q] = make_double2(hre[q], him[q]);
+        }
+        ctx_finish(ctx, "gw_W_copy_full");
+    } catch (...) {
+        ctx_free(ctx, d); ctx_free(ctx, work); ctx_free(ctx, re); ctx_free(ctx, im);
+        ctx_free(ctx, T); ctx_free(ctx, Wre); ctx_free(ctx, Wim);
+        throw;
+    }
+    ctx_free(ctx, d); ctx_free(ctx, work); ctx_free(ctx, re); ctx_free(ctx, im);
+    ctx_free(ctx, T); ctx_free(ctx, Wre); ctx_free(ctx, Wim);
+    API_END
+}
+
+extern "C" gw_status gw_sigma_copy(gw_ctx* ctx, const gw_sigma* s, double* c, double* sigma,
+                                   double* sigc, double* sigma_x) {
+    if (!ctx || !s) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    const int N = s->W->chi0->grid.n_omega;
+    if (c) download(ctx, c, s->c, (size_t)s->R * N);
+    if (sigma) download(ctx, sigma, s->sig, (size_t)s->n_states * s->n_sig);
+    if (sigc) download(ctx, reinterpret_cast<double2*>(sigc), s->sigc, (size_t)s->n_states * (2 * N - 1));
+    if (sigma_x) download(ctx, sigma_x, s->sx, s->n_states);
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    API_END
+}
+
+extern "C" gw_status gw_sigma_grid(const gw_sigma* s, int* j0, int* n_sig) {
+    if (!s || !j0 || !n_sig) return GW_ERR_INVALID_ARG;
+    *j0 = s->j0;
+    *n_sig = s->n_sig;
+    return GW_OK;
+}

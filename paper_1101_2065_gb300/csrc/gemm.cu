@@ -1,0 +1,88 @@
+// Dense row-major GEMM C = alpha op(A) op(B) + beta C in binary64, used for
+// the plain matrix products of the path: g = X_r^T v X_r and Z = X_r xi
+// lambda^-1/2 (Eqs. projector0, subspace), U = V^EF Zup (Eq. subspace_chi0),
+// q = Zup^T V^{nk}, v V^{nk} (Eq. instantaneous), W = v + Zup chi Zup^T.
+// 64x64 output tile per CTA, K staged by 16 through shared memory, 4x4
+// outputs per thread; binary64 issue rate bounds it on this GPU.
+#include "internal.h"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha, const double* __restrict__ A,
+                                               long long lda, const double* __restrict__ B, long long ldb,
+                                               double beta, double* __restrict__ C, long long ldc, long long sA,
+                                               long long sB, long long sC) {
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    A += blockIdx.z * sA;
+    B += blockIdx.z * sB;
+    C += blockIdx.z * sC;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int i = threadIdx.x; i < BK * BM; i += 256) {
+            int kk, mm;
+            if (TA) { kk = i / BM; mm = i % BM; } else { mm = i / BK; kk = i % BK; }
+            int gm = m0 + mm, gk = k0 + kk;
+            double val = 0.0;
+            if (gm < M && gk < K) val = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+            As[kk][mm] = val;
+        }
+        for (int i = threadIdx.x; i < BK * BN; i += 256) {
+            int kk, nn;
+            if (!TB) { kk = i / BN; nn = i % BN; } else { nn = i / BK; kk = i % BK; }
+            int gn = n0 + nn, gk = k0 + kk;
+            double val = 0.0;
+            if (gn < N && gk < K) val = TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
+            Bs[kk][nn] = val;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            double* c = C + (long long)gm * ldc + gn;
+            *c = beta == 0.0 ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
+        }
+    }
+}
+
+}  // namespace
+
+void gemm_f64(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, double alpha, const double* A, long long lda,
+              const double* B, long long ldb, double beta, double* C, long long ldc, int batch, long long sA,
+              long long sB, long long sC) {
+    if (M <= 0 || N <= 0) return;
+    dim3 grid(div_up(N, BN), div_up(M, BM), batch);
+    if (!ta && !tb) k_dgemm<false, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
+    else if (ta && !tb) k_dgemm<true, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
+    else if (!ta && tb) k_dgemm<false, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
+    else k_dgemm<true, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
+    LAUNCH_CHECK(ctx, "k_dgemm");
+}

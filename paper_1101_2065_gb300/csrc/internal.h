@@ -1,0 +1,177 @@
+// Internal declarations of the GW library: context, handles, launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gw.h"
+
+// ------------------------------------------------------------------ status
+// Bits of the per-context device status word.  Kernels set them with
+// atomicOr; the host reads the word at the end of every API call.
+enum : int {
+    ST_NOT_SPD = 1,
+    ST_SINGULAR = 2,
+    ST_RANK = 4,
+    ST_NONFINITE = 8,
+    ST_BOUNDS = 16,
+    ST_TIMEOUT = 32,
+};
+
+struct GwError {
+    gw_status code;
+    std::string msg;
+};
+
+struct gw_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;
+    size_t in_use = 0;
+    size_t peak = 0;
+    long long launches = 0;
+    std::string err;
+    std::unordered_map<void*, size_t> blocks;
+    int* d_status = nullptr;
+    int* h_status = nullptr;
+    int num_sms = 0;
+};
+
+// Throws GwError; every extern "C" entry point catches and converts.
+void gw_throw(gw_status code, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+#define CUDA_CHECK(x) cuda_check((x), #x)
+
+void* ctx_alloc(gw_ctx* ctx, size_t bytes);
+void ctx_free(gw_ctx* ctx, void* p);
+template <class T>
+T* dalloc(gw_ctx* ctx, size_t n) { return static_cast<T*>(ctx_alloc(ctx, n * sizeof(T))); }
+
+// Counts a launch and checks the launch error.
+void after_launch(gw_ctx* ctx, const char* name);
+#define LAUNCH_CHECK(ctx, name) after_launch((ctx), (name))
+
+// Synchronise the context stream and convert status bits into an error.
+void ctx_finish(gw_ctx* ctx, const char* where);
+
+// ------------------------------------------------------------------ handles
+struct gw_mol {
+    gw_ctx* ctx = nullptr;
+    int n_atoms = 0, n_orb = 0, n_occ = 0, n_prod = 0, n_sub = 0;
+    int max_nloc = 0;
+    std::vector<double> h_eps;       // host copy (validation of the grid)
+    double* eps = nullptr;           // [n_orb]
+    double* X = nullptr;             // [n_orb*n_orb] X[a*n_orb+E]
+    double* vertex = nullptr;
+    long long* voff = nullptr;       // [n_prod+1]
+    double* v = nullptr;             // [n_prod*n_prod]
+    double* Z = nullptr;             // optional [n_prod*n_sub]
+    int* prod_atom = nullptr;        // [n_prod]
+    int* loc_ptr = nullptr;          // [n_atoms+1]
+    int* loc_idx = nullptr;          // local orbital lists
+    size_t vertex_len = 0;
+};
+
+struct gw_chi0 {
+    gw_ctx* ctx = nullptr;
+    const gw_mol* mol = nullptr;
+    gw_grid grid{};
+    gw_precision prec = GW_FP64;
+    int n_pair = 0, n_rank = 0, n_sub = 0;
+    int j_lo = 0, j_hi = 0;          // band of nonzero spectral bins (inclusive)
+    int nb_bins = 0;                 // number of pair bins j_lo..j_lo+nb_bins-1
+    int L = 0, logL = 0;             // FFT length 2*n_omega
+    // pair table (sorted)
+    int* pE = nullptr; int* pF = nullptr; int* pBin = nullptr;
+    double* pDelta = nullptr; double* pFrac = nullptr;
+    int* seg = nullptr;              // [nb_bins+1]
+    double* Z = nullptr;             // [n_prod*n_sub] (nullptr for Cholesky basis)
+    double* Zup = nullptr;           // [n_prod*n_sub]
+    double* Ut = nullptr;            // [n_sub*n_pair] U transposed
+    double2* tw = nullptr;           // [L/2] exp(-2 pi i k/L)
+    double2* C1 = nullptr;           // [L] FFT of the Toeplitz kernel
+    double2* C2 = nullptr;           // [L] FFT of the Hankel kernel
+    double2* chi0 = nullptr;         // [n_omega*n_sub*n_sub], lower triangle valid
+    // mixed precision copies
+    float* Ut32 = nullptr;
+    float2* tw32 = nullptr; float2* C1_32 = nullptr; float2* C2_32 = nullptr;
+    float2* chi0_32 = nullptr;
+};
+
+struct gw_W {
+    gw_ctx* ctx = nullptr;
+    const gw_chi0* chi0 = nullptr;
+    double2* fac = nullptr;          // [n_omega*n*n] strict lower L, diagonal D
+    float2* fac32 = nullptr;
+    double* piv = nullptr;           // [n_omega] min|d| / max|M|
+    double min_pivot_ratio = 0.0;
+};
+
+struct gw_sigma {
+    gw_ctx* ctx = nullptr;
+    const gw_W* W = nullptr;
+    int n_states = 0, R = 0;
+    std::vector<int> states;
+    int j0 = 0, n_sig = 0;
+    double* c = nullptr;             // [R*n_omega]
+    double* sig = nullptr;           // [n_states*n_sig]
+    double2* sigc = nullptr;         // [n_states*(2N-1)]
+    double* sx = nullptr;            // [n_states]
+    double* eks = nullptr;           // [n_states]
+};
+
+// ------------------------------------------------------------------ launchers
+// pairs.cu
+void launch_pair_table(gw_ctx* ctx, const gw_mol* mol, gw_chi0* c);
+void launch_invert_perm(gw_ctx* ctx, const gw_chi0* c, int* rank_of);
+// vertex.cu: out[mu*ld + col(e,f)] = sum_ab X[L_a,Es[e]] V^mu_ab X[L_b,Fs[f]],
+// col(e,f) = map ? map[e*nF+f] : e*nF+f
+void launch_vertex_contract(gw_ctx* ctx, const gw_mol* mol, const int* Es, int nE,
+                            const int* Fs, int nF, const int* map, double* out, long long ld);
+// gemm.cu: C = alpha*op(A) op(B) + beta*C, row-major, batched by stride.
+void gemm_f64(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, double alpha,
+              const double* A, long long lda, const double* B, long long ldb, double beta,
+              double* C, long long ldc, int batch = 1, long long sA = 0, long long sB = 0,
+              long long sC = 0);
+// linalg.cu
+void cholesky_lower(gw_ctx* ctx, double* A, int n);          // in place, zeroes upper
+int jacobi_eigh(gw_ctx* ctx, double* A, int n, double* evals, double* evecs);  // returns sweeps
+void select_top_scaled(gw_ctx* ctx, const double* evals, const double* evecs, int n,
+                       int n_sub, double* Bsel);
+// chi0.cu
+void launch_fft_tables(gw_ctx* ctx, gw_chi0* c);
+void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c);
+void launch_spectral_readback(gw_ctx* ctx, const gw_chi0* c, int j0, int nj, double* A);
+// screen.cu
+void launch_ldlt(gw_ctx* ctx, gw_W* W);
+void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* c);
+void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work);
+// sigma.cu
+void launch_sigma_grid(gw_ctx* ctx, gw_sigma* s);
+void launch_sigma_c(gw_ctx* ctx, gw_sigma* s);
+void launch_sigma_x(gw_ctx* ctx, gw_sigma* s, const double* Vnk, const double* T, int ld);
+void launch_qp(gw_ctx* ctx, const gw_sigma* s, const double* vxc, double* e, double* z, int* st);
+// utilities (misc kernels in linalg.cu)
+void launch_split_complex(gw_ctx* ctx, const double2* z, double* re, double* im, size_t n);
+
+// ------------------------------------------------------------------ complex
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ inline float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }

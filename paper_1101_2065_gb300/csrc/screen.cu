@@ -1,0 +1,291 @@
+// a5 + a6: screening and self-energy forms, one frequency per CTA.
+//
+// a5  M_k = 1 - chi0_k is complex symmetric (chi0 is symmetric in the real
+//     product basis, Sec. 4).  It is factorised in place as M_k = L D L^T
+//     (unit lower L, diagonal D, no pivoting) by a right-looking blocked
+//     algorithm: 16-column panels, diagonal block in shared memory, rows
+//     below solved against it, trailing lower triangle updated by 32x32
+//     tiles.  chi^RPA_k = M_k^-1 chi0_k = M_k^-1 - 1 (Eq. chi_RPA) is never
+//     formed on the hot path: the forms only need M_k^-1.
+// a6  c_r(s_k) = q_r^T gamma_k q_r with gamma_k = -(1/pi) Im chi^RPA_k, and
+//     q^T chi^RPA q = q^T M^-1 q - q^T q with q real, so
+//     c_r = -(1/pi) Im sum_i y_i^2 / d_i,  y = L^-1 q  (one forward
+//     substitution per right-hand side; D^-1 in the middle of the
+//     symmetric form).  c_r(s_0) = 0 (odd spectral function).
+#include <cmath>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int NB = 16;     // panel width
+constexpr int TS = 32;     // trailing tile
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    double r = 1.0 / (b.x * b.x + b.y * b.y);
+    return make_double2((a.x * b.x + a.y * b.y) * r, (a.y * b.x - a.x * b.y) * r);
+}
+
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {   // c + a*b
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {   // c - a*b
+    return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+
+__device__ double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if (threadIdx.x == 0) red[32] = w;
+    }
+    __syncthreads();
+    double r = red[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_ldlt(const double2* __restrict__ chi0, double2* __restrict__ fac, int n,
+                                              int N, double* __restrict__ piv, int* status) {
+    __shared__ double2 S[NB][NB + 1];
+    __shared__ double2 sL[TS][NB + 1];
+    __shared__ double2 sW[TS][NB + 1];
+    __shared__ double red[33];
+    const int tid = threadIdx.x;
+    const long long nn = (long long)n * n;
+    for (int k = blockIdx.x; k < N; k += gridDim.x) {
+        const double2* X = chi0 + k * nn;
+        double2* M = fac + k * nn;
+        double mx = 0.0;
+        for (long long t = tid; t < nn; t += blockDim.x) {
+            int i = (int)(t / n), j = (int)(t % n);
+            if (j > i) continue;
+            double2 x = X[t];
+            double2 m = make_double2((i == j ? 1.0 : 0.0) - x.x, -x.y);
+            M[t] = m;
+            mx = fmax(mx, hypot(m.x, m.y));
+        }
+        mx = block_max(mx, red);
+        double dmin = INFINITY;
+        for (int k0 = 0; k0 < n; k0 += NB) {
+            const int kb = min(NB, n - k0), k1 = k0 + kb;
+            // (a) diagonal block, unblocked L D L^T in shared memory
+            for (int t = tid; t < kb * kb; t += blockDim.x) {
+                int i = t / kb, j = t % kb;
+                if (j <= i) S[i][j] = M[(long long)(k0 + i) * n + k0 + j];
+            }
+            __syncthreads();
+            for (int j = 0; j < kb; ++j) {
+                double2 d = S[j][j];
+                for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[i][j] = cdiv(S[i][j], d);
+                __syncthreads();
+                for (int t = tid; t < kb * kb; t += blockDim.x) {
+                    int i = t / kb, l = t % kb;
+                    if (l > j && l <= i) S[i][l] = cfms(cmul(S[i][j], d), S[l][j], S[i][l]);
+                }
+                __syncthreads();
+            }
+            for (int t = tid; t < kb * kb; t += blockDim.x) {
+                int i = t / kb, j = t % kb;
+                if (j <= i) M[(long long)(k0 + i) * n + k0 + j] = S[i][j];
+            }
+            for (int j = 0; j < kb; ++j) dmin = fmin(dmin, hypot(S[j][j].x, S[j][j].y));
+            // (b) panel rows below: x D L11^T = a
+            for (int r = k1 + tid; r < n; r += blockDim.x) {
+                double2 x[NB];
+                double2* row = M + (long long)r * n + k0;
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    if (j < kb) {
+                        double2 a = row[j];
+#pragma unroll
+                        for (int p = 0; p < NB; ++p)
+                            if (p < j) a = cfms(cmul(x[p], S[p][p]), S[j][p], a);
+                        x[j] = cdiv(a, S[j][j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NB; ++j)
+                    if (j < kb) row[j] = x[j];
+            }
+            __syncthreads();
+            // (c) trailing update of the lower triangle: M22 -= L21 D L21^T
+            const int nt = (n - k1 + TS - 1) / TS;
+            const int ntile = nt * (nt + 1) / 2;
+            for (int tt = 0; tt < ntile; ++tt) {
+                int I = (int)((sqrt(8.0 * tt + 1.0) - 1.0) * 0.5);
+                while (I * (I + 1) / 2 > tt) --I;
+                while ((I + 1) * (I + 2) / 2 <= tt) ++I;
+                int J = tt - I * (I + 1) / 2;
+                const int r0 = k1 + I * TS, c0 = k1 + J * TS;
+                for (int t = tid; t < TS * NB; t += blockDim.x) {
+                    int rr = t / NB, p = t % NB;
+                    double2 lv = make_double2(0.0, 0.0), wv = make_double2(0.0, 0.0);
+                    if (p < kb) {
+                        if (r0 + rr < n) lv = M[(long long)(r0 + rr) * n + k0 + p];
+                        if (c0 + rr < n) wv = cmul(M[(long long)(c0 + rr) * n + k0 + p], S[p][p]);
+                    }
+                    sL[rr][p] = lv;
+                    sW[rr][p] = wv;
+                }
+                __syncthreads();
+                const int ty = tid / 16, tx = tid % 16;
+                double2 acc[2][2];
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) acc[a][b] = make_double2(0.0, 0.0);
+#pragma unroll
+                for (int p = 0; p < NB; ++p) {
+                    double2 l0 = sL[ty][p], l1 = sL[ty + 16][p];
+                    double2 w0 = sW[tx][p], w1 = sW[tx + 16][p];
+                    acc[0][0] = cfma(l0, w0, acc[0][0]);
+                    acc[0][1] = cfma(l0, w1, acc[0][1]);
+                    acc[1][0] = cfma(l1, w0, acc[1][0]);
+                    acc[1][1] = cfma(l1, w1, acc[1][1]);
+                }
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        int i = r0 + ty + 16 * a, j = c0 + tx + 16 * b;
+                        if (i < n && j <= i) {
+                            double2* m = M + (long long)i * n + j;
+                            *m = csub(*m, acc[a][b]);
+                        }
+                    }
+                __syncthreads();
+            }
+        }
+        if (tid == 0) {
+            double ratio = dmin / (mx > 0.0 ? mx : 1.0);
+            piv[k] = ratio;
+            if (!(dmin > 0.0) || !isfinite(dmin)) atomicOr(status, ST_SINGULAR);
+        }
+        __syncthreads();
+    }
+}
+
+// c[r*N + k] = -(1/pi) Im sum_i y_i^2/d_i, y = L_k^-1 q_r, for k >= 1.
+__global__ void __launch_bounds__(256) k_forms(const double2* __restrict__ fac, int n, int N,
+                                               const double* __restrict__ Q, int R, int RC,
+                                               double* __restrict__ c) {
+    extern __shared__ double2 sY[];          // [n][RC]
+    __shared__ double2 S[NB][NB + 1];
+    __shared__ double2 sL[TS][NB + 1];
+    __shared__ double2 acc[256];
+    const int tid = threadIdx.x;
+    const long long nn = (long long)n * n;
+    if (blockIdx.x == 0)
+        for (int r = tid; r < R; r += blockDim.x) c[(long long)r * N] = 0.0;
+    for (int k = 1 + blockIdx.x; k < N; k += gridDim.x) {
+        const double2* F = fac + k * nn;
+        for (int rc0 = 0; rc0 < R; rc0 += RC) {
+            const int rc = min(RC, R - rc0);
+            for (long long t = tid; t < (long long)n * RC; t += blockDim.x) {
+                int i = (int)(t / RC), r = (int)(t % RC);
+                sY[t] = make_double2(r < rc ? Q[(long long)i * R + rc0 + r] : 0.0, 0.0);
+            }
+            if (tid < RC) acc[tid] = make_double2(0.0, 0.0);
+            __syncthreads();
+            for (int k0 = 0; k0 < n; k0 += NB) {
+                const int kb = min(NB, n - k0), k1 = k0 + kb;
+                for (int t = tid; t < kb * kb; t += blockDim.x) {
+                    int i = t / kb, j = t % kb;
+                    if (j <= i) S[i][j] = F[(long long)(k0 + i) * n + k0 + j];
+                }
+                __syncthreads();
+                if (tid < rc) {
+                    const int r = tid;
+                    double2 a = acc[r];
+                    for (int i = 0; i < kb; ++i) {
+                        double2 y = sY[(k0 + i) * RC + r];
+                        for (int p = 0; p < i; ++p) y = cfms(S[i][p], sY[(k0 + p) * RC + r], y);
+                        sY[(k0 + i) * RC + r] = y;
+                        a = cadd(a, cdiv(cmul(y, y), S[i][i]));
+                    }
+                    acc[r] = a;
+                }
+                __syncthreads();
+                for (int r0 = k1; r0 < n; r0 += TS) {
+                    for (int t = tid; t < TS * NB; t += blockDim.x) {
+                        int rr = t / NB, p = t % NB;
+                        sL[rr][p] = (p < kb && r0 + rr < n) ? F[(long long)(r0 + rr) * n + k0 + p] : make_double2(0.0, 0.0);
+                    }
+                    __syncthreads();
+                    for (int t = tid; t < TS * rc; t += blockDim.x) {
+                        int rr = t / rc, r = t % rc;
+                        int i = r0 + rr;
+                        if (i >= n) continue;
+                        double2 y = sY[i * RC + r];
+#pragma unroll
+                        for (int p = 0; p < NB; ++p)
+                            if (p < kb) y = cfms(sL[rr][p], sY[(k0 + p) * RC + r], y);
+                        sY[i * RC + r] = y;
+                    }
+                    __syncthreads();
+                }
+            }
+            if (tid < rc) c[(long long)(rc0 + tid) * N + k] = -acc[tid].y / M_PI;
+            __syncthreads();
+        }
+    }
+}
+
+// out = M_k^-1 - 1 = chi^RPA_k from the factors (one CTA; test read-back).
+__global__ void __launch_bounds__(256) k_ldlt_inverse(const double2* __restrict__ F, int n, double2* __restrict__ X) {
+    // column c of X solves L D L^T x = e_c
+    for (int col = threadIdx.x; col < n; col += blockDim.x) {
+        double2* x = X + (long long)col;      // strided column (row-major X)
+        for (int i = 0; i < n; ++i) x[(long long)i * n] = make_double2(i == col ? 1.0 : 0.0, 0.0);
+        for (int i = 0; i < n; ++i) {
+            double2 y = x[(long long)i * n];
+            for (int p = 0; p < i; ++p) y = cfms(F[(long long)i * n + p], x[(long long)p * n], y);
+            x[(long long)i * n] = y;
+        }
+        for (int i = 0; i < n; ++i) x[(long long)i * n] = cdiv(x[(long long)i * n], F[(long long)i * n + i]);
+        for (int i = n - 1; i >= 0; --i) {
+            double2 y = x[(long long)i * n];
+            for (int p = i + 1; p < n; ++p) y = cfms(F[(long long)p * n + i], x[(long long)p * n], y);
+            x[(long long)i * n] = y;
+        }
+        x[(long long)col * n].x -= 1.0;
+    }
+}
+
+}  // namespace
+
+void launch_ldlt(gw_ctx* ctx, gw_W* W) {
+    const gw_chi0* c = W->chi0;
+    const int n = c->n_sub, N = c->grid.n_omega;
+    int grid = std::min(N, ctx->num_sms);   // 224 registers: one CTA per SM
+    k_ldlt<<<grid, 256, 0, ctx->stream>>>(c->chi0, W->fac, n, N, W->piv, ctx->d_status);
+    LAUNCH_CHECK(ctx, "k_ldlt");
+}
+
+void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
+    const gw_chi0* c = W->chi0;
+    const int n = c->n_sub, N = c->grid.n_omega;
+    const size_t budget = 190 * 1024;
+    int rc_max = (int)std::min<size_t>(256, budget / (sizeof(double2) * (size_t)n));
+    if (rc_max < 1) gw_throw(GW_ERR_INVALID_ARG, "n_sub too large for the binary64 forms kernel");
+    int chunks = div_up(R, rc_max);
+    int RC = div_up(R, chunks);
+    size_t smem = sizeof(double2) * (size_t)n * RC;
+    CUDA_CHECK(cudaFuncSetAttribute(k_forms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = std::min(N - 1, ctx->num_sms);
+    k_forms<<<std::max(grid, 1), 256, smem, ctx->stream>>>(W->fac, n, N, Q, R, RC, cout);
+    LAUNCH_CHECK(ctx, "k_forms");
+}
+
+void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work) {
+    (void)work;
+    const gw_chi0* c = W->chi0;
+    const long long nn = (long long)c->n_sub * c->n_sub;
+    k_ldlt_inverse<<<1, 256, 0, ctx->stream>>>(W->fac + k * nn, c->n_sub, out);
+    LAUNCH_CHECK(ctx, "k_ldlt_inverse");
+}

@@ -1,0 +1,368 @@
+"""Thin Python binding of libgw.so (C ABI in include/gw.h).
+
+Argument marshalling only: every step of the GW path runs in the library's
+CUDA kernels.  Importing this module fails loudly when the compiled library
+is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+GW_OK = 0
+ERRORS = {
+    -1: "GW_ERR_INVALID_ARG", -2: "GW_ERR_NOT_SPD", -3: "GW_ERR_GRID", -4: "GW_ERR_RANK",
+    -5: "GW_ERR_SINGULAR", -6: "GW_ERR_NO_CONVERGENCE", -7: "GW_ERR_OOM", -8: "GW_ERR_ADMISSION",
+    -9: "GW_ERR_TIMEOUT", -10: "GW_ERR_CUDA",
+}
+GW_FP64 = 0
+GW_MIXED = 1
+
+
+class GWError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MoleculeDesc(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("n_orb", C.c_int), ("n_occ", C.c_int), ("n_prod", C.c_int),
+                ("n_sub", C.c_int),
+                ("atom_norb", C.POINTER(C.c_int)), ("atom_nprod", C.POINTER(C.c_int)),
+                ("nbr_ptr", C.POINTER(C.c_int)), ("nbr_idx", C.POINTER(C.c_int)),
+                ("eps", C.POINTER(C.c_double)), ("X", C.POINTER(C.c_double)),
+                ("vertex", C.POINTER(C.c_double)), ("vertex_off", C.POINTER(C.c_longlong)),
+                ("v", C.POINTER(C.c_double)), ("Z", C.POINTER(C.c_double))]
+
+
+class Grid(C.Structure):
+    _fields_ = [("n_omega", C.c_int), ("d_omega", C.c_double), ("eta", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_orb", C.c_int), ("n_occ", C.c_int), ("n_prod", C.c_int), ("n_sub", C.c_int),
+                ("n_pair", C.c_int), ("n_rank", C.c_int), ("n_omega", C.c_int), ("j_lo", C.c_int),
+                ("j_hi", C.c_int), ("precision", C.c_int), ("min_pivot_ratio", C.c_double)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libgw.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libgw.so not built at {path}; run paper_1101_2065_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    pp = C.POINTER(C.c_void_p)
+    sigs = {
+        "gw_version": ([], C.c_char_p),
+        "gw_ctx_create": ([pp, I, C.c_size_t, P], I),
+        "gw_ctx_destroy": ([P], None),
+        "gw_last_error": ([P], C.c_char_p),
+        "gw_ctx_bytes_in_use": ([P], C.c_size_t),
+        "gw_ctx_launch_count": ([P], C.c_longlong),
+        "gw_mol_upload": ([P, C.POINTER(MoleculeDesc), pp], I),
+        "gw_mol_free": ([P], None),
+        "gw_build_chi0": ([P, P, C.POINTER(Grid), I, pp], I),
+        "gw_screen_W": ([P, P, pp], I),
+        "gw_sigma_diag": ([P, P, C.POINTER(C.c_int), I, pp], I),
+        "gw_qp_solve": ([P, P, P, P, P, P], I),
+        "gw_solve_host": ([P, C.POINTER(MoleculeDesc), C.POINTER(Grid), I, P, I, P, P, P, P, P], I),
+        "gw_chi0_free": ([P], None),
+        "gw_W_free": ([P], None),
+        "gw_sigma_free": ([P], None),
+        "gw_chi0_info": ([P, C.POINTER(Info)], I),
+        "gw_W_info": ([P, C.POINTER(Info)], I),
+        "gw_chi0_copy_pairs": ([P, P, P, P, P, P, P], I),
+        "gw_chi0_copy_basis": ([P, P, P, P], I),
+        "gw_chi0_copy_U": ([P, P, P], I),
+        "gw_chi0_copy_spectral": ([P, P, I, I, P], I),
+        "gw_chi0_copy": ([P, P, I, I, P], I),
+        "gw_W_copy_chi_rpa": ([P, P, P, I, P], I),
+        "gw_W_copy_full": ([P, P, P, I, P], I),
+        "gw_sigma_copy": ([P, P, P, P, P, P], I),
+        "gw_sigma_grid": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int)], I),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _LIB = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(ctx, code):
+    if code != GW_OK:
+        msg = load().gw_last_error(ctx.handle if ctx is not None else None)
+        raise GWError(code, msg.decode() if msg else "")
+
+
+class Context:
+    """Device, stream and HBM budget (gw_ctx)."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0, stream=None):
+        lib = load()
+        h = C.c_void_p()
+        code = lib.gw_ctx_create(C.byref(h), device, hbm_budget_bytes, stream)
+        if code != GW_OK:
+            raise GWError(code, "gw_ctx_create failed")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().gw_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def bytes_in_use(self):
+        return load().gw_ctx_bytes_in_use(self.handle)
+
+    @property
+    def launch_count(self):
+        return load().gw_ctx_launch_count(self.handle)
+
+
+class _Desc:
+    """Keeps the contiguous host arrays of a molecule alive for the C call."""
+
+    def __init__(self, mol, Z=None, pinned=False):
+        def a(x, dt):
+            x = np.ascontiguousarray(np.asarray(x), dtype=dt)
+            return x
+        self.atom_norb = a(mol.atom_norb, np.int32)
+        self.atom_nprod = a(mol.atom_nprod, np.int32)
+        self.nbr_ptr = a(mol.nbr_ptr, np.int32)
+        self.nbr_idx = a(mol.nbr_idx, np.int32) if len(mol.nbr_idx) else np.zeros(1, np.int32)
+        self.eps = a(mol.eps, np.float64)
+        self.X = a(mol.X, np.float64)
+        self.vertex = a(mol.vertex, np.float64)
+        self.vertex_off = a(mol.vertex_off, np.int64)
+        self.v = a(mol.v, np.float64)
+        self.Z = None if Z is None else a(Z, np.float64)
+        self.s = MoleculeDesc(
+            int(len(self.atom_norb)), int(self.atom_norb.sum()), int(mol.n_occ), int(self.atom_nprod.sum()),
+            int(mol.n_sub),
+            self.atom_norb.ctypes.data_as(C.POINTER(C.c_int)), self.atom_nprod.ctypes.data_as(C.POINTER(C.c_int)),
+            self.nbr_ptr.ctypes.data_as(C.POINTER(C.c_int)), self.nbr_idx.ctypes.data_as(C.POINTER(C.c_int)),
+            self.eps.ctypes.data_as(C.POINTER(C.c_double)), self.X.ctypes.data_as(C.POINTER(C.c_double)),
+            self.vertex.ctypes.data_as(C.POINTER(C.c_double)),
+            self.vertex_off.ctypes.data_as(C.POINTER(C.c_longlong)),
+            self.v.ctypes.data_as(C.POINTER(C.c_double)),
+            None if self.Z is None else self.Z.ctypes.data_as(C.POINTER(C.c_double)))
+
+
+def make_grid(grid):
+    return Grid(int(grid.n_omega), float(grid.d_omega), float(grid.eta))
+
+
+class _Handle:
+    _free = None
+
+    def __init__(self, ctx, h):
+        self.ctx, self.handle = ctx, h
+
+    def free(self):
+        if self.handle:
+            getattr(load(), self._free)(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Mol(_Handle):
+    _free = "gw_mol_free"
+
+
+class Chi0(_Handle):
+    _free = "gw_chi0_free"
+
+    def info(self):
+        i = Info()
+        _check(self.ctx, load().gw_chi0_info(self.handle, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in Info._fields_}
+
+    def pairs(self):
+        n = self.info()["n_pair"]
+        E = np.zeros(n, np.int32); F = np.zeros(n, np.int32); b = np.zeros(n, np.int32)
+        d = np.zeros(n); f = np.zeros(n)
+        _check(self.ctx, load().gw_chi0_copy_pairs(self.ctx.handle, self.handle, _ptr(E), _ptr(F), _ptr(d),
+                                                   _ptr(b), _ptr(f)))
+        return dict(E=E, F=F, delta=d, bin=b, frac=f)
+
+    def basis(self):
+        i = self.info()
+        Zup = np.zeros((i["n_prod"], i["n_sub"]))
+        Z = np.zeros_like(Zup) if i["n_rank"] > 0 or i["n_sub"] != i["n_prod"] else None
+        code = load().gw_chi0_copy_basis(self.ctx.handle, self.handle, _ptr(Z), _ptr(Zup))
+        if code != GW_OK and Z is not None:
+            Z = None
+            code = load().gw_chi0_copy_basis(self.ctx.handle, self.handle, None, _ptr(Zup))
+        _check(self.ctx, code)
+        return Z, Zup
+
+    def U(self):
+        i = self.info()
+        U = np.zeros((i["n_pair"], i["n_sub"]))
+        _check(self.ctx, load().gw_chi0_copy_U(self.ctx.handle, self.handle, _ptr(U)))
+        return U
+
+    def spectral(self, j0, nj):
+        n = self.info()["n_sub"]
+        A = np.zeros((nj, n, n))
+        _check(self.ctx, load().gw_chi0_copy_spectral(self.ctx.handle, self.handle, j0, nj, _ptr(A)))
+        return A
+
+    def chi0(self, k0, nk):
+        n = self.info()["n_sub"]
+        out = np.zeros((nk, n, n), np.complex128)
+        _check(self.ctx, load().gw_chi0_copy(self.ctx.handle, self.handle, k0, nk, _ptr(out)))
+        return out
+
+
+class W(_Handle):
+    _free = "gw_W_free"
+
+    def info(self):
+        i = Info()
+        _check(self.ctx, load().gw_W_info(self.handle, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in Info._fields_}
+
+    def chi_rpa(self, freqs):
+        freqs = np.ascontiguousarray(freqs, np.int32)
+        n = self.info()["n_sub"]
+        out = np.zeros((freqs.size, n, n), np.complex128)
+        _check(self.ctx, load().gw_W_copy_chi_rpa(self.ctx.handle, self.handle, _ptr(freqs), freqs.size, _ptr(out)))
+        return out
+
+    def full(self, freqs):
+        freqs = np.ascontiguousarray(freqs, np.int32)
+        n = self.info()["n_prod"]
+        out = np.zeros((freqs.size, n, n), np.complex128)
+        _check(self.ctx, load().gw_W_copy_full(self.ctx.handle, self.handle, _ptr(freqs), freqs.size, _ptr(out)))
+        return out
+
+
+class Sigma(_Handle):
+    _free = "gw_sigma_free"
+
+    def __init__(self, ctx, h, states, n_orb, n_omega):
+        super().__init__(ctx, h)
+        self.states, self.n_orb, self.n_omega = list(states), n_orb, n_omega
+
+    def grid(self):
+        j0, ns = C.c_int(), C.c_int()
+        _check(self.ctx, load().gw_sigma_grid(self.handle, C.byref(j0), C.byref(ns)))
+        return j0.value, ns.value
+
+    def copy(self):
+        j0, n_sig = self.grid()
+        ns, N = len(self.states), self.n_omega
+        c = np.zeros((ns, self.n_orb, N))
+        sig = np.zeros((ns, n_sig))
+        sigc = np.zeros((ns, 2 * N - 1), np.complex128)
+        sx = np.zeros(ns)
+        _check(self.ctx, load().gw_sigma_copy(self.ctx.handle, self.handle, _ptr(c), _ptr(sig), _ptr(sigc), _ptr(sx)))
+        return dict(c=c, sigma=sig, j0=j0, sigma_c=sigc, sigma_x=sx)
+
+
+# ------------------------------------------------------------------ entry points
+def gw_mol_upload(ctx, mol, Z=None):
+    d = _Desc(mol, Z)
+    h = C.c_void_p()
+    _check(ctx, load().gw_mol_upload(ctx.handle, C.byref(d.s), C.byref(h)))
+    m = Mol(ctx, h)
+    m.n_orb, m.n_occ = int(d.s.n_orb), int(d.s.n_occ)
+    m.eps = d.eps.copy()
+    return m
+
+
+def gw_build_chi0(ctx, mol, grid, prec=GW_FP64):
+    g = make_grid(grid)
+    h = C.c_void_p()
+    _check(ctx, load().gw_build_chi0(ctx.handle, mol.handle, C.byref(g), int(prec), C.byref(h)))
+    c = Chi0(ctx, h)
+    c.mol, c.n_omega = mol, int(grid.n_omega)
+    return c
+
+
+def gw_screen_W(ctx, chi0):
+    h = C.c_void_p()
+    _check(ctx, load().gw_screen_W(ctx.handle, chi0.handle, C.byref(h)))
+    w = W(ctx, h)
+    w.chi0 = chi0
+    return w
+
+
+def gw_sigma_diag(ctx, W_, states):
+    st = np.ascontiguousarray(states, np.int32)
+    h = C.c_void_p()
+    _check(ctx, load().gw_sigma_diag(ctx.handle, W_.handle, st.ctypes.data_as(C.POINTER(C.c_int)), st.size,
+                                     C.byref(h)))
+    s = Sigma(ctx, h, st, W_.chi0.mol.n_orb, W_.chi0.n_omega)
+    s.W = W_
+    return s
+
+
+def gw_qp_solve(ctx, sigma, vxc=None):
+    n = len(sigma.states)
+    e = np.zeros(n); z = np.zeros(n); st = np.zeros(n, np.int32)
+    v = None if vxc is None else np.ascontiguousarray(np.broadcast_to(np.asarray(vxc, float), (n,)))
+    _check(ctx, load().gw_qp_solve(ctx.handle, sigma.handle, _ptr(v), _ptr(e), _ptr(z), _ptr(st)))
+    return e, z, st
+
+
+def gw_solve_host(ctx, mol, grid, states, prec=GW_FP64, vxc=None, desc=None):
+    """One GW solve from host arrays to host results (upload included)."""
+    d = desc if desc is not None else _Desc(mol)
+    g = make_grid(grid)
+    st = np.ascontiguousarray(states, np.int32)
+    n = st.size
+    e = np.zeros(n); z = np.zeros(n); rs = np.zeros(n, np.int32); sx = np.zeros(n)
+    v = None if vxc is None else np.ascontiguousarray(np.broadcast_to(np.asarray(vxc, float), (n,)))
+    _check(ctx, load().gw_solve_host(ctx.handle, C.byref(d.s), C.byref(g), int(prec), _ptr(st), n, _ptr(v),
+                                     _ptr(e), _ptr(z), _ptr(rs), _ptr(sx)))
+    return e, z, rs, sx
+
+
+def solve(ctx, mol, grid, states=None, prec=GW_FP64, vxc=None, Z=None):
+    """Device-resident pipeline a0..a8; returns (handles, e_qp, z, status)."""
+    if states is None:
+        states = [mol.n_occ - 1, mol.n_occ]
+    m = gw_mol_upload(ctx, mol, Z)
+    c = gw_build_chi0(ctx, m, grid, prec)
+    w = gw_screen_W(ctx, c)
+    s = gw_sigma_diag(ctx, w, states)
+    e, z, st = gw_qp_solve(ctx, s, vxc)
+    return dict(mol=m, chi0=c, W=w, sigma=s), e, z, st

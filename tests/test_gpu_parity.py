@@ -1,0 +1,247 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar: integers bit-exact; binary64 results within relative Frobenius error
+1e-10 of the oracle (quasiparticle energies within 1e-9 Ha).  Elementwise
+checks of basis-dependent quantities (chi0_mn, chi^RPA_mn) pass the
+oracle's compression basis Z to the library; with the library's own Z only
+basis-invariant results are compared (W^{mu nu}, c_nk, sigma, Sigma, QP).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import gw as og
+from tests import pins
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="session")
+def gwlib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1101_2065_gb300 as gw
+    return gw
+
+
+@pytest.fixture(scope="session")
+def ctx(gwlib):
+    c = gwlib.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="session")
+def cfg2():
+    return synth.make_config(2)
+
+
+@pytest.fixture(scope="session")
+def cfg2_oracle(cfg2):
+    mol, grid = cfg2
+    return oracle.solve(mol, grid, keep_W_freqs=[1, 100, 400, 1023])
+
+
+def _run(gw, ctx, mol, grid, Z=None, states=None, vxc=None):
+    return gw.solve(ctx, mol, grid, states=states, vxc=vxc, Z=Z)
+
+
+def _free(h):
+    for k in ("sigma", "W", "chi0", "mol"):
+        h[k].free()
+
+
+# ------------------------------------------------------------------ config 1
+def test_chain4_uncompressed_all_steps(gwlib, ctx, cfg1, cfg1_oracle):
+    mol, grid = cfg1
+    r = cfg1_oracle
+    h, e, z, st = _run(gwlib, ctx, mol, grid)
+    try:
+        c = h["chi0"]
+        p = c.pairs()
+        assert np.array_equal(p["E"], r["pairs"]["E"]) and np.array_equal(p["F"], r["pairs"]["F"])
+        assert np.array_equal(p["bin"], r["pairs"]["bin"])
+        assert np.array_equal(p["delta"], r["pairs"]["delta"]) and np.array_equal(p["frac"], r["pairs"]["frac"])
+        _, Zup = c.basis()
+        assert rel(Zup, r["Zup"]) < TOL
+        assert rel(c.U(), r["U"]) < TOL
+        info = c.info()
+        A = c.spectral(info["j_lo"], info["j_hi"] - info["j_lo"] + 1)
+        assert rel(A, r["A"][info["j_lo"]:info["j_hi"] + 1]) < TOL
+        assert np.abs(r["A"][:info["j_lo"]]).max() == 0 and np.abs(r["A"][info["j_hi"] + 1:]).max() == 0
+        chi0 = c.chi0(0, grid.n_omega)
+        assert rel(chi0, r["chi0"]) < TOL
+        ks = [0, 1, 77, 128, 255]
+        assert rel(h["W"].chi_rpa(ks), r["chi_rpa"][ks]) < TOL
+        s = h["sigma"].copy()
+        assert rel(s["c"], r["c"]) < TOL
+        assert s["j0"] == r["j0"]
+        assert rel(s["sigma"], r["sigma"]) < TOL
+        assert rel(s["sigma_c"], r["sigma_c"]) < TOL
+        assert rel(s["sigma_x"], r["sigma_x"]) < 1e-12
+        assert np.abs(e - r["e_qp"]).max() < 1e-9
+        assert np.abs(z - r["z"]).max() < 1e-8
+        assert np.array_equal(st, r["status"])
+    finally:
+        _free(h)
+
+
+def test_chain4_full_W_invariant(gwlib, ctx, cfg1, cfg1_oracle):
+    mol, grid = cfg1
+    r = cfg1_oracle
+    h, *_ = _run(gwlib, ctx, mol, grid)
+    try:
+        ks = [3, 140]
+        Wg = h["W"].full(ks)
+        Wo = og.screened_W(mol, r["Zup"], r["chi_rpa"][ks])
+        assert rel(Wg - mol.v, Wo - mol.v) < TOL
+    finally:
+        _free(h)
+
+
+# ------------------------------------------------------------------ config 2 (bench workload)
+def test_ring12_elementwise_with_oracle_basis(gwlib, ctx, cfg2, cfg2_oracle):
+    mol, grid = cfg2
+    r = cfg2_oracle
+    h, e, z, st = _run(gwlib, ctx, mol, grid, Z=r["Z"])
+    try:
+        c = h["chi0"]
+        _, Zup = c.basis()
+        assert rel(Zup, r["Zup"]) < TOL
+        assert rel(c.U(), r["U"]) < TOL
+        for k0 in (0, 300, 700):
+            assert rel(c.chi0(k0, 64), r["chi0"][k0:k0 + 64]) < TOL
+        ks = [1, 100, 400, 1023]
+        assert rel(h["W"].chi_rpa(ks), r["chi_rpa"][ks]) < TOL
+        s = h["sigma"].copy()
+        assert rel(s["c"], r["c"]) < TOL
+        assert rel(s["sigma"], r["sigma"]) < TOL
+        assert rel(s["sigma_c"], r["sigma_c"]) < TOL
+        assert rel(s["sigma_x"], r["sigma_x"]) < 1e-12
+        assert np.abs(e - r["e_qp"]).max() < 1e-9
+        assert np.array_equal(st, r["status"])
+    finally:
+        _free(h)
+
+
+def test_ring12_own_basis_invariants(gwlib, ctx, cfg2, cfg2_oracle):
+    """The library's own Jacobi-built basis: invariant results only."""
+    mol, grid = cfg2
+    r = cfg2_oracle
+    h, e, z, st = _run(gwlib, ctx, mol, grid)
+    try:
+        c = h["chi0"]
+        info = c.info()
+        assert info["n_rank"] == r["n_rank"] == 540
+        Z, Zup = c.basis()
+        assert np.abs(Z.T @ mol.v @ Z - np.eye(mol.n_sub)).max() < 1e-9
+        # same subspace: projectors onto span(Zup) w.r.t. the v^-1 metric agree
+        P_g = Z @ Zup.T
+        P_o = r["Z"] @ r["Zup"].T
+        assert rel(P_g, P_o) < 1e-9
+        Wg = h["W"].full([1, 100, 400, 1023])
+        assert rel(Wg - mol.v, r["W"] - mol.v) < 1e-9
+        s = h["sigma"].copy()
+        assert rel(s["c"], r["c"]) < 1e-9
+        assert rel(s["sigma"], r["sigma"]) < 1e-9
+        assert np.abs(e - r["e_qp"]).max() < 1e-8
+        assert np.array_equal(st, r["status"])
+    finally:
+        _free(h)
+
+
+def test_end_to_end_host_call_matches_resident_path(gwlib, ctx, cfg1):
+    mol, grid = cfg1
+    states = [mol.n_occ - 1, mol.n_occ]
+    h, e, z, st = _run(gwlib, ctx, mol, grid)
+    _free(h)
+    e2, z2, st2, sx = gwlib.gw_solve_host(ctx, mol, grid, states)
+    assert np.array_equal(e, e2) and np.array_equal(z, z2) and np.array_equal(st, st2)
+
+
+# ------------------------------------------------------------------ small and edge cases
+def test_two_level_model(gwlib, ctx):
+    mol = synth.molecules.two_level(0.3, 1.2, -0.3, 0.2)
+    dw = 2.0 ** -9
+    grid = synth.Grid(1024, dw, 1.5 * dw)
+    Z = np.array([[1.0 / math.sqrt(1.2)]])
+    r = oracle.solve(mol, grid, states=[0, 1], vxc=0.0, Z=Z)
+    h, e, z, st = _run(gwlib, ctx, mol, grid, Z=Z, states=[0, 1], vxc=[0.0, 0.0])
+    try:
+        s = h["sigma"].copy()
+        assert rel(s["sigma_c"], r["sigma_c"]) < TOL
+        assert np.abs(e - r["e_qp"]).max() < 1e-9
+        assert np.array_equal(st, r["status"])
+    finally:
+        _free(h)
+
+
+@pytest.mark.parametrize("n_orb,n_occ,n_prod,n_sub,atoms", [
+    (8, 3, 8, 4, 2),       # compressed, n_rank = 15 (odd: padded Jacobi)
+    (7, 2, 9, 9, 1),       # uncompressed, ragged sizes
+    (12, 5, 40, 17, 2),    # compressed, n_sub spans several 16-panels with a ragged tail
+])
+def test_small_molecules(gwlib, ctx, n_orb, n_occ, n_prod, n_sub, atoms):
+    mol = pins.tiny_molecule(n_orb=n_orb, n_occ=n_occ, n_prod=n_prod, n_sub=n_sub, atoms=atoms, seed=21)
+    grid = synth.Grid(512)
+    states = list(range(n_orb))                       # every state, not only HOMO/LUMO
+    r = oracle.solve(mol, grid, states=states)
+    h, e, z, st = _run(gwlib, ctx, mol, grid, states=states)
+    try:
+        s = h["sigma"].copy()
+        assert rel(s["c"], r["c"]) < 1e-9
+        assert rel(s["sigma_c"], r["sigma_c"]) < 1e-9
+        assert rel(s["sigma_x"], r["sigma_x"]) < 1e-12
+        assert np.abs(e - r["e_qp"]).max() < 1e-8
+        assert np.array_equal(st, r["status"])
+        Wg = h["W"].full([7, 200])
+        Wo = og.screened_W(mol, r["Zup"], r["chi_rpa"][[7, 200]])
+        assert rel(Wg - mol.v, Wo - mol.v) < 1e-9
+    finally:
+        _free(h)
+
+
+def test_grid_error(gwlib, ctx, cfg1):
+    mol, _ = cfg1
+    with pytest.raises(gwlib.GWError) as ei:
+        _run(gwlib, ctx, mol, synth.Grid(128))            # 1.4 Ha > 128 * d_omega
+    assert ei.value.code == -3
+
+
+def test_not_spd(gwlib, ctx):
+    mol = pins.tiny_molecule(n_orb=6, n_occ=3, n_prod=5, seed=3)
+    mol.v = mol.v - 10.0 * np.eye(5)
+    with pytest.raises(gwlib.GWError) as ei:
+        _run(gwlib, ctx, mol, synth.Grid(512))
+    assert ei.value.code == -2
+
+
+def test_invalid_arguments(gwlib, ctx, cfg1):
+    mol, grid = cfg1
+    bad = synth.Grid(300)                                  # not a power of two
+    with pytest.raises(gwlib.GWError) as ei:
+        _run(gwlib, ctx, mol, bad)
+    assert ei.value.code == -1
+    before = ctx.bytes_in_use
+    m = gwlib.gw_mol_upload(ctx, mol)
+    c = gwlib.gw_build_chi0(ctx, m, grid)
+    w = gwlib.gw_screen_W(ctx, c)
+    try:
+        with pytest.raises(gwlib.GWError) as ei:
+            gwlib.gw_sigma_diag(ctx, w, [10_000])
+        assert ei.value.code == -1
+    finally:
+        w.free(); c.free(); m.free()
+    assert ctx.bytes_in_use == before                      # nothing leaked by the failures
