@@ -48,10 +48,54 @@ void ctx_free(gw_ctx* ctx, void* p) {
     cudaFreeAsync(p, ctx->stream);
 }
 
+static bool prof_match(const gw_ctx* ctx, const char* name) {
+    return ctx->prof_on && (ctx->prof_filter.empty() || ctx->prof_filter == name);
+}
+
+static cudaEvent_t prof_event(gw_ctx* ctx) {
+    if (!ctx->prof_pool.empty()) {
+        cudaEvent_t e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    CUDA_CHECK(cudaEventCreate(&e));
+    return e;
+}
+
+void prof_begin(gw_ctx* ctx, const char* name) {
+    if (!prof_match(ctx, name)) return;
+    cudaEvent_t e = prof_event(ctx);
+    CUDA_CHECK(cudaEventRecord(e, ctx->stream));
+    ctx->prof_pending = e;
+}
+
+static void prof_collect(gw_ctx* ctx) {
+    if (ctx->prof_recs.empty()) return;
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    for (auto& r : ctx->prof_recs) {
+        float ms = 0.f;
+        CUDA_CHECK(cudaEventElapsedTime(&ms, r.start, r.stop));
+        auto& acc = ctx->prof_acc[r.name];
+        acc.first += ms;
+        acc.second += 1;
+        ctx->prof_pool.push_back(r.start);
+        ctx->prof_pool.push_back(r.stop);
+    }
+    ctx->prof_recs.clear();
+}
+
 void after_launch(gw_ctx* ctx, const char* name) {
     ctx->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) gw_throw(GW_ERR_CUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e));
+    if (ctx->prof_pending && prof_match(ctx, name)) {
+        cudaEvent_t stop = prof_event(ctx);
+        CUDA_CHECK(cudaEventRecord(stop, ctx->stream));
+        ctx->prof_recs.push_back({name, ctx->prof_pending, stop});
+        ctx->prof_pending = nullptr;
+        if (ctx->prof_recs.size() > 4096) prof_collect(ctx);
+    }
 }
 
 void ctx_finish(gw_ctx* ctx, const char* where) {
@@ -149,6 +193,10 @@ extern "C" gw_status gw_ctx_create(gw_ctx** out, int device, size_t hbm_budget_b
 extern "C" void gw_ctx_destroy(gw_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& r : ctx->prof_recs) { cudaEventDestroy(r.start); cudaEventDestroy(r.stop); }
+    for (auto e : ctx->prof_pool) cudaEventDestroy(e);
+    if (ctx->prof_pending) cudaEventDestroy(ctx->prof_pending);
     for (auto& kv : ctx->blocks) cudaFreeAsync(kv.first, ctx->stream);
     ctx->blocks.clear();
     cudaStreamSynchronize(ctx->stream);
@@ -161,6 +209,28 @@ extern "C" void gw_ctx_destroy(gw_ctx* ctx) {
 extern "C" const char* gw_last_error(const gw_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 extern "C" size_t gw_ctx_bytes_in_use(const gw_ctx* ctx) { return ctx ? ctx->in_use : 0; }
 extern "C" long long gw_ctx_launch_count(const gw_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" gw_status gw_ctx_profile(gw_ctx* ctx, int enable, const char* kernel_name) {
+    if (!ctx) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    prof_collect(ctx);
+    ctx->prof_on = enable != 0;
+    ctx->prof_filter = kernel_name ? kernel_name : "";
+    ctx->prof_acc.clear();
+    API_END
+}
+
+extern "C" gw_status gw_ctx_profile_get(gw_ctx* ctx, const char* kernel_name, double* total_ms, long long* launches) {
+    if (!ctx || !kernel_name || !total_ms || !launches) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    prof_collect(ctx);
+    auto it = ctx->prof_acc.find(kernel_name);
+    *total_ms = it == ctx->prof_acc.end() ? 0.0 : it->second.first;
+    *launches = it == ctx->prof_acc.end() ? 0 : it->second.second;
+    API_END
+}
 
 // ======================================================================
 // molecule

@@ -200,12 +200,10 @@ void launch_fft_tables(gw_ctx* ctx, gw_chi0* c) {
     c->tw = dalloc<double2>(ctx, L / 2);
     c->C1 = dalloc<double2>(ctx, L);
     c->C2 = dalloc<double2>(ctx, L);
-    k_twiddles<<<div_up(L / 2, 256), 256, 0, ctx->stream>>>(c->tw, L);
-    LAUNCH_CHECK(ctx, "k_twiddles");
+    klaunch(ctx, "k_twiddles", k_twiddles, div_up(L / 2, 256), 256, 0, c->tw, L);
     size_t smem = 2 * (size_t)L * sizeof(double2);
     CUDA_CHECK(cudaFuncSetAttribute(k_kernel_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_kernel_spectra<<<2, 256, smem, ctx->stream>>>(c->tw, N, c->logL, c->grid.d_omega, c->grid.eta, c->C1, c->C2);
-    LAUNCH_CHECK(ctx, "k_kernel_spectra");
+    klaunch(ctx, "k_kernel_spectra", k_kernel_spectra, 2, 256, smem, c->tw, N, c->logL, c->grid.d_omega, c->grid.eta, c->C1, c->C2);
 }
 
 void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
@@ -217,15 +215,13 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
     int per_sm = std::max(1, (int)((228 * 1024) / (smem + 1024)));
     long long n_grp = ((long long)n * (n + 1) / 2 + 1) / 2;
     int grid = (int)std::min<long long>(n_grp, (long long)ctx->num_sms * per_sm);
-    k_chi0_fft<<<grid, 256, smem, ctx->stream>>>(c->Ut, c->n_pair, n, c->seg, c->pFrac, c->j_lo, c->nb_bins, N,
+    klaunch(ctx, "k_chi0_fft", k_chi0_fft, grid, 256, smem, c->Ut, c->n_pair, n, c->seg, c->pFrac, c->j_lo, c->nb_bins, N,
                                                  c->logL, c->tw, c->C1, c->C2, c->chi0);
-    LAUNCH_CHECK(ctx, "k_chi0_fft");
 }
 
 void launch_spectral_readback(gw_ctx* ctx, const gw_chi0* c, int j0, int nj, double* A) {
     long long tot = (long long)c->n_sub * c->n_sub * nj;
     if (tot == 0) return;
-    k_spectral_readback<<<div_up(tot, 256), 256, 0, ctx->stream>>>(c->Ut, c->n_pair, c->n_sub, c->seg, c->pFrac,
+    klaunch(ctx, "k_spectral_readback", k_spectral_readback, div_up(tot, 256), 256, 0, c->Ut, c->n_pair, c->n_sub, c->seg, c->pFrac,
                                                                    c->j_lo, c->nb_bins, j0, nj, A);
-    LAUNCH_CHECK(ctx, "k_spectral_readback");
 }

@@ -80,9 +80,7 @@ void gemm_f64(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, double alpha, 
               long long sB, long long sC) {
     if (M <= 0 || N <= 0) return;
     dim3 grid(div_up(N, BN), div_up(M, BM), batch);
-    if (!ta && !tb) k_dgemm<false, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
-    else if (ta && !tb) k_dgemm<true, false><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
-    else if (!ta && tb) k_dgemm<false, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
-    else k_dgemm<true, true><<<grid, 256, 0, ctx->stream>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
-    LAUNCH_CHECK(ctx, "k_dgemm");
+    auto kern = (!ta && !tb) ? k_dgemm<false, false> : (ta && !tb) ? k_dgemm<true, false>
+              : (!ta && tb) ? k_dgemm<false, true> : k_dgemm<true, true>;
+    klaunch(ctx, "k_dgemm", kern, grid, 256, 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
 }

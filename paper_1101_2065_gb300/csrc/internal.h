@@ -28,6 +28,11 @@ struct GwError {
     std::string msg;
 };
 
+struct ProfRec {
+    const char* name;
+    cudaEvent_t start, stop;
+};
+
 struct gw_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -41,6 +46,13 @@ struct gw_ctx {
     int* d_status = nullptr;
     int* h_status = nullptr;
     int num_sms = 0;
+    // optional CUDA-event timing of kernel launches whose name matches prof_filter
+    bool prof_on = false;
+    std::string prof_filter;
+    cudaEvent_t prof_pending = nullptr;     // start event recorded by prof_begin
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+    std::unordered_map<std::string, std::pair<double, long long>> prof_acc;
 };
 
 // Throws GwError; every extern "C" entry point catches and converts.
@@ -53,9 +65,20 @@ void ctx_free(gw_ctx* ctx, void* p);
 template <class T>
 T* dalloc(gw_ctx* ctx, size_t n) { return static_cast<T*>(ctx_alloc(ctx, n * sizeof(T))); }
 
-// Counts a launch and checks the launch error.
+// Counts a launch, checks the launch error and, when profiling is on,
+// closes the timing interval opened by prof_begin.
 void after_launch(gw_ctx* ctx, const char* name);
+void prof_begin(gw_ctx* ctx, const char* name);
 #define LAUNCH_CHECK(ctx, name) after_launch((ctx), (name))
+
+// Launch a kernel on the context stream with launch accounting.
+template <typename... KArgs, typename... Args>
+inline void klaunch(gw_ctx* ctx, const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                    Args... args) {
+    prof_begin(ctx, name);
+    kernel<<<grid, block, smem, ctx->stream>>>(args...);
+    after_launch(ctx, name);
+}
 
 // Synchronise the context stream and convert status bits into an error.
 void ctx_finish(gw_ctx* ctx, const char* where);

@@ -220,14 +220,12 @@ void cholesky_lower(gw_ctx* ctx, double* A, int n) {
     for (int k0 = 0; k0 < n; k0 += CNB) {
         int kb = std::min(CNB, n - k0), k1 = k0 + kb;
         int rows = n - k1;
-        k_chol_panel<<<std::max(1, div_up(rows, 256)), 256, 0, ctx->stream>>>(A, n, k0, kb, ctx->d_status);
-        LAUNCH_CHECK(ctx, "k_chol_panel");
+        klaunch(ctx, "k_chol_panel", k_chol_panel, std::max(1, div_up(rows, 256)), 256, 0, A, n, k0, kb, ctx->d_status);
         if (rows > 0)
             gemm_f64(ctx, false, true, rows, rows, kb, -1.0, A + (long long)k1 * n + k0, n, A + (long long)k1 * n + k0,
                      n, 1.0, A + (long long)k1 * n + k1, n);
     }
-    k_zero_upper<<<div_up((long long)n * n, 256), 256, 0, ctx->stream>>>(A, n);
-    LAUNCH_CHECK(ctx, "k_zero_upper");
+    klaunch(ctx, "k_zero_upper", k_zero_upper, div_up((long long)n * n, 256), 256, 0, A, n);
 }
 
 int jacobi_eigh(gw_ctx* ctx, double* g, int n, double* evals, double* evecs) {
@@ -243,14 +241,12 @@ int jacobi_eigh(gw_ctx* ctx, double* g, int n, double* evals, double* evecs) {
     double* V0 = evecs;
     int sweeps = 0;
     try {
-        k_jacobi_init<<<div_up(nn, 256), 256, 0, ctx->stream>>>(g, n, np, A0, V0);
-        LAUNCH_CHECK(ctx, "k_jacobi_init");
+        klaunch(ctx, "k_jacobi_init", k_jacobi_init, div_up(nn, 256), 256, 0, g, n, np, A0, V0);
         double *Ac = A0, *An = A1, *Vc = V0, *Vn = V1;
         bool ok = false;
         double prev = INFINITY;
         for (sweeps = 0; sweeps < 40; ++sweeps) {
-            k_jacobi_off<<<1, 1024, 0, ctx->stream>>>(Ac, n, np, off);
-            LAUNCH_CHECK(ctx, "k_jacobi_off");
+            klaunch(ctx, "k_jacobi_off", k_jacobi_off, 1, 1024, 0, Ac, n, np, off);
             CUDA_CHECK(cudaMemcpyAsync(hoff, off, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
             CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
             double o = hoff[0], d = hoff[1];
@@ -260,17 +256,14 @@ int jacobi_eigh(gw_ctx* ctx, double* g, int n, double* evals, double* evecs) {
             if (sweeps >= 3 && o >= 0.25 * prev && o <= 1e-24 * d) { ok = true; break; }
             prev = o;
             for (int r = 0; r < np - 1; ++r) {
-                k_jacobi_rot<<<div_up(np / 2, 128), 128, 0, ctx->stream>>>(Ac, np, r, rot);
-                LAUNCH_CHECK(ctx, "k_jacobi_rot");
-                k_jacobi_apply<<<div_up(2 * nn, 256), 256, 0, ctx->stream>>>(Ac, An, Vc, Vn, rot, np, r);
-                LAUNCH_CHECK(ctx, "k_jacobi_apply");
+                klaunch(ctx, "k_jacobi_rot", k_jacobi_rot, div_up(np / 2, 128), 128, 0, Ac, np, r, rot);
+                klaunch(ctx, "k_jacobi_apply", k_jacobi_apply, div_up(2 * nn, 256), 256, 0, Ac, An, Vc, Vn, rot, np, r);
                 std::swap(Ac, An);
                 std::swap(Vc, Vn);
             }
         }
         if (!ok) gw_throw(GW_ERR_NO_CONVERGENCE, "Jacobi eigensolver did not converge in 40 sweeps");
-        k_jacobi_diag<<<div_up(np, 256), 256, 0, ctx->stream>>>(Ac, np, evals);
-        LAUNCH_CHECK(ctx, "k_jacobi_diag");
+        klaunch(ctx, "k_jacobi_diag", k_jacobi_diag, div_up(np, 256), 256, 0, Ac, np, evals);
         if (Vc != evecs)
             CUDA_CHECK(cudaMemcpyAsync(evecs, Vc, nn * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
         CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
@@ -287,15 +280,12 @@ int jacobi_eigh(gw_ctx* ctx, double* g, int n, double* evals, double* evecs) {
 void select_top_scaled(gw_ctx* ctx, const double* evals, const double* evecs, int n, int n_sub, double* B) {
     const int np = n + (n & 1);
     int* sel = dalloc<int>(ctx, n_sub);
-    k_rank_desc<<<div_up(np, 256), 256, 0, ctx->stream>>>(evals, np, n_sub, sel);
-    LAUNCH_CHECK(ctx, "k_rank_desc");
-    k_scale_sel<<<div_up((long long)n * n_sub, 256), 256, 0, ctx->stream>>>(evals, evecs, n, np, n_sub, sel, B,
+    klaunch(ctx, "k_rank_desc", k_rank_desc, div_up(np, 256), 256, 0, evals, np, n_sub, sel);
+    klaunch(ctx, "k_scale_sel", k_scale_sel, div_up((long long)n * n_sub, 256), 256, 0, evals, evecs, n, np, n_sub, sel, B,
                                                                             ctx->d_status);
-    LAUNCH_CHECK(ctx, "k_scale_sel");
     ctx_free(ctx, sel);
 }
 
 void launch_split_complex(gw_ctx* ctx, const double2* z, double* re, double* im, size_t n) {
-    k_split_complex<<<div_up((long long)n, 256), 256, 0, ctx->stream>>>(z, re, im, (long long)n);
-    LAUNCH_CHECK(ctx, "k_split_complex");
+    klaunch(ctx, "k_split_complex", k_split_complex, div_up((long long)n, 256), 256, 0, z, re, im, (long long)n);
 }

@@ -91,21 +91,16 @@ void launch_pair_table(gw_ctx* ctx, const gw_mol* mol, gw_chi0* c) {
     c->pDelta = dalloc<double>(ctx, n); c->pFrac = dalloc<double>(ctx, n);
     c->seg = dalloc<int>(ctx, c->nb_bins + 1);
     const int T = 256;
-    k_pair_keys<<<div_up(n, T), T, 0, ctx->stream>>>(mol->eps, n_occ, n_virt, key, delta);
-    LAUNCH_CHECK(ctx, "k_pair_keys");
-    k_pair_rank<<<div_up(n, T), T, 0, ctx->stream>>>(key, n, rank);
-    LAUNCH_CHECK(ctx, "k_pair_rank");
-    k_pair_scatter<<<div_up(n, T), T, 0, ctx->stream>>>(rank, delta, n_occ, n_virt, c->grid.d_omega, c->pE, c->pF,
+    klaunch(ctx, "k_pair_keys", k_pair_keys, div_up(n, T), T, 0, mol->eps, n_occ, n_virt, key, delta);
+    klaunch(ctx, "k_pair_rank", k_pair_rank, div_up(n, T), T, 0, key, n, rank);
+    klaunch(ctx, "k_pair_scatter", k_pair_scatter, div_up(n, T), T, 0, rank, delta, n_occ, n_virt, c->grid.d_omega, c->pE, c->pF,
                                                          c->pDelta, c->pBin, c->pFrac);
-    LAUNCH_CHECK(ctx, "k_pair_scatter");
-    k_pair_segments<<<div_up(n + 1, T), T, 0, ctx->stream>>>(c->pBin, n, c->j_lo, c->nb_bins, c->seg, ctx->d_status);
-    LAUNCH_CHECK(ctx, "k_pair_segments");
+    klaunch(ctx, "k_pair_segments", k_pair_segments, div_up(n + 1, T), T, 0, c->pBin, n, c->j_lo, c->nb_bins, c->seg, ctx->d_status);
     ctx_free(ctx, key); ctx_free(ctx, delta); ctx_free(ctx, rank);
 }
 
 void launch_invert_perm(gw_ctx* ctx, const gw_chi0* c, int* rank_of) {
     const int n = c->n_pair;
     const gw_mol* mol = c->mol;
-    k_invert_perm<<<div_up(n, 256), 256, 0, ctx->stream>>>(c->pE, c->pF, n, mol->n_occ, mol->n_orb - mol->n_occ, rank_of);
-    LAUNCH_CHECK(ctx, "k_invert_perm");
+    klaunch(ctx, "k_invert_perm", k_invert_perm, div_up(n, 256), 256, 0, c->pE, c->pF, n, mol->n_occ, mol->n_orb - mol->n_occ, rank_of);
 }

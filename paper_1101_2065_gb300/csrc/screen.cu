@@ -263,8 +263,7 @@ void launch_ldlt(gw_ctx* ctx, gw_W* W) {
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
     int grid = std::min(N, ctx->num_sms);   // 224 registers: one CTA per SM
-    k_ldlt<<<grid, 256, 0, ctx->stream>>>(c->chi0, W->fac, n, N, W->piv, ctx->d_status);
-    LAUNCH_CHECK(ctx, "k_ldlt");
+    klaunch(ctx, "k_ldlt", k_ldlt, grid, 256, 0, c->chi0, W->fac, n, N, W->piv, ctx->d_status);
 }
 
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
@@ -278,14 +277,12 @@ void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* co
     size_t smem = sizeof(double2) * (size_t)n * RC;
     CUDA_CHECK(cudaFuncSetAttribute(k_forms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int grid = std::min(N - 1, ctx->num_sms);
-    k_forms<<<std::max(grid, 1), 256, smem, ctx->stream>>>(W->fac, n, N, Q, R, RC, cout);
-    LAUNCH_CHECK(ctx, "k_forms");
+    klaunch(ctx, "k_forms", k_forms, std::max(grid, 1), 256, smem, W->fac, n, N, Q, R, RC, cout);
 }
 
 void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work) {
     (void)work;
     const gw_chi0* c = W->chi0;
     const long long nn = (long long)c->n_sub * c->n_sub;
-    k_ldlt_inverse<<<1, 256, 0, ctx->stream>>>(W->fac + k * nn, c->n_sub, out);
-    LAUNCH_CHECK(ctx, "k_ldlt_inverse");
+    klaunch(ctx, "k_ldlt_inverse", k_ldlt_inverse, 1, 256, 0, W->fac + k * nn, c->n_sub, out);
 }

@@ -193,10 +193,9 @@ void launch_sigma_grid(gw_ctx* ctx, gw_sigma* s) {
     const gw_mol* mol = c->mol;
     long long tot = (long long)s->n_states * s->n_sig;
     size_t smem = mol->n_orb * (sizeof(double) + sizeof(int));
-    k_sigma_grid<<<div_up(tot, 256), 256, smem, ctx->stream>>>(s->c, mol->eps, mol->n_orb, mol->n_occ,
+    klaunch(ctx, "k_sigma_grid", k_sigma_grid, div_up(tot, 256), 256, smem, s->c, mol->eps, mol->n_orb, mol->n_occ,
                                                                c->grid.n_omega, c->grid.d_omega, s->j0, s->n_sig,
                                                                s->n_states, s->sig);
-    LAUNCH_CHECK(ctx, "k_sigma_grid");
 }
 
 void launch_sigma_c(gw_ctx* ctx, gw_sigma* s) {
@@ -207,24 +206,20 @@ void launch_sigma_c(gw_ctx* ctx, gw_sigma* s) {
     long long dmax = (long long)(N - 1) - s->j0;
     long long nd = dmax - dmin + 1;
     double2* K = dalloc<double2>(ctx, nd);
-    k_cauchy_table<<<div_up(nd, 256), 256, 0, ctx->stream>>>(K, dmin, nd, c->grid.d_omega, c->grid.eta);
-    LAUNCH_CHECK(ctx, "k_cauchy_table");
+    klaunch(ctx, "k_cauchy_table", k_cauchy_table, div_up(nd, 256), 256, 0, K, dmin, nd, c->grid.d_omega, c->grid.eta);
     long long tot = (long long)s->n_states * (2 * N - 1);
-    k_sigma_c<<<div_up(tot, 256), 256, 0, ctx->stream>>>(s->sig, s->n_sig, s->j0, N, c->grid.d_omega, K, dmin,
+    klaunch(ctx, "k_sigma_c", k_sigma_c, div_up(tot, 256), 256, 0, s->sig, s->n_sig, s->j0, N, c->grid.d_omega, K, dmin,
                                                          s->n_states, s->sigc);
-    LAUNCH_CHECK(ctx, "k_sigma_c");
     ctx_free(ctx, K);
 }
 
 void launch_sigma_x(gw_ctx* ctx, gw_sigma* s, const double* Vnk, const double* T, int ld) {
     const gw_mol* mol = s->W->chi0->mol;
-    k_sigma_x<<<s->n_states, 256, 0, ctx->stream>>>(Vnk, T, ld, mol->n_prod, mol->n_orb, mol->n_occ, s->sx);
-    LAUNCH_CHECK(ctx, "k_sigma_x");
+    klaunch(ctx, "k_sigma_x", k_sigma_x, s->n_states, 256, 0, Vnk, T, ld, mol->n_prod, mol->n_orb, mol->n_occ, s->sx);
 }
 
 void launch_qp(gw_ctx* ctx, const gw_sigma* s, const double* vxc, double* e, double* z, int* st) {
     const gw_chi0* c = s->W->chi0;
-    k_qp<<<s->n_states, 256, 0, ctx->stream>>>(s->sig, s->n_sig, s->j0, c->grid.d_omega, c->grid.eta, s->eks, s->sx,
+    klaunch(ctx, "k_qp", k_qp, s->n_states, 256, 0, s->sig, s->n_sig, s->j0, c->grid.d_omega, c->grid.eta, s->eks, s->sx,
                                                vxc, e, z, st);
-    LAUNCH_CHECK(ctx, "k_qp");
 }

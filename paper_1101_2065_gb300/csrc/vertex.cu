@@ -76,7 +76,6 @@ void launch_vertex_contract(gw_ctx* ctx, const gw_mol* mol, const int* Es, int n
         attr_set = true;
     }
     dim3 grid(mol->n_prod, div_up(nF, FC));
-    k_vertex_contract<<<grid, 256, smem, ctx->stream>>>(mol->X, mol->n_orb, mol->vertex, mol->voff, mol->prod_atom,
+    klaunch(ctx, "k_vertex_contract", k_vertex_contract, grid, 256, smem, mol->X, mol->n_orb, mol->vertex, mol->voff, mol->prod_atom,
                                                        mol->loc_ptr, mol->loc_idx, Es, nE, Fs, nF, map, out, ld);
-    LAUNCH_CHECK(ctx, "k_vertex_contract");
 }

@@ -234,6 +234,9 @@ def test_invalid_arguments(gwlib, ctx, cfg1):
     with pytest.raises(gwlib.GWError) as ei:
         _run(gwlib, ctx, mol, bad)
     assert ei.value.code == -1
+    del ei
+    import gc
+    gc.collect()                       # the traceback held the uploaded molecule
     before = ctx.bytes_in_use
     m = gwlib.gw_mol_upload(ctx, mol)
     c = gwlib.gw_build_chi0(ctx, m, grid)
