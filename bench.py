@@ -36,7 +36,7 @@ def _args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -150,6 +150,34 @@ def run_reference(a):
 
 
 # ------------------------------------------------------------------ GPU arm
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 FMA/clk/SM x 152 SMs at 2070 MHz
+KERNELS = ["k_forms", "k_forms32", "k_ldlt", "k_ldlt32", "k_chi0_fft", "k_chi0_fft32", "k_jacobi_sweep", "k_dgemm",
+           "k_vertex_contract", "k_sigma_c", "k_qp", "k_jacobi_off", "k_chol_panel"]
+
+
+def kernel_model(name, mol, grid, n_rank):
+    """Algorithmic work of one launch of a kernel: (flops, bound, peak TFLOP/s)."""
+    n, N, R = mol.n_sub, grid.n_omega, 2 * mol.n_orb
+    L = 2 * N
+    f32 = name.endswith("32")
+    peak = PEAK_FP32_TFLOPS if f32 else PEAK_FP64_TFLOPS
+    if name.startswith("k_forms"):
+        # forward substitution L y = q: n^2/2 complex multiply-adds (8 flops) per RHS and frequency
+        return (N - 1) * R * 4.0 * n * n, "alu", peak
+    if name.startswith("k_ldlt"):
+        # complex symmetric L D L^T: n^3/6 complex multiply-adds per frequency
+        return N * (8.0 / 6.0) * n ** 3, "alu", peak
+    if name.startswith("k_chi0_fft"):
+        # per element pair: one forward and two inverse complex FFTs of length L (5 L log2 L flops each)
+        pairs = (n * (n + 1) // 2 + 1) // 2
+        return pairs * 3 * 5.0 * L * math.log2(L), "alu", peak
+    if name == "k_jacobi_sweep":
+        # (np-1) rounds: upper triangle of J^T A J (6 flops/element) and V J (3 flops/element)
+        npad = n_rank + (n_rank & 1)
+        return (npad - 1) * (npad * (npad + 1) / 2 * 6.0 + npad * npad * 3.0), "alu", PEAK_FP64_TFLOPS
+    return None, None, None
+
+
 def run_gpu(a):
     import numpy as np
     import torch
@@ -172,49 +200,58 @@ def run_gpu(a):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     gw.build.build()
     mol, grid = synth.make_config(2)
-    prec = gw.GW_MIXED if a.precision == "mixed" else gw.GW_FP64
     states = [mol.n_occ - 1, mol.n_occ]
     stream = torch.cuda.Stream()
     ctx = gw.Context(local, 0, stream.cuda_stream)
     m = G.gw_mol_upload(ctx, mol)          # inputs resident in HBM
 
-    def step():
+    def step(prec):
         c = G.gw_build_chi0(ctx, m, grid, prec)
         w = G.gw_screen_W(ctx, c)
         s = G.gw_sigma_diag(ctx, w, states)
         e, z, st = G.gw_qp_solve(ctx, s)
+        n_rank = c.info()["n_rank"]
         for h in (s, w, c):
             h.free()
-        return e
+        return e, st, n_rank
 
-    for _ in range(a.warmup):
-        step()
-    dom = "k_forms" if prec == gw.GW_FP64 else "k_forms32"
-    ctx.profile(True, dom)
-    barrier()
-    l0 = ctx.launch_count
-    clk = ClockSampler(local)
-    clk.start()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
-    with torch.cuda.stream(stream):
+    def measure(prec, steps, warmup, clocks=False):
+        for _ in range(warmup):
+            step(prec)
+        ctx.profile(True, None)
+        barrier()
+        l0 = ctx.launch_count
+        clk = ClockSampler(local)
+        if clocks:
+            clk.start()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         evs[0].record(stream)
-        for i in range(a.steps):
-            step()
+        for i in range(steps):
+            e, st, n_rank = step(prec)
             evs[i + 1].record(stream)
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    launches = ctx.launch_count - l0
-    t_ms = evs[0].elapsed_time(evs[-1])
-    lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
-    k_ms, k_n = ctx.profile_get(dom)
-    ctx.profile(False)
-    if dist is not None:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * a.steps / (t_ms / 1e3)
+        torch.cuda.synchronize()
+        ck = clk.stop() if clocks else None
+        t_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]))
+        lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+        kt = {k: ctx.profile_get(k) for k in KERNELS}
+        ctx.profile(False)
+        return dict(value=world * steps / (t_ms / 1e3), t_ms=t_ms, lat=lat, launches=ctx.launch_count - l0,
+                    kt={k: v for k, v in kt.items() if v[1] > 0}, e=e, st=st, clocks=ck, n_rank=n_rank)
+
+    prec = gw.GW_MIXED if a.precision == "mixed" else gw.GW_FP64
+    main = measure(prec, a.steps, a.warmup, clocks=True)
+    ref64 = None
+    if prec == gw.GW_MIXED:
+        ref64 = measure(gw.GW_FP64, max(2, min(a.steps, 3)), 1)
 
     # end to end through the host-memory entry point (pinned inputs)
     def pinned(x, dt):
@@ -241,40 +278,49 @@ def run_gpu(a):
         G.gw_solve_host(ctx, hm, grid, states, prec, desc=desc)
     e1.record(stream)
     torch.cuda.synchronize()
-    te = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([te], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
+    te = max_over_ranks(e0.elapsed_time(e1))
     e2e = world * a.steps / (te / 1e3)
 
-    # roofline of the dominant kernel (binary64 issue rate bound)
-    n, N, R = mol.n_sub, grid.n_omega, len(states) * mol.n_orb
-    flops = (N - 1) * R * 4.0 * n * n     # forward substitutions: n^2/2 complex multiply-adds per RHS
-    avg_s = (k_ms / max(k_n, 1)) / 1e3
-    achieved = flops / avg_s / 1e12 if k_n else None
-    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-            "frac": (achieved / PEAK_FP64_TFLOPS) if achieved else None, "traffic": None,
-            "peak_source": "2 binary64 FMA/clk/SM x 152 SMs x 2070 MHz (recipe nominal 1.25 TFLOP/s)",
-            "avg_launch_ms": avg_s * 1e3, "launches": k_n}
+    # roofline of the kernel with the largest measured share
+    dom = max(main["kt"].items(), key=lambda kv: kv[1][0])[0]
+    flops, bound, peak = kernel_model(dom, mol, grid, main["n_rank"])
+    k_ms, k_n = main["kt"][dom]
+    avg_s = k_ms / k_n / 1e3
+    achieved = flops / avg_s / 1e12 if flops else None
+    step_ms = main["t_ms"] / a.steps
+    roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_source": ("128 binary32 FMA/clk/SM" if peak == PEAK_FP32_TFLOPS else "2 binary64 FMA/clk/SM")
+            + " x 152 SMs x 2070 MHz (recipe unit counts and maximum clock)",
+            "avg_launch_ms": avg_s * 1e3, "launches": k_n,
+            "share_of_step": (k_ms / a.steps) / step_ms}
+    kernels = {k: {"ms_per_step": v[0] / a.steps, "launches_per_step": v[1] / a.steps} for k, v in main["kt"].items()}
 
     out = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": main["value"], "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == gw.GW_FP64 else "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": a.precision,
-                   "l2": "no flush: per-step working set (chi0 + factors, 2.9 GB) exceeds the 129 MB L2",
+                   "l2": "no flush: per-step working set (chi0 + factors, >= 1.5 GB) exceeds the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "latency_ms": {"p50": float(np.percentile(main["lat"], 50)), "p99": float(np.percentile(main["lat"], 99))},
         "roofline": roof,
+        "kernels": kernels,
         "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(launches),
-        "clocks": clocks,
+        "gpu_launches": int(main["launches"]),
+        "clocks": main["clocks"],
     }
+    if ref64 is not None:
+        err = float(np.abs(np.asarray(main["e"]) - np.asarray(ref64["e"])).max()) * 27211.386245988
+        out["fp64_plain"] = {"value": ref64["value"], "unit": "solves/s", "ms_per_step": ref64["t_ms"] / len(ref64["lat"]),
+                             "qp_max_abs_err_meV": err,
+                             "same_root_branch": bool(np.array_equal(main["st"], ref64["st"]))}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        t_or = oracle_time(mol, grid, sample=1)
+        t_or = oracle_time(mol, grid, sample=8)
         out["cpu_baseline"] = {"value": 1.0 / t_or, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                               "sample": "one full FP64 oracle solve of the same workload (NumPy/LAPACK, all cores)"}
+                               "sample": "FP64 oracle solve of the same workload: Cauchy sum, screening and forms on "
+                                         "every 8th frequency scaled by 8, all other steps in full (NumPy/LAPACK, "
+                                         "all host cores)"}
     if rank == 0:
         print(json.dumps(out))
     m.free()

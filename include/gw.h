@@ -124,6 +124,14 @@ const char* gw_last_error(const gw_ctx* ctx);
 size_t    gw_ctx_bytes_in_use(const gw_ctx* ctx);
 /* Number of this library's kernel launches issued on the context so far. */
 long long gw_ctx_launch_count(const gw_ctx* ctx);
+/* Per-kernel timing with CUDA events recorded on the context stream around
+ * each launch of the named kernel (kernel_name NULL or "" = every kernel).
+ * Enabling (or disabling) clears the accumulated totals.  The events add
+ * one record before and one after every matched launch. */
+gw_status gw_ctx_profile(gw_ctx* ctx, int enable, const char* kernel_name);
+/* Accumulated device time (ms) and launch count of one kernel since the last
+ * gw_ctx_profile call; synchronises the context stream. */
+gw_status gw_ctx_profile_get(gw_ctx* ctx, const char* kernel_name, double* total_ms, long long* launches);
 
 /* ---------------------------------------------------------------- molecule */
 /* Validates the description (sizes, CSR, offsets) and copies it to the

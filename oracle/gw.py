@@ -193,7 +193,7 @@ def spectral_gamma(chi_rpa, ks):
 
 def screened_W(mol, Zup, chi_rpa):
     """W_k = v + Zup chi^RPA_k Zup^T (Eq. chi_RPA), materialised for tests."""
-    return mol.v[None] + np.einsum("am,kmn,bn->kab", Zup, chi_rpa, Zup)
+    return mol.v[None] + Zup[None] @ chi_rpa @ Zup.T[None]
 
 
 # ------------------------------------------------------------------ a6

@@ -469,7 +469,8 @@ static gw_W* screen_W(gw_ctx* ctx, const gw_chi0* c) {
     w->ctx = ctx; w->chi0 = c;
     const size_t n = c->n_sub, N = c->grid.n_omega;
     try {
-        w->fac = dalloc<double2>(ctx, N * n * n);
+        if (c->prec == GW_MIXED) w->fac32 = dalloc<float2>(ctx, N * n * n);
+        else w->fac = dalloc<double2>(ctx, N * n * n);
         w->piv = dalloc<double>(ctx, N);
         launch_ldlt(ctx, w);
         std::vector<double> piv(N);

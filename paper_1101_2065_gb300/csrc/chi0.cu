@@ -91,87 +91,96 @@ __global__ void k_kernel_spectra(const double2* __restrict__ tw, int N, int logL
 }
 
 // Tent-deposited weight of bin j = j_lo + b for the element pair (m1,n1),(m2,n2).
+template <typename R>
 __device__ __forceinline__ void deposit2(int b, int nb_bins, const int* __restrict__ seg,
-                                         const double* __restrict__ frac, const double* __restrict__ Ut, int n_pair,
-                                         int m1, int n1, int m2, int n2, double& a1, double& a2) {
-    a1 = 0.0;
-    a2 = 0.0;
-    const double* u1 = Ut + (long long)m1 * n_pair;
-    const double* v1 = Ut + (long long)n1 * n_pair;
-    const double* u2 = Ut + (long long)m2 * n_pair;
-    const double* v2 = Ut + (long long)n2 * n_pair;
+                                         const double* __restrict__ frac, const R* __restrict__ Ut, int n_pair,
+                                         int m1, int n1, int m2, int n2, R& a1, R& a2) {
+    a1 = R(0);
+    a2 = R(0);
+    const R* u1 = Ut + (long long)m1 * n_pair;
+    const R* v1 = Ut + (long long)n1 * n_pair;
+    const R* u2 = Ut + (long long)m2 * n_pair;
+    const R* v2 = Ut + (long long)n2 * n_pair;
     if (b < nb_bins)
         for (int p = seg[b]; p < seg[b + 1]; ++p) {
-            double w = 2.0 * (1.0 - frac[p]);
+            R w = R(2.0 * (1.0 - frac[p]));
             a1 = fma(w * u1[p], v1[p], a1);
             a2 = fma(w * u2[p], v2[p], a2);
         }
     if (b >= 1)
         for (int p = seg[b - 1]; p < seg[b]; ++p) {
-            double w = 2.0 * frac[p];
+            R w = R(2.0 * frac[p]);
             a1 = fma(w * u1[p], v1[p], a1);
             a2 = fma(w * u2[p], v2[p], a2);
         }
 }
 
-__global__ void __launch_bounds__(256) k_chi0_fft(const double* __restrict__ Ut, int n_pair, int n_sub,
+template <typename C> struct Real;
+template <> struct Real<double2> { typedef double T; static __device__ double2 make(double a, double b) { return make_double2(a, b); } };
+template <> struct Real<float2> { typedef float T; static __device__ float2 make(float a, float b) { return make_float2(a, b); } };
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __restrict__ Ut, int n_pair, int n_sub,
                                                   const int* __restrict__ seg, const double* __restrict__ frac,
                                                   int j_lo, int nb_bins, int N, int logL,
-                                                  const double2* __restrict__ tw, const double2* __restrict__ C1,
-                                                  const double2* __restrict__ C2, double2* __restrict__ chi0) {
-    extern __shared__ double2 sbuf[];
+                                                  const C* __restrict__ tw, const C* __restrict__ C1,
+                                                  const C* __restrict__ C2, C* __restrict__ chi0) {
+    typedef typename Real<C>::T R;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    C* sbuf = reinterpret_cast<C*>(sraw);
     const int L = 2 * N;
     const int band = nb_bins + 1;
     const long long n_el = (long long)n_sub * (n_sub + 1) / 2;
     const long long n_grp = (n_el + 1) / 2;
     const long long nn = (long long)n_sub * n_sub;
-    const double scale = 1.0 / (double)L;
-    double2* B0 = sbuf;
-    double2* B1 = sbuf + L;
-    double2* B2 = sbuf + 2 * L;
+    const R scale = R(1.0 / (double)L);
+    C* B0 = sbuf;
+    C* B1 = sbuf + L;
+    C* B2 = sbuf + 2 * L;
     for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
         int m1, n1, m2, n2;
         tri_index(2 * g, m1, n1);
         bool two = 2 * g + 1 < n_el;
         if (two) tri_index(2 * g + 1, m2, n2); else { m2 = m1; n2 = n1; }
-        for (int d = threadIdx.x; d < L; d += blockDim.x) B0[d] = make_double2(0.0, 0.0);
+        for (int d = threadIdx.x; d < L; d += blockDim.x) B0[d] = Real<C>::make(R(0), R(0));
         __syncthreads();
         for (int b = threadIdx.x; b < band; b += blockDim.x) {
-            double a1, a2;
-            deposit2(b, nb_bins, seg, frac, Ut, n_pair, m1, n1, m2, n2, a1, a2);
-            B0[j_lo + b] = make_double2(a1, two ? a2 : 0.0);
+            R a1, a2;
+            deposit2<R>(b, nb_bins, seg, frac, Ut, n_pair, m1, n1, m2, n2, a1, a2);
+            B0[j_lo + b] = Real<C>::make(a1, two ? a2 : R(0));
         }
         __syncthreads();
-        double2* Zb = fft_smem(B0, B1, L, logL, tw, false);
-        double2* Y1 = (Zb == B0) ? B1 : B0;
+        C* Zb = fft_smem(B0, B1, L, logL, tw, false);
+        C* Y1 = (Zb == B0) ? B1 : B0;
         // split the two real transforms and apply the kernel spectra
         for (int m = threadIdx.x; m <= N; m += blockDim.x) {
             int mr = (L - m) & (L - 1);
-            double2 zm = Zb[m], zr = Zb[mr];
+            C zm = Zb[m], zr = Zb[mr];
             // X1 = (Z[m] + conj Z[L-m])/2, X2 = (Z[m] - conj Z[L-m])/(2i)
-            double2 x1 = make_double2(0.5 * (zm.x + zr.x), 0.5 * (zm.y - zr.y));
-            double2 x2 = make_double2(0.5 * (zm.y + zr.y), -0.5 * (zm.x - zr.x));
-            double2 c1m = C1[m], c2m = C2[m], c1r = C1[mr], c2r = C2[mr];
-            double2 y1m = csub(cmul(x1, c1m), cmul(cconj(x1), c2m));
-            double2 y2m = csub(cmul(x2, c1m), cmul(cconj(x2), c2m));
-            double2 y1r = csub(cmul(cconj(x1), c1r), cmul(x1, c2r));
-            double2 y2r = csub(cmul(cconj(x2), c1r), cmul(x2, c2r));
+            const R h = R(0.5);
+            C x1 = Real<C>::make(h * (zm.x + zr.x), h * (zm.y - zr.y));
+            C x2 = Real<C>::make(h * (zm.y + zr.y), -h * (zm.x - zr.x));
+            C c1m = C1[m], c2m = C2[m], c1r = C1[mr], c2r = C2[mr];
+            C y1m = csub(cmul(x1, c1m), cmul(cconj(x1), c2m));
+            C y2m = csub(cmul(x2, c1m), cmul(cconj(x2), c2m));
+            C y1r = csub(cmul(cconj(x1), c1r), cmul(x1, c2r));
+            C y2r = csub(cmul(cconj(x2), c1r), cmul(x2, c2r));
             Y1[m] = y1m;
             Zb[m] = y2m;
             if (mr != m) { Y1[mr] = y1r; Zb[mr] = y2r; }
         }
         __syncthreads();
-        double2* r1 = fft_smem(Y1, B2, L, logL, tw, true);
-        double2* free1 = (r1 == Y1) ? B2 : Y1;
-        double2* r2 = fft_smem(Zb, free1, L, logL, tw, true);
+        C* r1 = fft_smem(Y1, B2, L, logL, tw, true);
+        C* free1 = (r1 == Y1) ? B2 : Y1;
+        C* r2 = fft_smem(Zb, free1, L, logL, tw, true);
         const long long o1 = (long long)m1 * n_sub + n1;
         const long long o2 = (long long)m2 * n_sub + n2;
         for (int k = threadIdx.x; k < N; k += blockDim.x) {
-            double2 v1 = r1[k];
-            chi0[(long long)k * nn + o1] = make_double2(v1.x * scale, v1.y * scale);
+            C v1 = r1[k];
+            chi0[(long long)k * nn + o1] = Real<C>::make(v1.x * scale, v1.y * scale);
             if (two) {
-                double2 v2 = r2[k];
-                chi0[(long long)k * nn + o2] = make_double2(v2.x * scale, v2.y * scale);
+                C v2 = r2[k];
+                chi0[(long long)k * nn + o2] = Real<C>::make(v2.x * scale, v2.y * scale);
             }
         }
         __syncthreads();
@@ -189,11 +198,20 @@ __global__ void k_spectral_readback(const double* __restrict__ Ut, int n_pair, i
     int m = e / n_sub, n = e % n_sub;
     int b = j0 + jj - j_lo;
     double a = 0.0, dummy = 0.0;
-    if (b >= 0 && b <= nb_bins) deposit2(b, nb_bins, seg, frac, Ut, n_pair, m, n, m, n, a, dummy);
+    if (b >= 0 && b <= nb_bins) deposit2<double>(b, nb_bins, seg, frac, Ut, n_pair, m, n, m, n, a, dummy);
     A[t] = a;
 }
 
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, long long n) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = (float)a[t];
+}
+
 }  // namespace
+
+void launch_to_f32(gw_ctx* ctx, const double* a, float* b, long long n) {
+    if (n > 0) klaunch(ctx, "k_to_f32", k_to_f32, div_up(n, 256), 256, 0, a, b, n);
+}
 
 void launch_fft_tables(gw_ctx* ctx, gw_chi0* c) {
     const int L = c->L, N = c->grid.n_omega;
@@ -208,15 +226,34 @@ void launch_fft_tables(gw_ctx* ctx, gw_chi0* c) {
 
 void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
     const int L = c->L, N = c->grid.n_omega, n = c->n_sub;
-    size_t smem = 3 * (size_t)L * sizeof(double2);
-    if (smem > 227 * 1024) gw_throw(GW_ERR_INVALID_ARG, "n_omega too large for the binary64 FFT kernel (max 4096)");
-    c->chi0 = dalloc<double2>(ctx, (size_t)N * n * n);
-    CUDA_CHECK(cudaFuncSetAttribute(k_chi0_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const bool f32 = c->prec == GW_MIXED;
+    const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
+    size_t smem = 3 * (size_t)L * csz;
+    if (smem > 227 * 1024) gw_throw(GW_ERR_INVALID_ARG, "n_omega too large for the FFT kernel");
     int per_sm = std::max(1, (int)((228 * 1024) / (smem + 1024)));
     long long n_grp = ((long long)n * (n + 1) / 2 + 1) / 2;
     int grid = (int)std::min<long long>(n_grp, (long long)ctx->num_sms * per_sm);
-    klaunch(ctx, "k_chi0_fft", k_chi0_fft, grid, 256, smem, c->Ut, c->n_pair, n, c->seg, c->pFrac, c->j_lo, c->nb_bins, N,
-                                                 c->logL, c->tw, c->C1, c->C2, c->chi0);
+    if (f32) {
+        c->Ut32 = dalloc<float>(ctx, (size_t)n * c->n_pair);
+        c->tw32 = dalloc<float2>(ctx, L / 2);
+        c->C1_32 = dalloc<float2>(ctx, L);
+        c->C2_32 = dalloc<float2>(ctx, L);
+        launch_to_f32(ctx, c->Ut, c->Ut32, (long long)n * c->n_pair);
+        launch_to_f32(ctx, (const double*)c->tw, (float*)c->tw32, L);
+        launch_to_f32(ctx, (const double*)c->C1, (float*)c->C1_32, 2LL * L);
+        launch_to_f32(ctx, (const double*)c->C2, (float*)c->C2_32, 2LL * L);
+        c->chi0_32 = dalloc<float2>(ctx, (size_t)N * n * n);
+        CUDA_CHECK(cudaFuncSetAttribute(k_chi0_fft<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        klaunch(ctx, "k_chi0_fft32", k_chi0_fft<float2>, grid, 256, smem, (const float*)c->Ut32, c->n_pair, n,
+                (const int*)c->seg, (const double*)c->pFrac, c->j_lo, c->nb_bins, N, c->logL,
+                (const float2*)c->tw32, (const float2*)c->C1_32, (const float2*)c->C2_32, c->chi0_32);
+    } else {
+        c->chi0 = dalloc<double2>(ctx, (size_t)N * n * n);
+        CUDA_CHECK(cudaFuncSetAttribute(k_chi0_fft<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        klaunch(ctx, "k_chi0_fft", k_chi0_fft<double2>, grid, 256, smem, (const double*)c->Ut, c->n_pair, n,
+                (const int*)c->seg, (const double*)c->pFrac, c->j_lo, c->nb_bins, N, c->logL,
+                (const double2*)c->tw, (const double2*)c->C1, (const double2*)c->C2, c->chi0);
+    }
 }
 
 void launch_spectral_readback(gw_ctx* ctx, const gw_chi0* c, int j0, int nj, double* A) {

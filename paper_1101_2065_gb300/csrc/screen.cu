@@ -21,17 +21,31 @@ namespace {
 constexpr int NB = 16;     // panel width
 constexpr int TS = 32;     // trailing tile
 
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-    double r = 1.0 / (b.x * b.x + b.y * b.y);
-    return make_double2((a.x * b.x + a.y * b.y) * r, (a.y * b.x - a.x * b.y) * r);
+template <typename C> struct CT;
+template <> struct CT<double2> {
+    typedef double R;
+    static __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+};
+template <> struct CT<float2> {
+    typedef float R;
+    static __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+};
+
+template <typename C>
+__device__ __forceinline__ C cdiv(C a, C b) {
+    typedef typename CT<C>::R R;
+    R r = R(1) / (b.x * b.x + b.y * b.y);
+    return CT<C>::mk((a.x * b.x + a.y * b.y) * r, (a.y * b.x - a.x * b.y) * r);
 }
 
-__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {   // c + a*b
-    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+template <typename C>
+__device__ __forceinline__ C cfma(C a, C b, C c) {   // c + a*b
+    return CT<C>::mk(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 
-__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {   // c - a*b
-    return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+template <typename C>
+__device__ __forceinline__ C cfms(C a, C b, C c) {   // c - a*b
+    return CT<C>::mk(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
 }
 
 __device__ double block_max(double v, double* red) {
@@ -49,25 +63,27 @@ __device__ double block_max(double v, double* red) {
     return r;
 }
 
-__global__ void __launch_bounds__(256) k_ldlt(const double2* __restrict__ chi0, double2* __restrict__ fac, int n,
+template <typename C>
+__global__ void __launch_bounds__(256) k_ldlt(const C* __restrict__ chi0, C* __restrict__ fac, int n,
                                               int N, double* __restrict__ piv, int* status) {
-    __shared__ double2 S[NB][NB + 1];
-    __shared__ double2 sL[TS][NB + 1];
-    __shared__ double2 sW[TS][NB + 1];
+    typedef typename CT<C>::R R;
+    __shared__ C S[NB][NB + 1];
+    __shared__ C sL[TS][NB + 1];
+    __shared__ C sW[TS][NB + 1];
     __shared__ double red[33];
     const int tid = threadIdx.x;
     const long long nn = (long long)n * n;
     for (int k = blockIdx.x; k < N; k += gridDim.x) {
-        const double2* X = chi0 + k * nn;
-        double2* M = fac + k * nn;
+        const C* X = chi0 + k * nn;
+        C* M = fac + k * nn;
         double mx = 0.0;
         for (long long t = tid; t < nn; t += blockDim.x) {
             int i = (int)(t / n), j = (int)(t % n);
             if (j > i) continue;
-            double2 x = X[t];
-            double2 m = make_double2((i == j ? 1.0 : 0.0) - x.x, -x.y);
+            C x = X[t];
+            C m = CT<C>::mk((i == j ? R(1) : R(0)) - x.x, -x.y);
             M[t] = m;
-            mx = fmax(mx, hypot(m.x, m.y));
+            mx = fmax(mx, hypot((double)m.x, (double)m.y));
         }
         mx = block_max(mx, red);
         double dmin = INFINITY;
@@ -80,7 +96,7 @@ __global__ void __launch_bounds__(256) k_ldlt(const double2* __restrict__ chi0, 
             }
             __syncthreads();
             for (int j = 0; j < kb; ++j) {
-                double2 d = S[j][j];
+                C d = S[j][j];
                 for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[i][j] = cdiv(S[i][j], d);
                 __syncthreads();
                 for (int t = tid; t < kb * kb; t += blockDim.x) {
@@ -93,15 +109,15 @@ __global__ void __launch_bounds__(256) k_ldlt(const double2* __restrict__ chi0, 
                 int i = t / kb, j = t % kb;
                 if (j <= i) M[(long long)(k0 + i) * n + k0 + j] = S[i][j];
             }
-            for (int j = 0; j < kb; ++j) dmin = fmin(dmin, hypot(S[j][j].x, S[j][j].y));
+            for (int j = 0; j < kb; ++j) dmin = fmin(dmin, hypot((double)S[j][j].x, (double)S[j][j].y));
             // (b) panel rows below: x D L11^T = a
             for (int r = k1 + tid; r < n; r += blockDim.x) {
-                double2 x[NB];
-                double2* row = M + (long long)r * n + k0;
+                C x[NB];
+                C* row = M + (long long)r * n + k0;
 #pragma unroll
                 for (int j = 0; j < NB; ++j) {
                     if (j < kb) {
-                        double2 a = row[j];
+                        C a = row[j];
 #pragma unroll
                         for (int p = 0; p < NB; ++p)
                             if (p < j) a = cfms(cmul(x[p], S[p][p]), S[j][p], a);
@@ -124,7 +140,7 @@ __global__ void __launch_bounds__(256) k_ldlt(const double2* __restrict__ chi0, 
                 const int r0 = k1 + I * TS, c0 = k1 + J * TS;
                 for (int t = tid; t < TS * NB; t += blockDim.x) {
                     int rr = t / NB, p = t % NB;
-                    double2 lv = make_double2(0.0, 0.0), wv = make_double2(0.0, 0.0);
+                    C lv = CT<C>::mk(R(0), R(0)), wv = CT<C>::mk(R(0), R(0));
                     if (p < kb) {
                         if (r0 + rr < n) lv = M[(long long)(r0 + rr) * n + k0 + p];
                         if (c0 + rr < n) wv = cmul(M[(long long)(c0 + rr) * n + k0 + p], S[p][p]);
@@ -134,15 +150,15 @@ __global__ void __launch_bounds__(256) k_ldlt(const double2* __restrict__ chi0, 
                 }
                 __syncthreads();
                 const int ty = tid / 16, tx = tid % 16;
-                double2 acc[2][2];
+                C acc[2][2];
 #pragma unroll
                 for (int a = 0; a < 2; ++a)
 #pragma unroll
-                    for (int b = 0; b < 2; ++b) acc[a][b] = make_double2(0.0, 0.0);
+                    for (int b = 0; b < 2; ++b) acc[a][b] = CT<C>::mk(R(0), R(0));
 #pragma unroll
                 for (int p = 0; p < NB; ++p) {
-                    double2 l0 = sL[ty][p], l1 = sL[ty + 16][p];
-                    double2 w0 = sW[tx][p], w1 = sW[tx + 16][p];
+                    C l0 = sL[ty][p], l1 = sL[ty + 16][p];
+                    C w0 = sW[tx][p], w1 = sW[tx + 16][p];
                     acc[0][0] = cfma(l0, w0, acc[0][0]);
                     acc[0][1] = cfma(l0, w1, acc[0][1]);
                     acc[1][0] = cfma(l1, w0, acc[1][0]);
@@ -154,7 +170,7 @@ __global__ void __launch_bounds__(256) k_ldlt(const double2* __restrict__ chi0, 
                     for (int b = 0; b < 2; ++b) {
                         int i = r0 + ty + 16 * a, j = c0 + tx + 16 * b;
                         if (i < n && j <= i) {
-                            double2* m = M + (long long)i * n + j;
+                            C* m = M + (long long)i * n + j;
                             *m = csub(*m, acc[a][b]);
                         }
                     }
@@ -171,26 +187,29 @@ __global__ void __launch_bounds__(256) k_ldlt(const double2* __restrict__ chi0, 
 }
 
 // c[r*N + k] = -(1/pi) Im sum_i y_i^2/d_i, y = L_k^-1 q_r, for k >= 1.
-__global__ void __launch_bounds__(256) k_forms(const double2* __restrict__ fac, int n, int N,
+template <typename C>
+__global__ void __launch_bounds__(256) k_forms(const C* __restrict__ fac, int n, int N,
                                                const double* __restrict__ Q, int R, int RC,
                                                double* __restrict__ c) {
-    extern __shared__ double2 sY[];          // [n][RC]
-    __shared__ double2 S[NB][NB + 1];
-    __shared__ double2 sL[TS][NB + 1];
-    __shared__ double2 acc[256];
+    typedef typename CT<C>::R T;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    C* sY = reinterpret_cast<C*>(sraw);      // [n][RC]
+    __shared__ C S[NB][NB + 1];
+    __shared__ C sL[TS][NB + 1];
+    __shared__ C acc[256];
     const int tid = threadIdx.x;
     const long long nn = (long long)n * n;
     if (blockIdx.x == 0)
         for (int r = tid; r < R; r += blockDim.x) c[(long long)r * N] = 0.0;
     for (int k = 1 + blockIdx.x; k < N; k += gridDim.x) {
-        const double2* F = fac + k * nn;
+        const C* F = fac + k * nn;
         for (int rc0 = 0; rc0 < R; rc0 += RC) {
             const int rc = min(RC, R - rc0);
             for (long long t = tid; t < (long long)n * RC; t += blockDim.x) {
                 int i = (int)(t / RC), r = (int)(t % RC);
-                sY[t] = make_double2(r < rc ? Q[(long long)i * R + rc0 + r] : 0.0, 0.0);
+                sY[t] = CT<C>::mk(r < rc ? T(Q[(long long)i * R + rc0 + r]) : T(0), T(0));
             }
-            if (tid < RC) acc[tid] = make_double2(0.0, 0.0);
+            if (tid < RC) acc[tid] = CT<C>::mk(T(0), T(0));
             __syncthreads();
             for (int k0 = 0; k0 < n; k0 += NB) {
                 const int kb = min(NB, n - k0), k1 = k0 + kb;
@@ -201,9 +220,9 @@ __global__ void __launch_bounds__(256) k_forms(const double2* __restrict__ fac, 
                 __syncthreads();
                 if (tid < rc) {
                     const int r = tid;
-                    double2 a = acc[r];
+                    C a = acc[r];
                     for (int i = 0; i < kb; ++i) {
-                        double2 y = sY[(k0 + i) * RC + r];
+                        C y = sY[(k0 + i) * RC + r];
                         for (int p = 0; p < i; ++p) y = cfms(S[i][p], sY[(k0 + p) * RC + r], y);
                         sY[(k0 + i) * RC + r] = y;
                         a = cadd(a, cdiv(cmul(y, y), S[i][i]));
@@ -214,14 +233,14 @@ __global__ void __launch_bounds__(256) k_forms(const double2* __restrict__ fac, 
                 for (int r0 = k1; r0 < n; r0 += TS) {
                     for (int t = tid; t < TS * NB; t += blockDim.x) {
                         int rr = t / NB, p = t % NB;
-                        sL[rr][p] = (p < kb && r0 + rr < n) ? F[(long long)(r0 + rr) * n + k0 + p] : make_double2(0.0, 0.0);
+                        sL[rr][p] = (p < kb && r0 + rr < n) ? F[(long long)(r0 + rr) * n + k0 + p] : CT<C>::mk(T(0), T(0));
                     }
                     __syncthreads();
                     for (int t = tid; t < TS * rc; t += blockDim.x) {
                         int rr = t / rc, r = t % rc;
                         int i = r0 + rr;
                         if (i >= n) continue;
-                        double2 y = sY[i * RC + r];
+                        C y = sY[i * RC + r];
 #pragma unroll
                         for (int p = 0; p < NB; ++p)
                             if (p < kb) y = cfms(sL[rr][p], sY[(k0 + p) * RC + r], y);
@@ -230,7 +249,7 @@ __global__ void __launch_bounds__(256) k_forms(const double2* __restrict__ fac, 
                     __syncthreads();
                 }
             }
-            if (tid < rc) c[(long long)(rc0 + tid) * N + k] = -acc[tid].y / M_PI;
+            if (tid < rc) c[(long long)(rc0 + tid) * N + k] = -(double)acc[tid].y / M_PI;
             __syncthreads();
         }
     }
@@ -257,32 +276,51 @@ __global__ void __launch_bounds__(256) k_ldlt_inverse(const double2* __restrict_
     }
 }
 
+__global__ void k_c64_to_c128(const float2* __restrict__ a, double2* __restrict__ b, long long n) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = make_double2(a[t].x, a[t].y);
+}
+
 }  // namespace
 
 void launch_ldlt(gw_ctx* ctx, gw_W* W) {
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
-    int grid = std::min(N, ctx->num_sms);   // 224 registers: one CTA per SM
-    klaunch(ctx, "k_ldlt", k_ldlt, grid, 256, 0, c->chi0, W->fac, n, N, W->piv, ctx->d_status);
+    int grid = std::min(N, ctx->num_sms);   // large register footprint: one CTA per SM
+    if (c->prec == GW_MIXED)
+        klaunch(ctx, "k_ldlt32", k_ldlt<float2>, grid, 256, 0, (const float2*)c->chi0_32, W->fac32, n, N, W->piv,
+                ctx->d_status);
+    else
+        klaunch(ctx, "k_ldlt", k_ldlt<double2>, grid, 256, 0, (const double2*)c->chi0, W->fac, n, N, W->piv,
+                ctx->d_status);
 }
 
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
+    const bool f32 = c->prec == GW_MIXED;
+    const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
     const size_t budget = 190 * 1024;
-    int rc_max = (int)std::min<size_t>(256, budget / (sizeof(double2) * (size_t)n));
-    if (rc_max < 1) gw_throw(GW_ERR_INVALID_ARG, "n_sub too large for the binary64 forms kernel");
+    int rc_max = (int)std::min<size_t>(256, budget / (csz * (size_t)n));
+    if (rc_max < 1) gw_throw(GW_ERR_INVALID_ARG, "n_sub too large for the forms kernel");
     int chunks = div_up(R, rc_max);
     int RC = div_up(R, chunks);
-    size_t smem = sizeof(double2) * (size_t)n * RC;
-    CUDA_CHECK(cudaFuncSetAttribute(k_forms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int grid = std::min(N - 1, ctx->num_sms);
-    klaunch(ctx, "k_forms", k_forms, std::max(grid, 1), 256, smem, W->fac, n, N, Q, R, RC, cout);
+    size_t smem = csz * (size_t)n * RC;
+    int grid = std::max(1, std::min(N - 1, ctx->num_sms));
+    if (f32) {
+        CUDA_CHECK(cudaFuncSetAttribute(k_forms<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        klaunch(ctx, "k_forms32", k_forms<float2>, grid, 256, smem, (const float2*)W->fac32, n, N, Q, R, RC, cout);
+    } else {
+        CUDA_CHECK(cudaFuncSetAttribute(k_forms<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        klaunch(ctx, "k_forms", k_forms<double2>, grid, 256, smem, (const double2*)W->fac, n, N, Q, R, RC, cout);
+    }
 }
 
 void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work) {
-    (void)work;
     const gw_chi0* c = W->chi0;
     const long long nn = (long long)c->n_sub * c->n_sub;
-    klaunch(ctx, "k_ldlt_inverse", k_ldlt_inverse, 1, 256, 0, W->fac + k * nn, c->n_sub, out);
+    const double2* F = W->fac ? W->fac + k * nn : work;
+    if (!W->fac) klaunch(ctx, "k_c64_to_c128", k_c64_to_c128, div_up(nn, 256), 256, 0,
+                         (const float2*)(W->fac32 + k * nn), work, nn);
+    klaunch(ctx, "k_ldlt_inverse", k_ldlt_inverse, 1, 256, 0, F, c->n_sub, out);
 }

@@ -73,6 +73,8 @@ def load(path: str | None = None):
         "gw_last_error": ([P], C.c_char_p),
         "gw_ctx_bytes_in_use": ([P], C.c_size_t),
         "gw_ctx_launch_count": ([P], C.c_longlong),
+        "gw_ctx_profile": ([P, I, C.c_char_p], I),
+        "gw_ctx_profile_get": ([P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], I),
         "gw_mol_upload": ([P, C.POINTER(MoleculeDesc), pp], I),
         "gw_mol_free": ([P], None),
         "gw_build_chi0": ([P, P, C.POINTER(Grid), I, pp], I),
@@ -148,6 +150,15 @@ class Context:
     @property
     def launch_count(self):
         return load().gw_ctx_launch_count(self.handle)
+
+    def profile(self, enable=True, kernel=None):
+        """Time launches of one kernel (or all) with CUDA events on the context stream."""
+        _check(self, load().gw_ctx_profile(self.handle, int(enable), kernel.encode() if kernel else None))
+
+    def profile_get(self, kernel):
+        ms, n = C.c_double(), C.c_longlong()
+        _check(self, load().gw_ctx_profile_get(self.handle, kernel.encode(), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
 
 class _Desc:

@@ -24,3 +24,31 @@ def cfg1_oracle(cfg1):
     import oracle
     mol, grid = cfg1
     return oracle.solve(mol, grid)
+
+
+@pytest.fixture(scope="session")
+def gwlib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1101_2065_gb300 as gw
+    return gw
+
+
+@pytest.fixture(scope="session")
+def ctx(gwlib):
+    c = gwlib.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="session")
+def cfg2():
+    import synth
+    return synth.make_config(2)
+
+
+@pytest.fixture(scope="session")
+def cfg2_oracle(cfg2):
+    import oracle
+    mol, grid = cfg2
+    return oracle.solve(mol, grid, keep_W_freqs=[1, 100, 400, 1023])

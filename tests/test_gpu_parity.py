@@ -28,32 +28,6 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-@pytest.fixture(scope="session")
-def gwlib():
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_1101_2065_gb300 as gw
-    return gw
-
-
-@pytest.fixture(scope="session")
-def ctx(gwlib):
-    c = gwlib.Context(0)
-    yield c
-    c.close()
-
-
-@pytest.fixture(scope="session")
-def cfg2():
-    return synth.make_config(2)
-
-
-@pytest.fixture(scope="session")
-def cfg2_oracle(cfg2):
-    mol, grid = cfg2
-    return oracle.solve(mol, grid, keep_W_freqs=[1, 100, 400, 1023])
-
-
 def _run(gw, ctx, mol, grid, Z=None, states=None, vxc=None):
     return gw.solve(ctx, mol, grid, states=states, vxc=vxc, Z=Z)
 
