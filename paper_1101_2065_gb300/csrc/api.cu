@@ -376,7 +376,7 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
     while ((1 << c->logL) < c->L) c->logL++;
     const int n_prod = mol->n_prod, n_sub = mol->n_sub, n_pair = c->n_pair;
     double* VEFt = nullptr;
-    double *T1 = nullptr, *g = nullptr, *evals = nullptr, *evecs = nullptr, *Bsel = nullptr;
+    double *T1 = nullptr, *g = nullptr, *Bsel = nullptr;
     int* occ = nullptr; int* virt = nullptr; int* rank_of = nullptr;
     try {
         // a0: pair table
@@ -409,12 +409,8 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
             // T1 = v X_r, g = X_r^T v X_r  (X_r = first nr columns of VEFt)
             gemm_f64(ctx, false, false, n_prod, nr, n_prod, 1.0, mol->v, n_prod, VEFt, n_pair, 0.0, T1, nr);
             gemm_f64(ctx, true, false, nr, nr, n_prod, 1.0, VEFt, n_pair, T1, nr, 0.0, g, nr);
-            int np = nr + (nr & 1);
-            evals = dalloc<double>(ctx, np);
-            evecs = dalloc<double>(ctx, (size_t)np * np);
-            jacobi_eigh(ctx, g, nr, evals, evecs);
             Bsel = dalloc<double>(ctx, (size_t)nr * n_sub);
-            select_top_scaled(ctx, evals, evecs, nr, n_sub, Bsel);
+            eigh_top_scaled(ctx, g, nr, n_sub, prec == GW_FP64 ? 2 : 1, Bsel);
             c->Z = dalloc<double>(ctx, (size_t)n_prod * n_sub);
             gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, VEFt, n_pair, Bsel, n_sub, 0.0, c->Z, n_sub);
             gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, T1, nr, Bsel, n_sub, 0.0, c->Zup, n_sub);
@@ -424,7 +420,6 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
         gemm_f64(ctx, true, false, n_sub, n_pair, n_prod, 1.0, c->Zup, n_sub, VEFt, n_pair, 0.0, c->Ut, n_pair);
         ctx_free(ctx, VEFt); VEFt = nullptr;
         ctx_free(ctx, T1); T1 = nullptr; ctx_free(ctx, g); g = nullptr;
-        ctx_free(ctx, evals); evals = nullptr; ctx_free(ctx, evecs); evecs = nullptr;
         ctx_free(ctx, Bsel); Bsel = nullptr;
         ctx_free(ctx, occ); occ = nullptr; ctx_free(ctx, virt); virt = nullptr;
         ctx_free(ctx, rank_of); rank_of = nullptr;
@@ -433,8 +428,7 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
         launch_chi0_fft(ctx, c);
         ctx_finish(ctx, "gw_build_chi0");
     } catch (...) {
-        ctx_free(ctx, VEFt); ctx_free(ctx, T1); ctx_free(ctx, g); ctx_free(ctx, evals);
-        ctx_free(ctx, evecs); ctx_free(ctx, Bsel); ctx_free(ctx, occ); ctx_free(ctx, virt);
+        ctx_free(ctx, VEFt); ctx_free(ctx, T1); ctx_free(ctx, g); ctx_free(ctx, Bsel); ctx_free(ctx, occ); ctx_free(ctx, virt);
         ctx_free(ctx, rank_of);
         chi0_release(c);
         throw;

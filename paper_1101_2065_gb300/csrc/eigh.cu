@@ -1,0 +1,409 @@
+// a0: dominant eigenpairs of g = X_r^T v X_r (Eqs. projector0, subspace).
+//
+// Mixed-precision symmetric eigensolver:
+//  1. binary32 Householder tridiagonalisation T = Q^T g Q in one CTA (the
+//     n x n matrix stays resident in L2; reflector k is kept in row k);
+//  2. all eigenvalues of T by bisection on Sturm counts (one thread each);
+//  3. eigenvectors of T by inverse iteration with a pivoted tridiagonal LU,
+//     Gram-Schmidt inside clusters of close eigenvalues (one thread per
+//     cluster);
+//  4. back-transformation X = Q Y (one warp per vector);
+//  5. binary64 refinement of the full eigenbasis by the iteration of Ogita
+//     and Aishima (2018): R = I - X^T X, S = X^T g X,
+//     lambda_i = S_ii / (1 - R_ii), E_ij = (S_ij + lambda_j R_ij)/(lambda_j -
+//     lambda_i) for well separated pairs, R_ij / 2 otherwise, X <- X + X E;
+//     each step squares the error (binary64 GEMMs only);
+//  6. the n_sub largest eigenpairs are selected, their block re-orthonormalised
+//     by one Newton-Schulz step X <- X (3 I - X^T X) / 2, and scaled by
+//     lambda^-1/2 (Eq. subspace).
+#include <cmath>
+
+#include "internal.h"
+
+namespace {
+
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide sum for a 1024-thread CTA; red has 33 floats
+__device__ float block_sum1024(float v, float* red) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        w = warp_sum(w);
+        if (threadIdx.x == 0) red[32] = w;
+    }
+    __syncthreads();
+    float r = red[32];
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------------------ 1
+__global__ void __launch_bounds__(1024) k_sytrd32(float* __restrict__ A, int n, float* __restrict__ d,
+                                                  float* __restrict__ e, float* __restrict__ tau) {
+    extern __shared__ float sm[];
+    float* sv = sm;          // reflector
+    float* sw = sm + n;      // p, then w
+    __shared__ float red[33];
+    __shared__ float s_par[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        float* rowk = A + (long long)k * n + k + 1;
+        float part = 0.f;
+        for (int j = tid; j < m; j += blockDim.x) {
+            float x = rowk[j];
+            sv[j] = x;
+            part += x * x;
+        }
+        float sig = block_sum1024(part, red);
+        if (tid == 0) {
+            float x0 = sv[0];
+            float alpha = sig > 0.f ? -copysignf(sqrtf(sig), x0) : 0.f;
+            float v0 = x0 - alpha;
+            float vtv = sig - x0 * x0 + v0 * v0;
+            float t = vtv > 0.f ? 2.f / vtv : 0.f;
+            sv[0] = v0;
+            d[k] = A[(long long)k * n + k];
+            e[k] = sig > 0.f ? alpha : x0;
+            tau[k] = t;
+            s_par[0] = t;
+        }
+        __syncthreads();
+        const float t = s_par[0];
+        for (int j = tid; j < m; j += blockDim.x) rowk[j] = sv[j];     // keep the reflector
+        // p = t A22 v, one warp per row
+        for (int i = warp; i < m; i += nw) {
+            const float* ri = A + (long long)(k + 1 + i) * n + k + 1;
+            float acc = 0.f;
+            for (int j = lane; j < m; j += 32) acc += ri[j] * sv[j];
+            acc = warp_sum(acc);
+            if (lane == 0) sw[i] = t * acc;
+        }
+        __syncthreads();
+        float pv = 0.f;
+        for (int j = tid; j < m; j += blockDim.x) pv += sw[j] * sv[j];
+        const float K = 0.5f * t * block_sum1024(pv, red);
+        for (int j = tid; j < m; j += blockDim.x) sw[j] -= K * sv[j];
+        __syncthreads();
+        // A22 -= v w^T + w v^T
+        for (int i = warp; i < m; i += nw) {
+            float* ri = A + (long long)(k + 1 + i) * n + k + 1;
+            const float vi = sv[i], wi = sw[i];
+            for (int j = lane; j < m; j += 32) ri[j] -= vi * sw[j] + wi * sv[j];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (n >= 2) {
+            d[n - 2] = A[(long long)(n - 2) * n + n - 2];
+            e[n - 2] = A[(long long)(n - 1) * n + n - 2];
+        }
+        d[n - 1] = A[(long long)(n - 1) * n + n - 1];
+        if (n >= 2) tau[n - 2] = 0.f;
+        tau[n - 1] = 0.f;
+    }
+}
+
+// ------------------------------------------------------------------ 2
+__device__ int sturm_count(const float* __restrict__ d, const float* __restrict__ e, int n, float x, float tiny) {
+    int c = 0;
+    float q = d[0] - x;
+    if (q < 0.f) ++c;
+    for (int i = 1; i < n; ++i) {
+        if (fabsf(q) < tiny) q = -tiny;
+        q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
+        if (q < 0.f) ++c;
+    }
+    return c;
+}
+
+__global__ void k_bisect(const float* __restrict__ d, const float* __restrict__ e, int n, float bnd,
+                         float* __restrict__ lam) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float lo = -bnd, hi = bnd;
+    const float tiny = 1e-30f;
+    for (int it = 0; it < 40; ++it) {
+        float mid = 0.5f * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (sturm_count(d, e, n, mid, tiny) <= i) lo = mid; else hi = mid;
+    }
+    lam[i] = 0.5f * (lo + hi);
+}
+
+// ------------------------------------------------------------------ 3
+// Solve (T - lam) x = b in place (b -> x) with the pivoted LU held in ws.
+__device__ void tri_factor(const float* __restrict__ d, const float* __restrict__ e, int n, float lam, float tiny,
+                           float* du, float* du1, float* du2, float* mul, unsigned char* piv) {
+    float ca = d[0] - lam, cb = n > 1 ? e[0] : 0.f;
+    for (int i = 0; i + 1 < n; ++i) {
+        const float c = e[i];
+        const float a1 = d[i + 1] - lam;
+        const float b1 = (i + 2 < n) ? e[i + 1] : 0.f;
+        if (fabsf(c) > fabsf(ca)) {
+            float m = ca / c;
+            du[i] = c; du1[i] = a1; du2[i] = b1; mul[i] = m; piv[i] = 1;
+            ca = cb - m * a1;
+            cb = -m * b1;
+        } else {
+            if (fabsf(ca) < tiny) ca = copysignf(tiny, ca);
+            float m = c / ca;
+            du[i] = ca; du1[i] = cb; du2[i] = 0.f; mul[i] = m; piv[i] = 0;
+            ca = a1 - m * cb;
+            cb = b1;
+        }
+    }
+    if (fabsf(ca) < tiny) ca = copysignf(tiny, ca);
+    du[n - 1] = ca;
+}
+
+__device__ void tri_solve(int n, const float* du, const float* du1, const float* du2, const float* mul,
+                          const unsigned char* piv, float* x) {
+    for (int i = 0; i + 1 < n; ++i) {
+        if (piv[i]) { float t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
+        x[i + 1] -= mul[i] * x[i];
+    }
+    x[n - 1] /= du[n - 1];
+    if (n >= 2) x[n - 2] = (x[n - 2] - du1[n - 2] * x[n - 1]) / du[n - 2];
+    for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du1[i] * x[i + 1] - du2[i] * x[i + 2]) / du[i];
+}
+
+// One thread per cluster (maximal run of eigenvalues with gaps < tol).
+__global__ void k_invit(const float* __restrict__ d, const float* __restrict__ e, const float* __restrict__ lam, int n,
+                        float tol, float tiny, float* __restrict__ Y, float* __restrict__ ws,
+                        unsigned char* __restrict__ pv) {
+    int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 >= n) return;
+    if (i0 > 0 && lam[i0] - lam[i0 - 1] < tol) return;      // not a cluster start
+    float* du = ws + (long long)i0 * 4 * n;
+    float* du1 = du + n;
+    float* du2 = du1 + n;
+    float* mul = du2 + n;
+    unsigned char* piv = pv + (long long)i0 * n;
+    for (int i = i0; i < n && (i == i0 || lam[i] - lam[i - 1] < tol); ++i) {
+        float* x = Y + (long long)i * n;
+        tri_factor(d, e, n, lam[i], tiny, du, du1, du2, mul, piv);
+        for (int j = 0; j < n; ++j) x[j] = 1.f + 0.001f * (float)((j * 7 + i * 13) % 17);
+        for (int it = 0; it < 3; ++it) {
+            tri_solve(n, du, du1, du2, mul, piv, x);
+            for (int pass = 0; pass < 2; ++pass)
+                for (int q = i0; q < i; ++q) {
+                    const float* y = Y + (long long)q * n;
+                    float s = 0.f;
+                    for (int j = 0; j < n; ++j) s += y[j] * x[j];
+                    for (int j = 0; j < n; ++j) x[j] -= s * y[j];
+                }
+            float nr = 0.f;
+            for (int j = 0; j < n; ++j) nr += x[j] * x[j];
+            nr = rsqrtf(fmaxf(nr, 1e-38f));
+            for (int j = 0; j < n; ++j) x[j] *= nr;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ 4
+// X[:, i] = Q Y[i], Q = H_0 ... H_{n-3}; one warp per eigenvector.
+__global__ void __launch_bounds__(256) k_backtransform(const float* __restrict__ A, const float* __restrict__ tau,
+                                                       int n, const float* __restrict__ Y, double* __restrict__ X) {
+    extern __shared__ float sy[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * (blockDim.x >> 5) + w;
+    if (i >= n) return;
+    float* y = sy + (long long)w * n;
+    for (int j = lane; j < n; j += 32) y[j] = Y[(long long)i * n + j];
+    __syncwarp();
+    for (int k = n - 3; k >= 0; --k) {
+        const float t = tau[k];
+        if (t == 0.f) continue;
+        const float* v = A + (long long)k * n + k + 1;
+        float s = 0.f;
+        for (int j = lane; j < n - k - 1; j += 32) s += v[j] * y[k + 1 + j];
+        s = warp_sum(s) * t;
+        for (int j = lane; j < n - k - 1; j += 32) y[k + 1 + j] -= s * v[j];
+        __syncwarp();
+    }
+    for (int j = lane; j < n; j += 32) X[(long long)j * n + i] = (double)y[j];
+}
+
+// ------------------------------------------------------------------ 5
+__global__ void k_identity_minus(double* __restrict__ R, int n) {     // R <- I - R
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)n * n) return;
+    int i = (int)(t / n), j = (int)(t % n);
+    R[t] = (i == j ? 1.0 : 0.0) - R[t];
+}
+
+// lam_i = S_ii/(1 - R_ii); sums for delta (single CTA, deterministic)
+__global__ void __launch_bounds__(1024) k_oa_stats(const double* __restrict__ S, const double* __restrict__ R,
+                                                   const double* __restrict__ g, int n, double* __restrict__ lam,
+                                                   double* __restrict__ out) {
+    __shared__ double s1[1024], s2[1024], s3[1024];
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        lam[i] = S[(long long)i * n + i] / (1.0 - R[(long long)i * n + i]);
+    __syncthreads();
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
+        int i = (int)(t / n), j = (int)(t % n);
+        double s = S[t] - (i == j ? lam[i] : 0.0);
+        a += s * s;
+        b += R[t] * R[t];
+        c += g[t] * g[t];
+    }
+    s1[threadIdx.x] = a; s2[threadIdx.x] = b; s3[threadIdx.x] = c;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            s1[threadIdx.x] += s1[threadIdx.x + s];
+            s2[threadIdx.x] += s2[threadIdx.x + s];
+            s3[threadIdx.x] += s3[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = 2.0 * (sqrt(s1[0]) + sqrt(s3[0]) * sqrt(s2[0]));
+}
+
+__global__ void k_oa_E(const double* __restrict__ S, const double* __restrict__ R, const double* __restrict__ lam,
+                       const double* __restrict__ delta, int n, double* __restrict__ E) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)n * n) return;
+    int i = (int)(t / n), j = (int)(t % n);
+    double r = R[t];
+    if (i == j) { E[t] = 0.5 * r; return; }
+    double dl = lam[j] - lam[i];
+    E[t] = fabs(dl) > *delta ? (S[t] + lam[j] * r) / dl : 0.5 * r;
+}
+
+// ------------------------------------------------------------------ 6
+__global__ void k_rank_desc_ld(const double* __restrict__ ev, int n, int n_sub, int* __restrict__ sel) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double e = ev[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) {
+        double f = ev[j];
+        r += (f > e) || (f == e && j < i);
+    }
+    if (r < n_sub) sel[r] = i;
+}
+
+__global__ void k_gather_cols(const double* __restrict__ X, int n, int n_sub, const int* __restrict__ sel,
+                              double* __restrict__ B) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)n * n_sub) return;
+    int row = (int)(t / n_sub), k = (int)(t % n_sub);
+    B[t] = X[(long long)row * n + sel[k]];
+}
+
+__global__ void k_ns_coeff(double* __restrict__ G, int m) {          // G <- (3 I - G)/2
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)m * m) return;
+    int i = (int)(t / m), j = (int)(t % m);
+    G[t] = 0.5 * ((i == j ? 3.0 : 0.0) - G[t]);
+}
+
+__global__ void k_scale_cols(double* __restrict__ B, int n, int n_sub, const double* __restrict__ lam,
+                             const int* __restrict__ sel, int* status) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t == 0) {
+        double lmax = lam[sel[0]], lmin = lam[sel[n_sub - 1]];
+        if (!(lmin >= 1e-12 * lmax) || !(lmax > 0.0)) atomicOr(status, ST_RANK);
+    }
+    if (t >= (long long)n * n_sub) return;
+    double l = lam[sel[(int)(t % n_sub)]];
+    B[t] = l > 0.0 ? B[t] / sqrt(l) : 0.0;
+}
+
+}  // namespace
+
+void launch_to_f32(gw_ctx* ctx, const double* a, float* b, long long n);
+
+// g (n x n, binary64, symmetric) -> B (n x n_sub) = xi_top lambda_top^-1/2
+void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iters, double* B) {
+    const long long nn = (long long)n * n;
+    float* A32 = nullptr; float *d = nullptr, *e = nullptr, *tau = nullptr, *lam32 = nullptr, *Y = nullptr;
+    float* ws = nullptr; unsigned char* pv = nullptr;
+    double *X = nullptr, *X2 = nullptr, *R = nullptr, *S = nullptr, *T = nullptr, *E = nullptr, *lam = nullptr;
+    double *stat = nullptr, *G = nullptr, *Bt = nullptr;
+    int* sel = nullptr;
+    auto release = [&]() {
+        for (void* p : {(void*)A32, (void*)d, (void*)e, (void*)tau, (void*)lam32, (void*)Y, (void*)ws, (void*)pv,
+                        (void*)X, (void*)X2, (void*)R, (void*)S, (void*)T, (void*)E, (void*)lam, (void*)stat,
+                        (void*)G, (void*)Bt, (void*)sel})
+            ctx_free(ctx, p);
+    };
+    try {
+        A32 = dalloc<float>(ctx, nn);
+        d = dalloc<float>(ctx, n); e = dalloc<float>(ctx, n); tau = dalloc<float>(ctx, n);
+        lam32 = dalloc<float>(ctx, n);
+        Y = dalloc<float>(ctx, nn);
+        ws = dalloc<float>(ctx, 4 * nn);
+        pv = dalloc<unsigned char>(ctx, nn);
+        X = dalloc<double>(ctx, nn);
+        launch_to_f32(ctx, g, A32, nn);
+        size_t smem = 2 * (size_t)n * sizeof(float);
+        if (smem > 200 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for the eigensolver");
+        CUDA_CHECK(cudaFuncSetAttribute(k_sytrd32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        klaunch(ctx, "k_sytrd32", k_sytrd32, 1, 1024, smem, A32, n, d, e, tau);
+        // Gershgorin bound of T (host needs d, e: small copy)
+        std::vector<float> hd(n), he(n);
+        CUDA_CHECK(cudaMemcpyAsync(hd.data(), d, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_CHECK(cudaMemcpyAsync(he.data(), e, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        float bnd = 0.f;
+        for (int i = 0; i < n; ++i) {
+            float r = std::fabs(hd[i]) + (i > 0 ? std::fabs(he[i - 1]) : 0.f) + (i + 1 < n ? std::fabs(he[i]) : 0.f);
+            bnd = std::max(bnd, r);
+        }
+        bnd = bnd * 1.01f + 1e-30f;
+        klaunch(ctx, "k_bisect", k_bisect, div_up(n, 64), 64, 0, (const float*)d, (const float*)e, n, bnd, lam32);
+        klaunch(ctx, "k_invit", k_invit, div_up(n, 64), 64, 0, (const float*)d, (const float*)e,
+                (const float*)lam32, n, 1e-4f * bnd, 1e-7f * bnd, Y, ws, pv);
+        klaunch(ctx, "k_backtransform", k_backtransform, div_up(n, 8), 256, 8 * (size_t)n * sizeof(float),
+                (const float*)A32, (const float*)tau, n, (const float*)Y, X);
+        // binary64 refinement
+        X2 = dalloc<double>(ctx, nn); R = dalloc<double>(ctx, nn); S = dalloc<double>(ctx, nn);
+        T = dalloc<double>(ctx, nn); E = dalloc<double>(ctx, nn); lam = dalloc<double>(ctx, n);
+        stat = dalloc<double>(ctx, 2);
+        for (int it = 0; it < oa_iters; ++it) {
+            gemm_f64(ctx, true, false, n, n, n, 1.0, X, n, X, n, 0.0, R, n);           // X^T X
+            klaunch(ctx, "k_identity_minus", k_identity_minus, div_up(nn, 256), 256, 0, R, n);
+            gemm_f64(ctx, false, false, n, n, n, 1.0, g, n, X, n, 0.0, T, n);          // g X
+            gemm_f64(ctx, true, false, n, n, n, 1.0, X, n, T, n, 0.0, S, n);           // X^T g X
+            klaunch(ctx, "k_oa_stats", k_oa_stats, 1, 1024, 0, (const double*)S, (const double*)R, g, n, lam, stat);
+            klaunch(ctx, "k_oa_E", k_oa_E, div_up(nn, 256), 256, 0, (const double*)S, (const double*)R,
+                    (const double*)lam, (const double*)stat, n, E);
+            CUDA_CHECK(cudaMemcpyAsync(X2, X, nn * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+            gemm_f64(ctx, false, false, n, n, n, 1.0, X, n, E, n, 1.0, X2, n);         // X + X E
+            std::swap(X, X2);
+        }
+        if (oa_iters == 0) {
+            // Rayleigh quotients of the binary32 vectors
+            gemm_f64(ctx, false, false, n, n, n, 1.0, g, n, X, n, 0.0, T, n);
+            gemm_f64(ctx, true, false, n, n, n, 1.0, X, n, T, n, 0.0, S, n);
+            CUDA_CHECK(cudaMemsetAsync(R, 0, nn * sizeof(double), ctx->stream));
+            klaunch(ctx, "k_oa_stats", k_oa_stats, 1, 1024, 0, (const double*)S, (const double*)R, g, n, lam, stat);
+        }
+        // select, re-orthonormalise, scale
+        sel = dalloc<int>(ctx, n_sub);
+        klaunch(ctx, "k_rank_desc_ld", k_rank_desc_ld, div_up(n, 256), 256, 0, (const double*)lam, n, n_sub, sel);
+        Bt = dalloc<double>(ctx, (size_t)n * n_sub);
+        G = dalloc<double>(ctx, (size_t)n_sub * n_sub);
+        klaunch(ctx, "k_gather_cols", k_gather_cols, div_up((long long)n * n_sub, 256), 256, 0, (const double*)X, n,
+                n_sub, (const int*)sel, Bt);
+        gemm_f64(ctx, true, false, n_sub, n_sub, n, 1.0, Bt, n_sub, Bt, n_sub, 0.0, G, n_sub);
+        klaunch(ctx, "k_ns_coeff", k_ns_coeff, div_up((long long)n_sub * n_sub, 256), 256, 0, G, n_sub);
+        gemm_f64(ctx, false, false, n, n_sub, n_sub, 1.0, Bt, n_sub, G, n_sub, 0.0, B, n_sub);
+        klaunch(ctx, "k_scale_cols", k_scale_cols, div_up((long long)n * n_sub, 256), 256, 0, B, n, n_sub,
+                (const double*)lam, (const int*)sel, ctx->d_status);
+    } catch (...) {
+        release();
+        throw;
+    }
+    release();
+}

@@ -164,13 +164,13 @@ void gemm_f64(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, double alpha,
               long long sC = 0);
 // linalg.cu
 void cholesky_lower(gw_ctx* ctx, double* A, int n);          // in place, zeroes upper
-int jacobi_eigh(gw_ctx* ctx, double* A, int n, double* evals, double* evecs);  // returns sweeps
-void select_top_scaled(gw_ctx* ctx, const double* evals, const double* evecs, int n,
-                       int n_sub, double* Bsel);
+// eigh.cu: B = xi lambda^-1/2 for the n_sub largest eigenpairs of g
+void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iters, double* B);
 // chi0.cu
 void launch_fft_tables(gw_ctx* ctx, gw_chi0* c);
 void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c);
 void launch_spectral_readback(gw_ctx* ctx, const gw_chi0* c, int j0, int nj, double* A);
+void launch_to_f32(gw_ctx* ctx, const double* a, float* b, long long n);
 // screen.cu
 void launch_ldlt(gw_ctx* ctx, gw_W* W);
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* c);
