@@ -151,7 +151,7 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ GPU arm
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 FMA/clk/SM x 152 SMs at 2070 MHz
-KERNELS = ["k_forms", "k_forms32", "k_ldlt", "k_ldlt32", "k_chi0_fft", "k_chi0_fft32", "k_dgemm", "k_sytrd32",
+KERNELS = ["k_forms", "k_forms32", "k_ldlt", "k_ldlt32", "k_chi0_fft", "k_chi0_fft32", "k_dgemm", "k_sytrd32", "k_sytrd32_cl", "k_cluster_mgs",
            "k_bisect", "k_invit", "k_backtransform", "k_oa_stats", "k_oa_E", "k_vertex_contract", "k_sigma_c",
            "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_to_f32", "k_kernel_spectra"]
 
@@ -172,7 +172,7 @@ def kernel_model(name, mol, grid, n_rank):
         # per element pair: one forward and two inverse complex FFTs of length L (5 L log2 L flops each)
         pairs = (n * (n + 1) // 2 + 1) // 2
         return pairs * 3 * 5.0 * L * math.log2(L), "alu", peak
-    if name == "k_sytrd32":
+    if name.startswith("k_sytrd32"):
         # Householder tridiagonalisation: matvec + rank-2 update, 4 n^3/3 multiply-adds
         return (8.0 / 3.0) * n_rank ** 3, "alu", PEAK_FP32_TFLOPS
     return None, None, None

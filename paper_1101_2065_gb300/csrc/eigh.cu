@@ -1,12 +1,14 @@
 // a0: dominant eigenpairs of g = X_r^T v X_r (Eqs. projector0, subspace).
 //
 // Mixed-precision symmetric eigensolver:
-//  1. binary32 Householder tridiagonalisation T = Q^T g Q in one CTA (the
-//     n x n matrix stays resident in L2; reflector k is kept in row k);
+//  1. binary32 Householder tridiagonalisation T = Q^T g Q on a cluster of 8
+//     CTAs holding the matrix row-cyclically in distributed shared memory
+//     (one CTA with the matrix in L2 when it does not fit); reflector k is
+//     kept in row k of the global copy;
 //  2. all eigenvalues of T by bisection on Sturm counts (one thread each);
-//  3. eigenvectors of T by inverse iteration with a pivoted tridiagonal LU,
-//     Gram-Schmidt inside clusters of close eigenvalues (one thread per
-//     cluster);
+//  3. eigenvectors of T by inverse iteration with a pivoted tridiagonal LU
+//     (one thread per eigenvalue), then modified Gram-Schmidt inside each
+//     cluster of close eigenvalues (one CTA per cluster);
 //  4. back-transformation X = Q Y (one warp per vector);
 //  5. binary64 refinement of the full eigenbasis by the iteration of Ogita
 //     and Aishima (2018): R = I - X^T X, S = X^T g X,
@@ -16,9 +18,13 @@
 //  6. the n_sub largest eigenpairs are selected, their block re-orthonormalised
 //     by one Newton-Schulz step X <- X (3 I - X^T X) / 2, and scaled by
 //     lambda^-1/2 (Eq. subspace).
+#include <cooperative_groups.h>
+
 #include <cmath>
 
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -110,6 +116,122 @@ __global__ void __launch_bounds__(1024) k_sytrd32(float* __restrict__ A, int n, 
     }
 }
 
+// Same reduction on a cluster of CL CTAs: CTA r holds the rows i = r (mod CL)
+// of the matrix in its shared memory; the reflector, the partial dot
+// products and w travel through distributed shared memory.
+constexpr int CL = 8;
+
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024)
+    k_sytrd32_cl(float* __restrict__ A, int n, float* __restrict__ d, float* __restrict__ e, float* __restrict__ tau) {
+    extern __shared__ float sm[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int rows = (n + CL - 1) / CL;
+    float* Ar = sm;                       // [rows][n] own rows
+    float* sv = Ar + (long long)rows * n; // [n] reflector (full)
+    float* sw = sv + n;                   // [n] w (full)
+    float* own_w = sw + n;                // [rows] w of own rows
+    float* own_p = own_w + rows;          // [rows] p of own rows
+    __shared__ float red[33];
+    __shared__ float s_part;
+    __shared__ float s_tau;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (long long t = tid; t < (long long)rows * n; t += blockDim.x) {
+        int li = (int)(t / n), j = (int)(t % n);
+        int i = li * CL + rank;
+        Ar[t] = i < n ? A[(long long)i * n + j] : 0.f;
+    }
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        const int owner = k % CL;
+        cluster.sync();
+        if (rank == owner) {
+            float* rk = Ar + (long long)(k / CL) * n + k + 1;
+            float part = 0.f;
+            for (int j = tid; j < m; j += blockDim.x) {
+                float x = rk[j];
+                sv[j] = x;
+                part += x * x;
+            }
+            float sig = block_sum1024(part, red);
+            if (tid == 0) {
+                float x0 = sv[0];
+                float alpha = sig > 0.f ? -copysignf(sqrtf(sig), x0) : 0.f;
+                float v0 = x0 - alpha;
+                float vtv = sig - x0 * x0 + v0 * v0;
+                float t = vtv > 0.f ? 2.f / vtv : 0.f;
+                sv[0] = v0;
+                d[k] = Ar[(long long)(k / CL) * n + k];
+                e[k] = sig > 0.f ? alpha : x0;
+                tau[k] = t;
+                s_tau = t;
+            }
+            __syncthreads();
+            for (int j = tid; j < m; j += blockDim.x) A[(long long)k * n + k + 1 + j] = sv[j];   // reflector
+        }
+        cluster.sync();
+        if (rank != owner) {
+            const float* rv = cluster.map_shared_rank(sv, owner);
+            for (int j = tid; j < m; j += blockDim.x) sv[j] = rv[j];
+            if (tid == 0) s_tau = *cluster.map_shared_rank(&s_tau, owner);
+        }
+        __syncthreads();
+        const float t = s_tau;
+        // own rows i > k: p_i = t sum_j A[i][j] v_j
+        const int li0 = (k + 1 - rank + CL - 1) / CL;      // first own row index with i >= k+1
+        float pv = 0.f;
+        for (int li = li0 + warp; li < rows; li += nw) {
+            const int i = li * CL + rank;
+            if (i >= n) break;
+            const float* ri = Ar + (long long)li * n + k + 1;
+            float acc = 0.f;
+            for (int j = lane; j < m; j += 32) acc += ri[j] * sv[j];
+            acc = warp_sum(acc) * t;
+            if (lane == 0) {
+                own_p[li] = acc;
+                pv += acc * sv[i - k - 1];
+            }
+        }
+        pv = block_sum1024(pv, red);
+        if (tid == 0) s_part = pv;
+        cluster.sync();
+        float tot = 0.f;
+        for (int r = 0; r < CL; ++r) tot += *cluster.map_shared_rank(&s_part, r);
+        const float K = 0.5f * t * tot;
+        for (int li = li0 + tid; li < rows; li += blockDim.x) {
+            const int i = li * CL + rank;
+            if (i < n) own_w[li] = own_p[li] - K * sv[i - k - 1];
+        }
+        cluster.sync();
+        for (int j = tid; j < m; j += blockDim.x) {
+            const int i = k + 1 + j;
+            sw[j] = *cluster.map_shared_rank(own_w + i / CL, i % CL);
+        }
+        __syncthreads();
+        for (int li = li0 + warp; li < rows; li += nw) {
+            const int i = li * CL + rank;
+            if (i >= n) break;
+            float* ri = Ar + (long long)li * n + k + 1;
+            const float vi = sv[i - k - 1], wi = sw[i - k - 1];
+            for (int j = lane; j < m; j += 32) ri[j] -= vi * sw[j] + wi * sv[j];
+        }
+    }
+    cluster.sync();
+    if (tid == 0 && n >= 2) {
+        const int a = n - 2, b = n - 1;
+        if (a % CL == rank) {
+            d[a] = Ar[(long long)(a / CL) * n + a];
+            tau[a] = 0.f;
+        }
+        if (b % CL == rank) {
+            d[b] = Ar[(long long)(b / CL) * n + b];
+            e[a] = Ar[(long long)(b / CL) * n + a];
+            tau[b] = 0.f;
+        }
+    }
+    cluster.sync();
+}
+
 // ------------------------------------------------------------------ 2
 __device__ int sturm_count(const float* __restrict__ d, const float* __restrict__ e, int n, float x, float tiny) {
     int c = 0;
@@ -174,36 +296,62 @@ __device__ void tri_solve(int n, const float* du, const float* du1, const float*
     for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du1[i] * x[i + 1] - du2[i] * x[i + 2]) / du[i];
 }
 
-// One thread per cluster (maximal run of eigenvalues with gaps < tol).
-__global__ void k_invit(const float* __restrict__ d, const float* __restrict__ e, const float* __restrict__ lam, int n,
-                        float tol, float tiny, float* __restrict__ Y, float* __restrict__ ws,
-                        unsigned char* __restrict__ pv) {
-    int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i0 >= n) return;
-    if (i0 > 0 && lam[i0] - lam[i0 - 1] < tol) return;      // not a cluster start
-    float* du = ws + (long long)i0 * 4 * n;
+// Inverse iteration, one thread per eigenvalue; the pivoted LU of T - lam
+// lives in shared memory (IT threads per CTA).  Vectors of close eigenvalues
+// are orthogonalised afterwards by k_cluster_mgs.
+constexpr int IT = 8;
+
+__global__ void __launch_bounds__(IT) k_invit(const float* __restrict__ d, const float* __restrict__ e,
+                                              const float* __restrict__ lam, int n, float tiny,
+                                              float* __restrict__ Y) {
+    extern __shared__ float sws[];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float* du = sws + (long long)threadIdx.x * 5 * n;
     float* du1 = du + n;
     float* du2 = du1 + n;
     float* mul = du2 + n;
-    unsigned char* piv = pv + (long long)i0 * n;
-    for (int i = i0; i < n && (i == i0 || lam[i] - lam[i - 1] < tol); ++i) {
+    float* x = mul + n;
+    unsigned char* piv = reinterpret_cast<unsigned char*>(sws + (long long)IT * 5 * n) + (long long)threadIdx.x * n;
+    tri_factor(d, e, n, lam[i], tiny, du, du1, du2, mul, piv);
+    for (int j = 0; j < n; ++j) x[j] = 1.f + 0.001f * (float)((j * 7 + i * 13) % 17);
+    for (int it = 0; it < 3; ++it) {
+        tri_solve(n, du, du1, du2, mul, piv, x);
+        float nr = 0.f;
+        for (int j = 0; j < n; ++j) nr += x[j] * x[j];
+        nr = rsqrtf(fmaxf(nr, 1e-38f));
+        for (int j = 0; j < n; ++j) x[j] *= nr;
+    }
+    float* yo = Y + (long long)i * n;
+    for (int j = 0; j < n; ++j) yo[j] = x[j];
+}
+
+// Modified Gram-Schmidt inside each cluster (maximal run of eigenvalues with
+// consecutive gaps < tol), one CTA per cluster start, twice.
+__global__ void __launch_bounds__(256) k_cluster_mgs(const float* __restrict__ lam, int n, float tol,
+                                                     float* __restrict__ Y) {
+    __shared__ float red[33];
+    const int i0 = blockIdx.x;
+    if (i0 > 0 && lam[i0] - lam[i0 - 1] < tol) return;
+    int i1 = i0 + 1;
+    while (i1 < n && lam[i1] - lam[i1 - 1] < tol) ++i1;
+    if (i1 - i0 < 2) return;
+    for (int i = i0; i < i1; ++i) {
         float* x = Y + (long long)i * n;
-        tri_factor(d, e, n, lam[i], tiny, du, du1, du2, mul, piv);
-        for (int j = 0; j < n; ++j) x[j] = 1.f + 0.001f * (float)((j * 7 + i * 13) % 17);
-        for (int it = 0; it < 3; ++it) {
-            tri_solve(n, du, du1, du2, mul, piv, x);
-            for (int pass = 0; pass < 2; ++pass)
-                for (int q = i0; q < i; ++q) {
-                    const float* y = Y + (long long)q * n;
-                    float s = 0.f;
-                    for (int j = 0; j < n; ++j) s += y[j] * x[j];
-                    for (int j = 0; j < n; ++j) x[j] -= s * y[j];
-                }
-            float nr = 0.f;
-            for (int j = 0; j < n; ++j) nr += x[j] * x[j];
-            nr = rsqrtf(fmaxf(nr, 1e-38f));
-            for (int j = 0; j < n; ++j) x[j] *= nr;
-        }
+        for (int pass = 0; pass < 2; ++pass)
+            for (int q = i0; q < i; ++q) {
+                const float* y = Y + (long long)q * n;
+                float s = 0.f;
+                for (int j = threadIdx.x; j < n; j += blockDim.x) s += y[j] * x[j];
+                s = block_sum1024(s, red);
+                for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] -= s * y[j];
+                __syncthreads();
+            }
+        float nr = 0.f;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) nr += x[j] * x[j];
+        nr = rsqrtf(fmaxf(block_sum1024(nr, red), 1e-38f));
+        for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] *= nr;
+        __syncthreads();
     }
 }
 
@@ -342,14 +490,19 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         d = dalloc<float>(ctx, n); e = dalloc<float>(ctx, n); tau = dalloc<float>(ctx, n);
         lam32 = dalloc<float>(ctx, n);
         Y = dalloc<float>(ctx, nn);
-        ws = dalloc<float>(ctx, 4 * nn);
-        pv = dalloc<unsigned char>(ctx, nn);
         X = dalloc<double>(ctx, nn);
         launch_to_f32(ctx, g, A32, nn);
-        size_t smem = 2 * (size_t)n * sizeof(float);
-        if (smem > 200 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for the eigensolver");
-        CUDA_CHECK(cudaFuncSetAttribute(k_sytrd32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        klaunch(ctx, "k_sytrd32", k_sytrd32, 1, 1024, smem, A32, n, d, e, tau);
+        const int rows = (n + CL - 1) / CL;
+        const size_t smem_cl = sizeof(float) * ((size_t)rows * n + 2 * (size_t)n + 2 * (size_t)rows);
+        if (smem_cl <= 220 * 1024) {
+            CUDA_CHECK(cudaFuncSetAttribute(k_sytrd32_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl));
+            klaunch(ctx, "k_sytrd32_cl", k_sytrd32_cl, CL, 1024, smem_cl, A32, n, d, e, tau);
+        } else {
+            size_t smem = 2 * (size_t)n * sizeof(float);
+            if (smem > 200 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for the eigensolver");
+            CUDA_CHECK(cudaFuncSetAttribute(k_sytrd32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            klaunch(ctx, "k_sytrd32", k_sytrd32, 1, 1024, smem, A32, n, d, e, tau);
+        }
         // Gershgorin bound of T (host needs d, e: small copy)
         std::vector<float> hd(n), he(n);
         CUDA_CHECK(cudaMemcpyAsync(hd.data(), d, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
@@ -362,8 +515,12 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         }
         bnd = bnd * 1.01f + 1e-30f;
         klaunch(ctx, "k_bisect", k_bisect, div_up(n, 64), 64, 0, (const float*)d, (const float*)e, n, bnd, lam32);
-        klaunch(ctx, "k_invit", k_invit, div_up(n, 64), 64, 0, (const float*)d, (const float*)e,
-                (const float*)lam32, n, 1e-4f * bnd, 1e-7f * bnd, Y, ws, pv);
+        const size_t smem_it = (size_t)IT * n * (5 * sizeof(float) + 1);
+        if (smem_it > 220 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for inverse iteration");
+        CUDA_CHECK(cudaFuncSetAttribute(k_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_it));
+        klaunch(ctx, "k_invit", k_invit, div_up(n, IT), IT, smem_it, (const float*)d, (const float*)e,
+                (const float*)lam32, n, 1e-7f * bnd, Y);
+        klaunch(ctx, "k_cluster_mgs", k_cluster_mgs, n, 256, 0, (const float*)lam32, n, 1e-3f * bnd, Y);
         klaunch(ctx, "k_backtransform", k_backtransform, div_up(n, 8), 256, 8 * (size_t)n * sizeof(float),
                 (const float*)A32, (const float*)tau, n, (const float*)Y, X);
         // binary64 refinement

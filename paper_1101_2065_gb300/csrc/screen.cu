@@ -19,7 +19,8 @@
 namespace {
 
 constexpr int NB = 16;     // panel width
-constexpr int TS = 32;     // trailing tile
+constexpr int CB = 5;      // right-hand-side columns per thread in the forms update (RC <= 16*CB)
+constexpr int TS = 64;     // trailing tile
 
 template <typename C> struct CT;
 template <> struct CT<double2> {
@@ -129,11 +130,12 @@ __global__ void __launch_bounds__(256) k_ldlt(const C* __restrict__ chi0, C* __r
                     if (j < kb) row[j] = x[j];
             }
             __syncthreads();
-            // (c) trailing update of the lower triangle: M22 -= L21 D L21^T
+            // (c) trailing update of the lower triangle: M22 -= L21 D L21^T,
+            //     64x64 tiles, 4x4 complex outputs per thread
             const int nt = (n - k1 + TS - 1) / TS;
             const int ntile = nt * (nt + 1) / 2;
             for (int tt = 0; tt < ntile; ++tt) {
-                int I = (int)((sqrt(8.0 * tt + 1.0) - 1.0) * 0.5);
+                int I = (int)((sqrtf(8.0f * tt + 1.0f) - 1.0f) * 0.5f);
                 while (I * (I + 1) / 2 > tt) --I;
                 while ((I + 1) * (I + 2) / 2 <= tt) ++I;
                 int J = tt - I * (I + 1) / 2;
@@ -150,24 +152,27 @@ __global__ void __launch_bounds__(256) k_ldlt(const C* __restrict__ chi0, C* __r
                 }
                 __syncthreads();
                 const int ty = tid / 16, tx = tid % 16;
-                C acc[2][2];
+                C acc[4][4];
 #pragma unroll
-                for (int a = 0; a < 2; ++a)
+                for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 2; ++b) acc[a][b] = CT<C>::mk(R(0), R(0));
+                    for (int b = 0; b < 4; ++b) acc[a][b] = CT<C>::mk(R(0), R(0));
 #pragma unroll
                 for (int p = 0; p < NB; ++p) {
-                    C l0 = sL[ty][p], l1 = sL[ty + 16][p];
-                    C w0 = sW[tx][p], w1 = sW[tx + 16][p];
-                    acc[0][0] = cfma(l0, w0, acc[0][0]);
-                    acc[0][1] = cfma(l0, w1, acc[0][1]);
-                    acc[1][0] = cfma(l1, w0, acc[1][0]);
-                    acc[1][1] = cfma(l1, w1, acc[1][1]);
+                    C l[4], w[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) l[a] = sL[ty + 16 * a][p];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) w[b] = sW[tx + 16 * b][p];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = cfma(l[a], w[b], acc[a][b]);
                 }
 #pragma unroll
-                for (int a = 0; a < 2; ++a)
+                for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 2; ++b) {
+                    for (int b = 0; b < 4; ++b) {
                         int i = r0 + ty + 16 * a, j = c0 + tx + 16 * b;
                         if (i < n && j <= i) {
                             C* m = M + (long long)i * n + j;
@@ -236,15 +241,37 @@ __global__ void __launch_bounds__(256) k_forms(const C* __restrict__ fac, int n,
                         sL[rr][p] = (p < kb && r0 + rr < n) ? F[(long long)(r0 + rr) * n + k0 + p] : CT<C>::mk(T(0), T(0));
                     }
                     __syncthreads();
-                    for (int t = tid; t < TS * rc; t += blockDim.x) {
-                        int rr = t / rc, r = t % rc;
-                        int i = r0 + rr;
-                        if (i >= n) continue;
-                        C y = sY[i * RC + r];
+                    // thread (ty, tx): rows ty + 16a (a < 4), columns tx + 16b (b < CB)
+                    const int ty = tid / 16, tx = tid % 16;
+                    C acc2[4][CB];
 #pragma unroll
-                        for (int p = 0; p < NB; ++p)
-                            if (p < kb) y = cfms(sL[rr][p], sY[(k0 + p) * RC + r], y);
-                        sY[i * RC + r] = y;
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < CB; ++b) acc2[a][b] = CT<C>::mk(T(0), T(0));
+#pragma unroll
+                    for (int p = 0; p < NB; ++p) {
+                        C l[4], y[CB];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) l[a] = sL[ty + 16 * a][p];
+#pragma unroll
+                        for (int b = 0; b < CB; ++b) {
+                            int r = tx + 16 * b;
+                            y[b] = r < RC ? sY[(k0 + p) * RC + r] : CT<C>::mk(T(0), T(0));
+                        }
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int b = 0; b < CB; ++b) acc2[a][b] = cfma(l[a], y[b], acc2[a][b]);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int i = r0 + ty + 16 * a;
+                        if (i >= n) continue;
+#pragma unroll
+                        for (int b = 0; b < CB; ++b) {
+                            const int r = tx + 16 * b;
+                            if (r < rc) sY[i * RC + r] = csub(sY[i * RC + r], acc2[a][b]);
+                        }
                     }
                     __syncthreads();
                 }
@@ -301,7 +328,7 @@ void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* co
     const bool f32 = c->prec == GW_MIXED;
     const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
     const size_t budget = 190 * 1024;
-    int rc_max = (int)std::min<size_t>(256, budget / (csz * (size_t)n));
+    int rc_max = (int)std::min<size_t>(16 * CB, budget / (csz * (size_t)n));
     if (rc_max < 1) gw_throw(GW_ERR_INVALID_ARG, "n_sub too large for the forms kernel");
     int chunks = div_up(R, rc_max);
     int RC = div_up(R, chunks);
