@@ -6,9 +6,8 @@
 //     (one CTA with the matrix in L2 when it does not fit); reflector k is
 //     kept in row k of the global copy;
 //  2. all eigenvalues of T by bisection on Sturm counts (one thread each);
-//  3. eigenvectors of T by inverse iteration with a pivoted tridiagonal LU
-//     (one thread per eigenvalue), then modified Gram-Schmidt inside each
-//     cluster of close eigenvalues (one CTA per cluster);
+//  3. eigenvectors of T by binary64 inverse iteration with a pivoted
+//     tridiagonal LU (one thread per eigenvalue);
 //  4. back-transformation X = Q Y (one warp per vector);
 //  5. binary64 refinement of the full eigenbasis by the iteration of Ogita
 //     and Aishima (2018): R = I - X^T X, S = X^T g X,
@@ -261,34 +260,36 @@ __global__ void k_bisect(const float* __restrict__ d, const float* __restrict__ 
 
 // ------------------------------------------------------------------ 3
 // Solve (T - lam) x = b in place (b -> x) with the pivoted LU held in ws.
-__device__ void tri_factor(const float* __restrict__ d, const float* __restrict__ e, int n, float lam, float tiny,
-                           float* du, float* du1, float* du2, float* mul, unsigned char* piv) {
-    float ca = d[0] - lam, cb = n > 1 ? e[0] : 0.f;
+template <typename R>
+__device__ void tri_factor(const float* __restrict__ d, const float* __restrict__ e, int n, R lam, R tiny,
+                           R* du, R* du1, R* du2, R* mul, unsigned char* piv) {
+    R ca = R(d[0]) - lam, cb = n > 1 ? R(e[0]) : R(0);
     for (int i = 0; i + 1 < n; ++i) {
-        const float c = e[i];
-        const float a1 = d[i + 1] - lam;
-        const float b1 = (i + 2 < n) ? e[i + 1] : 0.f;
-        if (fabsf(c) > fabsf(ca)) {
-            float m = ca / c;
+        const R c = e[i];
+        const R a1 = R(d[i + 1]) - lam;
+        const R b1 = (i + 2 < n) ? R(e[i + 1]) : R(0);
+        if (fabs(c) > fabs(ca)) {
+            R m = ca / c;
             du[i] = c; du1[i] = a1; du2[i] = b1; mul[i] = m; piv[i] = 1;
             ca = cb - m * a1;
             cb = -m * b1;
         } else {
-            if (fabsf(ca) < tiny) ca = copysignf(tiny, ca);
-            float m = c / ca;
-            du[i] = ca; du1[i] = cb; du2[i] = 0.f; mul[i] = m; piv[i] = 0;
+            if (fabs(ca) < tiny) ca = copysign(tiny, ca);
+            R m = c / ca;
+            du[i] = ca; du1[i] = cb; du2[i] = R(0); mul[i] = m; piv[i] = 0;
             ca = a1 - m * cb;
             cb = b1;
         }
     }
-    if (fabsf(ca) < tiny) ca = copysignf(tiny, ca);
+    if (fabs(ca) < tiny) ca = copysign(tiny, ca);
     du[n - 1] = ca;
 }
 
-__device__ void tri_solve(int n, const float* du, const float* du1, const float* du2, const float* mul,
-                          const unsigned char* piv, float* x) {
+template <typename R>
+__device__ void tri_solve(int n, const R* du, const R* du1, const R* du2, const R* mul,
+                          const unsigned char* piv, R* x) {
     for (int i = 0; i + 1 < n; ++i) {
-        if (piv[i]) { float t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
+        if (piv[i]) { R t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
         x[i + 1] -= mul[i] * x[i];
     }
     x[n - 1] /= du[n - 1];
@@ -296,63 +297,36 @@ __device__ void tri_solve(int n, const float* du, const float* du1, const float*
     for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du1[i] * x[i + 1] - du2[i] * x[i + 2]) / du[i];
 }
 
-// Inverse iteration, one thread per eigenvalue; the pivoted LU of T - lam
-// lives in shared memory (IT threads per CTA).  Vectors of close eigenvalues
-// are orthogonalised afterwards by k_cluster_mgs.
+// Inverse iteration in binary64, one thread per eigenvalue; the pivoted LU
+// of T - lam lives in shared memory (IT threads per CTA).  In binary64 the
+// vectors of distinct eigenvalues come out orthogonal to ~u64 |T| / gap, so
+// no re-orthogonalisation is needed (the binary64 refinement that follows
+// removes what is left).
 constexpr int IT = 8;
 
 __global__ void __launch_bounds__(IT) k_invit(const float* __restrict__ d, const float* __restrict__ e,
-                                              const float* __restrict__ lam, int n, float tiny,
+                                              const float* __restrict__ lam, int n, double tiny,
                                               float* __restrict__ Y) {
-    extern __shared__ float sws[];
+    extern __shared__ double swd[];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float* du = sws + (long long)threadIdx.x * 5 * n;
-    float* du1 = du + n;
-    float* du2 = du1 + n;
-    float* mul = du2 + n;
-    float* x = mul + n;
-    unsigned char* piv = reinterpret_cast<unsigned char*>(sws + (long long)IT * 5 * n) + (long long)threadIdx.x * n;
-    tri_factor(d, e, n, lam[i], tiny, du, du1, du2, mul, piv);
-    for (int j = 0; j < n; ++j) x[j] = 1.f + 0.001f * (float)((j * 7 + i * 13) % 17);
+    double* du = swd + (long long)threadIdx.x * 5 * n;
+    double* du1 = du + n;
+    double* du2 = du1 + n;
+    double* mul = du2 + n;
+    double* x = mul + n;
+    unsigned char* piv = reinterpret_cast<unsigned char*>(swd + (long long)blockDim.x * 5 * n) + (long long)threadIdx.x * n;
+    tri_factor<double>(d, e, n, (double)lam[i], tiny, du, du1, du2, mul, piv);
+    for (int j = 0; j < n; ++j) x[j] = 1.0 + 0.001 * (double)((j * 7 + i * 13) % 17);
     for (int it = 0; it < 3; ++it) {
-        tri_solve(n, du, du1, du2, mul, piv, x);
-        float nr = 0.f;
+        tri_solve<double>(n, du, du1, du2, mul, piv, x);
+        double nr = 0.0;
         for (int j = 0; j < n; ++j) nr += x[j] * x[j];
-        nr = rsqrtf(fmaxf(nr, 1e-38f));
+        nr = 1.0 / sqrt(fmax(nr, 1e-300));
         for (int j = 0; j < n; ++j) x[j] *= nr;
     }
     float* yo = Y + (long long)i * n;
-    for (int j = 0; j < n; ++j) yo[j] = x[j];
-}
-
-// Modified Gram-Schmidt inside each cluster (maximal run of eigenvalues with
-// consecutive gaps < tol), one CTA per cluster start, twice.
-__global__ void __launch_bounds__(256) k_cluster_mgs(const float* __restrict__ lam, int n, float tol,
-                                                     float* __restrict__ Y) {
-    __shared__ float red[33];
-    const int i0 = blockIdx.x;
-    if (i0 > 0 && lam[i0] - lam[i0 - 1] < tol) return;
-    int i1 = i0 + 1;
-    while (i1 < n && lam[i1] - lam[i1 - 1] < tol) ++i1;
-    if (i1 - i0 < 2) return;
-    for (int i = i0; i < i1; ++i) {
-        float* x = Y + (long long)i * n;
-        for (int pass = 0; pass < 2; ++pass)
-            for (int q = i0; q < i; ++q) {
-                const float* y = Y + (long long)q * n;
-                float s = 0.f;
-                for (int j = threadIdx.x; j < n; j += blockDim.x) s += y[j] * x[j];
-                s = block_sum1024(s, red);
-                for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] -= s * y[j];
-                __syncthreads();
-            }
-        float nr = 0.f;
-        for (int j = threadIdx.x; j < n; j += blockDim.x) nr += x[j] * x[j];
-        nr = rsqrtf(fmaxf(block_sum1024(nr, red), 1e-38f));
-        for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] *= nr;
-        __syncthreads();
-    }
+    for (int j = 0; j < n; ++j) yo[j] = (float)x[j];
 }
 
 // ------------------------------------------------------------------ 4
@@ -515,12 +489,13 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         }
         bnd = bnd * 1.01f + 1e-30f;
         klaunch(ctx, "k_bisect", k_bisect, div_up(n, 64), 64, 0, (const float*)d, (const float*)e, n, bnd, lam32);
-        const size_t smem_it = (size_t)IT * n * (5 * sizeof(float) + 1);
-        if (smem_it > 220 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for inverse iteration");
+        const size_t per_thread = (size_t)n * (5 * sizeof(double) + 1);
+        const int it_threads = (int)std::max<size_t>(1, std::min<size_t>(IT, (200 * 1024) / per_thread));
+        if (per_thread > 220 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for inverse iteration");
+        const size_t smem_it = per_thread * it_threads;
         CUDA_CHECK(cudaFuncSetAttribute(k_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_it));
-        klaunch(ctx, "k_invit", k_invit, div_up(n, IT), IT, smem_it, (const float*)d, (const float*)e,
-                (const float*)lam32, n, 1e-7f * bnd, Y);
-        klaunch(ctx, "k_cluster_mgs", k_cluster_mgs, n, 256, 0, (const float*)lam32, n, 1e-3f * bnd, Y);
+        klaunch(ctx, "k_invit", k_invit, div_up(n, it_threads), it_threads, smem_it, (const float*)d, (const float*)e,
+                (const float*)lam32, n, 1e-13 * (double)bnd, Y);
         klaunch(ctx, "k_backtransform", k_backtransform, div_up(n, 8), 256, 8 * (size_t)n * sizeof(float),
                 (const float*)A32, (const float*)tau, n, (const float*)Y, X);
         // binary64 refinement

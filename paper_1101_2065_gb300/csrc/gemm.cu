@@ -8,13 +8,15 @@
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BK = 16;
 
-template <bool TA, bool TB>
+// BM x BM output tile per CTA, (BM/16)^2 outputs per thread.
+template <bool TA, bool TB, int BM>
 __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha, const double* __restrict__ A,
                                                long long lda, const double* __restrict__ B, long long ldb,
                                                double beta, double* __restrict__ C, long long ldc, long long sA,
                                                long long sB, long long sC) {
+    constexpr int BN = BM, RM = BM / 16;
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
     A += blockIdx.z * sA;
@@ -22,11 +24,11 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha
     C += blockIdx.z * sC;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[4][4];
+    double acc[RM][RM];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < RM; ++j) acc[i][j] = 0.0;
     for (int k0 = 0; k0 < K; k0 += BK) {
         for (int i = threadIdx.x; i < BK * BM; i += 256) {
             int kk, mm;
@@ -47,24 +49,24 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double a[4], b[4];
+            double a[RM], b[RM];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < RM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < RM; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RM; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < RM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RM; ++i) {
         int gm = m0 + ty + 16 * i;
         if (gm >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < RM; ++j) {
             int gn = n0 + tx + 16 * j;
             if (gn >= N) continue;
             double* c = C + (long long)gm * ldc + gn;
@@ -79,8 +81,13 @@ void gemm_f64(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, double alpha, 
               const double* B, long long ldb, double beta, double* C, long long ldc, int batch, long long sA,
               long long sB, long long sC) {
     if (M <= 0 || N <= 0) return;
-    dim3 grid(div_up(N, BN), div_up(M, BM), batch);
-    auto kern = (!ta && !tb) ? k_dgemm<false, false> : (ta && !tb) ? k_dgemm<true, false>
-              : (!ta && tb) ? k_dgemm<false, true> : k_dgemm<true, true>;
+    // 64x64 tiles when they fill the GPU twice over, else 32x32
+    const bool big = (long long)div_up(N, 64) * div_up(M, 64) * batch >= 2LL * ctx->num_sms;
+    const int bm = big ? 64 : 32;
+    dim3 grid(div_up(N, bm), div_up(M, bm), batch);
+    auto kern = big ? ((!ta && !tb) ? k_dgemm<false, false, 64> : (ta && !tb) ? k_dgemm<true, false, 64>
+                     : (!ta && tb) ? k_dgemm<false, true, 64> : k_dgemm<true, true, 64>)
+                    : ((!ta && !tb) ? k_dgemm<false, false, 32> : (ta && !tb) ? k_dgemm<true, false, 32>
+                     : (!ta && tb) ? k_dgemm<false, true, 32> : k_dgemm<true, true, 32>);
     klaunch(ctx, "k_dgemm", kern, grid, 256, 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
 }

@@ -19,8 +19,13 @@
 namespace {
 
 constexpr int NB = 16;     // panel width
-constexpr int CB = 5;      // right-hand-side columns per thread in the forms update (RC <= 16*CB)
-constexpr int TS = 64;     // trailing tile
+constexpr int TS = 64;     // row tile of the forms update
+// Trailing-update tile of the factorisation and right-hand-side columns per
+// thread of the forms update: binary64 is issue-bound (small tiles waste
+// less on the triangle), binary32 needs register blocking.
+template <typename C> struct Tile;
+template <> struct Tile<double2> { static constexpr int T = 32, A = 2, CB = 2; };
+template <> struct Tile<float2> { static constexpr int T = 64, A = 4, CB = 5; };
 
 template <typename C> struct CT;
 template <> struct CT<double2> {
@@ -69,8 +74,9 @@ __global__ void __launch_bounds__(256) k_ldlt(const C* __restrict__ chi0, C* __r
                                               int N, double* __restrict__ piv, int* status) {
     typedef typename CT<C>::R R;
     __shared__ C S[NB][NB + 1];
-    __shared__ C sL[TS][NB + 1];
-    __shared__ C sW[TS][NB + 1];
+    constexpr int TT = Tile<C>::T, TA = Tile<C>::A;
+    __shared__ C sL[TT][NB + 1];
+    __shared__ C sW[TT][NB + 1];
     __shared__ double red[33];
     const int tid = threadIdx.x;
     const long long nn = (long long)n * n;
@@ -131,16 +137,16 @@ __global__ void __launch_bounds__(256) k_ldlt(const C* __restrict__ chi0, C* __r
             }
             __syncthreads();
             // (c) trailing update of the lower triangle: M22 -= L21 D L21^T,
-            //     64x64 tiles, 4x4 complex outputs per thread
-            const int nt = (n - k1 + TS - 1) / TS;
+            //     TT x TT tiles, TA x TA complex outputs per thread
+            const int nt = (n - k1 + TT - 1) / TT;
             const int ntile = nt * (nt + 1) / 2;
             for (int tt = 0; tt < ntile; ++tt) {
                 int I = (int)((sqrtf(8.0f * tt + 1.0f) - 1.0f) * 0.5f);
                 while (I * (I + 1) / 2 > tt) --I;
                 while ((I + 1) * (I + 2) / 2 <= tt) ++I;
                 int J = tt - I * (I + 1) / 2;
-                const int r0 = k1 + I * TS, c0 = k1 + J * TS;
-                for (int t = tid; t < TS * NB; t += blockDim.x) {
+                const int r0 = k1 + I * TT, c0 = k1 + J * TT;
+                for (int t = tid; t < TT * NB; t += blockDim.x) {
                     int rr = t / NB, p = t % NB;
                     C lv = CT<C>::mk(R(0), R(0)), wv = CT<C>::mk(R(0), R(0));
                     if (p < kb) {
@@ -152,27 +158,27 @@ __global__ void __launch_bounds__(256) k_ldlt(const C* __restrict__ chi0, C* __r
                 }
                 __syncthreads();
                 const int ty = tid / 16, tx = tid % 16;
-                C acc[4][4];
+                C acc[TA][TA];
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < TA; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = CT<C>::mk(R(0), R(0));
+                    for (int b = 0; b < TA; ++b) acc[a][b] = CT<C>::mk(R(0), R(0));
 #pragma unroll
                 for (int p = 0; p < NB; ++p) {
-                    C l[4], w[4];
+                    C l[TA], w[TA];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) l[a] = sL[ty + 16 * a][p];
+                    for (int a = 0; a < TA; ++a) l[a] = sL[ty + 16 * a][p];
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) w[b] = sW[tx + 16 * b][p];
+                    for (int b = 0; b < TA; ++b) w[b] = sW[tx + 16 * b][p];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
+                    for (int a = 0; a < TA; ++a)
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) acc[a][b] = cfma(l[a], w[b], acc[a][b]);
+                        for (int b = 0; b < TA; ++b) acc[a][b] = cfma(l[a], w[b], acc[a][b]);
                 }
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < TA; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
+                    for (int b = 0; b < TA; ++b) {
                         int i = r0 + ty + 16 * a, j = c0 + tx + 16 * b;
                         if (i < n && j <= i) {
                             C* m = M + (long long)i * n + j;
@@ -197,6 +203,7 @@ __global__ void __launch_bounds__(256) k_forms(const C* __restrict__ fac, int n,
                                                const double* __restrict__ Q, int R, int RC,
                                                double* __restrict__ c) {
     typedef typename CT<C>::R T;
+    constexpr int CB = Tile<C>::CB;
     extern __shared__ __align__(16) unsigned char sraw[];
     C* sY = reinterpret_cast<C*>(sraw);      // [n][RC]
     __shared__ C S[NB][NB + 1];
@@ -313,7 +320,8 @@ __global__ void k_c64_to_c128(const float2* __restrict__ a, double2* __restrict_
 void launch_ldlt(gw_ctx* ctx, gw_W* W) {
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
-    int grid = std::min(N, ctx->num_sms);   // large register footprint: one CTA per SM
+    // binary64: 254 registers, one CTA per SM; binary32: 128 registers, two
+    int grid = std::min(N, ctx->num_sms * (c->prec == GW_MIXED ? 2 : 1));
     if (c->prec == GW_MIXED)
         klaunch(ctx, "k_ldlt32", k_ldlt<float2>, grid, 256, 0, (const float2*)c->chi0_32, W->fac32, n, N, W->piv,
                 ctx->d_status);
@@ -328,10 +336,10 @@ void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* co
     const bool f32 = c->prec == GW_MIXED;
     const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
     const size_t budget = 190 * 1024;
-    int rc_max = (int)std::min<size_t>(16 * CB, budget / (csz * (size_t)n));
+    int rc_max = (int)std::min<size_t>(16 * (f32 ? Tile<float2>::CB : Tile<double2>::CB), budget / (csz * (size_t)n));
     if (rc_max < 1) gw_throw(GW_ERR_INVALID_ARG, "n_sub too large for the forms kernel");
     int chunks = div_up(R, rc_max);
-    int RC = div_up(R, chunks);
+    int RC = f32 ? div_up(R, chunks) : rc_max;     // binary64: full 16-wide column groups
     size_t smem = csz * (size_t)n * RC;
     int grid = std::max(1, std::min(N - 1, ctx->num_sms));
     if (f32) {
