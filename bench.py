@@ -156,6 +156,12 @@ KERNELS = ["k_forms", "k_forms32", "k_ldlt", "k_ldlt32", "k_chi0_fft", "k_chi0_f
            "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_to_f32", "k_kernel_spectra"]
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
+# of the current kernel version on this workload (profiles/k_*_ring12.md);
+# an entry is dropped whenever its kernel changes.
+NCU_TRAFFIC = {"k_ldlt32": 2.997e9, "k_forms32": 4.102e8}
+
+
 def kernel_model(name, mol, grid, n_rank):
     """Algorithmic work of one launch of a kernel: (flops, bound, peak TFLOP/s)."""
     n, N, R = mol.n_sub, grid.n_omega, 2 * mol.n_orb
@@ -289,7 +295,7 @@ def run_gpu(a):
     achieved = flops / avg_s / 1e12 if flops else None
     step_ms = main["t_ms"] / a.steps
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None, "traffic": NCU_TRAFFIC.get(dom),
             "peak_source": ("128 binary32 FMA/clk/SM" if peak == PEAK_FP32_TFLOPS else "2 binary64 FMA/clk/SM")
             + " x 152 SMs x 2070 MHz (recipe unit counts and maximum clock)",
             "avg_launch_ms": avg_s * 1e3, "launches": k_n,
