@@ -178,6 +178,27 @@ gw_status gw_solve_host(gw_ctx* ctx, const gw_molecule_desc* desc, const gw_grid
                         const double* vxc, double* e_qp, double* z_factor,
                         int* root_status, double* sigma_x);
 
+/* Allocation-free Sigma_c grid (no counterpart in the paper: an interface
+ * for callers that cannot allocate device memory, such as an application
+ * whose device memory belongs to another allocator or a latency-critical
+ * loop).  Computes the same Sigma_c(w_k), k = -(n_omega-1)..n_omega-1, as
+ * gw_sigma_diag from sigma_n(s_j), s_j = (j0 + i) d_omega.
+ *   sigma  device [n_states*n_sig] binary64, read
+ *   sigc   device [n_states*(2 n_omega - 1)] complex binary64, written
+ *   stream cudaStream_t to enqueue on (NULL: legacy default stream); the
+ *          call is asynchronous and does not synchronise
+ *   err    optional host buffer of err_len bytes for a message
+ * Scratch: a fixed table of n_sig + 2 n_omega - 1 complex entries inside
+ * the library, at most 65536 entries (1 MiB, held on every GPU that loads
+ * the library until the process exits); larger requests return
+ * GW_ERR_INVALID_ARG.  Allocates no device or host memory.  All calls on
+ * a device share the table: calls that overlap on the GPU race.  The first
+ * call on a device resolves the table's address with that device current;
+ * make it before any stream capture.  Launch errors return GW_ERR_CUDA. */
+gw_status gw_sigma_c_static(const double* sigma, int n_states, int n_sig, int j0, int n_omega,
+                            double d_omega, double eta, double* sigc, void* stream, char* err,
+                            size_t err_len);
+
 void gw_chi0_free(gw_chi0* chi0);
 void gw_W_free(gw_W* W);
 void gw_sigma_free(gw_sigma* sigma);

@@ -96,6 +96,7 @@ def load(path: str | None = None):
         "gw_W_copy_full": ([P, P, P, I, P], I),
         "gw_sigma_copy": ([P, P, P, P, P, P], I),
         "gw_sigma_grid": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int)], I),
+        "gw_sigma_c_static": ([P, I, I, I, I, D, D, P, P, C.c_char_p, C.c_size_t], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
