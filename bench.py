@@ -192,26 +192,18 @@ def run_gpu(a):
     import paper_1101_2065_gb300 as gw
     from paper_1101_2065_gb300 import gw as G
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1101_2065_gb300.replicas import Replicas, world as _world
+
+    rank, world, local = _world()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    reps = Replicas("nccl")
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        reps.barrier()
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reps.max(x)
 
     gw.build.build()
     mol, grid = synth.make_config(2)
@@ -331,8 +323,7 @@ def run_gpu(a):
         print(json.dumps(out))
     m.free()
     ctx.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    reps.close()
 
 
 if __name__ == "__main__":

@@ -1,0 +1,38 @@
+"""Plant mistakes in a copy of the oracle (on the CPU) and check that the
+pins catch each one."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = [
+    ("A[j] += 2.0 * (1.0 - f) * uu", "A[j] += 1.0 * (1.0 - f) * uu"),                  # spin factor
+    ("A[j + 1] += 2.0 * f * uu", "A[j + 1] += 2.0 * (1.0 - f) * uu"),                   # tent weight
+    ("- 1.0 / ((k + j) * d_omega + 1j * eta)", "+ 1.0 / ((k + j) * d_omega + 1j * eta)"),  # odd a(s)
+    ("1.0 / ((k - j) * d_omega + 1j * eta)", "1.0 / ((k - j) * d_omega - 1j * eta)"),   # sign of i eta
+    ("np.add.at(sig[n], i - jp - j0, (1.0 - f) * ck)", "np.add.at(sig[n], i + jp - j0, (1.0 - f) * ck)"),
+    ('return -np.einsum("nka,ab,nkb->n"', 'return np.einsum("nka,ab,nkb->n"'),        # Sigma_x sign
+    ("return d_omega * (sig @ K.T)", "return (sig @ K.T)"),                             # d_omega in Sigma_c
+    ("    re = d_omega * np.sum(sig_n * x / den)", "    re = np.sum(sig_n * x / den)"),
+    ("q = Vnk @ Zup ", "q = Vnk @ Zup * 1.0001 "),
+    ("Z = Xr @ xi[:, idx] / np.sqrt(lam_top)", "Z = Xr @ xi[:, idx] / lam_top"),
+    ("return np.linalg.solve(I[None] - chi0[ks], chi0[ks])", "return np.linalg.solve(I[None] + chi0[ks], chi0[ks])"),
+]
+
+
+@pytest.mark.parametrize("old,new", MUTATIONS)
+def test_pins_catch_planted_mistake(tmp_path, old, new):
+    for d in ("synth", "oracle", "tests"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+                        ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path)
+    src = (tmp_path / "oracle" / "gw.py").read_text()
+    assert old in src
+    (tmp_path / "oracle" / "gw.py").write_text(src.replace(old, new, 1))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
+                        "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True)
+    assert r.returncode != 0, "planted mistake went unnoticed"
