@@ -178,6 +178,37 @@ gw_status gw_solve_host(gw_ctx* ctx, const gw_molecule_desc* desc, const gw_grid
                         const double* vxc, double* e_qp, double* z_factor,
                         int* root_status, double* sigma_x);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of GW jobs on one device.  n_workers host threads,
+ * each with its own context and CUDA stream, take jobs from a FIFO queue;
+ * the head job is admitted as soon as its estimated device footprint fits
+ * the remaining hbm_budget_bytes (0 = unlimited), so jobs arriving while
+ * others run start as memory frees up and overlap on the GPU.  A job is
+ * one molecule through a0-a8 (as gw_solve_host); the description is copied
+ * at submission.  Results do not depend on the other jobs in flight
+ * (fixed-order reductions, no cross-job state). */
+typedef struct gw_server gw_server;
+gw_status gw_server_create(gw_server** out, int device, int n_workers, size_t hbm_budget_bytes);
+/* Stops the workers after their running jobs; queued jobs are dropped. */
+void      gw_server_destroy(gw_server* s);
+/* GW_ERR_ADMISSION if the job alone exceeds the budget. */
+gw_status gw_server_submit(gw_server* s, const gw_molecule_desc* desc, const gw_grid* grid,
+                           gw_precision prec, const int* states, int n_states, const double* vxc,
+                           long long* job_id);
+/* 0 queued, 1 running, 2 done; a negative gw_status if the job failed. */
+int       gw_server_poll(gw_server* s, long long job_id);
+/* Waits up to timeout_ms (< 0: no limit; GW_ERR_TIMEOUT when it runs out),
+ * copies the results (host arrays [n_states], each may be NULL) and
+ * releases the job.  times_ms [3] (nullable): queue wait, run time, total.
+ * err (nullable, err_len bytes) receives the failure message.  Returns the
+ * job's status. */
+gw_status gw_server_wait(gw_server* s, long long job_id, int timeout_ms, double* e_qp,
+                         double* z_factor, int* root_status, double* sigma_x, double* times_ms,
+                         char* err, size_t err_len);
+/* Estimated device footprint of a job (bytes), as used for admission. */
+size_t    gw_server_job_bytes(const gw_molecule_desc* desc, const gw_grid* grid, gw_precision prec,
+                              int n_states);
+
 /* Allocation-free Sigma_c grid (no counterpart in the paper: an interface
  * for callers that cannot allocate device memory, such as an application
  * whose device memory belongs to another allocator or a latency-critical

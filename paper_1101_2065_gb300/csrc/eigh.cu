@@ -2,9 +2,9 @@
 //
 // Mixed-precision symmetric eigensolver:
 //  1. binary32 Householder tridiagonalisation T = Q^T g Q on a cluster of 8
-//     CTAs holding the matrix row-cyclically in distributed shared memory
-//     (one CTA with the matrix in L2 when it does not fit); reflector k is
-//     kept in row k of the global copy;
+//     CTAs holding the matrix row-cyclically in distributed shared memory,
+//     or, when it does not fit, on the whole GPU (cooperative launch, matrix
+//     in L2); reflector k is kept in row k of the global copy;
 //  2. all eigenvalues of T by bisection on Sturm counts (one thread each);
 //  3. eigenvectors of T by binary64 inverse iteration with a pivoted
 //     tridiagonal LU (one thread per eigenvalue);
@@ -13,7 +13,8 @@
 //     and Aishima (2018): R = I - X^T X, S = X^T g X,
 //     lambda_i = S_ii / (1 - R_ii), E_ij = (S_ij + lambda_j R_ij)/(lambda_j -
 //     lambda_i) for well separated pairs, R_ij / 2 otherwise, X <- X + X E;
-//     each step squares the error (binary64 GEMMs only);
+//     each step squares the error (binary64 GEMMs only); repeated until
+//     |S - diag| / |g| falls below a tolerance, at most oa_iters times;
 //  6. the n_sub largest eigenpairs are selected, their block re-orthonormalised
 //     by one Newton-Schulz step X <- X (3 I - X^T X) / 2, and scaled by
 //     lambda^-1/2 (Eq. subspace).
@@ -49,72 +50,6 @@ __device__ float block_sum1024(float v, float* red) {
 }
 
 // ------------------------------------------------------------------ 1
-__global__ void __launch_bounds__(1024) k_sytrd32(float* __restrict__ A, int n, float* __restrict__ d,
-                                                  float* __restrict__ e, float* __restrict__ tau) {
-    extern __shared__ float sm[];
-    float* sv = sm;          // reflector
-    float* sw = sm + n;      // p, then w
-    __shared__ float red[33];
-    __shared__ float s_par[2];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (int k = 0; k + 2 < n; ++k) {
-        const int m = n - k - 1;
-        float* rowk = A + (long long)k * n + k + 1;
-        float part = 0.f;
-        for (int j = tid; j < m; j += blockDim.x) {
-            float x = rowk[j];
-            sv[j] = x;
-            part += x * x;
-        }
-        float sig = block_sum1024(part, red);
-        if (tid == 0) {
-            float x0 = sv[0];
-            float alpha = sig > 0.f ? -copysignf(sqrtf(sig), x0) : 0.f;
-            float v0 = x0 - alpha;
-            float vtv = sig - x0 * x0 + v0 * v0;
-            float t = vtv > 0.f ? 2.f / vtv : 0.f;
-            sv[0] = v0;
-            d[k] = A[(long long)k * n + k];
-            e[k] = sig > 0.f ? alpha : x0;
-            tau[k] = t;
-            s_par[0] = t;
-        }
-        __syncthreads();
-        const float t = s_par[0];
-        for (int j = tid; j < m; j += blockDim.x) rowk[j] = sv[j];     // keep the reflector
-        // p = t A22 v, one warp per row
-        for (int i = warp; i < m; i += nw) {
-            const float* ri = A + (long long)(k + 1 + i) * n + k + 1;
-            float acc = 0.f;
-            for (int j = lane; j < m; j += 32) acc += ri[j] * sv[j];
-            acc = warp_sum(acc);
-            if (lane == 0) sw[i] = t * acc;
-        }
-        __syncthreads();
-        float pv = 0.f;
-        for (int j = tid; j < m; j += blockDim.x) pv += sw[j] * sv[j];
-        const float K = 0.5f * t * block_sum1024(pv, red);
-        for (int j = tid; j < m; j += blockDim.x) sw[j] -= K * sv[j];
-        __syncthreads();
-        // A22 -= v w^T + w v^T
-        for (int i = warp; i < m; i += nw) {
-            float* ri = A + (long long)(k + 1 + i) * n + k + 1;
-            const float vi = sv[i], wi = sw[i];
-            for (int j = lane; j < m; j += 32) ri[j] -= vi * sw[j] + wi * sv[j];
-        }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        if (n >= 2) {
-            d[n - 2] = A[(long long)(n - 2) * n + n - 2];
-            e[n - 2] = A[(long long)(n - 1) * n + n - 2];
-        }
-        d[n - 1] = A[(long long)(n - 1) * n + n - 1];
-        if (n >= 2) tau[n - 2] = 0.f;
-        tau[n - 1] = 0.f;
-    }
-}
-
 // Same reduction on a cluster of CL CTAs: CTA r holds the rows i = r (mod CL)
 // of the matrix in its shared memory; the reflector, the partial dot
 // products and w travel through distributed shared memory.
@@ -231,6 +166,114 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024)
     cluster.sync();
 }
 
+// Same reduction on the whole GPU for ranks too large for the cluster:
+// cooperative launch, matrix in global memory (L2), three grid barriers per
+// Householder step.
+__device__ bool grid_barrier(unsigned int* bar, int* status, int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = bar + 1;
+        unsigned int gen = *vgen;
+        int ok = 1;
+        __threadfence();
+        unsigned int arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long polls = 0;
+            while (*vgen == gen) {
+                if (++polls > (1ull << 25)) { atomicOr(status, ST_TIMEOUT); ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+__global__ void __launch_bounds__(512) k_sytrd32_grid(float* __restrict__ A, int n, float* __restrict__ d,
+                                                      float* __restrict__ e, float* __restrict__ tau,
+                                                      float* __restrict__ vbuf, float* __restrict__ pbuf,
+                                                      float* __restrict__ part, unsigned int* bar, int* status) {
+    extern __shared__ float sm[];
+    float* sv = sm;          // v
+    float* sw = sm + n;      // w
+    __shared__ float red[33];
+    __shared__ int s_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int gwarp = blockIdx.x * nw + warp, nwarps = gridDim.x * nw;
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        if (blockIdx.x == 0) {
+            float* rowk = A + (long long)k * n + k + 1;
+            float pp = 0.f;
+            for (int j = tid; j < m; j += blockDim.x) {
+                float x = rowk[j];
+                sv[j] = x;
+                pp += x * x;
+            }
+            float sig = block_sum1024(pp, red);
+            if (tid == 0) {
+                float x0 = sv[0];
+                float alpha = sig > 0.f ? -copysignf(sqrtf(sig), x0) : 0.f;
+                float v0 = x0 - alpha;
+                float vtv = sig - x0 * x0 + v0 * v0;
+                sv[0] = v0;
+                d[k] = A[(long long)k * n + k];
+                e[k] = sig > 0.f ? alpha : x0;
+                tau[k] = vtv > 0.f ? 2.f / vtv : 0.f;
+            }
+            __syncthreads();
+            for (int j = tid; j < m; j += blockDim.x) {
+                vbuf[j] = sv[j];
+                rowk[j] = sv[j];
+            }
+        }
+        if (!grid_barrier(bar, status, &s_flag)) return;
+        const float t = tau[k];
+        for (int j = tid; j < m; j += blockDim.x) sv[j] = vbuf[j];
+        __syncthreads();
+        float pv = 0.f;
+        for (int i = gwarp; i < m; i += nwarps) {
+            const float* ri = A + (long long)(k + 1 + i) * n + k + 1;
+            float acc = 0.f;
+            for (int j = lane; j < m; j += 32) acc += ri[j] * sv[j];
+            acc = warp_sum(acc) * t;
+            if (lane == 0) {
+                pbuf[i] = acc;
+                pv += acc * sv[i];
+            }
+        }
+        pv = block_sum1024(pv, red);
+        if (tid == 0) part[blockIdx.x] = pv;
+        if (!grid_barrier(bar, status, &s_flag)) return;
+        float tot = 0.f;
+        for (int b = 0; b < (int)gridDim.x; ++b) tot += part[b];
+        const float K = 0.5f * t * tot;
+        for (int j = tid; j < m; j += blockDim.x) sw[j] = pbuf[j] - K * sv[j];
+        __syncthreads();
+        for (int i = gwarp; i < m; i += nwarps) {
+            float* ri = A + (long long)(k + 1 + i) * n + k + 1;
+            const float vi = sv[i], wi = sw[i];
+            for (int j = lane; j < m; j += 32) ri[j] -= vi * sw[j] + wi * sv[j];
+        }
+        if (!grid_barrier(bar, status, &s_flag)) return;
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        if (n >= 2) {
+            d[n - 2] = A[(long long)(n - 2) * n + n - 2];
+            e[n - 2] = A[(long long)(n - 1) * n + n - 2];
+            tau[n - 2] = 0.f;
+        }
+        d[n - 1] = A[(long long)(n - 1) * n + n - 1];
+        tau[n - 1] = 0.f;
+    }
+}
+
 // ------------------------------------------------------------------ 2
 __device__ int sturm_count(const float* __restrict__ d, const float* __restrict__ e, int n, float x, float tiny) {
     int c = 0;
@@ -306,16 +349,19 @@ constexpr int IT = 8;
 
 __global__ void __launch_bounds__(IT) k_invit(const float* __restrict__ d, const float* __restrict__ e,
                                               const float* __restrict__ lam, int n, double tiny,
-                                              float* __restrict__ Y) {
+                                              float* __restrict__ Y, double* __restrict__ gws) {
     extern __shared__ double swd[];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double* du = swd + (long long)threadIdx.x * 5 * n;
+    // scratch: shared memory, or a per-eigenvalue slice of gws when it is given
+    double* base = gws ? gws + (long long)i * (5 * n + (n + 7) / 8) : swd + (long long)threadIdx.x * 5 * n;
+    double* du = base;
     double* du1 = du + n;
     double* du2 = du1 + n;
     double* mul = du2 + n;
     double* x = mul + n;
-    unsigned char* piv = reinterpret_cast<unsigned char*>(swd + (long long)blockDim.x * 5 * n) + (long long)threadIdx.x * n;
+    unsigned char* piv = gws ? reinterpret_cast<unsigned char*>(base + 5 * n)
+                             : reinterpret_cast<unsigned char*>(swd + (long long)blockDim.x * 5 * n) + (long long)threadIdx.x * n;
     tri_factor<double>(d, e, n, (double)lam[i], tiny, du, du1, du2, mul, piv);
     for (int j = 0; j < n; ++j) x[j] = 1.0 + 0.001 * (double)((j * 7 + i * 13) % 17);
     for (int it = 0; it < 3; ++it) {
@@ -337,7 +383,7 @@ __global__ void __launch_bounds__(256) k_backtransform(const float* __restrict__
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * (blockDim.x >> 5) + w;
     if (i >= n) return;
-    float* y = sy + (long long)w * n;
+    float* y = sy + (long long)w * n;   // one vector per warp
     for (int j = lane; j < n; j += 32) y[j] = Y[(long long)i * n + j];
     __syncwarp();
     for (int k = n - 3; k >= 0; --k) {
@@ -387,7 +433,11 @@ __global__ void __launch_bounds__(1024) k_oa_stats(const double* __restrict__ S,
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = 2.0 * (sqrt(s1[0]) + sqrt(s3[0]) * sqrt(s2[0]));
+    if (threadIdx.x == 0) {
+        out[0] = 2.0 * (sqrt(s1[0]) + sqrt(s3[0]) * sqrt(s2[0]));
+        out[1] = sqrt(s1[0]) / fmax(sqrt(s3[0]), 1e-300);   // |S - diag| / |g|
+        out[2] = sqrt(s2[0]);                               // |I - X^T X|
+    }
 }
 
 __global__ void k_oa_E(const double* __restrict__ S, const double* __restrict__ R, const double* __restrict__ lam,
@@ -446,17 +496,19 @@ __global__ void k_scale_cols(double* __restrict__ B, int n, int n_sub, const dou
 void launch_to_f32(gw_ctx* ctx, const double* a, float* b, long long n);
 
 // g (n x n, binary64, symmetric) -> B (n x n_sub) = xi_top lambda_top^-1/2
-void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iters, double* B) {
+void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iters, double oa_tol, double* B) {
     const long long nn = (long long)n * n;
     float* A32 = nullptr; float *d = nullptr, *e = nullptr, *tau = nullptr, *lam32 = nullptr, *Y = nullptr;
-    float* ws = nullptr; unsigned char* pv = nullptr;
     double *X = nullptr, *X2 = nullptr, *R = nullptr, *S = nullptr, *T = nullptr, *E = nullptr, *lam = nullptr;
-    double *stat = nullptr, *G = nullptr, *Bt = nullptr;
+    double *stat = nullptr, *G = nullptr, *Bt = nullptr, *gws = nullptr;
+    float *vb = nullptr, *pb = nullptr, *pt = nullptr;
+    unsigned int* bar = nullptr;
     int* sel = nullptr;
     auto release = [&]() {
-        for (void* p : {(void*)A32, (void*)d, (void*)e, (void*)tau, (void*)lam32, (void*)Y, (void*)ws, (void*)pv,
+        for (void* p : {(void*)A32, (void*)d, (void*)e, (void*)tau, (void*)lam32, (void*)Y,
                         (void*)X, (void*)X2, (void*)R, (void*)S, (void*)T, (void*)E, (void*)lam, (void*)stat,
-                        (void*)G, (void*)Bt, (void*)sel})
+                        (void*)G, (void*)Bt, (void*)sel, (void*)gws, (void*)vb, (void*)pb, (void*)pt,
+                        (void*)bar})
             ctx_free(ctx, p);
     };
     try {
@@ -472,10 +524,23 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
             CUDA_CHECK(cudaFuncSetAttribute(k_sytrd32_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl));
             klaunch(ctx, "k_sytrd32_cl", k_sytrd32_cl, CL, 1024, smem_cl, A32, n, d, e, tau);
         } else {
-            size_t smem = 2 * (size_t)n * sizeof(float);
+            const size_t smem = 2 * (size_t)n * sizeof(float);
             if (smem > 200 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for the eigensolver");
-            CUDA_CHECK(cudaFuncSetAttribute(k_sytrd32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            klaunch(ctx, "k_sytrd32", k_sytrd32, 1, 1024, smem, A32, n, d, e, tau);
+            CUDA_CHECK(cudaFuncSetAttribute(k_sytrd32_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int per_sm = 0;
+            CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sytrd32_grid, 512, smem));
+            if (per_sm < 1) gw_throw(GW_ERR_CUDA, "tridiagonalisation kernel cannot be resident");
+            const int grid = ctx->num_sms;          // one CTA per SM, co-resident (cooperative launch)
+            vb = dalloc<float>(ctx, n);
+            pb = dalloc<float>(ctx, n);
+            pt = dalloc<float>(ctx, grid);
+            bar = dalloc<unsigned int>(ctx, 2);
+            CUDA_CHECK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), ctx->stream));
+            void* args[] = {&A32, (void*)&n, &d, &e, &tau, &vb, &pb, &pt, &bar, &ctx->d_status};
+            prof_begin(ctx, "k_sytrd32_grid");
+            CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)k_sytrd32_grid, dim3(grid), dim3(512), args, smem,
+                                                   ctx->stream));
+            after_launch(ctx, "k_sytrd32_grid");
         }
         // Gershgorin bound of T (host needs d, e: small copy)
         std::vector<float> hd(n), he(n);
@@ -490,18 +555,27 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         bnd = bnd * 1.01f + 1e-30f;
         klaunch(ctx, "k_bisect", k_bisect, div_up(n, 64), 64, 0, (const float*)d, (const float*)e, n, bnd, lam32);
         const size_t per_thread = (size_t)n * (5 * sizeof(double) + 1);
-        const int it_threads = (int)std::max<size_t>(1, std::min<size_t>(IT, (200 * 1024) / per_thread));
-        if (per_thread > 220 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for inverse iteration");
-        const size_t smem_it = per_thread * it_threads;
-        CUDA_CHECK(cudaFuncSetAttribute(k_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_it));
-        klaunch(ctx, "k_invit", k_invit, div_up(n, it_threads), it_threads, smem_it, (const float*)d, (const float*)e,
-                (const float*)lam32, n, 1e-13 * (double)bnd, Y);
-        klaunch(ctx, "k_backtransform", k_backtransform, div_up(n, 8), 256, 8 * (size_t)n * sizeof(float),
+        if (per_thread <= 200 * 1024) {
+            const int it_threads = (int)std::max<size_t>(1, std::min<size_t>(IT, (200 * 1024) / per_thread));
+            const size_t smem_it = per_thread * it_threads;
+            CUDA_CHECK(cudaFuncSetAttribute(k_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_it));
+            klaunch(ctx, "k_invit", k_invit, div_up(n, it_threads), it_threads, smem_it, (const float*)d,
+                    (const float*)e, (const float*)lam32, n, 1e-13 * (double)bnd, Y, (double*)nullptr);
+        } else {
+            gws = dalloc<double>(ctx, (size_t)n * (5 * (size_t)n + (n + 7) / 8));
+            klaunch(ctx, "k_invit", k_invit, div_up(n, IT), IT, 0, (const float*)d, (const float*)e,
+                    (const float*)lam32, n, 1e-13 * (double)bnd, Y, gws);
+        }
+        const int bt_warps = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / ((size_t)n * sizeof(float))));
+        const size_t smem_bt = (size_t)bt_warps * n * sizeof(float);
+        CUDA_CHECK(cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bt));
+        klaunch(ctx, "k_backtransform", k_backtransform, div_up(n, bt_warps), 32 * bt_warps, smem_bt,
                 (const float*)A32, (const float*)tau, n, (const float*)Y, X);
         // binary64 refinement
         X2 = dalloc<double>(ctx, nn); R = dalloc<double>(ctx, nn); S = dalloc<double>(ctx, nn);
         T = dalloc<double>(ctx, nn); E = dalloc<double>(ctx, nn); lam = dalloc<double>(ctx, n);
-        stat = dalloc<double>(ctx, 2);
+        stat = dalloc<double>(ctx, 3);
+        double hstat[3] = {0, 0, 0};
         for (int it = 0; it < oa_iters; ++it) {
             gemm_f64(ctx, true, false, n, n, n, 1.0, X, n, X, n, 0.0, R, n);           // X^T X
             klaunch(ctx, "k_identity_minus", k_identity_minus, div_up(nn, 256), 256, 0, R, n);
@@ -510,9 +584,15 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
             klaunch(ctx, "k_oa_stats", k_oa_stats, 1, 1024, 0, (const double*)S, (const double*)R, g, n, lam, stat);
             klaunch(ctx, "k_oa_E", k_oa_E, div_up(nn, 256), 256, 0, (const double*)S, (const double*)R,
                     (const double*)lam, (const double*)stat, n, E);
+            // stop once the basis is an eigenbasis to working accuracy (residual of
+            // the previous iterate; the correction below squares it once more)
+            CUDA_CHECK(cudaMemcpyAsync(hstat, stat, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+            CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+            const bool done = it > 0 && hstat[1] < oa_tol && hstat[2] < 1e3 * oa_tol;
             CUDA_CHECK(cudaMemcpyAsync(X2, X, nn * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
             gemm_f64(ctx, false, false, n, n, n, 1.0, X, n, E, n, 1.0, X2, n);         // X + X E
             std::swap(X, X2);
+            if (done) break;
         }
         if (oa_iters == 0) {
             // Rayleigh quotients of the binary32 vectors

@@ -97,6 +97,13 @@ def load(path: str | None = None):
         "gw_sigma_copy": ([P, P, P, P, P, P], I),
         "gw_sigma_grid": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int)], I),
         "gw_sigma_c_static": ([P, I, I, I, I, D, D, P, P, C.c_char_p, C.c_size_t], I),
+        "gw_server_create": ([pp, I, I, C.c_size_t], I),
+        "gw_server_destroy": ([P], None),
+        "gw_server_submit": ([P, C.POINTER(MoleculeDesc), C.POINTER(Grid), I, P, I, P,
+                              C.POINTER(C.c_longlong)], I),
+        "gw_server_poll": ([P, C.c_longlong], I),
+        "gw_server_wait": ([P, C.c_longlong, I, P, P, P, P, P, C.c_char_p, C.c_size_t], I),
+        "gw_server_job_bytes": ([C.POINTER(MoleculeDesc), C.POINTER(Grid), I, I], C.c_size_t),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -366,6 +373,61 @@ def gw_solve_host(ctx, mol, grid, states, prec=GW_FP64, vxc=None, desc=None):
     _check(ctx, load().gw_solve_host(ctx.handle, C.byref(d.s), C.byref(g), int(prec), _ptr(st), n, _ptr(v),
                                      _ptr(e), _ptr(z), _ptr(rs), _ptr(sx)))
     return e, z, rs, sx
+
+
+class Server:
+    """Continuous-batching GW service (gw_server)."""
+
+    def __init__(self, device=0, n_workers=2, hbm_budget_bytes=0):
+        h = C.c_void_p()
+        code = load().gw_server_create(C.byref(h), device, n_workers, hbm_budget_bytes)
+        if code != GW_OK:
+            raise GWError(code, "gw_server_create failed")
+        self.handle = h
+
+    def submit(self, mol, grid, states=None, prec=GW_FP64, vxc=None):
+        if states is None:
+            states = [mol.n_occ - 1, mol.n_occ]
+        d = _Desc(mol)
+        g = make_grid(grid)
+        st = np.ascontiguousarray(states, np.int32)
+        v = None if vxc is None else np.ascontiguousarray(np.broadcast_to(np.asarray(vxc, float), (st.size,)))
+        jid = C.c_longlong()
+        code = load().gw_server_submit(self.handle, C.byref(d.s), C.byref(g), int(prec), _ptr(st), st.size,
+                                       _ptr(v), C.byref(jid))
+        if code != GW_OK:
+            raise GWError(code, "gw_server_submit failed")
+        return jid.value, st.size
+
+    def poll(self, job):
+        return load().gw_server_poll(self.handle, job[0])
+
+    def wait(self, job, timeout_ms=-1):
+        jid, n = job
+        e = np.zeros(n); z = np.zeros(n); rs = np.zeros(n, np.int32); sx = np.zeros(n); t = np.zeros(3)
+        err = C.create_string_buffer(512)
+        code = load().gw_server_wait(self.handle, jid, timeout_ms, _ptr(e), _ptr(z), _ptr(rs), _ptr(sx), _ptr(t),
+                                     err, 512)
+        if code != GW_OK:
+            raise GWError(code, err.value.decode())
+        return dict(e_qp=e, z=z, status=rs, sigma_x=sx, queue_ms=t[0], run_ms=t[1], total_ms=t[2])
+
+    @staticmethod
+    def job_bytes(mol, grid, prec=GW_FP64, n_states=2):
+        d = _Desc(mol)
+        g = make_grid(grid)
+        return load().gw_server_job_bytes(C.byref(d.s), C.byref(g), int(prec), n_states)
+
+    def close(self):
+        if self.handle:
+            load().gw_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve(ctx, mol, grid, states=None, prec=GW_FP64, vxc=None, Z=None):

@@ -1,0 +1,117 @@
+"""Serving and batching drivers for the GW engine (gw_server).
+
+serve: replays a seeded Poisson arrival trace of molecules of uneven size
+       through the continuous-batching engine and reports throughput and
+       p50/p99 latency (submit to result), then times the plain FP64 path
+       closed-loop on a sample of the same jobs and compares the
+       quasiparticle energies.
+batch: submits a whole batch of uneven molecules at once.
+
+Usage: python -m paper_1101_2065_gb300.serve serve --jobs 60 --rate 10 --lo 4 --hi 16
+       python -m paper_1101_2065_gb300.serve batch
+Prints one JSON line.
+"""
+import argparse
+import json
+import os
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+from synth import molecules as sm  # noqa: E402
+
+from . import gw  # noqa: E402
+
+HA_MEV = 27211.386245988
+
+
+def _pct(x, q):
+    return float(np.percentile(np.asarray(x), q)) if len(x) else None
+
+
+def run_jobs(mols, grid, arrivals, prec, workers, budget):
+    """Submit mols[i] at arrivals[i] seconds; return per-job results and the span."""
+    srv = gw.Server(0, n_workers=workers, hbm_budget_bytes=budget)
+    handles = [None] * len(mols)
+    results = [None] * len(mols)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, (m, t) in enumerate(zip(mols, arrivals)):
+            dt = t - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            handles[i] = srv.submit(m, grid, prec=prec)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    for i in range(len(mols)):
+        while handles[i] is None:
+            time.sleep(0.0005)
+        results[i] = srv.wait(handles[i])
+    span = time.perf_counter() - t0
+    th.join()
+    srv.close()
+    return results, span
+
+
+def summarize(results, span, mols):
+    lat = [r["total_ms"] for r in results]
+    return {"jobs": len(results), "solves_per_s": len(results) / span, "span_s": span,
+            "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "max": max(lat)},
+            "queue_ms": {"p50": _pct([r["queue_ms"] for r in results], 50),
+                         "p99": _pct([r["queue_ms"] for r in results], 99)},
+            "run_ms": {"p50": _pct([r["run_ms"] for r in results], 50)},
+            "atoms": {"min": int(min(m.n_atoms for m in mols)), "max": int(max(m.n_atoms for m in mols))}}
+
+
+def fp64_compare(mols, grid, mixed_results, sample, workers=1):
+    idx = list(range(0, len(mols), max(1, len(mols) // sample)))[:sample]
+    sub = [mols[i] for i in idx]
+    res, span = run_jobs(sub, grid, [0.0] * len(sub), gw.GW_FP64, workers, 0)
+    err = max(float(np.abs(a["e_qp"] - mixed_results[i]["e_qp"]).max()) for a, i in zip(res, idx)) * HA_MEV
+    same = all(np.array_equal(a["status"], mixed_results[i]["status"]) for a, i in zip(res, idx))
+    return {"jobs": len(sub), "solves_per_s_closed_loop": len(sub) / span,
+            "qp_max_abs_err_meV_mixed_vs_fp64": err, "same_root_branch": same}
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("mode", choices=["serve", "batch"])
+    p.add_argument("--jobs", type=int, default=60)
+    p.add_argument("--rate", type=float, default=20.0)
+    p.add_argument("--lo", type=int, default=10)
+    p.add_argument("--hi", type=int, default=120)
+    p.add_argument("--n-omega", type=int, default=None)
+    p.add_argument("--workers", type=int, default=3)
+    p.add_argument("--budget-gb", type=float, default=150.0)
+    p.add_argument("--fp64-sample", type=int, default=4)
+    a = p.parse_args(argv)
+    gw.load() if os.path.exists(gw.lib_path()) else gw._build.build()
+    budget = int(a.budget_gb * (1 << 30))
+    if a.mode == "serve":
+        arrivals, jobs, grid = synth.make_serving_trace(a.jobs, a.rate, a.lo, a.hi, a.n_omega or 1024)
+        mols = [synth.molecules.build_job(j) for j in jobs]
+        arrivals = list(arrivals)
+    else:
+        mols, grid = synth.make_batch(n_omega=a.n_omega or 512)
+        arrivals = [0.0] * len(mols)
+    res, span = run_jobs(mols, grid, arrivals, gw.GW_MIXED, a.workers, budget)
+    out = {"mode": a.mode, "precision": "mixed", "n_omega": grid.n_omega, "workers": a.workers,
+           "hbm_budget_gb": a.budget_gb, **summarize(res, span, mols)}
+    if a.mode == "serve":
+        out["offered_rate_per_s"] = a.rate
+    if a.fp64_sample > 0:
+        out["fp64_plain"] = fp64_compare(mols, grid, res, a.fp64_sample)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

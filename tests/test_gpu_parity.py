@@ -222,3 +222,23 @@ def test_invalid_arguments(gwlib, ctx, cfg1):
     finally:
         w.free(); c.free(); m.free()
     assert ctx.bytes_in_use == before                      # nothing leaked by the failures
+
+
+def test_large_rank_grid_tridiagonalisation(gwlib, ctx):
+    """N_rank = 780 exceeds the thread-block-cluster eigensolver: the grid-wide
+    tridiagonalisation runs; invariants and QP energies against the oracle."""
+    from synth import molecules as sm
+    mol = sm._uniform_molecule("chain", 12, sm.SEED_BASE + 4321)
+    grid = synth.Grid(256)
+    r = oracle.solve(mol, grid, keep_W_freqs=[20, 130])
+    h, e, z, st = _run(gwlib, ctx, mol, grid)
+    try:
+        assert h["chi0"].info()["n_rank"] == 780
+        s = h["sigma"].copy()
+        assert rel(s["c"], r["c"]) < 1e-9
+        assert np.abs(e - r["e_qp"]).max() < 1e-8
+        assert np.array_equal(st, r["status"])
+        Wg = h["W"].full([20, 130])
+        assert rel(Wg - mol.v, r["W"] - mol.v) < 1e-9
+    finally:
+        _free(h)
