@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "internal.h"
@@ -46,6 +47,21 @@ void ctx_free(gw_ctx* ctx, void* p) {
     ctx->in_use -= it->second;
     ctx->blocks.erase(it);
     cudaFreeAsync(p, ctx->stream);
+}
+
+void allow_max_smem_impl(const void* func) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, bool> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[func]) return;
+    int dev = 0, optin = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    CUDA_CHECK(cudaFuncGetAttributes(&fa, func));
+    CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin - (int)fa.sharedSizeBytes));
+    done[func] = true;
 }
 
 static bool prof_match(const gw_ctx* ctx, const char* name) {

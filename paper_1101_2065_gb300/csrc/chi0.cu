@@ -220,7 +220,7 @@ void launch_fft_tables(gw_ctx* ctx, gw_chi0* c) {
     c->C2 = dalloc<double2>(ctx, L);
     klaunch(ctx, "k_twiddles", k_twiddles, div_up(L / 2, 256), 256, 0, c->tw, L);
     size_t smem = 2 * (size_t)L * sizeof(double2);
-    CUDA_CHECK(cudaFuncSetAttribute(k_kernel_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    allow_max_smem(k_kernel_spectra);
     klaunch(ctx, "k_kernel_spectra", k_kernel_spectra, 2, 256, smem, c->tw, N, c->logL, c->grid.d_omega, c->grid.eta, c->C1, c->C2);
 }
 
@@ -243,13 +243,13 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
         launch_to_f32(ctx, (const double*)c->C1, (float*)c->C1_32, 2LL * L);
         launch_to_f32(ctx, (const double*)c->C2, (float*)c->C2_32, 2LL * L);
         c->chi0_32 = dalloc<float2>(ctx, (size_t)N * n * n);
-        CUDA_CHECK(cudaFuncSetAttribute(k_chi0_fft<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        allow_max_smem(k_chi0_fft<float2>);
         klaunch(ctx, "k_chi0_fft32", k_chi0_fft<float2>, grid, 256, smem, (const float*)c->Ut32, c->n_pair, n,
                 (const int*)c->seg, (const double*)c->pFrac, c->j_lo, c->nb_bins, N, c->logL,
                 (const float2*)c->tw32, (const float2*)c->C1_32, (const float2*)c->C2_32, c->chi0_32);
     } else {
         c->chi0 = dalloc<double2>(ctx, (size_t)N * n * n);
-        CUDA_CHECK(cudaFuncSetAttribute(k_chi0_fft<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        allow_max_smem(k_chi0_fft<double2>);
         klaunch(ctx, "k_chi0_fft", k_chi0_fft<double2>, grid, 256, smem, (const double*)c->Ut, c->n_pair, n,
                 (const int*)c->seg, (const double*)c->pFrac, c->j_lo, c->nb_bins, N, c->logL,
                 (const double2*)c->tw, (const double2*)c->C1, (const double2*)c->C2, c->chi0);

@@ -7,7 +7,9 @@
 //     in L2); reflector k is kept in row k of the global copy;
 //  2. all eigenvalues of T by bisection on Sturm counts (one thread each);
 //  3. eigenvectors of T by binary64 inverse iteration with a pivoted
-//     tridiagonal LU (one thread per eigenvalue);
+//     tridiagonal LU (one thread per eigenvalue, hashed random start), then
+//     Gram-Schmidt inside clusters of near-degenerate eigenvalues (such as
+//     the null space of g when N_rank exceeds N_prod);
 //  4. back-transformation X = Q Y (one warp per vector);
 //  5. binary64 refinement of the full eigenbasis by the iteration of Ogita
 //     and Aishima (2018): R = I - X^T X, S = X^T g X,
@@ -363,7 +365,13 @@ __global__ void __launch_bounds__(IT) k_invit(const float* __restrict__ d, const
     unsigned char* piv = gws ? reinterpret_cast<unsigned char*>(base + 5 * n)
                              : reinterpret_cast<unsigned char*>(swd + (long long)blockDim.x * 5 * n) + (long long)threadIdx.x * n;
     tri_factor<double>(d, e, n, (double)lam[i], tiny, du, du1, du2, mul, piv);
-    for (int j = 0; j < n; ++j) x[j] = 1.0 + 0.001 * (double)((j * 7 + i * 13) % 17);
+    // start from a hashed pseudo-random vector so that the vectors of a
+    // degenerate eigenvalue start in different directions
+    for (int j = 0; j < n; ++j) {
+        unsigned int h = (unsigned int)i * 2654435761u ^ ((unsigned int)j * 2246822519u + 0x9e3779b9u);
+        h ^= h >> 15; h *= 2246822519u; h ^= h >> 13; h *= 3266489917u; h ^= h >> 16;
+        x[j] = 0.5 + (double)(h & 0xffffff) * (1.0 / 16777216.0);
+    }
     for (int it = 0; it < 3; ++it) {
         tri_solve<double>(n, du, du1, du2, mul, piv, x);
         double nr = 0.0;
@@ -373,6 +381,38 @@ __global__ void __launch_bounds__(IT) k_invit(const float* __restrict__ d, const
     }
     float* yo = Y + (long long)i * n;
     for (int j = 0; j < n; ++j) yo[j] = (float)x[j];
+}
+
+// Modified Gram-Schmidt (twice) inside each cluster of near-degenerate
+// eigenvalues (consecutive gaps < tol), one CTA per cluster.  Inverse
+// iteration cannot separate the vectors of an (almost) multiple eigenvalue;
+// Gram-Schmidt turns the differently started vectors into an orthonormal
+// basis of the eigenspace.
+__global__ void __launch_bounds__(256) k_cluster_mgs(const float* __restrict__ lam, int n, float tol,
+                                                     float* __restrict__ Y) {
+    __shared__ float red[33];
+    const int i0 = blockIdx.x;
+    if (i0 > 0 && lam[i0] - lam[i0 - 1] < tol) return;
+    int i1 = i0 + 1;
+    while (i1 < n && lam[i1] - lam[i1 - 1] < tol) ++i1;
+    if (i1 - i0 < 2) return;
+    for (int i = i0; i < i1; ++i) {
+        float* x = Y + (long long)i * n;
+        for (int pass = 0; pass < 2; ++pass)
+            for (int q = i0; q < i; ++q) {
+                const float* y = Y + (long long)q * n;
+                float s = 0.f;
+                for (int j = threadIdx.x; j < n; j += blockDim.x) s += y[j] * x[j];
+                s = block_sum1024(s, red);
+                for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] -= s * y[j];
+                __syncthreads();
+            }
+        float nr = 0.f;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) nr += x[j] * x[j];
+        nr = rsqrtf(fmaxf(block_sum1024(nr, red), 1e-38f));
+        for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] *= nr;
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------------ 4
@@ -521,12 +561,12 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         const int rows = (n + CL - 1) / CL;
         const size_t smem_cl = sizeof(float) * ((size_t)rows * n + 2 * (size_t)n + 2 * (size_t)rows);
         if (smem_cl <= 220 * 1024) {
-            CUDA_CHECK(cudaFuncSetAttribute(k_sytrd32_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cl));
+            allow_max_smem(k_sytrd32_cl);
             klaunch(ctx, "k_sytrd32_cl", k_sytrd32_cl, CL, 1024, smem_cl, A32, n, d, e, tau);
         } else {
             const size_t smem = 2 * (size_t)n * sizeof(float);
             if (smem > 200 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for the eigensolver");
-            CUDA_CHECK(cudaFuncSetAttribute(k_sytrd32_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            allow_max_smem(k_sytrd32_grid);
             int per_sm = 0;
             CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sytrd32_grid, 512, smem));
             if (per_sm < 1) gw_throw(GW_ERR_CUDA, "tridiagonalisation kernel cannot be resident");
@@ -558,7 +598,7 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         if (per_thread <= 200 * 1024) {
             const int it_threads = (int)std::max<size_t>(1, std::min<size_t>(IT, (200 * 1024) / per_thread));
             const size_t smem_it = per_thread * it_threads;
-            CUDA_CHECK(cudaFuncSetAttribute(k_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_it));
+            allow_max_smem(k_invit);
             klaunch(ctx, "k_invit", k_invit, div_up(n, it_threads), it_threads, smem_it, (const float*)d,
                     (const float*)e, (const float*)lam32, n, 1e-13 * (double)bnd, Y, (double*)nullptr);
         } else {
@@ -566,9 +606,10 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
             klaunch(ctx, "k_invit", k_invit, div_up(n, IT), IT, 0, (const float*)d, (const float*)e,
                     (const float*)lam32, n, 1e-13 * (double)bnd, Y, gws);
         }
+        klaunch(ctx, "k_cluster_mgs", k_cluster_mgs, n, 256, 0, (const float*)lam32, n, 1e-6f * bnd, Y);
         const int bt_warps = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / ((size_t)n * sizeof(float))));
         const size_t smem_bt = (size_t)bt_warps * n * sizeof(float);
-        CUDA_CHECK(cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bt));
+        allow_max_smem(k_backtransform);
         klaunch(ctx, "k_backtransform", k_backtransform, div_up(n, bt_warps), 32 * bt_warps, smem_bt,
                 (const float*)A32, (const float*)tau, n, (const float*)Y, X);
         // binary64 refinement

@@ -71,6 +71,13 @@ void after_launch(gw_ctx* ctx, const char* name);
 void prof_begin(gw_ctx* ctx, const char* name);
 #define LAUNCH_CHECK(ctx, name) after_launch((ctx), (name))
 
+// Allow a kernel the device's full dynamic shared memory, once per process.
+// (The attribute is process-wide: setting per-call sizes from concurrent
+// host threads would race.)
+void allow_max_smem_impl(const void* func);
+template <typename... KArgs>
+inline void allow_max_smem(void (*kernel)(KArgs...)) { allow_max_smem_impl((const void*)kernel); }
+
 // Launch a kernel on the context stream with launch accounting.
 template <typename... KArgs, typename... Args>
 inline void klaunch(gw_ctx* ctx, const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,

@@ -343,10 +343,10 @@ void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* co
     size_t smem = csz * (size_t)n * RC;
     int grid = std::max(1, std::min(N - 1, ctx->num_sms));
     if (f32) {
-        CUDA_CHECK(cudaFuncSetAttribute(k_forms<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        allow_max_smem(k_forms<float2>);
         klaunch(ctx, "k_forms32", k_forms<float2>, grid, 256, smem, (const float2*)W->fac32, n, N, Q, R, RC, cout);
     } else {
-        CUDA_CHECK(cudaFuncSetAttribute(k_forms<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        allow_max_smem(k_forms<double2>);
         klaunch(ctx, "k_forms", k_forms<double2>, grid, 256, smem, (const double2*)W->fac, n, N, Q, R, RC, cout);
     }
 }

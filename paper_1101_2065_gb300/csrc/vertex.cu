@@ -70,11 +70,7 @@ void launch_vertex_contract(gw_ctx* ctx, const gw_mol* mol, const int* Es, int n
                             const int* map, double* out, long long ld) {
     const int nl = mol->max_nloc;
     size_t smem = sizeof(double) * ((size_t)nl * nl + (size_t)nl * (2 * FC + EC));
-    static bool attr_set = false;
-    if (!attr_set) {
-        CUDA_CHECK(cudaFuncSetAttribute(k_vertex_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr_set = true;
-    }
+    allow_max_smem(k_vertex_contract);
     dim3 grid(mol->n_prod, div_up(nF, FC));
     klaunch(ctx, "k_vertex_contract", k_vertex_contract, grid, 256, smem, mol->X, mol->n_orb, mol->vertex, mol->voff, mol->prod_atom,
                                                        mol->loc_ptr, mol->loc_idx, Es, nE, Fs, nF, map, out, ld);
