@@ -151,7 +151,9 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ GPU arm
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 FMA/clk/SM x 152 SMs at 2070 MHz
-KERNELS = ["k_forms", "k_forms32", "k_ldlt", "k_ldlt32", "k_chi0_fft", "k_chi0_fft32", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl",
+KERNELS = ["k_forms_diag", "k_forms_update", "k_forms32_diag", "k_forms32_update",
+           "k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk", "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk",
+           "k_chi0_fft", "k_chi0_fft32", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl",
            "k_bisect", "k_invit", "k_backtransform", "k_oa_stats", "k_oa_E", "k_vertex_contract", "k_sigma_c",
            "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_to_f32", "k_kernel_spectra"]
 
@@ -159,21 +161,40 @@ KERNELS = ["k_forms", "k_forms32", "k_ldlt", "k_ldlt32", "k_chi0_fft", "k_chi0_f
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
 # of the current kernel version on this workload (profiles/k_*_ring12.md);
 # an entry is dropped whenever its kernel changes.
-NCU_TRAFFIC = {"k_ldlt32": 2.997e9, "k_forms32": 4.102e8}
+NCU_TRAFFIC = {}
+
+
+def _panels(n, nb):
+    """(kb, m) per panel step of the blocked factorisation: panel width and rows below it."""
+    out = []
+    for k0 in range(0, n, nb):
+        kb = min(nb, n - k0)
+        out.append((kb, n - k0 - kb))
+    return out
 
 
 def kernel_model(name, mol, grid, n_rank):
-    """Algorithmic work of one launch of a kernel: (flops, bound, peak TFLOP/s)."""
+    """Algorithmic work of one step's launches of a kernel: (flops, bound, peak TFLOP/s).
+
+    Complex multiply-adds count 8 flops.  The blocked factorisation and
+    forward substitution launch once per panel with shrinking sizes, so the
+    figure is summed over the step's launches (achieved = flops / kernel time
+    per step = average flops per launch / average launch time)."""
     n, N, R = mol.n_sub, grid.n_omega, 2 * mol.n_orb
     L = 2 * N
-    f32 = name.endswith("32")
+    f32 = "32" in name
     peak = PEAK_FP32_TFLOPS if f32 else PEAK_FP64_TFLOPS
-    if name.startswith("k_forms"):
-        # forward substitution L y = q: n^2/2 complex multiply-adds (8 flops) per RHS and frequency
-        return (N - 1) * R * 4.0 * n * n, "alu", peak
-    if name.startswith("k_ldlt"):
-        # complex symmetric L D L^T: n^3/6 complex multiply-adds per frequency
-        return N * (8.0 / 6.0) * n ** 3, "alu", peak
+    nb = 32 if f32 else 16
+    P = _panels(n, nb)
+    if name.startswith("k_ldlt") and name.endswith("_syrk"):
+        # trailing lower triangle (incl. diagonal) x panel width, every frequency
+        return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if m > 0), "alu", peak
+    if name.startswith("k_ldlt") and name.endswith("_panel"):
+        return N * 8.0 * sum(kb ** 3 / 6 + m * kb * (kb - 1) / 2 for kb, m in P), "alu", peak
+    if name.startswith("k_forms") and name.endswith("_update"):
+        return (N - 1) * 8.0 * R * sum(m * kb for kb, m in P if m > 0), "alu", peak
+    if name.startswith("k_forms") and name.endswith("_diag"):
+        return (N - 1) * 8.0 * R * sum(kb * (kb - 1) / 2 for kb, m in P), "alu", peak
     if name.startswith("k_chi0_fft"):
         # per element pair: one forward and two inverse complex FFTs of length L (5 L log2 L flops each)
         pairs = (n * (n + 1) // 2 + 1) // 2
@@ -284,13 +305,14 @@ def run_gpu(a):
     flops, bound, peak = kernel_model(dom, mol, grid, main["n_rank"])
     k_ms, k_n = main["kt"][dom]
     avg_s = k_ms / k_n / 1e3
-    achieved = flops / avg_s / 1e12 if flops else None
+    per_launch = flops / (k_n / a.steps) if flops else None
+    achieved = per_launch / avg_s / 1e12 if flops else None
     step_ms = main["t_ms"] / a.steps
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": NCU_TRAFFIC.get(dom),
             "peak_source": ("128 binary32 FMA/clk/SM" if peak == PEAK_FP32_TFLOPS else "2 binary64 FMA/clk/SM")
             + " x 152 SMs x 2070 MHz (recipe unit counts and maximum clock)",
-            "avg_launch_ms": avg_s * 1e3, "launches": k_n,
+            "avg_launch_ms": avg_s * 1e3, "launches": k_n, "flops_per_launch": per_launch,
             "share_of_step": (k_ms / a.steps) / step_ms}
     kernels = {k: {"ms_per_step": v[0] / a.steps, "launches_per_step": v[1] / a.steps} for k, v in main["kt"].items()}
 

@@ -483,7 +483,7 @@ static gw_W* screen_W(gw_ctx* ctx, const gw_chi0* c) {
     try {
         if (c->prec == GW_MIXED) w->fac32 = dalloc<float2>(ctx, N * n * n);
         else w->fac = dalloc<double2>(ctx, N * n * n);
-        w->piv = dalloc<double>(ctx, N);
+        w->piv = dalloc<double>(ctx, 2 * N);      // [N) ratios, [N, 2N) running min |d|
         launch_ldlt(ctx, w);
         std::vector<double> piv(N);
         download(ctx, piv.data(), w->piv, N);
