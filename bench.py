@@ -151,7 +151,7 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ GPU arm
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 FMA/clk/SM x 152 SMs at 2070 MHz
-KERNELS = ["k_forms_diag", "k_forms_update", "k_forms32_diag", "k_forms32_update",
+KERNELS = ["k_forms", "k_forms32",
            "k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk", "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk",
            "k_chi0_fft", "k_chi0_fft32", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl",
            "k_bisect", "k_invit", "k_backtransform", "k_oa_stats", "k_oa_E", "k_vertex_contract", "k_sigma_c",
@@ -191,10 +191,9 @@ def kernel_model(name, mol, grid, n_rank):
         return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if m > 0), "alu", peak
     if name.startswith("k_ldlt") and name.endswith("_panel"):
         return N * 8.0 * sum(kb ** 3 / 6 + m * kb * (kb - 1) / 2 for kb, m in P), "alu", peak
-    if name.startswith("k_forms") and name.endswith("_update"):
-        return (N - 1) * 8.0 * R * sum(m * kb for kb, m in P if m > 0), "alu", peak
-    if name.startswith("k_forms") and name.endswith("_diag"):
-        return (N - 1) * 8.0 * R * sum(kb * (kb - 1) / 2 for kb, m in P), "alu", peak
+    if name.startswith("k_forms"):
+        # forward substitution L y = q: n(n-1)/2 complex multiply-adds per right-hand side and frequency
+        return (N - 1) * 8.0 * R * n * (n - 1) / 2, "alu", peak
     if name.startswith("k_chi0_fft"):
         # per element pair: one forward and two inverse complex FFTs of length L (5 L log2 L flops each)
         pairs = (n * (n + 1) // 2 + 1) // 2

@@ -139,6 +139,7 @@ struct gw_W {
     const gw_chi0* chi0 = nullptr;
     double2* fac = nullptr;          // [n_omega*n*n] strict lower L, diagonal D
     float2* fac32 = nullptr;
+    void* linv = nullptr;            // [n_omega][panels][NB][NB] inverses of the unit lower diagonal blocks
     double* piv = nullptr;           // [n_omega] min|d| / max|M|
     double min_pivot_ratio = 0.0;
 };
@@ -179,6 +180,7 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c);
 void launch_spectral_readback(gw_ctx* ctx, const gw_chi0* c, int j0, int nj, double* A);
 void launch_to_f32(gw_ctx* ctx, const double* a, float* b, long long n);
 // screen.cu
+size_t ldlt_linv_bytes(int n, int n_omega, gw_precision prec);
 void launch_ldlt(gw_ctx* ctx, gw_W* W);
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* c);
 void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work);

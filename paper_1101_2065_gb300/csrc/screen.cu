@@ -13,11 +13,13 @@
 //     never formed on the hot path: the forms only need M_k^-1.
 // a6  c_r(s_k) = q_r^T gamma_k q_r with gamma_k = -(1/pi) Im chi^RPA_k, and
 //     q^T chi^RPA q = q^T M^-1 q - q^T q with q real, so
-//     c_r = -(1/pi) Im sum_i y_i^2 / d_i,  y = L^-1 q.  All right-hand sides
-//     of all frequencies go through the same blocked forward substitution:
-//     k_forms_diag solves the NB rows of the diagonal block (one thread per
-//     right-hand side) and accumulates y_i^2/d_i in binary64, k_forms_update
-//     applies Y_rest -= L_rest,b Y_b.  c_r(s_0) = 0 (odd spectral function).
+//     c_r = -(1/pi) Im sum_i y_i^2 / d_i,  y = L^-1 q.  One CTA per
+//     frequency and chunk of right-hand sides keeps its chunk of Y in shared
+//     memory for the whole blocked forward substitution: per panel it applies
+//     the inverse of the unit lower diagonal block (precomputed by the panel
+//     step of a5, so no serial chain remains), adds y_i^2/d_i to binary64
+//     sums, and updates the rows below from L tiles streamed through a
+//     cp.async double buffer.  c_r(s_0) = 0 (odd spectral function).
 #include <cmath>
 
 #include "internal.h"
@@ -25,12 +27,18 @@
 namespace {
 
 // Panel width NB; trailing-update tile T x T with A x A complex outputs per
-// thread; forms update tile FT rows x FC right-hand sides, FA x FA per
-// thread.  binary64 is issue-bound (1/64 of the binary32 rate): small tiles
-// waste less on the triangle and keep the panel row in registers.
+// thread; the forms stream L in tiles of FT = 16 FA rows and give each
+// thread FA rows x CB right-hand sides (RC <= 16 CB per CTA).  binary64 is
+// issue-bound (1/64 of the binary32 rate): small tiles waste less on the
+// triangle and keep the panel row in registers.
 template <typename C> struct Tile;
-template <> struct Tile<double2> { static constexpr int NB = 16, T = 32, A = 2, FT = 32, FC = 32, FA = 2; };
-template <> struct Tile<float2> { static constexpr int NB = 32, T = 64, A = 4, FT = 64, FC = 64, FA = 4; };
+template <> struct Tile<double2> { static constexpr int NB = 16, T = 32, A = 2, FT = 32, FA = 2, CB = 2; };
+template <> struct Tile<float2> { static constexpr int NB = 32, T = 64, A = 4, FT = 64, FA = 4, CB = 5; };
+
+// shared-memory row pitch of an NB-wide tile (a multiple of 16 bytes, for cp.async)
+template <typename C> __host__ __device__ constexpr int tile_pitch() {
+    return sizeof(C) == 8 ? Tile<C>::NB + 2 : Tile<C>::NB + 1;
+}
 
 template <typename C> struct CT;
 template <> struct CT<double2> {
@@ -104,78 +112,141 @@ __global__ void __launch_bounds__(256) k_ldlt_init(const C* __restrict__ chi0, C
     if (threadIdx.x == 0) piv[k] = sqrt(mx);
 }
 
-// Panel k0 of every frequency: factor the diagonal block, then solve the
-// rows below, x D L11^T = a.  piv[N + k] carries min |d| between steps; the
-// last panel writes piv[k] = min |d| / max |M| and flags a zero pivot.
+// x D L11^T = a for one panel row held in registers: x_j = (a_j - sum_{p<j}
+// x_p SD[j][p]) / d_j.
+template <typename C, bool FULL>
+__device__ __forceinline__ void panel_row_solve(C* __restrict__ row, const C (*SD)[Tile<C>::NB + 1],
+                                                const C* Dinv, int kb) {
+    constexpr int NB = Tile<C>::NB;
+    C x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (FULL || j < kb) x[j] = row[j];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (FULL || j < kb) {
+            C a = x[j];
+#pragma unroll
+            for (int p = 0; p < j; ++p) a = cfms(x[p], SD[j][p], a);
+            x[j] = cmul(a, Dinv[j]);
+        }
+        asm volatile("" ::: "memory");   // keep the SD loads of later rows from being hoisted (registers)
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (FULL || j < kb) row[j] = x[j];
+}
+
+// Panel k0 of every frequency: factor the diagonal block, solve the rows
+// below (x D L11^T = a), and store L11^-1 for the forward substitution of
+// a6.  piv[N + k] carries min |d| between steps; the last panel writes
+// piv[k] = min |d| / max |M| and flags a zero pivot.
 template <typename C>
 __global__ void __launch_bounds__(256, 2) k_ldlt_panel(C* __restrict__ fac, int n, int N, int k0,
-                                                    double* __restrict__ piv, int* status) {
-    constexpr int NB = Tile<C>::NB;
+                                                    C* __restrict__ linv, double* __restrict__ piv, int* status) {
+    constexpr int NB = Tile<C>::NB, H = NB / 2, NPAIR = NB * (NB - 1) / 2, PPT = (NPAIR + 255) / 256;
     __shared__ C S[NB][NB + 1];     // L11 strictly below the diagonal, D on it
     __shared__ C SD[NB][NB + 1];    // SD[j][p] = L_jp d_p
+    __shared__ C X[NB][NB + 1];     // L11^-1
     __shared__ C Dinv[NB];
     const int k = blockIdx.x, tid = threadIdx.x;
     C* A = fac + (long long)k * n * n;
     const int kb = min(NB, n - k0), k1 = k0 + kb;
-    for (int t = tid; t < kb * kb; t += blockDim.x) {
-        int i = t / kb, j = t % kb;
-        if (j <= i) S[i][j] = A[(long long)(k0 + i) * n + k0 + j];
+    for (int t = tid; t < NB * NB; t += blockDim.x) {
+        const int i = t / NB, j = t % NB;
+        // outside kb: identity, so the block inverse below needs no special case
+        S[i][j] = (i < kb && j < kb) ? (j <= i ? A[(long long)(k0 + i) * n + k0 + j] : CT<C>::mk(0, 0))
+                                     : CT<C>::mk(i == j ? 1 : 0, 0);
+    }
+    // pairs (i, l), 1 <= l <= i < NB, owned by this thread for the whole factorisation
+    int pi[PPT], pl[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int t = tid + 256 * q;
+        int I = 0, J = 0;
+        if (t < NPAIR) tri_ij(t, I, J);
+        pi[q] = t < NPAIR ? I + 1 : -1;
+        pl[q] = J + 1;
     }
     __syncthreads();
-    // unblocked L D L^T of the diagonal block, one column per step: every
-    // thread updates pairs (i, l), j < l <= i, with the unscaled column j,
-    // then column j is scaled by 1/d_j
+    // unblocked L D L^T of the diagonal block, one column per step: the pairs
+    // with l > j take the update with the unscaled column j, then column j is
+    // scaled by 1/d_j
     for (int j = 0; j < kb; ++j) {
         const C dinv = cdiv(CT<C>::mk(1, 0), S[j][j]);
-        const int m = kb - 1 - j;
-        for (int t = tid; t < m * (m + 1) / 2; t += blockDim.x) {
-            int ii, ll;
-            tri_ij(t, ii, ll);
-            const int i = j + 1 + ii, l = j + 1 + ll;
-            S[i][l] = cfms(cmul(S[i][j], dinv), S[l][j], S[i][l]);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            const int i = pi[q], l = pl[q];
+            if (i >= 0 && l > j && i < kb) S[i][l] = cfms(cmul(S[i][j], dinv), S[l][j], S[i][l]);
         }
         __syncthreads();
         if (tid > j && tid < kb) S[tid][j] = cmul(S[tid][j], dinv);
     }
     __syncthreads();
     for (int t = tid; t < kb * kb; t += blockDim.x) {
-        int i = t / kb, p = t % kb;
+        const int i = t / kb, p = t % kb;
         if (p < i) SD[i][p] = cmul(S[i][p], S[p][p]);
         if (p <= i) A[(long long)(k0 + i) * n + k0 + p] = S[i][p];
     }
     if (tid < kb) Dinv[tid] = cdiv(CT<C>::mk(1, 0), S[tid][tid]);
     __syncthreads();
-    C x[NB];
-    for (int r = k1 + tid; r < n; r += blockDim.x) {
-        C* row = A + (long long)r * n + k0;
+    if (tid < 32) {
+        // warp 0: L11^-1 = [[A^-1, 0], [-C^-1 B A^-1, C^-1]] with H x H blocks
+        // (the unit diagonal is implied: S holds D there, replaced by 1 here)
+        const int lane = tid;
+        if (lane < NB) {
+            const int off = lane < H ? 0 : H, c = lane % H;
+            C x[H];
 #pragma unroll
-        for (int j = 0; j < NB; ++j)
-            if (j < kb) x[j] = row[j];
+            for (int i = 0; i < H; ++i) {
+                C v = CT<C>::mk(i == c ? 1 : 0, 0);
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            if (j < kb) {
-                C a = x[j];
-#pragma unroll
-                for (int p = 0; p < NB; ++p)
-                    if (p < j) a = cfms(x[p], SD[j][p], a);
-                x[j] = cmul(a, Dinv[j]);
+                for (int p = 0; p < i; ++p)
+                    if (p >= c) v = cfms(S[off + i][off + p], x[p], v);
+                x[i] = v;
+                asm volatile("" ::: "memory");
             }
-            asm volatile("" ::: "memory");   // keep the SD loads of later rows from being hoisted (registers)
-        }
 #pragma unroll
-        for (int j = 0; j < NB; ++j)
-            if (j < kb) row[j] = x[j];
-    }
-    if (tid == 0) {
-        typename CT<C>::R d2 = S[0][0].x * S[0][0].x + S[0][0].y * S[0][0].y;
-        for (int j = 1; j < kb; ++j) d2 = fmin(d2, S[j][j].x * S[j][j].x + S[j][j].y * S[j][j].y);
-        double dm = sqrt((double)d2);
-        if (k0 > 0) dm = fmin(dm, piv[N + k]);
-        if (k1 < n) piv[N + k] = dm;
-        else {
-            const double mx = piv[k];
-            piv[k] = dm / (mx > 0.0 ? mx : 1.0);
-            if (!(dm > 0.0) || !isfinite(dm)) atomicOr(status, ST_SINGULAR);
+            for (int i = 0; i < H; ++i) X[off + i][off + c] = x[i];
+        }
+        __syncwarp();
+        // W = B A^-1 into the (zero) upper right block of X
+        for (int t = lane; t < H * H; t += 32) {
+            const int i = t / H, j = t % H;
+            C w = CT<C>::mk(0, 0);
+            for (int p = j; p < H; ++p) w = cfma(S[H + i][p], X[p][j], w);
+            X[i][H + j] = w;
+        }
+        __syncwarp();
+        for (int t = lane; t < H * H; t += 32) {
+            const int i = t / H, j = t % H;
+            C w = CT<C>::mk(0, 0);
+            for (int p = 0; p <= i; ++p) w = cfma(X[H + i][H + p], X[p][H + j], w);
+            X[H + i][j] = CT<C>::mk(-w.x, -w.y);
+        }
+        __syncwarp();
+        C* Li = linv + ((long long)k * ((n + NB - 1) / NB) + k0 / NB) * NB * NB;
+        for (int t = lane; t < NB * NB; t += 32) {
+            const int i = t / NB, j = t % NB;
+            Li[t] = (i < kb && j < kb && j <= i) ? X[i][j] : CT<C>::mk(0, 0);
+        }
+        if (lane == 0) {
+            typename CT<C>::R d2 = S[0][0].x * S[0][0].x + S[0][0].y * S[0][0].y;
+            for (int j = 1; j < kb; ++j) d2 = fmin(d2, S[j][j].x * S[j][j].x + S[j][j].y * S[j][j].y);
+            double dm = sqrt((double)d2);
+            if (k0 > 0) dm = fmin(dm, piv[N + k]);
+            if (k1 < n) piv[N + k] = dm;
+            else {
+                const double mx = piv[k];
+                piv[k] = dm / (mx > 0.0 ? mx : 1.0);
+                if (!(dm > 0.0) || !isfinite(dm)) atomicOr(status, ST_SINGULAR);
+            }
+        }
+    } else {
+        const int nthr = blockDim.x - 32;
+        for (int r = k1 + tid - 32; r < n; r += nthr) {
+            if (kb == NB) panel_row_solve<C, true>(A + (long long)r * n + k0, SD, Dinv, kb);
+            else panel_row_solve<C, false>(A + (long long)r * n + k0, SD, Dinv, kb);
         }
     }
 }
@@ -238,121 +309,214 @@ __global__ void __launch_bounds__(256) k_ldlt_syrk(C* __restrict__ fac, int n, i
         }
 }
 
-// Forward substitution, diagonal block k0 of frequency k = 1 + blockIdx.x:
-// L_bb y_b = y_b for every right-hand side (one thread each), then
-// acc_r += y_i^2 / d_i in binary64.  Before the first update the
-// right-hand sides are the real q (Q [n][R]); afterwards Y [N-1][n][R].
-// The last block writes c[r*N + k] = -(1/pi) Im acc_r.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+template <typename C> __device__ __forceinline__ void cp_async_c(C* dst, const C* src) {
+    if (sizeof(C) == 8) cp_async8(dst, src);
+    else cp_async16(dst, src);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
+// rows [r0, r0 + FT) x columns [k0, k0 + NB) of F into a pitched tile (zero
+// outside the matrix or the panel); no commit
 template <typename C>
-__global__ void __launch_bounds__(256, 2) k_forms_diag(const C* __restrict__ fac, int n, int N,
-                                                    const double* __restrict__ Q, int R, C* __restrict__ Y,
-                                                    double2* __restrict__ accum, double* __restrict__ c, int k0) {
-    typedef typename CT<C>::R T;
-    constexpr int NB = Tile<C>::NB;
-    __shared__ C S[NB][NB + 1];
-    __shared__ C dinv[NB];
-    const int k = 1 + blockIdx.x, tid = threadIdx.x;
-    const C* F = fac + (long long)k * n * n;
-    C* Yk = Y + (long long)(k - 1) * n * R;
-    const int kb = min(NB, n - k0), k1 = k0 + kb;
-    const bool last = k1 == n;
-    for (int t = tid; t < kb * kb; t += blockDim.x) {
-        int i = t / kb, j = t % kb;
-        if (j <= i) S[i][j] = F[(long long)(k0 + i) * n + k0 + j];
-    }
-    __syncthreads();
-    if (tid < kb) dinv[tid] = cdiv(CT<C>::mk(T(1), T(0)), S[tid][tid]);
-    __syncthreads();
-    for (int r = tid; r < R; r += blockDim.x) {
-        C y[NB];
-#pragma unroll
-        for (int i = 0; i < NB; ++i)
-            if (i < kb) {
-                const long long o = (long long)(k0 + i) * R + r;
-                y[i] = k0 == 0 ? CT<C>::mk(T(Q[o]), T(0)) : Yk[o];
-            }
-        // this block's y_i^2/d_i summed in the working precision, added to the
-        // binary64 running sum once per block
-        C part = CT<C>::mk(T(0), T(0));
-#pragma unroll
-        for (int i = 0; i < NB; ++i)
-            if (i < kb) {
-                C v = y[i];
-#pragma unroll
-                for (int p = 0; p < NB; ++p)
-                    if (p < i) v = cfms(S[i][p], y[p], v);
-                y[i] = v;
-                part = cfma(cmul(v, v), dinv[i], part);
-                asm volatile("" ::: "memory");
-            }
-        double2 a = k0 == 0 ? make_double2(0.0, 0.0) : accum[(long long)(k - 1) * R + r];
-        a.x += (double)part.x;
-        a.y += (double)part.y;
-        if (last) {
-            c[(long long)r * N + k] = -a.y / M_PI;
-            if (k == 1) c[(long long)r * N] = 0.0;
-        } else {
-            accum[(long long)(k - 1) * R + r] = a;
-#pragma unroll
-            for (int i = 0; i < NB; ++i)
-                if (i < kb) Yk[(long long)(k0 + i) * R + r] = y[i];
-        }
+__device__ __forceinline__ void load_l_tile(C* dst, const C* __restrict__ F, int n, int r0, int k0, int kb) {
+    constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, LP = tile_pitch<C>();
+    for (int t = threadIdx.x; t < FT * NB; t += blockDim.x) {
+        const int rr = t / NB, p = t % NB;
+        C* d = dst + rr * LP + p;
+        if (p < kb && r0 + rr < n) cp_async_c(d, F + (long long)(r0 + rr) * n + k0 + p);
+        else *d = CT<C>::mk(0, 0);
     }
 }
 
-// Forward substitution update after block k0: Y_rest -= L_rest,b Y_b, rows
-// tile blockIdx.x, right-hand-side tile blockIdx.y, frequency 1 + blockIdx.z.
+// L11^-1 of panel k0 (NB x NB, zero outside kb) and its pivots d_i; no commit
 template <typename C>
-__global__ void __launch_bounds__(256) k_forms_update(const C* __restrict__ fac, int n, const double* __restrict__ Q,
-                                                      int R, C* __restrict__ Y, int k0) {
+__device__ __forceinline__ void load_diag_data(C* sLi, C* sD, const C* __restrict__ Li, const C* __restrict__ F,
+                                               int n, int k0, int kb) {
+    constexpr int NB = Tile<C>::NB, V = 16 / sizeof(C);
+    for (int t = threadIdx.x; t < NB * NB / V; t += blockDim.x) cp_async16(sLi + t * V, Li + t * V);
+    for (int i = threadIdx.x; i < NB; i += blockDim.x) {
+        if (i < kb) cp_async_c(sD + i, F + (long long)(k0 + i) * n + k0 + i);
+        else sD[i] = CT<C>::mk(0, 0);
+    }
+}
+
+__device__ __forceinline__ void load_pair(const float2* p, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void load_pair(const double2* p, double2& a, double2& b) {
+    a = p[0];
+    b = p[1];
+}
+
+// acc[a][b] += sum_p A[(arow + a) lda + p] Yb[p RC + tx + 16 b], p < kb.
+// Columns past RC read the next row or the zero padding after Y (finite
+// values, never stored); no per-column branch, so the accumulator chains
+// interleave.
+template <typename C, int RA, bool FULL>
+__device__ __forceinline__ void mma_rows(C (&acc)[RA][Tile<C>::CB], const C* __restrict__ A, int lda, int arow,
+                                         const C* __restrict__ Yb, int RC, int kb) {
     typedef typename CT<C>::R T;
-    constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, FC = Tile<C>::FC, FA = Tile<C>::FA;
-    __shared__ C sL[FT][NB + 1];
-    __shared__ C sY[NB][FC];
-    const int tid = threadIdx.x, k = 1 + blockIdx.z;
-    const C* F = fac + (long long)k * n * n;
-    C* Yk = Y + (long long)(k - 1) * n * R;
-    const int kb = min(NB, n - k0), k1 = k0 + kb;
-    const int r0 = k1 + blockIdx.x * FT, c0 = blockIdx.y * FC;
-    for (int t = tid; t < FT * NB; t += blockDim.x) {
-        int rr = t / NB, p = t % NB;
-        sL[rr][p] = (p < kb && r0 + rr < n) ? F[(long long)(r0 + rr) * n + k0 + p] : CT<C>::mk(T(0), T(0));
-    }
-    for (int t = tid; t < NB * FC; t += blockDim.x) {
-        int p = t / FC, cc = t % FC;
-        sY[p][cc] = (p < kb && c0 + cc < R) ? Yk[(long long)(k0 + p) * R + c0 + cc] : CT<C>::mk(T(0), T(0));
-    }
-    __syncthreads();
-    const int ty = tid / 16, tx = tid % 16;
-    C acc[FA][FA];
+    constexpr int NB = Tile<C>::NB, CB = Tile<C>::CB;
+    const int tx = threadIdx.x % 16;
+#pragma unroll 2
+    for (int p = 0; p < NB; p += 2) {
+        if (!FULL && p >= kb) break;
+        C l0[RA], l1[RA];
 #pragma unroll
-    for (int a = 0; a < FA; ++a)
+        for (int a = 0; a < RA; ++a) load_pair(A + (arow + a) * lda + p, l0[a], l1[a]);
+        const bool two = FULL || p + 1 < kb;
+        C y0[CB], y1[CB];
 #pragma unroll
-        for (int b = 0; b < FA; ++b) acc[a][b] = CT<C>::mk(T(0), T(0));
-#pragma unroll 8
-    for (int p = 0; p < NB; ++p) {
-        C l[FA], y[FA];
-#pragma unroll
-        for (int a = 0; a < FA; ++a) l[a] = sL[ty + 16 * a][p];
-#pragma unroll
-        for (int b = 0; b < FA; ++b) y[b] = sY[p][tx + 16 * b];
-#pragma unroll
-        for (int a = 0; a < FA; ++a)
-#pragma unroll
-            for (int b = 0; b < FA; ++b) acc[a][b] = cfma(l[a], y[b], acc[a][b]);
-    }
-#pragma unroll
-    for (int a = 0; a < FA; ++a) {
-        const int i = r0 + ty + 16 * a;
-        if (i >= n) continue;
-#pragma unroll
-        for (int b = 0; b < FA; ++b) {
-            const int cc = c0 + tx + 16 * b;
-            if (cc >= R) continue;
-            const long long o = (long long)i * R + cc;
-            const C src = k0 == 0 ? CT<C>::mk(T(Q[o]), T(0)) : Yk[o];
-            Yk[o] = csub(src, acc[a][b]);
+        for (int b = 0; b < CB; ++b) {
+            y0[b] = Yb[p * RC + tx + 16 * b];
+            y1[b] = two ? Yb[(p + 1) * RC + tx + 16 * b] : CT<C>::mk(T(0), T(0));
         }
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+#pragma unroll
+            for (int b = 0; b < CB; ++b) acc[a][b] = cfma(l0[a], y0[b], acc[a][b]);
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+#pragma unroll
+            for (int b = 0; b < CB; ++b) acc[a][b] = cfma(l1[a], y1[b], acc[a][b]);
+    }
+}
+
+// c[r*N + k] = -(1/pi) Im sum_i y_i^2/d_i, y = L_k^-1 q_r: right-hand sides
+// [chunk*RC, chunk*RC + RC) of frequency k = 1 + blockIdx.y, chunk = blockIdx.x.
+// Shared memory: two L tiles [FT][LP], two L11^-1 [NB][NB] and pivots [NB]
+// (next panel prefetched), Y [n][RC] + one padding row of 16 CB.  Thread
+// (ty, tx) owns rows ty*FA .. ty*FA + FA - 1 of a tile and columns tx + 16 b.
+template <typename C>
+__global__ void __launch_bounds__(256, 1) k_forms(const C* __restrict__ fac, const C* __restrict__ linv, int n,
+                                                  int N, const double* __restrict__ Q, int R, int RC,
+                                                  double* __restrict__ c) {
+    typedef typename CT<C>::R T;
+    constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, FA = Tile<C>::FA, CB = Tile<C>::CB, LP = tile_pitch<C>();
+    constexpr int DA = NB / 16;                         // diagonal-block rows per thread
+    extern __shared__ __align__(16) unsigned char sraw[];
+    C* sL = reinterpret_cast<C*>(sraw);                 // [2][FT][LP]
+    C* sLi = sL + 2 * FT * LP;                          // [2][NB][NB]
+    C* sD = sLi + 2 * NB * NB;                          // [2][NB]
+    C* sY = sD + 2 * NB;                                // [n][RC] + 16 CB
+    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+    const int k = 1 + blockIdx.y, rc0 = blockIdx.x * RC, rc = min(RC, R - rc0), ncb = (rc + 15) / 16;
+    const C* F = fac + (long long)k * n * n;
+    const int nblk = (n + NB - 1) / NB;
+    const C* Lk = linv + (long long)k * nblk * NB * NB;
+    load_diag_data<C>(sLi, sD, Lk, F, n, 0, min(NB, n));
+    if (n > NB) load_l_tile<C>(sL, F, n, NB, 0, NB);
+    cp_async_commit();
+    for (long long t = tid; t < (long long)n * RC + 16 * CB; t += blockDim.x) {
+        const int i = (int)(t / RC), r = (int)(t % RC);
+        sY[t] = CT<C>::mk((i < n && r < rc) ? T(Q[(long long)i * R + rc0 + r]) : T(0), T(0));
+    }
+    double2 part[CB];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) part[b] = make_double2(0.0, 0.0);
+    int buf = 0;
+    for (int blk = 0; blk < nblk; ++blk) {
+        const int k0 = blk * NB, kb = min(NB, n - k0), k1 = k0 + kb, db = blk & 1;
+        const int ntile = (n - k1 + FT - 1) / FT;
+        cp_async_wait<0>();
+        __syncthreads();
+        if (blk + 1 < nblk)
+            load_diag_data<C>(sLi + (db ^ 1) * NB * NB, sD + (db ^ 1) * NB, Lk + (long long)(blk + 1) * NB * NB, F, n,
+                              k1, min(NB, n - k1));
+        cp_async_commit();
+        // y_b = L11^-1 y_b, then y_i^2/d_i into the binary64 sums
+        {
+            C acc[DA][CB];
+#pragma unroll
+            for (int a = 0; a < DA; ++a)
+#pragma unroll
+                for (int b = 0; b < CB; ++b) acc[a][b] = CT<C>::mk(T(0), T(0));
+            if (kb == NB) mma_rows<C, DA, true>(acc, sLi + db * NB * NB, NB, ty * DA, sY + (long long)k0 * RC, RC, kb);
+            else mma_rows<C, DA, false>(acc, sLi + db * NB * NB, NB, ty * DA, sY + (long long)k0 * RC, RC, kb);
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < DA; ++a) {
+                const int i = ty * DA + a;
+                if (i >= kb) continue;
+                const C di = sD[db * NB + i];
+#pragma unroll
+                for (int b = 0; b < CB; ++b) {
+                    const int r = tx + 16 * b;
+                    if (b >= ncb || r >= RC) continue;
+                    sY[(long long)(k0 + i) * RC + r] = acc[a][b];
+                    const C q = cdiv(cmul(acc[a][b], acc[a][b]), di);
+                    part[b].x += (double)q.x;
+                    part[b].y += (double)q.y;
+                }
+            }
+            __syncthreads();
+        }
+        // Y[k1:n] -= L[k1:n, k0:k1] y_b, FT rows per tile; the next tile (of
+        // this panel or the first of the next) streams in meanwhile
+        for (int t = 0; t < ntile; ++t) {
+            const int r0 = k1 + t * FT;
+            int nr0 = n, nk0 = k0, nkb = kb;
+            if (t + 1 < ntile) nr0 = r0 + FT;
+            else if (blk + 1 < nblk) {
+                nk0 = k1;
+                nkb = min(NB, n - k1);
+                nr0 = nk0 + nkb;
+            }
+            if (nr0 < n) load_l_tile<C>(sL + (buf ^ 1) * FT * LP, F, n, nr0, nk0, nkb);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            const int row0 = r0 + ty * FA;
+            if (row0 < n) {
+                C acc[FA][CB];
+#pragma unroll
+                for (int a = 0; a < FA; ++a)
+#pragma unroll
+                    for (int b = 0; b < CB; ++b) acc[a][b] = CT<C>::mk(T(0), T(0));
+                const C* Lt = sL + buf * FT * LP;
+                if (kb == NB) mma_rows<C, FA, true>(acc, Lt, LP, ty * FA, sY + (long long)k0 * RC, RC, kb);
+                else mma_rows<C, FA, false>(acc, Lt, LP, ty * FA, sY + (long long)k0 * RC, RC, kb);
+#pragma unroll
+                for (int a = 0; a < FA; ++a) {
+                    const int i = row0 + a;
+                    if (i >= n) continue;
+#pragma unroll
+                    for (int b = 0; b < CB; ++b) {
+                        const int r = tx + 16 * b;
+                        if (b < ncb && r < RC) sY[(long long)i * RC + r] = csub(sY[(long long)i * RC + r], acc[a][b]);
+                    }
+                }
+            }
+            __syncthreads();      // the buffer just read is refilled next
+            buf ^= 1;
+        }
+    }
+    cp_async_wait<0>();
+    // sum the 16 row groups of each column (reusing the start of sY)
+    double2* red = reinterpret_cast<double2*>(sY);
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < CB; ++b) red[ty * (16 * CB) + tx + 16 * b] = part[b];
+    __syncthreads();
+    for (int r = tid; r < rc; r += blockDim.x) {
+        double im = 0.0;
+        const int b = r / 16, x = r % 16;
+        for (int g = 0; g < 16; ++g) im += red[g * (16 * CB) + x + 16 * b].y;
+        c[(long long)(rc0 + r) * N + k] = -im / M_PI;
+        if (k == 1) c[(long long)(rc0 + r) * N] = 0.0;
     }
 }
 
@@ -385,11 +549,12 @@ __global__ void k_c64_to_c128(const float2* __restrict__ a, double2* __restrict_
 }  // namespace
 
 template <typename C>
-static void ldlt_steps(gw_ctx* ctx, const C* chi0, C* fac, int n, int N, double* piv, const char* const names[3]) {
+static void ldlt_steps(gw_ctx* ctx, const C* chi0, C* fac, int n, int N, C* linv, double* piv,
+                       const char* const names[3]) {
     constexpr int NB = Tile<C>::NB, TT = Tile<C>::T;
     klaunch(ctx, names[0], k_ldlt_init<C>, N, 256, 0, chi0, fac, n, piv);
     for (int k0 = 0; k0 < n; k0 += NB) {
-        klaunch(ctx, names[1], k_ldlt_panel<C>, N, 256, 0, fac, n, N, k0, piv, ctx->d_status);
+        klaunch(ctx, names[1], k_ldlt_panel<C>, N, 256, 0, fac, n, N, k0, linv, piv, ctx->d_status);
         const int m = n - std::min(n, k0 + NB);
         if (m == 0) break;
         const int nt = div_up(m, TT);
@@ -397,53 +562,47 @@ static void ldlt_steps(gw_ctx* ctx, const C* chi0, C* fac, int n, int N, double*
     }
 }
 
+size_t ldlt_linv_bytes(int n, int N, gw_precision prec) {
+    if (prec == GW_MIXED) return (size_t)N * div_up(n, Tile<float2>::NB) * Tile<float2>::NB * Tile<float2>::NB * sizeof(float2);
+    return (size_t)N * div_up(n, Tile<double2>::NB) * Tile<double2>::NB * Tile<double2>::NB * sizeof(double2);
+}
+
 void launch_ldlt(gw_ctx* ctx, gw_W* W) {
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
     if (c->prec == GW_MIXED) {
         static const char* const nm[3] = {"k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk"};
-        ldlt_steps<float2>(ctx, (const float2*)c->chi0_32, W->fac32, n, N, W->piv, nm);
+        ldlt_steps<float2>(ctx, (const float2*)c->chi0_32, W->fac32, n, N, (float2*)W->linv, W->piv, nm);
     } else {
         static const char* const nm[3] = {"k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk"};
-        ldlt_steps<double2>(ctx, (const double2*)c->chi0, W->fac, n, N, W->piv, nm);
+        ldlt_steps<double2>(ctx, (const double2*)c->chi0, W->fac, n, N, (double2*)W->linv, W->piv, nm);
     }
 }
 
 template <typename C>
-static void forms_steps(gw_ctx* ctx, const C* fac, int n, int N, const double* Q, int R, double* cout,
-                        const char* const names[2]) {
-    constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, FC = Tile<C>::FC;
-    C* Y = dalloc<C>(ctx, (size_t)(N - 1) * n * R);
-    double2* acc = nullptr;
-    try {
-        acc = dalloc<double2>(ctx, (size_t)(N - 1) * R);
-        for (int k0 = 0; k0 < n; k0 += NB) {
-            klaunch(ctx, names[0], k_forms_diag<C>, N - 1, 256, 0, fac, n, N, Q, R, Y, acc, cout, k0);
-            const int m = n - std::min(n, k0 + NB);
-            if (m == 0) break;
-            klaunch(ctx, names[1], k_forms_update<C>, dim3(div_up(m, FT), div_up(R, FC), N - 1), 256, 0, fac, n, Q,
-                    R, Y, k0);
-        }
-    } catch (...) {
-        ctx_free(ctx, Y);
-        ctx_free(ctx, acc);
-        throw;
-    }
-    ctx_free(ctx, Y);
-    ctx_free(ctx, acc);
+static void forms_run(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, const double* Q, int R, double* cout,
+                      const char* name) {
+    constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, CB = Tile<C>::CB, LP = tile_pitch<C>();
+    const size_t fixed = sizeof(C) * ((size_t)2 * FT * LP + 2 * NB * NB + 2 * NB + 16 * CB);
+    const size_t budget = 224 * 1024;
+    const size_t red = sizeof(double2) * 16 * 16 * CB;            // final reduction reuses Y
+    int rc_max = (int)std::min<size_t>(16 * CB, budget > fixed ? (budget - fixed) / (sizeof(C) * (size_t)n) : 0);
+    if (rc_max < 1) gw_throw(GW_ERR_INVALID_ARG, "n_sub too large for the forms kernel");
+    const int chunks = div_up(R, rc_max);
+    const int RC = div_up(R, chunks);
+    const size_t smem = fixed + std::max(sizeof(C) * (size_t)n * RC, red);
+    if (chunks > 65535 || N - 1 > 65535) gw_throw(GW_ERR_INVALID_ARG, "too many right-hand sides or frequencies");
+    allow_max_smem(k_forms<C>);
+    klaunch(ctx, name, k_forms<C>, dim3(chunks, N - 1), 256, smem, fac, linv, n, N, Q, R, RC, cout);
 }
 
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
-    if (N < 2) gw_throw(GW_ERR_GRID, "the forms need at least two frequencies");
-    if (c->prec == GW_MIXED) {
-        static const char* const nm[2] = {"k_forms32_diag", "k_forms32_update"};
-        forms_steps<float2>(ctx, W->fac32, n, N, Q, R, cout, nm);
-    } else {
-        static const char* const nm[2] = {"k_forms_diag", "k_forms_update"};
-        forms_steps<double2>(ctx, W->fac, n, N, Q, R, cout, nm);
-    }
+    if (c->prec == GW_MIXED)
+        forms_run<float2>(ctx, W->fac32, (const float2*)W->linv, n, N, Q, R, cout, "k_forms32");
+    else
+        forms_run<double2>(ctx, W->fac, (const double2*)W->linv, n, N, Q, R, cout, "k_forms");
 }
 
 void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work) {
