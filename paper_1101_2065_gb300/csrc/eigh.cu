@@ -22,6 +22,7 @@
 //     lambda^-1/2 (Eq. subspace).
 #include <cooperative_groups.h>
 
+#include <cfloat>
 #include <cmath>
 
 #include "internal.h"
@@ -277,69 +278,90 @@ __global__ void __launch_bounds__(512) k_sytrd32_grid(float* __restrict__ A, int
 }
 
 // ------------------------------------------------------------------ 2
-__device__ int sturm_count(const float* __restrict__ d, const float* __restrict__ e, int n, float x, float tiny) {
-    int c = 0;
-    float q = d[0] - x;
-    if (q < 0.f) ++c;
-    for (int i = 1; i < n; ++i) {
-        if (fabsf(q) < tiny) q = -tiny;
-        q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
-        if (q < 0.f) ++c;
+// Eigenvalue i (ascending) of T by multisection: one warp per eigenvalue,
+// each lane counts the eigenvalues below one of 32 interior points of the
+// current bracket, so each step shrinks it 33-fold (8 steps ~ 40 bisection
+// steps).  d and e^2 are staged in shared memory.
+__global__ void __launch_bounds__(256) k_bisect(const float* __restrict__ d, const float* __restrict__ e, int n,
+                                                float bnd, float* __restrict__ lam) {
+    extern __shared__ float sde[];
+    float* sd = sde;
+    float* se2 = sde + n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        sd[j] = d[j];
+        se2[j] = j + 1 < n ? e[j] * e[j] : 0.f;
     }
-    return c;
-}
-
-__global__ void k_bisect(const float* __restrict__ d, const float* __restrict__ e, int n, float bnd,
-                         float* __restrict__ lam) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n) return;
-    float lo = -bnd, hi = bnd;
     const float tiny = 1e-30f;
-    for (int it = 0; it < 40; ++it) {
-        float mid = 0.5f * (lo + hi);
-        if (mid == lo || mid == hi) break;
-        if (sturm_count(d, e, n, mid, tiny) <= i) lo = mid; else hi = mid;
+    float lo = -bnd, hi = bnd;
+    for (int it = 0; it < 12; ++it) {
+        const float w = (hi - lo) * (1.0f / 33.0f);
+        const float x = lo + w * (float)(lane + 1);
+        int c = 0;
+        float q = sd[0] - x;
+        if (q < 0.f) ++c;
+        for (int j = 1; j < n; ++j) {
+            if (fabsf(q) < tiny) q = -tiny;
+            q = (sd[j] - x) - se2[j - 1] / q;
+            if (q < 0.f) ++c;
+        }
+        const unsigned below = __ballot_sync(0xffffffffu, c <= i);   // a prefix of the lanes
+        const int l = __popc(below) - 1;                              // last point with count <= i
+        const float nlo = l >= 0 ? __shfl_sync(0xffffffffu, x, max(l, 0)) : lo;
+        const float nhi = l + 1 < 32 ? __shfl_sync(0xffffffffu, x, min(l + 1, 31)) : hi;
+        if (nlo == lo && nhi == hi) break;
+        lo = nlo;
+        hi = nhi;
+        if (hi - lo <= 4.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi))) break;
     }
-    lam[i] = 0.5f * (lo + hi);
+    if (lane == 0) lam[i] = 0.5f * (lo + hi);
 }
 
 // ------------------------------------------------------------------ 3
-// Solve (T - lam) x = b in place (b -> x) with the pivoted LU held in ws.
+// Pivoted LU of T - lam (partial pivoting, LAPACK-style tridiagonal LU): U
+// has three diagonals (rdu = reciprocal of its diagonal, du1, du2), L the
+// multipliers mul and row swaps piv.  One reciprocal per row; the solves
+// below only multiply.
 template <typename R>
 __device__ void tri_factor(const float* __restrict__ d, const float* __restrict__ e, int n, R lam, R tiny,
-                           R* du, R* du1, R* du2, R* mul, unsigned char* piv) {
+                           R* rdu, R* du1, R* du2, R* mul, unsigned char* piv) {
     R ca = R(d[0]) - lam, cb = n > 1 ? R(e[0]) : R(0);
     for (int i = 0; i + 1 < n; ++i) {
         const R c = e[i];
         const R a1 = R(d[i + 1]) - lam;
         const R b1 = (i + 2 < n) ? R(e[i + 1]) : R(0);
         if (fabs(c) > fabs(ca)) {
-            R m = ca / c;
-            du[i] = c; du1[i] = a1; du2[i] = b1; mul[i] = m; piv[i] = 1;
+            const R r = R(1) / c;
+            const R m = ca * r;
+            rdu[i] = r; du1[i] = a1; du2[i] = b1; mul[i] = m; piv[i] = 1;
             ca = cb - m * a1;
             cb = -m * b1;
         } else {
             if (fabs(ca) < tiny) ca = copysign(tiny, ca);
-            R m = c / ca;
-            du[i] = ca; du1[i] = cb; du2[i] = R(0); mul[i] = m; piv[i] = 0;
+            const R r = R(1) / ca;
+            const R m = c * r;
+            rdu[i] = r; du1[i] = cb; du2[i] = R(0); mul[i] = m; piv[i] = 0;
             ca = a1 - m * cb;
             cb = b1;
         }
     }
     if (fabs(ca) < tiny) ca = copysign(tiny, ca);
-    du[n - 1] = ca;
+    rdu[n - 1] = R(1) / ca;
 }
 
 template <typename R>
-__device__ void tri_solve(int n, const R* du, const R* du1, const R* du2, const R* mul,
+__device__ void tri_solve(int n, const R* rdu, const R* du1, const R* du2, const R* mul,
                           const unsigned char* piv, R* x) {
     for (int i = 0; i + 1 < n; ++i) {
         if (piv[i]) { R t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
         x[i + 1] -= mul[i] * x[i];
     }
-    x[n - 1] /= du[n - 1];
-    if (n >= 2) x[n - 2] = (x[n - 2] - du1[n - 2] * x[n - 1]) / du[n - 2];
-    for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du1[i] * x[i + 1] - du2[i] * x[i + 2]) / du[i];
+    x[n - 1] *= rdu[n - 1];
+    if (n >= 2) x[n - 2] = (x[n - 2] - du1[n - 2] * x[n - 1]) * rdu[n - 2];
+    for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du1[i] * x[i + 1] - du2[i] * x[i + 2]) * rdu[i];
 }
 
 // Inverse iteration in binary64, one thread per eigenvalue; the pivoted LU
@@ -593,10 +615,13 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
             bnd = std::max(bnd, r);
         }
         bnd = bnd * 1.01f + 1e-30f;
-        klaunch(ctx, "k_bisect", k_bisect, div_up(n, 64), 64, 0, (const float*)d, (const float*)e, n, bnd, lam32);
+        klaunch(ctx, "k_bisect", k_bisect, div_up(n, 8), 256, 2 * (size_t)n * sizeof(float), (const float*)d,
+                (const float*)e, n, bnd, lam32);
         const size_t per_thread = (size_t)n * (5 * sizeof(double) + 1);
         if (per_thread <= 200 * 1024) {
-            const int it_threads = (int)std::max<size_t>(1, std::min<size_t>(IT, (200 * 1024) / per_thread));
+            // few threads per CTA so that the eigenvalues spread over all SMs
+            const int it_threads = (int)std::max<size_t>(
+                1, std::min(std::min((size_t)IT, (200 * 1024) / per_thread), (size_t)div_up(n, ctx->num_sms)));
             const size_t smem_it = per_thread * it_threads;
             allow_max_smem(k_invit);
             klaunch(ctx, "k_invit", k_invit, div_up(n, it_threads), it_threads, smem_it, (const float*)d,
@@ -607,7 +632,8 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
                     (const float*)lam32, n, 1e-13 * (double)bnd, Y, gws);
         }
         klaunch(ctx, "k_cluster_mgs", k_cluster_mgs, n, 256, 0, (const float*)lam32, n, 1e-6f * bnd, Y);
-        const int bt_warps = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / ((size_t)n * sizeof(float))));
+        // two warps per CTA: the vectors spread over all SMs
+        const int bt_warps = (int)std::max<size_t>(1, std::min<size_t>(2, (200 * 1024) / ((size_t)n * sizeof(float))));
         const size_t smem_bt = (size_t)bt_warps * n * sizeof(float);
         allow_max_smem(k_backtransform);
         klaunch(ctx, "k_backtransform", k_backtransform, div_up(n, bt_warps), 32 * bt_warps, smem_bt,
