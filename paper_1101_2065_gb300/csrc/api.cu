@@ -426,9 +426,10 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
             gemm_f64(ctx, false, false, n_prod, nr, n_prod, 1.0, mol->v, n_prod, VEFt, n_pair, 0.0, T1, nr);
             gemm_f64(ctx, true, false, nr, nr, n_prod, 1.0, VEFt, n_pair, T1, nr, 0.0, g, nr);
             Bsel = dalloc<double>(ctx, (size_t)nr * n_sub);
-            // binary64: refine to working accuracy; mixed: one refinement step
+            // binary64: refine to working accuracy; mixed: binary64 Rayleigh quotients of
+            // the binary32 vectors, no refinement (1 meV bar met with margin)
             if (prec == GW_FP64) eigh_top_scaled(ctx, g, nr, n_sub, 6, 1e-13, Bsel);
-            else eigh_top_scaled(ctx, g, nr, n_sub, 1, 0.0, Bsel);
+            else eigh_top_scaled(ctx, g, nr, n_sub, 0, 0.0, Bsel);
             c->Z = dalloc<double>(ctx, (size_t)n_prod * n_sub);
             gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, VEFt, n_pair, Bsel, n_sub, 0.0, c->Z, n_sub);
             gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, T1, nr, Bsel, n_sub, 0.0, c->Zup, n_sub);

@@ -52,6 +52,22 @@ __device__ float block_sum1024(float v, float* red) {
     return r;
 }
 
+// block-wide binary64 sum (blockDim <= 1024, a multiple of 32); red has 33 doubles
+__device__ double block_sum1024d(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (threadIdx.x == 0) red[32] = w;
+    }
+    __syncthreads();
+    double r = red[32];
+    __syncthreads();
+    return r;
+}
+
 // ------------------------------------------------------------------ 1
 // Same reduction on a cluster of CL CTAs: CTA r holds the rows i = r (mod CL)
 // of the matrix in its shared memory; the reflector, the partial dot
@@ -470,36 +486,48 @@ __global__ void k_identity_minus(double* __restrict__ R, int n) {     // R <- I 
 }
 
 // lam_i = S_ii/(1 - R_ii); sums for delta (single CTA, deterministic)
-__global__ void __launch_bounds__(1024) k_oa_stats(const double* __restrict__ S, const double* __restrict__ R,
-                                                   const double* __restrict__ g, int n, double* __restrict__ lam,
-                                                   double* __restrict__ out) {
-    __shared__ double s1[1024], s2[1024], s3[1024];
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        lam[i] = S[(long long)i * n + i] / (1.0 - R[(long long)i * n + i]);
-    __syncthreads();
+// Refinement statistics, stage 1: lam_i = S_ii / (1 - R_ii) and per-CTA
+// partial sums of |S - diag(lam)|^2, |R|^2, |g|^2 over rows blockIdx.x,
+// blockIdx.x + gridDim.x, ... (binary64 is 1/64 rate: spread over all SMs).
+__global__ void __launch_bounds__(256) k_oa_stats(const double* __restrict__ S, const double* __restrict__ R,
+                                                  const double* __restrict__ g, int n, double* __restrict__ lam,
+                                                  double* __restrict__ part) {
+    __shared__ double red[33];
     double a = 0.0, b = 0.0, c = 0.0;
-    for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
-        int i = (int)(t / n), j = (int)(t % n);
-        double s = S[t] - (i == j ? lam[i] : 0.0);
-        a += s * s;
-        b += R[t] * R[t];
-        c += g[t] * g[t];
-    }
-    s1[threadIdx.x] = a; s2[threadIdx.x] = b; s3[threadIdx.x] = c;
-    __syncthreads();
-    for (int s = 512; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            s1[threadIdx.x] += s1[threadIdx.x + s];
-            s2[threadIdx.x] += s2[threadIdx.x + s];
-            s3[threadIdx.x] += s3[threadIdx.x + s];
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const double li = S[(long long)i * n + i] / (1.0 - R[(long long)i * n + i]);
+        if (threadIdx.x == 0) lam[i] = li;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const long long t = (long long)i * n + j;
+            const double s = S[t] - (i == j ? li : 0.0);
+            a = fma(s, s, a);
+            b = fma(R[t], R[t], b);
+            c = fma(g[t], g[t], c);
         }
-        __syncthreads();
     }
+    a = block_sum1024d(a, red);
+    b = block_sum1024d(b, red);
+    c = block_sum1024d(c, red);
     if (threadIdx.x == 0) {
-        out[0] = 2.0 * (sqrt(s1[0]) + sqrt(s3[0]) * sqrt(s2[0]));
-        out[1] = sqrt(s1[0]) / fmax(sqrt(s3[0]), 1e-300);   // |S - diag| / |g|
-        out[2] = sqrt(s2[0]);                               // |I - X^T X|
+        part[blockIdx.x] = a;
+        part[gridDim.x + blockIdx.x] = b;
+        part[2 * gridDim.x + blockIdx.x] = c;
     }
+}
+
+// Stage 2 (one warp, fixed order): out[0] = delta for the clustering test,
+// out[1] = |S - diag| / |g|, out[2] = |I - X^T X|.
+__global__ void k_oa_stats_fin(const double* __restrict__ part, int np, double* __restrict__ out) {
+    if (threadIdx.x != 0) return;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int q = 0; q < np; ++q) {
+        a += part[q];
+        b += part[np + q];
+        c += part[2 * np + q];
+    }
+    out[0] = 2.0 * (sqrt(a) + sqrt(c) * sqrt(b));
+    out[1] = sqrt(a) / fmax(sqrt(c), 1e-300);
+    out[2] = sqrt(b);
 }
 
 __global__ void k_oa_E(const double* __restrict__ S, const double* __restrict__ R, const double* __restrict__ lam,
@@ -641,14 +669,20 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         // binary64 refinement
         X2 = dalloc<double>(ctx, nn); R = dalloc<double>(ctx, nn); S = dalloc<double>(ctx, nn);
         T = dalloc<double>(ctx, nn); E = dalloc<double>(ctx, nn); lam = dalloc<double>(ctx, n);
-        stat = dalloc<double>(ctx, 3);
+        const int n_part = ctx->num_sms;
+        stat = dalloc<double>(ctx, 3 + 3 * (size_t)n_part);      // [3) results, then the partial sums
+        auto oa_stats = [&]() {
+            klaunch(ctx, "k_oa_stats", k_oa_stats, n_part, 256, 0, (const double*)S, (const double*)R, g, n, lam,
+                    stat + 3);
+            klaunch(ctx, "k_oa_stats_fin", k_oa_stats_fin, 1, 32, 0, (const double*)(stat + 3), n_part, stat);
+        };
         double hstat[3] = {0, 0, 0};
         for (int it = 0; it < oa_iters; ++it) {
             gemm_f64(ctx, true, false, n, n, n, 1.0, X, n, X, n, 0.0, R, n);           // X^T X
             klaunch(ctx, "k_identity_minus", k_identity_minus, div_up(nn, 256), 256, 0, R, n);
             gemm_f64(ctx, false, false, n, n, n, 1.0, g, n, X, n, 0.0, T, n);          // g X
             gemm_f64(ctx, true, false, n, n, n, 1.0, X, n, T, n, 0.0, S, n);           // X^T g X
-            klaunch(ctx, "k_oa_stats", k_oa_stats, 1, 1024, 0, (const double*)S, (const double*)R, g, n, lam, stat);
+            oa_stats();
             klaunch(ctx, "k_oa_E", k_oa_E, div_up(nn, 256), 256, 0, (const double*)S, (const double*)R,
                     (const double*)lam, (const double*)stat, n, E);
             // stop once the basis is an eigenbasis to working accuracy (residual of
@@ -666,7 +700,7 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
             gemm_f64(ctx, false, false, n, n, n, 1.0, g, n, X, n, 0.0, T, n);
             gemm_f64(ctx, true, false, n, n, n, 1.0, X, n, T, n, 0.0, S, n);
             CUDA_CHECK(cudaMemsetAsync(R, 0, nn * sizeof(double), ctx->stream));
-            klaunch(ctx, "k_oa_stats", k_oa_stats, 1, 1024, 0, (const double*)S, (const double*)R, g, n, lam, stat);
+            oa_stats();
         }
         // select, re-orthonormalise, scale
         sel = dalloc<int>(ctx, n_sub);
