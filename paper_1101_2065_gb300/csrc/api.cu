@@ -354,6 +354,7 @@ static void chi0_release(gw_chi0* c) {
     gw_ctx* x = c->ctx;
     ctx_free(x, c->pE); ctx_free(x, c->pF); ctx_free(x, c->pBin); ctx_free(x, c->pDelta);
     ctx_free(x, c->pFrac); ctx_free(x, c->seg); ctx_free(x, c->Z); ctx_free(x, c->Zup);
+    ctx_free(x, c->Xr); ctx_free(x, c->Bsel);
     ctx_free(x, c->Ut); ctx_free(x, c->tw); ctx_free(x, c->C1); ctx_free(x, c->C2);
     ctx_free(x, c->chi0); ctx_free(x, c->Ut32); ctx_free(x, c->tw32); ctx_free(x, c->C1_32);
     ctx_free(x, c->C2_32); ctx_free(x, c->chi0_32);
@@ -430,9 +431,13 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
             // the binary32 vectors, no refinement (1 meV bar met with margin)
             if (prec == GW_FP64) eigh_top_scaled(ctx, g, nr, n_sub, 6, 1e-13, Bsel);
             else eigh_top_scaled(ctx, g, nr, n_sub, 0, 0.0, Bsel);
-            c->Z = dalloc<double>(ctx, (size_t)n_prod * n_sub);
-            gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, VEFt, n_pair, Bsel, n_sub, 0.0, c->Z, n_sub);
             gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, T1, nr, Bsel, n_sub, 0.0, c->Zup, n_sub);
+            // Z = X_r Bsel is only read back: keep its factors, form it on request
+            c->Xr = dalloc<double>(ctx, (size_t)n_prod * nr);
+            CUDA_CHECK(cudaMemcpy2DAsync(c->Xr, sizeof(double) * nr, VEFt, sizeof(double) * n_pair, sizeof(double) * nr,
+                                         n_prod, cudaMemcpyDeviceToDevice, ctx->stream));
+            c->Bsel = Bsel;
+            Bsel = nullptr;
         }
         // a2: U^T = Zup^T V^EF  -> [n_sub][n_pair]
         c->Ut = dalloc<double>(ctx, (size_t)n_sub * n_pair);
@@ -682,7 +687,13 @@ extern "C" gw_status gw_chi0_copy_basis(gw_ctx* ctx, const gw_chi0* c, double* Z
     CUDA_CHECK(cudaSetDevice(ctx->device));
     size_t n = (size_t)c->mol->n_prod * c->n_sub;
     if (Z) {
-        REQUIRE(c->Z, "Z is not formed for the Cholesky (uncompressed) basis; read Zup");
+        REQUIRE(c->Z || c->Bsel, "Z is not formed for the Cholesky (uncompressed) basis; read Zup");
+        if (!c->Z) {
+            gw_chi0* cm = const_cast<gw_chi0*>(c);      // cached product, same value on every read
+            cm->Z = dalloc<double>(ctx, n);
+            gemm_f64(ctx, false, false, c->mol->n_prod, c->n_sub, c->n_rank, 1.0, c->Xr, c->n_rank, c->Bsel, c->n_sub,
+                     0.0, cm->Z, c->n_sub);
+        }
         download(ctx, Z, c->Z, n);
     }
     if (Zup) download(ctx, Zup, c->Zup, n);

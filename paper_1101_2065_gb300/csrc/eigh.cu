@@ -569,6 +569,36 @@ __global__ void k_ns_coeff(double* __restrict__ G, int m) {          // G <- (3 
     G[t] = 0.5 * ((i == j ? 3.0 : 0.0) - G[t]);
 }
 
+// lam[k] = B[:, k]^T T[:, k] (B, T row-major n x n_sub), one CTA per column
+__global__ void __launch_bounds__(256) k_rayleigh_cols(const double* __restrict__ B, const double* __restrict__ T,
+                                                       int n, int n_sub, double* __restrict__ lam) {
+    __shared__ double red[33];
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(B[(long long)i * n_sub + k], T[(long long)i * n_sub + k], s);
+    s = block_sum1024d(s, red);
+    if (threadIdx.x == 0) lam[k] = s;
+}
+// B[:, k] /= sqrt(lam[k]); flags a rank-deficient selection
+__global__ void k_scale_cols_by(double* __restrict__ B, int n, int n_sub, const double* __restrict__ lam,
+                                int* status) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t == 0) {
+        double lmax = lam[0], lmin = lam[0];
+        for (int k = 1; k < n_sub; ++k) {
+            lmax = fmax(lmax, lam[k]);
+            lmin = fmin(lmin, lam[k]);
+        }
+        if (!(lmin >= 1e-12 * lmax) || !(lmax > 0.0)) atomicOr(status, ST_RANK);
+    }
+    if (t >= (long long)n * n_sub) return;
+    double l = lam[(int)(t % n_sub)];
+    B[t] = l > 0.0 ? B[t] / sqrt(l) : 0.0;
+}
+__global__ void k_top_indices(int n, int n_sub, int* __restrict__ sel) {   // ascending order -> top n_sub, descending
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_sub) sel[k] = n - 1 - k;
+}
 __global__ void k_scale_cols(double* __restrict__ B, int n, int n_sub, const double* __restrict__ lam,
                              const int* __restrict__ sel, int* status) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -667,8 +697,11 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         klaunch(ctx, "k_backtransform", k_backtransform, div_up(n, bt_warps), 32 * bt_warps, smem_bt,
                 (const float*)A32, (const float*)tau, n, (const float*)Y, X);
         // binary64 refinement
-        X2 = dalloc<double>(ctx, nn); R = dalloc<double>(ctx, nn); S = dalloc<double>(ctx, nn);
-        T = dalloc<double>(ctx, nn); E = dalloc<double>(ctx, nn); lam = dalloc<double>(ctx, n);
+        if (oa_iters > 0) {
+            X2 = dalloc<double>(ctx, nn); R = dalloc<double>(ctx, nn); S = dalloc<double>(ctx, nn);
+            E = dalloc<double>(ctx, nn);
+        }
+        T = dalloc<double>(ctx, nn); lam = dalloc<double>(ctx, n);
         const int n_part = ctx->num_sms;
         stat = dalloc<double>(ctx, 3 + 3 * (size_t)n_part);      // [3) results, then the partial sums
         auto oa_stats = [&]() {
@@ -695,25 +728,32 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
             std::swap(X, X2);
             if (done) break;
         }
-        if (oa_iters == 0) {
-            // Rayleigh quotients of the binary32 vectors
-            gemm_f64(ctx, false, false, n, n, n, 1.0, g, n, X, n, 0.0, T, n);
-            gemm_f64(ctx, true, false, n, n, n, 1.0, X, n, T, n, 0.0, S, n);
-            CUDA_CHECK(cudaMemsetAsync(R, 0, nn * sizeof(double), ctx->stream));
-            oa_stats();
-        }
-        // select, re-orthonormalise, scale
         sel = dalloc<int>(ctx, n_sub);
-        klaunch(ctx, "k_rank_desc_ld", k_rank_desc_ld, div_up(n, 256), 256, 0, (const double*)lam, n, n_sub, sel);
         Bt = dalloc<double>(ctx, (size_t)n * n_sub);
         G = dalloc<double>(ctx, (size_t)n_sub * n_sub);
+        if (oa_iters == 0) {
+            // no refinement: the top n_sub of the binary32 eigenvalues (ascending
+            // from the bisection), re-orthonormalised, scaled by the binary64
+            // Rayleigh quotients of the re-orthonormalised vectors
+            klaunch(ctx, "k_top_indices", k_top_indices, div_up(n_sub, 256), 256, 0, n, n_sub, sel);
+        } else {
+            klaunch(ctx, "k_rank_desc_ld", k_rank_desc_ld, div_up(n, 256), 256, 0, (const double*)lam, n, n_sub, sel);
+        }
         klaunch(ctx, "k_gather_cols", k_gather_cols, div_up((long long)n * n_sub, 256), 256, 0, (const double*)X, n,
                 n_sub, (const int*)sel, Bt);
         gemm_f64(ctx, true, false, n_sub, n_sub, n, 1.0, Bt, n_sub, Bt, n_sub, 0.0, G, n_sub);
         klaunch(ctx, "k_ns_coeff", k_ns_coeff, div_up((long long)n_sub * n_sub, 256), 256, 0, G, n_sub);
         gemm_f64(ctx, false, false, n, n_sub, n_sub, 1.0, Bt, n_sub, G, n_sub, 0.0, B, n_sub);
-        klaunch(ctx, "k_scale_cols", k_scale_cols, div_up((long long)n * n_sub, 256), 256, 0, B, n, n_sub,
-                (const double*)lam, (const int*)sel, ctx->d_status);
+        if (oa_iters == 0) {
+            gemm_f64(ctx, false, false, n, n_sub, n, 1.0, g, n, B, n_sub, 0.0, T, n_sub);     // g B
+            klaunch(ctx, "k_rayleigh_cols", k_rayleigh_cols, n_sub, 256, 0, (const double*)B, (const double*)T, n,
+                    n_sub, lam);
+            klaunch(ctx, "k_scale_cols_by", k_scale_cols_by, div_up((long long)n * n_sub, 256), 256, 0, B, n, n_sub,
+                    (const double*)lam, ctx->d_status);
+        } else {
+            klaunch(ctx, "k_scale_cols", k_scale_cols, div_up((long long)n * n_sub, 256), 256, 0, B, n, n_sub,
+                    (const double*)lam, (const int*)sel, ctx->d_status);
+        }
     } catch (...) {
         release();
         throw;

@@ -121,7 +121,9 @@ struct gw_chi0 {
     int* pE = nullptr; int* pF = nullptr; int* pBin = nullptr;
     double* pDelta = nullptr; double* pFrac = nullptr;
     int* seg = nullptr;              // [nb_bins+1]
-    double* Z = nullptr;             // [n_prod*n_sub] (nullptr for Cholesky basis)
+    double* Z = nullptr;             // [n_prod*n_sub] (nullptr for Cholesky basis; formed on first read-back)
+    double* Xr = nullptr;            // [n_prod*n_rank] and [n_rank*n_sub]: Z = Xr Bsel, kept for the read-back
+    double* Bsel = nullptr;
     double* Zup = nullptr;           // [n_prod*n_sub]
     double* Ut = nullptr;            // [n_sub*n_pair] U transposed
     double2* tw = nullptr;           // [L/2] exp(-2 pi i k/L)
