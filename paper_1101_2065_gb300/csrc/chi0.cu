@@ -19,27 +19,125 @@
 
 namespace {
 
-// Radix-2 Stockham FFT in shared memory (natural order in and out).
-// Returns the buffer holding the result (a or b).  All threads of the CTA
-// must call it.
+// Mixed-radix Stockham FFT in shared memory (natural order in and out):
+// one radix-2 or radix-4 pass first (no twiddles), then radix-8 passes.
+// tws = exp(-2 pi i t / L), t < L/2, in shared memory.  The inverse uses
+// conjugate twiddles and rotations (unnormalised).  Returns the buffer
+// holding the result (a or b).  All threads of the CTA must call it.
 template <typename C>
-__device__ C* fft_smem(C* a, C* b, int L, int logL, const C* __restrict__ tw, bool inverse) {
-    const int half = L >> 1;
-    int Ns = 1;
-    for (int t = 0; t < logL; ++t, Ns <<= 1) {
-        const int stride = half / Ns;   // twiddle index step: L/(2 Ns)
-        for (int j = threadIdx.x; j < half; j += blockDim.x) {
-            int k = j & (Ns - 1);
-            C w = tw[k * stride];
-            if (inverse) w.y = -w.y;
-            C u0 = a[j];
-            C u1 = cmul(a[j + half], w);
-            int idx = ((j - k) << 1) + k;
-            b[idx] = cadd(u0, u1);
-            b[idx + Ns] = csub(u0, u1);
+__device__ __forceinline__ C tw_at(const C* tws, int t, int L) {     // exp(-2 pi i t / L), 0 <= t < L
+    const int h = L >> 1;
+    if (t < h) return tws[t];
+    C w = tws[t - h];
+    w.x = -w.x;
+    w.y = -w.y;
+    return w;
+}
+template <typename C, bool INV>
+__device__ __forceinline__ C rot_mi(C z) {        // z * (-i) forward, z * (+i) inverse
+    C r;
+    if (INV) { r.x = -z.y; r.y = z.x; }
+    else { r.x = z.y; r.y = -z.x; }
+    return r;
+}
+template <typename C, bool INV>
+__device__ __forceinline__ void dft4(C& z0, C& z1, C& z2, C& z3) {
+    const C c0 = cadd(z0, z2), c1 = csub(z0, z2), c2 = cadd(z1, z3), c3 = rot_mi<C, INV>(csub(z1, z3));
+    z0 = cadd(c0, c2);
+    z2 = csub(c0, c2);
+    z1 = cadd(c1, c3);
+    z3 = csub(c1, c3);
+}
+template <typename C, bool INV>
+__device__ __forceinline__ void dft8(C (&x)[8]) {
+    typedef decltype(x[0].x) R;
+    const R s = R(0.70710678118654752440);
+    C a[4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        a[r] = cadd(x[r], x[r + 4]);
+        b[r] = csub(x[r], x[r + 4]);
+    }
+    // b_r *= w8^r (forward w8 = exp(-i pi/4))
+    {
+        C t = b[1];
+        if (INV) { b[1].x = s * (t.x - t.y); b[1].y = s * (t.x + t.y); }
+        else { b[1].x = s * (t.x + t.y); b[1].y = s * (t.y - t.x); }
+        b[2] = rot_mi<C, INV>(b[2]);
+        t = b[3];
+        if (INV) { b[3].x = -s * (t.x + t.y); b[3].y = s * (t.x - t.y); }
+        else { b[3].x = s * (t.y - t.x); b[3].y = -s * (t.x + t.y); }
+    }
+    dft4<C, INV>(a[0], a[1], a[2], a[3]);
+    dft4<C, INV>(b[0], b[1], b[2], b[3]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        x[2 * q] = a[q];
+        x[2 * q + 1] = b[q];
+    }
+}
+
+template <typename C, int RAD, bool INV>
+__device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __restrict__ b, int L, int Ns,
+                                              const C* tws) {
+    const int nb = L / RAD;
+    const int c = L / (RAD * Ns);           // twiddle exponent step
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const int k = j & (Ns - 1);
+        C x[RAD];
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) x[r] = a[j + r * nb];
+        if (Ns > 1) {
+            if constexpr (RAD == 8) {
+                C w1 = tw_at(tws, k * c, L), w2 = tw_at(tws, 2 * k * c, L), w4 = tw_at(tws, 4 * k * c, L);
+                if (INV) { w1.y = -w1.y; w2.y = -w2.y; w4.y = -w4.y; }
+                const C w3 = cmul(w1, w2), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+                x[1] = cmul(x[1], w1); x[2] = cmul(x[2], w2); x[3] = cmul(x[3], w3);
+                x[4] = cmul(x[4], w4); x[5] = cmul(x[5], w5); x[6] = cmul(x[6], w6); x[7] = cmul(x[7], w7);
+            } else {
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) {
+                    C w = tw_at(tws, r * k * c, L);
+                    if (INV) w.y = -w.y;
+                    x[r] = cmul(x[r], w);
+                }
+            }
         }
+        if constexpr (RAD == 8) {
+            dft8<C, INV>(x);
+        } else if constexpr (RAD == 4) {
+            dft4<C, INV>(x[0], x[1], x[2], x[3]);
+        } else {
+            const C u0 = x[0];
+            x[0] = cadd(u0, x[1]);
+            x[1] = csub(u0, x[1]);
+        }
+        const int base = (j - k) * RAD + k;
+#pragma unroll
+        for (int q = 0; q < RAD; ++q) b[base + q * Ns] = x[q];
+    }
+}
+
+template <typename C>
+__device__ C* fft_smem(C* a, C* b, int L, int logL, const C* tws, bool inverse) {
+    int Ns = 1;
+    const int rem = logL % 3;
+    if (rem == 1) {
+        if (inverse) stockham_pass<C, 2, true>(a, b, L, Ns, tws); else stockham_pass<C, 2, false>(a, b, L, Ns, tws);
+        Ns *= 2;
+    } else if (rem == 2) {
+        if (inverse) stockham_pass<C, 4, true>(a, b, L, Ns, tws); else stockham_pass<C, 4, false>(a, b, L, Ns, tws);
+        Ns *= 4;
+    }
+    if (rem) {
         __syncthreads();
-        C* tmp = a; a = b; b = tmp;
+        C* t = a; a = b; b = t;
+    }
+    for (int s = 0; s < logL / 3; ++s) {
+        if (inverse) stockham_pass<C, 8, true>(a, b, L, Ns, tws); else stockham_pass<C, 8, false>(a, b, L, Ns, tws);
+        Ns *= 8;
+        __syncthreads();
+        C* t = a; a = b; b = t;
     }
     return a;
 }
@@ -74,6 +172,8 @@ __global__ void k_kernel_spectra(const double2* __restrict__ tw, int N, int logL
     const int L = 2 * N;
     double2* a = sbuf;
     double2* b = sbuf + L;
+    double2* tws = sbuf + 2 * L;
+    for (int t = threadIdx.x; t < L / 2; t += blockDim.x) tws[t] = tw[t];
     for (int d = threadIdx.x; d < L; d += blockDim.x) {
         double2 v = make_double2(0.0, 0.0);
         if (blockIdx.x == 0) {
@@ -85,7 +185,7 @@ __global__ void k_kernel_spectra(const double2* __restrict__ tw, int N, int logL
         a[d] = v;
     }
     __syncthreads();
-    double2* r = fft_smem(a, b, L, logL, tw, false);
+    double2* r = fft_smem(a, b, L, logL, (const double2*)tws, false);
     double2* out = blockIdx.x == 0 ? C1 : C2;
     for (int d = threadIdx.x; d < L; d += blockDim.x) out[d] = r[d];
 }
@@ -137,6 +237,8 @@ __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __r
     C* B0 = sbuf;
     C* B1 = sbuf + L;
     C* B2 = sbuf + 2 * L;
+    C* tws = sbuf + 3 * L;                 // exp(-2 pi i t / L), t < L/2
+    for (int t = threadIdx.x; t < L / 2; t += blockDim.x) tws[t] = tw[t];
     for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
         int m1, n1, m2, n2;
         tri_index(2 * g, m1, n1);
@@ -150,7 +252,7 @@ __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __r
             B0[j_lo + b] = Real<C>::make(a1, two ? a2 : R(0));
         }
         __syncthreads();
-        C* Zb = fft_smem(B0, B1, L, logL, tw, false);
+        C* Zb = fft_smem(B0, B1, L, logL, (const C*)tws, false);
         C* Y1 = (Zb == B0) ? B1 : B0;
         // split the two real transforms and apply the kernel spectra
         for (int m = threadIdx.x; m <= N; m += blockDim.x) {
@@ -170,9 +272,9 @@ __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __r
             if (mr != m) { Y1[mr] = y1r; Zb[mr] = y2r; }
         }
         __syncthreads();
-        C* r1 = fft_smem(Y1, B2, L, logL, tw, true);
+        C* r1 = fft_smem(Y1, B2, L, logL, (const C*)tws, true);
         C* free1 = (r1 == Y1) ? B2 : Y1;
-        C* r2 = fft_smem(Zb, free1, L, logL, tw, true);
+        C* r2 = fft_smem(Zb, free1, L, logL, (const C*)tws, true);
         const long long o1 = (long long)m1 * n_sub + n1;
         const long long o2 = (long long)m2 * n_sub + n2;
         for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -219,7 +321,7 @@ void launch_fft_tables(gw_ctx* ctx, gw_chi0* c) {
     c->C1 = dalloc<double2>(ctx, L);
     c->C2 = dalloc<double2>(ctx, L);
     klaunch(ctx, "k_twiddles", k_twiddles, div_up(L / 2, 256), 256, 0, c->tw, L);
-    size_t smem = 2 * (size_t)L * sizeof(double2);
+    size_t smem = (2 * (size_t)L + L / 2) * sizeof(double2);
     allow_max_smem(k_kernel_spectra);
     klaunch(ctx, "k_kernel_spectra", k_kernel_spectra, 2, 256, smem, c->tw, N, c->logL, c->grid.d_omega, c->grid.eta, c->C1, c->C2);
 }
@@ -228,7 +330,7 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
     const int L = c->L, N = c->grid.n_omega, n = c->n_sub;
     const bool f32 = c->prec == GW_MIXED;
     const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
-    size_t smem = 3 * (size_t)L * csz;
+    size_t smem = (3 * (size_t)L + L / 2) * csz;
     if (smem > 227 * 1024) gw_throw(GW_ERR_INVALID_ARG, "n_omega too large for the FFT kernel");
     int per_sm = std::max(1, (int)((228 * 1024) / (smem + 1024)));
     long long n_grp = ((long long)n * (n + 1) / 2 + 1) / 2;
