@@ -27,13 +27,12 @@
 namespace {
 
 // Panel width NB; trailing-update tile T x T with A x A complex outputs per
-// thread; the forms stream L in tiles of FT = 16 FA rows and give each
-// thread FA rows x CB right-hand sides (RC <= 16 CB per CTA).  binary64 is
-// issue-bound (1/64 of the binary32 rate): small tiles waste less on the
-// triangle and keep the panel row in registers.
+// thread; the forms stream L in tiles of FT rows.  binary64 is issue-bound
+// (1/64 of the binary32 rate): small tiles waste less on the triangle and
+// keep the panel row in registers.
 template <typename C> struct Tile;
-template <> struct Tile<double2> { static constexpr int NB = 16, T = 32, A = 2, FT = 32, FA = 2, CB = 2; };
-template <> struct Tile<float2> { static constexpr int NB = 32, T = 64, A = 4, FT = 64, FA = 4, CB = 5; };
+template <> struct Tile<double2> { static constexpr int NB = 16, T = 32, A = 2, FT = 32; };
+template <> struct Tile<float2> { static constexpr int NB = 32, T = 64, A = 4, FT = 64; };
 
 // shared-memory row pitch of an NB-wide tile (a multiple of 16 bytes, for cp.async)
 template <typename C> __host__ __device__ constexpr int tile_pitch() {
@@ -361,72 +360,70 @@ __device__ __forceinline__ void load_pair(const double2* p, double2& a, double2&
     b = p[1];
 }
 
-// acc[a][b] += sum_p A[(arow + a) lda + p] Yb[p RC + tx + 16 b], p < kb.
-// Columns past RC read the next row or the zero padding after Y (finite
-// values, never stored); no per-column branch, so the accumulator chains
-// interleave.
-template <typename C, int RA, bool FULL>
-__device__ __forceinline__ void mma_rows(C (&acc)[RA][Tile<C>::CB], const C* __restrict__ A, int lda, int arow,
-                                         const C* __restrict__ Yb, int RC, int kb) {
+// c[r*N + k] = -(1/pi) Im sum_i y_i^2/d_i, y = L_k^-1 q_r: right-hand sides
+// [chunk*RC, chunk*RC + RC) of frequency k = 1 + blockIdx.y, chunk = blockIdx.x.
+// Thread (g, c), g < FG, c < RC (blockDim = FG*RC) owns column c: per panel
+// it keeps y_b[:, c] (NB values) in registers and walks the rows g, g + FG,
+// ... with the L rows read from shared memory (the same row for all threads
+// of a group).  Shared memory: two L tiles [FT][LP], two L11^-1 [NB][NB]
+// and pivots [NB] (next panel prefetched), Y [n][RC].
+constexpr int FG = 4;          // row groups per CTA
+constexpr int FR = 4;          // rows per thread in flight
+
+template <typename C>
+__device__ __forceinline__ void load_yb(C (&y)[Tile<C>::NB], const C* __restrict__ sY, int RC, int k0, int kb, int c) {
+    constexpr int NB = Tile<C>::NB;
+#pragma unroll
+    for (int p = 0; p < NB; ++p) y[p] = p < kb ? sY[(long long)(k0 + p) * RC + c] : CT<C>::mk(0, 0);
+}
+
+// acc[q] = sum_p A[rows[q]*lda + p] y[p] for FR rows (p over the full panel;
+// A is zero beyond kb)
+template <typename C>
+__device__ __forceinline__ void rows_dot(C (&acc)[FR], const C* __restrict__ A, int lda, const int (&rows)[FR],
+                                         const C (&y)[Tile<C>::NB]) {
     typedef typename CT<C>::R T;
-    constexpr int NB = Tile<C>::NB, CB = Tile<C>::CB;
-    const int tx = threadIdx.x % 16;
-#pragma unroll 2
+    constexpr int NB = Tile<C>::NB;
+#pragma unroll
+    for (int q = 0; q < FR; ++q) acc[q] = CT<C>::mk(T(0), T(0));
+#pragma unroll
     for (int p = 0; p < NB; p += 2) {
-        if (!FULL && p >= kb) break;
-        C l0[RA], l1[RA];
+        C l0[FR], l1[FR];
 #pragma unroll
-        for (int a = 0; a < RA; ++a) load_pair(A + (arow + a) * lda + p, l0[a], l1[a]);
-        const bool two = FULL || p + 1 < kb;
-        C y0[CB], y1[CB];
+        for (int q = 0; q < FR; ++q) load_pair(A + rows[q] * lda + p, l0[q], l1[q]);
 #pragma unroll
-        for (int b = 0; b < CB; ++b) {
-            y0[b] = Yb[p * RC + tx + 16 * b];
-            y1[b] = two ? Yb[(p + 1) * RC + tx + 16 * b] : CT<C>::mk(T(0), T(0));
-        }
-#pragma unroll
-        for (int a = 0; a < RA; ++a)
-#pragma unroll
-            for (int b = 0; b < CB; ++b) acc[a][b] = cfma(l0[a], y0[b], acc[a][b]);
-#pragma unroll
-        for (int a = 0; a < RA; ++a)
-#pragma unroll
-            for (int b = 0; b < CB; ++b) acc[a][b] = cfma(l1[a], y1[b], acc[a][b]);
+        for (int q = 0; q < FR; ++q) acc[q] = cfma(l1[q], y[p + 1], cfma(l0[q], y[p], acc[q]));
     }
 }
 
-// c[r*N + k] = -(1/pi) Im sum_i y_i^2/d_i, y = L_k^-1 q_r: right-hand sides
-// [chunk*RC, chunk*RC + RC) of frequency k = 1 + blockIdx.y, chunk = blockIdx.x.
-// Shared memory: two L tiles [FT][LP], two L11^-1 [NB][NB] and pivots [NB]
-// (next panel prefetched), Y [n][RC] + one padding row of 16 CB.  Thread
-// (ty, tx) owns rows ty*FA .. ty*FA + FA - 1 of a tile and columns tx + 16 b.
 template <typename C>
-__global__ void __launch_bounds__(256, 1) k_forms(const C* __restrict__ fac, const C* __restrict__ linv, int n,
-                                                  int N, const double* __restrict__ Q, int R, int RC,
+__global__ void __launch_bounds__(320, 1) k_forms(const C* __restrict__ fac, const C* __restrict__ linv, int n, int N,
+                                                  const double* __restrict__ Q, int R, int RC,
                                                   double* __restrict__ c) {
     typedef typename CT<C>::R T;
-    constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, FA = Tile<C>::FA, CB = Tile<C>::CB, LP = tile_pitch<C>();
-    constexpr int DA = NB / 16;                         // diagonal-block rows per thread
+    constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, LP = tile_pitch<C>();
     extern __shared__ __align__(16) unsigned char sraw[];
     C* sL = reinterpret_cast<C*>(sraw);                 // [2][FT][LP]
     C* sLi = sL + 2 * FT * LP;                          // [2][NB][NB]
     C* sD = sLi + 2 * NB * NB;                          // [2][NB]
-    C* sY = sD + 2 * NB;                                // [n][RC] + 16 CB
-    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-    const int k = 1 + blockIdx.y, rc0 = blockIdx.x * RC, rc = min(RC, R - rc0), ncb = (rc + 15) / 16;
+    C* sY = sD + 2 * NB;                                // [n][RC]
+    const int tid = threadIdx.x, col = tid % RC, g = tid / RC;
+    const int k = 1 + blockIdx.y, rc0 = blockIdx.x * RC, rc = min(RC, R - rc0);
     const C* F = fac + (long long)k * n * n;
     const int nblk = (n + NB - 1) / NB;
     const C* Lk = linv + (long long)k * nblk * NB * NB;
     load_diag_data<C>(sLi, sD, Lk, F, n, 0, min(NB, n));
     if (n > NB) load_l_tile<C>(sL, F, n, NB, 0, NB);
     cp_async_commit();
-    for (long long t = tid; t < (long long)n * RC + 16 * CB; t += blockDim.x) {
-        const int i = (int)(t / RC), r = (int)(t % RC);
-        sY[t] = CT<C>::mk((i < n && r < rc) ? T(Q[(long long)i * R + rc0 + r]) : T(0), T(0));
+    {
+        // thread (g, col) fills rows g, g + FG, ... of its column (no integer division)
+        const double* q = Q + rc0 + col;
+        const bool live = col < rc;
+#pragma unroll 8
+        for (int i = g; i < n; i += FG) sY[i * RC + col] = CT<C>::mk(live ? T(q[(long long)i * R]) : T(0), T(0));
     }
-    double2 part[CB];
-#pragma unroll
-    for (int b = 0; b < CB; ++b) part[b] = make_double2(0.0, 0.0);
+    double2 part = make_double2(0.0, 0.0);
+    C y[NB];
     int buf = 0;
     for (int blk = 0; blk < nblk; ++blk) {
         const int k0 = blk * NB, kb = min(NB, n - k0), k1 = k0 + kb, db = blk & 1;
@@ -437,33 +434,31 @@ __global__ void __launch_bounds__(256, 1) k_forms(const C* __restrict__ fac, con
             load_diag_data<C>(sLi + (db ^ 1) * NB * NB, sD + (db ^ 1) * NB, Lk + (long long)(blk + 1) * NB * NB, F, n,
                               k1, min(NB, n - k1));
         cp_async_commit();
-        // y_b = L11^-1 y_b, then y_i^2/d_i into the binary64 sums
+        // y_b = L11^-1 y_b: this thread's rows g, g + FG, ... of the block
+        load_yb<C>(y, sY, RC, k0, kb, col);
+        __syncthreads();
         {
-            C acc[DA][CB];
+            const C* Li = sLi + db * NB * NB;
+            for (int i0 = g; i0 < kb; i0 += FG * FR) {
+                int rows[FR];
 #pragma unroll
-            for (int a = 0; a < DA; ++a)
+                for (int q = 0; q < FR; ++q) rows[q] = min(i0 + FG * q, NB - 1);
+                C acc[FR];
+                rows_dot<C>(acc, Li, NB, rows, y);
 #pragma unroll
-                for (int b = 0; b < CB; ++b) acc[a][b] = CT<C>::mk(T(0), T(0));
-            if (kb == NB) mma_rows<C, DA, true>(acc, sLi + db * NB * NB, NB, ty * DA, sY + (long long)k0 * RC, RC, kb);
-            else mma_rows<C, DA, false>(acc, sLi + db * NB * NB, NB, ty * DA, sY + (long long)k0 * RC, RC, kb);
-            __syncthreads();
-#pragma unroll
-            for (int a = 0; a < DA; ++a) {
-                const int i = ty * DA + a;
-                if (i >= kb) continue;
-                const C di = sD[db * NB + i];
-#pragma unroll
-                for (int b = 0; b < CB; ++b) {
-                    const int r = tx + 16 * b;
-                    if (b >= ncb || r >= RC) continue;
-                    sY[(long long)(k0 + i) * RC + r] = acc[a][b];
-                    const C q = cdiv(cmul(acc[a][b], acc[a][b]), di);
-                    part[b].x += (double)q.x;
-                    part[b].y += (double)q.y;
+                for (int q = 0; q < FR; ++q) {
+                    const int i = i0 + FG * q;
+                    if (i < kb) {
+                        sY[(long long)(k0 + i) * RC + col] = acc[q];
+                        const C v = cdiv(cmul(acc[q], acc[q]), sD[db * NB + i]);
+                        part.x += (double)v.x;
+                        part.y += (double)v.y;
+                    }
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
+        load_yb<C>(y, sY, RC, k0, kb, col);
         // Y[k1:n] -= L[k1:n, k0:k1] y_b, FT rows per tile; the next tile (of
         // this panel or the first of the next) streams in meanwhile
         for (int t = 0; t < ntile; ++t) {
@@ -479,24 +474,20 @@ __global__ void __launch_bounds__(256, 1) k_forms(const C* __restrict__ fac, con
             cp_async_commit();
             cp_async_wait<1>();
             __syncthreads();
-            const int row0 = r0 + ty * FA;
-            if (row0 < n) {
-                C acc[FA][CB];
+            const C* Lt = sL + buf * FT * LP;
+            const int nrow = min(FT, n - r0);
+            for (int i0 = g; i0 < nrow; i0 += FG * FR) {
+                int rows[FR];
 #pragma unroll
-                for (int a = 0; a < FA; ++a)
+                for (int q = 0; q < FR; ++q) rows[q] = min(i0 + FG * q, FT - 1);
+                C acc[FR];
+                rows_dot<C>(acc, Lt, LP, rows, y);
 #pragma unroll
-                    for (int b = 0; b < CB; ++b) acc[a][b] = CT<C>::mk(T(0), T(0));
-                const C* Lt = sL + buf * FT * LP;
-                if (kb == NB) mma_rows<C, FA, true>(acc, Lt, LP, ty * FA, sY + (long long)k0 * RC, RC, kb);
-                else mma_rows<C, FA, false>(acc, Lt, LP, ty * FA, sY + (long long)k0 * RC, RC, kb);
-#pragma unroll
-                for (int a = 0; a < FA; ++a) {
-                    const int i = row0 + a;
-                    if (i >= n) continue;
-#pragma unroll
-                    for (int b = 0; b < CB; ++b) {
-                        const int r = tx + 16 * b;
-                        if (b < ncb && r < RC) sY[(long long)i * RC + r] = csub(sY[(long long)i * RC + r], acc[a][b]);
+                for (int q = 0; q < FR; ++q) {
+                    const int i = i0 + FG * q;
+                    if (i < nrow) {
+                        C* yy = sY + (long long)(r0 + i) * RC + col;
+                        *yy = csub(*yy, acc[q]);
                     }
                 }
             }
@@ -505,18 +496,16 @@ __global__ void __launch_bounds__(256, 1) k_forms(const C* __restrict__ fac, con
         }
     }
     cp_async_wait<0>();
-    // sum the 16 row groups of each column (reusing the start of sY)
-    double2* red = reinterpret_cast<double2*>(sY);
+    // sum the FG row groups of each column (reusing the start of sY)
+    double* red = reinterpret_cast<double*>(sY);
     __syncthreads();
-#pragma unroll
-    for (int b = 0; b < CB; ++b) red[ty * (16 * CB) + tx + 16 * b] = part[b];
+    red[g * RC + col] = part.y;
     __syncthreads();
-    for (int r = tid; r < rc; r += blockDim.x) {
+    if (tid < rc) {
         double im = 0.0;
-        const int b = r / 16, x = r % 16;
-        for (int g = 0; g < 16; ++g) im += red[g * (16 * CB) + x + 16 * b].y;
-        c[(long long)(rc0 + r) * N + k] = -im / M_PI;
-        if (k == 1) c[(long long)(rc0 + r) * N] = 0.0;
+        for (int q = 0; q < FG; ++q) im += red[q * RC + tid];
+        c[(long long)(rc0 + tid) * N + k] = -im / M_PI;
+        if (k == 1) c[(long long)(rc0 + tid) * N] = 0.0;
     }
 }
 
@@ -582,18 +571,18 @@ void launch_ldlt(gw_ctx* ctx, gw_W* W) {
 template <typename C>
 static void forms_run(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, const double* Q, int R, double* cout,
                       const char* name) {
-    constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, CB = Tile<C>::CB, LP = tile_pitch<C>();
-    const size_t fixed = sizeof(C) * ((size_t)2 * FT * LP + 2 * NB * NB + 2 * NB + 16 * CB);
+    constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, LP = tile_pitch<C>();
+    const size_t fixed = sizeof(C) * ((size_t)2 * FT * LP + 2 * NB * NB + 2 * NB);
     const size_t budget = 224 * 1024;
-    const size_t red = sizeof(double2) * 16 * 16 * CB;            // final reduction reuses Y
-    int rc_max = (int)std::min<size_t>(16 * CB, budget > fixed ? (budget - fixed) / (sizeof(C) * (size_t)n) : 0);
+    // columns per CTA: at most 320 / FG threads, and Y [n][RC] must fit
+    int rc_max = (int)std::min<size_t>(320 / FG, budget > fixed ? (budget - fixed) / (sizeof(C) * (size_t)n) : 0);
     if (rc_max < 1) gw_throw(GW_ERR_INVALID_ARG, "n_sub too large for the forms kernel");
     const int chunks = div_up(R, rc_max);
     const int RC = div_up(R, chunks);
-    const size_t smem = fixed + std::max(sizeof(C) * (size_t)n * RC, red);
+    const size_t smem = fixed + std::max(sizeof(C) * (size_t)n * RC, sizeof(double) * FG * (size_t)RC);
     if (chunks > 65535 || N - 1 > 65535) gw_throw(GW_ERR_INVALID_ARG, "too many right-hand sides or frequencies");
     allow_max_smem(k_forms<C>);
-    klaunch(ctx, name, k_forms<C>, dim3(chunks, N - 1), 256, smem, fac, linv, n, N, Q, R, RC, cout);
+    klaunch(ctx, name, k_forms<C>, dim3(chunks, N - 1), FG * RC, smem, fac, linv, n, N, Q, R, RC, cout);
 }
 
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
