@@ -80,24 +80,31 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024)
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int rows = (n + CL - 1) / CL;
-    float* Ar = sm;                       // [rows][n] own rows
-    float* sv = Ar + (long long)rows * n; // [n] reflector (full)
-    float* sw = sv + n;                   // [n] w (full)
-    float* own_w = sw + n;                // [rows] w of own rows
-    float* own_p = own_w + rows;          // [rows] p of own rows
+    float* Ar = sm;                        // [rows][n] own rows
+    float* svb = Ar + (long long)rows * n; // [2][n] reflector, pushed by its owner (by step parity)
+    float* pb = svb + 2 * n;               // [2][n] p_i, i > k, pushed by the CTA owning row i
+    float* sw = pb + 2 * n;                // [n] w
     __shared__ float red[33];
-    __shared__ float s_part;
-    __shared__ float s_tau;
+    __shared__ float s_part[2][CL];        // partial v^T p of every CTA, pushed
+    __shared__ float s_tau[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (long long t = tid; t < (long long)rows * n; t += blockDim.x) {
-        int li = (int)(t / n), j = (int)(t % n);
-        int i = li * CL + rank;
-        Ar[t] = i < n ? A[(long long)i * n + j] : 0.f;
+    for (int li = 0; li < rows; ++li) {
+        const int i = li * CL + rank;
+        for (int j = tid; j < n; j += blockDim.x) Ar[(long long)li * n + j] = i < n ? A[(long long)i * n + j] : 0.f;
     }
+    // Two cluster barriers per step.  Everything another CTA needs is
+    // stored into that CTA's shared memory before a barrier (distributed
+    // shared memory stores), so after each barrier all reads are local:
+    //   (1) the owner of row k pushes the reflector v and tau;
+    //   (2) every CTA pushes p_i of its rows and its partial v^T p.
+    // Buffers alternate by step parity: a CTA that runs ahead writes the
+    // other half.
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
-        const int owner = k % CL;
-        cluster.sync();
+        const int owner = k % CL, par = k & 1;
+        float* sv = svb + par * n;
+        float* p = pb + par * n;
+        __syncthreads();
         if (rank == owner) {
             float* rk = Ar + (long long)(k / CL) * n + k + 1;
             float part = 0.f;
@@ -117,20 +124,20 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024)
                 d[k] = Ar[(long long)(k / CL) * n + k];
                 e[k] = sig > 0.f ? alpha : x0;
                 tau[k] = t;
-                s_tau = t;
+                for (int r = 0; r < CL; ++r) cluster.map_shared_rank(s_tau, r)[par] = t;
             }
             __syncthreads();
-            for (int j = tid; j < m; j += blockDim.x) A[(long long)k * n + k + 1 + j] = sv[j];   // reflector
+            for (int j = tid; j < m; j += blockDim.x) {
+                const float x = sv[j];
+                A[(long long)k * n + k + 1 + j] = x;   // reflector
+#pragma unroll
+                for (int r = 0; r < CL; ++r)
+                    if (r != owner) cluster.map_shared_rank(sv, r)[j] = x;
+            }
         }
         cluster.sync();
-        if (rank != owner) {
-            const float* rv = cluster.map_shared_rank(sv, owner);
-            for (int j = tid; j < m; j += blockDim.x) sv[j] = rv[j];
-            if (tid == 0) s_tau = *cluster.map_shared_rank(&s_tau, owner);
-        }
-        __syncthreads();
-        const float t = s_tau;
-        // own rows i > k: p_i = t sum_j A[i][j] v_j
+        const float t = s_tau[par];
+        // own rows i > k: p_i = t sum_j A[i][j] v_j, pushed to every CTA
         const int li0 = (k + 1 - rank + CL - 1) / CL;      // first own row index with i >= k+1
         float pv = 0.f;
         for (int li = li0 + warp; li < rows; li += nw) {
@@ -140,26 +147,17 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024)
             float acc = 0.f;
             for (int j = lane; j < m; j += 32) acc += ri[j] * sv[j];
             acc = warp_sum(acc) * t;
-            if (lane == 0) {
-                own_p[li] = acc;
-                pv += acc * sv[i - k - 1];
-            }
+            if (lane < CL) cluster.map_shared_rank(p, lane)[i - k - 1] = acc;
+            if (lane == 0) pv += acc * sv[i - k - 1];
         }
         pv = block_sum1024(pv, red);
-        if (tid == 0) s_part = pv;
+        if (tid < CL) cluster.map_shared_rank(&s_part[0][0], tid)[par * CL + rank] = pv;
         cluster.sync();
         float tot = 0.f;
-        for (int r = 0; r < CL; ++r) tot += *cluster.map_shared_rank(&s_part, r);
+#pragma unroll
+        for (int r = 0; r < CL; ++r) tot += s_part[par][r];
         const float K = 0.5f * t * tot;
-        for (int li = li0 + tid; li < rows; li += blockDim.x) {
-            const int i = li * CL + rank;
-            if (i < n) own_w[li] = own_p[li] - K * sv[i - k - 1];
-        }
-        cluster.sync();
-        for (int j = tid; j < m; j += blockDim.x) {
-            const int i = k + 1 + j;
-            sw[j] = *cluster.map_shared_rank(own_w + i / CL, i % CL);
-        }
+        for (int j = tid; j < m; j += blockDim.x) sw[j] = p[j] - K * sv[j];
         __syncthreads();
         for (int li = li0 + warp; li < rows; li += nw) {
             const int i = li * CL + rank;
@@ -639,7 +637,7 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         X = dalloc<double>(ctx, nn);
         launch_to_f32(ctx, g, A32, nn);
         const int rows = (n + CL - 1) / CL;
-        const size_t smem_cl = sizeof(float) * ((size_t)rows * n + 2 * (size_t)n + 2 * (size_t)rows);
+        const size_t smem_cl = sizeof(float) * ((size_t)rows * n + 5 * (size_t)n);
         if (smem_cl <= 220 * 1024) {
             allow_max_smem(k_sytrd32_cl);
             klaunch(ctx, "k_sytrd32_cl", k_sytrd32_cl, CL, 1024, smem_cl, A32, n, d, e, tau);
