@@ -84,8 +84,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024)
     float* svb = Ar + (long long)rows * n; // [2][n] reflector, pushed by its owner (by step parity)
     float* pb = svb + 2 * n;               // [2][n] p_i, i > k, pushed by the CTA owning row i
     float* sw = pb + 2 * n;                // [n] w
-    __shared__ float red[33];
-    __shared__ float s_part[2][CL];        // partial v^T p of every CTA, pushed
+    __shared__ float s_part[2][CL][32];    // partial v^T p of every warp of every CTA, pushed
     __shared__ float s_tau[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (int li = 0; li < rows; ++li) {
@@ -106,25 +105,25 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024)
         float* p = pb + par * n;
         __syncthreads();
         if (rank == owner) {
-            float* rk = Ar + (long long)(k / CL) * n + k + 1;
-            float part = 0.f;
-            for (int j = tid; j < m; j += blockDim.x) {
-                float x = rk[j];
-                sv[j] = x;
-                part += x * x;
-            }
-            float sig = block_sum1024(part, red);
-            if (tid == 0) {
-                float x0 = sv[0];
-                float alpha = sig > 0.f ? -copysignf(sqrtf(sig), x0) : 0.f;
-                float v0 = x0 - alpha;
-                float vtv = sig - x0 * x0 + v0 * v0;
-                float t = vtv > 0.f ? 2.f / vtv : 0.f;
-                sv[0] = v0;
-                d[k] = Ar[(long long)(k / CL) * n + k];
-                e[k] = sig > 0.f ? alpha : x0;
-                tau[k] = t;
-                for (int r = 0; r < CL; ++r) cluster.map_shared_rank(s_tau, r)[par] = t;
+            const float* rk = Ar + (long long)(k / CL) * n + k + 1;
+            for (int j = tid; j < m; j += blockDim.x) sv[j] = rk[j];
+            if (warp == 0) {
+                // |x|^2 by one warp (no block-wide barrier)
+                float part = 0.f;
+                for (int j = lane; j < m; j += 32) part += rk[j] * rk[j];
+                const float sig = warp_sum(part);
+                if (lane == 0) {
+                    const float x0 = rk[0];
+                    const float alpha = sig > 0.f ? -copysignf(sqrtf(sig), x0) : 0.f;
+                    const float v0 = x0 - alpha;
+                    const float vtv = sig - x0 * x0 + v0 * v0;
+                    const float t = vtv > 0.f ? 2.f / vtv : 0.f;
+                    sv[0] = v0;
+                    d[k] = Ar[(long long)(k / CL) * n + k];
+                    e[k] = sig > 0.f ? alpha : x0;
+                    tau[k] = t;
+                    for (int r = 0; r < CL; ++r) cluster.map_shared_rank(s_tau, r)[par] = t;
+                }
             }
             __syncthreads();
             for (int j = tid; j < m; j += blockDim.x) {
@@ -150,12 +149,14 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024)
             if (lane < CL) cluster.map_shared_rank(p, lane)[i - k - 1] = acc;
             if (lane == 0) pv += acc * sv[i - k - 1];
         }
-        pv = block_sum1024(pv, red);
-        if (tid < CL) cluster.map_shared_rank(&s_part[0][0], tid)[par * CL + rank] = pv;
+        // lane 0 holds this warp's partial v^T p: push it to every CTA
+        pv = __shfl_sync(0xffffffffu, pv, 0);
+        if (lane < CL) cluster.map_shared_rank(&s_part[0][0][0], lane)[(par * CL + rank) * 32 + warp] = pv;
         cluster.sync();
         float tot = 0.f;
 #pragma unroll
-        for (int r = 0; r < CL; ++r) tot += s_part[par][r];
+        for (int r = 0; r < CL; ++r) tot += (lane < nw) ? s_part[par][r][lane] : 0.f;
+        tot = warp_sum(tot);
         const float K = 0.5f * t * tot;
         for (int j = tid; j < m; j += blockDim.x) sw[j] = p[j] - K * sv[j];
         __syncthreads();
