@@ -429,8 +429,8 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
             Bsel = dalloc<double>(ctx, (size_t)nr * n_sub);
             // binary64: refine to working accuracy; mixed: binary64 Rayleigh quotients of
             // the binary32 vectors, no refinement (1 meV bar met with margin)
-            if (prec == GW_FP64) eigh_top_scaled(ctx, g, nr, n_sub, 6, 1e-13, Bsel);
-            else eigh_top_scaled(ctx, g, nr, n_sub, 0, 0.0, Bsel);
+            if (prec == GW_FP64) eigh_top_scaled(ctx, g, nr, n_sub, 6, 1e-13, true, Bsel);
+            else eigh_top_scaled(ctx, g, nr, n_sub, 0, 0.0, false, Bsel);
             gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, T1, nr, Bsel, n_sub, 0.0, c->Zup, n_sub);
             // Z = X_r Bsel is only read back: keep its factors, form it on request
             c->Xr = dalloc<double>(ctx, (size_t)n_prod * nr);

@@ -379,41 +379,43 @@ __device__ void tri_solve(int n, const R* rdu, const R* du1, const R* du2, const
     for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du1[i] * x[i + 1] - du2[i] * x[i + 2]) * rdu[i];
 }
 
-// Inverse iteration in binary64, one thread per eigenvalue; the pivoted LU
-// of T - lam lives in shared memory (IT threads per CTA).  In binary64 the
-// vectors of distinct eigenvalues come out orthogonal to ~u64 |T| / gap, so
-// no re-orthogonalisation is needed (the binary64 refinement that follows
-// removes what is left).
+// Inverse iteration, one thread per eigenvalue, in binary64 (R = double)
+// or binary32 (R = float); the pivoted LU of T - lam lives in shared memory
+// (IT threads per CTA) or in a per-eigenvalue slice of gws.  The vectors of
+// distinct eigenvalues come out orthogonal to ~u |T| / gap; vectors inside
+// clusters of close eigenvalues are orthonormalised by k_cluster_mgs.
 constexpr int IT = 8;
 
+template <typename R>
 __global__ void __launch_bounds__(IT) k_invit(const float* __restrict__ d, const float* __restrict__ e,
                                               const float* __restrict__ lam, int n, double tiny,
-                                              float* __restrict__ Y, double* __restrict__ gws) {
-    extern __shared__ double swd[];
+                                              float* __restrict__ Y, R* __restrict__ gws) {
+    extern __shared__ __align__(16) unsigned char swraw[];
+    R* swd = reinterpret_cast<R*>(swraw);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    // scratch: shared memory, or a per-eigenvalue slice of gws when it is given
-    double* base = gws ? gws + (long long)i * (5 * n + (n + 7) / 8) : swd + (long long)threadIdx.x * 5 * n;
-    double* du = base;
-    double* du1 = du + n;
-    double* du2 = du1 + n;
-    double* mul = du2 + n;
-    double* x = mul + n;
+    const long long per = 5LL * n + (n + sizeof(R) - 1) / sizeof(R);   // R words per eigenvalue in gws
+    R* base = gws ? gws + (long long)i * per : swd + (long long)threadIdx.x * 5 * n;
+    R* du = base;
+    R* du1 = du + n;
+    R* du2 = du1 + n;
+    R* mul = du2 + n;
+    R* x = mul + n;
     unsigned char* piv = gws ? reinterpret_cast<unsigned char*>(base + 5 * n)
                              : reinterpret_cast<unsigned char*>(swd + (long long)blockDim.x * 5 * n) + (long long)threadIdx.x * n;
-    tri_factor<double>(d, e, n, (double)lam[i], tiny, du, du1, du2, mul, piv);
+    tri_factor<R>(d, e, n, (R)lam[i], (R)tiny, du, du1, du2, mul, piv);
     // start from a hashed pseudo-random vector so that the vectors of a
     // degenerate eigenvalue start in different directions
     for (int j = 0; j < n; ++j) {
         unsigned int h = (unsigned int)i * 2654435761u ^ ((unsigned int)j * 2246822519u + 0x9e3779b9u);
         h ^= h >> 15; h *= 2246822519u; h ^= h >> 13; h *= 3266489917u; h ^= h >> 16;
-        x[j] = 0.5 + (double)(h & 0xffffff) * (1.0 / 16777216.0);
+        x[j] = R(0.5) + (R)(h & 0xffffff) * R(1.0 / 16777216.0);
     }
     for (int it = 0; it < 3; ++it) {
-        tri_solve<double>(n, du, du1, du2, mul, piv, x);
-        double nr = 0.0;
+        tri_solve<R>(n, du, du1, du2, mul, piv, x);
+        R nr = R(0);
         for (int j = 0; j < n; ++j) nr += x[j] * x[j];
-        nr = 1.0 / sqrt(fmax(nr, 1e-300));
+        nr = R(1) / sqrt(fmax(nr, sizeof(R) == 8 ? R(1e-300) : R(1e-38)));
         for (int j = 0; j < n; ++j) x[j] *= nr;
     }
     float* yo = Y + (long long)i * n;
@@ -615,11 +617,13 @@ __global__ void k_scale_cols(double* __restrict__ B, int n, int n_sub, const dou
 void launch_to_f32(gw_ctx* ctx, const double* a, float* b, long long n);
 
 // g (n x n, binary64, symmetric) -> B (n x n_sub) = xi_top lambda_top^-1/2
-void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iters, double oa_tol, double* B) {
+void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iters, double oa_tol, bool vectors_f64,
+                     double* B) {
     const long long nn = (long long)n * n;
     float* A32 = nullptr; float *d = nullptr, *e = nullptr, *tau = nullptr, *lam32 = nullptr, *Y = nullptr;
     double *X = nullptr, *X2 = nullptr, *R = nullptr, *S = nullptr, *T = nullptr, *E = nullptr, *lam = nullptr;
-    double *stat = nullptr, *G = nullptr, *Bt = nullptr, *gws = nullptr;
+    double *stat = nullptr, *G = nullptr, *Bt = nullptr;
+    void* gws = nullptr;
     float *vb = nullptr, *pb = nullptr, *pt = nullptr;
     unsigned int* bar = nullptr;
     int* sel = nullptr;
@@ -674,21 +678,32 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         bnd = bnd * 1.01f + 1e-30f;
         klaunch(ctx, "k_bisect", k_bisect, div_up(n, 8), 256, 2 * (size_t)n * sizeof(float), (const float*)d,
                 (const float*)e, n, bnd, lam32);
-        const size_t per_thread = (size_t)n * (5 * sizeof(double) + 1);
-        if (per_thread <= 200 * 1024) {
-            // few threads per CTA so that the eigenvalues spread over all SMs
-            const int it_threads = (int)std::max<size_t>(
-                1, std::min(std::min((size_t)IT, (200 * 1024) / per_thread), (size_t)div_up(n, ctx->num_sms)));
-            const size_t smem_it = per_thread * it_threads;
-            allow_max_smem(k_invit);
-            klaunch(ctx, "k_invit", k_invit, div_up(n, it_threads), it_threads, smem_it, (const float*)d,
-                    (const float*)e, (const float*)lam32, n, 1e-13 * (double)bnd, Y, (double*)nullptr);
-        } else {
-            gws = dalloc<double>(ctx, (size_t)n * (5 * (size_t)n + (n + 7) / 8));
-            klaunch(ctx, "k_invit", k_invit, div_up(n, IT), IT, 0, (const float*)d, (const float*)e,
-                    (const float*)lam32, n, 1e-13 * (double)bnd, Y, gws);
-        }
-        klaunch(ctx, "k_cluster_mgs", k_cluster_mgs, n, 256, 0, (const float*)lam32, n, 1e-6f * bnd, Y);
+        // binary64 vectors when they are refined to binary64 accuracy afterwards
+        auto invit = [&](auto zero) {
+            typedef decltype(zero) R;
+            const double tiny = (sizeof(R) == 8 ? 1e-13 : 1e-6) * (double)bnd;
+            const size_t per_thread = (size_t)n * (5 * sizeof(R) + 1);
+            if (per_thread <= 200 * 1024) {
+                // few threads per CTA so that the eigenvalues spread over all SMs
+                const int it_threads = (int)std::max<size_t>(
+                    1, std::min(std::min((size_t)IT, (200 * 1024) / per_thread), (size_t)div_up(n, ctx->num_sms)));
+                const size_t smem_it = per_thread * it_threads + 16;
+                allow_max_smem(k_invit<R>);
+                klaunch(ctx, "k_invit", k_invit<R>, div_up(n, it_threads), it_threads, smem_it, (const float*)d,
+                        (const float*)e, (const float*)lam32, n, tiny, Y, (R*)nullptr);
+            } else {
+                const size_t per = 5 * (size_t)n + (n + sizeof(R) - 1) / sizeof(R);
+                gws = ctx_alloc(ctx, (size_t)n * per * sizeof(R));
+                klaunch(ctx, "k_invit", k_invit<R>, div_up(n, IT), IT, 0, (const float*)d, (const float*)e,
+                        (const float*)lam32, n, tiny, Y, (R*)gws);
+            }
+        };
+        if (vectors_f64) invit(0.0);
+        else invit(0.0f);
+        // clusters: eigenvalue gaps below which inverse iteration cannot keep
+        // the vectors orthogonal in its working precision
+        klaunch(ctx, "k_cluster_mgs", k_cluster_mgs, n, 256, 0, (const float*)lam32, n,
+                (vectors_f64 ? 1e-6f : 1e-4f) * bnd, Y);
         // two warps per CTA: the vectors spread over all SMs
         const int bt_warps = (int)std::max<size_t>(1, std::min<size_t>(2, (200 * 1024) / ((size_t)n * sizeof(float))));
         const size_t smem_bt = (size_t)bt_warps * n * sizeof(float);

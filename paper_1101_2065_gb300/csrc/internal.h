@@ -175,7 +175,8 @@ void gemm_f64(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, double alpha,
 // linalg.cu
 void cholesky_lower(gw_ctx* ctx, double* A, int n);          // in place, zeroes upper
 // eigh.cu: B = xi lambda^-1/2 for the n_sub largest eigenpairs of g
-void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iters, double oa_tol, double* B);
+void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iters, double oa_tol, bool vectors_f64,
+                     double* B);
 // chi0.cu
 void launch_fft_tables(gw_ctx* ctx, gw_chi0* c);
 void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c);

@@ -250,6 +250,46 @@ __global__ void __launch_bounds__(256, 2) k_ldlt_panel(C* __restrict__ fac, int 
     }
 }
 
+// acc = sL sW^T on one tile and M -= acc on the lower triangle.  Thread
+// (ty, tx) owns rows ty + 16a and columns tx + 16b; on a diagonal tile the
+// sub-blocks b > a lie above the diagonal and are skipped at compile time.
+template <typename C, bool DIAG>
+__device__ __forceinline__ void syrk_tile(C* __restrict__ A, int n, int r0, int c0,
+                                          const C (*sL)[Tile<C>::NB + 1], const C (*sW)[Tile<C>::NB + 1]) {
+    typedef typename CT<C>::R R;
+    constexpr int NB = Tile<C>::NB, TA = Tile<C>::A;
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    C acc[TA][TA];
+#pragma unroll
+    for (int a = 0; a < TA; ++a)
+#pragma unroll
+        for (int b = 0; b < TA; ++b) acc[a][b] = CT<C>::mk(R(0), R(0));
+#pragma unroll 8
+    for (int p = 0; p < NB; ++p) {
+        C l[TA], w[TA];
+#pragma unroll
+        for (int a = 0; a < TA; ++a) l[a] = sL[ty + 16 * a][p];
+#pragma unroll
+        for (int b = 0; b < TA; ++b) w[b] = sW[tx + 16 * b][p];
+#pragma unroll
+        for (int a = 0; a < TA; ++a)
+#pragma unroll
+            for (int b = 0; b < TA; ++b)
+                if (!DIAG || b <= a) acc[a][b] = cfma(l[a], w[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < TA; ++a)
+#pragma unroll
+        for (int b = 0; b < TA; ++b) {
+            if (DIAG && b > a) continue;
+            const int i = r0 + ty + 16 * a, j = c0 + tx + 16 * b;
+            if (i < n && j <= i) {
+                C* m = A + (long long)i * n + j;
+                *m = csub(*m, acc[a][b]);
+            }
+        }
+}
+
 // Trailing update after panel k0: M22 -= L21 D L21^T on the lower triangle,
 // tile blockIdx.x of frequency blockIdx.y.
 template <typename C>
@@ -278,34 +318,8 @@ __global__ void __launch_bounds__(256) k_ldlt_syrk(C* __restrict__ fac, int n, i
         sW[rr][p] = wv;
     }
     __syncthreads();
-    const int ty = tid / 16, tx = tid % 16;
-    C acc[TA][TA];
-#pragma unroll
-    for (int a = 0; a < TA; ++a)
-#pragma unroll
-        for (int b = 0; b < TA; ++b) acc[a][b] = CT<C>::mk(R(0), R(0));
-#pragma unroll 8
-    for (int p = 0; p < NB; ++p) {
-        C l[TA], w[TA];
-#pragma unroll
-        for (int a = 0; a < TA; ++a) l[a] = sL[ty + 16 * a][p];
-#pragma unroll
-        for (int b = 0; b < TA; ++b) w[b] = sW[tx + 16 * b][p];
-#pragma unroll
-        for (int a = 0; a < TA; ++a)
-#pragma unroll
-            for (int b = 0; b < TA; ++b) acc[a][b] = cfma(l[a], w[b], acc[a][b]);
-    }
-#pragma unroll
-    for (int a = 0; a < TA; ++a)
-#pragma unroll
-        for (int b = 0; b < TA; ++b) {
-            int i = r0 + ty + 16 * a, j = c0 + tx + 16 * b;
-            if (i < n && j <= i) {
-                C* m = A + (long long)i * n + j;
-                *m = csub(*m, acc[a][b]);
-            }
-        }
+    if (I == J) syrk_tile<C, true>(A, n, r0, c0, sL, sW);
+    else syrk_tile<C, false>(A, n, r0, c0, sL, sW);
 }
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
