@@ -21,17 +21,39 @@ namespace {
 
 // Mixed-radix Stockham FFT in shared memory (natural order in and out):
 // one radix-2 or radix-4 pass first (no twiddles), then radix-8 passes.
-// tws = exp(-2 pi i t / L), t < L/2, in shared memory.  The inverse uses
-// conjugate twiddles and rotations (unnormalised).  Returns the buffer
-// holding the result (a or b).  All threads of the CTA must call it.
+// The radix-8 passes read their twiddles from per-pass tables
+// [w^k | w^2k | w^4k], k < Ns, w = exp(-2 pi i c / L), c = L / (8 Ns),
+// built once per CTA (build_pass_twiddles), so consecutive butterflies read
+// consecutive entries.  The inverse uses conjugate twiddles and rotations
+// (unnormalised).  Returns the buffer holding the result (a or b).  All
+// threads of the CTA must call it.
 template <typename C>
-__device__ __forceinline__ C tw_at(const C* tws, int t, int L) {     // exp(-2 pi i t / L), 0 <= t < L
+__device__ __forceinline__ C tw_at(const C* __restrict__ tw, int t, int L) {   // exp(-2 pi i t / L), 0 <= t < L
     const int h = L >> 1;
-    if (t < h) return tws[t];
-    C w = tws[t - h];
+    if (t < h) return tw[t];
+    C w = tw[t - h];
     w.x = -w.x;
     w.y = -w.y;
     return w;
+}
+__device__ __forceinline__ int first_radix(int logL) { return logL % 3 == 1 ? 2 : logL % 3 == 2 ? 4 : 1; }
+__host__ __device__ __forceinline__ int pass_twiddle_count(int logL) {   // entries of all per-pass tables
+    int Ns = logL % 3 == 1 ? 2 : logL % 3 == 2 ? 4 : 1, tot = 0;
+    for (int s = 0; s < logL / 3; ++s, Ns *= 8) tot += 3 * Ns;
+    return tot;
+}
+// tw = exp(-2 pi i t / L), t < L/2 (global); ptw = per-pass tables (shared)
+template <typename C>
+__device__ void build_pass_twiddles(C* ptw, const C* __restrict__ tw, int L, int logL) {
+    int Ns = first_radix(logL), off = 0;
+    for (int s = 0; s < logL / 3; ++s, Ns *= 8) {
+        const int c = L / (8 * Ns);
+        for (int t = threadIdx.x; t < 3 * Ns; t += blockDim.x) {
+            const int r = t / Ns, k = t % Ns;            // r = 0, 1, 2 -> power 1, 2, 4
+            ptw[off + t] = tw_at(tw, (1 << r) * k * c, L);
+        }
+        off += 3 * Ns;
+    }
 }
 template <typename C, bool INV>
 __device__ __forceinline__ C rot_mi(C z) {        // z * (-i) forward, z * (+i) inverse
@@ -77,36 +99,26 @@ __device__ __forceinline__ void dft8(C (&x)[8]) {
     }
 }
 
+// One Stockham pass of radix RAD on L points, Ns = product of the radices
+// before it; ptw = this pass's table (radix 8 only).
 template <typename C, int RAD, bool INV>
 __device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __restrict__ b, int L, int Ns,
-                                              const C* tws) {
+                                              const C* __restrict__ ptw) {
     const int nb = L / RAD;
-    const int c = L / (RAD * Ns);           // twiddle exponent step
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
         const int k = j & (Ns - 1);
         C x[RAD];
 #pragma unroll
         for (int r = 0; r < RAD; ++r) x[r] = a[j + r * nb];
-        if (Ns > 1) {
-            if constexpr (RAD == 8) {
-                C w1 = tw_at(tws, k * c, L), w2 = tw_at(tws, 2 * k * c, L), w4 = tw_at(tws, 4 * k * c, L);
-                if (INV) { w1.y = -w1.y; w2.y = -w2.y; w4.y = -w4.y; }
-                const C w3 = cmul(w1, w2), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
-                x[1] = cmul(x[1], w1); x[2] = cmul(x[2], w2); x[3] = cmul(x[3], w3);
-                x[4] = cmul(x[4], w4); x[5] = cmul(x[5], w5); x[6] = cmul(x[6], w6); x[7] = cmul(x[7], w7);
-            } else {
-#pragma unroll
-                for (int r = 1; r < RAD; ++r) {
-                    C w = tw_at(tws, r * k * c, L);
-                    if (INV) w.y = -w.y;
-                    x[r] = cmul(x[r], w);
-                }
-            }
-        }
         if constexpr (RAD == 8) {
+            C w1 = ptw[k], w2 = ptw[Ns + k], w4 = ptw[2 * Ns + k];
+            if (INV) { w1.y = -w1.y; w2.y = -w2.y; w4.y = -w4.y; }
+            const C w3 = cmul(w1, w2), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+            x[1] = cmul(x[1], w1); x[2] = cmul(x[2], w2); x[3] = cmul(x[3], w3);
+            x[4] = cmul(x[4], w4); x[5] = cmul(x[5], w5); x[6] = cmul(x[6], w6); x[7] = cmul(x[7], w7);
             dft8<C, INV>(x);
         } else if constexpr (RAD == 4) {
-            dft4<C, INV>(x[0], x[1], x[2], x[3]);
+            dft4<C, INV>(x[0], x[1], x[2], x[3]);       // first pass: Ns = 1, no twiddles
         } else {
             const C u0 = x[0];
             x[0] = cadd(u0, x[1]);
@@ -119,14 +131,14 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __rest
 }
 
 template <typename C>
-__device__ C* fft_smem(C* a, C* b, int L, int logL, const C* tws, bool inverse) {
+__device__ C* fft_smem(C* a, C* b, int L, int logL, const C* ptw, bool inverse) {
     int Ns = 1;
     const int rem = logL % 3;
     if (rem == 1) {
-        if (inverse) stockham_pass<C, 2, true>(a, b, L, Ns, tws); else stockham_pass<C, 2, false>(a, b, L, Ns, tws);
+        if (inverse) stockham_pass<C, 2, true>(a, b, L, Ns, ptw); else stockham_pass<C, 2, false>(a, b, L, Ns, ptw);
         Ns *= 2;
     } else if (rem == 2) {
-        if (inverse) stockham_pass<C, 4, true>(a, b, L, Ns, tws); else stockham_pass<C, 4, false>(a, b, L, Ns, tws);
+        if (inverse) stockham_pass<C, 4, true>(a, b, L, Ns, ptw); else stockham_pass<C, 4, false>(a, b, L, Ns, ptw);
         Ns *= 4;
     }
     if (rem) {
@@ -134,7 +146,8 @@ __device__ C* fft_smem(C* a, C* b, int L, int logL, const C* tws, bool inverse) 
         C* t = a; a = b; b = t;
     }
     for (int s = 0; s < logL / 3; ++s) {
-        if (inverse) stockham_pass<C, 8, true>(a, b, L, Ns, tws); else stockham_pass<C, 8, false>(a, b, L, Ns, tws);
+        if (inverse) stockham_pass<C, 8, true>(a, b, L, Ns, ptw); else stockham_pass<C, 8, false>(a, b, L, Ns, ptw);
+        ptw += 3 * Ns;
         Ns *= 8;
         __syncthreads();
         C* t = a; a = b; b = t;
@@ -173,7 +186,7 @@ __global__ void k_kernel_spectra(const double2* __restrict__ tw, int N, int logL
     double2* a = sbuf;
     double2* b = sbuf + L;
     double2* tws = sbuf + 2 * L;
-    for (int t = threadIdx.x; t < L / 2; t += blockDim.x) tws[t] = tw[t];
+    build_pass_twiddles(tws, tw, L, logL);
     for (int d = threadIdx.x; d < L; d += blockDim.x) {
         double2 v = make_double2(0.0, 0.0);
         if (blockIdx.x == 0) {
@@ -237,8 +250,8 @@ __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __r
     C* B0 = sbuf;
     C* B1 = sbuf + L;
     C* B2 = sbuf + 2 * L;
-    C* tws = sbuf + 3 * L;                 // exp(-2 pi i t / L), t < L/2
-    for (int t = threadIdx.x; t < L / 2; t += blockDim.x) tws[t] = tw[t];
+    C* tws = sbuf + 3 * L;                 // per-pass twiddle tables
+    build_pass_twiddles(tws, tw, L, logL);
     for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
         int m1, n1, m2, n2;
         tri_index(2 * g, m1, n1);
@@ -321,7 +334,7 @@ void launch_fft_tables(gw_ctx* ctx, gw_chi0* c) {
     c->C1 = dalloc<double2>(ctx, L);
     c->C2 = dalloc<double2>(ctx, L);
     klaunch(ctx, "k_twiddles", k_twiddles, div_up(L / 2, 256), 256, 0, c->tw, L);
-    size_t smem = (2 * (size_t)L + L / 2) * sizeof(double2);
+    size_t smem = (2 * (size_t)L + pass_twiddle_count(c->logL)) * sizeof(double2);
     allow_max_smem(k_kernel_spectra);
     klaunch(ctx, "k_kernel_spectra", k_kernel_spectra, 2, 256, smem, c->tw, N, c->logL, c->grid.d_omega, c->grid.eta, c->C1, c->C2);
 }
@@ -330,7 +343,7 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
     const int L = c->L, N = c->grid.n_omega, n = c->n_sub;
     const bool f32 = c->prec == GW_MIXED;
     const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
-    size_t smem = (3 * (size_t)L + L / 2) * csz;
+    size_t smem = (3 * (size_t)L + pass_twiddle_count(c->logL)) * csz;
     if (smem > 227 * 1024) gw_throw(GW_ERR_INVALID_ARG, "n_omega too large for the FFT kernel");
     int per_sm = std::max(1, (int)((228 * 1024) / (smem + 1024)));
     long long n_grp = ((long long)n * (n + 1) / 2 + 1) / 2;

@@ -455,7 +455,11 @@ __global__ void __launch_bounds__(256) k_cluster_mgs(const float* __restrict__ l
 }
 
 // ------------------------------------------------------------------ 4
-// X[:, i] = Q Y[i], Q = H_0 ... H_{n-3}; one warp per eigenvector.
+// X[:, i] = Q Y[i], Q = H_0 ... H_{n-3}; one warp per eigenvector.  With
+// MT > 0 each lane keeps its MT entries of the current reflector in
+// registers and the next reflector is loaded while the current one is
+// applied (n <= 32 MT); MT = 0 is the plain loop for any n.
+template <int MT>
 __global__ void __launch_bounds__(256) k_backtransform(const float* __restrict__ A, const float* __restrict__ tau,
                                                        int n, const float* __restrict__ Y, double* __restrict__ X) {
     extern __shared__ float sy[];
@@ -465,15 +469,54 @@ __global__ void __launch_bounds__(256) k_backtransform(const float* __restrict__
     float* y = sy + (long long)w * n;   // one vector per warp
     for (int j = lane; j < n; j += 32) y[j] = Y[(long long)i * n + j];
     __syncwarp();
-    for (int k = n - 3; k >= 0; --k) {
-        const float t = tau[k];
-        if (t == 0.f) continue;
-        const float* v = A + (long long)k * n + k + 1;
-        float s = 0.f;
-        for (int j = lane; j < n - k - 1; j += 32) s += v[j] * y[k + 1 + j];
-        s = warp_sum(s) * t;
-        for (int j = lane; j < n - k - 1; j += 32) y[k + 1 + j] -= s * v[j];
-        __syncwarp();
+    if constexpr (MT == 0) {
+        for (int k = n - 3; k >= 0; --k) {
+            const float t = tau[k];
+            if (t == 0.f) continue;
+            const float* v = A + (long long)k * n + k + 1;
+            float s = 0.f;
+            for (int j = lane; j < n - k - 1; j += 32) s += v[j] * y[k + 1 + j];
+            s = warp_sum(s) * t;
+            for (int j = lane; j < n - k - 1; j += 32) y[k + 1 + j] -= s * v[j];
+            __syncwarp();
+        }
+    } else {
+        float vn[MT], vc[MT];
+        auto load = [&](float (&v)[MT], int k) {
+            const float* src = A + (long long)k * n + k + 1;
+            const int m = n - k - 1;
+#pragma unroll
+            for (int q = 0; q < MT; ++q) {
+                const int j = lane + 32 * q;
+                v[q] = j < m ? src[j] : 0.f;
+            }
+        };
+        if (n >= 3) load(vn, n - 3);
+        float tn = n >= 3 ? tau[n - 3] : 0.f;
+        for (int k = n - 3; k >= 0; --k) {
+            const float t = tn;
+#pragma unroll
+            for (int q = 0; q < MT; ++q) vc[q] = vn[q];
+            if (k > 0) {
+                load(vn, k - 1);
+                tn = tau[k - 1];
+            }
+            if (t == 0.f) continue;
+            const int m = n - k - 1;
+            float s = 0.f;
+#pragma unroll
+            for (int q = 0; q < MT; ++q) {
+                const int j = lane + 32 * q;
+                if (j < m) s += vc[q] * y[k + 1 + j];
+            }
+            s = warp_sum(s) * t;
+#pragma unroll
+            for (int q = 0; q < MT; ++q) {
+                const int j = lane + 32 * q;
+                if (j < m) y[k + 1 + j] -= s * vc[q];
+            }
+            __syncwarp();
+        }
     }
     for (int j = lane; j < n; j += 32) X[(long long)j * n + i] = (double)y[j];
 }
@@ -707,9 +750,15 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         // two warps per CTA: the vectors spread over all SMs
         const int bt_warps = (int)std::max<size_t>(1, std::min<size_t>(2, (200 * 1024) / ((size_t)n * sizeof(float))));
         const size_t smem_bt = (size_t)bt_warps * n * sizeof(float);
-        allow_max_smem(k_backtransform);
-        klaunch(ctx, "k_backtransform", k_backtransform, div_up(n, bt_warps), 32 * bt_warps, smem_bt,
-                (const float*)A32, (const float*)tau, n, (const float*)Y, X);
+        auto backtransform = [&](auto kern) {
+            allow_max_smem(kern);
+            klaunch(ctx, "k_backtransform", kern, div_up(n, bt_warps), 32 * bt_warps, smem_bt, (const float*)A32,
+                    (const float*)tau, n, (const float*)Y, X);
+        };
+        if (n <= 32 * 8) backtransform(k_backtransform<8>);
+        else if (n <= 32 * 16) backtransform(k_backtransform<16>);
+        else if (n <= 32 * 24) backtransform(k_backtransform<24>);
+        else backtransform(k_backtransform<0>);
         // binary64 refinement
         if (oa_iters > 0) {
             X2 = dalloc<double>(ctx, nn); R = dalloc<double>(ctx, nn); S = dalloc<double>(ctx, nn);
