@@ -161,13 +161,16 @@ KERNELS = ["k_forms", "k_forms32",
            "k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk", "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk",
            "k_chi0_fft", "k_chi0_fft32", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl",
            "k_bisect", "k_invit", "k_backtransform", "k_oa_stats", "k_oa_E", "k_vertex_contract", "k_sigma_c",
-           "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_to_f32", "k_kernel_spectra"]
+           "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_to_f32", "k_kernel_spectra",
+           "k_cluster_mgs", "k_scale_cols_by", "k_rayleigh_cols", "k_top_indices", "k_gather_cols", "k_ns_coeff",
+           "k_pair_keys", "k_pair_scatter", "k_pair_segments", "k_invert_perm", "k_twiddles", "k_cauchy_table",
+           "k_oa_stats_fin"]
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
 # of the current kernel version on this workload (profiles/k_*_ring12.md);
 # an entry is dropped whenever its kernel changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"k_forms32": 4.772e8}
 
 
 def _panels(n, nb):
@@ -382,6 +385,7 @@ def run_gpu(a):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency_ms": {"p50": pct(batched["lat"], 50), "p99": pct(batched["lat"], 99)},
         "single_stream": {"value": single["value"], "unit": "solves/s", "ms_per_solve": single_ms,
+                          "launches_per_solve": single["launches"] / a.steps,
                           "latency_ms": {"p50": pct(single["lat"], 50), "p99": pct(single["lat"], 99)}},
         "roofline": roof,
         "kernels": kernels,
