@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(IT) k_invit(const float* __restrict__ d, const
 // iteration cannot separate the vectors of an (almost) multiple eigenvalue;
 // Gram-Schmidt turns the differently started vectors into an orthonormal
 // basis of the eigenspace.
-__global__ void __launch_bounds__(256) k_cluster_mgs(const float* __restrict__ lam, int n, float tol,
+__global__ void __launch_bounds__(256) k_cluster_mgs(const float* __restrict__ lam, int n, float tol, int n_keep,
                                                      float* __restrict__ Y) {
     __shared__ float red[33];
     const int i0 = blockIdx.x;
@@ -435,6 +435,7 @@ __global__ void __launch_bounds__(256) k_cluster_mgs(const float* __restrict__ l
     int i1 = i0 + 1;
     while (i1 < n && lam[i1] - lam[i1 - 1] < tol) ++i1;
     if (i1 - i0 < 2) return;
+    if (i1 <= n - n_keep) return;        // cluster entirely among the discarded (smallest) eigenvalues
     for (int i = i0; i < i1; ++i) {
         float* x = Y + (long long)i * n;
         for (int pass = 0; pass < 2; ++pass)
@@ -745,8 +746,10 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         else invit(0.0f);
         // clusters: eigenvalue gaps below which inverse iteration cannot keep
         // the vectors orthogonal in its working precision
+        // (the refinement of the binary64 path works on every vector; without
+        // it only the kept top n_sub matter)
         klaunch(ctx, "k_cluster_mgs", k_cluster_mgs, n, 256, 0, (const float*)lam32, n,
-                (vectors_f64 ? 1e-6f : 1e-4f) * bnd, Y);
+                (vectors_f64 ? 1e-6f : 1e-4f) * bnd, oa_iters > 0 ? n : n_sub, Y);
         // two warps per CTA: the vectors spread over all SMs
         const int bt_warps = (int)std::max<size_t>(1, std::min<size_t>(2, (200 * 1024) / ((size_t)n * sizeof(float))));
         const size_t smem_bt = (size_t)bt_warps * n * sizeof(float);

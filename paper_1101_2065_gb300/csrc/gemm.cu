@@ -2,8 +2,9 @@
 // the plain matrix products of the path: g = X_r^T v X_r and Z = X_r xi
 // lambda^-1/2 (Eqs. projector0, subspace), U = V^EF Zup (Eq. subspace_chi0),
 // q = Zup^T V^{nk}, v V^{nk} (Eq. instantaneous), W = v + Zup chi Zup^T.
-// 64x64 output tile per CTA, K staged by 16 through shared memory, 4x4
-// outputs per thread; binary64 issue rate bounds it on this GPU.
+// 64x64, 32x32 or 16x16 output tile per CTA (chosen per call to balance the
+// SMs), K staged by 16 through shared memory, (BM/16)^2 outputs per thread;
+// binary64 issue rate bounds it on this GPU.
 #include "internal.h"
 
 namespace {
@@ -81,13 +82,21 @@ void gemm_f64(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, double alpha, 
               const double* B, long long ldb, double beta, double* C, long long ldc, int batch, long long sA,
               long long sB, long long sC) {
     if (M <= 0 || N <= 0) return;
-    // 64x64 tiles when they fill the GPU twice over, else 32x32
-    const bool big = (long long)div_up(N, 64) * div_up(M, 64) * batch >= 2LL * ctx->num_sms;
-    const int bm = big ? 64 : 32;
+    // Tile edge: binary64 FMA throughput bounds every SM, so the time is the
+    // work of the busiest SM, ceil(tiles / SMs) * bm^2 (per unit of K); take
+    // the smallest, preferring larger tiles on ties (fewer loads).
+    int bm = 64;
+    long long best = -1;
+    for (int t : {64, 32, 16}) {
+        const long long tiles = (long long)div_up(N, t) * div_up(M, t) * batch;
+        const long long span = (tiles + ctx->num_sms - 1) / ctx->num_sms * t * t;
+        if (best < 0 || span < best) { best = span; bm = t; }
+    }
     dim3 grid(div_up(N, bm), div_up(M, bm), batch);
-    auto kern = big ? ((!ta && !tb) ? k_dgemm<false, false, 64> : (ta && !tb) ? k_dgemm<true, false, 64>
-                     : (!ta && tb) ? k_dgemm<false, true, 64> : k_dgemm<true, true, 64>)
-                    : ((!ta && !tb) ? k_dgemm<false, false, 32> : (ta && !tb) ? k_dgemm<true, false, 32>
-                     : (!ta && tb) ? k_dgemm<false, true, 32> : k_dgemm<true, true, 32>);
+    auto pick = [&](auto k64, auto k32, auto k16) { return bm == 64 ? k64 : bm == 32 ? k32 : k16; };
+    auto kern = (!ta && !tb) ? pick(k_dgemm<false, false, 64>, k_dgemm<false, false, 32>, k_dgemm<false, false, 16>)
+              : (ta && !tb)  ? pick(k_dgemm<true, false, 64>, k_dgemm<true, false, 32>, k_dgemm<true, false, 16>)
+              : (!ta && tb)  ? pick(k_dgemm<false, true, 64>, k_dgemm<false, true, 32>, k_dgemm<false, true, 16>)
+                             : pick(k_dgemm<true, true, 64>, k_dgemm<true, true, 32>, k_dgemm<true, true, 16>);
     klaunch(ctx, "k_dgemm", kern, grid, 256, 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
 }

@@ -55,24 +55,32 @@ __global__ void k_cauchy_table(double2* __restrict__ K, long long dmin, long lon
     K[t] = make_double2(x / den, -eta / den);
 }
 
+// One warp per output point (binary64 runs at 1/64 rate: the sum over the
+// sigma grid is spread over the lanes and all SMs, then reduced in a fixed
+// order).
 __global__ void __launch_bounds__(256) k_sigma_c(const double* __restrict__ sig, int n_sig, int j0, int N, double dw,
                                                  const double2* __restrict__ K, long long dmin, int n_states,
                                                  double2* __restrict__ out) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     const int nk = 2 * N - 1;
     if (t >= (long long)n_states * nk) return;
-    int s = (int)(t / nk);
-    int k = (int)(t % nk) - (N - 1);
+    const int s = (int)(t / nk);
+    const int k = (int)(t % nk) - (N - 1);
     const double* sg = sig + (long long)s * n_sig;
     double re = 0.0, im = 0.0;
-    for (int q = 0; q < n_sig; ++q) {
-        int j = j0 + q;
-        double2 kv = K[(long long)(k - j) - dmin];
-        double v = sg[q];
+    for (int q = lane; q < n_sig; q += 32) {
+        const int j = j0 + q;
+        const double2 kv = K[(long long)(k - j) - dmin];
+        const double v = sg[q];
         re = fma(v, kv.x, re);
         im = fma(v, j >= 0 ? kv.y : -kv.y, im);
     }
-    out[t] = make_double2(dw * re, dw * im);
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) out[t] = make_double2(dw * re, dw * im);
 }
 
 __device__ double block_sum(double v, double* red) {
@@ -207,7 +215,7 @@ void launch_sigma_c(gw_ctx* ctx, gw_sigma* s) {
     long long nd = dmax - dmin + 1;
     double2* K = dalloc<double2>(ctx, nd);
     klaunch(ctx, "k_cauchy_table", k_cauchy_table, div_up(nd, 256), 256, 0, K, dmin, nd, c->grid.d_omega, c->grid.eta);
-    long long tot = (long long)s->n_states * (2 * N - 1);
+    long long tot = (long long)s->n_states * (2 * N - 1) * 32;      // one warp per output
     klaunch(ctx, "k_sigma_c", k_sigma_c, div_up(tot, 256), 256, 0, s->sig, s->n_sig, s->j0, N, c->grid.d_omega, K, dmin,
                                                          s->n_states, s->sigc);
     ctx_free(ctx, K);
