@@ -164,7 +164,7 @@ KERNELS = ["k_forms", "k_forms32",
            "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_to_f32", "k_kernel_spectra",
            "k_cluster_mgs", "k_scale_cols_by", "k_rayleigh_cols", "k_top_indices", "k_gather_cols", "k_ns_coeff",
            "k_pair_keys", "k_pair_scatter", "k_pair_segments", "k_invert_perm", "k_twiddles", "k_cauchy_table",
-           "k_oa_stats_fin"]
+           "k_oa_stats_fin", "k_deposit_syrk", "k_deposit_syrk32"]
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
@@ -203,6 +203,10 @@ def kernel_model(name, mol, grid, n_rank):
     if name.startswith("k_forms"):
         # forward substitution L y = q: n(n-1)/2 complex multiply-adds per right-hand side and frequency
         return (N - 1) * 8.0 * R * n * (n - 1) / 2, "alu", peak
+    if name.startswith("k_deposit_syrk"):
+        # every pair enters two bins (tent): 2 N_pair multiply-adds per element of the packed lower triangle
+        n_pair = int(mol.n_occ) * (int(mol.n_orb) - int(mol.n_occ))
+        return 2.0 * 2 * n_pair * (n * (n + 1) / 2), "alu", peak
     if name.startswith("k_chi0_fft"):
         # per element pair: one forward and two inverse complex FFTs of length L (5 L log2 L flops each)
         pairs = (n * (n + 1) // 2 + 1) // 2

@@ -10,9 +10,12 @@
 //   chi0 = IFFT( FFT(A) C1 - conj(FFT(A)) C2 )[0..n_omega)
 // where C1 = FFT of kap(d) on d in (-(N-1), N-1) (index d mod L) and
 // C2 = FFT of kap(d) on d in [0, 2N-2] (the Hankel sum is a correlation).
-// Two real elements share one forward complex FFT.  The deposit of A_j is
-// fused into the same CTA (the pair segments of each bin are read from U),
-// so A is never written to HBM.
+// Two real elements share one forward complex FFT.  The deposit (a3) is a
+// segmented SYRK over the frequency bins, A_j = U_j^T W_j U_j with U_j the
+// pairs of bins j-1 and j and W_j their tent weights, computed by 64 x 64
+// element tiles (U staged through shared memory, each U value reused by 64
+// outputs) and written once as A[bin][element] (packed lower triangle); the
+// FFT kernel reads its two elements' band from there.
 #include <cmath>
 
 #include "internal.h"
@@ -228,13 +231,86 @@ __device__ __forceinline__ void deposit2(int b, int nb_bins, const int* __restri
         }
 }
 
+// lower-triangular tile index tt -> (I, J), J <= I
+__device__ __forceinline__ void tile_ij(int tt, int& I, int& J) {
+    I = (int)((sqrtf(8.0f * tt + 1.0f) - 1.0f) * 0.5f);
+    while (I * (I + 1) / 2 > tt) --I;
+    while ((I + 1) * (I + 2) / 2 <= tt) ++I;
+    J = tt - I * (I + 1) / 2;
+}
+
+// a3: A[b][e] = sum_p w_bp u_pm u_pn for output bin b (band index; bin
+// j_lo + b), e = m(m+1)/2 + n, n <= m.  Bin b takes the pairs of segment b
+// with weight 2(1 - f_p) and of segment b-1 with weight 2 f_p (tent, spin 2);
+// those pairs are contiguous in the sorted table: [seg[b-1], seg[b+1]).
+// Tile (I, J) of 64 x 64 elements = blockIdx.x, bins [blockIdx.y BC, + BC).
+template <typename R>
+__global__ void __launch_bounds__(256) k_deposit_syrk(const R* __restrict__ Ut, int n_pair, int n_sub,
+                                                      const int* __restrict__ seg, const double* __restrict__ frac,
+                                                      int nb_bins, int BC, long long n_el, R* __restrict__ A) {
+    constexpr int T = 64, KC = 32;
+    __shared__ R Um[KC][T + 1];     // w_p u_pm for the tile's rows m
+    __shared__ R Un[KC][T + 1];     // u_pn for the tile's columns n
+    int I, J;
+    tile_ij(blockIdx.x, I, J);
+    const int m0 = I * T, n0 = J * T;
+    const int band = nb_bins + 1;
+    const int b0 = blockIdx.y * BC, b1 = min(b0 + BC, band);
+    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+    for (int b = b0; b < b1; ++b) {
+        const int lo = seg[b > 0 ? b - 1 : 0], mid = seg[b], hi = seg[b < nb_bins ? b + 1 : nb_bins];
+        R acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = R(0);
+        for (int p0 = lo; p0 < hi; p0 += KC) {
+            __syncthreads();
+            for (int t = tid; t < KC * T; t += blockDim.x) {
+                const int r = t / KC, k = t % KC, p = p0 + k;
+                R um = R(0), un = R(0);
+                if (p < hi) {
+                    const R w = R(p < mid ? 2.0 * frac[p] : 2.0 * (1.0 - frac[p]));
+                    if (m0 + r < n_sub) um = w * Ut[(long long)(m0 + r) * n_pair + p];
+                    if (n0 + r < n_sub) un = Ut[(long long)(n0 + r) * n_pair + p];
+                }
+                Um[k][r] = um;
+                Un[k][r] = un;
+            }
+            __syncthreads();
+            const int kc = min(KC, hi - p0);
+            for (int k = 0; k < kc; ++k) {
+                R a[4], c[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = Um[k][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) c[j] = Un[k][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], c[j], acc[i][j]);
+            }
+        }
+        R* Ab = A + (long long)b * n_el;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int m = m0 + ty + 16 * i;
+            if (m >= n_sub) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = n0 + tx + 16 * j;
+                if (n <= m) Ab[(long long)m * (m + 1) / 2 + n] = acc[i][j];
+            }
+        }
+    }
+}
+
 template <typename C> struct Real;
 template <> struct Real<double2> { typedef double T; static __device__ double2 make(double a, double b) { return make_double2(a, b); } };
 template <> struct Real<float2> { typedef float T; static __device__ float2 make(float a, float b) { return make_float2(a, b); } };
 
 template <typename C>
-__global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __restrict__ Ut, int n_pair, int n_sub,
-                                                  const int* __restrict__ seg, const double* __restrict__ frac,
+__global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __restrict__ A, int n_sub,
                                                   int j_lo, int nb_bins, int N, int logL,
                                                   const C* __restrict__ tw, const C* __restrict__ C1,
                                                   const C* __restrict__ C2, C* __restrict__ chi0) {
@@ -260,9 +336,8 @@ __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __r
         for (int d = threadIdx.x; d < L; d += blockDim.x) B0[d] = Real<C>::make(R(0), R(0));
         __syncthreads();
         for (int b = threadIdx.x; b < band; b += blockDim.x) {
-            R a1, a2;
-            deposit2<R>(b, nb_bins, seg, frac, Ut, n_pair, m1, n1, m2, n2, a1, a2);
-            B0[j_lo + b] = Real<C>::make(a1, two ? a2 : R(0));
+            const R* Ab = A + (long long)b * n_el + 2 * g;
+            B0[j_lo + b] = Real<C>::make(Ab[0], two ? Ab[1] : R(0));
         }
         __syncthreads();
         C* Zb = fft_smem(B0, B1, L, logL, (const C*)tws, false);
@@ -339,6 +414,18 @@ void launch_fft_tables(gw_ctx* ctx, gw_chi0* c) {
     klaunch(ctx, "k_kernel_spectra", k_kernel_spectra, 2, 256, smem, c->tw, N, c->logL, c->grid.d_omega, c->grid.eta, c->C1, c->C2);
 }
 
+template <typename R>
+static void deposit(gw_ctx* ctx, const gw_chi0* c, const R* Ut, R* A, long long n_el) {
+    const int n = c->n_sub, band = c->nb_bins + 1;
+    const int nt = div_up(n, 64), tiles = nt * (nt + 1) / 2;
+    // bins per CTA: about eight CTAs per SM in all
+    const int BC = std::max(1, (int)std::min<long long>(band, (long long)tiles * band / (8LL * ctx->num_sms)));
+    const int nbc = div_up(band, BC);
+    if (nbc > 65535) gw_throw(GW_ERR_INVALID_ARG, "spectral band too wide for the deposit kernel");
+    klaunch(ctx, sizeof(R) == 4 ? "k_deposit_syrk32" : "k_deposit_syrk", k_deposit_syrk<R>, dim3(tiles, nbc), 256, 0,
+            Ut, c->n_pair, n, (const int*)c->seg, (const double*)c->pFrac, c->nb_bins, BC, n_el, A);
+}
+
 void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
     const int L = c->L, N = c->grid.n_omega, n = c->n_sub;
     const bool f32 = c->prec == GW_MIXED;
@@ -346,8 +433,10 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
     size_t smem = (3 * (size_t)L + pass_twiddle_count(c->logL)) * csz;
     if (smem > 227 * 1024) gw_throw(GW_ERR_INVALID_ARG, "n_omega too large for the FFT kernel");
     int per_sm = std::max(1, (int)((228 * 1024) / (smem + 1024)));
-    long long n_grp = ((long long)n * (n + 1) / 2 + 1) / 2;
+    const long long n_el = (long long)n * (n + 1) / 2;
+    long long n_grp = (n_el + 1) / 2;
     int grid = (int)std::min<long long>(n_grp, (long long)ctx->num_sms * per_sm);
+    const size_t band = (size_t)c->nb_bins + 1;
     if (f32) {
         c->Ut32 = dalloc<float>(ctx, (size_t)n * c->n_pair);
         c->tw32 = dalloc<float2>(ctx, L / 2);
@@ -357,17 +446,31 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
         launch_to_f32(ctx, (const double*)c->tw, (float*)c->tw32, L);
         launch_to_f32(ctx, (const double*)c->C1, (float*)c->C1_32, 2LL * L);
         launch_to_f32(ctx, (const double*)c->C2, (float*)c->C2_32, 2LL * L);
-        c->chi0_32 = dalloc<float2>(ctx, (size_t)N * n * n);
-        allow_max_smem(k_chi0_fft<float2>);
-        klaunch(ctx, "k_chi0_fft32", k_chi0_fft<float2>, grid, 256, smem, (const float*)c->Ut32, c->n_pair, n,
-                (const int*)c->seg, (const double*)c->pFrac, c->j_lo, c->nb_bins, N, c->logL,
-                (const float2*)c->tw32, (const float2*)c->C1_32, (const float2*)c->C2_32, c->chi0_32);
+        float* A = dalloc<float>(ctx, band * n_el);
+        try {
+            deposit<float>(ctx, c, c->Ut32, A, n_el);
+            c->chi0_32 = dalloc<float2>(ctx, (size_t)N * n * n);
+            allow_max_smem(k_chi0_fft<float2>);
+            klaunch(ctx, "k_chi0_fft32", k_chi0_fft<float2>, grid, 256, smem, (const float*)A, n, c->j_lo, c->nb_bins,
+                    N, c->logL, (const float2*)c->tw32, (const float2*)c->C1_32, (const float2*)c->C2_32, c->chi0_32);
+        } catch (...) {
+            ctx_free(ctx, A);
+            throw;
+        }
+        ctx_free(ctx, A);
     } else {
-        c->chi0 = dalloc<double2>(ctx, (size_t)N * n * n);
-        allow_max_smem(k_chi0_fft<double2>);
-        klaunch(ctx, "k_chi0_fft", k_chi0_fft<double2>, grid, 256, smem, (const double*)c->Ut, c->n_pair, n,
-                (const int*)c->seg, (const double*)c->pFrac, c->j_lo, c->nb_bins, N, c->logL,
-                (const double2*)c->tw, (const double2*)c->C1, (const double2*)c->C2, c->chi0);
+        double* A = dalloc<double>(ctx, band * n_el);
+        try {
+            deposit<double>(ctx, c, c->Ut, A, n_el);
+            c->chi0 = dalloc<double2>(ctx, (size_t)N * n * n);
+            allow_max_smem(k_chi0_fft<double2>);
+            klaunch(ctx, "k_chi0_fft", k_chi0_fft<double2>, grid, 256, smem, (const double*)A, n, c->j_lo, c->nb_bins,
+                    N, c->logL, (const double2*)c->tw, (const double2*)c->C1, (const double2*)c->C2, c->chi0);
+        } catch (...) {
+            ctx_free(ctx, A);
+            throw;
+        }
+        ctx_free(ctx, A);
     }
 }
 
