@@ -421,27 +421,74 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
         } else {
             const int nr = std::min(n_pair, std::max(5 * n_orb, n_sub));
             c->n_rank = nr;
-            T1 = dalloc<double>(ctx, (size_t)n_prod * nr);
-            g = dalloc<double>(ctx, (size_t)nr * nr);
-            // T1 = v X_r, g = X_r^T v X_r  (X_r = first nr columns of VEFt)
-            gemm_f64(ctx, false, false, n_prod, nr, n_prod, 1.0, mol->v, n_prod, VEFt, n_pair, 0.0, T1, nr);
-            gemm_f64(ctx, true, false, nr, nr, n_prod, 1.0, VEFt, n_pair, T1, nr, 0.0, g, nr);
             Bsel = dalloc<double>(ctx, (size_t)nr * n_sub);
-            // binary64: refine to working accuracy; mixed: binary64 Rayleigh quotients of
-            // the binary32 vectors, no refinement (1 meV bar met with margin)
-            if (prec == GW_FP64) eigh_top_scaled(ctx, g, nr, n_sub, 6, 1e-13, true, Bsel);
-            else eigh_top_scaled(ctx, g, nr, n_sub, 0, 0.0, false, Bsel);
-            gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, T1, nr, Bsel, n_sub, 0.0, c->Zup, n_sub);
-            // Z = X_r Bsel is only read back: keep its factors, form it on request
-            c->Xr = dalloc<double>(ctx, (size_t)n_prod * nr);
-            CUDA_CHECK(cudaMemcpy2DAsync(c->Xr, sizeof(double) * nr, VEFt, sizeof(double) * n_pair, sizeof(double) * nr,
-                                         n_prod, cudaMemcpyDeviceToDevice, ctx->stream));
-            c->Bsel = Bsel;
-            Bsel = nullptr;
+            if (prec == GW_FP64) {
+                T1 = dalloc<double>(ctx, (size_t)n_prod * nr);
+                g = dalloc<double>(ctx, (size_t)nr * nr);
+                // T1 = v X_r, g = X_r^T v X_r  (X_r = first nr columns of VEFt)
+                gemm_f64(ctx, false, false, n_prod, nr, n_prod, 1.0, mol->v, n_prod, VEFt, n_pair, 0.0, T1, nr);
+                gemm_f64(ctx, true, false, nr, nr, n_prod, 1.0, VEFt, n_pair, T1, nr, 0.0, g, nr);
+                // binary32 start refined to binary64 accuracy
+                eigh_top_scaled(ctx, g, nullptr, nr, n_sub, 6, 1e-13, true, Bsel);
+                gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, T1, nr, Bsel, n_sub, 0.0, c->Zup, n_sub);
+                // Z = X_r Bsel is only read back: keep its factors, form it on request
+                c->Xr = dalloc<double>(ctx, (size_t)n_prod * nr);
+                CUDA_CHECK(cudaMemcpy2DAsync(c->Xr, sizeof(double) * nr, VEFt, sizeof(double) * n_pair,
+                                             sizeof(double) * nr, n_prod, cudaMemcpyDeviceToDevice, ctx->stream));
+                c->Bsel = Bsel;
+                Bsel = nullptr;
+            } else {
+                // mixed: g only feeds the binary32 eigensolver, so it is formed in
+                // binary32; the basis Z = X_r B, Zup = v Z is formed in binary64
+                // from the kept (re-orthonormalised) vectors and scaled by the
+                // binary64 Rayleigh quotients Z_j^T v Z_j, so Z^T v Z has a unit
+                // diagonal to binary64 accuracy (no binary64 refinement)
+                float* v32 = dalloc<float>(ctx, (size_t)n_prod * n_prod);
+                float* X32 = dalloc<float>(ctx, (size_t)n_prod * nr);
+                float* T32 = dalloc<float>(ctx, (size_t)n_prod * nr);
+                float* g32 = dalloc<float>(ctx, (size_t)nr * nr);
+                try {
+                    launch_to_f32(ctx, mol->v, v32, (long long)n_prod * n_prod);
+                    launch_f64_to_f32_2d(ctx, VEFt, n_pair, n_prod, nr, X32);
+                    gemm_f32(ctx, false, false, n_prod, nr, n_prod, 1.f, v32, n_prod, X32, nr, 0.f, T32, nr);
+                    gemm_f32(ctx, true, false, nr, nr, n_prod, 1.f, X32, nr, T32, nr, 0.f, g32, nr);
+                    ctx_free(ctx, v32); v32 = nullptr;
+                    ctx_free(ctx, X32); X32 = nullptr;
+                    ctx_free(ctx, T32); T32 = nullptr;
+                    eigh_top_scaled(ctx, nullptr, g32, nr, n_sub, 0, 0.0, false, Bsel);
+                } catch (...) {
+                    ctx_free(ctx, v32); ctx_free(ctx, X32); ctx_free(ctx, T32); ctx_free(ctx, g32);
+                    throw;
+                }
+                ctx_free(ctx, g32);
+                c->Z = dalloc<double>(ctx, (size_t)n_prod * n_sub);
+                gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, VEFt, n_pair, Bsel, n_sub, 0.0, c->Z, n_sub);
+                gemm_f64(ctx, false, false, n_prod, n_sub, n_prod, 1.0, mol->v, n_prod, c->Z, n_sub, 0.0, c->Zup,
+                         n_sub);
+                basis_rayleigh_scale(ctx, c->Z, c->Zup, n_prod, n_sub);
+            }
         }
-        // a2: U^T = Zup^T V^EF  -> [n_sub][n_pair]
-        c->Ut = dalloc<double>(ctx, (size_t)n_sub * n_pair);
-        gemm_f64(ctx, true, false, n_sub, n_pair, n_prod, 1.0, c->Zup, n_sub, VEFt, n_pair, 0.0, c->Ut, n_pair);
+        // a2: U^T = Zup^T V^EF  -> [n_sub][n_pair]; the mixed path only ever
+        // uses it in binary32, so it is formed in binary32 there
+        if (prec == GW_MIXED) {
+            float* Zup32 = dalloc<float>(ctx, (size_t)n_prod * n_sub);
+            float* V32 = nullptr;
+            try {
+                V32 = dalloc<float>(ctx, (size_t)n_prod * n_pair);
+                launch_to_f32(ctx, c->Zup, Zup32, (long long)n_prod * n_sub);
+                launch_to_f32(ctx, VEFt, V32, (long long)n_prod * n_pair);
+                c->Ut32 = dalloc<float>(ctx, (size_t)n_sub * n_pair);
+                gemm_f32(ctx, true, false, n_sub, n_pair, n_prod, 1.f, Zup32, n_sub, V32, n_pair, 0.f, c->Ut32, n_pair);
+            } catch (...) {
+                ctx_free(ctx, Zup32); ctx_free(ctx, V32);
+                throw;
+            }
+            ctx_free(ctx, Zup32);
+            ctx_free(ctx, V32);
+        } else {
+            c->Ut = dalloc<double>(ctx, (size_t)n_sub * n_pair);
+            gemm_f64(ctx, true, false, n_sub, n_pair, n_prod, 1.0, c->Zup, n_sub, VEFt, n_pair, 0.0, c->Ut, n_pair);
+        }
         ctx_free(ctx, VEFt); VEFt = nullptr;
         ctx_free(ctx, T1); T1 = nullptr; ctx_free(ctx, g); g = nullptr;
         ctx_free(ctx, Bsel); Bsel = nullptr;
@@ -706,7 +753,14 @@ extern "C" gw_status gw_chi0_copy_U(gw_ctx* ctx, const gw_chi0* c, double* U) {
     API_BEGIN(ctx)
     CUDA_CHECK(cudaSetDevice(ctx->device));
     std::vector<double> t((size_t)c->n_sub * c->n_pair);
-    download(ctx, t.data(), c->Ut, t.size());
+    if (c->Ut) {
+        download(ctx, t.data(), c->Ut, t.size());
+    } else {                   // mixed path: binary32 only
+        std::vector<float> t32(t.size());
+        download(ctx, t32.data(), c->Ut32, t32.size());
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        for (size_t i = 0; i < t.size(); ++i) t[i] = t32[i];
+    }
     CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
     for (int m = 0; m < c->n_sub; ++m)
         for (int p = 0; p < c->n_pair; ++p) U[(size_t)p * c->n_sub + m] = t[(size_t)m * c->n_pair + p];

@@ -397,10 +397,19 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, lo
     if (t < n) b[t] = (float)a[t];
 }
 
+__global__ void k_to_f64(const float* __restrict__ a, double* __restrict__ b, long long n) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = (double)a[t];
+}
+
 }  // namespace
 
 void launch_to_f32(gw_ctx* ctx, const double* a, float* b, long long n) {
     if (n > 0) klaunch(ctx, "k_to_f32", k_to_f32, div_up(n, 256), 256, 0, a, b, n);
+}
+
+void launch_to_f64(gw_ctx* ctx, const float* a, double* b, long long n) {
+    if (n > 0) klaunch(ctx, "k_to_f64", k_to_f64, div_up(n, 256), 256, 0, a, b, n);
 }
 
 void launch_fft_tables(gw_ctx* ctx, gw_chi0* c) {
@@ -438,11 +447,13 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
     int grid = (int)std::min<long long>(n_grp, (long long)ctx->num_sms * per_sm);
     const size_t band = (size_t)c->nb_bins + 1;
     if (f32) {
-        c->Ut32 = dalloc<float>(ctx, (size_t)n * c->n_pair);
+        if (!c->Ut32) {        // U^T in binary32 (normally produced directly by the a2 product)
+            c->Ut32 = dalloc<float>(ctx, (size_t)n * c->n_pair);
+            launch_to_f32(ctx, c->Ut, c->Ut32, (long long)n * c->n_pair);
+        }
         c->tw32 = dalloc<float2>(ctx, L / 2);
         c->C1_32 = dalloc<float2>(ctx, L);
         c->C2_32 = dalloc<float2>(ctx, L);
-        launch_to_f32(ctx, c->Ut, c->Ut32, (long long)n * c->n_pair);
         launch_to_f32(ctx, (const double*)c->tw, (float*)c->tw32, L);
         launch_to_f32(ctx, (const double*)c->C1, (float*)c->C1_32, 2LL * L);
         launch_to_f32(ctx, (const double*)c->C2, (float*)c->C2_32, 2LL * L);
@@ -477,6 +488,20 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
 void launch_spectral_readback(gw_ctx* ctx, const gw_chi0* c, int j0, int nj, double* A) {
     long long tot = (long long)c->n_sub * c->n_sub * nj;
     if (tot == 0) return;
-    klaunch(ctx, "k_spectral_readback", k_spectral_readback, div_up(tot, 256), 256, 0, c->Ut, c->n_pair, c->n_sub, c->seg, c->pFrac,
-                                                                   c->j_lo, c->nb_bins, j0, nj, A);
+    const double* Ut = c->Ut;
+    double* tmp = nullptr;
+    if (!Ut) {                 // mixed path: U^T exists in binary32 only
+        const long long nu = (long long)c->n_sub * c->n_pair;
+        tmp = dalloc<double>(ctx, nu);
+        launch_to_f64(ctx, c->Ut32, tmp, nu);
+        Ut = tmp;
+    }
+    try {
+        klaunch(ctx, "k_spectral_readback", k_spectral_readback, div_up(tot, 256), 256, 0, Ut, c->n_pair, c->n_sub,
+                c->seg, c->pFrac, c->j_lo, c->nb_bins, j0, nj, A);
+    } catch (...) {
+        ctx_free(ctx, tmp);
+        throw;
+    }
+    ctx_free(ctx, tmp);
 }

@@ -661,8 +661,28 @@ __global__ void k_scale_cols(double* __restrict__ B, int n, int n_sub, const dou
 void launch_to_f32(gw_ctx* ctx, const double* a, float* b, long long n);
 
 // g (n x n, binary64, symmetric) -> B (n x n_sub) = xi_top lambda_top^-1/2
-void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iters, double oa_tol, bool vectors_f64,
-                     double* B) {
+// Z[:, j] and Zup[:, j] (rows x n_sub, row-major) scaled by lambda_j^-1/2,
+// lambda_j = Z[:, j]^T Zup[:, j] (= Z_j^T v Z_j when Zup = v Z), so that
+// Z^T v Z has a unit diagonal in binary64; flags a rank-deficient basis.
+void basis_rayleigh_scale(gw_ctx* ctx, double* Z, double* Zup, int rows, int n_sub) {
+    double* lam = dalloc<double>(ctx, n_sub);
+    try {
+        klaunch(ctx, "k_rayleigh_cols", k_rayleigh_cols, n_sub, 256, 0, (const double*)Z, (const double*)Zup, rows,
+                n_sub, lam);
+        klaunch(ctx, "k_scale_cols_by", k_scale_cols_by, div_up((long long)rows * n_sub, 256), 256, 0, Z, rows, n_sub,
+                (const double*)lam, ctx->d_status);
+        klaunch(ctx, "k_scale_cols_by", k_scale_cols_by, div_up((long long)rows * n_sub, 256), 256, 0, Zup, rows,
+                n_sub, (const double*)lam, ctx->d_status);
+    } catch (...) {
+        ctx_free(ctx, lam);
+        throw;
+    }
+    ctx_free(ctx, lam);
+}
+
+void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int n_sub, int oa_iters, double oa_tol,
+                     bool vectors_f64, double* B) {
+    if (!g && oa_iters > 0) gw_throw(GW_ERR_INVALID_ARG, "eigensolver refinement needs the binary64 matrix");
     const long long nn = (long long)n * n;
     float* A32 = nullptr; float *d = nullptr, *e = nullptr, *tau = nullptr, *lam32 = nullptr, *Y = nullptr;
     double *X = nullptr, *X2 = nullptr, *R = nullptr, *S = nullptr, *T = nullptr, *E = nullptr, *lam = nullptr;
@@ -684,7 +704,8 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         lam32 = dalloc<float>(ctx, n);
         Y = dalloc<float>(ctx, nn);
         X = dalloc<double>(ctx, nn);
-        launch_to_f32(ctx, g, A32, nn);
+        if (g32) CUDA_CHECK(cudaMemcpyAsync(A32, g32, sizeof(float) * nn, cudaMemcpyDeviceToDevice, ctx->stream));
+        else launch_to_f32(ctx, g, A32, nn);
         const int rows = (n + CL - 1) / CL;
         const size_t smem_cl = sizeof(float) * ((size_t)rows * n + 5 * (size_t)n);
         if (smem_cl <= 220 * 1024) {
@@ -810,7 +831,10 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iter
         gemm_f64(ctx, true, false, n_sub, n_sub, n, 1.0, Bt, n_sub, Bt, n_sub, 0.0, G, n_sub);
         klaunch(ctx, "k_ns_coeff", k_ns_coeff, div_up((long long)n_sub * n_sub, 256), 256, 0, G, n_sub);
         gemm_f64(ctx, false, false, n, n_sub, n_sub, 1.0, Bt, n_sub, G, n_sub, 0.0, B, n_sub);
-        if (oa_iters == 0) {
+        if (oa_iters == 0 && !g) {
+            // no binary64 g: B is returned orthonormal and unscaled (the caller
+            // scales the basis it builds from it)
+        } else if (oa_iters == 0) {
             gemm_f64(ctx, false, false, n, n_sub, n, 1.0, g, n, B, n_sub, 0.0, T, n_sub);     // g B
             klaunch(ctx, "k_rayleigh_cols", k_rayleigh_cols, n_sub, 256, 0, (const double*)B, (const double*)T, n,
                     n_sub, lam);

@@ -175,13 +175,18 @@ void gemm_f64(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, double alpha,
 // linalg.cu
 void cholesky_lower(gw_ctx* ctx, double* A, int n);          // in place, zeroes upper
 // eigh.cu: B = xi lambda^-1/2 for the n_sub largest eigenpairs of g
-void eigh_top_scaled(gw_ctx* ctx, const double* g, int n, int n_sub, int oa_iters, double oa_tol, bool vectors_f64,
-                     double* B);
+void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int n_sub, int oa_iters, double oa_tol,
+                     bool vectors_f64, double* B);
+void basis_rayleigh_scale(gw_ctx* ctx, double* Z, double* Zup, int rows, int n_sub);
 // chi0.cu
 void launch_fft_tables(gw_ctx* ctx, gw_chi0* c);
 void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c);
 void launch_spectral_readback(gw_ctx* ctx, const gw_chi0* c, int j0, int nj, double* A);
 void launch_to_f32(gw_ctx* ctx, const double* a, float* b, long long n);
+void launch_to_f64(gw_ctx* ctx, const float* a, double* b, long long n);
+void launch_f64_to_f32_2d(gw_ctx* ctx, const double* a, long long lda, int rows, int cols, float* b);
+void gemm_f32(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, float alpha, const float* A, long long lda,
+              const float* B, long long ldb, float beta, float* C, long long ldc);
 // screen.cu
 size_t ldlt_linv_bytes(int n, int n_omega, gw_precision prec);
 void launch_ldlt(gw_ctx* ctx, gw_W* W);
