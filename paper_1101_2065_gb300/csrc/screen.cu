@@ -523,6 +523,122 @@ __global__ void __launch_bounds__(320, 1) k_forms(const C* __restrict__ fac, con
     }
 }
 
+// Batched forward substitution for large n (the right-hand-side chunk no
+// longer fits on chip): Y [nb][n][R] lives in HBM for a batch of nb
+// frequencies k = kbase + z, and every panel takes two launches over the
+// whole batch.  k_formsb_diag: y_b = L11^-1 y_b for 64 right-hand sides per
+// CTA (one column per thread group, the column's NB values in registers),
+// y_i^2/d_i added to the binary64 sums acc [nb][R]; the last panel writes
+// c.  k_formsb_update: Y_rest -= L_rest,b y_b by T x T tiles.  Before the
+// first update the right-hand sides are the real q (Q [n][R]).
+template <typename C>
+__global__ void __launch_bounds__(256) k_formsb_diag(const C* __restrict__ fac, const C* __restrict__ linv, int n,
+                                                     int N, const double* __restrict__ Q, int R, C* __restrict__ Y,
+                                                     double* __restrict__ acc, double* __restrict__ c, int k0,
+                                                     int kbase) {
+    typedef typename CT<C>::R T;
+    constexpr int NB = Tile<C>::NB, G = 4, RPT = NB / G;     // row groups, rows per thread
+    __shared__ C sLi[NB][NB];
+    __shared__ C sD[NB];
+    __shared__ double red[G][64];
+    const int tid = threadIdx.x, cl = tid % 64, g = tid / 64;
+    const int z = blockIdx.y, k = kbase + z, col = blockIdx.x * 64 + cl;
+    const C* F = fac + (long long)k * n * n;
+    C* Yk = Y + (long long)z * n * R;
+    const int kb = min(NB, n - k0), nblk = (n + NB - 1) / NB;
+    const bool last = k0 + kb == n;
+    const C* Li = linv + ((long long)k * nblk + k0 / NB) * NB * NB;
+    for (int t = tid; t < NB * NB; t += blockDim.x) sLi[t / NB][t % NB] = Li[t];
+    if (tid < NB) sD[tid] = tid < kb ? F[(long long)(k0 + tid) * n + k0 + tid] : CT<C>::mk(T(1), T(0));
+    C y[NB];
+    const bool live = col < R;
+#pragma unroll
+    for (int p = 0; p < NB; ++p) {
+        const long long o = (long long)(k0 + p) * R + col;
+        y[p] = (live && p < kb) ? (k0 == 0 ? CT<C>::mk(T(Q[o]), T(0)) : Yk[o]) : CT<C>::mk(T(0), T(0));
+    }
+    __syncthreads();                    // every column read before any row is rewritten
+    C part = CT<C>::mk(T(0), T(0));
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int i = g + G * q;
+        C v = CT<C>::mk(T(0), T(0));
+#pragma unroll
+        for (int p = 0; p < NB; ++p) v = cfma(sLi[i][p], y[p], v);
+        if (live && i < kb) {
+            if (!last) Yk[(long long)(k0 + i) * R + col] = v;
+            part = cadd(part, cdiv(cmul(v, v), sD[i]));
+        }
+    }
+    red[g][cl] = (double)part.y;
+    __syncthreads();
+    if (g == 0 && live) {
+        double s = red[0][cl] + red[1][cl] + red[2][cl] + red[3][cl];
+        double* a = acc + (long long)z * R + col;
+        s += k0 == 0 ? 0.0 : *a;
+        if (last) {
+            c[(long long)col * N + k] = -s / M_PI;
+            if (k == 1) c[(long long)col * N] = 0.0;
+        } else {
+            *a = s;
+        }
+    }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_formsb_update(const C* __restrict__ fac, int n, const double* __restrict__ Q,
+                                                       int R, C* __restrict__ Y, int k0, int kbase) {
+    typedef typename CT<C>::R T;
+    constexpr int NB = Tile<C>::NB, TT = Tile<C>::T, TA = Tile<C>::A;
+    __shared__ C sL[TT][NB + 1];
+    __shared__ C sY[NB][TT];
+    const int tid = threadIdx.x, z = blockIdx.z, k = kbase + z;
+    const C* F = fac + (long long)k * n * n;
+    C* Yk = Y + (long long)z * n * R;
+    const int kb = min(NB, n - k0), k1 = k0 + kb;
+    const int r0 = k1 + blockIdx.x * TT, c0 = blockIdx.y * TT;
+    for (int t = tid; t < TT * NB; t += blockDim.x) {
+        const int rr = t / NB, p = t % NB;
+        sL[rr][p] = (p < kb && r0 + rr < n) ? F[(long long)(r0 + rr) * n + k0 + p] : CT<C>::mk(T(0), T(0));
+    }
+    for (int t = tid; t < NB * TT; t += blockDim.x) {
+        const int p = t / TT, cc = t % TT;
+        sY[p][cc] = (p < kb && c0 + cc < R) ? Yk[(long long)(k0 + p) * R + c0 + cc] : CT<C>::mk(T(0), T(0));
+    }
+    __syncthreads();
+    const int ty = tid / 16, tx = tid % 16;
+    C acc[TA][TA];
+#pragma unroll
+    for (int a = 0; a < TA; ++a)
+#pragma unroll
+        for (int b = 0; b < TA; ++b) acc[a][b] = CT<C>::mk(T(0), T(0));
+#pragma unroll 8
+    for (int p = 0; p < NB; ++p) {
+        C l[TA], yv[TA];
+#pragma unroll
+        for (int a = 0; a < TA; ++a) l[a] = sL[ty + 16 * a][p];
+#pragma unroll
+        for (int b = 0; b < TA; ++b) yv[b] = sY[p][tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < TA; ++a)
+#pragma unroll
+            for (int b = 0; b < TA; ++b) acc[a][b] = cfma(l[a], yv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < TA; ++a) {
+        const int i = r0 + ty + 16 * a;
+        if (i >= n) continue;
+#pragma unroll
+        for (int b = 0; b < TA; ++b) {
+            const int cc = c0 + tx + 16 * b;
+            if (cc >= R) continue;
+            const long long o = (long long)i * R + cc;
+            const C src = k0 == 0 ? CT<C>::mk(T(Q[o]), T(0)) : Yk[o];
+            Yk[o] = csub(src, acc[a][b]);
+        }
+    }
+}
+
 // out = M_k^-1 - 1 = chi^RPA_k from the factors (one CTA; test read-back).
 __global__ void __launch_bounds__(256) k_ldlt_inverse(const double2* __restrict__ F, int n, double2* __restrict__ X) {
     // column c of X solves L D L^T x = e_c
@@ -583,14 +699,50 @@ void launch_ldlt(gw_ctx* ctx, gw_W* W) {
 }
 
 template <typename C>
+static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, const double* Q, int R,
+                          double* cout, const char* const names[2]) {
+    constexpr int NB = Tile<C>::NB, TT = Tile<C>::T;
+    // frequencies per batch: Y [nb][n][R] within about 2 GB
+    const size_t per = sizeof(C) * (size_t)n * R;
+    const int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)(N - 1), ((size_t)2 << 30) / per));
+    if (nb > 65535 || div_up(R, 64) > 65535) gw_throw(GW_ERR_INVALID_ARG, "forms batch too large");
+    C* Y = dalloc<C>(ctx, (size_t)nb * n * R);
+    double* acc = nullptr;
+    try {
+        acc = dalloc<double>(ctx, (size_t)nb * R);
+        for (int kbase = 1; kbase < N; kbase += nb) {
+            const int nbb = std::min(nb, N - kbase);
+            for (int k0 = 0; k0 < n; k0 += NB) {
+                klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R, Y, acc,
+                        cout, k0, kbase);
+                const int m = n - std::min(n, k0 + NB);
+                if (m == 0) break;
+                klaunch(ctx, names[1], k_formsb_update<C>, dim3(div_up(m, TT), div_up(R, TT), nbb), 256, 0, fac, n, Q, R,
+                        Y, k0, kbase);
+            }
+        }
+    } catch (...) {
+        ctx_free(ctx, Y);
+        ctx_free(ctx, acc);
+        throw;
+    }
+    ctx_free(ctx, Y);
+    ctx_free(ctx, acc);
+}
+
+template <typename C>
 static void forms_run(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, const double* Q, int R, double* cout,
-                      const char* name) {
+                      const char* name, const char* const bnames[2]) {
     constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, LP = tile_pitch<C>();
     const size_t fixed = sizeof(C) * ((size_t)2 * FT * LP + 2 * NB * NB + 2 * NB);
     const size_t budget = 224 * 1024;
     // columns per CTA: at most 320 / FG threads, and Y [n][RC] must fit
     int rc_max = (int)std::min<size_t>(320 / FG, budget > fixed ? (budget - fixed) / (sizeof(C) * (size_t)n) : 0);
-    if (rc_max < 1) gw_throw(GW_ERR_INVALID_ARG, "n_sub too large for the forms kernel");
+    // too few resident right-hand sides per CTA: Y in HBM instead
+    if (rc_max < std::min(R, 48)) {
+        forms_batched<C>(ctx, fac, linv, n, N, Q, R, cout, bnames);
+        return;
+    }
     const int chunks = div_up(R, rc_max);
     const int RC = div_up(R, chunks);
     const size_t smem = fixed + std::max(sizeof(C) * (size_t)n * RC, sizeof(double) * FG * (size_t)RC);
@@ -602,10 +754,12 @@ static void forms_run(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, co
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
+    static const char* const b32[2] = {"k_forms32_diag", "k_forms32_update"};
+    static const char* const b64[2] = {"k_forms_diag", "k_forms_update"};
     if (c->prec == GW_MIXED)
-        forms_run<float2>(ctx, W->fac32, (const float2*)W->linv, n, N, Q, R, cout, "k_forms32");
+        forms_run<float2>(ctx, W->fac32, (const float2*)W->linv, n, N, Q, R, cout, "k_forms32", b32);
     else
-        forms_run<double2>(ctx, W->fac, (const double2*)W->linv, n, N, Q, R, cout, "k_forms");
+        forms_run<double2>(ctx, W->fac, (const double2*)W->linv, n, N, Q, R, cout, "k_forms", b64);
 }
 
 void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work) {
