@@ -534,8 +534,8 @@ static gw_W* screen_W(gw_ctx* ctx, const gw_chi0* c) {
     w->ctx = ctx; w->chi0 = c;
     const size_t n = c->n_sub, N = c->grid.n_omega;
     try {
-        if (c->prec == GW_MIXED) w->fac32 = dalloc<float2>(ctx, N * n * n);
-        else w->fac = dalloc<double2>(ctx, N * n * n);
+        if (c->prec == GW_MIXED) w->fac32 = dalloc<float2>(ctx, N * (size_t)tri(n));     // packed lower triangles
+        else w->fac = dalloc<double2>(ctx, N * (size_t)tri(n));
         w->linv = ctx_alloc(ctx, ldlt_linv_bytes((int)n, (int)N, c->prec));
         w->piv = dalloc<double>(ctx, 2 * N);      // [N) ratios, [N, 2N) running min |d|
         launch_ldlt(ctx, w);
@@ -788,23 +788,24 @@ extern "C" gw_status gw_chi0_copy(gw_ctx* ctx, const gw_chi0* c, int k0, int nk,
     API_BEGIN(ctx)
     CUDA_CHECK(cudaSetDevice(ctx->device));
     REQUIRE(nk >= 0 && k0 >= 0 && k0 + nk <= c->grid.n_omega, "frequency range outside the grid");
-    const size_t n = c->n_sub;
-    std::vector<double2> t(nk * n * n);
+    const size_t n = c->n_sub, pk = (size_t)tri(n);
+    std::vector<double2> t(nk * pk);
     if (c->prec == GW_MIXED && c->chi0_32) {
         std::vector<float2> t32(t.size());
-        download(ctx, t32.data(), c->chi0_32 + (size_t)k0 * n * n, t32.size());
+        download(ctx, t32.data(), c->chi0_32 + (size_t)k0 * pk, t32.size());
         CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
         for (size_t i = 0; i < t.size(); ++i) t[i] = make_double2(t32[i].x, t32[i].y);
     } else {
-        download(ctx, t.data(), c->chi0 + (size_t)k0 * n * n, t.size());
+        download(ctx, t.data(), c->chi0 + (size_t)k0 * pk, t.size());
         CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
     }
+    // packed lower triangle -> full symmetric matrices
     double2* o = reinterpret_cast<double2*>(out);
     for (int k = 0; k < nk; ++k)
         for (size_t i = 0; i < n; ++i)
             for (size_t j = 0; j < n; ++j) {
                 size_t a = std::max(i, j), b = std::min(i, j);
-                o[(k * n + i) * n + j] = t[(k * n + a) * n + b];
+                o[(k * n + i) * n + j] = t[k * pk + (size_t)tri(a) + b];
             }
     API_END
 }

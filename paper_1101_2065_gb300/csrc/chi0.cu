@@ -321,7 +321,6 @@ __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __r
     const int band = nb_bins + 1;
     const long long n_el = (long long)n_sub * (n_sub + 1) / 2;
     const long long n_grp = (n_el + 1) / 2;
-    const long long nn = (long long)n_sub * n_sub;
     const R scale = R(1.0 / (double)L);
     C* B0 = sbuf;
     C* B1 = sbuf + L;
@@ -363,14 +362,14 @@ __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __r
         C* r1 = fft_smem(Y1, B2, L, logL, (const C*)tws, true);
         C* free1 = (r1 == Y1) ? B2 : Y1;
         C* r2 = fft_smem(Zb, free1, L, logL, (const C*)tws, true);
-        const long long o1 = (long long)m1 * n_sub + n1;
-        const long long o2 = (long long)m2 * n_sub + n2;
+        // packed lower triangle: the group's elements are 2g and 2g + 1
         for (int k = threadIdx.x; k < N; k += blockDim.x) {
             C v1 = r1[k];
-            chi0[(long long)k * nn + o1] = Real<C>::make(v1.x * scale, v1.y * scale);
+            C* row = chi0 + (long long)k * n_el + 2 * g;
+            row[0] = Real<C>::make(v1.x * scale, v1.y * scale);
             if (two) {
                 C v2 = r2[k];
-                chi0[(long long)k * nn + o2] = Real<C>::make(v2.x * scale, v2.y * scale);
+                row[1] = Real<C>::make(v2.x * scale, v2.y * scale);
             }
         }
         __syncthreads();
@@ -460,7 +459,7 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
         float* A = dalloc<float>(ctx, band * n_el);
         try {
             deposit<float>(ctx, c, c->Ut32, A, n_el);
-            c->chi0_32 = dalloc<float2>(ctx, (size_t)N * n * n);
+            c->chi0_32 = dalloc<float2>(ctx, (size_t)N * n_el);
             allow_max_smem(k_chi0_fft<float2>);
             klaunch(ctx, "k_chi0_fft32", k_chi0_fft<float2>, grid, 256, smem, (const float*)A, n, c->j_lo, c->nb_bins,
                     N, c->logL, (const float2*)c->tw32, (const float2*)c->C1_32, (const float2*)c->C2_32, c->chi0_32);
@@ -473,7 +472,7 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
         double* A = dalloc<double>(ctx, band * n_el);
         try {
             deposit<double>(ctx, c, c->Ut, A, n_el);
-            c->chi0 = dalloc<double2>(ctx, (size_t)N * n * n);
+            c->chi0 = dalloc<double2>(ctx, (size_t)N * n_el);
             allow_max_smem(k_chi0_fft<double2>);
             klaunch(ctx, "k_chi0_fft", k_chi0_fft<double2>, grid, 256, smem, (const double*)A, n, c->j_lo, c->nb_bins,
                     N, c->logL, (const double2*)c->tw, (const double2*)c->C1, (const double2*)c->C2, c->chi0);

@@ -201,6 +201,10 @@ void launch_qp(gw_ctx* ctx, const gw_sigma* s, const double* vxc, double* e, dou
 void launch_split_complex(gw_ctx* ctx, const double2* z, double* re, double* im, size_t n);
 
 // ------------------------------------------------------------------ complex
+// Packed lower triangle (row-major): element (i, j), j <= i, of an n x n
+// symmetric matrix sits at tri(i) + j; a matrix takes tri(n) elements.
+__host__ __device__ inline long long tri(long long i) { return i * (i + 1) / 2; }
+
 __host__ __device__ inline double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }

@@ -96,15 +96,15 @@ __global__ void __launch_bounds__(256) k_ldlt_init(const C* __restrict__ chi0, C
     typedef typename CT<C>::R R;
     __shared__ double red[33];
     const int k = blockIdx.x;
-    const long long nn = (long long)n * n;
-    const C* X = chi0 + k * nn;
-    C* M = fac + k * nn;
+    const long long pk = tri(n);
+    const C* X = chi0 + k * pk;
+    C* M = fac + k * pk;
     R mx2 = R(0);     // max |M|^2 in the working precision (binary64 arithmetic is 1/64 rate)
     for (int i = 0; i < n; ++i)
         for (int j = threadIdx.x; j <= i; j += blockDim.x) {
-            C x = X[(long long)i * n + j];
+            C x = X[tri(i) + j];
             C m = CT<C>::mk((i == j ? R(1) : R(0)) - x.x, -x.y);
-            M[(long long)i * n + j] = m;
+            M[tri(i) + j] = m;
             mx2 = fmax(mx2, m.x * m.x + m.y * m.y);
         }
     const double mx = block_max((double)mx2, red);
@@ -149,12 +149,12 @@ __global__ void __launch_bounds__(256, 2) k_ldlt_panel(C* __restrict__ fac, int 
     __shared__ C X[NB][NB + 1];     // L11^-1
     __shared__ C Dinv[NB];
     const int k = blockIdx.x, tid = threadIdx.x;
-    C* A = fac + (long long)k * n * n;
+    C* A = fac + (long long)k * tri(n);
     const int kb = min(NB, n - k0), k1 = k0 + kb;
     for (int t = tid; t < NB * NB; t += blockDim.x) {
         const int i = t / NB, j = t % NB;
         // outside kb: identity, so the block inverse below needs no special case
-        S[i][j] = (i < kb && j < kb) ? (j <= i ? A[(long long)(k0 + i) * n + k0 + j] : CT<C>::mk(0, 0))
+        S[i][j] = (i < kb && j < kb) ? (j <= i ? A[tri(k0 + i) + k0 + j] : CT<C>::mk(0, 0))
                                      : CT<C>::mk(i == j ? 1 : 0, 0);
     }
     // pairs (i, l), 1 <= l <= i < NB, owned by this thread for the whole factorisation
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256, 2) k_ldlt_panel(C* __restrict__ fac, int 
     for (int t = tid; t < kb * kb; t += blockDim.x) {
         const int i = t / kb, p = t % kb;
         if (p < i) SD[i][p] = cmul(S[i][p], S[p][p]);
-        if (p <= i) A[(long long)(k0 + i) * n + k0 + p] = S[i][p];
+        if (p <= i) A[tri(k0 + i) + k0 + p] = S[i][p];
     }
     if (tid < kb) Dinv[tid] = cdiv(CT<C>::mk(1, 0), S[tid][tid]);
     __syncthreads();
@@ -244,8 +244,8 @@ __global__ void __launch_bounds__(256, 2) k_ldlt_panel(C* __restrict__ fac, int 
     } else {
         const int nthr = blockDim.x - 32;
         for (int r = k1 + tid - 32; r < n; r += nthr) {
-            if (kb == NB) panel_row_solve<C, true>(A + (long long)r * n + k0, SD, Dinv, kb);
-            else panel_row_solve<C, false>(A + (long long)r * n + k0, SD, Dinv, kb);
+            if (kb == NB) panel_row_solve<C, true>(A + tri(r) + k0, SD, Dinv, kb);
+            else panel_row_solve<C, false>(A + tri(r) + k0, SD, Dinv, kb);
         }
     }
 }
@@ -284,7 +284,7 @@ __device__ __forceinline__ void syrk_tile(C* __restrict__ A, int n, int r0, int 
             if (DIAG && b > a) continue;
             const int i = r0 + ty + 16 * a, j = c0 + tx + 16 * b;
             if (i < n && j <= i) {
-                C* m = A + (long long)i * n + j;
+                C* m = A + tri(i) + j;
                 *m = csub(*m, acc[a][b]);
             }
         }
@@ -300,19 +300,19 @@ __global__ void __launch_bounds__(256) k_ldlt_syrk(C* __restrict__ fac, int n, i
     __shared__ C sW[TT][NB + 1];
     __shared__ C dd[NB];
     const int tid = threadIdx.x;
-    C* A = fac + (long long)blockIdx.y * n * n;
+    C* A = fac + (long long)blockIdx.y * tri(n);
     const int kb = min(NB, n - k0), k1 = k0 + kb;
     int I, J;
     tri_ij(blockIdx.x, I, J);
     const int r0 = k1 + I * TT, c0 = k1 + J * TT;
-    if (tid < NB) dd[tid] = tid < kb ? A[(long long)(k0 + tid) * n + k0 + tid] : CT<C>::mk(R(0), R(0));
+    if (tid < NB) dd[tid] = tid < kb ? A[tri(k0 + tid) + k0 + tid] : CT<C>::mk(R(0), R(0));
     __syncthreads();
     for (int t = tid; t < TT * NB; t += blockDim.x) {
         int rr = t / NB, p = t % NB;
         C lv = CT<C>::mk(R(0), R(0)), wv = CT<C>::mk(R(0), R(0));
         if (p < kb) {
-            if (r0 + rr < n) lv = A[(long long)(r0 + rr) * n + k0 + p];
-            if (c0 + rr < n) wv = cmul(A[(long long)(c0 + rr) * n + k0 + p], dd[p]);
+            if (r0 + rr < n) lv = A[tri(r0 + rr) + k0 + p];
+            if (c0 + rr < n) wv = cmul(A[tri(c0 + rr) + k0 + p], dd[p]);
         }
         sL[rr][p] = lv;
         sW[rr][p] = wv;
@@ -347,7 +347,7 @@ __device__ __forceinline__ void load_l_tile(C* dst, const C* __restrict__ F, int
     for (int t = threadIdx.x; t < FT * NB; t += blockDim.x) {
         const int rr = t / NB, p = t % NB;
         C* d = dst + rr * LP + p;
-        if (p < kb && r0 + rr < n) cp_async_c(d, F + (long long)(r0 + rr) * n + k0 + p);
+        if (p < kb && r0 + rr < n) cp_async_c(d, F + tri(r0 + rr) + k0 + p);
         else *d = CT<C>::mk(0, 0);
     }
 }
@@ -359,7 +359,7 @@ __device__ __forceinline__ void load_diag_data(C* sLi, C* sD, const C* __restric
     constexpr int NB = Tile<C>::NB, V = 16 / sizeof(C);
     for (int t = threadIdx.x; t < NB * NB / V; t += blockDim.x) cp_async16(sLi + t * V, Li + t * V);
     for (int i = threadIdx.x; i < NB; i += blockDim.x) {
-        if (i < kb) cp_async_c(sD + i, F + (long long)(k0 + i) * n + k0 + i);
+        if (i < kb) cp_async_c(sD + i, F + tri(k0 + i) + k0 + i);
         else sD[i] = CT<C>::mk(0, 0);
     }
 }
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(320, 1) k_forms(const C* __restrict__ fac, con
     C* sY = sD + 2 * NB;                                // [n][RC]
     const int tid = threadIdx.x, col = tid % RC, g = tid / RC;
     const int k = 1 + blockIdx.y, rc0 = blockIdx.x * RC, rc = min(RC, R - rc0);
-    const C* F = fac + (long long)k * n * n;
+    const C* F = fac + (long long)k * tri(n);
     const int nblk = (n + NB - 1) / NB;
     const C* Lk = linv + (long long)k * nblk * NB * NB;
     load_diag_data<C>(sLi, sD, Lk, F, n, 0, min(NB, n));
@@ -543,13 +543,13 @@ __global__ void __launch_bounds__(256) k_formsb_diag(const C* __restrict__ fac, 
     __shared__ double red[G][64];
     const int tid = threadIdx.x, cl = tid % 64, g = tid / 64;
     const int z = blockIdx.y, k = kbase + z, col = blockIdx.x * 64 + cl;
-    const C* F = fac + (long long)k * n * n;
+    const C* F = fac + (long long)k * tri(n);
     C* Yk = Y + (long long)z * n * R;
     const int kb = min(NB, n - k0), nblk = (n + NB - 1) / NB;
     const bool last = k0 + kb == n;
     const C* Li = linv + ((long long)k * nblk + k0 / NB) * NB * NB;
     for (int t = tid; t < NB * NB; t += blockDim.x) sLi[t / NB][t % NB] = Li[t];
-    if (tid < NB) sD[tid] = tid < kb ? F[(long long)(k0 + tid) * n + k0 + tid] : CT<C>::mk(T(1), T(0));
+    if (tid < NB) sD[tid] = tid < kb ? F[tri(k0 + tid) + k0 + tid] : CT<C>::mk(T(1), T(0));
     C y[NB];
     const bool live = col < R;
 #pragma unroll
@@ -593,13 +593,13 @@ __global__ void __launch_bounds__(256) k_formsb_update(const C* __restrict__ fac
     __shared__ C sL[TT][NB + 1];
     __shared__ C sY[NB][TT];
     const int tid = threadIdx.x, z = blockIdx.z, k = kbase + z;
-    const C* F = fac + (long long)k * n * n;
+    const C* F = fac + (long long)k * tri(n);
     C* Yk = Y + (long long)z * n * R;
     const int kb = min(NB, n - k0), k1 = k0 + kb;
     const int r0 = k1 + blockIdx.x * TT, c0 = blockIdx.y * TT;
     for (int t = tid; t < TT * NB; t += blockDim.x) {
         const int rr = t / NB, p = t % NB;
-        sL[rr][p] = (p < kb && r0 + rr < n) ? F[(long long)(r0 + rr) * n + k0 + p] : CT<C>::mk(T(0), T(0));
+        sL[rr][p] = (p < kb && r0 + rr < n) ? F[tri(r0 + rr) + k0 + p] : CT<C>::mk(T(0), T(0));
     }
     for (int t = tid; t < NB * TT; t += blockDim.x) {
         const int p = t / TT, cc = t % TT;
@@ -647,13 +647,13 @@ __global__ void __launch_bounds__(256) k_ldlt_inverse(const double2* __restrict_
         for (int i = 0; i < n; ++i) x[(long long)i * n] = make_double2(i == col ? 1.0 : 0.0, 0.0);
         for (int i = 0; i < n; ++i) {
             double2 y = x[(long long)i * n];
-            for (int p = 0; p < i; ++p) y = cfms(F[(long long)i * n + p], x[(long long)p * n], y);
+            for (int p = 0; p < i; ++p) y = cfms(F[tri(i) + p], x[(long long)p * n], y);
             x[(long long)i * n] = y;
         }
-        for (int i = 0; i < n; ++i) x[(long long)i * n] = cdiv(x[(long long)i * n], F[(long long)i * n + i]);
+        for (int i = 0; i < n; ++i) x[(long long)i * n] = cdiv(x[(long long)i * n], F[tri(i) + i]);
         for (int i = n - 1; i >= 0; --i) {
             double2 y = x[(long long)i * n];
-            for (int p = i + 1; p < n; ++p) y = cfms(F[(long long)p * n + i], x[(long long)p * n], y);
+            for (int p = i + 1; p < n; ++p) y = cfms(F[tri(p) + i], x[(long long)p * n], y);
             x[(long long)i * n] = y;
         }
         x[(long long)col * n].x -= 1.0;
@@ -764,9 +764,9 @@ void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* co
 
 void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work) {
     const gw_chi0* c = W->chi0;
-    const long long nn = (long long)c->n_sub * c->n_sub;
-    const double2* F = W->fac ? W->fac + k * nn : work;
-    if (!W->fac) klaunch(ctx, "k_c64_to_c128", k_c64_to_c128, div_up(nn, 256), 256, 0,
-                         (const float2*)(W->fac32 + k * nn), work, nn);
+    const long long pk = tri(c->n_sub);
+    const double2* F = W->fac ? W->fac + k * pk : work;
+    if (!W->fac) klaunch(ctx, "k_c64_to_c128", k_c64_to_c128, div_up(pk, 256), 256, 0,
+                         (const float2*)(W->fac32 + k * pk), work, pk);
     klaunch(ctx, "k_ldlt_inverse", k_ldlt_inverse, 1, 256, 0, F, c->n_sub, out);
 }

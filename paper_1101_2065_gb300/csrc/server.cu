@@ -63,7 +63,7 @@ static size_t job_bytes(const Job& j) {
     const size_t n_pair = (size_t)j.n_occ * (j.n_orb - j.n_occ);
     const size_t cz = j.prec == GW_MIXED ? sizeof(float2) : sizeof(double2);
     const size_t n_rank = std::min(n_pair, std::max<size_t>(5 * no, n));
-    size_t b = 2 * N * n * n * cz + N * (n + 32) * 32 * cz;   // chi0 + factors + diagonal-block inverses
+    size_t b = N * n * (n + 1) * cz + N * (n + 32) * 32 * cz;   // chi0 + factors (packed) + block inverses
     b += np * n_pair * 8 + 2 * n * n_pair * 8;                       // V^EF, U^T (+binary32 copy)
     b += np * np * 8 + j.vertex_len * 8 + no * no * 8;               // molecule
     b += 12 * n_rank * n_rank * 8;                                   // eigensolver work
