@@ -639,10 +639,12 @@ __global__ void __launch_bounds__(256) k_formsb_update(const C* __restrict__ fac
     }
 }
 
-// out = M_k^-1 - 1 = chi^RPA_k from the factors (one CTA; test read-back).
+// out = M_k^-1 - 1 = chi^RPA_k from the factors (test read-back): column
+// col = blockIdx.x * blockDim.x + threadIdx.x of X solves L D L^T x = e_col.
 __global__ void __launch_bounds__(256) k_ldlt_inverse(const double2* __restrict__ F, int n, double2* __restrict__ X) {
-    // column c of X solves L D L^T x = e_c
-    for (int col = threadIdx.x; col < n; col += blockDim.x) {
+    {
+        const int col = blockIdx.x * blockDim.x + threadIdx.x;
+        if (col >= n) return;
         double2* x = X + (long long)col;      // strided column (row-major X)
         for (int i = 0; i < n; ++i) x[(long long)i * n] = make_double2(i == col ? 1.0 : 0.0, 0.0);
         for (int i = 0; i < n; ++i) {
@@ -768,5 +770,5 @@ void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double
     const double2* F = W->fac ? W->fac + k * pk : work;
     if (!W->fac) klaunch(ctx, "k_c64_to_c128", k_c64_to_c128, div_up(pk, 256), 256, 0,
                          (const float2*)(W->fac32 + k * pk), work, pk);
-    klaunch(ctx, "k_ldlt_inverse", k_ldlt_inverse, 1, 256, 0, F, c->n_sub, out);
+    klaunch(ctx, "k_ldlt_inverse", k_ldlt_inverse, div_up(c->n_sub, 64), 64, 0, F, c->n_sub, out);
 }

@@ -63,11 +63,18 @@ static size_t job_bytes(const Job& j) {
     const size_t n_pair = (size_t)j.n_occ * (j.n_orb - j.n_occ);
     const size_t cz = j.prec == GW_MIXED ? sizeof(float2) : sizeof(double2);
     const size_t n_rank = std::min(n_pair, std::max<size_t>(5 * no, n));
+    const size_t rz = cz / 2;                                        // real element of the working precision
+    const size_t R = (size_t)j.states.size() * no;
     size_t b = N * n * (n + 1) * cz + N * (n + 32) * 32 * cz;   // chi0 + factors (packed) + block inverses
-    b += np * n_pair * 8 + 2 * n * n_pair * 8;                       // V^EF, U^T (+binary32 copy)
+    b += np * n_pair * (8 + rz) + n * n_pair * (8 + rz);             // V^EF (+binary32 copy), U^T
+    // spectral weights A[bin][element]: the band spans at most the eigenvalue range
+    const double span = j.eps.empty() ? 0.0 : j.eps.back() - j.eps.front();
+    const size_t band = (size_t)(span / j.grid.d_omega) + 3;
+    b += band * (n * (n + 1) / 2) * rz;
+    b += std::min<size_t>((size_t)2 << 30, (N ? N - 1 : 0) * n * R * cz);   // forms right-hand sides (batched path)
     b += np * np * 8 + j.vertex_len * 8 + no * no * 8;               // molecule
     b += 12 * n_rank * n_rank * 8;                                   // eigensolver work
-    b += 3 * np * (size_t)j.states.size() * no * 8;                  // V^nk, q, v V^nk
+    b += 3 * np * R * 8;                                             // V^nk, q, v V^nk
     return b + b / 8 + (64u << 20);
 }
 
