@@ -741,6 +741,8 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int 
             bnd = std::max(bnd, r);
         }
         bnd = bnd * 1.01f + 1e-30f;
+        allow_max_smem(k_bisect);       // d and e^2 staged in shared memory: 8 n bytes
+        if (2 * (size_t)n * sizeof(float) > 200 * 1024) gw_throw(GW_ERR_INVALID_ARG, "rank too large for the bisection");
         klaunch(ctx, "k_bisect", k_bisect, div_up(n, 8), 256, 2 * (size_t)n * sizeof(float), (const float*)d,
                 (const float*)e, n, bnd, lam32);
         // binary64 vectors when they are refined to binary64 accuracy afterwards

@@ -56,25 +56,29 @@ struct gw_server {
     std::vector<gw_ctx*> ctxs;
 };
 
-// Device bytes a job holds at its peak (chi0 and its factors dominate).
+// Device bytes a job holds at its peak.  The phases of a solve do not hold
+// their buffers at the same time: basis and U (V^EF and its binary32 copy,
+// eigensolver work), chi0 (U, spectral weights A, chi0), then W and Sigma
+// (chi0, U, factors, block inverses, forms right-hand sides); the molecule
+// stays resident throughout.
 static size_t job_bytes(const Job& j) {
     const size_t N = j.grid.n_omega, n = j.n_sub, np = j.n_prod, no = j.n_orb;
     if (j.n_occ <= 0 || j.n_occ >= j.n_orb) return ~size_t(0) / 4;
     const size_t n_pair = (size_t)j.n_occ * (j.n_orb - j.n_occ);
     const size_t cz = j.prec == GW_MIXED ? sizeof(float2) : sizeof(double2);
-    const size_t n_rank = std::min(n_pair, std::max<size_t>(5 * no, n));
     const size_t rz = cz / 2;                                        // real element of the working precision
+    const size_t n_rank = std::min(n_pair, std::max<size_t>(5 * no, n));
     const size_t R = (size_t)j.states.size() * no;
-    size_t b = N * n * (n + 1) * cz + N * (n + 32) * 32 * cz;   // chi0 + factors (packed) + block inverses
-    b += np * n_pair * (8 + rz) + n * n_pair * (8 + rz);             // V^EF (+binary32 copy), U^T
-    // spectral weights A[bin][element]: the band spans at most the eigenvalue range
+    const size_t pk = n * (n + 1) / 2;                               // packed triangle
     const double span = j.eps.empty() ? 0.0 : j.eps.back() - j.eps.front();
-    const size_t band = (size_t)(span / j.grid.d_omega) + 3;
-    b += band * (n * (n + 1) / 2) * rz;
-    b += std::min<size_t>((size_t)2 << 30, (N ? N - 1 : 0) * n * R * cz);   // forms right-hand sides (batched path)
-    b += np * np * 8 + j.vertex_len * 8 + no * no * 8;               // molecule
-    b += 12 * n_rank * n_rank * 8;                                   // eigensolver work
-    b += 3 * np * R * 8;                                             // V^nk, q, v V^nk
+    const size_t band = (size_t)(span / j.grid.d_omega) + 3;         // spectral bins (upper bound)
+    const size_t mol = np * np * 8 + j.vertex_len * 8 + no * no * 8;
+    const size_t U = n * n_pair * rz;
+    const size_t basis = np * n_pair * (8 + rz) + U + 12 * n_rank * n_rank * 8 + 3 * np * n * 8;
+    const size_t chi0 = U + band * pk * rz + N * pk * cz;
+    const size_t screen = U + 2 * N * pk * cz + N * (n + 32) * 32 * cz +
+                          std::min<size_t>((size_t)2 << 30, (N ? N - 1 : 0) * n * R * cz) + 3 * np * R * 8;
+    const size_t b = mol + std::max(basis, std::max(chi0, screen));
     return b + b / 8 + (64u << 20);
 }
 

@@ -37,10 +37,13 @@ def _pct(x, q):
 
 
 def run_jobs(mols, grid, arrivals, prec, workers, budget):
-    """Submit mols[i] at arrivals[i] seconds; return per-job results and the span."""
+    """Submit mols[i] at arrivals[i] seconds; return per-job results (None for
+    a job the server rejected or that failed, with its error in `errors`) and
+    the span."""
     srv = gw.Server(0, n_workers=workers, hbm_budget_bytes=budget)
     handles = [None] * len(mols)
     results = [None] * len(mols)
+    errors = {}
     t0 = time.perf_counter()
 
     def submitter():
@@ -48,23 +51,35 @@ def run_jobs(mols, grid, arrivals, prec, workers, budget):
             dt = t - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
-            handles[i] = srv.submit(m, grid, prec=prec)
+            try:
+                handles[i] = srv.submit(m, grid, prec=prec)
+            except gw.GWError as ex:
+                errors[i] = str(ex)
+                handles[i] = False
 
     th = threading.Thread(target=submitter)
     th.start()
     for i in range(len(mols)):
         while handles[i] is None:
             time.sleep(0.0005)
-        results[i] = srv.wait(handles[i])
+        if handles[i] is False:
+            continue
+        try:
+            results[i] = srv.wait(handles[i])
+        except gw.GWError as ex:
+            errors[i] = str(ex)
     span = time.perf_counter() - t0
     th.join()
     srv.close()
-    return results, span
+    return results, span, errors
 
 
-def summarize(results, span, mols):
-    lat = [r["total_ms"] for r in results]
-    return {"jobs": len(results), "solves_per_s": len(results) / span, "span_s": span,
+def summarize(results, span, mols, errors=None):
+    ok = [r for r in results if r is not None]
+    lat = [r["total_ms"] for r in ok]
+    results = ok
+    return {"jobs": len(mols), "completed": len(ok), "failed": {str(k): v for k, v in (errors or {}).items()},
+            "solves_per_s": len(results) / span, "span_s": span,
             "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "max": max(lat)},
             "queue_ms": {"p50": _pct([r["queue_ms"] for r in results], 50),
                          "p99": _pct([r["queue_ms"] for r in results], 99)},
@@ -72,14 +87,19 @@ def summarize(results, span, mols):
             "atoms": {"min": int(min(m.n_atoms for m in mols)), "max": int(max(m.n_atoms for m in mols))}}
 
 
-def fp64_compare(mols, grid, mixed_results, sample, workers=1):
-    idx = list(range(0, len(mols), max(1, len(mols) // sample)))[:sample]
+def fp64_compare(mols, grid, mixed_results, sample, workers=1, budget=0):
+    idx = [i for i in range(0, len(mols), max(1, len(mols) // sample)) if mixed_results[i] is not None][:sample]
     sub = [mols[i] for i in idx]
-    res, span = run_jobs(sub, grid, [0.0] * len(sub), gw.GW_FP64, workers, 0)
-    err = max(float(np.abs(a["e_qp"] - mixed_results[i]["e_qp"]).max()) for a, i in zip(res, idx)) * HA_MEV
-    same = all(np.array_equal(a["status"], mixed_results[i]["status"]) for a, i in zip(res, idx))
-    return {"jobs": len(sub), "solves_per_s_closed_loop": len(sub) / span,
-            "qp_max_abs_err_meV_mixed_vs_fp64": err, "same_root_branch": same}
+    res, span, errors = run_jobs(sub, grid, [0.0] * len(sub), gw.GW_FP64, workers, budget)
+    pairs = [(a, i) for a, i in zip(res, idx) if a is not None]
+    err = max((float(np.abs(a["e_qp"] - mixed_results[i]["e_qp"]).max()) for a, i in pairs), default=None)
+    same = all(np.array_equal(a["status"], mixed_results[i]["status"]) for a, i in pairs)
+    lat = [a["run_ms"] for a, _ in pairs]
+    return {"jobs": len(sub), "completed": len(pairs), "failed": {str(idx[k]): v for k, v in errors.items()},
+            "atoms": [int(mols[i].n_atoms) for i in idx],
+            "solves_per_s_closed_loop": len(pairs) / span, "run_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99)},
+            "qp_max_abs_err_meV_mixed_vs_fp64": None if err is None else err * HA_MEV,
+            "same_root_branch": same}
 
 
 def main(argv=None):
@@ -103,13 +123,13 @@ def main(argv=None):
     else:
         mols, grid = synth.make_batch(n_omega=a.n_omega or 512)
         arrivals = [0.0] * len(mols)
-    res, span = run_jobs(mols, grid, arrivals, gw.GW_MIXED, a.workers, budget)
+    res, span, errors = run_jobs(mols, grid, arrivals, gw.GW_MIXED, a.workers, budget)
     out = {"mode": a.mode, "precision": "mixed", "n_omega": grid.n_omega, "workers": a.workers,
-           "hbm_budget_gb": a.budget_gb, **summarize(res, span, mols)}
+           "hbm_budget_gb": a.budget_gb, **summarize(res, span, mols, errors)}
     if a.mode == "serve":
         out["offered_rate_per_s"] = a.rate
     if a.fp64_sample > 0:
-        out["fp64_plain"] = fp64_compare(mols, grid, res, a.fp64_sample)
+        out["fp64_plain"] = fp64_compare(mols, grid, res, a.fp64_sample, budget=budget)
     print(json.dumps(out))
 
 
