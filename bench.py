@@ -164,7 +164,7 @@ KERNELS = ["k_forms", "k_forms32", "k_forms_diag", "k_forms_update", "k_forms32_
            "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_to_f32", "k_kernel_spectra",
            "k_cluster_mgs", "k_scale_cols_by", "k_rayleigh_cols", "k_top_indices", "k_gather_cols", "k_ns_coeff",
            "k_pair_keys", "k_pair_scatter", "k_pair_segments", "k_invert_perm", "k_twiddles", "k_cauchy_table",
-           "k_oa_stats_fin", "k_deposit_syrk", "k_deposit_syrk32", "k_sgemm", "k_to_f64"]
+           "k_oa_stats_fin", "k_deposit_syrk", "k_deposit_syrk32", "k_sgemm", "k_sgemm_tc", "k_to_f64"]
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture

@@ -187,6 +187,9 @@ void launch_to_f64(gw_ctx* ctx, const float* a, double* b, long long n);
 void launch_f64_to_f32_2d(gw_ctx* ctx, const double* a, long long lda, int rows, int cols, float* b);
 void gemm_f32(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, float alpha, const float* A, long long lda,
               const float* B, long long ldb, float beta, float* C, long long ldc);
+// tcgen05 3xTF32 tile GEMM; false when the shape is not worth it (caller falls back)
+bool sgemm_tc(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, float alpha, const float* A, long long lda,
+              const float* B, long long ldb, float beta, float* C, long long ldc);
 // screen.cu
 size_t ldlt_linv_bytes(int n, int n_omega, gw_precision prec);
 void launch_ldlt(gw_ctx* ctx, gw_W* W);
