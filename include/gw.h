@@ -132,6 +132,15 @@ gw_status gw_ctx_profile(gw_ctx* ctx, int enable, const char* kernel_name);
 /* Accumulated device time (ms) and launch count of one kernel since the last
  * gw_ctx_profile call; synchronises the context stream. */
 gw_status gw_ctx_profile_get(gw_ctx* ctx, const char* kernel_name, double* total_ms, long long* launches);
+/* Kernel selection switches of a context (implementation choices with the
+ * same results within the precision's tolerance; the paper has no
+ * counterpart).  GW_OPT_FORMS_TENSOR (value 0 or 1, default 0): run the
+ * binary32 path's quadratic forms (Eqs. spectral_3 and chi_RPA) with the
+ * updates below each panel as 3xTF32 tensor-core products instead of on the
+ * binary32 FMA units; applies when N_sub is at most about 330.
+ * GW_ERR_INVALID_ARG for an unknown option or value. */
+enum { GW_OPT_FORMS_TENSOR = 1 };
+gw_status gw_ctx_set_option(gw_ctx* ctx, int option, int value);
 
 /* ---------------------------------------------------------------- molecule */
 /* Validates the description (sizes, CSR, offsets) and copies it to the

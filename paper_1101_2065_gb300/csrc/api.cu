@@ -248,6 +248,16 @@ extern "C" gw_status gw_ctx_profile_get(gw_ctx* ctx, const char* kernel_name, do
     API_END
 }
 
+extern "C" gw_status gw_ctx_set_option(gw_ctx* ctx, int option, int value) {
+    if (!ctx) return GW_ERR_INVALID_ARG;
+    if (option == GW_OPT_FORMS_TENSOR && (value == 0 || value == 1)) {
+        ctx->forms_tensor = value != 0;
+        return GW_OK;
+    }
+    ctx->err = "gw_ctx_set_option: unknown option or value";
+    return GW_ERR_INVALID_ARG;
+}
+
 // ======================================================================
 // molecule
 // ======================================================================

@@ -23,6 +23,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "tc.cuh"
 
 namespace {
 
@@ -523,6 +524,215 @@ __global__ void __launch_bounds__(320, 1) k_forms(const C* __restrict__ fac, con
     }
 }
 
+// Forms of the binary32 path on the tensor cores: the same resident scheme as
+// k_forms (one CTA per frequency k = 1 + blockIdx.y and chunk of 32
+// right-hand sides, Y [n][33] in shared memory, diagonal blocks by the
+// stored L11^-1), with the update of the rows below each panel as one real
+// TF32 product per 128-row tile (3xTF32, two tensor-memory accumulators):
+//   [Re dY | Im dY] (128 x 64) = [L_re | L_im] (128 x 64) [[y_re, y_im], [-y_im, y_re]]
+// The y_b operand is built once per panel; L row tiles are staged hi/lo in
+// the canonical K-major layout (8 consecutive lanes fill one core matrix with
+// 16-byte stores), the MMAs of a tile are committed to an mbarrier (bounded
+// wait), and the warps read the accumulators back with tcgen05.ld and
+// subtract them from Y.
+constexpr int TCF_RC = 32, TCF_PITCH = 33, TCF_M = 128, TCF_K = 64, TCF_N = 64;
+constexpr int TCF_A_BYTES = TCF_M * TCF_K * 4;      // one 128 x 64 binary32 operand
+constexpr int TCF_B_BYTES = TCF_N * TCF_K * 4;      // one 64 x 64 binary32 operand
+constexpr uint32_t TCF_SBO = (TCF_K / 4) * 128;     // bytes between 8-row groups
+constexpr uint32_t TCF_IDESC = tc::idesc_tf32(TCF_M, TCF_N);
+
+__device__ __forceinline__ void st_shared_v4(unsigned char* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(tc::smem_u32(p)), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+// four consecutive K entries (kq-th quad) of row r, split hi/lo into the two tiles
+__device__ __forceinline__ void stage_quad(unsigned char* hi, unsigned char* lo, int r, int kq, const float (&v)[4]) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tc::split_tf32(v[q], h[q], l[q]);
+    const uint32_t o = tc::core_off(r, 4 * kq, TCF_K / 4);
+    st_shared_v4(hi + o, h[0], h[1], h[2], h[3]);
+    st_shared_v4(lo + o, l[0], l[1], l[2], l[3]);
+}
+
+// cp.async the raw rows r0 .. r0 + 127 (columns k0 .. k0 + 31) of F into sRaw (zero past n); commits
+__device__ __forceinline__ void prefetch_l_rows(float2* sRaw, const float2* __restrict__ F, int n, int r0, int k0) {
+    for (int t = threadIdx.x; t < TCF_M * 32; t += blockDim.x) {
+        const int r = t >> 5, p = t & 31;
+        float2* d = sRaw + t;
+        if (r0 + r < n) cp_async8(d, F + tri(r0 + r) + k0 + p);
+        else *d = make_float2(0.f, 0.f);
+    }
+    cp_async_commit();
+}
+
+__global__ void __launch_bounds__(256, 1) k_forms_tc(const float2* __restrict__ fac, const float2* __restrict__ linv,
+                                                     int n, int N, const double* __restrict__ Q, int R,
+                                                     double* __restrict__ c, int* status) {
+    constexpr int NB = 32;
+    extern __shared__ __align__(1024) unsigned char sraw[];
+    unsigned char* sAhi = sraw;
+    unsigned char* sAlo = sAhi + TCF_A_BYTES;
+    unsigned char* sBhi = sAlo + TCF_A_BYTES;
+    unsigned char* sBlo = sBhi + TCF_B_BYTES;
+    float2* sRaw = reinterpret_cast<float2*>(sBlo + TCF_B_BYTES);   // [TCF_M][NB] raw L rows of the next tile
+    float2* sLi = sRaw + TCF_M * NB;                                 // [NB][NB]
+    float2* sD = sLi + NB * NB;                                      // [NB]
+    float2* sY = sD + NB;                                            // [n][TCF_PITCH]
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tbase;
+    __shared__ double red[8][TCF_RC];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int col = tid % TCF_RC, g = tid / TCF_RC;                  // 8 row groups
+    const int k = 1 + blockIdx.y, rc0 = blockIdx.x * TCF_RC, rc = min(TCF_RC, R - rc0);
+    const float2* F = fac + (long long)k * tri(n);
+    const int nblk = (n + NB - 1) / NB;
+    const float2* Lk = linv + (long long)k * nblk * NB * NB;
+    if (warp == 0) tc::tmem_alloc(&tbase, 2 * TCF_N);
+    if (tid == 0) tc::mbar_init(&mbar);
+    {
+        const double* q = Q + rc0 + col;
+        const bool live = col < rc;
+#pragma unroll 4
+        for (int i = g; i < n; i += 8) sY[i * TCF_PITCH + col] = make_float2(live ? (float)q[(long long)i * R] : 0.f, 0.f);
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t taddr = tbase, mb = tc::smem_u32(&mbar);
+    uint32_t uses = 0;
+    bool ok = true, raw_pending = false;
+    double2 part = make_double2(0.0, 0.0);
+    for (int blk = 0; blk < nblk && ok; ++blk) {
+        const int k0 = blk * NB, kb = min(NB, n - k0), k1 = k0 + kb;
+        const float2* Li = Lk + (long long)blk * NB * NB;
+        for (int t = tid; t < NB * NB; t += blockDim.x) sLi[t] = Li[t];
+        if (tid < NB) sD[tid] = tid < kb ? F[tri(k0 + tid) + k0 + tid] : make_float2(1.f, 0.f);
+        // y_b = L11^-1 y_b: rows g, g + 8, g + 16, g + 24 of this thread's column
+        float2 y[NB];
+#pragma unroll
+        for (int p = 0; p < NB; ++p) y[p] = p < kb ? sY[(k0 + p) * TCF_PITCH + col] : make_float2(0.f, 0.f);
+        __syncthreads();
+#pragma unroll
+        for (int qq = 0; qq < NB / 8; ++qq) {
+            const int i = g + 8 * qq;
+            float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int p = 0; p < NB; ++p) v = cfma(sLi[i * NB + p], y[p], v);
+            if (i < kb) {
+                sY[(k0 + i) * TCF_PITCH + col] = v;
+                const float2 w = cdiv(cmul(v, v), sD[i]);
+                part.x += (double)w.x;
+                part.y += (double)w.y;
+            }
+        }
+        __syncthreads();
+        if (k1 >= n) break;
+        // B = [[y_re, y_im], [-y_im, y_re]] as a 64 x 64 K-major operand (rows: output
+        // columns j, Re for j < 32 and Im for j >= 32; K: L_re part then L_im part)
+        for (int t = tid; t < TCF_N * (TCF_K / 4); t += blockDim.x) {
+            const int rr = t & 7, kq = (t >> 3) & 15, rg = t >> 7;
+            const int j = rg * 8 + rr, cc = j & (TCF_RC - 1);
+            const bool im_out = j >= TCF_RC, im_in = kq >= 8;
+            float v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 yy = sY[(k0 + 4 * (kq & 7) + q) * TCF_PITCH + cc];
+                // Re out: (L_re, y_re), (L_im, -y_im); Im out: (L_re, y_im), (L_im, y_re)
+                v[q] = im_out ? (im_in ? yy.x : yy.y) : (im_in ? -yy.y : yy.x);
+            }
+            stage_quad(sBhi, sBlo, j, kq, v);
+        }
+        if (!raw_pending) prefetch_l_rows(sRaw, F, n, k1, k0);
+        raw_pending = false;
+        for (int r0 = k1; r0 < n; r0 += TCF_M) {
+            // A = [L_re | L_im] for rows r0 .. r0 + 127 of panel k0, from the prefetched raw rows
+            cp_async_wait<0>();
+            __syncthreads();
+            for (int t = tid; t < TCF_M * (TCF_K / 4); t += blockDim.x) {
+                const int rr = t & 7, kq = (t >> 3) & 15, rg = t >> 7;
+                const int r = rg * 8 + rr, pb = 4 * (kq & 7);
+                const float2* src = sRaw + r * NB + pb;
+                float v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = kq >= 8 ? src[q].y : src[q].x;
+                stage_quad(sAhi, sAlo, r, kq, v);
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            // the next tile's raw rows (this panel, or the first of the next panel)
+            // stream in while this tile is multiplied and written back
+            if (r0 + TCF_M < n) prefetch_l_rows(sRaw, F, n, r0 + TCF_M, k0);
+            else if (k1 + NB < n) {
+                prefetch_l_rows(sRaw, F, n, k1 + NB, k1);
+                raw_pending = true;
+            }
+            if (tid == 0) {
+                tc::fence_after();
+                const uint32_t ah = tc::smem_u32(sAhi), al = tc::smem_u32(sAlo);
+                const uint32_t bh = tc::smem_u32(sBhi), bl = tc::smem_u32(sBlo);
+#pragma unroll
+                for (int ks = 0; ks < TCF_K / 8; ++ks) {
+                    const uint32_t o = ks * 2 * 128;
+                    const uint32_t first = ks > 0 ? 1u : 0u;
+                    tc::mma_tf32(taddr, tc::smem_desc(ah + o, TCF_SBO), tc::smem_desc(bh + o, TCF_SBO), TCF_IDESC, first);
+                    tc::mma_tf32(taddr + TCF_N, tc::smem_desc(ah + o, TCF_SBO), tc::smem_desc(bl + o, TCF_SBO),
+                                 TCF_IDESC, first);
+                    tc::mma_tf32(taddr + TCF_N, tc::smem_desc(al + o, TCF_SBO), tc::smem_desc(bh + o, TCF_SBO),
+                                 TCF_IDESC, 1u);
+                }
+                tc::commit(mb);
+            }
+            ok = tc::mbar_wait(mb, uses & 1) && ok;
+            ++uses;
+            ok = __syncthreads_and(ok);     // warp-collective tensor-memory loads need a uniform decision
+            tc::fence_after();
+            if (ok) {
+                // warp w: tile rows 32 (w % 4) + lane, complex columns 16 (w / 4) .. + 15
+                const int r = r0 + 32 * (warp & 3) + lane, h = warp >> 2;
+                const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * h;
+                uint32_t re1[16], im1[16], re2[16], im2[16];
+                tc::tmem_ld16(base, re1);
+                tc::tmem_ld16(base + TCF_RC, im1);
+                tc::tmem_ld16(base + TCF_N, re2);
+                tc::tmem_ld16(base + TCF_N + TCF_RC, im2);
+                tc::tmem_wait_ld();
+                if (r < n) {
+                    float2* yr = sY + r * TCF_PITCH + 16 * h;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float2 o = yr[j];
+                        yr[j] = make_float2(o.x - (__uint_as_float(re1[j]) + __uint_as_float(re2[j])),
+                                            o.y - (__uint_as_float(im1[j]) + __uint_as_float(im2[j])));
+                    }
+                }
+            }
+            tc::fence_before();
+            // operand tiles and accumulators are reused by the next tile; a timeout
+            // anywhere stops every thread at the same point
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+        }
+    }
+    cp_async_wait<0>();
+    if (!ok && tid == 0) atomicOr(status, ST_TIMEOUT);
+    red[g][col] = part.y;
+    __syncthreads();
+    if (ok && tid < rc) {
+        double im = 0.0;
+        for (int q = 0; q < 8; ++q) im += red[q][tid];
+        c[(long long)(rc0 + tid) * N + k] = -im / M_PI;
+        if (k == 1) c[(long long)(rc0 + tid) * N] = 0.0;
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(taddr, 2 * TCF_N);
+    }
+}
+
 // Batched forward substitution for large n (the right-hand-side chunk no
 // longer fits on chip): Y [nb][n][R] lives in HBM for a batch of nb
 // frequencies k = kbase + z, and every panel takes two launches over the
@@ -753,9 +963,30 @@ static void forms_run(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, co
     klaunch(ctx, name, k_forms<C>, dim3(chunks, N - 1), FG * RC, smem, fac, linv, n, N, Q, R, RC, cout);
 }
 
+// Tensor-core forms (opt-in, GW_OPT_FORMS_TENSOR) when the 32-column chunk of Y
+// fits beside the operand tiles.  Correct, but on the ring it takes 4.4 ms
+// against 3.3 ms for k_forms: one CTA per SM and a serial split -> MMA ->
+// tensor-memory read-back chain per 128-row tile leave the tensor cores
+// idle most of the time; beating the FMA version needs several tiles in
+// flight (warp-specialised producer / MMA / epilogue stages).
+static bool forms_tc(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
+    const gw_chi0* c = W->chi0;
+    const int n = c->n_sub, N = c->grid.n_omega;
+    const size_t smem = 2 * (size_t)TCF_A_BYTES + 2 * (size_t)TCF_B_BYTES +
+                        sizeof(float2) * ((size_t)TCF_M * 32 + 32 * 32 + 32 + (size_t)n * TCF_PITCH);
+    if (smem > 224 * 1024 || n <= 32) return false;
+    const int chunks = div_up(R, TCF_RC);
+    if (chunks > 65535 || N - 1 > 65535) return false;
+    allow_max_smem(k_forms_tc);
+    klaunch(ctx, "k_forms32_tc", k_forms_tc, dim3(chunks, N - 1), 256, smem, (const float2*)W->fac32,
+            (const float2*)W->linv, n, N, Q, R, cout, ctx->d_status);
+    return true;
+}
+
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
+    if (c->prec == GW_MIXED && ctx->forms_tensor && forms_tc(ctx, W, Q, R, cout)) return;
     static const char* const b32[2] = {"k_forms32_diag", "k_forms32_update"};
     static const char* const b64[2] = {"k_forms_diag", "k_forms_update"};
     if (c->prec == GW_MIXED)

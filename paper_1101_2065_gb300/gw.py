@@ -23,6 +23,7 @@ ERRORS = {
 }
 GW_FP64 = 0
 GW_MIXED = 1
+GW_OPT_FORMS_TENSOR = 1
 
 
 class GWError(RuntimeError):
@@ -75,6 +76,7 @@ def load(path: str | None = None):
         "gw_ctx_launch_count": ([P], C.c_longlong),
         "gw_ctx_profile": ([P, I, C.c_char_p], I),
         "gw_ctx_profile_get": ([P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], I),
+        "gw_ctx_set_option": ([P, I, I], I),
         "gw_mol_upload": ([P, C.POINTER(MoleculeDesc), pp], I),
         "gw_mol_free": ([P], None),
         "gw_build_chi0": ([P, P, C.POINTER(Grid), I, pp], I),
@@ -162,6 +164,10 @@ class Context:
     def profile(self, enable=True, kernel=None):
         """Time launches of one kernel (or all) with CUDA events on the context stream."""
         _check(self, load().gw_ctx_profile(self.handle, int(enable), kernel.encode() if kernel else None))
+
+    def set_option(self, option, value):
+        """Kernel selection switch (GW_OPT_FORMS_TENSOR: tensor-core forms on the binary32 path)."""
+        _check(self, load().gw_ctx_set_option(self.handle, int(option), int(value)))
 
     def profile_get(self, kernel):
         ms, n = C.c_double(), C.c_longlong()

@@ -72,3 +72,23 @@ def test_ring12_mixed_W_meets_1e5(gwlib, ctx, cfg2, cfg2_oracle):
         assert rel(h["W"].chi_rpa(ks), r["chi_rpa"][ks]) < 1e-5
     finally:
         _free(h)
+
+
+def test_ring12_mixed_tensor_core_forms(gwlib, ctx, cfg2, cfg2_oracle):
+    """The opt-in tcgen05 (3xTF32) forms agree with the oracle like the
+    default binary32 forms: c within 1e-3 relative, QP within 1 meV, same
+    root branch."""
+    mol, grid = cfg2
+    r = cfg2_oracle
+    ctx.set_option(gwlib.GW_OPT_FORMS_TENSOR, 1)
+    try:
+        h, e, z, st = _mixed(gwlib, ctx, mol, grid, Z=r["Z"])
+        try:
+            s = h["sigma"].copy()
+            assert rel(s["c"], r["c"]) < 1e-3
+            assert np.abs(e - r["e_qp"]).max() < MEV
+            assert np.array_equal(st, r["status"])
+        finally:
+            _free(h)
+    finally:
+        ctx.set_option(gwlib.GW_OPT_FORMS_TENSOR, 0)
