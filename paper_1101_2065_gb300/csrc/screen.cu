@@ -342,9 +342,9 @@ template <int K> __device__ __forceinline__ void cp_async_wait() {
 
 // rows [r0, r0 + FT) x columns [k0, k0 + NB) of F into a pitched tile (zero
 // outside the matrix or the panel); no commit
-template <typename C>
+template <typename C, int FT = Tile<C>::FT>
 __device__ __forceinline__ void load_l_tile(C* dst, const C* __restrict__ F, int n, int r0, int k0, int kb) {
-    constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, LP = tile_pitch<C>();
+    constexpr int NB = Tile<C>::NB, LP = tile_pitch<C>();
     for (int t = threadIdx.x; t < FT * NB; t += blockDim.x) {
         const int rr = t / NB, p = t % NB;
         C* d = dst + rr * LP + p;
@@ -382,7 +382,7 @@ __device__ __forceinline__ void load_pair(const double2* p, double2& a, double2&
 // ... with the L rows read from shared memory (the same row for all threads
 // of a group).  Shared memory: two L tiles [FT][LP], two L11^-1 [NB][NB]
 // and pivots [NB] (next panel prefetched), Y [n][RC].
-constexpr int FG = 4;          // row groups per CTA
+constexpr int FG = 4;          // row groups per CTA (default variant)
 constexpr int FR = 4;          // rows per thread in flight
 
 template <typename C>
@@ -411,12 +411,16 @@ __device__ __forceinline__ void rows_dot(C (&acc)[FR], const C* __restrict__ A, 
     }
 }
 
-template <typename C>
-__global__ void __launch_bounds__(320, 1) k_forms(const C* __restrict__ fac, const C* __restrict__ linv, int n, int N,
-                                                  const double* __restrict__ Q, int R, int RC,
-                                                  double* __restrict__ c) {
+// Variants: G row groups and FT-row L tiles; <C, 4, 64> holds up to 80
+// right-hand sides per CTA (one CTA per SM), <float2, 8, 32> about 32 with
+// half the shared memory, so two CTAs share an SM (twice the warps to hide
+// latency, L read twice as often from L2).
+template <typename C, int G, int FT>
+__global__ void __launch_bounds__(G == 4 ? 320 : 8 * 40, G == 4 ? 1 : 2)
+    k_forms(const C* __restrict__ fac, const C* __restrict__ linv, int n, int N, const double* __restrict__ Q, int R,
+            int RC, double* __restrict__ c) {
     typedef typename CT<C>::R T;
-    constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, LP = tile_pitch<C>();
+    constexpr int NB = Tile<C>::NB, LP = tile_pitch<C>(), FG = G;
     extern __shared__ __align__(16) unsigned char sraw[];
     C* sL = reinterpret_cast<C*>(sraw);                 // [2][FT][LP]
     C* sLi = sL + 2 * FT * LP;                          // [2][NB][NB]
@@ -428,7 +432,7 @@ __global__ void __launch_bounds__(320, 1) k_forms(const C* __restrict__ fac, con
     const int nblk = (n + NB - 1) / NB;
     const C* Lk = linv + (long long)k * nblk * NB * NB;
     load_diag_data<C>(sLi, sD, Lk, F, n, 0, min(NB, n));
-    if (n > NB) load_l_tile<C>(sL, F, n, NB, 0, NB);
+    if (n > NB) load_l_tile<C, FT>(sL, F, n, NB, 0, NB);
     cp_async_commit();
     {
         // thread (g, col) fills rows g, g + FG, ... of its column (no integer division)
@@ -485,7 +489,7 @@ __global__ void __launch_bounds__(320, 1) k_forms(const C* __restrict__ fac, con
                 nkb = min(NB, n - k1);
                 nr0 = nk0 + nkb;
             }
-            if (nr0 < n) load_l_tile<C>(sL + (buf ^ 1) * FT * LP, F, n, nr0, nk0, nkb);
+            if (nr0 < n) load_l_tile<C, FT>(sL + (buf ^ 1) * FT * LP, F, n, nr0, nk0, nkb);
             cp_async_commit();
             cp_async_wait<1>();
             __syncthreads();
@@ -946,6 +950,25 @@ template <typename C>
 static void forms_run(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, const double* Q, int R, double* cout,
                       const char* name, const char* const bnames[2]) {
     constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, LP = tile_pitch<C>();
+    if (N - 1 > 65535) gw_throw(GW_ERR_INVALID_ARG, "too many frequencies for the forms kernel");
+    if (sizeof(C) == 8) {
+        // two CTAs per SM with 32-row L tiles and 8 row groups, when a useful chunk fits in half the SM
+        constexpr int FT2 = 32;
+        const size_t fixed2 = sizeof(C) * ((size_t)2 * FT2 * LP + 2 * NB * NB + 2 * NB);
+        const size_t half = 110 * 1024;
+        const int rc2 = (int)std::min<size_t>(40, half > fixed2 ? (half - fixed2) / (sizeof(C) * (size_t)n) : 0);
+        if (rc2 >= std::min(R, 24)) {
+            const int chunks = div_up(R, rc2);
+            const int RC = div_up(R, chunks);
+            const size_t smem = fixed2 + std::max(sizeof(C) * (size_t)n * RC, sizeof(double) * 8 * (size_t)RC);
+            if (chunks <= 65535) {
+                allow_max_smem(k_forms<C, 8, FT2>);
+                klaunch(ctx, name, k_forms<C, 8, FT2>, dim3(chunks, N - 1), 8 * RC, smem, fac, linv, n, N, Q, R, RC,
+                        cout);
+                return;
+            }
+        }
+    }
     const size_t fixed = sizeof(C) * ((size_t)2 * FT * LP + 2 * NB * NB + 2 * NB);
     const size_t budget = 224 * 1024;
     // columns per CTA: at most 320 / FG threads, and Y [n][RC] must fit
@@ -958,9 +981,9 @@ static void forms_run(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, co
     const int chunks = div_up(R, rc_max);
     const int RC = div_up(R, chunks);
     const size_t smem = fixed + std::max(sizeof(C) * (size_t)n * RC, sizeof(double) * FG * (size_t)RC);
-    if (chunks > 65535 || N - 1 > 65535) gw_throw(GW_ERR_INVALID_ARG, "too many right-hand sides or frequencies");
-    allow_max_smem(k_forms<C>);
-    klaunch(ctx, name, k_forms<C>, dim3(chunks, N - 1), FG * RC, smem, fac, linv, n, N, Q, R, RC, cout);
+    if (chunks > 65535) gw_throw(GW_ERR_INVALID_ARG, "too many right-hand sides for the forms kernel");
+    allow_max_smem(k_forms<C, FG, FT>);
+    klaunch(ctx, name, k_forms<C, FG, FT>, dim3(chunks, N - 1), FG * RC, smem, fac, linv, n, N, Q, R, RC, cout);
 }
 
 // Tensor-core forms (opt-in, GW_OPT_FORMS_TENSOR) when the 32-column chunk of Y
