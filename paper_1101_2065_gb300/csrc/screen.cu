@@ -411,12 +411,12 @@ __device__ __forceinline__ void rows_dot(C (&acc)[FR], const C* __restrict__ A, 
     }
 }
 
-// Variants: G row groups and FT-row L tiles; <C, 4, 64> holds up to 80
-// right-hand sides per CTA (one CTA per SM), <float2, 8, 32> about 32 with
-// half the shared memory, so two CTAs share an SM (twice the warps to hide
-// latency, L read twice as often from L2).
+// G row groups and FT-row L tiles; the launch uses <C, FG, Tile<C>::FT>: up to
+// 80 right-hand sides per CTA, one CTA per SM.  (Halving the chunk to fit two
+// CTAs per SM with eight row groups measured slower on the ring, 3.75 vs
+// 3.34 ms: the doubled L re-reads cost more than the extra warps recover.)
 template <typename C, int G, int FT>
-__global__ void __launch_bounds__(G == 4 ? 320 : 8 * 40, G == 4 ? 1 : 2)
+__global__ void __launch_bounds__(320, 1)
     k_forms(const C* __restrict__ fac, const C* __restrict__ linv, int n, int N, const double* __restrict__ Q, int R,
             int RC, double* __restrict__ c) {
     typedef typename CT<C>::R T;
@@ -951,24 +951,6 @@ static void forms_run(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, co
                       const char* name, const char* const bnames[2]) {
     constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, LP = tile_pitch<C>();
     if (N - 1 > 65535) gw_throw(GW_ERR_INVALID_ARG, "too many frequencies for the forms kernel");
-    if (sizeof(C) == 8) {
-        // two CTAs per SM with 32-row L tiles and 8 row groups, when a useful chunk fits in half the SM
-        constexpr int FT2 = 32;
-        const size_t fixed2 = sizeof(C) * ((size_t)2 * FT2 * LP + 2 * NB * NB + 2 * NB);
-        const size_t half = 110 * 1024;
-        const int rc2 = (int)std::min<size_t>(40, half > fixed2 ? (half - fixed2) / (sizeof(C) * (size_t)n) : 0);
-        if (rc2 >= std::min(R, 24)) {
-            const int chunks = div_up(R, rc2);
-            const int RC = div_up(R, chunks);
-            const size_t smem = fixed2 + std::max(sizeof(C) * (size_t)n * RC, sizeof(double) * 8 * (size_t)RC);
-            if (chunks <= 65535) {
-                allow_max_smem(k_forms<C, 8, FT2>);
-                klaunch(ctx, name, k_forms<C, 8, FT2>, dim3(chunks, N - 1), 8 * RC, smem, fac, linv, n, N, Q, R, RC,
-                        cout);
-                return;
-            }
-        }
-    }
     const size_t fixed = sizeof(C) * ((size_t)2 * FT * LP + 2 * NB * NB + 2 * NB);
     const size_t budget = 224 * 1024;
     // columns per CTA: at most 320 / FG threads, and Y [n][RC] must fit
