@@ -403,6 +403,7 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
     while ((1 << c->logL) < c->L) c->logL++;
     const int n_prod = mol->n_prod, n_sub = mol->n_sub, n_pair = c->n_pair;
     double* VEFt = nullptr;
+    float* V32 = nullptr;
     double *T1 = nullptr, *g = nullptr, *Bsel = nullptr;
     int* occ = nullptr; int* virt = nullptr; int* rank_of = nullptr;
     try {
@@ -417,8 +418,14 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
         rank_of = dalloc<int>(ctx, n_pair);
         // inverse permutation: natural pair index -> sorted position
         launch_invert_perm(ctx, c, rank_of);
-        VEFt = dalloc<double>(ctx, (size_t)n_prod * n_pair);
-        launch_vertex_contract(ctx, mol, occ, n_occ, virt, n_virt, rank_of, VEFt, n_pair);
+        if (prec == GW_MIXED) {
+            // the mixed path uses V^EF only in binary32 (g, U, and X_r for Z)
+            V32 = dalloc<float>(ctx, (size_t)n_prod * n_pair);
+            launch_vertex_contract32(ctx, mol, occ, n_occ, virt, n_virt, rank_of, V32, n_pair);
+        } else {
+            VEFt = dalloc<double>(ctx, (size_t)n_prod * n_pair);
+            launch_vertex_contract(ctx, mol, occ, n_occ, virt, n_virt, rank_of, VEFt, n_pair);
+        }
         // a0: basis
         c->Zup = dalloc<double>(ctx, (size_t)n_prod * n_sub);
         if (mol->Z) {
@@ -457,22 +464,32 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
                 float* X32 = dalloc<float>(ctx, (size_t)n_prod * nr);
                 float* T32 = dalloc<float>(ctx, (size_t)n_prod * nr);
                 float* g32 = dalloc<float>(ctx, (size_t)nr * nr);
+                float* B32 = nullptr;
+                float* Z32 = nullptr;
                 try {
                     launch_to_f32(ctx, mol->v, v32, (long long)n_prod * n_prod);
-                    launch_f64_to_f32_2d(ctx, VEFt, n_pair, n_prod, nr, X32);
+                    CUDA_CHECK(cudaMemcpy2DAsync(X32, sizeof(float) * nr, V32, sizeof(float) * n_pair, sizeof(float) * nr,
+                                                 n_prod, cudaMemcpyDeviceToDevice, ctx->stream));
                     gemm_f32(ctx, false, false, n_prod, nr, n_prod, 1.f, v32, n_prod, X32, nr, 0.f, T32, nr);
                     gemm_f32(ctx, true, false, nr, nr, n_prod, 1.f, X32, nr, T32, nr, 0.f, g32, nr);
                     ctx_free(ctx, v32); v32 = nullptr;
-                    ctx_free(ctx, X32); X32 = nullptr;
                     ctx_free(ctx, T32); T32 = nullptr;
                     eigh_top_scaled(ctx, nullptr, g32, nr, n_sub, 0, 0.0, false, Bsel);
+                    ctx_free(ctx, g32); g32 = nullptr;
+                    // Z = X_r B (binary32 product; the scaling below is exact for whatever
+                    // Z results), then Zup = v Z and the Rayleigh scaling in binary64
+                    B32 = dalloc<float>(ctx, (size_t)nr * n_sub);
+                    Z32 = dalloc<float>(ctx, (size_t)n_prod * n_sub);
+                    launch_to_f32(ctx, Bsel, B32, (long long)nr * n_sub);
+                    gemm_f32(ctx, false, false, n_prod, n_sub, nr, 1.f, X32, nr, B32, n_sub, 0.f, Z32, n_sub);
+                    c->Z = dalloc<double>(ctx, (size_t)n_prod * n_sub);
+                    launch_to_f64(ctx, Z32, c->Z, (long long)n_prod * n_sub);
                 } catch (...) {
                     ctx_free(ctx, v32); ctx_free(ctx, X32); ctx_free(ctx, T32); ctx_free(ctx, g32);
+                    ctx_free(ctx, B32); ctx_free(ctx, Z32);
                     throw;
                 }
-                ctx_free(ctx, g32);
-                c->Z = dalloc<double>(ctx, (size_t)n_prod * n_sub);
-                gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, VEFt, n_pair, Bsel, n_sub, 0.0, c->Z, n_sub);
+                ctx_free(ctx, X32); ctx_free(ctx, B32); ctx_free(ctx, Z32);
                 gemm_f64(ctx, false, false, n_prod, n_sub, n_prod, 1.0, mol->v, n_prod, c->Z, n_sub, 0.0, c->Zup,
                          n_sub);
                 basis_rayleigh_scale(ctx, c->Z, c->Zup, n_prod, n_sub);
@@ -482,19 +499,16 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
         // uses it in binary32, so it is formed in binary32 there
         if (prec == GW_MIXED) {
             float* Zup32 = dalloc<float>(ctx, (size_t)n_prod * n_sub);
-            float* V32 = nullptr;
             try {
-                V32 = dalloc<float>(ctx, (size_t)n_prod * n_pair);
                 launch_to_f32(ctx, c->Zup, Zup32, (long long)n_prod * n_sub);
-                launch_to_f32(ctx, VEFt, V32, (long long)n_prod * n_pair);
                 c->Ut32 = dalloc<float>(ctx, (size_t)n_sub * n_pair);
                 gemm_f32(ctx, true, false, n_sub, n_pair, n_prod, 1.f, Zup32, n_sub, V32, n_pair, 0.f, c->Ut32, n_pair);
             } catch (...) {
-                ctx_free(ctx, Zup32); ctx_free(ctx, V32);
+                ctx_free(ctx, Zup32);
                 throw;
             }
             ctx_free(ctx, Zup32);
-            ctx_free(ctx, V32);
+            ctx_free(ctx, V32); V32 = nullptr;
         } else {
             c->Ut = dalloc<double>(ctx, (size_t)n_sub * n_pair);
             gemm_f64(ctx, true, false, n_sub, n_pair, n_prod, 1.0, c->Zup, n_sub, VEFt, n_pair, 0.0, c->Ut, n_pair);
@@ -509,8 +523,8 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
         launch_chi0_fft(ctx, c);
         ctx_finish(ctx, "gw_build_chi0");
     } catch (...) {
-        ctx_free(ctx, VEFt); ctx_free(ctx, T1); ctx_free(ctx, g); ctx_free(ctx, Bsel); ctx_free(ctx, occ); ctx_free(ctx, virt);
-        ctx_free(ctx, rank_of);
+        ctx_free(ctx, VEFt); ctx_free(ctx, V32); ctx_free(ctx, T1); ctx_free(ctx, g); ctx_free(ctx, Bsel);
+        ctx_free(ctx, occ); ctx_free(ctx, virt); ctx_free(ctx, rank_of);
         chi0_release(c);
         throw;
     }

@@ -168,6 +168,8 @@ void launch_invert_perm(gw_ctx* ctx, const gw_chi0* c, int* rank_of);
 // col(e,f) = map ? map[e*nF+f] : e*nF+f
 void launch_vertex_contract(gw_ctx* ctx, const gw_mol* mol, const int* Es, int nE,
                             const int* Fs, int nF, const int* map, double* out, long long ld);
+void launch_vertex_contract32(gw_ctx* ctx, const gw_mol* mol, const int* Es, int nE, const int* Fs, int nF,
+                              const int* map, float* out, long long ld);
 // gemm.cu: C = alpha*op(A) op(B) + beta*C, row-major, batched by stride.
 void gemm_f64(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, double alpha,
               const double* A, long long lda, const double* B, long long ldb, double beta,

@@ -74,7 +74,7 @@ static size_t job_bytes(const Job& j) {
     const size_t band = (size_t)(span / j.grid.d_omega) + 3;         // spectral bins (upper bound)
     const size_t mol = np * np * 8 + j.vertex_len * 8 + no * no * 8;
     const size_t U = n * n_pair * rz;
-    const size_t basis = np * n_pair * (8 + rz) + U + 12 * n_rank * n_rank * 8 + 3 * np * n * 8;
+    const size_t basis = np * n_pair * (j.prec == GW_MIXED ? 4 : 8) + U + 12 * n_rank * n_rank * 8 + 3 * np * n * 8;
     const size_t chi0 = U + band * pk * rz + N * pk * cz;
     const size_t screen = U + 2 * N * pk * cz + N * (n + 32) * 32 * cz +
                           std::min<size_t>((size_t)2 << 30, (N ? N - 1 : 0) * n * R * cz) + 3 * np * R * 8;
