@@ -184,7 +184,7 @@ KERNELS = ["k_forms", "k_forms32", "k_forms32_tc", "k_forms_diag", "k_forms_upda
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
 # of the current kernel version on this workload (profiles/k_*_ring12.md);
 # an entry is dropped whenever its kernel changes.
-NCU_TRAFFIC = {"k_forms32": 4.772e8}
+NCU_TRAFFIC = {"k_forms32": 4.489e8}
 
 
 def _panels(n, nb):
