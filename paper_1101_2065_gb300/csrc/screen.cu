@@ -90,24 +90,59 @@ __device__ double block_max(double v, double* red) {
     return r;
 }
 
-// M_k = 1 - chi0_k on the lower triangle; piv[k] = max |M_k|.
+// row of packed lower-triangular index t (tri(i) <= t < tri(i + 1))
+__device__ __forceinline__ int tri_row(long long t) {
+    int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (tri(i) > t) --i;
+    while (tri(i + 1) <= t) ++i;
+    return i;
+}
+
+// M = delta - X for packed entry t (delta = 1 on the diagonal); returns |M|^2
+template <typename C>
+__device__ __forceinline__ typename CT<C>::R init_elem(const C* __restrict__ X, C* __restrict__ M, long long t) {
+    typedef typename CT<C>::R R;
+    const int i = tri_row(t);
+    const C x = X[t];
+    const C m = CT<C>::mk((t == tri(i) + i ? R(1) : R(0)) - x.x, -x.y);
+    M[t] = m;
+    return m.x * m.x + m.y * m.y;
+}
+
+// M_k = 1 - chi0_k on the lower triangle; piv[k] = max |M_k|.  A flat pass
+// over the packed triangle (pairs of binary32 entries as one 16-byte access);
+// the row of an entry, needed only to spot the diagonal, comes from a float
+// square root corrected in integers.
 template <typename C>
 __global__ void __launch_bounds__(256) k_ldlt_init(const C* __restrict__ chi0, C* __restrict__ fac, int n,
                                                    double* __restrict__ piv) {
     typedef typename CT<C>::R R;
     __shared__ double red[33];
-    const int k = blockIdx.x;
-    const long long pk = tri(n);
-    const C* X = chi0 + k * pk;
-    C* M = fac + k * pk;
+    const int k = blockIdx.x, tid = threadIdx.x;
+    const long long pk = tri(n), base = k * pk;
+    const C* X = chi0 + base;
+    C* M = fac + base;
     R mx2 = R(0);     // max |M|^2 in the working precision (binary64 arithmetic is 1/64 rate)
-    for (int i = 0; i < n; ++i)
-        for (int j = threadIdx.x; j <= i; j += blockDim.x) {
-            C x = X[tri(i) + j];
-            C m = CT<C>::mk((i == j ? R(1) : R(0)) - x.x, -x.y);
-            M[tri(i) + j] = m;
-            mx2 = fmax(mx2, m.x * m.x + m.y * m.y);
+    if (sizeof(C) == 8) {
+        // binary32: entry pairs (t, t + 1) with base + t even are 16-byte aligned
+        const long long t0 = base & 1;
+        if (t0 && tid == 0 && pk > 0) mx2 = fmax(mx2, init_elem<C>(X, M, 0));
+        const long long np = (pk - t0) / 2;
+#pragma unroll 4
+        for (long long q = tid; q < np; q += blockDim.x) {
+            const long long t = t0 + 2 * q;
+            const int i = tri_row(t);
+            const long long d = tri(i) + i;       // t + 1 can only be diagonal of row i
+            const float4 x = *reinterpret_cast<const float4*>(X + t);
+            const float4 m = make_float4((t == d ? 1.f : 0.f) - x.x, -x.y, (t + 1 == d ? 1.f : 0.f) - x.z, -x.w);
+            *reinterpret_cast<float4*>(M + t) = m;
+            mx2 = fmax(mx2, R(fmaxf(m.x * m.x + m.y * m.y, m.z * m.z + m.w * m.w)));
         }
+        if (((pk - t0) & 1) && tid == 0) mx2 = fmax(mx2, init_elem<C>(X, M, pk - 1));
+    } else {
+#pragma unroll 4
+        for (long long t = tid; t < pk; t += blockDim.x) mx2 = fmax(mx2, init_elem<C>(X, M, t));
+    }
     const double mx = block_max((double)mx2, red);
     if (threadIdx.x == 0) piv[k] = sqrt(mx);
 }
@@ -251,20 +286,38 @@ __global__ void __launch_bounds__(256, 2) k_ldlt_panel(C* __restrict__ fac, int 
     }
 }
 
-// acc = sL sW^T on one tile and M -= acc on the lower triangle.  Thread
-// (ty, tx) owns rows ty + 16a and columns tx + 16b; on a diagonal tile the
-// sub-blocks b > a lie above the diagonal and are skipped at compile time.
+// M -= sL sW^T on one tile of the lower triangle.  Thread (ty, tx) owns rows
+// ty + 16a and columns tx + 16b; on a diagonal tile the sub-blocks b > a lie
+// above the diagonal and are skipped at compile time.  The thread's entries
+// of M are loaded into the accumulators before the panel tiles are staged, so
+// that both global-load latencies overlap.
 template <typename C, bool DIAG>
-__device__ __forceinline__ void syrk_tile(C* __restrict__ A, int n, int r0, int c0,
-                                          const C (*sL)[Tile<C>::NB + 1], const C (*sW)[Tile<C>::NB + 1]) {
+__device__ __forceinline__ void syrk_tile(C* __restrict__ A, int n, int k0, int kb, int r0, int c0,
+                                          C (*sL)[Tile<C>::NB + 1], C (*sW)[Tile<C>::NB + 1], C* dd) {
     typedef typename CT<C>::R R;
-    constexpr int NB = Tile<C>::NB, TA = Tile<C>::A;
-    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    constexpr int NB = Tile<C>::NB, TT = Tile<C>::T, TA = Tile<C>::A;
+    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     C acc[TA][TA];
 #pragma unroll
     for (int a = 0; a < TA; ++a)
 #pragma unroll
-        for (int b = 0; b < TA; ++b) acc[a][b] = CT<C>::mk(R(0), R(0));
+        for (int b = 0; b < TA; ++b) {
+            const int i = r0 + ty + 16 * a, j = c0 + tx + 16 * b;
+            acc[a][b] = ((!DIAG || b <= a) && i < n && j <= i) ? A[tri(i) + j] : CT<C>::mk(R(0), R(0));
+        }
+    if (tid < NB) dd[tid] = tid < kb ? A[tri(k0 + tid) + k0 + tid] : CT<C>::mk(R(0), R(0));
+    __syncthreads();
+    for (int t = tid; t < TT * NB; t += blockDim.x) {
+        const int rr = t / NB, p = t % NB;
+        C lv = CT<C>::mk(R(0), R(0)), wv = CT<C>::mk(R(0), R(0));
+        if (p < kb) {
+            if (r0 + rr < n) lv = A[tri(r0 + rr) + k0 + p];
+            if (c0 + rr < n) wv = cmul(A[tri(c0 + rr) + k0 + p], dd[p]);
+        }
+        sL[rr][p] = lv;
+        sW[rr][p] = wv;
+    }
+    __syncthreads();
 #pragma unroll 8
     for (int p = 0; p < NB; ++p) {
         C l[TA], w[TA];
@@ -276,7 +329,7 @@ __device__ __forceinline__ void syrk_tile(C* __restrict__ A, int n, int r0, int 
         for (int a = 0; a < TA; ++a)
 #pragma unroll
             for (int b = 0; b < TA; ++b)
-                if (!DIAG || b <= a) acc[a][b] = cfma(l[a], w[b], acc[a][b]);
+                if (!DIAG || b <= a) acc[a][b] = cfms(l[a], w[b], acc[a][b]);
     }
 #pragma unroll
     for (int a = 0; a < TA; ++a)
@@ -284,10 +337,7 @@ __device__ __forceinline__ void syrk_tile(C* __restrict__ A, int n, int r0, int 
         for (int b = 0; b < TA; ++b) {
             if (DIAG && b > a) continue;
             const int i = r0 + ty + 16 * a, j = c0 + tx + 16 * b;
-            if (i < n && j <= i) {
-                C* m = A + tri(i) + j;
-                *m = csub(*m, acc[a][b]);
-            }
+            if (i < n && j <= i) A[tri(i) + j] = acc[a][b];
         }
 }
 
@@ -295,32 +345,17 @@ __device__ __forceinline__ void syrk_tile(C* __restrict__ A, int n, int r0, int 
 // tile blockIdx.x of frequency blockIdx.y.
 template <typename C>
 __global__ void __launch_bounds__(256) k_ldlt_syrk(C* __restrict__ fac, int n, int k0) {
-    typedef typename CT<C>::R R;
-    constexpr int NB = Tile<C>::NB, TT = Tile<C>::T, TA = Tile<C>::A;
+    constexpr int NB = Tile<C>::NB, TT = Tile<C>::T;
     __shared__ C sL[TT][NB + 1];
     __shared__ C sW[TT][NB + 1];
     __shared__ C dd[NB];
-    const int tid = threadIdx.x;
     C* A = fac + (long long)blockIdx.y * tri(n);
     const int kb = min(NB, n - k0), k1 = k0 + kb;
     int I, J;
     tri_ij(blockIdx.x, I, J);
     const int r0 = k1 + I * TT, c0 = k1 + J * TT;
-    if (tid < NB) dd[tid] = tid < kb ? A[tri(k0 + tid) + k0 + tid] : CT<C>::mk(R(0), R(0));
-    __syncthreads();
-    for (int t = tid; t < TT * NB; t += blockDim.x) {
-        int rr = t / NB, p = t % NB;
-        C lv = CT<C>::mk(R(0), R(0)), wv = CT<C>::mk(R(0), R(0));
-        if (p < kb) {
-            if (r0 + rr < n) lv = A[tri(r0 + rr) + k0 + p];
-            if (c0 + rr < n) wv = cmul(A[tri(c0 + rr) + k0 + p], dd[p]);
-        }
-        sL[rr][p] = lv;
-        sW[rr][p] = wv;
-    }
-    __syncthreads();
-    if (I == J) syrk_tile<C, true>(A, n, r0, c0, sL, sW);
-    else syrk_tile<C, false>(A, n, r0, c0, sL, sW);
+    if (I == J) syrk_tile<C, true>(A, n, k0, kb, r0, c0, sL, sW, dd);
+    else syrk_tile<C, false>(A, n, k0, kb, r0, c0, sL, sW, dd);
 }
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
@@ -575,8 +610,8 @@ __global__ void __launch_bounds__(256, 1) k_forms_tc(const float2* __restrict__ 
                                                      int n, int N, const double* __restrict__ Q, int R,
                                                      double* __restrict__ c, int* status) {
     constexpr int NB = 32;
-    extern __shared__ __align__(1024) unsigned char sraw[];
-    unsigned char* sAhi = sraw;
+    extern __shared__ __align__(1024) unsigned char sraw_tc[];
+    unsigned char* sAhi = sraw_tc;
     unsigned char* sAlo = sAhi + TCF_A_BYTES;
     unsigned char* sBhi = sAlo + TCF_A_BYTES;
     unsigned char* sBlo = sBhi + TCF_B_BYTES;
