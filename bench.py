@@ -171,7 +171,7 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ GPU arm
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 FMA/clk/SM x 152 SMs at 2070 MHz
-KERNELS = ["k_forms", "k_forms32", "k_forms32_tc", "k_forms_diag", "k_forms_update", "k_forms32_diag", "k_forms32_update",
+KERNELS = ["k_forms", "k_forms32", "k_forms32_tc", "k_forms32_tm", "k_forms_diag", "k_forms_update", "k_forms32_diag", "k_forms32_update",
            "k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk", "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk",
            "k_chi0_fft", "k_chi0_fft32", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl",
            "k_bisect", "k_invit", "k_backtransform", "k_oa_stats", "k_oa_E", "k_vertex_contract", "k_vertex_contract32", "k_sigma_c",
@@ -214,7 +214,7 @@ def kernel_model(name, mol, grid, n_rank):
         return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if m > 0), "alu", peak
     if name.startswith("k_ldlt") and name.endswith("_panel"):
         return N * 8.0 * sum(kb ** 3 / 6 + m * kb * (kb - 1) / 2 for kb, m in P), "alu", peak
-    if name == "k_forms32_tc":
+    if name in ("k_forms32_tc", "k_forms32_tm"):
         # same forward substitution; the updates below the panels run as 3xTF32 tensor-core products
         return (N - 1) * 8.0 * R * n * (n - 1) / 2, "tensor", PEAK_TF32_TFLOPS
     if name.startswith("k_forms"):

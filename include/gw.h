@@ -138,8 +138,11 @@ gw_status gw_ctx_profile_get(gw_ctx* ctx, const char* kernel_name, double* total
  * binary32 path's quadratic forms (Eqs. spectral_3 and chi_RPA) with the
  * updates below each panel as 3xTF32 tensor-core products instead of on the
  * binary32 FMA units; applies when N_sub is at most about 330.
+ * GW_OPT_FORMS_SIMT (value 0 or 1, default 0): for 32 < N_sub <= 384 the
+ * binary32 path by default keeps the forward substitution's updates in
+ * tensor memory (3xTF32 products); 1 runs it on the FMA units instead.
  * GW_ERR_INVALID_ARG for an unknown option or value. */
-enum { GW_OPT_FORMS_TENSOR = 1 };
+enum { GW_OPT_FORMS_TENSOR = 1, GW_OPT_FORMS_SIMT = 2 };
 gw_status gw_ctx_set_option(gw_ctx* ctx, int option, int value);
 
 /* ---------------------------------------------------------------- molecule */

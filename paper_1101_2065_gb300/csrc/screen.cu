@@ -563,6 +563,281 @@ __global__ void __launch_bounds__(320, 1)
     }
 }
 
+// Forms of the binary32 path with the updates of Y kept in tensor memory.
+// One CTA per frequency k = 1 + blockIdx.y and chunk of TM_RC right-hand
+// sides.  The update of every row below panel b,
+//   dY[r] -= L[r, panel b] y_b,
+// is one real TF32 product per 128-row tile and 16-column half panel
+// (3xTF32, hi products and cross terms in two accumulators), with the
+// complex entries interleaved along K so that a raw row segment of L is the
+// A operand as it lies in memory:
+//   A[r][2p] = Re L[r][p],  A[r][2p+1] = Im L[r][p]
+//   B[c][2p] = -Re y_p[c], B[c][2p+1] = Im y_p[c]      (output Re Y[., c])
+//   B[TM_RC+c][2p] = -Im y_p[c], B[TM_RC+c][2p+1] = -Re y_p[c]   (output Im)
+// The accumulators of all tiles (rows 0 .. n-1 as tensor-memory lanes) hold
+// dY for the whole forward substitution and are never written back: panel b
+// reads its own 32 rows once (two warps, tcgen05.ld), adds q, applies the
+// stored L11^-1 and the forms sum, and builds its B operand; its MMAs then
+// run while the next panel is prepared.  The MMAs of the tile that holds the
+// next panel's rows are issued first and committed to their own mbarrier, so
+// the serial chain per panel is one tile's MMAs, not the whole update.  L
+// rows stream through TM_NS operand stages (register prefetch one stage
+// ahead); every mbarrier wait is bounded.
+__device__ __forceinline__ void st_shared_v4(unsigned char* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(tc::smem_u32(p)), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+constexpr int TM_RC = 40, TM_N = 2 * TM_RC, TM_KS = 32, TM_NS = 3, TM_MAXT = 3;
+constexpr int TM_A_BYTES = 128 * TM_KS * 4;         // one 128 x 32 binary32 operand (hi or lo)
+constexpr int TM_B_BYTES = TM_N * 64 * 4;           // one 80 x 64 binary32 operand (hi or lo)
+constexpr uint32_t TM_SBO_A = (TM_KS / 4) * 128, TM_SBO_B = (64 / 4) * 128;
+constexpr uint32_t TM_IDESC = tc::idesc_tf32(128, TM_N);
+constexpr int TM_GROUPS = 6;                        // row groups of the y_b step (6 x 40 = 240 threads)
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void st_shared_f32(unsigned char* p, uint32_t v) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(tc::smem_u32(p)), "r"(v) : "memory");
+}
+
+// stage = (panel b, tile T, half h); the panels with rows below them are
+// b = 0 .. nblk - 2, the tiles of panel b are T = (32 (b + 1)) / 128 .. nt - 1
+struct TmStage {
+    int b, T, h;
+};
+__device__ __forceinline__ bool tm_next(TmStage& s, int nblk, int nt) {
+    if (s.h == 0) { s.h = 1; return true; }
+    s.h = 0;
+    if (++s.T < nt) return true;
+    if (++s.b >= nblk - 1) return false;
+    s.T = (32 * (s.b + 1)) >> 7;
+    return true;
+}
+
+// this thread's four K-quads of stage s: rows 8 rg + rr, quad kq (idx = tid + 256 j)
+__device__ __forceinline__ void tm_load(float (&v)[4][4], const float2* __restrict__ F, int n, const TmStage& s) {
+    const int k0 = 32 * s.b, k1 = k0 + 32;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int idx = threadIdx.x + 256 * j, rr = idx & 7, kq = (idx >> 3) & 7, rg = idx >> 6;
+        const int r = 128 * s.T + 8 * rg + rr;
+        if (r >= k1 && r < n) {
+            const float2* src = F + tri(r) + k0 + 16 * s.h + 2 * kq;
+            const float2 a = src[0], b = src[1];
+            v[j][0] = a.x; v[j][1] = a.y; v[j][2] = b.x; v[j][3] = b.y;
+        } else {
+            v[j][0] = v[j][1] = v[j][2] = v[j][3] = 0.f;
+        }
+    }
+}
+
+__device__ __forceinline__ void tm_store(unsigned char* hi, unsigned char* lo, const float (&v)[4][4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int idx = threadIdx.x + 256 * j, rr = idx & 7, kq = (idx >> 3) & 7, rg = idx >> 6;
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tc::split_tf32(v[j][q], h[q], l[q]);
+        const uint32_t o = tc::core_off(8 * rg + rr, 4 * kq, TM_KS / 4);
+        st_shared_v4(hi + o, h[0], h[1], h[2], h[3]);
+        st_shared_v4(lo + o, l[0], l[1], l[2], l[3]);
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ fac, const float2* __restrict__ linv,
+                                                     int n, int N, const double* __restrict__ Q, int R,
+                                                     double* __restrict__ c, int* status) {
+    constexpr int NB = 32, RC = TM_RC;
+    extern __shared__ __align__(1024) unsigned char sraw_tm[];
+    unsigned char* sA = sraw_tm;                                     // [TM_NS][hi, lo][TM_A_BYTES]
+    unsigned char* sB = sA + 2 * TM_NS * TM_A_BYTES;                 // [2][hi, lo][TM_B_BYTES]
+    float2* sYb = reinterpret_cast<float2*>(sB + 4 * TM_B_BYTES);    // [NB][RC]
+    float2* sLi = sYb + NB * RC;                                     // [2][NB][NB]
+    float2* sD = sLi + 2 * NB * NB;                                  // [2][NB]
+    double* red = reinterpret_cast<double*>(sD + 2 * NB);            // [TM_GROUPS][RC]
+    __shared__ __align__(8) uint64_t mbar_buf[TM_NS];
+    __shared__ __align__(8) uint64_t mbar_next;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int col = tid % RC, grp = tid / RC;                        // grp < TM_GROUPS: a y_b thread
+    const int k = 1 + blockIdx.y, rc0 = blockIdx.x * RC, rc = min(RC, R - rc0);
+    const float2* F = fac + (long long)k * tri(n);
+    const int nblk = (n + NB - 1) / NB, nt = (n + 127) >> 7;
+    const float2* Lk = linv + (long long)k * nblk * NB * NB;
+    if (warp == 0) tc::tmem_alloc(&tbase, 512);
+    if (tid == 0) {
+        for (int i = 0; i < TM_NS; ++i) tc::mbar_init(&mbar_buf[i]);
+        tc::mbar_init(&mbar_next);
+    }
+    load_diag_data<float2>(sLi, sD, Lk, F, n, 0, min(NB, n));
+    cp_async_commit();
+    // q of this thread's rows of panel 0
+    const bool ythread = grp < TM_GROUPS, live = ythread && col < rc;
+    float qr[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+        const int i = grp + TM_GROUPS * m;
+        qr[m] = (live && i < NB && i < n) ? (float)Q[(long long)i * R + rc0 + col] : 0.f;
+    }
+    // the first stage's operand rows
+    TmStage cur{0, (32 >> 7), 0};
+    bool have = nblk > 1;
+    float av[4][4];
+    if (have) tm_load(av, F, n, cur);
+    tc::fence_async_smem();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t taddr = tbase;
+    uint32_t uses[TM_NS] = {0, 0, 0};
+    int stage = 0;
+    bool ok = true;
+    double part = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        const int k0 = b * NB, kb = min(NB, n - k0), k1 = k0 + kb, db = b & 1;
+        // Y_b = q_b + dY_b
+        if (b > 0) {
+            ok = tc::mbar_wait(tc::smem_u32(&mbar_next), (b - 1) & 1) && ok;
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+            tc::fence_after();
+            const int T = k0 >> 7, qd = (k0 >> 5) & 3;
+            if ((warp & 3) == qd) {
+                const int part_im = warp >> 2;          // warp qd: Re columns, warp qd + 4: Im columns
+                const uint32_t base = taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(2 * T * TM_N + RC * part_im);
+#pragma unroll
+                for (int j = 0; j < RC / 8; ++j) {
+                    uint32_t v[8], u[8];
+                    tmem_ld8(base + 8 * j, v);
+                    tmem_ld8(base + TM_N + 8 * j, u);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        float* dst = reinterpret_cast<float*>(sYb + lane * RC + 8 * j + e) + part_im;
+                        *dst = __uint_as_float(v[e]) + __uint_as_float(u[e]);
+                    }
+                }
+            }
+            tc::fence_before();
+        }
+        __syncthreads();
+        if (ythread) {
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                const int i = grp + TM_GROUPS * m;
+                if (i < NB) {
+                    float2* y = sYb + i * RC + col;
+                    if (b > 0) y->x += qr[m];
+                    else *y = make_float2(qr[m], 0.f);
+                }
+            }
+            // q of the next panel's rows, in flight while this panel runs
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                const int i = k1 + grp + TM_GROUPS * m;
+                qr[m] = (live && grp + TM_GROUPS * m < NB && i < n) ? (float)Q[(long long)i * R + rc0 + col] : 0.f;
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+        // y_b = L11^-1 Y_b, the forms sum, and the B operand of this panel
+        if (ythread) {
+            const float2* Li = sLi + db * NB * NB;
+            unsigned char* bh = sB + 2 * db * TM_B_BYTES;
+            unsigned char* bl = bh + TM_B_BYTES;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                const int i = grp + TM_GROUPS * m;
+                if (i < NB) {
+                    float2 y = make_float2(0.f, 0.f);
+#pragma unroll 8
+                    for (int p = 0; p < NB; ++p) y = cfma(Li[i * NB + p], sYb[p * RC + col], y);
+                    if (i < kb) {
+                        const float2 w = cdiv(cmul(y, y), sD[db * NB + i]);
+                        part += (double)w.y;
+                    } else {
+                        y = make_float2(0.f, 0.f);
+                    }
+                    const float e[4] = {-y.x, y.y, -y.y, -y.x};
+                    const int rows[4] = {col, col, RC + col, RC + col}, ks[4] = {2 * i, 2 * i + 1, 2 * i, 2 * i + 1};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        uint32_t h, l;
+                        tc::split_tf32(e[t], h, l);
+                        const uint32_t o = tc::core_off(rows[t], ks[t], 16);
+                        st_shared_f32(bh + o, h);
+                        st_shared_f32(bl + o, l);
+                    }
+                }
+            }
+        }
+        tc::fence_async_smem();
+        __syncthreads();
+        if (b + 1 < nblk) {
+            // next panel's L11^-1 and pivots (its buffer was last read two panels ago)
+            load_diag_data<float2>(sLi + (db ^ 1) * NB * NB, sD + (db ^ 1) * NB,
+                                   Lk + (long long)(b + 1) * NB * NB, F, n, k1, min(NB, n - k1));
+        }
+        cp_async_commit();
+        if (k1 >= n) break;
+        // MMAs of this panel: tiles T_first .. nt - 1, two K halves each
+        const int T_first = k1 >> 7;
+        for (int T = T_first; T < nt; ++T) {
+            for (int h = 0; h < 2; ++h, ++stage) {
+                const int buf = stage % TM_NS;
+                if (stage >= TM_NS) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[buf]), (uses[buf] - 1) & 1) && ok;
+                unsigned char* ah = sA + 2 * buf * TM_A_BYTES;
+                tm_store(ah, ah + TM_A_BYTES, av);
+                have = tm_next(cur, nblk, nt);
+                if (have) tm_load(av, F, n, cur);
+                tc::fence_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    tc::fence_after();
+                    const uint32_t a0 = tc::smem_u32(ah), a1 = a0 + TM_A_BYTES;
+                    const uint32_t b0 = tc::smem_u32(sB + 2 * db * TM_B_BYTES), b1 = b0 + TM_B_BYTES;
+                    const uint32_t dh = taddr + (uint32_t)(2 * T * TM_N), dx = dh + TM_N;
+#pragma unroll
+                    for (int ks = 0; ks < TM_KS / 8; ++ks) {
+                        const uint32_t oa = ks * 256, ob = (8 * h + 2 * ks) * 128;
+                        const uint32_t acc = (b > 0 || h > 0 || ks > 0) ? 1u : 0u;
+                        tc::mma_tf32(dh, tc::smem_desc(a0 + oa, TM_SBO_A), tc::smem_desc(b0 + ob, TM_SBO_B), TM_IDESC, acc);
+                        tc::mma_tf32(dx, tc::smem_desc(a0 + oa, TM_SBO_A), tc::smem_desc(b1 + ob, TM_SBO_B), TM_IDESC, acc);
+                        tc::mma_tf32(dx, tc::smem_desc(a1 + oa, TM_SBO_A), tc::smem_desc(b0 + ob, TM_SBO_B), TM_IDESC, 1u);
+                    }
+                    tc::commit(tc::smem_u32(&mbar_buf[buf]));
+                    if (T == T_first && h == 1) tc::commit(tc::smem_u32(&mbar_next));
+                }
+                ++uses[buf];
+            }
+        }
+    }
+    // every MMA done before the accumulators are released
+    for (int i = 0; i < TM_NS; ++i)
+        if (uses[i] > 0) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[i]), (uses[i] - 1) & 1) && ok;
+    cp_async_wait<0>();
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0) atomicOr(status, ST_TIMEOUT);
+    if (ythread) red[grp * RC + col] = part;
+    __syncthreads();
+    if (ok && tid < rc) {
+        double im = 0.0;
+        for (int q = 0; q < TM_GROUPS; ++q) im += red[q * RC + tid];
+        c[(long long)(rc0 + tid) * N + k] = -im / M_PI;
+        if (k == 1) c[(long long)(rc0 + tid) * N] = 0.0;
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(taddr, 512);
+    }
+}
+
 // Forms of the binary32 path on the tensor cores: the same resident scheme as
 // k_forms (one CTA per frequency k = 1 + blockIdx.y and chunk of 32
 // right-hand sides, Y [n][33] in shared memory, diagonal blocks by the
@@ -579,11 +854,6 @@ constexpr int TCF_A_BYTES = TCF_M * TCF_K * 4;      // one 128 x 64 binary32 ope
 constexpr int TCF_B_BYTES = TCF_N * TCF_K * 4;      // one 64 x 64 binary32 operand
 constexpr uint32_t TCF_SBO = (TCF_K / 4) * 128;     // bytes between 8-row groups
 constexpr uint32_t TCF_IDESC = tc::idesc_tf32(TCF_M, TCF_N);
-
-__device__ __forceinline__ void st_shared_v4(unsigned char* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(tc::smem_u32(p)), "r"(a), "r"(b), "r"(c), "r"(d)
-                 : "memory");
-}
 
 // four consecutive K entries (kq-th quad) of row r, split hi/lo into the two tiles
 __device__ __forceinline__ void stage_quad(unsigned char* hi, unsigned char* lo, int r, int kq, const float (&v)[4]) {
@@ -1023,10 +1293,30 @@ static bool forms_tc(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double*
     return true;
 }
 
+// Forms with dY in tensor memory: n <= 384 (three 128-lane tiles of two
+// 80-column accumulators within the 512 columns of an SM).
+static size_t forms_tm_smem() {
+    return 2 * (size_t)TM_NS * TM_A_BYTES + 4 * (size_t)TM_B_BYTES +
+           sizeof(float2) * ((size_t)32 * TM_RC + 2 * 32 * 32 + 2 * 32) + sizeof(double) * TM_GROUPS * TM_RC;
+}
+
+static bool forms_tm(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
+    const gw_chi0* c = W->chi0;
+    const int n = c->n_sub, N = c->grid.n_omega;
+    if (n <= 32 || n > 128 * TM_MAXT) return false;
+    const int chunks = div_up(R, TM_RC);
+    if (chunks > 65535 || N - 1 > 65535) return false;
+    allow_max_smem(k_forms_tm);
+    klaunch(ctx, "k_forms32_tm", k_forms_tm, dim3(chunks, N - 1), 256, forms_tm_smem(), (const float2*)W->fac32,
+            (const float2*)W->linv, n, N, Q, R, cout, ctx->d_status);
+    return true;
+}
+
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
     if (c->prec == GW_MIXED && ctx->forms_tensor && forms_tc(ctx, W, Q, R, cout)) return;
+    if (c->prec == GW_MIXED && !ctx->forms_simt && forms_tm(ctx, W, Q, R, cout)) return;
     static const char* const b32[2] = {"k_forms32_diag", "k_forms32_update"};
     static const char* const b64[2] = {"k_forms_diag", "k_forms_update"};
     if (c->prec == GW_MIXED)

@@ -24,6 +24,7 @@ ERRORS = {
 GW_FP64 = 0
 GW_MIXED = 1
 GW_OPT_FORMS_TENSOR = 1
+GW_OPT_FORMS_SIMT = 2
 
 
 class GWError(RuntimeError):
@@ -166,7 +167,8 @@ class Context:
         _check(self, load().gw_ctx_profile(self.handle, int(enable), kernel.encode() if kernel else None))
 
     def set_option(self, option, value):
-        """Kernel selection switch (GW_OPT_FORMS_TENSOR: tensor-core forms on the binary32 path)."""
+        """Kernel selection switch (GW_OPT_FORMS_TENSOR: per-tile tensor-core forms; GW_OPT_FORMS_SIMT: FMA-unit
+        forms instead of the default tensor-memory forms on the binary32 path)."""
         _check(self, load().gw_ctx_set_option(self.handle, int(option), int(value)))
 
     def profile_get(self, kernel):

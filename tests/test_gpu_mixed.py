@@ -92,3 +92,34 @@ def test_ring12_mixed_tensor_core_forms(gwlib, ctx, cfg2, cfg2_oracle):
             _free(h)
     finally:
         ctx.set_option(gwlib.GW_OPT_FORMS_TENSOR, 0)
+
+
+def test_ring12_forms_tensor_memory_vs_fma(gwlib, ctx, cfg2, cfg2_oracle):
+    """The default binary32 forms (updates of Y accumulated in tensor memory,
+    3xTF32) and the FMA-unit forms compute the same c_r(s_j) to binary32
+    accuracy, and both meet the oracle's bars (c within 1e-3 relative, QP
+    within 1 meV, same root branch)."""
+    mol, grid = cfg2
+    r = cfg2_oracle
+    h, e, z, st = _mixed(gwlib, ctx, mol, grid, Z=r["Z"])
+    try:
+        c_tm = h["sigma"].copy()["c"]
+        assert rel(c_tm, r["c"]) < 1e-3
+        assert np.abs(e - r["e_qp"]).max() < MEV
+        assert np.array_equal(st, r["status"])
+    finally:
+        _free(h)
+    ctx.set_option(gwlib.GW_OPT_FORMS_SIMT, 1)
+    try:
+        h, e2, z2, st2 = _mixed(gwlib, ctx, mol, grid, Z=r["Z"])
+        try:
+            c_fma = h["sigma"].copy()["c"]
+            assert rel(c_fma, r["c"]) < 1e-3
+            assert np.abs(e2 - r["e_qp"]).max() < MEV
+            assert np.array_equal(st2, r["status"])
+        finally:
+            _free(h)
+    finally:
+        ctx.set_option(gwlib.GW_OPT_FORMS_SIMT, 0)
+    assert rel(c_tm, c_fma) < 2e-5
+    assert np.abs(e - e2).max() < 0.05 * MEV
