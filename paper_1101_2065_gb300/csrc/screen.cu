@@ -684,11 +684,17 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
         const int i = grp + TM_GROUPS * m;
         qr[m] = (live && i < NB && i < n) ? (float)Q[(long long)i * R + rc0 + col] : 0.f;
     }
-    // the first stage's operand rows
-    TmStage cur{0, (32 >> 7), 0};
+    // operand rows of the first two stages; stages alternate h = 0, 1, and the
+    // set of half h is refilled with the stage two ahead as soon as it is stored
+    TmStage ld{0, (32 >> 7), 0};
     bool have = nblk > 1;
-    float av[4][4];
-    if (have) tm_load(av, F, n, cur);
+    float av0[4][4], av1[4][4];
+    if (have) {
+        tm_load(av0, F, n, ld);
+        tm_next(ld, nblk, nt);
+        tm_load(av1, F, n, ld);
+        have = tm_next(ld, nblk, nt);
+    }
     tc::fence_async_smem();
     __syncthreads();
     tc::fence_after();
@@ -709,18 +715,20 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
             if ((warp & 3) == qd) {
                 const int part_im = warp >> 2;          // warp qd: Re columns, warp qd + 4: Im columns
                 const uint32_t base = taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(2 * T * TM_N + RC * part_im);
+                uint32_t v[RC / 8][8], u[RC / 8][8];
 #pragma unroll
                 for (int j = 0; j < RC / 8; ++j) {
-                    uint32_t v[8], u[8];
-                    tmem_ld8(base + 8 * j, v);
-                    tmem_ld8(base + TM_N + 8 * j, u);
-                    tc::tmem_wait_ld();
+                    tmem_ld8(base + 8 * j, v[j]);
+                    tmem_ld8(base + TM_N + 8 * j, u[j]);
+                }
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < RC / 8; ++j)
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         float* dst = reinterpret_cast<float*>(sYb + lane * RC + 8 * j + e) + part_im;
-                        *dst = __uint_as_float(v[e]) + __uint_as_float(u[e]);
+                        *dst = __uint_as_float(v[j][e]) + __uint_as_float(u[j][e]);
                     }
-                }
             }
             tc::fence_before();
         }
@@ -787,13 +795,19 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
         // MMAs of this panel: tiles T_first .. nt - 1, two K halves each
         const int T_first = k1 >> 7;
         for (int T = T_first; T < nt; ++T) {
+#pragma unroll
             for (int h = 0; h < 2; ++h, ++stage) {
                 const int buf = stage % TM_NS;
                 if (stage >= TM_NS) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[buf]), (uses[buf] - 1) & 1) && ok;
                 unsigned char* ah = sA + 2 * buf * TM_A_BYTES;
-                tm_store(ah, ah + TM_A_BYTES, av);
-                have = tm_next(cur, nblk, nt);
-                if (have) tm_load(av, F, n, cur);
+                if (h == 0) {
+                    tm_store(ah, ah + TM_A_BYTES, av0);
+                    if (have) tm_load(av0, F, n, ld);
+                } else {
+                    tm_store(ah, ah + TM_A_BYTES, av1);
+                    if (have) tm_load(av1, F, n, ld);
+                }
+                if (have) have = tm_next(ld, nblk, nt);
                 tc::fence_async_smem();
                 __syncthreads();
                 if (tid == 0) {
