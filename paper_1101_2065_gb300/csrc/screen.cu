@@ -563,14 +563,19 @@ __global__ void __launch_bounds__(320, 1)
     }
 }
 
+__device__ __forceinline__ void st_shared_v4(unsigned char* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(tc::smem_u32(p)), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
 // Forms of the binary32 path with the updates of Y kept in tensor memory.
 // One CTA per frequency k = 1 + blockIdx.y and chunk of TM_RC right-hand
-// sides.  The update of every row below panel b,
+// sides, two CTAs per SM.  The update of every row below panel b,
 //   dY[r] -= L[r, panel b] y_b,
-// is one real TF32 product per 128-row tile and 16-column half panel
-// (3xTF32, hi products and cross terms in two accumulators), with the
-// complex entries interleaved along K so that a raw row segment of L is the
-// A operand as it lies in memory:
+// is one real TF32 product per 128-row tile and quarter panel (3xTF32 into
+// one binary32 accumulator per tile), with the complex entries interleaved
+// along K so that a raw row segment of L is the A operand as it lies in
+// memory:
 //   A[r][2p] = Re L[r][p],  A[r][2p+1] = Im L[r][p]
 //   B[c][2p] = -Re y_p[c], B[c][2p+1] = Im y_p[c]      (output Re Y[., c])
 //   B[TM_RC+c][2p] = -Im y_p[c], B[TM_RC+c][2p+1] = -Re y_p[c]   (output Im)
@@ -578,22 +583,19 @@ __global__ void __launch_bounds__(320, 1)
 // dY for the whole forward substitution and are never written back: panel b
 // reads its own 32 rows once (two warps, tcgen05.ld), adds q, applies the
 // stored L11^-1 and the forms sum, and builds its B operand; its MMAs then
-// run while the next panel is prepared.  The MMAs of the tile that holds the
-// next panel's rows are issued first and committed to their own mbarrier, so
-// the serial chain per panel is one tile's MMAs, not the whole update.  L
-// rows stream through TM_NS operand stages (register prefetch one stage
-// ahead); every mbarrier wait is bounded.
-__device__ __forceinline__ void st_shared_v4(unsigned char* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(tc::smem_u32(p)), "r"(a), "r"(b), "r"(c), "r"(d)
-                 : "memory");
-}
-
-constexpr int TM_RC = 40, TM_N = 2 * TM_RC, TM_KS = 32, TM_NS = 3, TM_MAXT = 3;
-constexpr int TM_A_BYTES = 128 * TM_KS * 4;         // one 128 x 32 binary32 operand (hi or lo)
+// run while the next panel is prepared (and while the other CTA of the SM
+// runs its own serial steps).  The MMAs of the tile that holds the next
+// panel's rows are committed to their own mbarrier, so the next panel waits
+// for that tile only; the B operand is rebuilt once the whole panel's MMAs
+// are done.  L rows stream through TM_NS operand stages (register prefetch
+// two stages ahead); every mbarrier wait is bounded.
+constexpr int TM_RC = 40, TM_N = 2 * TM_RC, TM_KS = 16, TM_NS = 3, TM_MAXT = 3, TM_RCP = TM_RC + 1;
+constexpr int TM_A_BYTES = 128 * TM_KS * 4;         // one 128 x 16 binary32 operand (hi or lo)
 constexpr int TM_B_BYTES = TM_N * 64 * 4;           // one 80 x 64 binary32 operand (hi or lo)
 constexpr uint32_t TM_SBO_A = (TM_KS / 4) * 128, TM_SBO_B = (64 / 4) * 128;
 constexpr uint32_t TM_IDESC = tc::idesc_tf32(128, TM_N);
 constexpr int TM_GROUPS = 6;                        // row groups of the y_b step (6 x 40 = 240 threads)
+constexpr int TM_TMEM_COLS = 256;                   // TM_MAXT x TM_N = 240, rounded to a power of two
 
 __device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&v)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -605,29 +607,31 @@ __device__ __forceinline__ void st_shared_f32(unsigned char* p, uint32_t v) {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(tc::smem_u32(p)), "r"(v) : "memory");
 }
 
-// stage = (panel b, tile T, half h); the panels with rows below them are
-// b = 0 .. nblk - 2, the tiles of panel b are T = (32 (b + 1)) / 128 .. nt - 1
+// stage = (panel b, tile T, quarter qk of the panel's 32 complex columns);
+// the panels with rows below them are b = 0 .. nblk - 2, the tiles of panel
+// b are T = (32 (b + 1)) / 128 .. nt - 1
 struct TmStage {
-    int b, T, h;
+    int b, T, qk;
 };
 __device__ __forceinline__ bool tm_next(TmStage& s, int nblk, int nt) {
-    if (s.h == 0) { s.h = 1; return true; }
-    s.h = 0;
+    if (++s.qk < 4) return true;
+    s.qk = 0;
     if (++s.T < nt) return true;
     if (++s.b >= nblk - 1) return false;
     s.T = (32 * (s.b + 1)) >> 7;
     return true;
 }
 
-// this thread's four K-quads of stage s: rows 8 rg + rr, quad kq (idx = tid + 256 j)
-__device__ __forceinline__ void tm_load(float (&v)[4][4], const float2* __restrict__ F, int n, const TmStage& s) {
+// this thread's two K-quads of stage s: rows 8 rg + rr of the tile, quad kq
+// (idx = tid + 256 j); zero outside rows [k1, n)
+__device__ __forceinline__ void tm_load(float (&v)[2][4], const float2* __restrict__ F, int n, const TmStage& s) {
     const int k0 = 32 * s.b, k1 = k0 + 32;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int idx = threadIdx.x + 256 * j, rr = idx & 7, kq = (idx >> 3) & 7, rg = idx >> 6;
+    for (int j = 0; j < 2; ++j) {
+        const int idx = threadIdx.x + 256 * j, rr = idx & 7, kq = (idx >> 3) & 3, rg = idx >> 5;
         const int r = 128 * s.T + 8 * rg + rr;
         if (r >= k1 && r < n) {
-            const float2* src = F + tri(r) + k0 + 16 * s.h + 2 * kq;
+            const float2* src = F + tri(r) + k0 + 8 * s.qk + 2 * kq;
             const float2 a = src[0], b = src[1];
             v[j][0] = a.x; v[j][1] = a.y; v[j][2] = b.x; v[j][3] = b.y;
         } else {
@@ -636,10 +640,10 @@ __device__ __forceinline__ void tm_load(float (&v)[4][4], const float2* __restri
     }
 }
 
-__device__ __forceinline__ void tm_store(unsigned char* hi, unsigned char* lo, const float (&v)[4][4]) {
+__device__ __forceinline__ void tm_store(unsigned char* hi, unsigned char* lo, const float (&v)[2][4]) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int idx = threadIdx.x + 256 * j, rr = idx & 7, kq = (idx >> 3) & 7, rg = idx >> 6;
+    for (int j = 0; j < 2; ++j) {
+        const int idx = threadIdx.x + 256 * j, rr = idx & 7, kq = (idx >> 3) & 3, rg = idx >> 5;
         uint32_t h[4], l[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) tc::split_tf32(v[j][q], h[q], l[q]);
@@ -649,19 +653,19 @@ __device__ __forceinline__ void tm_store(unsigned char* hi, unsigned char* lo, c
     }
 }
 
-__global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ fac, const float2* __restrict__ linv,
+__global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ fac, const float2* __restrict__ linv,
                                                      int n, int N, const double* __restrict__ Q, int R,
                                                      double* __restrict__ c, int* status) {
-    constexpr int NB = 32, RC = TM_RC;
-    extern __shared__ __align__(1024) unsigned char sraw_tm[];
+    constexpr int NB = 32, RC = TM_RC, RCP = TM_RCP;
+    extern __shared__ __align__(128) unsigned char sraw_tm[];
     unsigned char* sA = sraw_tm;                                     // [TM_NS][hi, lo][TM_A_BYTES]
-    unsigned char* sB = sA + 2 * TM_NS * TM_A_BYTES;                 // [2][hi, lo][TM_B_BYTES]
-    float2* sYb = reinterpret_cast<float2*>(sB + 4 * TM_B_BYTES);    // [NB][RC]
-    float2* sLi = sYb + NB * RC;                                     // [2][NB][NB]
-    float2* sD = sLi + 2 * NB * NB;                                  // [2][NB]
-    double* red = reinterpret_cast<double*>(sD + 2 * NB);            // [TM_GROUPS][RC]
+    unsigned char* sB = sA + 2 * TM_NS * TM_A_BYTES;                 // [hi, lo][TM_B_BYTES]
+    float2* sYb = reinterpret_cast<float2*>(sB + 2 * TM_B_BYTES);    // [NB][RCP]
+    float2* sLi = sYb + NB * RCP;                                    // [NB][NB]
+    float2* sD = sLi + NB * NB;                                      // [NB]
+    double* red = reinterpret_cast<double*>(sYb);                    // [TM_GROUPS][RC], after the last panel
     __shared__ __align__(8) uint64_t mbar_buf[TM_NS];
-    __shared__ __align__(8) uint64_t mbar_next;
+    __shared__ __align__(8) uint64_t mbar_next, mbar_all;
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int col = tid % RC, grp = tid / RC;                        // grp < TM_GROUPS: a y_b thread
@@ -669,10 +673,11 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
     const float2* F = fac + (long long)k * tri(n);
     const int nblk = (n + NB - 1) / NB, nt = (n + 127) >> 7;
     const float2* Lk = linv + (long long)k * nblk * NB * NB;
-    if (warp == 0) tc::tmem_alloc(&tbase, 512);
+    if (warp == 0) tc::tmem_alloc(&tbase, TM_TMEM_COLS);
     if (tid == 0) {
         for (int i = 0; i < TM_NS; ++i) tc::mbar_init(&mbar_buf[i]);
         tc::mbar_init(&mbar_next);
+        tc::mbar_init(&mbar_all);
     }
     load_diag_data<float2>(sLi, sD, Lk, F, n, 0, min(NB, n));
     cp_async_commit();
@@ -684,11 +689,12 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
         const int i = grp + TM_GROUPS * m;
         qr[m] = (live && i < NB && i < n) ? (float)Q[(long long)i * R + rc0 + col] : 0.f;
     }
-    // operand rows of the first two stages; stages alternate h = 0, 1, and the
-    // set of half h is refilled with the stage two ahead as soon as it is stored
+    // operand rows of the first two stages; stages alternate the parity of
+    // qk, and the set of a parity is refilled with the stage two ahead as soon
+    // as it is stored
     TmStage ld{0, (32 >> 7), 0};
     bool have = nblk > 1;
-    float av0[4][4], av1[4][4];
+    float av0[2][4], av1[2][4];
     if (have) {
         tm_load(av0, F, n, ld);
         tm_next(ld, nblk, nt);
@@ -704,7 +710,7 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
     bool ok = true;
     double part = 0.0;
     for (int b = 0; b < nblk; ++b) {
-        const int k0 = b * NB, kb = min(NB, n - k0), k1 = k0 + kb, db = b & 1;
+        const int k0 = b * NB, kb = min(NB, n - k0), k1 = k0 + kb;
         // Y_b = q_b + dY_b
         if (b > 0) {
             ok = tc::mbar_wait(tc::smem_u32(&mbar_next), (b - 1) & 1) && ok;
@@ -714,21 +720,16 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
             const int T = k0 >> 7, qd = (k0 >> 5) & 3;
             if ((warp & 3) == qd) {
                 const int part_im = warp >> 2;          // warp qd: Re columns, warp qd + 4: Im columns
-                const uint32_t base = taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(2 * T * TM_N + RC * part_im);
-                uint32_t v[RC / 8][8], u[RC / 8][8];
+                const uint32_t base = taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(T * TM_N + RC * part_im);
+                uint32_t v[RC / 8][8];
 #pragma unroll
-                for (int j = 0; j < RC / 8; ++j) {
-                    tmem_ld8(base + 8 * j, v[j]);
-                    tmem_ld8(base + TM_N + 8 * j, u[j]);
-                }
+                for (int j = 0; j < RC / 8; ++j) tmem_ld8(base + 8 * j, v[j]);
                 tc::tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < RC / 8; ++j)
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        float* dst = reinterpret_cast<float*>(sYb + lane * RC + 8 * j + e) + part_im;
-                        *dst = __uint_as_float(v[j][e]) + __uint_as_float(u[j][e]);
-                    }
+                    for (int e = 0; e < 8; ++e)
+                        reinterpret_cast<float*>(sYb + lane * RCP + 8 * j + e)[part_im] = __uint_as_float(v[j][e]);
             }
             tc::fence_before();
         }
@@ -738,7 +739,7 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
             for (int m = 0; m < 6; ++m) {
                 const int i = grp + TM_GROUPS * m;
                 if (i < NB) {
-                    float2* y = sYb + i * RC + col;
+                    float2* y = sYb + i * RCP + col;
                     if (b > 0) y->x += qr[m];
                     else *y = make_float2(qr[m], 0.f);
                 }
@@ -752,55 +753,71 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
         }
         cp_async_wait<0>();
         __syncthreads();
-        // y_b = L11^-1 Y_b, the forms sum, and the B operand of this panel
+        // y_b = L11^-1 Y_b for rows grp + 6 m of column col, and the forms sum
+        float2 yb[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) yb[m] = make_float2(0.f, 0.f);
         if (ythread) {
-            const float2* Li = sLi + db * NB * NB;
-            unsigned char* bh = sB + 2 * db * TM_B_BYTES;
-            unsigned char* bl = bh + TM_B_BYTES;
+#pragma unroll 4
+            for (int p = 0; p < NB; ++p) {
+                const float2 yv = sYb[p * RCP + col];
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    const int i = min(grp + TM_GROUPS * m, NB - 1);
+                    yb[m] = cfma(sLi[i * NB + p], yv, yb[m]);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                const int i = grp + TM_GROUPS * m;
+                if (i < kb) {
+                    const float2 w = cdiv(cmul(yb[m], yb[m]), sD[i]);
+                    part += (double)w.y;
+                } else {
+                    yb[m] = make_float2(0.f, 0.f);
+                }
+            }
+        }
+        // the previous panel's MMAs read the B operand: all done before it is rebuilt
+        if (b > 0 && k0 < n) ok = tc::mbar_wait(tc::smem_u32(&mbar_all), (b - 1) & 1) && ok;
+        if (ythread && k1 < n) {
 #pragma unroll
             for (int m = 0; m < 6; ++m) {
                 const int i = grp + TM_GROUPS * m;
                 if (i < NB) {
-                    float2 y = make_float2(0.f, 0.f);
-#pragma unroll 8
-                    for (int p = 0; p < NB; ++p) y = cfma(Li[i * NB + p], sYb[p * RC + col], y);
-                    if (i < kb) {
-                        const float2 w = cdiv(cmul(y, y), sD[db * NB + i]);
-                        part += (double)w.y;
-                    } else {
-                        y = make_float2(0.f, 0.f);
-                    }
-                    const float e[4] = {-y.x, y.y, -y.y, -y.x};
-                    const int rows[4] = {col, col, RC + col, RC + col}, ks[4] = {2 * i, 2 * i + 1, 2 * i, 2 * i + 1};
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        uint32_t h, l;
-                        tc::split_tf32(e[t], h, l);
-                        const uint32_t o = tc::core_off(rows[t], ks[t], 16);
-                        st_shared_f32(bh + o, h);
-                        st_shared_f32(bl + o, l);
-                    }
+                    uint32_t rh, rl, ih, il;
+                    tc::split_tf32(yb[m].x, rh, rl);
+                    tc::split_tf32(yb[m].y, ih, il);
+                    const uint32_t sg = 0x80000000u;
+                    const uint32_t o0 = tc::core_off(col, 2 * i, 16), o1 = tc::core_off(col, 2 * i + 1, 16);
+                    const uint32_t o2 = tc::core_off(RC + col, 2 * i, 16), o3 = tc::core_off(RC + col, 2 * i + 1, 16);
+                    st_shared_f32(sB + o0, rh ^ sg);
+                    st_shared_f32(sB + TM_B_BYTES + o0, rl ^ sg);
+                    st_shared_f32(sB + o1, ih);
+                    st_shared_f32(sB + TM_B_BYTES + o1, il);
+                    st_shared_f32(sB + o2, ih ^ sg);
+                    st_shared_f32(sB + TM_B_BYTES + o2, il ^ sg);
+                    st_shared_f32(sB + o3, rh ^ sg);
+                    st_shared_f32(sB + TM_B_BYTES + o3, rl ^ sg);
                 }
             }
         }
         tc::fence_async_smem();
-        __syncthreads();
-        if (b + 1 < nblk) {
-            // next panel's L11^-1 and pivots (its buffer was last read two panels ago)
-            load_diag_data<float2>(sLi + (db ^ 1) * NB * NB, sD + (db ^ 1) * NB,
-                                   Lk + (long long)(b + 1) * NB * NB, F, n, k1, min(NB, n - k1));
-        }
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        if (b + 1 < nblk)      // next panel's L11^-1 and pivots: this panel's are no longer read
+            load_diag_data<float2>(sLi, sD, Lk + (long long)(b + 1) * NB * NB, F, n, k1, min(NB, n - k1));
         cp_async_commit();
         if (k1 >= n) break;
-        // MMAs of this panel: tiles T_first .. nt - 1, two K halves each
+        // MMAs of this panel: tiles T_first .. nt - 1, four K quarters each
         const int T_first = k1 >> 7;
         for (int T = T_first; T < nt; ++T) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h, ++stage) {
+            for (int qk = 0; qk < 4; ++qk, ++stage) {
                 const int buf = stage % TM_NS;
                 if (stage >= TM_NS) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[buf]), (uses[buf] - 1) & 1) && ok;
                 unsigned char* ah = sA + 2 * buf * TM_A_BYTES;
-                if (h == 0) {
+                if ((qk & 1) == 0) {
                     tm_store(ah, ah + TM_A_BYTES, av0);
                     if (have) tm_load(av0, F, n, ld);
                 } else {
@@ -813,18 +830,19 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
                 if (tid == 0) {
                     tc::fence_after();
                     const uint32_t a0 = tc::smem_u32(ah), a1 = a0 + TM_A_BYTES;
-                    const uint32_t b0 = tc::smem_u32(sB + 2 * db * TM_B_BYTES), b1 = b0 + TM_B_BYTES;
-                    const uint32_t dh = taddr + (uint32_t)(2 * T * TM_N), dx = dh + TM_N;
+                    const uint32_t b0 = tc::smem_u32(sB), b1 = b0 + TM_B_BYTES;
+                    const uint32_t d = taddr + (uint32_t)(T * TM_N);
 #pragma unroll
                     for (int ks = 0; ks < TM_KS / 8; ++ks) {
-                        const uint32_t oa = ks * 256, ob = (8 * h + 2 * ks) * 128;
-                        const uint32_t acc = (b > 0 || h > 0 || ks > 0) ? 1u : 0u;
-                        tc::mma_tf32(dh, tc::smem_desc(a0 + oa, TM_SBO_A), tc::smem_desc(b0 + ob, TM_SBO_B), TM_IDESC, acc);
-                        tc::mma_tf32(dx, tc::smem_desc(a0 + oa, TM_SBO_A), tc::smem_desc(b1 + ob, TM_SBO_B), TM_IDESC, acc);
-                        tc::mma_tf32(dx, tc::smem_desc(a1 + oa, TM_SBO_A), tc::smem_desc(b0 + ob, TM_SBO_B), TM_IDESC, 1u);
+                        const uint32_t oa = ks * 256, ob = (4 * qk + 2 * ks) * 128;
+                        const uint32_t acc = (b > 0 || qk > 0 || ks > 0) ? 1u : 0u;
+                        tc::mma_tf32(d, tc::smem_desc(a0 + oa, TM_SBO_A), tc::smem_desc(b0 + ob, TM_SBO_B), TM_IDESC, acc);
+                        tc::mma_tf32(d, tc::smem_desc(a0 + oa, TM_SBO_A), tc::smem_desc(b1 + ob, TM_SBO_B), TM_IDESC, 1u);
+                        tc::mma_tf32(d, tc::smem_desc(a1 + oa, TM_SBO_A), tc::smem_desc(b0 + ob, TM_SBO_B), TM_IDESC, 1u);
                     }
                     tc::commit(tc::smem_u32(&mbar_buf[buf]));
-                    if (T == T_first && h == 1) tc::commit(tc::smem_u32(&mbar_next));
+                    if (T == T_first && qk == 3) tc::commit(tc::smem_u32(&mbar_next));
+                    if (T == nt - 1 && qk == 3) tc::commit(tc::smem_u32(&mbar_all));
                 }
                 ++uses[buf];
             }
@@ -848,7 +866,7 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
     __syncthreads();
     if (warp == 0) {
         tc::fence_after();
-        tc::tmem_dealloc(taddr, 512);
+        tc::tmem_dealloc(taddr, TM_TMEM_COLS);
     }
 }
 
@@ -1307,11 +1325,11 @@ static bool forms_tc(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double*
     return true;
 }
 
-// Forms with dY in tensor memory: n <= 384 (three 128-lane tiles of two
-// 80-column accumulators within the 512 columns of an SM).
+// Forms with dY in tensor memory: n <= 384 (three 128-lane tiles of an
+// 80-column accumulator, 256 columns per CTA, two CTAs per SM).
 static size_t forms_tm_smem() {
-    return 2 * (size_t)TM_NS * TM_A_BYTES + 4 * (size_t)TM_B_BYTES +
-           sizeof(float2) * ((size_t)32 * TM_RC + 2 * 32 * 32 + 2 * 32) + sizeof(double) * TM_GROUPS * TM_RC;
+    return 2 * (size_t)TM_NS * TM_A_BYTES + 2 * (size_t)TM_B_BYTES +
+           sizeof(float2) * ((size_t)32 * TM_RCP + 32 * 32 + 32);
 }
 
 static bool forms_tm(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
