@@ -758,14 +758,15 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
 #pragma unroll
         for (int m = 0; m < 6; ++m) yb[m] = make_float2(0.f, 0.f);
         if (ythread) {
-#pragma unroll 4
+            // L11^-1 is lower triangular: row grp + 6 m needs p <= 6 m + 5 at most
+            const float2* lrow = sLi + grp * NB;
+#pragma unroll
             for (int p = 0; p < NB; ++p) {
                 const float2 yv = sYb[p * RCP + col];
 #pragma unroll
-                for (int m = 0; m < 6; ++m) {
-                    const int i = min(grp + TM_GROUPS * m, NB - 1);
-                    yb[m] = cfma(sLi[i * NB + p], yv, yb[m]);
-                }
+                for (int m = 0; m < 6; ++m)
+                    if (TM_GROUPS * m + TM_GROUPS - 1 >= p && (m < 5 || TM_GROUPS * m < NB))
+                        yb[m] = cfma(lrow[min(TM_GROUPS * m * NB + p, (NB - 1 - grp) * NB + p)], yv, yb[m]);
             }
 #pragma unroll
             for (int m = 0; m < 6; ++m) {
