@@ -172,7 +172,7 @@ def run_reference(a):
 # ------------------------------------------------------------------ GPU arm
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 FMA/clk/SM x 152 SMs at 2070 MHz
 KERNELS = ["k_forms", "k_forms32", "k_forms32_tc", "k_forms32_tm", "k_forms_diag", "k_forms_update", "k_forms32_diag", "k_forms32_update",
-           "k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk", "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk",
+           "k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk", "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk", "k_ldlt32_syrk_tc",
            "k_chi0_fft", "k_chi0_fft32", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl",
            "k_bisect", "k_invit", "k_backtransform", "k_oa_stats", "k_oa_E", "k_vertex_contract", "k_vertex_contract32", "k_sigma_c",
            "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_to_f32", "k_kernel_spectra",

@@ -141,8 +141,11 @@ gw_status gw_ctx_profile_get(gw_ctx* ctx, const char* kernel_name, double* total
  * GW_OPT_FORMS_SIMT (value 0 or 1, default 0): for 32 < N_sub <= 384 the
  * binary32 path by default keeps the forward substitution's updates in
  * tensor memory (3xTF32 products); 1 runs it on the FMA units instead.
+ * GW_OPT_SYRK_SIMT (value 0 or 1, default 0): the binary32 factorisation
+ * runs its trailing updates of 128 or more rows as 3xTF32 tensor-core
+ * products by default; 1 keeps them on the FMA units.
  * GW_ERR_INVALID_ARG for an unknown option or value. */
-enum { GW_OPT_FORMS_TENSOR = 1, GW_OPT_FORMS_SIMT = 2 };
+enum { GW_OPT_FORMS_TENSOR = 1, GW_OPT_FORMS_SIMT = 2, GW_OPT_SYRK_SIMT = 3 };
 gw_status gw_ctx_set_option(gw_ctx* ctx, int option, int value);
 
 /* ---------------------------------------------------------------- molecule */

@@ -258,6 +258,10 @@ extern "C" gw_status gw_ctx_set_option(gw_ctx* ctx, int option, int value) {
         ctx->forms_simt = value != 0;
         return GW_OK;
     }
+    if (option == GW_OPT_SYRK_SIMT && (value == 0 || value == 1)) {
+        ctx->syrk_simt = value != 0;
+        return GW_OK;
+    }
     ctx->err = "gw_ctx_set_option: unknown option or value";
     return GW_ERR_INVALID_ARG;
 }

@@ -48,6 +48,7 @@ struct gw_ctx {
     int num_sms = 0;
     bool forms_tensor = false;       // GW_OPT_FORMS_TENSOR
     bool forms_simt = false;         // GW_OPT_FORMS_SIMT
+    bool syrk_simt = false;          // GW_OPT_SYRK_SIMT
     // optional CUDA-event timing of kernel launches whose name matches prof_filter
     bool prof_on = false;
     std::string prof_filter;

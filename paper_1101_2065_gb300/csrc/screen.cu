@@ -358,6 +358,141 @@ __global__ void __launch_bounds__(256) k_ldlt_syrk(C* __restrict__ fac, int n, i
     else syrk_tile<C, false>(A, n, k0, kb, r0, c0, sL, sW, dd);
 }
 
+// Trailing update of the binary32 factorisation on the tensor cores: the tile
+// (128 rows) x (32 complex columns) of M22 -= L21 D L21^T is one real TF32
+// product with the complex entries interleaved along K (3xTF32, hi products
+// and cross terms in two tensor-memory accumulators):
+//   A[r][2p] = Re L[r][p], A[r][2p+1] = Im L[r][p]             (rows r of the tile)
+//   B[q][2p] = Re w, B[q][2p+1] = -Im w;  B[32+q][2p] = Im w, B[32+q][2p+1] = Re w
+// with w = L[c_q][p] d_p for the tile's columns c_q, so that accumulator
+// columns q and 32 + q hold Re and Im of (L21 D L21^T)[r][c_q].  Each thread
+// loads the 16 entries of M it updates before the operands are staged; the
+// tiles that straddle the diagonal skip their upper entries.  Row block I of
+// the trailing matrix holds min(ceil(m / 32), 4 I + 4) column tiles.
+constexpr int ST_NC = 32, ST_N = 2 * ST_NC;
+constexpr int ST_A_BYTES = 128 * 64 * 4;            // 128 x 64 binary32 (hi or lo)
+constexpr int ST_B_BYTES = ST_N * 64 * 4;           // 64 x 64 binary32 (hi or lo)
+constexpr uint32_t ST_SBO = (64 / 4) * 128;
+constexpr uint32_t ST_IDESC = tc::idesc_tf32(128, ST_N);
+
+__host__ __device__ inline int st_row_tiles(int nj, int I) { return nj < 4 * I + 4 ? nj : 4 * I + 4; }
+
+__host__ inline long long st_tile_count(int m) {
+    const int ni = (m + 127) / 128, nj = (m + ST_NC - 1) / ST_NC;
+    long long t = 0;
+    for (int I = 0; I < ni; ++I) t += st_row_tiles(nj, I);
+    return t;
+}
+
+__device__ __forceinline__ void st_shared_quad(unsigned char* hi, unsigned char* lo, uint32_t o, float a, float b,
+                                               float c, float d) {
+    uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
+    tc::split_tf32(a, h0, l0);
+    tc::split_tf32(b, h1, l1);
+    tc::split_tf32(c, h2, l2);
+    tc::split_tf32(d, h3, l3);
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(tc::smem_u32(hi + o)), "r"(h0), "r"(h1), "r"(h2),
+                 "r"(h3) : "memory");
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(tc::smem_u32(lo + o)), "r"(l0), "r"(l1), "r"(l2),
+                 "r"(l3) : "memory");
+}
+
+__global__ void __launch_bounds__(256, 2) k_ldlt_syrk_tc(float2* __restrict__ fac, int n, int k0, int* status) {
+    extern __shared__ __align__(128) unsigned char sraw_st[];
+    unsigned char* sAh = sraw_st;
+    unsigned char* sAl = sAh + ST_A_BYTES;
+    unsigned char* sBh = sAl + ST_A_BYTES;
+    unsigned char* sBl = sBh + ST_B_BYTES;
+    __shared__ float2 dd[32];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float2* A = fac + (long long)blockIdx.y * tri(n);
+    const int k1 = k0 + 32, m = n - k1, nj = (m + ST_NC - 1) / ST_NC;
+    int I = 0, J = blockIdx.x;
+    while (J >= st_row_tiles(nj, I)) J -= st_row_tiles(nj, I++);
+    const int r0 = k1 + 128 * I, c0 = k1 + ST_NC * J;
+    if (warp == 0) tc::tmem_alloc(&tbase, 2 * ST_N);
+    if (tid == 0) tc::mbar_init(&mbar);
+    if (tid < 32) dd[tid] = A[tri(k0 + tid) + k0 + tid];
+    // the entries of M this thread updates: row r, complex columns c_e + j
+    const int r = r0 + 32 * (warp & 3) + lane, ce = c0 + 16 * (warp >> 2);
+    float2 cv[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) cv[j] = (r < n && ce + j <= r) ? A[tri(r) + ce + j] : make_float2(0.f, 0.f);
+    // A operand: rows r0 .. r0 + 127 of the panel
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int idx = tid + 256 * j, rr = idx & 7, kq = (idx >> 3) & 15, rg = idx >> 7;
+        const int ra = r0 + 8 * rg + rr;
+        float2 a = make_float2(0.f, 0.f), b = a;
+        if (ra < n) {
+            const float2* src = A + tri(ra) + k0 + 2 * kq;
+            a = src[0];
+            b = src[1];
+        }
+        st_shared_quad(sAh, sAl, tc::core_off(8 * rg + rr, 4 * kq, 16), a.x, a.y, b.x, b.y);
+    }
+    __syncthreads();
+    // B operand: w = L[c][p] d_p for the tile's 32 columns
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int idx = tid + 256 * j, rr = idx & 7, kq = (idx >> 3) & 15, rg = idx >> 7;
+        const int q = 8 * rg + rr, cc = c0 + q;
+        float2 w0 = make_float2(0.f, 0.f), w1 = w0;
+        if (cc < n) {
+            const float2* src = A + tri(cc) + k0 + 2 * kq;
+            w0 = cmul(src[0], dd[2 * kq]);
+            w1 = cmul(src[1], dd[2 * kq + 1]);
+        }
+        st_shared_quad(sBh, sBl, tc::core_off(q, 4 * kq, 16), w0.x, -w0.y, w1.x, -w1.y);
+        st_shared_quad(sBh, sBl, tc::core_off(ST_NC + q, 4 * kq, 16), w0.y, w0.x, w1.y, w1.x);
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t taddr = tbase;
+    if (tid == 0) {
+        const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks) {
+            const uint32_t o = ks * 256, acc = ks > 0 ? 1u : 0u;
+            tc::mma_tf32(taddr, tc::smem_desc(ah + o, ST_SBO), tc::smem_desc(bh + o, ST_SBO), ST_IDESC, acc);
+            tc::mma_tf32(taddr + ST_N, tc::smem_desc(ah + o, ST_SBO), tc::smem_desc(bl + o, ST_SBO), ST_IDESC, acc);
+            tc::mma_tf32(taddr + ST_N, tc::smem_desc(al + o, ST_SBO), tc::smem_desc(bh + o, ST_SBO), ST_IDESC, 1u);
+        }
+        tc::commit(tc::smem_u32(&mbar));
+    }
+    bool ok = tc::mbar_wait(tc::smem_u32(&mbar), 0);
+    ok = __syncthreads_and(ok);
+    tc::fence_after();
+    if (!ok) {
+        if (tid == 0) atomicOr(status, ST_TIMEOUT);
+    } else {
+        const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * (warp >> 2));
+        uint32_t re[16], im[16], re2[16], im2[16];
+        tc::tmem_ld16(base, re);
+        tc::tmem_ld16(base + ST_NC, im);
+        tc::tmem_ld16(base + ST_N, re2);
+        tc::tmem_ld16(base + ST_N + ST_NC, im2);
+        tc::tmem_wait_ld();
+        if (r < n) {
+            float2* row = A + tri(r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (ce + j <= r)
+                    row[ce + j] = make_float2(cv[j].x - (__uint_as_float(re[j]) + __uint_as_float(re2[j])),
+                                              cv[j].y - (__uint_as_float(im[j]) + __uint_as_float(im2[j])));
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(taddr, 2 * ST_N);
+    }
+}
+
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
@@ -1223,13 +1358,24 @@ __global__ void k_c64_to_c128(const float2* __restrict__ a, double2* __restrict_
 
 template <typename C>
 static void ldlt_steps(gw_ctx* ctx, const C* chi0, C* fac, int n, int N, C* linv, double* piv,
-                       const char* const names[3]) {
+                       const char* const names[4]) {
     constexpr int NB = Tile<C>::NB, TT = Tile<C>::T;
     klaunch(ctx, names[0], k_ldlt_init<C>, N, 256, 0, chi0, fac, n, piv);
     for (int k0 = 0; k0 < n; k0 += NB) {
         klaunch(ctx, names[1], k_ldlt_panel<C>, N, 256, 0, fac, n, N, k0, linv, piv, ctx->d_status);
         const int m = n - std::min(n, k0 + NB);
         if (m == 0) break;
+        if constexpr (sizeof(C) == 8) {
+            // binary32: trailing updates with at least one full 128-row block on the tensor cores
+            const long long tiles = st_tile_count(m);
+            if (!ctx->syrk_simt && m >= 128 && tiles <= 0x7fffffffLL && N <= 65535) {
+                const size_t smem = 2 * (size_t)ST_A_BYTES + 2 * (size_t)ST_B_BYTES;
+                allow_max_smem(k_ldlt_syrk_tc);
+                klaunch(ctx, names[3], k_ldlt_syrk_tc, dim3((unsigned)tiles, N), 256, smem, (float2*)fac, n, k0,
+                        ctx->d_status);
+                continue;
+            }
+        }
         const int nt = div_up(m, TT);
         klaunch(ctx, names[2], k_ldlt_syrk<C>, dim3(nt * (nt + 1) / 2, N), 256, 0, fac, n, k0);
     }
@@ -1244,10 +1390,10 @@ void launch_ldlt(gw_ctx* ctx, gw_W* W) {
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
     if (c->prec == GW_MIXED) {
-        static const char* const nm[3] = {"k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk"};
+        static const char* const nm[4] = {"k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk", "k_ldlt32_syrk_tc"};
         ldlt_steps<float2>(ctx, (const float2*)c->chi0_32, W->fac32, n, N, (float2*)W->linv, W->piv, nm);
     } else {
-        static const char* const nm[3] = {"k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk"};
+        static const char* const nm[4] = {"k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk", "k_ldlt_syrk_tc"};
         ldlt_steps<double2>(ctx, (const double2*)c->chi0, W->fac, n, N, (double2*)W->linv, W->piv, nm);
     }
 }

@@ -25,6 +25,7 @@ GW_FP64 = 0
 GW_MIXED = 1
 GW_OPT_FORMS_TENSOR = 1
 GW_OPT_FORMS_SIMT = 2
+GW_OPT_SYRK_SIMT = 3
 
 
 class GWError(RuntimeError):

@@ -123,3 +123,32 @@ def test_ring12_forms_tensor_memory_vs_fma(gwlib, ctx, cfg2, cfg2_oracle):
         ctx.set_option(gwlib.GW_OPT_FORMS_SIMT, 0)
     assert rel(c_tm, c_fma) < 2e-5
     assert np.abs(e - e2).max() < 0.05 * MEV
+
+
+def test_ring12_syrk_tensor_vs_fma(gwlib, ctx, cfg2, cfg2_oracle):
+    """The binary32 factorisation with its trailing updates on the tensor
+    cores (default, 3xTF32) and on the FMA units gives the same screened
+    interaction and quasiparticle energies to binary32 accuracy, and both
+    meet the oracle's bars."""
+    mol, grid = cfg2
+    r = cfg2_oracle
+    ks = [1, 100, 400, 1023]
+    out = []
+    for simt in (0, 1):
+        ctx.set_option(gwlib.GW_OPT_SYRK_SIMT, simt)
+        try:
+            h, e, z, st = _mixed(gwlib, ctx, mol, grid, Z=r["Z"])
+            try:
+                chi = h["W"].chi_rpa(ks)
+                assert rel(chi, r["chi_rpa"][ks]) < 3e-4
+                assert np.abs(e - r["e_qp"]).max() < MEV
+                assert np.array_equal(st, r["status"])
+                out.append((chi, e, h["sigma"].copy()["c"]))
+            finally:
+                _free(h)
+        finally:
+            ctx.set_option(gwlib.GW_OPT_SYRK_SIMT, 0)
+    (chi_tc, e_tc, c_tc), (chi_fma, e_fma, c_fma) = out
+    assert rel(chi_tc, chi_fma) < 1e-4
+    assert rel(c_tc, c_fma) < 1e-4
+    assert np.abs(e_tc - e_fma).max() < 0.05 * MEV
