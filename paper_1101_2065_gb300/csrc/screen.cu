@@ -365,24 +365,21 @@ __global__ void __launch_bounds__(256) k_ldlt_syrk(C* __restrict__ fac, int n, i
 //   A[r][2p] = Re L[r][p], A[r][2p+1] = Im L[r][p]             (rows r of the tile)
 //   B[q][2p] = Re w, B[q][2p+1] = -Im w;  B[32+q][2p] = Im w, B[32+q][2p+1] = Re w
 // with w = L[c_q][p] d_p for the tile's columns c_q, so that accumulator
-// columns q and 32 + q hold Re and Im of (L21 D L21^T)[r][c_q].  Each thread
-// loads the 16 entries of M it updates before the operands are staged; the
-// tiles that straddle the diagonal skip their upper entries.  Row block I of
-// the trailing matrix holds min(ceil(m / 32), 4 I + 4) column tiles.
-constexpr int ST_NC = 32, ST_N = 2 * ST_NC;
+// columns q and 32 + q hold Re and Im of (L21 D L21^T)[r][c_q].  One CTA per
+// frequency and 128-row block I of the trailing matrix stages the block's
+// panel rows (A) once and walks its min(ceil(m / 32), 4 I + 4) column tiles
+// with two accumulator sets and two B buffers: the MMAs of tile J run while
+// tile J - 1 is read back, subtracted and stored.  The read-back goes through
+// a per-warp shared-memory transpose so that the read-modify-write of M is
+// row-contiguous; entries above the diagonal are skipped.
+constexpr int ST_NC = 32, ST_N = 2 * ST_NC, ST_XP = 17;
 constexpr int ST_A_BYTES = 128 * 64 * 4;            // 128 x 64 binary32 (hi or lo)
 constexpr int ST_B_BYTES = ST_N * 64 * 4;           // 64 x 64 binary32 (hi or lo)
 constexpr uint32_t ST_SBO = (64 / 4) * 128;
 constexpr uint32_t ST_IDESC = tc::idesc_tf32(128, ST_N);
+constexpr size_t ST_SMEM = 2 * (size_t)ST_A_BYTES + 4 * (size_t)ST_B_BYTES + 8 * 32 * ST_XP * sizeof(float2);
 
 __host__ __device__ inline int st_row_tiles(int nj, int I) { return nj < 4 * I + 4 ? nj : 4 * I + 4; }
-
-__host__ inline long long st_tile_count(int m) {
-    const int ni = (m + 127) / 128, nj = (m + ST_NC - 1) / ST_NC;
-    long long t = 0;
-    for (int I = 0; I < ni; ++I) t += st_row_tiles(nj, I);
-    return t;
-}
 
 __device__ __forceinline__ void st_shared_quad(unsigned char* hi, unsigned char* lo, uint32_t o, float a, float b,
                                                float c, float d) {
@@ -397,30 +394,60 @@ __device__ __forceinline__ void st_shared_quad(unsigned char* hi, unsigned char*
                  "r"(l3) : "memory");
 }
 
-__global__ void __launch_bounds__(256, 2) k_ldlt_syrk_tc(float2* __restrict__ fac, int n, int k0, int* status) {
+// raw panel entries of the B operand of column tile c0: two K-quads per thread
+__device__ __forceinline__ void st_load_b(float2 (&wr)[2][2], const float2* __restrict__ A, int n, int k0, int c0) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int idx = threadIdx.x + 256 * j, kq = (idx >> 3) & 15, q = 8 * (idx >> 7) + (idx & 7), cc = c0 + q;
+        wr[j][0] = wr[j][1] = make_float2(0.f, 0.f);
+        if (cc < n) {
+            const float2* src = A + tri(cc) + k0 + 2 * kq;
+            wr[j][0] = src[0];
+            wr[j][1] = src[1];
+        }
+    }
+}
+
+// this lane's entries of M in the row-contiguous read-back layout: rows
+// rb + (lane >> 2) + 8 i, complex columns cb + 4 (lane & 3) + t
+__device__ __forceinline__ void st_load_c(float2 (&cv)[4][4], const float2* __restrict__ A, int n, int rb, int cb) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = rb + (lane >> 2) + 8 * i;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int cc = cb + 4 * (lane & 3) + t;
+            cv[i][t] = (r < n && cc <= r) ? A[tri(r) + cc] : make_float2(0.f, 0.f);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fac, int n, int k0, int* status) {
     extern __shared__ __align__(128) unsigned char sraw_st[];
     unsigned char* sAh = sraw_st;
     unsigned char* sAl = sAh + ST_A_BYTES;
-    unsigned char* sBh = sAl + ST_A_BYTES;
-    unsigned char* sBl = sBh + ST_B_BYTES;
+    unsigned char* sB = sAl + ST_A_BYTES;                            // [2][hi, lo][ST_B_BYTES]
+    float2* sX = reinterpret_cast<float2*>(sB + 4 * ST_B_BYTES);     // [8 warps][32][ST_XP]
     __shared__ float2 dd[32];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float2* A = fac + (long long)blockIdx.y * tri(n);
-    const int k1 = k0 + 32, m = n - k1, nj = (m + ST_NC - 1) / ST_NC;
-    int I = 0, J = blockIdx.x;
-    while (J >= st_row_tiles(nj, I)) J -= st_row_tiles(nj, I++);
-    const int r0 = k1 + 128 * I, c0 = k1 + ST_NC * J;
-    if (warp == 0) tc::tmem_alloc(&tbase, 2 * ST_N);
-    if (tid == 0) tc::mbar_init(&mbar);
+    const int k1 = k0 + 32, m = n - k1, nj = (m + ST_NC - 1) / ST_NC, I = blockIdx.x;
+    const int r0 = k1 + 128 * I, ntile = st_row_tiles(nj, I);
+    // this warp's read-back block: rows rw .. rw + 31, complex columns 16 h .. + 15 of a tile
+    const int rw = r0 + 32 * (warp & 3), h = warp >> 2;
+    if (warp == 0) tc::tmem_alloc(&tbase, 4 * ST_N);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0]);
+        tc::mbar_init(&mbar[1]);
+    }
     if (tid < 32) dd[tid] = A[tri(k0 + tid) + k0 + tid];
-    // the entries of M this thread updates: row r, complex columns c_e + j
-    const int r = r0 + 32 * (warp & 3) + lane, ce = c0 + 16 * (warp >> 2);
-    float2 cv[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) cv[j] = (r < n && ce + j <= r) ? A[tri(r) + ce + j] : make_float2(0.f, 0.f);
-    // A operand: rows r0 .. r0 + 127 of the panel
+    float2 wr[2][2], cn[4][4], cp[4][4];
+    st_load_b(wr, A, n, k0, k1);
+    st_load_c(cn, A, n, rw, k1 + 16 * h);
+    // A operand: rows r0 .. r0 + 127 of the panel, staged once
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int idx = tid + 256 * j, rr = idx & 7, kq = (idx >> 3) & 15, rg = idx >> 7;
@@ -434,62 +461,98 @@ __global__ void __launch_bounds__(256, 2) k_ldlt_syrk_tc(float2* __restrict__ fa
         st_shared_quad(sAh, sAl, tc::core_off(8 * rg + rr, 4 * kq, 16), a.x, a.y, b.x, b.y);
     }
     __syncthreads();
-    // B operand: w = L[c][p] d_p for the tile's 32 columns
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int idx = tid + 256 * j, rr = idx & 7, kq = (idx >> 3) & 15, rg = idx >> 7;
-        const int q = 8 * rg + rr, cc = c0 + q;
-        float2 w0 = make_float2(0.f, 0.f), w1 = w0;
-        if (cc < n) {
-            const float2* src = A + tri(cc) + k0 + 2 * kq;
-            w0 = cmul(src[0], dd[2 * kq]);
-            w1 = cmul(src[1], dd[2 * kq + 1]);
-        }
-        st_shared_quad(sBh, sBl, tc::core_off(q, 4 * kq, 16), w0.x, -w0.y, w1.x, -w1.y);
-        st_shared_quad(sBh, sBl, tc::core_off(ST_NC + q, 4 * kq, 16), w0.y, w0.x, w1.y, w1.x);
-    }
-    tc::fence_async_smem();
-    __syncthreads();
     tc::fence_after();
     const uint32_t taddr = tbase;
-    if (tid == 0) {
-        const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+    bool ok = true;
+    float2* X = sX + warp * 32 * ST_XP;
+    int J = 0;
+    for (; J <= ntile; ++J) {
+        if (J < ntile) {
+            // B operand of tile J (its buffer was last read by the MMAs of tile J - 2, complete)
+            unsigned char* bh = sB + 2 * (J & 1) * ST_B_BYTES;
+            unsigned char* bl = bh + ST_B_BYTES;
 #pragma unroll
-        for (int ks = 0; ks < 8; ++ks) {
-            const uint32_t o = ks * 256, acc = ks > 0 ? 1u : 0u;
-            tc::mma_tf32(taddr, tc::smem_desc(ah + o, ST_SBO), tc::smem_desc(bh + o, ST_SBO), ST_IDESC, acc);
-            tc::mma_tf32(taddr + ST_N, tc::smem_desc(ah + o, ST_SBO), tc::smem_desc(bl + o, ST_SBO), ST_IDESC, acc);
-            tc::mma_tf32(taddr + ST_N, tc::smem_desc(al + o, ST_SBO), tc::smem_desc(bh + o, ST_SBO), ST_IDESC, 1u);
+            for (int j = 0; j < 2; ++j) {
+                const int idx = tid + 256 * j, rr = idx & 7, kq = (idx >> 3) & 15, rg = idx >> 7, q = 8 * rg + rr;
+                const float2 w0 = cmul(wr[j][0], dd[2 * kq]), w1 = cmul(wr[j][1], dd[2 * kq + 1]);
+                st_shared_quad(bh, bl, tc::core_off(q, 4 * kq, 16), w0.x, -w0.y, w1.x, -w1.y);
+                st_shared_quad(bh, bl, tc::core_off(ST_NC + q, 4 * kq, 16), w0.y, w0.x, w1.y, w1.x);
+            }
+            if (J + 1 < ntile) st_load_b(wr, A, n, k0, k1 + ST_NC * (J + 1));
+            tc::fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after();
+                const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl);
+                const uint32_t b0 = tc::smem_u32(bh), b1 = tc::smem_u32(bl);
+                const uint32_t d = taddr + (uint32_t)(2 * ST_N * (J & 1));
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks) {
+                    const uint32_t o = ks * 256, acc = ks > 0 ? 1u : 0u;
+                    tc::mma_tf32(d, tc::smem_desc(ah + o, ST_SBO), tc::smem_desc(b0 + o, ST_SBO), ST_IDESC, acc);
+                    tc::mma_tf32(d + ST_N, tc::smem_desc(ah + o, ST_SBO), tc::smem_desc(b1 + o, ST_SBO), ST_IDESC, acc);
+                    tc::mma_tf32(d + ST_N, tc::smem_desc(al + o, ST_SBO), tc::smem_desc(b0 + o, ST_SBO), ST_IDESC, 1u);
+                }
+                tc::commit(tc::smem_u32(&mbar[J & 1]));
+            }
         }
-        tc::commit(tc::smem_u32(&mbar));
-    }
-    bool ok = tc::mbar_wait(tc::smem_u32(&mbar), 0);
-    ok = __syncthreads_and(ok);
-    tc::fence_after();
-    if (!ok) {
-        if (tid == 0) atomicOr(status, ST_TIMEOUT);
-    } else {
-        const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * (warp >> 2));
-        uint32_t re[16], im[16], re2[16], im2[16];
-        tc::tmem_ld16(base, re);
-        tc::tmem_ld16(base + ST_NC, im);
-        tc::tmem_ld16(base + ST_N, re2);
-        tc::tmem_ld16(base + ST_N + ST_NC, im2);
-        tc::tmem_wait_ld();
-        if (r < n) {
-            float2* row = A + tri(r);
+        if (J >= 1) {
+            // tile J - 1: read back, transpose through shared memory, M -= product
+            const int Jp = J - 1, cb = k1 + ST_NC * Jp + 16 * h;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) cp[i][t] = cn[i][t];
+            if (J < ntile) st_load_c(cn, A, n, rw, k1 + ST_NC * J + 16 * h);
+            ok = tc::mbar_wait(tc::smem_u32(&mbar[Jp & 1]), (Jp >> 1) & 1) && ok;
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+            tc::fence_after();
+            const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(2 * ST_N * (Jp & 1) + 16 * h);
+            uint32_t re[16], im[16], re2[16], im2[16];
+            tc::tmem_ld16(base, re);
+            tc::tmem_ld16(base + ST_NC, im);
+            tc::tmem_ld16(base + ST_N, re2);
+            tc::tmem_ld16(base + ST_N + ST_NC, im2);
+            tc::tmem_wait_ld();
+            tc::fence_before();
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-                if (ce + j <= r)
-                    row[ce + j] = make_float2(cv[j].x - (__uint_as_float(re[j]) + __uint_as_float(re2[j])),
-                                              cv[j].y - (__uint_as_float(im[j]) + __uint_as_float(im2[j])));
+                X[lane * ST_XP + j] = make_float2(__uint_as_float(re[j]) + __uint_as_float(re2[j]),
+                                                  __uint_as_float(im[j]) + __uint_as_float(im2[j]));
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int rl = (lane >> 2) + 8 * i, r = rw + rl;
+                if (r < n) {
+                    float2* row = A + tri(r);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int cl = 4 * (lane & 3) + t, cc = cb + cl;
+                        if (cc <= r) {
+                            const float2 x = X[rl * ST_XP + cl];
+                            row[cc] = make_float2(cp[i][t].x - x.x, cp[i][t].y - x.y);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (!ok) {
+        // the loop ended early at tile J: the MMAs issued so far finish before the columns are freed
+        if (tid == 0) atomicOr(status, ST_TIMEOUT);
+        const int issued = min(J + 1, ntile);
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int cnt = (issued - s2 + 1) / 2;
+            if (cnt > 0) tc::mbar_wait(tc::smem_u32(&mbar[s2]), (cnt - 1) & 1);
         }
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 0) {
         tc::fence_after();
-        tc::tmem_dealloc(taddr, 2 * ST_N);
+        tc::tmem_dealloc(taddr, 4 * ST_N);
     }
 }
 
@@ -1367,11 +1430,9 @@ static void ldlt_steps(gw_ctx* ctx, const C* chi0, C* fac, int n, int N, C* linv
         if (m == 0) break;
         if constexpr (sizeof(C) == 8) {
             // binary32: trailing updates with at least one full 128-row block on the tensor cores
-            const long long tiles = st_tile_count(m);
-            if (!ctx->syrk_simt && m >= 128 && tiles <= 0x7fffffffLL && N <= 65535) {
-                const size_t smem = 2 * (size_t)ST_A_BYTES + 2 * (size_t)ST_B_BYTES;
+            if (!ctx->syrk_simt && m >= 128 && N <= 65535) {
                 allow_max_smem(k_ldlt_syrk_tc);
-                klaunch(ctx, names[3], k_ldlt_syrk_tc, dim3((unsigned)tiles, N), 256, smem, (float2*)fac, n, k0,
+                klaunch(ctx, names[3], k_ldlt_syrk_tc, dim3(div_up(m, 128), N), 256, ST_SMEM, (float2*)fac, n, k0,
                         ctx->d_status);
                 continue;
             }
