@@ -184,7 +184,7 @@ KERNELS = ["k_forms", "k_forms32", "k_forms32_tc", "k_forms32_tm", "k_forms_diag
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
 # of the current kernel version on this workload (profiles/k_*_ring12.md);
 # an entry is dropped whenever its kernel changes.
-NCU_TRAFFIC = {"k_forms32": 4.489e8}
+NCU_TRAFFIC = {}
 
 
 def _panels(n, nb):
@@ -215,8 +215,12 @@ def kernel_model(name, mol, grid, n_rank):
     if name.startswith("k_ldlt") and name.endswith("_panel"):
         return N * 8.0 * sum(kb ** 3 / 6 + m * kb * (kb - 1) / 2 for kb, m in P), "alu", peak
     if name in ("k_forms32_tc", "k_forms32_tm"):
-        # same forward substitution; the updates below the panels run as 3xTF32 tensor-core products
-        return (N - 1) * 8.0 * R * n * (n - 1) / 2, "tensor", PEAK_TF32_TFLOPS
+        # same forward substitution; the updates below the panels run as 3xTF32 tensor-core products,
+        # whose binary32-product ceiling is a third of the TF32 peak
+        return (N - 1) * 8.0 * R * n * (n - 1) / 2, "tensor", PEAK_TF32_TFLOPS / 3
+    if name == "k_ldlt32_syrk_tc":
+        # the trailing updates of 128 rows or more (the smaller ones stay on the FMA units)
+        return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if m >= 128), "tensor", PEAK_TF32_TFLOPS / 3
     if name.startswith("k_forms"):
         # forward substitution L y = q: n(n-1)/2 complex multiply-adds per right-hand side and frequency
         return (N - 1) * 8.0 * R * n * (n - 1) / 2, "alu", peak
@@ -386,8 +390,8 @@ def run_gpu(a):
     single_ms = single["t_ms"] / a.steps
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": NCU_TRAFFIC.get(dom),
-            "peak_source": (PEAK_TF32_SOURCE + " (dense TF32 tensor; 3xTF32 issues 3x the algorithmic products)"
-                            if peak == PEAK_TF32_TFLOPS else
+            "peak_source": (PEAK_TF32_SOURCE + " = dense TF32 tensor peak, / 3: 3xTF32 takes three TF32 products "
+                            "per binary32 product" if bound == "tensor" else
                             ("128 binary32 FMA/clk/SM" if peak == PEAK_FP32_TFLOPS else "2 binary64 FMA/clk/SM")
                             + " x 152 SMs x 2070 MHz (recipe unit counts and maximum clock)"),
             "avg_launch_ms": avg_s * 1e3, "launches": k_n, "flops_per_launch": per_launch,
