@@ -444,9 +444,11 @@ __global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fa
         tc::mbar_init(&mbar[1]);
     }
     if (tid < 32) dd[tid] = A[tri(k0 + tid) + k0 + tid];
-    float2 wr[2][2], cn[4][4], cp[4][4];
+    // entries of M of the next two tiles in flight (tile J - 1 is read back while J and J + 1 load)
+    float2 wr[2][2], cn[4][4], cn2[4][4], cp[4][4];
     st_load_b(wr, A, n, k0, k1);
     st_load_c(cn, A, n, rw, k1 + 16 * h);
+    if (ntile > 1) st_load_c(cn2, A, n, rw, k1 + ST_NC + 16 * h);
     // A operand: rows r0 .. r0 + 127 of the panel, staged once
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -502,8 +504,11 @@ __global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fa
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int t = 0; t < 4; ++t) cp[i][t] = cn[i][t];
-            if (J < ntile) st_load_c(cn, A, n, rw, k1 + ST_NC * J + 16 * h);
+                for (int t = 0; t < 4; ++t) {
+                    cp[i][t] = cn[i][t];
+                    cn[i][t] = cn2[i][t];
+                }
+            if (J + 1 < ntile) st_load_c(cn2, A, n, rw, k1 + ST_NC * (J + 1) + 16 * h);
             ok = tc::mbar_wait(tc::smem_u32(&mbar[Jp & 1]), (Jp >> 1) & 1) && ok;
             ok = __syncthreads_and(ok);
             if (!ok) break;
