@@ -908,8 +908,7 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
     __syncthreads();
     tc::fence_after();
     const uint32_t taddr = tbase;
-    uint32_t uses[TM_NS] = {0, 0, 0};
-    int stage = 0;
+    int stage = 0;          // operand stages issued; stage s uses buffer s % TM_NS for the (s / TM_NS)-th time
     bool ok = true;
     double part = 0.0;
     for (int b = 0; b < nblk; ++b) {
@@ -1019,7 +1018,7 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
 #pragma unroll
             for (int qk = 0; qk < 4; ++qk, ++stage) {
                 const int buf = stage % TM_NS;
-                if (stage >= TM_NS) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[buf]), (uses[buf] - 1) & 1) && ok;
+                if (stage >= TM_NS) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[buf]), ((stage / TM_NS) - 1) & 1) && ok;
                 unsigned char* ah = sA + 2 * buf * TM_A_BYTES;
                 if ((qk & 1) == 0) {
                     tm_store(ah, ah + TM_A_BYTES, av0);
@@ -1048,13 +1047,14 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
                     if (T == T_first && qk == 3) tc::commit(tc::smem_u32(&mbar_next));
                     if (T == nt - 1 && qk == 3) tc::commit(tc::smem_u32(&mbar_all));
                 }
-                ++uses[buf];
             }
         }
     }
     // every MMA done before the accumulators are released
-    for (int i = 0; i < TM_NS; ++i)
-        if (uses[i] > 0) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[i]), (uses[i] - 1) & 1) && ok;
+    for (int i = 0; i < TM_NS; ++i) {
+        const int cnt = (stage - i + TM_NS - 1) / TM_NS;     // stages that used buffer i
+        if (cnt > 0) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[i]), (cnt - 1) & 1) && ok;
+    }
     cp_async_wait<0>();
     ok = __syncthreads_and(ok);
     if (!ok && tid == 0) atomicOr(status, ST_TIMEOUT);

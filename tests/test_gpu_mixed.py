@@ -152,3 +152,37 @@ def test_ring12_syrk_tensor_vs_fma(gwlib, ctx, cfg2, cfg2_oracle):
     assert rel(chi_tc, chi_fma) < 1e-4
     assert rel(c_tc, c_fma) < 1e-4
     assert np.abs(e_tc - e_fma).max() < 0.05 * MEV
+
+
+@pytest.mark.parametrize("atoms", [4, 5, 12])
+def test_tensor_memory_forms_sizes(gwlib, ctx, atoms):
+    """Tensor-memory forms over one, two and three 128-row tiles (N_sub = 120,
+    150, 360; ragged last tile) and, at N_sub = 360, the tensor-core trailing
+    updates: the same c_r(s_j) as the FMA-unit forms to binary32 accuracy,
+    quasiparticle energies within 1 meV of the oracle on the same root
+    branch."""
+    import oracle
+    import synth
+    from synth import molecules as sm
+    mol = sm._uniform_molecule("chain", atoms, sm.SEED_BASE + 7700 + atoms)
+    assert mol.n_sub == 30 * atoms
+    grid = synth.Grid(256)
+    r = oracle.solve(mol, grid)
+    h, e, z, st = _mixed(gwlib, ctx, mol, grid)
+    try:
+        c_tm = h["sigma"].copy()["c"]
+        assert np.abs(e - r["e_qp"]).max() < MEV
+        assert np.array_equal(st, r["status"])
+    finally:
+        _free(h)
+    ctx.set_option(gwlib.GW_OPT_FORMS_SIMT, 1)
+    try:
+        h, e2, z2, st2 = _mixed(gwlib, ctx, mol, grid)
+        try:
+            c_fma = h["sigma"].copy()["c"]
+        finally:
+            _free(h)
+    finally:
+        ctx.set_option(gwlib.GW_OPT_FORMS_SIMT, 0)
+    assert rel(c_tm, c_fma) < 2e-5
+    assert np.abs(e - e2).max() < 0.05 * MEV
