@@ -632,9 +632,27 @@ static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n
         // V^{nk}_mu, columns r = i*n_orb + k
         Vnk = dalloc<double>(ctx, (size_t)n_prod * R);
         launch_vertex_contract(ctx, mol, Es, n_states, Fs, n_orb, nullptr, Vnk, R);
-        // q_nk = Zup^T V^{nk}: Q [n_sub][R]
+        // q_nk = Zup^T V^{nk}: Q [n_sub][R] (the binary32 forms read it in
+        // binary32, so the mixed path forms it in binary32)
         Q = dalloc<double>(ctx, (size_t)n_sub * R);
-        gemm_f64(ctx, true, false, n_sub, R, n_prod, 1.0, c->Zup, n_sub, Vnk, R, 0.0, Q, R);
+        if (c->prec == GW_MIXED) {
+            float *Zup32 = nullptr, *V32 = nullptr, *Q32 = nullptr;
+            try {
+                Zup32 = dalloc<float>(ctx, (size_t)n_prod * n_sub);
+                V32 = dalloc<float>(ctx, (size_t)n_prod * R);
+                Q32 = dalloc<float>(ctx, (size_t)n_sub * R);
+                launch_to_f32(ctx, c->Zup, Zup32, (long long)n_prod * n_sub);
+                launch_to_f32(ctx, Vnk, V32, (long long)n_prod * R);
+                gemm_f32(ctx, true, false, n_sub, R, n_prod, 1.f, Zup32, n_sub, V32, R, 0.f, Q32, R);
+                launch_to_f64(ctx, Q32, Q, (long long)n_sub * R);
+            } catch (...) {
+                ctx_free(ctx, Zup32); ctx_free(ctx, V32); ctx_free(ctx, Q32);
+                throw;
+            }
+            ctx_free(ctx, Zup32); ctx_free(ctx, V32); ctx_free(ctx, Q32);
+        } else {
+            gemm_f64(ctx, true, false, n_sub, R, n_prod, 1.0, c->Zup, n_sub, Vnk, R, 0.0, Q, R);
+        }
         // c_nk(s_j)
         s->c = dalloc<double>(ctx, (size_t)R * N);
         launch_forms(ctx, W, Q, R, s->c);

@@ -614,6 +614,13 @@ __global__ void k_ns_coeff(double* __restrict__ G, int m) {          // G <- (3 
     G[t] = 0.5 * ((i == j ? 3.0 : 0.0) - G[t]);
 }
 
+__global__ void k_ns_coeff32(float* __restrict__ G, int m) {          // G <- (3 I - G)/2
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)m * m) return;
+    int i = (int)(t / m), j = (int)(t % m);
+    G[t] = 0.5f * ((i == j ? 3.f : 0.f) - G[t]);
+}
+
 // lam[k] = B[:, k]^T T[:, k] (B, T row-major n x n_sub), one CTA per column
 __global__ void __launch_bounds__(256) k_rayleigh_cols(const double* __restrict__ B, const double* __restrict__ T,
                                                        int n, int n_sub, double* __restrict__ lam) {
@@ -688,14 +695,14 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int 
     double *X = nullptr, *X2 = nullptr, *R = nullptr, *S = nullptr, *T = nullptr, *E = nullptr, *lam = nullptr;
     double *stat = nullptr, *G = nullptr, *Bt = nullptr;
     void* gws = nullptr;
-    float *vb = nullptr, *pb = nullptr, *pt = nullptr;
+    float *vb = nullptr, *pb = nullptr, *pt = nullptr, *Bt32 = nullptr, *G32 = nullptr, *B32 = nullptr;
     unsigned int* bar = nullptr;
     int* sel = nullptr;
     auto release = [&]() {
         for (void* p : {(void*)A32, (void*)d, (void*)e, (void*)tau, (void*)lam32, (void*)Y,
                         (void*)X, (void*)X2, (void*)R, (void*)S, (void*)T, (void*)E, (void*)lam, (void*)stat,
                         (void*)G, (void*)Bt, (void*)sel, (void*)gws, (void*)vb, (void*)pb, (void*)pt,
-                        (void*)bar})
+                        (void*)bar, (void*)Bt32, (void*)G32, (void*)B32})
             ctx_free(ctx, p);
     };
     try {
@@ -830,9 +837,22 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int 
         }
         klaunch(ctx, "k_gather_cols", k_gather_cols, div_up((long long)n * n_sub, 256), 256, 0, (const double*)X, n,
                 n_sub, (const int*)sel, Bt);
-        gemm_f64(ctx, true, false, n_sub, n_sub, n, 1.0, Bt, n_sub, Bt, n_sub, 0.0, G, n_sub);
-        klaunch(ctx, "k_ns_coeff", k_ns_coeff, div_up((long long)n_sub * n_sub, 256), 256, 0, G, n_sub);
-        gemm_f64(ctx, false, false, n, n_sub, n_sub, 1.0, Bt, n_sub, G, n_sub, 0.0, B, n_sub);
+        if (oa_iters == 0 && !g) {
+            // binary32 basis (the caller forms Z = X_r B in binary32): the
+            // Newton-Schulz step B = Bt (3 I - Bt^T Bt) / 2 in binary32 as well
+            Bt32 = dalloc<float>(ctx, (size_t)n * n_sub);
+            G32 = dalloc<float>(ctx, (size_t)n_sub * n_sub);
+            B32 = dalloc<float>(ctx, (size_t)n * n_sub);
+            launch_to_f32(ctx, Bt, Bt32, (long long)n * n_sub);
+            gemm_f32(ctx, true, false, n_sub, n_sub, n, 1.f, Bt32, n_sub, Bt32, n_sub, 0.f, G32, n_sub);
+            klaunch(ctx, "k_ns_coeff32", k_ns_coeff32, div_up((long long)n_sub * n_sub, 256), 256, 0, G32, n_sub);
+            gemm_f32(ctx, false, false, n, n_sub, n_sub, 1.f, Bt32, n_sub, G32, n_sub, 0.f, B32, n_sub);
+            launch_to_f64(ctx, B32, B, (long long)n * n_sub);
+        } else {
+            gemm_f64(ctx, true, false, n_sub, n_sub, n, 1.0, Bt, n_sub, Bt, n_sub, 0.0, G, n_sub);
+            klaunch(ctx, "k_ns_coeff", k_ns_coeff, div_up((long long)n_sub * n_sub, 256), 256, 0, G, n_sub);
+            gemm_f64(ctx, false, false, n, n_sub, n_sub, 1.0, Bt, n_sub, G, n_sub, 0.0, B, n_sub);
+        }
         if (oa_iters == 0 && !g) {
             // no binary64 g: B is returned orthonormal and unscaled (the caller
             // scales the basis it builds from it)
