@@ -492,14 +492,21 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
                     gemm_f32(ctx, false, false, n_prod, n_sub, nr, 1.f, X32, nr, B32, n_sub, 0.f, Z32, n_sub);
                     c->Z = dalloc<double>(ctx, (size_t)n_prod * n_sub);
                     launch_to_f64(ctx, Z32, c->Z, (long long)n_prod * n_sub);
+                    // Zup = v Z in binary32 too (B32 is reused for it)
+                    ctx_free(ctx, B32); B32 = nullptr;
+                    v32 = dalloc<float>(ctx, (size_t)n_prod * n_prod);
+                    B32 = dalloc<float>(ctx, (size_t)n_prod * n_sub);
+                    launch_to_f32(ctx, mol->v, v32, (long long)n_prod * n_prod);
+                    gemm_f32(ctx, false, false, n_prod, n_sub, n_prod, 1.f, v32, n_prod, Z32, n_sub, 0.f, B32, n_sub);
+                    launch_to_f64(ctx, B32, c->Zup, (long long)n_prod * n_sub);
                 } catch (...) {
                     ctx_free(ctx, v32); ctx_free(ctx, X32); ctx_free(ctx, T32); ctx_free(ctx, g32);
                     ctx_free(ctx, B32); ctx_free(ctx, Z32);
                     throw;
                 }
-                ctx_free(ctx, X32); ctx_free(ctx, B32); ctx_free(ctx, Z32);
-                gemm_f64(ctx, false, false, n_prod, n_sub, n_prod, 1.0, mol->v, n_prod, c->Z, n_sub, 0.0, c->Zup,
-                         n_sub);
+                ctx_free(ctx, v32); ctx_free(ctx, X32); ctx_free(ctx, B32); ctx_free(ctx, Z32);
+                // binary64 Rayleigh quotients Z_j^T Zup_j of the stored pair; the
+                // scaling makes them exactly one
                 basis_rayleigh_scale(ctx, c->Z, c->Zup, n_prod, n_sub);
             }
         }
@@ -629,29 +636,38 @@ static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n
         std::vector<double> eks(n_states);
         for (int i = 0; i < n_states; ++i) eks[i] = mol->h_eps[states[i]];
         s->eks = upload(ctx, eks.data(), n_states);
-        // V^{nk}_mu, columns r = i*n_orb + k
+        // V^{nk}_mu, columns r = i*n_orb + k; q_nk = Zup^T V^{nk}: Q [n_sub][R];
+        // T = v V^{nk} for Sigma_x.  The mixed path forms all three in
+        // binary32 (its forms read q in binary32) and keeps binary64 copies
+        // of V^{nk} and T for the Sigma_x sums.
         Vnk = dalloc<double>(ctx, (size_t)n_prod * R);
-        launch_vertex_contract(ctx, mol, Es, n_states, Fs, n_orb, nullptr, Vnk, R);
-        // q_nk = Zup^T V^{nk}: Q [n_sub][R] (the binary32 forms read it in
-        // binary32, so the mixed path forms it in binary32)
         Q = dalloc<double>(ctx, (size_t)n_sub * R);
+        T = dalloc<double>(ctx, (size_t)n_prod * R);
         if (c->prec == GW_MIXED) {
-            float *Zup32 = nullptr, *V32 = nullptr, *Q32 = nullptr;
+            float *Zup32 = nullptr, *V32 = nullptr, *Q32 = nullptr, *v32 = nullptr, *T32 = nullptr;
             try {
-                Zup32 = dalloc<float>(ctx, (size_t)n_prod * n_sub);
                 V32 = dalloc<float>(ctx, (size_t)n_prod * R);
+                launch_vertex_contract32(ctx, mol, Es, n_states, Fs, n_orb, nullptr, V32, R);
+                Zup32 = dalloc<float>(ctx, (size_t)n_prod * n_sub);
                 Q32 = dalloc<float>(ctx, (size_t)n_sub * R);
                 launch_to_f32(ctx, c->Zup, Zup32, (long long)n_prod * n_sub);
-                launch_to_f32(ctx, Vnk, V32, (long long)n_prod * R);
                 gemm_f32(ctx, true, false, n_sub, R, n_prod, 1.f, Zup32, n_sub, V32, R, 0.f, Q32, R);
                 launch_to_f64(ctx, Q32, Q, (long long)n_sub * R);
+                v32 = dalloc<float>(ctx, (size_t)n_prod * n_prod);
+                T32 = dalloc<float>(ctx, (size_t)n_prod * R);
+                launch_to_f32(ctx, mol->v, v32, (long long)n_prod * n_prod);
+                gemm_f32(ctx, false, false, n_prod, R, n_prod, 1.f, v32, n_prod, V32, R, 0.f, T32, R);
+                launch_to_f64(ctx, V32, Vnk, (long long)n_prod * R);
+                launch_to_f64(ctx, T32, T, (long long)n_prod * R);
             } catch (...) {
-                ctx_free(ctx, Zup32); ctx_free(ctx, V32); ctx_free(ctx, Q32);
+                ctx_free(ctx, Zup32); ctx_free(ctx, V32); ctx_free(ctx, Q32); ctx_free(ctx, v32); ctx_free(ctx, T32);
                 throw;
             }
-            ctx_free(ctx, Zup32); ctx_free(ctx, V32); ctx_free(ctx, Q32);
+            ctx_free(ctx, Zup32); ctx_free(ctx, V32); ctx_free(ctx, Q32); ctx_free(ctx, v32); ctx_free(ctx, T32);
         } else {
+            launch_vertex_contract(ctx, mol, Es, n_states, Fs, n_orb, nullptr, Vnk, R);
             gemm_f64(ctx, true, false, n_sub, R, n_prod, 1.0, c->Zup, n_sub, Vnk, R, 0.0, Q, R);
+            gemm_f64(ctx, false, false, n_prod, R, n_prod, 1.0, mol->v, n_prod, Vnk, R, 0.0, T, R);
         }
         // c_nk(s_j)
         s->c = dalloc<double>(ctx, (size_t)R * N);
@@ -662,8 +678,6 @@ static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n
         s->sigc = dalloc<double2>(ctx, (size_t)n_states * (2 * N - 1));
         launch_sigma_c(ctx, s);
         // Sigma_x = -sum_{k occ} V^{nk} v V^{nk}
-        T = dalloc<double>(ctx, (size_t)n_prod * R);
-        gemm_f64(ctx, false, false, n_prod, R, n_prod, 1.0, mol->v, n_prod, Vnk, R, 0.0, T, R);
         s->sx = dalloc<double>(ctx, n_states);
         launch_sigma_x(ctx, s, Vnk, T, R);
         ctx_finish(ctx, "gw_sigma_diag");
