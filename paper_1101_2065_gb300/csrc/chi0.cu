@@ -158,15 +158,6 @@ __device__ C* fft_smem(C* a, C* b, int L, int logL, const C* ptw, bool inverse) 
     return a;
 }
 
-__device__ __forceinline__ void tri_index(long long e, int& m, int& n) {
-    // packed lower triangle: e = m(m+1)/2 + n, 0 <= n <= m
-    long long mm = (long long)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-    while (mm * (mm + 1) / 2 > e) --mm;
-    while ((mm + 1) * (mm + 2) / 2 <= e) ++mm;
-    m = (int)mm;
-    n = (int)(e - mm * (mm + 1) / 2);
-}
-
 __global__ void k_twiddles(double2* __restrict__ tw, int L) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L / 2) return;
@@ -204,31 +195,6 @@ __global__ void k_kernel_spectra(const double2* __restrict__ tw, int N, int logL
     double2* r = fft_smem(a, b, L, logL, (const double2*)tws, false);
     double2* out = blockIdx.x == 0 ? C1 : C2;
     for (int d = threadIdx.x; d < L; d += blockDim.x) out[d] = r[d];
-}
-
-// Tent-deposited weight of bin j = j_lo + b for the element pair (m1,n1),(m2,n2).
-template <typename R>
-__device__ __forceinline__ void deposit2(int b, int nb_bins, const int* __restrict__ seg,
-                                         const double* __restrict__ frac, const R* __restrict__ Ut, int n_pair,
-                                         int m1, int n1, int m2, int n2, R& a1, R& a2) {
-    a1 = R(0);
-    a2 = R(0);
-    const R* u1 = Ut + (long long)m1 * n_pair;
-    const R* v1 = Ut + (long long)n1 * n_pair;
-    const R* u2 = Ut + (long long)m2 * n_pair;
-    const R* v2 = Ut + (long long)n2 * n_pair;
-    if (b < nb_bins)
-        for (int p = seg[b]; p < seg[b + 1]; ++p) {
-            R w = R(2.0 * (1.0 - frac[p]));
-            a1 = fma(w * u1[p], v1[p], a1);
-            a2 = fma(w * u2[p], v2[p], a2);
-        }
-    if (b >= 1)
-        for (int p = seg[b - 1]; p < seg[b]; ++p) {
-            R w = R(2.0 * frac[p]);
-            a1 = fma(w * u1[p], v1[p], a1);
-            a2 = fma(w * u2[p], v2[p], a2);
-        }
 }
 
 // lower-triangular tile index tt -> (I, J), J <= I
@@ -328,10 +294,7 @@ __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __r
     C* tws = sbuf + 3 * L;                 // per-pass twiddle tables
     build_pass_twiddles(tws, tw, L, logL);
     for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
-        int m1, n1, m2, n2;
-        tri_index(2 * g, m1, n1);
-        bool two = 2 * g + 1 < n_el;
-        if (two) tri_index(2 * g + 1, m2, n2); else { m2 = m1; n2 = n1; }
+        const bool two = 2 * g + 1 < n_el;
         for (int d = threadIdx.x; d < L; d += blockDim.x) B0[d] = Real<C>::make(R(0), R(0));
         __syncthreads();
         for (int b = threadIdx.x; b < band; b += blockDim.x) {
