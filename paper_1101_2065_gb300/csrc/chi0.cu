@@ -197,6 +197,31 @@ __global__ void k_kernel_spectra(const double2* __restrict__ tw, int N, int logL
     for (int d = threadIdx.x; d < L; d += blockDim.x) out[d] = r[d];
 }
 
+// Tent-deposited weight of bin j = j_lo + b for the element pair (m1,n1),(m2,n2).
+template <typename R>
+__device__ __forceinline__ void deposit2(int b, int nb_bins, const int* __restrict__ seg,
+                                         const double* __restrict__ frac, const R* __restrict__ Ut, int n_pair,
+                                         int m1, int n1, int m2, int n2, R& a1, R& a2) {
+    a1 = R(0);
+    a2 = R(0);
+    const R* u1 = Ut + (long long)m1 * n_pair;
+    const R* v1 = Ut + (long long)n1 * n_pair;
+    const R* u2 = Ut + (long long)m2 * n_pair;
+    const R* v2 = Ut + (long long)n2 * n_pair;
+    if (b < nb_bins)
+        for (int p = seg[b]; p < seg[b + 1]; ++p) {
+            R w = R(2.0 * (1.0 - frac[p]));
+            a1 = fma(w * u1[p], v1[p], a1);
+            a2 = fma(w * u2[p], v2[p], a2);
+        }
+    if (b >= 1)
+        for (int p = seg[b - 1]; p < seg[b]; ++p) {
+            R w = R(2.0 * frac[p]);
+            a1 = fma(w * u1[p], v1[p], a1);
+            a2 = fma(w * u2[p], v2[p], a2);
+        }
+}
+
 // lower-triangular tile index tt -> (I, J), J <= I
 __device__ __forceinline__ void tile_ij(int tt, int& I, int& J) {
     I = (int)((sqrtf(8.0f * tt + 1.0f) - 1.0f) * 0.5f);
