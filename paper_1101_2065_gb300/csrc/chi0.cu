@@ -39,6 +39,10 @@ __device__ __forceinline__ C tw_at(const C* __restrict__ tw, int t, int L) {   /
     w.y = -w.y;
     return w;
 }
+// FFT buffers in shared memory are padded by one entry per 16 (index fp(i)):
+// the strided writes of the first two passes then fall in distinct banks.
+__host__ __device__ __forceinline__ int fp(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int fft_buf_len(int L) { return L + (L >> 4); }
 __device__ __forceinline__ int first_radix(int logL) { return logL % 3 == 1 ? 2 : logL % 3 == 2 ? 4 : 1; }
 __host__ __device__ __forceinline__ int pass_twiddle_count(int logL) {   // entries of all per-pass tables
     int Ns = logL % 3 == 1 ? 2 : logL % 3 == 2 ? 4 : 1, tot = 0;
@@ -112,7 +116,7 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __rest
         const int k = j & (Ns - 1);
         C x[RAD];
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) x[r] = a[j + r * nb];
+        for (int r = 0; r < RAD; ++r) x[r] = a[fp(j + r * nb)];
         if constexpr (RAD == 8) {
             C w1 = ptw[k], w2 = ptw[Ns + k], w4 = ptw[2 * Ns + k];
             if (INV) { w1.y = -w1.y; w2.y = -w2.y; w4.y = -w4.y; }
@@ -129,7 +133,7 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ a, C* __rest
         }
         const int base = (j - k) * RAD + k;
 #pragma unroll
-        for (int q = 0; q < RAD; ++q) b[base + q * Ns] = x[q];
+        for (int q = 0; q < RAD; ++q) b[fp(base + q * Ns)] = x[q];
     }
 }
 
@@ -172,14 +176,20 @@ __device__ __forceinline__ double2 kappa(long long d, double dw, double eta) {
     return make_double2(x / den, -eta / den);
 }
 
+// per-pass twiddle tables of the FFT in global memory (one CTA)
+template <typename C>
+__global__ void k_pass_twiddles(const C* __restrict__ tw, int L, int logL, C* __restrict__ ptw) {
+    build_pass_twiddles(ptw, tw, L, logL);
+}
+
 // C1 and C2 (one CTA each): build the kernel sequence, forward FFT.
 __global__ void k_kernel_spectra(const double2* __restrict__ tw, int N, int logL, double dw, double eta,
                                  double2* __restrict__ C1, double2* __restrict__ C2) {
     extern __shared__ double2 sbuf[];
-    const int L = 2 * N;
+    const int L = 2 * N, LB = fft_buf_len(L);
     double2* a = sbuf;
-    double2* b = sbuf + L;
-    double2* tws = sbuf + 2 * L;
+    double2* b = sbuf + LB;
+    double2* tws = sbuf + 2 * LB;
     build_pass_twiddles(tws, tw, L, logL);
     for (int d = threadIdx.x; d < L; d += blockDim.x) {
         double2 v = make_double2(0.0, 0.0);
@@ -189,12 +199,12 @@ __global__ void k_kernel_spectra(const double2* __restrict__ tw, int N, int logL
         } else {
             if (d <= 2 * N - 2) v = kappa(d, dw, eta);
         }
-        a[d] = v;
+        a[fp(d)] = v;
     }
     __syncthreads();
     double2* r = fft_smem(a, b, L, logL, (const double2*)tws, false);
     double2* out = blockIdx.x == 0 ? C1 : C2;
-    for (int d = threadIdx.x; d < L; d += blockDim.x) out[d] = r[d];
+    for (int d = threadIdx.x; d < L; d += blockDim.x) out[d] = r[fp(d)];
 }
 
 // Tent-deposited weight of bin j = j_lo + b for the element pair (m1,n1),(m2,n2).
@@ -303,28 +313,27 @@ template <> struct Real<float2> { typedef float T; static __device__ float2 make
 template <typename C>
 __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __restrict__ A, int n_sub,
                                                   int j_lo, int nb_bins, int N, int logL,
-                                                  const C* __restrict__ tw, const C* __restrict__ C1,
+                                                  const C* __restrict__ ptw, const C* __restrict__ C1,
                                                   const C* __restrict__ C2, C* __restrict__ chi0) {
     typedef typename Real<C>::T R;
     extern __shared__ __align__(16) unsigned char sraw[];
     C* sbuf = reinterpret_cast<C*>(sraw);
-    const int L = 2 * N;
+    const int L = 2 * N, LB = fft_buf_len(L);
     const int band = nb_bins + 1;
     const long long n_el = (long long)n_sub * (n_sub + 1) / 2;
     const long long n_grp = (n_el + 1) / 2;
     const R scale = R(1.0 / (double)L);
     C* B0 = sbuf;
-    C* B1 = sbuf + L;
-    C* B2 = sbuf + 2 * L;
-    C* tws = sbuf + 3 * L;                 // per-pass twiddle tables
-    build_pass_twiddles(tws, tw, L, logL);
+    C* B1 = sbuf + LB;
+    C* B2 = sbuf + 2 * LB;
+    const C* tws = ptw;                    // per-pass twiddle tables (global, cached)
     for (long long g = blockIdx.x; g < n_grp; g += gridDim.x) {
         const bool two = 2 * g + 1 < n_el;
-        for (int d = threadIdx.x; d < L; d += blockDim.x) B0[d] = Real<C>::make(R(0), R(0));
+        for (int d = threadIdx.x; d < LB; d += blockDim.x) B0[d] = Real<C>::make(R(0), R(0));
         __syncthreads();
         for (int b = threadIdx.x; b < band; b += blockDim.x) {
             const R* Ab = A + (long long)b * n_el + 2 * g;
-            B0[j_lo + b] = Real<C>::make(Ab[0], two ? Ab[1] : R(0));
+            B0[fp(j_lo + b)] = Real<C>::make(Ab[0], two ? Ab[1] : R(0));
         }
         __syncthreads();
         C* Zb = fft_smem(B0, B1, L, logL, (const C*)tws, false);
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __r
         // split the two real transforms and apply the kernel spectra
         for (int m = threadIdx.x; m <= N; m += blockDim.x) {
             int mr = (L - m) & (L - 1);
-            C zm = Zb[m], zr = Zb[mr];
+            C zm = Zb[fp(m)], zr = Zb[fp(mr)];
             // X1 = (Z[m] + conj Z[L-m])/2, X2 = (Z[m] - conj Z[L-m])/(2i)
             const R h = R(0.5);
             C x1 = Real<C>::make(h * (zm.x + zr.x), h * (zm.y - zr.y));
@@ -342,9 +351,9 @@ __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __r
             C y2m = csub(cmul(x2, c1m), cmul(cconj(x2), c2m));
             C y1r = csub(cmul(cconj(x1), c1r), cmul(x1, c2r));
             C y2r = csub(cmul(cconj(x2), c1r), cmul(x2, c2r));
-            Y1[m] = y1m;
-            Zb[m] = y2m;
-            if (mr != m) { Y1[mr] = y1r; Zb[mr] = y2r; }
+            Y1[fp(m)] = y1m;
+            Zb[fp(m)] = y2m;
+            if (mr != m) { Y1[fp(mr)] = y1r; Zb[fp(mr)] = y2r; }
         }
         __syncthreads();
         C* r1 = fft_smem(Y1, B2, L, logL, (const C*)tws, true);
@@ -352,11 +361,11 @@ __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __r
         C* r2 = fft_smem(Zb, free1, L, logL, (const C*)tws, true);
         // packed lower triangle: the group's elements are 2g and 2g + 1
         for (int k = threadIdx.x; k < N; k += blockDim.x) {
-            C v1 = r1[k];
+            C v1 = r1[fp(k)];
             C* row = chi0 + (long long)k * n_el + 2 * g;
             row[0] = Real<C>::make(v1.x * scale, v1.y * scale);
             if (two) {
-                C v2 = r2[k];
+                C v2 = r2[fp(k)];
                 row[1] = Real<C>::make(v2.x * scale, v2.y * scale);
             }
         }
@@ -405,7 +414,7 @@ void launch_fft_tables(gw_ctx* ctx, gw_chi0* c) {
     c->C1 = dalloc<double2>(ctx, L);
     c->C2 = dalloc<double2>(ctx, L);
     klaunch(ctx, "k_twiddles", k_twiddles, div_up(L / 2, 256), 256, 0, c->tw, L);
-    size_t smem = (2 * (size_t)L + pass_twiddle_count(c->logL)) * sizeof(double2);
+    size_t smem = (2 * (size_t)fft_buf_len(L) + pass_twiddle_count(c->logL)) * sizeof(double2);
     allow_max_smem(k_kernel_spectra);
     klaunch(ctx, "k_kernel_spectra", k_kernel_spectra, 2, 256, smem, c->tw, N, c->logL, c->grid.d_omega, c->grid.eta, c->C1, c->C2);
 }
@@ -426,8 +435,9 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
     const int L = c->L, N = c->grid.n_omega, n = c->n_sub;
     const bool f32 = c->prec == GW_MIXED;
     const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
-    size_t smem = (3 * (size_t)L + pass_twiddle_count(c->logL)) * csz;
+    size_t smem = 3 * (size_t)fft_buf_len(L) * csz;
     if (smem > 227 * 1024) gw_throw(GW_ERR_INVALID_ARG, "n_omega too large for the FFT kernel");
+    const int ntw = pass_twiddle_count(c->logL);
     int per_sm = std::max(1, (int)((228 * 1024) / (smem + 1024)));
     const long long n_el = (long long)n * (n + 1) / 2;
     long long n_grp = (n_el + 1) / 2;
@@ -445,29 +455,39 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
         launch_to_f32(ctx, (const double*)c->C1, (float*)c->C1_32, 2LL * L);
         launch_to_f32(ctx, (const double*)c->C2, (float*)c->C2_32, 2LL * L);
         float* A = dalloc<float>(ctx, band * n_el);
+        float2* ptw = nullptr;
         try {
+            ptw = dalloc<float2>(ctx, std::max(ntw, 1));
+            klaunch(ctx, "k_pass_twiddles", k_pass_twiddles<float2>, 1, 256, 0, (const float2*)c->tw32, L, c->logL, ptw);
             deposit<float>(ctx, c, c->Ut32, A, n_el);
             c->chi0_32 = dalloc<float2>(ctx, (size_t)N * n_el);
             allow_max_smem(k_chi0_fft<float2>);
             klaunch(ctx, "k_chi0_fft32", k_chi0_fft<float2>, grid, 256, smem, (const float*)A, n, c->j_lo, c->nb_bins,
-                    N, c->logL, (const float2*)c->tw32, (const float2*)c->C1_32, (const float2*)c->C2_32, c->chi0_32);
+                    N, c->logL, (const float2*)ptw, (const float2*)c->C1_32, (const float2*)c->C2_32, c->chi0_32);
         } catch (...) {
             ctx_free(ctx, A);
+            ctx_free(ctx, ptw);
             throw;
         }
         ctx_free(ctx, A);
+        ctx_free(ctx, ptw);
     } else {
         double* A = dalloc<double>(ctx, band * n_el);
+        double2* ptw = nullptr;
         try {
+            ptw = dalloc<double2>(ctx, std::max(ntw, 1));
+            klaunch(ctx, "k_pass_twiddles", k_pass_twiddles<double2>, 1, 256, 0, (const double2*)c->tw, L, c->logL, ptw);
             deposit<double>(ctx, c, c->Ut, A, n_el);
             c->chi0 = dalloc<double2>(ctx, (size_t)N * n_el);
             allow_max_smem(k_chi0_fft<double2>);
             klaunch(ctx, "k_chi0_fft", k_chi0_fft<double2>, grid, 256, smem, (const double*)A, n, c->j_lo, c->nb_bins,
-                    N, c->logL, (const double2*)c->tw, (const double2*)c->C1, (const double2*)c->C2, c->chi0);
+                    N, c->logL, (const double2*)ptw, (const double2*)c->C1, (const double2*)c->C2, c->chi0);
         } catch (...) {
             ctx_free(ctx, A);
+            ctx_free(ctx, ptw);
             throw;
         }
+        ctx_free(ctx, ptw);
         ctx_free(ctx, A);
     }
 }
