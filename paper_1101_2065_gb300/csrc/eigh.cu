@@ -621,7 +621,8 @@ __global__ void k_ns_coeff32(float* __restrict__ G, int m) {          // G <- (3
     G[t] = 0.5f * ((i == j ? 3.f : 0.f) - G[t]);
 }
 
-// lam[k] = B[:, k]^T T[:, k] (B, T row-major n x n_sub), one CTA per column
+// lam[k] = B[:, k]^T T[:, k] (B, T row-major n x n_sub), one CTA per column;
+// lam[n_sub + k] = lam[k]^-1/2 (0 for lam[k] <= 0), the column's scale factor
 __global__ void __launch_bounds__(256) k_rayleigh_cols(const double* __restrict__ B, const double* __restrict__ T,
                                                        int n, int n_sub, double* __restrict__ lam) {
     __shared__ double red[33];
@@ -629,9 +630,12 @@ __global__ void __launch_bounds__(256) k_rayleigh_cols(const double* __restrict_
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(B[(long long)i * n_sub + k], T[(long long)i * n_sub + k], s);
     s = block_sum1024d(s, red);
-    if (threadIdx.x == 0) lam[k] = s;
+    if (threadIdx.x == 0) {
+        lam[k] = s;
+        lam[n_sub + k] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    }
 }
-// B[:, k] /= sqrt(lam[k]); flags a rank-deficient selection
+// B[:, k] *= lam[n_sub + k] (= lam[k]^-1/2); flags a rank-deficient selection
 __global__ void k_scale_cols_by(double* __restrict__ B, int n, int n_sub, const double* __restrict__ lam,
                                 int* status) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -644,8 +648,7 @@ __global__ void k_scale_cols_by(double* __restrict__ B, int n, int n_sub, const 
         if (!(lmin >= 1e-12 * lmax) || !(lmax > 0.0)) atomicOr(status, ST_RANK);
     }
     if (t >= (long long)n * n_sub) return;
-    double l = lam[(int)(t % n_sub)];
-    B[t] = l > 0.0 ? B[t] / sqrt(l) : 0.0;
+    B[t] *= lam[n_sub + (int)(t % n_sub)];
 }
 __global__ void k_top_indices(int n, int n_sub, int* __restrict__ sel) {   // ascending order -> top n_sub, descending
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -672,7 +675,7 @@ void launch_to_f32(gw_ctx* ctx, const double* a, float* b, long long n);
 // lambda_j = Z[:, j]^T Zup[:, j] (= Z_j^T v Z_j when Zup = v Z), so that
 // Z^T v Z has a unit diagonal in binary64; flags a rank-deficient basis.
 void basis_rayleigh_scale(gw_ctx* ctx, double* Z, double* Zup, int rows, int n_sub) {
-    double* lam = dalloc<double>(ctx, n_sub);
+    double* lam = dalloc<double>(ctx, 2 * (size_t)n_sub);      // quotients, then their scale factors
     try {
         klaunch(ctx, "k_rayleigh_cols", k_rayleigh_cols, n_sub, 256, 0, (const double*)Z, (const double*)Zup, rows,
                 n_sub, lam);
@@ -797,7 +800,7 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int 
             X2 = dalloc<double>(ctx, nn); R = dalloc<double>(ctx, nn); S = dalloc<double>(ctx, nn);
             E = dalloc<double>(ctx, nn);
         }
-        T = dalloc<double>(ctx, nn); lam = dalloc<double>(ctx, n);
+        T = dalloc<double>(ctx, nn); lam = dalloc<double>(ctx, std::max(n, 2 * n_sub));
         const int n_part = ctx->num_sms;
         stat = dalloc<double>(ctx, 3 + 3 * (size_t)n_part);      // [3) results, then the partial sums
         auto oa_stats = [&]() {

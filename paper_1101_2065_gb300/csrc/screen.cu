@@ -591,6 +591,21 @@ __device__ __forceinline__ void load_l_tile(C* dst, const C* __restrict__ F, int
     }
 }
 
+// L11^-1 of panel k0 into rows of pitch LIP (a multiple of 16 bytes) and its
+// pivots d_i (binary32 only); no commit
+template <int LIP>
+__device__ __forceinline__ void load_diag_pitched(float2* sLi, float2* sD, const float2* __restrict__ Li,
+                                                  const float2* __restrict__ F, int n, int k0, int kb) {
+    for (int t = threadIdx.x; t < 32 * 16; t += blockDim.x) {
+        const int r = t >> 4, q = t & 15;
+        cp_async16(sLi + r * LIP + 2 * q, Li + r * 32 + 2 * q);
+    }
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) {
+        if (i < kb) cp_async8(sD + i, F + tri(k0 + i) + k0 + i);
+        else sD[i] = make_float2(0.f, 0.f);
+    }
+}
+
 // L11^-1 of panel k0 (NB x NB, zero outside kb) and its pivots d_i; no commit
 template <typename C>
 __device__ __forceinline__ void load_diag_data(C* sLi, C* sD, const C* __restrict__ Li, const C* __restrict__ F,
@@ -799,6 +814,7 @@ constexpr uint32_t TM_SBO_A = (TM_KS / 4) * 128, TM_SBO_B = (64 / 4) * 128;
 constexpr uint32_t TM_IDESC = tc::idesc_tf32(128, TM_N);
 constexpr int TM_GROUPS = 6;                        // row groups of the y_b step (6 x 40 = 240 threads)
 constexpr int TM_TMEM_COLS = 256;                   // TM_MAXT x TM_N = 240, rounded to a power of two
+constexpr int TM_LIP = 34;                          // L11^-1 row pitch: rows 16 bytes apart in the banks
 
 __device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&v)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -864,8 +880,8 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
     unsigned char* sA = sraw_tm;                                     // [TM_NS][hi, lo][TM_A_BYTES]
     unsigned char* sB = sA + 2 * TM_NS * TM_A_BYTES;                 // [hi, lo][TM_B_BYTES]
     float2* sYb = reinterpret_cast<float2*>(sB + 2 * TM_B_BYTES);    // [NB][RCP]
-    float2* sLi = sYb + NB * RCP;                                    // [NB][NB]
-    float2* sD = sLi + NB * NB;                                      // [NB]
+    float2* sLi = sYb + NB * RCP;                                    // [NB][TM_LIP]
+    float2* sD = sLi + NB * TM_LIP;                                  // [NB]
     double* red = reinterpret_cast<double*>(sYb);                    // [TM_GROUPS][RC], after the last panel
     __shared__ __align__(8) uint64_t mbar_buf[TM_NS];
     __shared__ __align__(8) uint64_t mbar_next, mbar_all;
@@ -882,7 +898,7 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
         tc::mbar_init(&mbar_next);
         tc::mbar_init(&mbar_all);
     }
-    load_diag_data<float2>(sLi, sD, Lk, F, n, 0, min(NB, n));
+    load_diag_pitched<TM_LIP>(sLi, sD, Lk, F, n, 0, min(NB, n));
     cp_async_commit();
     // q of this thread's rows of panel 0
     const bool ythread = grp < TM_GROUPS, live = ythread && col < rc;
@@ -961,14 +977,14 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
         for (int m = 0; m < 6; ++m) yb[m] = make_float2(0.f, 0.f);
         if (ythread) {
             // L11^-1 is lower triangular: row grp + 6 m needs p <= 6 m + 5 at most
-            const float2* lrow = sLi + grp * NB;
+            const float2* lrow = sLi + grp * TM_LIP;
 #pragma unroll
             for (int p = 0; p < NB; ++p) {
                 const float2 yv = sYb[p * RCP + col];
 #pragma unroll
                 for (int m = 0; m < 6; ++m)
                     if (TM_GROUPS * m + TM_GROUPS - 1 >= p && (m < 5 || TM_GROUPS * m < NB))
-                        yb[m] = cfma(lrow[min(TM_GROUPS * m * NB + p, (NB - 1 - grp) * NB + p)], yv, yb[m]);
+                        yb[m] = cfma(lrow[min(TM_GROUPS * m, NB - 1 - grp) * TM_LIP + p], yv, yb[m]);
             }
 #pragma unroll
             for (int m = 0; m < 6; ++m) {
@@ -983,33 +999,39 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
         }
         // the previous panel's MMAs read the B operand: all done before it is rebuilt
         if (b > 0 && k0 < n) ok = tc::mbar_wait(tc::smem_u32(&mbar_all), (b - 1) & 1) && ok;
-        if (ythread && k1 < n) {
+        if (k1 < n) {
+            // y_b replaces Y_b in sYb, then the B operand is written in 16-byte
+            // quads (rows 2q, 2q + 1 of y_b for one output column), lanes
+            // spread over the eight rows of a core matrix
+            __syncthreads();
+            if (ythread) {
 #pragma unroll
-            for (int m = 0; m < 6; ++m) {
-                const int i = grp + TM_GROUPS * m;
-                if (i < NB) {
-                    uint32_t rh, rl, ih, il;
-                    tc::split_tf32(yb[m].x, rh, rl);
-                    tc::split_tf32(yb[m].y, ih, il);
-                    const uint32_t sg = 0x80000000u;
-                    const uint32_t o0 = tc::core_off(col, 2 * i, 16), o1 = tc::core_off(col, 2 * i + 1, 16);
-                    const uint32_t o2 = tc::core_off(RC + col, 2 * i, 16), o3 = tc::core_off(RC + col, 2 * i + 1, 16);
-                    st_shared_f32(sB + o0, rh ^ sg);
-                    st_shared_f32(sB + TM_B_BYTES + o0, rl ^ sg);
-                    st_shared_f32(sB + o1, ih);
-                    st_shared_f32(sB + TM_B_BYTES + o1, il);
-                    st_shared_f32(sB + o2, ih ^ sg);
-                    st_shared_f32(sB + TM_B_BYTES + o2, il ^ sg);
-                    st_shared_f32(sB + o3, rh ^ sg);
-                    st_shared_f32(sB + TM_B_BYTES + o3, rl ^ sg);
+                for (int m = 0; m < 6; ++m) {
+                    const int i = grp + TM_GROUPS * m;
+                    if (i < NB) sYb[i * RCP + col] = yb[m];
                 }
+            }
+            __syncthreads();
+            for (int t = tid; t < TM_N * 16; t += blockDim.x) {
+                const int rr = t & 7, q = (t >> 3) & 15, rg = t >> 7;    // B row 8 rg + rr, K quad q
+                const int nr = 8 * rg + rr, c = nr < RC ? nr : nr - RC;
+                const float2 y0 = sYb[(2 * q) * RCP + c], y1 = sYb[(2 * q + 1) * RCP + c];
+                float v[4];
+                if (nr < RC) { v[0] = -y0.x; v[1] = y0.y; v[2] = -y1.x; v[3] = y1.y; }
+                else { v[0] = -y0.y; v[1] = -y0.x; v[2] = -y1.y; v[3] = -y1.x; }
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) tc::split_tf32(v[e], h[e], l[e]);
+                const uint32_t o = tc::core_off(nr, 4 * q, 16);
+                st_shared_v4(sB + o, h[0], h[1], h[2], h[3]);
+                st_shared_v4(sB + TM_B_BYTES + o, l[0], l[1], l[2], l[3]);
             }
         }
         tc::fence_async_smem();
         ok = __syncthreads_and(ok);
         if (!ok) break;
         if (b + 1 < nblk)      // next panel's L11^-1 and pivots: this panel's are no longer read
-            load_diag_data<float2>(sLi, sD, Lk + (long long)(b + 1) * NB * NB, F, n, k1, min(NB, n - k1));
+            load_diag_pitched<TM_LIP>(sLi, sD, Lk + (long long)(b + 1) * NB * NB, F, n, k1, min(NB, n - k1));
         cp_async_commit();
         if (k1 >= n) break;
         // MMAs of this panel: tiles T_first .. nt - 1, four K quarters each
@@ -1542,7 +1564,7 @@ static bool forms_tc(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double*
 // 80-column accumulator, 256 columns per CTA, two CTAs per SM).
 static size_t forms_tm_smem() {
     return 2 * (size_t)TM_NS * TM_A_BYTES + 2 * (size_t)TM_B_BYTES +
-           sizeof(float2) * ((size_t)32 * TM_RCP + 32 * 32 + 32);
+           sizeof(float2) * ((size_t)32 * TM_RCP + 32 * TM_LIP + 32);
 }
 
 static bool forms_tm(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
