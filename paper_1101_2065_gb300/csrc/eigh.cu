@@ -636,16 +636,35 @@ __global__ void __launch_bounds__(256) k_rayleigh_cols(const double* __restrict_
     }
 }
 // B[:, k] *= lam[n_sub + k] (= lam[k]^-1/2); flags a rank-deficient selection
-__global__ void k_scale_cols_by(double* __restrict__ B, int n, int n_sub, const double* __restrict__ lam,
-                                int* status) {
+__global__ void __launch_bounds__(256) k_scale_cols_by(double* __restrict__ B, int n, int n_sub,
+                                                       const double* __restrict__ lam, int* status) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t == 0) {
-        double lmax = lam[0], lmin = lam[0];
-        for (int k = 1; k < n_sub; ++k) {
+    if (blockIdx.x == 0) {
+        // the rank check: min and max of the quotients by the whole first block
+        __shared__ double smin[8], smax[8];
+        double lmax = -INFINITY, lmin = INFINITY;
+        for (int k = threadIdx.x; k < n_sub; k += blockDim.x) {
             lmax = fmax(lmax, lam[k]);
             lmin = fmin(lmin, lam[k]);
         }
-        if (!(lmin >= 1e-12 * lmax) || !(lmax > 0.0)) atomicOr(status, ST_RANK);
+        for (int o = 16; o > 0; o >>= 1) {
+            lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+            lmin = fmin(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            smax[threadIdx.x >> 5] = lmax;
+            smin[threadIdx.x >> 5] = lmin;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                lmax = fmax(lmax, smax[w]);
+                lmin = fmin(lmin, smin[w]);
+            }
+            lmax = fmax(lmax, smax[0]);
+            lmin = fmin(lmin, smin[0]);
+            if (!(lmin >= 1e-12 * lmax) || !(lmax > 0.0)) atomicOr(status, ST_RANK);
+        }
     }
     if (t >= (long long)n * n_sub) return;
     B[t] *= lam[n_sub + (int)(t % n_sub)];
