@@ -372,16 +372,12 @@ __global__ void __launch_bounds__(256) k_ldlt_syrk(C* __restrict__ fac, int n, i
 // tile J - 1 is read back, subtracted and stored.  The read-back goes through
 // a per-warp shared-memory transpose so that the read-modify-write of M is
 // row-contiguous; entries above the diagonal are skipped.
-constexpr int ST_NC = 32, ST_N = 2 * ST_NC;
-constexpr int ST_T = 512;                           // threads: 16 warps, four per tensor-memory lane quarter
-constexpr int ST_CW = ST_NC / (ST_T / 128);         // complex columns a warp reads back per tile (8)
-constexpr int ST_LPR = ST_CW / 4, ST_RPI = 32 / ST_LPR, ST_NI = 32 / ST_RPI;   // read-back layout
-constexpr int ST_XP = ST_CW + 1;                    // transpose scratch pitch
+constexpr int ST_NC = 32, ST_N = 2 * ST_NC, ST_XP = 17;
 constexpr int ST_A_BYTES = 128 * 64 * 4;            // 128 x 64 binary32 (hi or lo)
 constexpr int ST_B_BYTES = ST_N * 64 * 4;           // 64 x 64 binary32 (hi or lo)
 constexpr uint32_t ST_SBO = (64 / 4) * 128;
 constexpr uint32_t ST_IDESC = tc::idesc_tf32(128, ST_N);
-constexpr size_t ST_SMEM = 2 * (size_t)ST_A_BYTES + 4 * (size_t)ST_B_BYTES + (ST_T / 32) * 32 * ST_XP * sizeof(float2);
+constexpr size_t ST_SMEM = 2 * (size_t)ST_A_BYTES + 4 * (size_t)ST_B_BYTES + 8 * 32 * ST_XP * sizeof(float2);
 
 __host__ __device__ inline int st_row_tiles(int nj, int I) { return nj < 4 * I + 4 ? nj : 4 * I + 4; }
 
@@ -398,39 +394,41 @@ __device__ __forceinline__ void st_shared_quad(unsigned char* hi, unsigned char*
                  "r"(l3) : "memory");
 }
 
-// raw panel entries of the B operand of column tile c0: one K-quad (32 columns
-// x 16 quads over the 512 threads)
-__device__ __forceinline__ void st_load_b(float2 (&wr)[2], const float2* __restrict__ A, int n, int k0, int c0) {
-    const int idx = threadIdx.x, kq = (idx >> 3) & 15, q = 8 * (idx >> 7) + (idx & 7), cc = c0 + q;
-    wr[0] = wr[1] = make_float2(0.f, 0.f);
-    if (cc < n) {
-        const float2* src = A + tri(cc) + k0 + 2 * kq;
-        wr[0] = src[0];
-        wr[1] = src[1];
+// raw panel entries of the B operand of column tile c0: two K-quads per thread
+__device__ __forceinline__ void st_load_b(float2 (&wr)[2][2], const float2* __restrict__ A, int n, int k0, int c0) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int idx = threadIdx.x + 256 * j, kq = (idx >> 3) & 15, q = 8 * (idx >> 7) + (idx & 7), cc = c0 + q;
+        wr[j][0] = wr[j][1] = make_float2(0.f, 0.f);
+        if (cc < n) {
+            const float2* src = A + tri(cc) + k0 + 2 * kq;
+            wr[j][0] = src[0];
+            wr[j][1] = src[1];
+        }
     }
 }
 
 // this lane's entries of M in the row-contiguous read-back layout: rows
-// rb + lane / ST_LPR + ST_RPI i, complex columns cb + 4 (lane % ST_LPR) + t
-__device__ __forceinline__ void st_load_c(float2 (&cv)[ST_NI][4], const float2* __restrict__ A, int n, int rb, int cb) {
+// rb + (lane >> 2) + 8 i, complex columns cb + 4 (lane & 3) + t
+__device__ __forceinline__ void st_load_c(float2 (&cv)[4][4], const float2* __restrict__ A, int n, int rb, int cb) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int i = 0; i < ST_NI; ++i) {
-        const int r = rb + lane / ST_LPR + ST_RPI * i;
+    for (int i = 0; i < 4; ++i) {
+        const int r = rb + (lane >> 2) + 8 * i;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            const int cc = cb + 4 * (lane % ST_LPR) + t;
+            const int cc = cb + 4 * (lane & 3) + t;
             cv[i][t] = (r < n && cc <= r) ? A[tri(r) + cc] : make_float2(0.f, 0.f);
         }
     }
 }
 
-__global__ void __launch_bounds__(ST_T, 1) k_ldlt_syrk_tc(float2* __restrict__ fac, int n, int k0, int* status) {
+__global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fac, int n, int k0, int* status) {
     extern __shared__ __align__(128) unsigned char sraw_st[];
     unsigned char* sAh = sraw_st;
     unsigned char* sAl = sAh + ST_A_BYTES;
     unsigned char* sB = sAl + ST_A_BYTES;                            // [2][hi, lo][ST_B_BYTES]
-    float2* sX = reinterpret_cast<float2*>(sB + 4 * ST_B_BYTES);     // [warps][32][ST_XP]
+    float2* sX = reinterpret_cast<float2*>(sB + 4 * ST_B_BYTES);     // [8 warps][32][ST_XP]
     __shared__ float2 dd[32];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tbase;
@@ -438,7 +436,7 @@ __global__ void __launch_bounds__(ST_T, 1) k_ldlt_syrk_tc(float2* __restrict__ f
     float2* A = fac + (long long)blockIdx.y * tri(n);
     const int k1 = k0 + 32, m = n - k1, nj = (m + ST_NC - 1) / ST_NC, I = blockIdx.x;
     const int r0 = k1 + 128 * I, ntile = st_row_tiles(nj, I);
-    // this warp's read-back block: rows rw .. rw + 31, complex columns ST_CW h .. + ST_CW - 1 of a tile
+    // this warp's read-back block: rows rw .. rw + 31, complex columns 16 h .. + 15 of a tile
     const int rw = r0 + 32 * (warp & 3), h = warp >> 2;
     if (warp == 0) tc::tmem_alloc(&tbase, 4 * ST_N);
     if (tid == 0) {
@@ -447,14 +445,14 @@ __global__ void __launch_bounds__(ST_T, 1) k_ldlt_syrk_tc(float2* __restrict__ f
     }
     if (tid < 32) dd[tid] = A[tri(k0 + tid) + k0 + tid];
     // entries of M of the next two tiles in flight (tile J - 1 is read back while J and J + 1 load)
-    float2 wr[2], cn[ST_NI][4], cn2[ST_NI][4], cp[ST_NI][4];
+    float2 wr[2][2], cn[4][4], cn2[4][4], cp[4][4];
     st_load_b(wr, A, n, k0, k1);
-    st_load_c(cn, A, n, rw, k1 + ST_CW * h);
-    if (ntile > 1) st_load_c(cn2, A, n, rw, k1 + ST_NC + ST_CW * h);
+    st_load_c(cn, A, n, rw, k1 + 16 * h);
+    if (ntile > 1) st_load_c(cn2, A, n, rw, k1 + ST_NC + 16 * h);
     // A operand: rows r0 .. r0 + 127 of the panel, staged once
 #pragma unroll
-    for (int j = 0; j < 2048 / ST_T; ++j) {
-        const int idx = tid + ST_T * j, rr = idx & 7, kq = (idx >> 3) & 15, rg = idx >> 7;
+    for (int j = 0; j < 8; ++j) {
+        const int idx = tid + 256 * j, rr = idx & 7, kq = (idx >> 3) & 15, rg = idx >> 7;
         const int ra = r0 + 8 * rg + rr;
         float2 a = make_float2(0.f, 0.f), b = a;
         if (ra < n) {
@@ -475,9 +473,10 @@ __global__ void __launch_bounds__(ST_T, 1) k_ldlt_syrk_tc(float2* __restrict__ f
             // B operand of tile J (its buffer was last read by the MMAs of tile J - 2, complete)
             unsigned char* bh = sB + 2 * (J & 1) * ST_B_BYTES;
             unsigned char* bl = bh + ST_B_BYTES;
-            {
-                const int idx = tid, rr = idx & 7, kq = (idx >> 3) & 15, rg = idx >> 7, q = 8 * rg + rr;
-                const float2 w0 = cmul(wr[0], dd[2 * kq]), w1 = cmul(wr[1], dd[2 * kq + 1]);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int idx = tid + 256 * j, rr = idx & 7, kq = (idx >> 3) & 15, rg = idx >> 7, q = 8 * rg + rr;
+                const float2 w0 = cmul(wr[j][0], dd[2 * kq]), w1 = cmul(wr[j][1], dd[2 * kq + 1]);
                 st_shared_quad(bh, bl, tc::core_off(q, 4 * kq, 16), w0.x, -w0.y, w1.x, -w1.y);
                 st_shared_quad(bh, bl, tc::core_off(ST_NC + q, 4 * kq, 16), w0.y, w0.x, w1.y, w1.x);
             }
@@ -501,40 +500,40 @@ __global__ void __launch_bounds__(ST_T, 1) k_ldlt_syrk_tc(float2* __restrict__ f
         }
         if (J >= 1) {
             // tile J - 1: read back, transpose through shared memory, M -= product
-            const int Jp = J - 1, cb = k1 + ST_NC * Jp + ST_CW * h;
+            const int Jp = J - 1, cb = k1 + ST_NC * Jp + 16 * h;
 #pragma unroll
-            for (int i = 0; i < ST_NI; ++i)
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     cp[i][t] = cn[i][t];
                     cn[i][t] = cn2[i][t];
                 }
-            if (J + 1 < ntile) st_load_c(cn2, A, n, rw, k1 + ST_NC * (J + 1) + ST_CW * h);
+            if (J + 1 < ntile) st_load_c(cn2, A, n, rw, k1 + ST_NC * (J + 1) + 16 * h);
             ok = tc::mbar_wait(tc::smem_u32(&mbar[Jp & 1]), (Jp >> 1) & 1) && ok;
             ok = __syncthreads_and(ok);
             if (!ok) break;
             tc::fence_after();
-            const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(2 * ST_N * (Jp & 1) + ST_CW * h);
-            uint32_t re[ST_CW], im[ST_CW], re2[ST_CW], im2[ST_CW];
-            tc::tmem_ld8(base, re);
-            tc::tmem_ld8(base + ST_NC, im);
-            tc::tmem_ld8(base + ST_N, re2);
-            tc::tmem_ld8(base + ST_N + ST_NC, im2);
+            const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(2 * ST_N * (Jp & 1) + 16 * h);
+            uint32_t re[16], im[16], re2[16], im2[16];
+            tc::tmem_ld16(base, re);
+            tc::tmem_ld16(base + ST_NC, im);
+            tc::tmem_ld16(base + ST_N, re2);
+            tc::tmem_ld16(base + ST_N + ST_NC, im2);
             tc::tmem_wait_ld();
             tc::fence_before();
 #pragma unroll
-            for (int j = 0; j < ST_CW; ++j)
+            for (int j = 0; j < 16; ++j)
                 X[lane * ST_XP + j] = make_float2(__uint_as_float(re[j]) + __uint_as_float(re2[j]),
                                                   __uint_as_float(im[j]) + __uint_as_float(im2[j]));
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < ST_NI; ++i) {
-                const int rl = lane / ST_LPR + ST_RPI * i, r = rw + rl;
+            for (int i = 0; i < 4; ++i) {
+                const int rl = (lane >> 2) + 8 * i, r = rw + rl;
                 if (r < n) {
                     float2* row = A + tri(r);
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        const int cl = 4 * (lane % ST_LPR) + t, cc = cb + cl;
+                        const int cl = 4 * (lane & 3) + t, cc = cb + cl;
                         if (cc <= r) {
                             const float2 x = X[rl * ST_XP + cl];
                             row[cc] = make_float2(cp[i][t].x - x.x, cp[i][t].y - x.y);
@@ -817,6 +816,12 @@ constexpr int TM_GROUPS = 6;                        // row groups of the y_b ste
 constexpr int TM_TMEM_COLS = 256;                   // TM_MAXT x TM_N = 240, rounded to a power of two
 constexpr int TM_LIP = 34;                          // L11^-1 row pitch: rows 16 bytes apart in the banks
 
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(addr));
+}
+
 __device__ __forceinline__ void st_shared_f32(unsigned char* p, uint32_t v) {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(tc::smem_u32(p)), "r"(v) : "memory");
 }
@@ -936,7 +941,7 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
                 const uint32_t base = taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(T * TM_N + RC * part_im);
                 uint32_t v[RC / 8][8];
 #pragma unroll
-                for (int j = 0; j < RC / 8; ++j) tc::tmem_ld8(base + 8 * j, v[j]);
+                for (int j = 0; j < RC / 8; ++j) tmem_ld8(base + 8 * j, v[j]);
                 tc::tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < RC / 8; ++j)
@@ -1454,7 +1459,7 @@ static void ldlt_steps(gw_ctx* ctx, const C* chi0, C* fac, int n, int N, C* linv
             // binary32: trailing updates with at least one full 128-row block on the tensor cores
             if (!ctx->syrk_simt && m >= 128 && N <= 65535) {
                 allow_max_smem(k_ldlt_syrk_tc);
-                klaunch(ctx, names[3], k_ldlt_syrk_tc, dim3(div_up(m, 128), N), ST_T, ST_SMEM, (float2*)fac, n, k0,
+                klaunch(ctx, names[3], k_ldlt_syrk_tc, dim3(div_up(m, 128), N), 256, ST_SMEM, (float2*)fac, n, k0,
                         ctx->d_status);
                 continue;
             }
