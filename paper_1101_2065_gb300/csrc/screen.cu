@@ -859,10 +859,15 @@ __device__ __forceinline__ void tm_load(float (&v)[2][4], const float2* __restri
     }
 }
 
-__device__ __forceinline__ void tm_store(unsigned char* hi, unsigned char* lo, const float (&v)[2][4]) {
+// rows outside [rlo, rhi) of the tile are not staged: they meet only
+// accumulator lanes whose rows are already final (above the panel) or do not
+// exist (n and beyond), which are never read again
+__device__ __forceinline__ void tm_store(unsigned char* hi, unsigned char* lo, const float (&v)[2][4], int rlo,
+                                         int rhi) {
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
         const int idx = threadIdx.x + 256 * j, rr = idx & 7, kq = (idx >> 3) & 3, rg = idx >> 5;
+        if (8 * rg + rr < rlo || 8 * rg + rr >= rhi) continue;
         uint32_t h[4], l[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) tc::split_tf32(v[j][q], h[q], l[q]);
@@ -1043,10 +1048,10 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
                 if (stage >= TM_NS) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[buf]), ((stage / TM_NS) - 1) & 1) && ok;
                 unsigned char* ah = sA + 2 * buf * TM_A_BYTES;
                 if ((qk & 1) == 0) {
-                    tm_store(ah, ah + TM_A_BYTES, av0);
+                    tm_store(ah, ah + TM_A_BYTES, av0, k1 - 128 * T, n - 128 * T);
                     if (have) tm_load(av0, F, n, ld);
                 } else {
-                    tm_store(ah, ah + TM_A_BYTES, av1);
+                    tm_store(ah, ah + TM_A_BYTES, av1, k1 - 128 * T, n - 128 * T);
                     if (have) tm_load(av1, F, n, ld);
                 }
                 if (have) have = tm_next(ld, nblk, nt);

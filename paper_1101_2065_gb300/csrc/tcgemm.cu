@@ -62,27 +62,36 @@ __global__ void __launch_bounds__(256, 1) k_sgemm_tc(int M, int N, int K, float 
     for (int c = 0; c < nchunk; ++c) {
         const int s = c % NSTAGE, k0 = c * KC;
         unsigned char* st = sm + s * STAGE_BYTES;
-        if (c >= NSTAGE) {           // the MMAs that read this stage two chunks ago are done
-            ok = tc::mbar_wait(tc::smem_u32(&mbar[s]), (uses[s] - 1) & 1) && ok;
-        }
-        // stage op(A)[m0 .. +128)[k0 .. +32) and op(B)^T[n0 .. +128)[k0 .. +32)
-        for (int t = tid; t < TM * KC; t += blockDim.x) {
+        // stage op(A)[m0 .. +128)[k0 .. +32) and op(B)^T[n0 .. +128)[k0 .. +32):
+        // each thread loads its 16 + 16 values first (all loads in flight at
+        // once), then splits and stores them
+        constexpr int PER = TM * KC / 256;
+        float va[PER], vb[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int t = tid + 256 * u;
             int r, k;
             if (TA) { k = t / TM; r = t % TM; } else { r = t / KC; k = t % KC; }
             const int gm = m0 + r, gk = k0 + k;
-            const float a = (gm < M && gk < K) ? (TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : 0.f;
+            va[u] = (gm < M && gk < K) ? (TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : 0.f;
+            if (TB) { r = t / KC; k = t % KC; } else { k = t / TN; r = t % TN; }
+            const int gn = n0 + r, gk2 = k0 + k;
+            vb[u] = (gn < N && gk2 < K) ? (TB ? B[(long long)gn * ldb + gk2] : B[(long long)gk2 * ldb + gn]) : 0.f;
+        }
+        if (c >= NSTAGE) {           // the MMAs that read this stage two chunks ago are done
+            ok = tc::mbar_wait(tc::smem_u32(&mbar[s]), (uses[s] - 1) & 1) && ok;
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int t = tid + 256 * u;
+            int r, k;
             uint32_t hi, lo;
-            tc::split_tf32(a, hi, lo);
+            if (TA) { k = t / TM; r = t % TM; } else { r = t / KC; k = t % KC; }
+            tc::split_tf32(va[u], hi, lo);
             *reinterpret_cast<uint32_t*>(st + tile_off(r, k)) = hi;
             *reinterpret_cast<uint32_t*>(st + TILE_BYTES + tile_off(r, k)) = lo;
-        }
-        for (int t = tid; t < TN * KC; t += blockDim.x) {
-            int r, k;
             if (TB) { r = t / KC; k = t % KC; } else { k = t / TN; r = t % TN; }
-            const int gn = n0 + r, gk = k0 + k;
-            const float b = (gn < N && gk < K) ? (TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn]) : 0.f;
-            uint32_t hi, lo;
-            tc::split_tf32(b, hi, lo);
+            tc::split_tf32(vb[u], hi, lo);
             *reinterpret_cast<uint32_t*>(st + 2 * TILE_BYTES + tile_off(r, k)) = hi;
             *reinterpret_cast<uint32_t*>(st + 3 * TILE_BYTES + tile_off(r, k)) = lo;
         }
