@@ -948,11 +948,14 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
 #pragma unroll
                 for (int j = 0; j < RC / 8; ++j) tmem_ld8(base + 8 * j, v[j]);
                 tc::tmem_wait_ld();
+                // lanes past n hold whatever the unstaged operand rows produced: zero
+                const bool row_live = k0 + lane < n;
 #pragma unroll
                 for (int j = 0; j < RC / 8; ++j)
 #pragma unroll
                     for (int e = 0; e < 8; ++e)
-                        reinterpret_cast<float*>(sYb + lane * RCP + 8 * j + e)[part_im] = __uint_as_float(v[j][e]);
+                        reinterpret_cast<float*>(sYb + lane * RCP + 8 * j + e)[part_im] =
+                            row_live ? __uint_as_float(v[j][e]) : 0.f;
             }
             tc::fence_before();
         }
