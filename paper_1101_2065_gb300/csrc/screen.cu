@@ -835,7 +835,7 @@ __device__ __forceinline__ void st_shared_v4(unsigned char* p, uint32_t a, uint3
 
 // Forms of the binary32 path with the updates of Y kept in tensor memory.
 // One CTA per frequency k = 1 + blockIdx.y and chunk of TM_RC right-hand
-// sides, one CTA per SM.  The update of every row below panel b,
+// sides, two CTAs per SM.  The update of every row below panel b,
 //   dY[r] -= L[r, panel b] y_b,
 // is one real TF32 product per 128-row tile and quarter panel (3xTF32 into
 // one binary32 accumulator per tile), with the complex entries interleaved
@@ -848,21 +848,19 @@ __device__ __forceinline__ void st_shared_v4(unsigned char* p, uint32_t a, uint3
 // dY for the whole forward substitution and are never written back: panel b
 // reads its own 32 rows once (two warps, tcgen05.ld), adds q, applies the
 // stored L11^-1 and the forms sum, and builds its B operand; its MMAs then
-// run while the next panel is prepared.  The MMAs of the tile that holds the
-// next panel's rows are committed to their own mbarrier, so the next panel
-// waits for that tile only; the B operand is rebuilt once the whole panel's
-// MMAs are done.  The A operands are the pre-split blocks the panel step
-// wrote: one thread streams them through TM_NS shared-memory stages with
-// 16 KB bulk copies, up to TM_NS stages ahead of its MMAs (the depth hides
-// the copy and MMA completion latencies); every mbarrier wait is bounded.
-constexpr int TM_RC = 80, TM_N = 2 * TM_RC, TM_KS = 16, TM_NS = 7, TM_MAXT = 3, TM_RCP = TM_RC + 1;
+// run while the next panel is prepared (and while the other CTA of the SM
+// runs its own serial steps).  The MMAs of the tile that holds the next
+// panel's rows are committed to their own mbarrier, so the next panel waits
+// for that tile only; the B operand is rebuilt once the whole panel's MMAs
+// are done.  L rows stream through TM_NS operand stages (register prefetch
+// two stages ahead); every mbarrier wait is bounded.
+constexpr int TM_RC = 40, TM_N = 2 * TM_RC, TM_KS = 16, TM_NS = 3, TM_MAXT = 3, TM_RCP = TM_RC + 1;
 constexpr int TM_A_BYTES = 128 * TM_KS * 4;         // one 128 x 16 binary32 operand (hi or lo)
-constexpr int TM_B_BYTES = TM_N * 64 * 4;           // one 160 x 64 binary32 operand (hi or lo)
+constexpr int TM_B_BYTES = TM_N * 64 * 4;           // one 80 x 64 binary32 operand (hi or lo)
 constexpr uint32_t TM_SBO_A = (TM_KS / 4) * 128, TM_SBO_B = (64 / 4) * 128;
 constexpr uint32_t TM_IDESC = tc::idesc_tf32(128, TM_N);
-constexpr int TM_GROUPS = 3;                        // row groups of the y_b step (3 x 80 = 240 threads)
-constexpr int TM_RPT = (32 + TM_GROUPS - 1) / TM_GROUPS;   // panel rows per y_b thread
-constexpr int TM_TMEM_COLS = 512;                   // TM_MAXT x TM_N = 480, rounded to a power of two
+constexpr int TM_GROUPS = 6;                        // row groups of the y_b step (6 x 40 = 240 threads)
+constexpr int TM_TMEM_COLS = 256;                   // TM_MAXT x TM_N = 240, rounded to a power of two
 constexpr int TM_LIP = 34;                          // L11^-1 row pitch: rows 16 bytes apart in the banks
 
 __device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&v)[8]) {
@@ -875,7 +873,7 @@ __device__ __forceinline__ void st_shared_f32(unsigned char* p, uint32_t v) {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(tc::smem_u32(p)), "r"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ fac, const float2* __restrict__ linv,
+__global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ fac, const float2* __restrict__ linv,
                                                      const float* __restrict__ split, int nst, int n, int N,
                                                      const double* __restrict__ Q, int R, double* __restrict__ c,
                                                      int* status) {
@@ -910,9 +908,9 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
     cp_async_commit();
     // q of this thread's rows of panel 0
     const bool ythread = grp < TM_GROUPS, live = ythread && col < rc;
-    float qr[TM_RPT];
+    float qr[6];
 #pragma unroll
-    for (int m = 0; m < TM_RPT; ++m) {
+    for (int m = 0; m < 6; ++m) {
         const int i = grp + TM_GROUPS * m;
         qr[m] = (live && i < NB && i < n) ? (float)Q[(long long)i * R + rc0 + col] : 0.f;
     }
@@ -970,7 +968,7 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
         __syncthreads();
         if (ythread) {
 #pragma unroll
-            for (int m = 0; m < TM_RPT; ++m) {
+            for (int m = 0; m < 6; ++m) {
                 const int i = grp + TM_GROUPS * m;
                 if (i < NB) {
                     float2* y = sYb + i * RCP + col;
@@ -980,7 +978,7 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
             }
             // q of the next panel's rows, in flight while this panel runs
 #pragma unroll
-            for (int m = 0; m < TM_RPT; ++m) {
+            for (int m = 0; m < 6; ++m) {
                 const int i = k1 + grp + TM_GROUPS * m;
                 qr[m] = (live && grp + TM_GROUPS * m < NB && i < n) ? (float)Q[(long long)i * R + rc0 + col] : 0.f;
             }
@@ -988,9 +986,9 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
         cp_async_wait<0>();
         __syncthreads();
         // y_b = L11^-1 Y_b for rows grp + 6 m of column col, and the forms sum
-        float2 yb[TM_RPT];
+        float2 yb[6];
 #pragma unroll
-        for (int m = 0; m < TM_RPT; ++m) yb[m] = make_float2(0.f, 0.f);
+        for (int m = 0; m < 6; ++m) yb[m] = make_float2(0.f, 0.f);
         if (ythread) {
             // L11^-1 is lower triangular: row grp + 6 m needs p <= 6 m + 5 at most
             const float2* lrow = sLi + grp * TM_LIP;
@@ -998,12 +996,12 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
             for (int p = 0; p < NB; ++p) {
                 const float2 yv = sYb[p * RCP + col];
 #pragma unroll
-                for (int m = 0; m < TM_RPT; ++m)
-                    if (TM_GROUPS * m + TM_GROUPS - 1 >= p && TM_GROUPS * m < NB)
+                for (int m = 0; m < 6; ++m)
+                    if (TM_GROUPS * m + TM_GROUPS - 1 >= p && (m < 5 || TM_GROUPS * m < NB))
                         yb[m] = cfma(lrow[min(TM_GROUPS * m, NB - 1 - grp) * TM_LIP + p], yv, yb[m]);
             }
 #pragma unroll
-            for (int m = 0; m < TM_RPT; ++m) {
+            for (int m = 0; m < 6; ++m) {
                 const int i = grp + TM_GROUPS * m;
                 if (i < kb) {
                     const float2 w = cdiv(cmul(yb[m], yb[m]), sD[i]);
@@ -1022,7 +1020,7 @@ __global__ void __launch_bounds__(256, 1) k_forms_tm(const float2* __restrict__ 
             __syncthreads();
             if (ythread) {
 #pragma unroll
-                for (int m = 0; m < TM_RPT; ++m) {
+                for (int m = 0; m < 6; ++m) {
                     const int i = grp + TM_GROUPS * m;
                     if (i < NB) sYb[i * RCP + col] = yb[m];
                 }
@@ -1577,8 +1575,8 @@ static bool forms_tc(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double*
     return true;
 }
 
-// Forms with dY in tensor memory: n <= 384 (three 128-lane tiles of a
-// 160-column accumulator within the 512 columns of an SM).
+// Forms with dY in tensor memory: n <= 384 (three 128-lane tiles of an
+// 80-column accumulator, 256 columns per CTA, two CTAs per SM).
 static size_t forms_tm_smem() {
     return 2 * (size_t)TM_NS * TM_A_BYTES + 2 * (size_t)TM_B_BYTES +
            sizeof(float2) * ((size_t)32 * TM_RCP + 32 * TM_LIP + 32);
