@@ -564,7 +564,6 @@ extern "C" void gw_chi0_free(gw_chi0* c) { chi0_release(c); }
 static void W_release(gw_W* w) {
     if (!w) return;
     ctx_free(w->ctx, w->fac); ctx_free(w->ctx, w->fac32); ctx_free(w->ctx, w->linv); ctx_free(w->ctx, w->piv);
-    ctx_free(w->ctx, w->fsplit);
     delete w;
 }
 
@@ -577,8 +576,6 @@ static gw_W* screen_W(gw_ctx* ctx, const gw_chi0* c) {
         if (c->prec == GW_MIXED) w->fac32 = dalloc<float2>(ctx, N * (size_t)tri(n));     // packed lower triangles
         else w->fac = dalloc<double2>(ctx, N * (size_t)tri(n));
         w->linv = ctx_alloc(ctx, ldlt_linv_bytes((int)n, (int)N, c->prec));
-        if (const size_t fsb = forms_split_bytes(ctx, (int)n, (int)N, c->prec))
-            w->fsplit = (float*)ctx_alloc(ctx, fsb);
         w->piv = dalloc<double>(ctx, 2 * N);      // [N) ratios, [N, 2N) running min |d|
         launch_ldlt(ctx, w);
         std::vector<double> piv(N);

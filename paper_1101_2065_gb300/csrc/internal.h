@@ -145,7 +145,6 @@ struct gw_W {
     double2* fac = nullptr;          // [n_omega*n*n] strict lower L, diagonal D
     float2* fac32 = nullptr;
     void* linv = nullptr;            // [n_omega][panels][NB][NB] inverses of the unit lower diagonal blocks
-    float* fsplit = nullptr;         // binary32, N_sub <= 384: the forms' pre-split operand blocks
     double* piv = nullptr;           // [n_omega] min|d| / max|M|
     double min_pivot_ratio = 0.0;
 };
@@ -198,9 +197,6 @@ bool sgemm_tc(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, float alpha, c
               const float* B, long long ldb, float beta, float* C, long long ldc);
 // screen.cu
 size_t ldlt_linv_bytes(int n, int n_omega, gw_precision prec);
-// bytes of the tensor-memory forms' operand blocks (0 where those forms do not
-// apply; ctx null: default kernel options)
-size_t forms_split_bytes(const gw_ctx* ctx, int n, int n_omega, gw_precision prec);
 void launch_ldlt(gw_ctx* ctx, gw_W* W);
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* c);
 void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work);

@@ -147,33 +147,11 @@ __global__ void __launch_bounds__(256) k_ldlt_init(const C* __restrict__ chi0, C
     if (threadIdx.x == 0) piv[k] = sqrt(mx);
 }
 
-// Operand blocks of the tensor-memory forms (binary32 path), written by the
-// panel step: for every frequency, the stages (panel b, 128-row tile
-// T >= 32 (b + 1) / 128, quarter qk of the panel's 32 complex columns) in
-// that order, each 16 KB: the TF32 hi parts, then the lo parts, of the
-// tile's rows x 16 binary32 values (A[r][2p] = Re L, A[r][2p+1] = Im L) in
-// the canonical K-major core-matrix layout.  Rows above the panel and past n
-// are never written: they meet only accumulator lanes that are never read.
-constexpr int FS_BLOCK_FLOATS = 4096;
-__host__ __device__ inline int fs_tfirst(int b) { return (32 * (b + 1)) >> 7; }
-__host__ __device__ inline int fs_base(int b, int nt) {        // first stage of panel b
-    int s = 0;
-    for (int q = 0; q < b; ++q) s += 4 * (nt - fs_tfirst(q));
-    return s;
-}
-__host__ __device__ inline int fs_stages(int n) { return fs_base((n + 31) / 32 - 1, (n + 127) >> 7); }
-
-__device__ __forceinline__ void st_global_v4(float* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
-}
-
 // x D L11^T = a for one panel row held in registers: x_j = (a_j - sum_{p<j}
-// x_p SD[j][p]) / d_j.  With sp set (binary32 path), the row also goes to the
-// forms' operand blocks of its tile (sp: the block of quarter 0, rr: the row
-// within the tile).
+// x_p SD[j][p]) / d_j.
 template <typename C, bool FULL>
 __device__ __forceinline__ void panel_row_solve(C* __restrict__ row, const C (*SD)[Tile<C>::NB + 1],
-                                                const C* Dinv, int kb, float* sp = nullptr, int rr = 0) {
+                                                const C* Dinv, int kb) {
     constexpr int NB = Tile<C>::NB;
     C x[NB];
 #pragma unroll
@@ -192,23 +170,6 @@ __device__ __forceinline__ void panel_row_solve(C* __restrict__ row, const C (*S
 #pragma unroll
     for (int j = 0; j < NB; ++j)
         if (FULL || j < kb) row[j] = x[j];
-    if constexpr (sizeof(C) == 8 && FULL) {
-        if (sp) {
-#pragma unroll
-            for (int qk = 0; qk < 4; ++qk)
-#pragma unroll
-                for (int kq = 0; kq < 4; ++kq) {
-                    const int p = 8 * qk + 2 * kq;
-                    const float v[4] = {x[p].x, x[p].y, x[p + 1].x, x[p + 1].y};
-                    uint32_t h[4], l[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) tc::split_tf32(v[e], h[e], l[e]);
-                    float* blk = sp + qk * FS_BLOCK_FLOATS + tc::core_off(rr, 4 * kq, 4) / 4;
-                    st_global_v4(blk, h[0], h[1], h[2], h[3]);
-                    st_global_v4(blk + FS_BLOCK_FLOATS / 2, l[0], l[1], l[2], l[3]);
-                }
-        }
-    }
 }
 
 // Panel k0 of every frequency: factor the diagonal block, solve the rows
@@ -217,8 +178,7 @@ __device__ __forceinline__ void panel_row_solve(C* __restrict__ row, const C (*S
 // piv[k] = min |d| / max |M| and flags a zero pivot.
 template <typename C>
 __global__ void __launch_bounds__(256, 2) k_ldlt_panel(C* __restrict__ fac, int n, int N, int k0,
-                                                    C* __restrict__ linv, double* __restrict__ piv, int* status,
-                                                    float* __restrict__ split, int nst) {
+                                                    C* __restrict__ linv, double* __restrict__ piv, int* status) {
     constexpr int NB = Tile<C>::NB, H = NB / 2, NPAIR = NB * (NB - 1) / 2, PPT = (NPAIR + 255) / 256;
     __shared__ C S[NB][NB + 1];     // L11 strictly below the diagonal, D on it
     __shared__ C SD[NB][NB + 1];    // SD[j][p] = L_jp d_p
@@ -319,16 +279,9 @@ __global__ void __launch_bounds__(256, 2) k_ldlt_panel(C* __restrict__ fac, int 
         }
     } else {
         const int nthr = blockDim.x - 32;
-        const int nt = (n + 127) >> 7, b = k0 / NB;
         for (int r = k1 + tid - 32; r < n; r += nthr) {
-            if (kb == NB) {
-                float* sp = nullptr;
-                if (split)
-                    sp = split + ((size_t)k * nst + fs_base(b, nt) + 4 * ((r >> 7) - fs_tfirst(b))) * FS_BLOCK_FLOATS;
-                panel_row_solve<C, true>(A + tri(r) + k0, SD, Dinv, kb, sp, r & 127);
-            } else {
-                panel_row_solve<C, false>(A + tri(r) + k0, SD, Dinv, kb);
-            }
+            if (kb == NB) panel_row_solve<C, true>(A + tri(r) + k0, SD, Dinv, kb);
+            else panel_row_solve<C, false>(A + tri(r) + k0, SD, Dinv, kb);
         }
     }
 }
@@ -873,10 +826,60 @@ __device__ __forceinline__ void st_shared_f32(unsigned char* p, uint32_t v) {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(tc::smem_u32(p)), "r"(v) : "memory");
 }
 
+// stage = (panel b, tile T, quarter qk of the panel's 32 complex columns);
+// the panels with rows below them are b = 0 .. nblk - 2, the tiles of panel
+// b are T = (32 (b + 1)) / 128 .. nt - 1
+struct TmStage {
+    int b, T, qk;
+};
+__device__ __forceinline__ bool tm_next(TmStage& s, int nblk, int nt) {
+    if (++s.qk < 4) return true;
+    s.qk = 0;
+    if (++s.T < nt) return true;
+    if (++s.b >= nblk - 1) return false;
+    s.T = (32 * (s.b + 1)) >> 7;
+    return true;
+}
+
+// this thread's two K-quads of stage s: rows 8 rg + rr of the tile, quad kq
+// (idx = tid + 256 j); zero outside rows [k1, n)
+__device__ __forceinline__ void tm_load(float (&v)[2][4], const float2* __restrict__ F, int n, const TmStage& s) {
+    const int k0 = 32 * s.b, k1 = k0 + 32;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int idx = threadIdx.x + 256 * j, rr = idx & 7, kq = (idx >> 3) & 3, rg = idx >> 5;
+        const int r = 128 * s.T + 8 * rg + rr;
+        if (r >= k1 && r < n) {
+            const float2* src = F + tri(r) + k0 + 8 * s.qk + 2 * kq;
+            const float2 a = src[0], b = src[1];
+            v[j][0] = a.x; v[j][1] = a.y; v[j][2] = b.x; v[j][3] = b.y;
+        } else {
+            v[j][0] = v[j][1] = v[j][2] = v[j][3] = 0.f;
+        }
+    }
+}
+
+// rows outside [rlo, rhi) of the tile are not staged: they meet only
+// accumulator lanes whose rows are already final (above the panel) or do not
+// exist (n and beyond), which are never read again
+__device__ __forceinline__ void tm_store(unsigned char* hi, unsigned char* lo, const float (&v)[2][4], int rlo,
+                                         int rhi) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int idx = threadIdx.x + 256 * j, rr = idx & 7, kq = (idx >> 3) & 3, rg = idx >> 5;
+        if (8 * rg + rr < rlo || 8 * rg + rr >= rhi) continue;
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tc::split_tf32(v[j][q], h[q], l[q]);
+        const uint32_t o = tc::core_off(8 * rg + rr, 4 * kq, TM_KS / 4);
+        st_shared_v4(hi + o, h[0], h[1], h[2], h[3]);
+        st_shared_v4(lo + o, l[0], l[1], l[2], l[3]);
+    }
+}
+
 __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ fac, const float2* __restrict__ linv,
-                                                     const float* __restrict__ split, int nst, int n, int N,
-                                                     const double* __restrict__ Q, int R, double* __restrict__ c,
-                                                     int* status) {
+                                                     int n, int N, const double* __restrict__ Q, int R,
+                                                     double* __restrict__ c, int* status) {
     constexpr int NB = 32, RC = TM_RC, RCP = TM_RCP;
     extern __shared__ __align__(128) unsigned char sraw_tm[];
     unsigned char* sA = sraw_tm;                                     // [TM_NS][hi, lo][TM_A_BYTES]
@@ -885,8 +888,7 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
     float2* sLi = sYb + NB * RCP;                                    // [NB][TM_LIP]
     float2* sD = sLi + NB * TM_LIP;                                  // [NB]
     double* red = reinterpret_cast<double*>(sYb);                    // [TM_GROUPS][RC], after the last panel
-    __shared__ __align__(8) uint64_t mbar_buf[TM_NS];      // operand stage read by its MMAs
-    __shared__ __align__(8) uint64_t mbar_full[TM_NS];     // operand stage landed
+    __shared__ __align__(8) uint64_t mbar_buf[TM_NS];
     __shared__ __align__(8) uint64_t mbar_next, mbar_all;
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -897,10 +899,7 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
     const float2* Lk = linv + (long long)k * nblk * NB * NB;
     if (warp == 0) tc::tmem_alloc(&tbase, TM_TMEM_COLS);
     if (tid == 0) {
-        for (int i = 0; i < TM_NS; ++i) {
-            tc::mbar_init(&mbar_buf[i]);
-            tc::mbar_init(&mbar_full[i]);
-        }
+        for (int i = 0; i < TM_NS; ++i) tc::mbar_init(&mbar_buf[i]);
         tc::mbar_init(&mbar_next);
         tc::mbar_init(&mbar_all);
     }
@@ -914,29 +913,24 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
         const int i = grp + TM_GROUPS * m;
         qr[m] = (live && i < NB && i < n) ? (float)Q[(long long)i * R + rc0 + col] : 0.f;
     }
-    // operand blocks of this frequency, one 16 KB bulk copy per stage (thread 0)
-    const float* Fs = split + (size_t)k * nst * FS_BLOCK_FLOATS;
-    int s_issue = 0;        // next stage to copy (thread 0)
-    if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // operand rows of the first two stages; stages alternate the parity of
+    // qk, and the set of a parity is refilled with the stage two ahead as soon
+    // as it is stored
+    TmStage ld{0, (32 >> 7), 0};
+    bool have = nblk > 1;
+    float av0[2][4], av1[2][4];
+    if (have) {
+        tm_load(av0, F, n, ld);
+        tm_next(ld, nblk, nt);
+        tm_load(av1, F, n, ld);
+        have = tm_next(ld, nblk, nt);
+    }
     tc::fence_async_smem();
     __syncthreads();
     tc::fence_after();
     const uint32_t taddr = tbase;
+    int stage = 0;          // operand stages issued; stage s uses buffer s % TM_NS for the (s / TM_NS)-th time
     bool ok = true;
-    int stage = 0;          // stages multiplied (thread 0); stage s uses buffer s % TM_NS for the (s / TM_NS)-th time
-    // thread 0: copies of the stages before `upto` (at most TM_NS ahead of the MMAs)
-    auto issue_copies = [&](int upto) {
-        while (s_issue < upto) {
-            const int buf = s_issue % TM_NS;
-            if (s_issue >= TM_NS) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[buf]), ((s_issue / TM_NS) - 1) & 1) && ok;
-            const uint32_t fb = tc::smem_u32(&mbar_full[buf]);
-            tc::mbar_expect_tx(fb, 2 * TM_A_BYTES);
-            tc::bulk_g2s(tc::smem_u32(sA + 2 * buf * TM_A_BYTES), Fs + (size_t)s_issue * FS_BLOCK_FLOATS,
-                         2 * TM_A_BYTES, fb);
-            ++s_issue;
-        }
-    };
-    if (tid == 0) issue_copies(min(nst, TM_NS));
     double part = 0.0;
     for (int b = 0; b < nblk; ++b) {
         const int k0 = b * NB, kb = min(NB, n - k0), k1 = k0 + kb;
@@ -1048,18 +1042,28 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
             load_diag_pitched<TM_LIP>(sLi, sD, Lk + (long long)(b + 1) * NB * NB, F, n, k1, min(NB, n - k1));
         cp_async_commit();
         if (k1 >= n) break;
-        // MMAs of this panel (thread 0): tiles T_first .. nt - 1, four K quarters
-        // each, their operand blocks copied up to TM_NS stages ahead
+        // MMAs of this panel: tiles T_first .. nt - 1, four K quarters each
         const int T_first = k1 >> 7;
-        if (tid == 0) {
-            const uint32_t b0 = tc::smem_u32(sB), b1 = b0 + TM_B_BYTES;
-            for (int T = T_first; T < nt; ++T) {
-                for (int qk = 0; qk < 4; ++qk, ++stage) {
-                    issue_copies(min(nst, stage + TM_NS));
-                    const int buf = stage % TM_NS;
-                    ok = tc::mbar_wait(tc::smem_u32(&mbar_full[buf]), (stage / TM_NS) & 1) && ok;
+        for (int T = T_first; T < nt; ++T) {
+#pragma unroll
+            for (int qk = 0; qk < 4; ++qk, ++stage) {
+                const int buf = stage % TM_NS;
+                if (stage >= TM_NS) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[buf]), ((stage / TM_NS) - 1) & 1) && ok;
+                unsigned char* ah = sA + 2 * buf * TM_A_BYTES;
+                if ((qk & 1) == 0) {
+                    tm_store(ah, ah + TM_A_BYTES, av0, k1 - 128 * T, n - 128 * T);
+                    if (have) tm_load(av0, F, n, ld);
+                } else {
+                    tm_store(ah, ah + TM_A_BYTES, av1, k1 - 128 * T, n - 128 * T);
+                    if (have) tm_load(av1, F, n, ld);
+                }
+                if (have) have = tm_next(ld, nblk, nt);
+                tc::fence_async_smem();
+                __syncthreads();
+                if (tid == 0) {
                     tc::fence_after();
-                    const uint32_t a0 = tc::smem_u32(sA + 2 * buf * TM_A_BYTES), a1 = a0 + TM_A_BYTES;
+                    const uint32_t a0 = tc::smem_u32(ah), a1 = a0 + TM_A_BYTES;
+                    const uint32_t b0 = tc::smem_u32(sB), b1 = b0 + TM_B_BYTES;
                     const uint32_t d = taddr + (uint32_t)(T * TM_N);
 #pragma unroll
                     for (int ks = 0; ks < TM_KS / 8; ++ks) {
@@ -1076,14 +1080,10 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
             }
         }
     }
-    // every MMA done and every copy landed before the accumulators are released
-    if (tid == 0) {
-        for (int i = 0; i < TM_NS; ++i) {
-            const int cnt = (stage - i + TM_NS - 1) / TM_NS;     // stages multiplied from buffer i
-            if (cnt > 0) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[i]), (cnt - 1) & 1) && ok;
-        }
-        for (int s2 = stage; s2 < s_issue; ++s2)                 // copied, not multiplied (after a timeout)
-            tc::mbar_wait(tc::smem_u32(&mbar_full[s2 % TM_NS]), (s2 / TM_NS) & 1);
+    // every MMA done before the accumulators are released
+    for (int i = 0; i < TM_NS; ++i) {
+        const int cnt = (stage - i + TM_NS - 1) / TM_NS;     // stages that used buffer i
+        if (cnt > 0) ok = tc::mbar_wait(tc::smem_u32(&mbar_buf[i]), (cnt - 1) & 1) && ok;
     }
     cp_async_wait<0>();
     ok = __syncthreads_and(ok);
@@ -1456,12 +1456,11 @@ __global__ void k_c64_to_c128(const float2* __restrict__ a, double2* __restrict_
 
 template <typename C>
 static void ldlt_steps(gw_ctx* ctx, const C* chi0, C* fac, int n, int N, C* linv, double* piv,
-                       const char* const names[4], float* split) {
-    const int nst = split ? fs_stages(n) : 0;
+                       const char* const names[4]) {
     constexpr int NB = Tile<C>::NB, TT = Tile<C>::T;
     klaunch(ctx, names[0], k_ldlt_init<C>, N, 256, 0, chi0, fac, n, piv);
     for (int k0 = 0; k0 < n; k0 += NB) {
-        klaunch(ctx, names[1], k_ldlt_panel<C>, N, 256, 0, fac, n, N, k0, linv, piv, ctx->d_status, split, nst);
+        klaunch(ctx, names[1], k_ldlt_panel<C>, N, 256, 0, fac, n, N, k0, linv, piv, ctx->d_status);
         const int m = n - std::min(n, k0 + NB);
         if (m == 0) break;
         if constexpr (sizeof(C) == 8) {
@@ -1478,12 +1477,6 @@ static void ldlt_steps(gw_ctx* ctx, const C* chi0, C* fac, int n, int N, C* linv
     }
 }
 
-size_t forms_split_bytes(const gw_ctx* ctx, int n, int N, gw_precision prec) {
-    if (prec != GW_MIXED || n <= 32 || n > 128 * TM_MAXT) return 0;
-    if (ctx && (ctx->forms_simt || ctx->forms_tensor)) return 0;
-    return (size_t)N * fs_stages(n) * FS_BLOCK_FLOATS * sizeof(float);
-}
-
 size_t ldlt_linv_bytes(int n, int N, gw_precision prec) {
     if (prec == GW_MIXED) return (size_t)N * div_up(n, Tile<float2>::NB) * Tile<float2>::NB * Tile<float2>::NB * sizeof(float2);
     return (size_t)N * div_up(n, Tile<double2>::NB) * Tile<double2>::NB * Tile<double2>::NB * sizeof(double2);
@@ -1494,10 +1487,10 @@ void launch_ldlt(gw_ctx* ctx, gw_W* W) {
     const int n = c->n_sub, N = c->grid.n_omega;
     if (c->prec == GW_MIXED) {
         static const char* const nm[4] = {"k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk", "k_ldlt32_syrk_tc"};
-        ldlt_steps<float2>(ctx, (const float2*)c->chi0_32, W->fac32, n, N, (float2*)W->linv, W->piv, nm, W->fsplit);
+        ldlt_steps<float2>(ctx, (const float2*)c->chi0_32, W->fac32, n, N, (float2*)W->linv, W->piv, nm);
     } else {
         static const char* const nm[4] = {"k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk", "k_ldlt_syrk_tc"};
-        ldlt_steps<double2>(ctx, (const double2*)c->chi0, W->fac, n, N, (double2*)W->linv, W->piv, nm, nullptr);
+        ldlt_steps<double2>(ctx, (const double2*)c->chi0, W->fac, n, N, (double2*)W->linv, W->piv, nm);
     }
 }
 
@@ -1588,10 +1581,9 @@ static bool forms_tm(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double*
     if (n <= 32 || n > 128 * TM_MAXT) return false;
     const int chunks = div_up(R, TM_RC);
     if (chunks > 65535 || N - 1 > 65535) return false;
-    if (!W->fsplit) return false;
     allow_max_smem(k_forms_tm);
     klaunch(ctx, "k_forms32_tm", k_forms_tm, dim3(chunks, N - 1), 256, forms_tm_smem(), (const float2*)W->fac32,
-            (const float2*)W->linv, (const float*)W->fsplit, fs_stages(n), n, N, Q, R, cout, ctx->d_status);
+            (const float2*)W->linv, n, N, Q, R, cout, ctx->d_status);
     return true;
 }
 

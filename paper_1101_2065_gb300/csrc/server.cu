@@ -77,8 +77,7 @@ static size_t job_bytes(const Job& j) {
     const size_t basis = np * n_pair * (j.prec == GW_MIXED ? 4 : 8) + U + 12 * n_rank * n_rank * 8 + 3 * np * n * 8;
     const size_t chi0 = U + band * pk * rz + N * pk * cz;
     const size_t screen = U + 2 * N * pk * cz + N * (n + 32) * 32 * cz +
-                          std::min<size_t>((size_t)2 << 30, (N ? N - 1 : 0) * n * R * cz) + 3 * np * R * 8 +
-                          forms_split_bytes(nullptr, (int)n, (int)N, j.prec);
+                          std::min<size_t>((size_t)2 << 30, (N ? N - 1 : 0) * n * R * cz) + 3 * np * R * 8;
     const size_t b = mol + std::max(basis, std::max(chi0, screen));
     return b + b / 8 + (64u << 20);
 }

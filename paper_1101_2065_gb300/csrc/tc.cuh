@@ -86,18 +86,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
 }
 
-// arrive on an mbarrier and add bytes to the transaction count its phase waits for
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-
-// bulk copy (1-D TMA) of bytes from global to shared memory, completing on mbar;
-// both addresses 16-byte aligned, bytes a multiple of 16
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
-}
-
 // bounded wait for the given parity of an mbarrier; false on timeout
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     for (long it = 0; it < (1L << 24); ++it) {
