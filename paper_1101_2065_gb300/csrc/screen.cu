@@ -6,11 +6,14 @@
 //     algorithm with NB-column panels.  Each panel step is two launches over
 //     all N frequencies at once: k_ldlt_panel (one CTA per frequency: the
 //     NB x NB diagonal block factorised by one warp in shared memory, the
-//     rows below solved against it one row per thread) and k_ldlt_syrk (the
-//     trailing lower triangle M22 -= L21 D L21^T, one CTA per frequency and
-//     tile).  The steps are small one by one, but N of them side by side
-//     fill the GPU.  chi^RPA_k = M_k^-1 chi0_k = M_k^-1 - 1 (Eq. chi_RPA) is
-//     never formed on the hot path: the forms only need M_k^-1.
+//     rows below solved against it one row per thread) and the trailing
+//     update M22 -= L21 D L21^T: k_ldlt_syrk (one CTA per frequency and
+//     64 x 64 tile, FMA units) or, on the binary32 path for 128 rows and
+//     more, k_ldlt_syrk_tc (one CTA per frequency and 128-row block, 3xTF32
+//     on the tensor cores).  The steps are small one by one, but N of them
+//     side by side fill the GPU.  chi^RPA_k = M_k^-1 chi0_k = M_k^-1 - 1
+//     (Eq. chi_RPA) is never formed on the hot path: the forms only need
+//     M_k^-1.
 // a6  c_r(s_k) = q_r^T gamma_k q_r with gamma_k = -(1/pi) Im chi^RPA_k, and
 //     q^T chi^RPA q = q^T M^-1 q - q^T q with q real, so
 //     c_r = -(1/pi) Im sum_i y_i^2 / d_i,  y = L^-1 q.  One CTA per
@@ -19,7 +22,9 @@
 //     the inverse of the unit lower diagonal block (precomputed by the panel
 //     step of a5, so no serial chain remains), adds y_i^2/d_i to binary64
 //     sums, and updates the rows below from L tiles streamed through a
-//     cp.async double buffer.  c_r(s_0) = 0 (odd spectral function).
+//     cp.async double buffer (k_forms).  The binary32 path with N_sub <= 384
+//     keeps the updates in tensor memory instead and runs them as 3xTF32
+//     products (k_forms_tm).  c_r(s_0) = 0 (odd spectral function).
 #include <cmath>
 
 #include "internal.h"
