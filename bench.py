@@ -48,6 +48,18 @@ def _tf32_peak():
 PEAK_TF32_TFLOPS, PEAK_TF32_SOURCE = _tf32_peak()
 
 
+def _hbm_peak():
+    """Measured HBM copy bandwidth (MEASURED_PEAKS.json), else the 6.8 TB/s fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+PEAK_HBM_GBS, PEAK_HBM_SOURCE = _hbm_peak()
+
+
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -213,8 +225,9 @@ def kernel_model(name, mol, grid, n_rank):
     nb = 32 if f32 else 16
     P = _panels(n, nb)
     if name.startswith("k_ldlt") and name.endswith("_syrk"):
-        # trailing lower triangle (incl. diagonal) x panel width, every frequency
-        return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if m > 0), "alu", peak
+        # trailing lower triangle (incl. diagonal) x panel width, every frequency; the binary32
+        # path leaves only the updates below 128 rows to this kernel
+        return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if m > 0 and (not f32 or m < 128)), "alu", peak
     if name.startswith("k_ldlt") and name.endswith("_panel"):
         return N * 8.0 * sum(kb ** 3 / 6 + m * kb * (kb - 1) / 2 for kb, m in P), "alu", peak
     if name in ("k_forms32_tc", "k_forms32_tm"):
@@ -239,6 +252,59 @@ def kernel_model(name, mol, grid, n_rank):
         # Householder tridiagonalisation: matvec + rank-2 update, 4 n^3/3 multiply-adds
         return (8.0 / 3.0) * n_rank ** 3, "alu", PEAK_FP32_TFLOPS
     return None, None, None
+
+
+def kernel_bytes(name, mol, grid):
+    """Algorithmic HBM bytes of one step's launches of a kernel (each operand
+    read once, each result written once), or None."""
+    import numpy as np
+    n, N = mol.n_sub, grid.n_omega
+    f32 = "32" in name
+    cz = 8 if f32 else 16                       # complex element of the working precision
+    tri = n * (n + 1) // 2
+    P = _panels(n, 32 if f32 else 16)
+    if name.startswith("k_ldlt") and name.endswith("_init"):
+        return 2.0 * N * tri * cz                  # read chi0, write M = 1 - chi0
+    if name.startswith("k_chi0_fft"):
+        eps = np.asarray(mol.eps)
+        d_lo = eps[mol.n_occ] - eps[mol.n_occ - 1]
+        d_hi = eps[-1] - eps[0]
+        band = int(math.floor(d_hi / grid.d_omega)) - int(math.floor(d_lo / grid.d_omega)) + 2
+        return band * tri * cz / 2 + N * tri * cz  # read the spectral weights, write chi0
+    if name == "k_ldlt32_syrk_tc":
+        # read-modify-write of the trailing triangle, panel rows read once
+        return N * sum(m * (m + 1) / 2 * 2 * cz + m * kb * cz for kb, m in P if m >= 128)
+    if name.startswith("k_ldlt") and name.endswith("_syrk"):
+        return N * sum(m * (m + 1) / 2 * 2 * cz + m * kb * cz for kb, m in P if m > 0 and (not f32 or m < 128))
+    if name.startswith("k_ldlt") and name.endswith("_panel"):
+        # panel columns read and written, diagonal-block inverse written
+        return N * sum((m + kb) * kb * 2 * cz + kb * kb * cz for kb, m in P)
+    if name in ("k_forms32_tm", "k_forms32", "k_forms"):
+        # the factor (packed) and the diagonal-block inverses read once per frequency
+        nb = 32 if f32 else 16
+        return (N - 1) * (tri * cz + ((n + nb - 1) // nb) * nb * nb * cz)
+    return None
+
+
+def per_kernel_roofline(kt, steps, mol, grid, n_rank, single_ms):
+    """Achieved fractions of the compute and HBM rooflines of the kernels
+    that take at least 1 % of the single-stream step."""
+    out = {}
+    for k, (ms, nl) in sorted(kt.items(), key=lambda kv: -kv[1][0]):
+        t = ms / steps / 1e3
+        if t <= 0 or t * 1e3 < 0.01 * single_ms:
+            continue
+        flops, bound, peak = kernel_model(k, mol, grid, n_rank)
+        b = kernel_bytes(k, mol, grid)
+        e = {"ms_per_step": ms / steps, "launches_per_step": nl / steps}
+        if flops:
+            e.update({"compute_bound": bound, "tflops": flops / t / 1e12, "compute_peak_tflops": peak,
+                      "compute_frac": flops / t / 1e12 / peak})
+        if b:
+            e.update({"hbm_gbs": b / t / 1e9, "hbm_frac": b / t / 1e9 / PEAK_HBM_GBS})
+        if flops or b:
+            out[k] = e
+    return out
 
 
 def run_gpu(a):
@@ -406,6 +472,7 @@ def run_gpu(a):
                            "it occupies; k_sytrd32_cl runs on one 8-CTA cluster)",
             "measured_in": "single-stream run (kernels not overlapped), CUDA events on the context stream"}
     kernels = {k: {"ms_per_step": v[0] / a.steps, "launches_per_step": v[1] / a.steps} for k, v in single["kt"].items()}
+    kernel_roofline = per_kernel_roofline(single["kt"], a.steps, mol, grid, single["n_rank"], single_ms)
 
     def pct(x, q):
         return float(np.percentile(np.asarray(x), q))
@@ -424,6 +491,9 @@ def run_gpu(a):
                           "latency_ms": {"p50": pct(single["lat"], 50), "p99": pct(single["lat"], 99)}},
         "roofline": roof,
         "kernels": kernels,
+        "kernel_roofline": {"hbm_peak_gbs": PEAK_HBM_GBS, "hbm_peak_source": PEAK_HBM_SOURCE,
+                            "note": "algorithmic flops and bytes per step over the single-stream kernel time; "
+                                    "compute peaks as in roofline.peak_source", "kernels": kernel_roofline},
         "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": int(W * h2d),
                 "d2h_bytes_per_step": int(W * d2h),
                 "path": f"gw_server with {W} workers, jobs submitted from pinned host arrays, wall clock",
