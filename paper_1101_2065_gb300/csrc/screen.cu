@@ -1319,8 +1319,11 @@ __global__ void __launch_bounds__(256, 1) k_forms_tc(const float2* __restrict__ 
 // whole batch.  k_formsb_diag: y_b = L11^-1 y_b for 64 right-hand sides per
 // CTA (one column per thread group, the column's NB values in registers),
 // y_i^2/d_i added to the binary64 sums acc [nb][R]; the last panel writes
-// c.  k_formsb_update: Y_rest -= L_rest,b y_b by T x T tiles.  Before the
-// first update the right-hand sides are the real q (Q [n][R]).
+// c.  k_formsb_update: Y -= L y_b by T x T tiles.  Panels go in pairs: the
+// first panel's update reaches only the second panel's rows, and the rows
+// below the pair take both panels' updates in one read-modify-write of Y
+// (K = 2 NB), which halves the HBM traffic of Y.  Before the first update
+// the right-hand sides are the real q (Q [n][R]).
 template <typename C>
 __global__ void __launch_bounds__(256) k_formsb_diag(const C* __restrict__ fac, const C* __restrict__ linv, int n,
                                                      int N, const double* __restrict__ Q, int R, C* __restrict__ Y,
@@ -1375,25 +1378,31 @@ __global__ void __launch_bounds__(256) k_formsb_diag(const C* __restrict__ fac, 
     }
 }
 
-template <typename C>
+// Y[r_lo, r_hi) -= L[r_lo.., kk0 .. kk0 + kw) y[kk0 .. kk0 + kw) for one
+// T x T tile (rows, right-hand sides) of frequency kbase + blockIdx.z; KW >=
+// kw is the compile-time panel width (one panel, or two panels at once so
+// that the rows below a panel pair are read and written once).  The first
+// update of an element starts from the real q (kk0 == 0).
+template <typename C, int KW>
 __global__ void __launch_bounds__(256) k_formsb_update(const C* __restrict__ fac, int n, const double* __restrict__ Q,
-                                                       int R, C* __restrict__ Y, int k0, int kbase) {
+                                                       int R, C* __restrict__ Y, int kk0, int kw, int r_lo, int r_hi,
+                                                       int kbase) {
     typedef typename CT<C>::R T;
-    constexpr int NB = Tile<C>::NB, TT = Tile<C>::T, TA = Tile<C>::A;
-    __shared__ C sL[TT][NB + 1];
-    __shared__ C sY[NB][TT];
+    constexpr int TT = Tile<C>::T, TA = Tile<C>::A;
+    extern __shared__ __align__(16) unsigned char sraw_fb[];
+    C (*sL)[KW + 1] = reinterpret_cast<C (*)[KW + 1]>(sraw_fb);
+    C (*sY)[TT] = reinterpret_cast<C (*)[TT]>(sraw_fb + sizeof(C) * TT * (KW + 1));
     const int tid = threadIdx.x, z = blockIdx.z, k = kbase + z;
     const C* F = fac + (long long)k * tri(n);
     C* Yk = Y + (long long)z * n * R;
-    const int kb = min(NB, n - k0), k1 = k0 + kb;
-    const int r0 = k1 + blockIdx.x * TT, c0 = blockIdx.y * TT;
-    for (int t = tid; t < TT * NB; t += blockDim.x) {
-        const int rr = t / NB, p = t % NB;
-        sL[rr][p] = (p < kb && r0 + rr < n) ? F[tri(r0 + rr) + k0 + p] : CT<C>::mk(T(0), T(0));
+    const int r0 = r_lo + blockIdx.x * TT, c0 = blockIdx.y * TT;
+    for (int t = tid; t < TT * KW; t += blockDim.x) {
+        const int rr = t / KW, p = t % KW;
+        sL[rr][p] = (p < kw && r0 + rr < r_hi) ? F[tri(r0 + rr) + kk0 + p] : CT<C>::mk(T(0), T(0));
     }
-    for (int t = tid; t < NB * TT; t += blockDim.x) {
+    for (int t = tid; t < KW * TT; t += blockDim.x) {
         const int p = t / TT, cc = t % TT;
-        sY[p][cc] = (p < kb && c0 + cc < R) ? Yk[(long long)(k0 + p) * R + c0 + cc] : CT<C>::mk(T(0), T(0));
+        sY[p][cc] = (p < kw && c0 + cc < R) ? Yk[(long long)(kk0 + p) * R + c0 + cc] : CT<C>::mk(T(0), T(0));
     }
     __syncthreads();
     const int ty = tid / 16, tx = tid % 16;
@@ -1403,7 +1412,7 @@ __global__ void __launch_bounds__(256) k_formsb_update(const C* __restrict__ fac
 #pragma unroll
         for (int b = 0; b < TA; ++b) acc[a][b] = CT<C>::mk(T(0), T(0));
 #pragma unroll 8
-    for (int p = 0; p < NB; ++p) {
+    for (int p = 0; p < KW; ++p) {
         C l[TA], yv[TA];
 #pragma unroll
         for (int a = 0; a < TA; ++a) l[a] = sL[ty + 16 * a][p];
@@ -1417,13 +1426,13 @@ __global__ void __launch_bounds__(256) k_formsb_update(const C* __restrict__ fac
 #pragma unroll
     for (int a = 0; a < TA; ++a) {
         const int i = r0 + ty + 16 * a;
-        if (i >= n) continue;
+        if (i >= r_hi) continue;
 #pragma unroll
         for (int b = 0; b < TA; ++b) {
             const int cc = c0 + tx + 16 * b;
             if (cc >= R) continue;
             const long long o = (long long)i * R + cc;
-            const C src = k0 == 0 ? CT<C>::mk(T(Q[o]), T(0)) : Yk[o];
+            const C src = kk0 == 0 ? CT<C>::mk(T(Q[o]), T(0)) : Yk[o];
             Yk[o] = csub(src, acc[a][b]);
         }
     }
@@ -1511,15 +1520,25 @@ static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N
     double* acc = nullptr;
     try {
         acc = dalloc<double>(ctx, (size_t)nb * R);
+        const size_t sm1 = sizeof(C) * ((size_t)TT * (NB + 1) + (size_t)NB * TT);
+        const size_t sm2 = sizeof(C) * ((size_t)TT * (2 * NB + 1) + (size_t)2 * NB * TT);
+        allow_max_smem(k_formsb_update<C, NB>);
+        allow_max_smem(k_formsb_update<C, 2 * NB>);
         for (int kbase = 1; kbase < N; kbase += nb) {
             const int nbb = std::min(nb, N - kbase);
-            for (int k0 = 0; k0 < n; k0 += NB) {
+            for (int k0 = 0; k0 < n; k0 += 2 * NB) {
+                // panel pair k0 .. k2: diagonal block, second panel's rows, diagonal block, rows below
+                const int k1 = std::min(n, k0 + NB), k2 = std::min(n, k1 + NB);
                 klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R, Y, acc,
                         cout, k0, kbase);
-                const int m = n - std::min(n, k0 + NB);
-                if (m == 0) break;
-                klaunch(ctx, names[1], k_formsb_update<C>, dim3(div_up(m, TT), div_up(R, TT), nbb), 256, 0, fac, n, Q, R,
-                        Y, k0, kbase);
+                if (k1 == n) break;
+                klaunch(ctx, names[1], k_formsb_update<C, NB>, dim3(div_up(k2 - k1, TT), div_up(R, TT), nbb), 256, sm1,
+                        fac, n, Q, R, Y, k0, k1 - k0, k1, k2, kbase);
+                klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R, Y, acc,
+                        cout, k1, kbase);
+                if (k2 == n) break;
+                klaunch(ctx, names[1], k_formsb_update<C, 2 * NB>, dim3(div_up(n - k2, TT), div_up(R, TT), nbb), 256,
+                        sm2, fac, n, Q, R, Y, k0, k2 - k0, k2, n, kbase);
             }
         }
     } catch (...) {
