@@ -75,7 +75,9 @@ def _args():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 50 ms; stop(window) keeps the samples whose
+    timestamps fall inside the host-time window of the timed region."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -90,11 +92,20 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, window=None):
+        """window = (t0, t1) host seconds (time.time()) of the timed region."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -105,19 +116,23 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                rows.append((float(f[1]), float(f[2]), f[5:9]))
+                rows.append((self._stamp(f[0]), float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
         os.unlink(self.path)
+        inside = [r for r in rows if window and r[0] is not None and window[0] - 0.05 <= r[0] <= window[1] + 0.05]
+        in_window = bool(inside)
+        rows = inside or rows
         if not rows:
             return None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[i] for _, _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": reasons, "samples": len(rows),
+                "samples_from": "timed region" if in_window else "sampler run (no sample inside the timed region)"}
 
 
 # ------------------------------------------------------------------ oracle timing
@@ -394,11 +409,12 @@ def run_gpu(a):
             for t in th:
                 t.join()
             return lat, out
+        clk = ClockSampler(local)
+        clk.start()                              # started before the warm-up: nvidia-smi takes a while to start
         run(warmup, False)
         barrier()
         l0 = sum(c.launch_count for c in ctxs)
-        clk = ClockSampler(local)
-        clk.start()
+        tw0 = time.time()
         start = torch.cuda.Event(enable_timing=True)
         start.record(streams[0])                 # the device is idle here (barrier above)
         lat, out = run(steps, True)
@@ -408,7 +424,7 @@ def run_gpu(a):
             ev.record(s_)
             ends.append(ev)
         torch.cuda.synchronize()
-        ck = clk.stop()
+        ck = clk.stop((tw0, time.time()))
         t_ms = max_over_ranks(max(start.elapsed_time(ev) for ev in ends))
         lats = [e0.elapsed_time(e1) for li in lat for (e0, e1) in li]
         return dict(value=world * W * steps / (t_ms / 1e3), t_ms=t_ms, lat=lats,
