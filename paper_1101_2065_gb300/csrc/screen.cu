@@ -1319,10 +1319,10 @@ __global__ void __launch_bounds__(256, 1) k_forms_tc(const float2* __restrict__ 
 // whole batch.  k_formsb_diag: y_b = L11^-1 y_b for 64 right-hand sides per
 // CTA (one column per thread group, the column's NB values in registers),
 // y_i^2/d_i added to the binary64 sums acc [nb][R]; the last panel writes
-// c.  k_formsb_update: Y -= L y_b by T x T tiles.  Panels go in pairs: the
-// first panel's update reaches only the second panel's rows, and the rows
-// below the pair take both panels' updates in one read-modify-write of Y
-// (K = 2 NB), which halves the HBM traffic of Y.  Before the first update
+// c.  k_formsb_update: Y -= L y_b by T x T tiles.  On the binary32 path
+// panels go in pairs: the first panel's update reaches only the second
+// panel's rows, and the rows below the pair take both panels' updates in one
+// read-modify-write of Y (K = 2 NB), which halves the HBM traffic of Y.  Before the first update
 // the right-hand sides are the real q (Q [n][R]).
 template <typename C>
 __global__ void __launch_bounds__(256) k_formsb_diag(const C* __restrict__ fac, const C* __restrict__ linv, int n,
@@ -1526,6 +1526,19 @@ static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N
         allow_max_smem(k_formsb_update<C, 2 * NB>);
         for (int kbase = 1; kbase < N; kbase += nb) {
             const int nbb = std::min(nb, N - kbase);
+            if constexpr (sizeof(C) == 16) {
+                // binary64: bound by the binary64 arithmetic, not by the traffic of Y, so one
+                // panel per update (fewer launches)
+                for (int k0 = 0; k0 < n; k0 += NB) {
+                    const int k1 = std::min(n, k0 + NB);
+                    klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R,
+                            Y, acc, cout, k0, kbase);
+                    if (k1 == n) break;
+                    klaunch(ctx, names[1], k_formsb_update<C, NB>, dim3(div_up(n - k1, TT), div_up(R, TT), nbb), 256,
+                            sm1, fac, n, Q, R, Y, k0, k1 - k0, k1, n, kbase);
+                }
+                continue;
+            }
             for (int k0 = 0; k0 < n; k0 += 2 * NB) {
                 // panel pair k0 .. k2: diagonal block, second panel's rows, diagonal block, rows below
                 const int k1 = std::min(n, k0 + NB), k2 = std::min(n, k1 + NB);
