@@ -449,11 +449,13 @@ __global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fa
         tc::mbar_init(&mbar[1]);
     }
     if (tid < 32) dd[tid] = A[tri(k0 + tid) + k0 + tid];
-    // entries of M of the next two tiles in flight (tile J - 1 is read back while J and J + 1 load)
-    float2 wr[2][2], cn[4][4], cn2[4][4], cp[4][4];
+    // entries of M: tile t lands in register set t % 3, two tiles ahead of its
+    // read-back (sets used in turn, no copies between them that would wait
+    // for the loads in flight)
+    float2 wr[2][2], cs0[4][4], cs1[4][4], cs2[4][4];
     st_load_b(wr, A, n, k0, k1);
-    st_load_c(cn, A, n, rw, k1 + 16 * h);
-    if (ntile > 1) st_load_c(cn2, A, n, rw, k1 + ST_NC + 16 * h);
+    st_load_c(cs0, A, n, rw, k1 + 16 * h);
+    if (ntile > 1) st_load_c(cs1, A, n, rw, k1 + ST_NC + 16 * h);
     // A operand: rows r0 .. r0 + 127 of the panel, staged once
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -473,7 +475,9 @@ __global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fa
     bool ok = true;
     float2* X = sX + warp * 32 * ST_XP;
     int J = 0;
-    for (; J <= ntile; ++J) {
+    // step J: stage and multiply tile J, read back tile J - 1 from register
+    // set `cp`, load tile J + 1 into set `cnx`; false once a wait timed out
+    auto step = [&](float2 (&cp)[4][4], float2 (&cnx)[4][4]) -> bool {
         if (J < ntile) {
             // B operand of tile J (its buffer was last read by the MMAs of tile J - 2, complete)
             unsigned char* bh = sB + 2 * (J & 1) * ST_B_BYTES;
@@ -506,17 +510,10 @@ __global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fa
         if (J >= 1) {
             // tile J - 1: read back, transpose through shared memory, M -= product
             const int Jp = J - 1, cb = k1 + ST_NC * Jp + 16 * h;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    cp[i][t] = cn[i][t];
-                    cn[i][t] = cn2[i][t];
-                }
-            if (J + 1 < ntile) st_load_c(cn2, A, n, rw, k1 + ST_NC * (J + 1) + 16 * h);
+            if (J + 1 < ntile) st_load_c(cnx, A, n, rw, k1 + ST_NC * (J + 1) + 16 * h);
             ok = tc::mbar_wait(tc::smem_u32(&mbar[Jp & 1]), (Jp >> 1) & 1) && ok;
             ok = __syncthreads_and(ok);
-            if (!ok) break;
+            if (!ok) return false;
             tc::fence_after();
             const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(2 * ST_N * (Jp & 1) + 16 * h);
             uint32_t re[16], im[16], re2[16], im2[16];
@@ -548,6 +545,14 @@ __global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fa
             }
             __syncwarp();
         }
+        return true;
+    };
+    // tile J - 1 sits in set (J - 1) % 3, tile J + 1 goes to set (J + 1) % 3
+    while (J <= ntile) {
+        if (!step(cs2, cs1) || ++J > ntile) break;
+        if (!step(cs0, cs2) || ++J > ntile) break;
+        if (!step(cs1, cs0)) break;
+        ++J;
     }
     if (!ok) {
         // the loop ended early at tile J: the MMAs issued so far finish before the columns are freed
