@@ -898,8 +898,7 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
     float2* sLi = sYb + NB * RCP;                                    // [NB][TM_LIP]
     float2* sD = sLi + NB * TM_LIP;                                  // [NB]
     double* red = reinterpret_cast<double*>(sYb);                    // [TM_GROUPS][RC], after the last panel
-    __shared__ __align__(8) uint64_t mbar_buf[TM_NS];      // operand stage read by its MMAs
-    __shared__ __align__(8) uint64_t mbar_full[TM_NS];     // operand stage written by every thread
+    __shared__ __align__(8) uint64_t mbar_buf[TM_NS];
     __shared__ __align__(8) uint64_t mbar_next, mbar_all;
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -910,10 +909,7 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
     const float2* Lk = linv + (long long)k * nblk * NB * NB;
     if (warp == 0) tc::tmem_alloc(&tbase, TM_TMEM_COLS);
     if (tid == 0) {
-        for (int i = 0; i < TM_NS; ++i) {
-            tc::mbar_init(&mbar_buf[i]);
-            tc::mbar_init_n(&mbar_full[i], blockDim.x);
-        }
+        for (int i = 0; i < TM_NS; ++i) tc::mbar_init(&mbar_buf[i]);
         tc::mbar_init(&mbar_next);
         tc::mbar_init(&mbar_all);
     }
@@ -1072,12 +1068,9 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
                     if (have) tm_load(av1, F, n, ld);
                 }
                 if (have) have = tm_next(ld, nblk, nt);
-                // the stage is complete once every thread has arrived (no block barrier:
-                // the other threads go on to the next stage while thread 0 issues the MMAs)
                 tc::fence_async_smem();
-                tc::mbar_arrive(tc::smem_u32(&mbar_full[buf]));
+                __syncthreads();
                 if (tid == 0) {
-                    ok = tc::mbar_wait(tc::smem_u32(&mbar_full[buf]), (stage / TM_NS) & 1) && ok;
                     tc::fence_after();
                     const uint32_t a0 = tc::smem_u32(ah), a1 = a0 + TM_A_BYTES;
                     const uint32_t b0 = tc::smem_u32(sB), b1 = b0 + TM_B_BYTES;

@@ -86,16 +86,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
 }
 
-// mbarrier expecting `count` arrivals per phase
-__device__ __forceinline__ void mbar_init_n(uint64_t* mbar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
-}
-
-// one arrival (release: this thread's earlier shared-memory writes are visible to the waiter)
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-}
-
 // bounded wait for the given parity of an mbarrier; false on timeout
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     for (long it = 0; it < (1L << 24); ++it) {
