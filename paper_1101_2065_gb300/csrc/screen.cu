@@ -832,10 +832,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&v)[8]) {
                  : "r"(addr));
 }
 
-__device__ __forceinline__ void st_shared_f32(unsigned char* p, uint32_t v) {
-    asm volatile("st.shared.b32 [%0], %1;" ::"r"(tc::smem_u32(p)), "r"(v) : "memory");
-}
-
 // stage = (panel b, tile T, quarter qk of the panel's 32 complex columns);
 // the panels with rows below them are b = 0 .. nblk - 2, the tiles of panel
 // b are T = (32 (b + 1)) / 128 .. nt - 1
@@ -1542,21 +1538,21 @@ static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N
                     klaunch(ctx, names[1], k_formsb_update<C, NB>, dim3(div_up(n - k1, TT), div_up(R, TT), nbb), 256,
                             sm1, fac, n, Q, R, Y, k0, k1 - k0, k1, n, kbase);
                 }
-                continue;
-            }
-            for (int k0 = 0; k0 < n; k0 += 2 * NB) {
-                // panel pair k0 .. k2: diagonal block, second panel's rows, diagonal block, rows below
-                const int k1 = std::min(n, k0 + NB), k2 = std::min(n, k1 + NB);
-                klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R, Y, acc,
-                        cout, k0, kbase);
-                if (k1 == n) break;
-                klaunch(ctx, names[1], k_formsb_update<C, NB>, dim3(div_up(k2 - k1, TT), div_up(R, TT), nbb), 256, sm1,
-                        fac, n, Q, R, Y, k0, k1 - k0, k1, k2, kbase);
-                klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R, Y, acc,
-                        cout, k1, kbase);
-                if (k2 == n) break;
-                klaunch(ctx, names[1], k_formsb_update<C, 2 * NB>, dim3(div_up(n - k2, TT), div_up(R, TT), nbb), 256,
-                        sm2, fac, n, Q, R, Y, k0, k2 - k0, k2, n, kbase);
+            } else {
+                for (int k0 = 0; k0 < n; k0 += 2 * NB) {
+                    // panel pair k0 .. k2: diagonal block, second panel's rows, diagonal block, rows below
+                    const int k1 = std::min(n, k0 + NB), k2 = std::min(n, k1 + NB);
+                    klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R, Y, acc,
+                            cout, k0, kbase);
+                    if (k1 == n) break;
+                    klaunch(ctx, names[1], k_formsb_update<C, NB>, dim3(div_up(k2 - k1, TT), div_up(R, TT), nbb), 256, sm1,
+                            fac, n, Q, R, Y, k0, k1 - k0, k1, k2, kbase);
+                    klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R, Y, acc,
+                            cout, k1, kbase);
+                    if (k2 == n) break;
+                    klaunch(ctx, names[1], k_formsb_update<C, 2 * NB>, dim3(div_up(n - k2, TT), div_up(R, TT), nbb), 256,
+                            sm2, fac, n, Q, R, Y, k0, k2 - k0, k2, n, kbase);
+                }
             }
         }
     } catch (...) {
