@@ -168,8 +168,10 @@ class Context:
         _check(self, load().gw_ctx_profile(self.handle, int(enable), kernel.encode() if kernel else None))
 
     def set_option(self, option, value):
-        """Kernel selection switch (GW_OPT_FORMS_TENSOR: per-tile tensor-core forms; GW_OPT_FORMS_SIMT: FMA-unit
-        forms instead of the default tensor-memory forms on the binary32 path)."""
+        """Kernel selection switch of the binary32 path, value 0 or 1 (results agree to binary32 accuracy):
+        GW_OPT_FORMS_TENSOR per-tile tensor-core forms; GW_OPT_FORMS_SIMT FMA-unit forms instead of the
+        default tensor-memory forms; GW_OPT_SYRK_SIMT FMA-unit trailing updates instead of the default
+        tensor-core ones (128 rows and more)."""
         _check(self, load().gw_ctx_set_option(self.handle, int(option), int(value)))
 
     def profile_get(self, kernel):
