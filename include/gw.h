@@ -110,6 +110,7 @@ typedef struct {
     int n_omega, j_lo, j_hi;       /* bins j_lo..j_hi carry all spectral weight */
     int precision;
     double min_pivot_ratio;        /* min_k min_i |d_i(k)| / max|1 - chi0_k| (after screen_W) */
+    int n_pole;                    /* frequencies refactorised in binary64 (GW_OPT_POLES_FP64) */
 } gw_info;
 
 /* ---------------------------------------------------------------- context */
@@ -134,18 +135,33 @@ gw_status gw_ctx_profile(gw_ctx* ctx, int enable, const char* kernel_name);
 gw_status gw_ctx_profile_get(gw_ctx* ctx, const char* kernel_name, double* total_ms, long long* launches);
 /* Kernel selection switches of a context (implementation choices with the
  * same results within the precision's tolerance; the paper has no
- * counterpart).  GW_OPT_FORMS_TENSOR (value 0 or 1, default 0): run the
- * binary32 path's quadratic forms (Eqs. spectral_3 and chi_RPA) with the
- * updates below each panel as 3xTF32 tensor-core products instead of on the
- * binary32 FMA units; applies when N_sub is at most about 330.
+ * counterpart).
  * GW_OPT_FORMS_SIMT (value 0 or 1, default 0): for 32 < N_sub <= 384 the
  * binary32 path by default keeps the forward substitution's updates in
  * tensor memory (3xTF32 products); 1 runs it on the FMA units instead.
  * GW_OPT_SYRK_SIMT (value 0 or 1, default 0): the binary32 factorisation
  * runs its trailing updates of 128 or more rows as 3xTF32 tensor-core
  * products by default; 1 keeps them on the FMA units.
+ * GW_OPT_GEMM_SIMT (value 0 or 1, default 0): the binary32 path's dense
+ * products (g, U, Z, Zup, q) run as 3xTF32 tensor-core products by default;
+ * 1 runs them on the binary32 FMA units (round to nearest throughout).
+ * GW_OPT_KK_TENSOR (value 0 or 1, default 0): the binary32 path's
+ * Cauchy (Kramers-Kronig) sum of Eq. chi_by_spectra runs on the binary32
+ * FMA units by default (round to nearest); 1 runs it as a 3xTF32
+ * tensor-core product, faster, but the tensor cores' accumulation shrinks
+ * every chi0 element by a few 1e-8 relative, which 1 - chi0 amplifies to
+ * about 3e-5 in W near the RPA poles.
+ * GW_OPT_POLES_FP64 (value t in 0..1000, default 0 = off; a precision
+ * policy, Eq. chi_RPA): on the binary32 path, gw_screen_W measures the
+ * spectral weight of chi^RPA_k along 8 fixed pseudo-random directions b,
+ * s(k) = sum_b |Im b^T (1 - chi0_k)^-1 b| from the binary32 factors, and
+ * the frequencies k >= 1 with s(k) >= (t/1000) max_k s(k), those near the
+ * poles of W, are factorised again in binary64 (from the binary32 chi0_k)
+ * where they are consumed: their quadratic forms in gw_sigma_diag and the
+ * read-back of chi^RPA and W.  gw_W_info reports how many (n_pole).
  * GW_ERR_INVALID_ARG for an unknown option or value. */
-enum { GW_OPT_FORMS_TENSOR = 1, GW_OPT_FORMS_SIMT = 2, GW_OPT_SYRK_SIMT = 3 };
+enum { GW_OPT_FORMS_SIMT = 2, GW_OPT_SYRK_SIMT = 3, GW_OPT_GEMM_SIMT = 4,
+       GW_OPT_KK_TENSOR = 5, GW_OPT_POLES_FP64 = 6 };
 gw_status gw_ctx_set_option(gw_ctx* ctx, int option, int value);
 
 /* ---------------------------------------------------------------- molecule */
@@ -265,6 +281,10 @@ gw_status gw_chi0_copy_U(gw_ctx* ctx, const gw_chi0* chi0, double* U);
 gw_status gw_chi0_copy_spectral(gw_ctx* ctx, const gw_chi0* chi0, int j0, int nj, double* A);
 /* chi0_k for k in [k0, k0+nk): [nk*n_sub*n_sub] complex (full symmetric) */
 gw_status gw_chi0_copy(gw_ctx* ctx, const gw_chi0* chi0, int k0, int nk, double* out);
+/* the frequencies refactorised in binary64 by GW_OPT_POLES_FP64, ascending, [n_pole] */
+gw_status gw_W_pole_freqs(const gw_W* W, int* freqs);
+/* min_i |d_i(k)| / max |1 - chi0_k| of the factorisation, [n_omega] */
+gw_status gw_W_copy_pivots(gw_ctx* ctx, const gw_W* W, double* ratio);
 /* chi^RPA_k (compressed, complex [nf*n_sub*n_sub]) for the host list freqs */
 gw_status gw_W_copy_chi_rpa(gw_ctx* ctx, const gw_W* W, const int* freqs, int nf, double* out);
 /* W_k = v + Zup chi^RPA_k Zup^T (complex [nf*n_prod*n_prod]) for the host list freqs */

@@ -250,16 +250,24 @@ extern "C" gw_status gw_ctx_profile_get(gw_ctx* ctx, const char* kernel_name, do
 
 extern "C" gw_status gw_ctx_set_option(gw_ctx* ctx, int option, int value) {
     if (!ctx) return GW_ERR_INVALID_ARG;
-    if (option == GW_OPT_FORMS_TENSOR && (value == 0 || value == 1)) {
-        ctx->forms_tensor = value != 0;
-        return GW_OK;
-    }
     if (option == GW_OPT_FORMS_SIMT && (value == 0 || value == 1)) {
         ctx->forms_simt = value != 0;
         return GW_OK;
     }
     if (option == GW_OPT_SYRK_SIMT && (value == 0 || value == 1)) {
         ctx->syrk_simt = value != 0;
+        return GW_OK;
+    }
+    if (option == GW_OPT_GEMM_SIMT && (value == 0 || value == 1)) {
+        ctx->gemm_simt = value != 0;
+        return GW_OK;
+    }
+    if (option == GW_OPT_KK_TENSOR && (value == 0 || value == 1)) {
+        ctx->kk_tensor = value != 0;
+        return GW_OK;
+    }
+    if (option == GW_OPT_POLES_FP64 && value >= 0 && value <= 1000) {
+        ctx->poles_permille = value;
         return GW_OK;
     }
     ctx->err = "gw_ctx_set_option: unknown option or value";
@@ -374,8 +382,7 @@ static void chi0_release(gw_chi0* c) {
     ctx_free(x, c->pFrac); ctx_free(x, c->seg); ctx_free(x, c->Z); ctx_free(x, c->Zup);
     ctx_free(x, c->Xr); ctx_free(x, c->Bsel);
     ctx_free(x, c->Ut); ctx_free(x, c->tw); ctx_free(x, c->C1); ctx_free(x, c->C2);
-    ctx_free(x, c->chi0); ctx_free(x, c->Ut32); ctx_free(x, c->tw32); ctx_free(x, c->C1_32);
-    ctx_free(x, c->C2_32); ctx_free(x, c->chi0_32);
+    ctx_free(x, c->chi0); ctx_free(x, c->Ut32); ctx_free(x, c->chi0_32); ctx_free(x, c->A64);
     delete c;
 }
 
@@ -426,10 +433,17 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
         rank_of = dalloc<int>(ctx, n_pair);
         // inverse permutation: natural pair index -> sorted position
         launch_invert_perm(ctx, c, rank_of);
+        // near-pole policy on the binary32 path: binary64 V^EF, U and weights as well,
+        // for the binary64 chi0 of the frequencies flagged by gw_screen_W
+        const bool poles64 = prec == GW_MIXED && ctx->poles_permille > 0;
         if (prec == GW_MIXED) {
             // the mixed path uses V^EF only in binary32 (g, U, and X_r for Z)
             V32 = dalloc<float>(ctx, (size_t)n_prod * n_pair);
             launch_vertex_contract32(ctx, mol, occ, n_occ, virt, n_virt, rank_of, V32, n_pair);
+            if (poles64) {
+                VEFt = dalloc<double>(ctx, (size_t)n_prod * n_pair);
+                launch_vertex_contract(ctx, mol, occ, n_occ, virt, n_virt, rank_of, VEFt, n_pair);
+            }
         } else {
             VEFt = dalloc<double>(ctx, (size_t)n_prod * n_pair);
             launch_vertex_contract(ctx, mol, occ, n_occ, virt, n_virt, rank_of, VEFt, n_pair);
@@ -517,13 +531,20 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
             try {
                 launch_to_f32(ctx, c->Zup, Zup32, (long long)n_prod * n_sub);
                 c->Ut32 = dalloc<float>(ctx, (size_t)n_sub * n_pair);
-                gemm_f32(ctx, true, false, n_sub, n_pair, n_prod, 1.f, Zup32, n_sub, V32, n_pair, 0.f, c->Ut32, n_pair);
+                // on the FMA units: the tensor cores' binary32 accumulation rounds toward zero,
+                // a common shrink of every u_p that chi0 squares and 1 - chi0 amplifies near its poles
+                gemm_f32_rn(ctx, true, false, n_sub, n_pair, n_prod, 1.f, Zup32, n_sub, V32, n_pair, 0.f, c->Ut32,
+                            n_pair);
             } catch (...) {
                 ctx_free(ctx, Zup32);
                 throw;
             }
             ctx_free(ctx, Zup32);
             ctx_free(ctx, V32); V32 = nullptr;
+            if (poles64) {
+                c->Ut = dalloc<double>(ctx, (size_t)n_sub * n_pair);
+                gemm_f64(ctx, true, false, n_sub, n_pair, n_prod, 1.0, c->Zup, n_sub, VEFt, n_pair, 0.0, c->Ut, n_pair);
+            }
         } else {
             c->Ut = dalloc<double>(ctx, (size_t)n_sub * n_pair);
             gemm_f64(ctx, true, false, n_sub, n_pair, n_prod, 1.0, c->Zup, n_sub, VEFt, n_pair, 0.0, c->Ut, n_pair);
@@ -534,8 +555,16 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
         ctx_free(ctx, occ); occ = nullptr; ctx_free(ctx, virt); virt = nullptr;
         ctx_free(ctx, rank_of); rank_of = nullptr;
         // a3 + a4: deposit and Cauchy transform by FFT
-        launch_fft_tables(ctx, c);
-        launch_chi0_fft(ctx, c);
+        if (prec == GW_MIXED) {
+            launch_chi0_kk32(ctx, c);
+            if (poles64) {
+                launch_spectral64(ctx, c);
+                ctx_free(ctx, c->Ut); c->Ut = nullptr;
+            }
+        } else {
+            launch_fft_tables(ctx, c);
+            launch_chi0_fft(ctx, c);
+        }
         ctx_finish(ctx, "gw_build_chi0");
     } catch (...) {
         ctx_free(ctx, VEFt); ctx_free(ctx, V32); ctx_free(ctx, T1); ctx_free(ctx, g); ctx_free(ctx, Bsel);
@@ -564,7 +593,51 @@ extern "C" void gw_chi0_free(gw_chi0* c) { chi0_release(c); }
 static void W_release(gw_W* w) {
     if (!w) return;
     ctx_free(w->ctx, w->fac); ctx_free(w->ctx, w->fac32); ctx_free(w->ctx, w->linv); ctx_free(w->ctx, w->piv);
+    ctx_free(w->ctx, w->d_pole);
     delete w;
+}
+
+// Near-pole policy of the binary32 path (Eq. chi_RPA near the poles of W):
+// the spectral weight of chi^RPA_k along 8 fixed pseudo-random directions b,
+// s(k) = sum_b |Im b^T (1 - chi0_k)^-1 b|, from the binary32 factors (the
+// forms kernel with the b as right-hand sides); frequencies k >= 1 with
+// s(k) >= tau max_k s(k) are refactorised in binary64 where consumed.
+static void flag_poles(gw_ctx* ctx, gw_W* w, double tau) {
+    const gw_chi0* c = w->chi0;
+    const int n = c->n_sub, N = c->grid.n_omega, NP = 8;
+    std::vector<double> hb((size_t)n * NP);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    for (auto& x : hb) {                    // splitmix64 -> uniform (-1, 1)
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        x = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+    }
+    double* b = nullptr;
+    double* cp = nullptr;
+    std::vector<double> hc((size_t)NP * N);
+    try {
+        b = upload(ctx, hb.data(), hb.size());
+        cp = dalloc<double>(ctx, (size_t)NP * N);
+        launch_forms(ctx, w, b, NP, cp);
+        download(ctx, hc.data(), cp, hc.size());
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    } catch (...) {
+        ctx_free(ctx, b); ctx_free(ctx, cp);
+        throw;
+    }
+    ctx_free(ctx, b); ctx_free(ctx, cp);
+    std::vector<double> sk(N, 0.0);
+    double mx = 0.0;
+    for (int k = 1; k < N; ++k) {
+        for (int p = 0; p < NP; ++p) sk[k] += std::fabs(hc[(size_t)p * N + k]);
+        mx = std::max(mx, sk[k]);
+    }
+    w->pole_k.clear();
+    for (int k = 1; k < N; ++k)
+        if (mx > 0.0 && sk[k] >= tau * mx) w->pole_k.push_back(k);
+    if (!w->pole_k.empty()) w->d_pole = upload(ctx, w->pole_k.data(), w->pole_k.size());
 }
 
 static gw_W* screen_W(gw_ctx* ctx, const gw_chi0* c) {
@@ -582,6 +655,10 @@ static gw_W* screen_W(gw_ctx* ctx, const gw_chi0* c) {
         download(ctx, piv.data(), w->piv, N);
         ctx_finish(ctx, "gw_screen_W");
         w->min_pivot_ratio = *std::min_element(piv.begin(), piv.end());
+        if (c->prec == GW_MIXED && ctx->poles_permille > 0) {
+            flag_poles(ctx, w, ctx->poles_permille * 1e-3);
+            ctx_finish(ctx, "gw_screen_W");
+        }
     } catch (...) {
         W_release(w);
         throw;
@@ -651,7 +728,7 @@ static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n
                 Zup32 = dalloc<float>(ctx, (size_t)n_prod * n_sub);
                 Q32 = dalloc<float>(ctx, (size_t)n_sub * R);
                 launch_to_f32(ctx, c->Zup, Zup32, (long long)n_prod * n_sub);
-                gemm_f32(ctx, true, false, n_sub, R, n_prod, 1.f, Zup32, n_sub, V32, R, 0.f, Q32, R);
+                gemm_f32_rn(ctx, true, false, n_sub, R, n_prod, 1.f, Zup32, n_sub, V32, R, 0.f, Q32, R);   // as U
                 launch_to_f64(ctx, Q32, Q, (long long)n_sub * R);
                 v32 = dalloc<float>(ctx, (size_t)n_prod * n_prod);
                 T32 = dalloc<float>(ctx, (size_t)n_prod * R);
@@ -672,6 +749,7 @@ static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n
         // c_nk(s_j)
         s->c = dalloc<double>(ctx, (size_t)R * N);
         launch_forms(ctx, W, Q, R, s->c);
+        launch_pole_forms(ctx, W, Q, R, s->c);      // near-pole frequencies in binary64 (policy on)
         // sigma_n(s), Sigma_c grid
         s->sig = dalloc<double>(ctx, (size_t)n_states * s->n_sig);
         launch_sigma_grid(ctx, s);
@@ -775,7 +853,14 @@ extern "C" gw_status gw_W_info(const gw_W* W, gw_info* out) {
     if (!W || !out) return GW_ERR_INVALID_ARG;
     gw_status s = gw_chi0_info(W->chi0, out);
     out->min_pivot_ratio = W->min_pivot_ratio;
+    out->n_pole = (int)W->pole_k.size();
     return s;
+}
+
+extern "C" gw_status gw_W_pole_freqs(const gw_W* W, int* freqs) {
+    if (!W || !freqs) return GW_ERR_INVALID_ARG;
+    std::copy(W->pole_k.begin(), W->pole_k.end(), freqs);
+    return GW_OK;
 }
 
 extern "C" gw_status gw_chi0_copy_pairs(gw_ctx* ctx, const gw_chi0* c, int* E, int* F,
@@ -871,6 +956,15 @@ extern "C" gw_status gw_chi0_copy(gw_ctx* ctx, const gw_chi0* c, int k0, int nk,
                 size_t a = std::max(i, j), b = std::min(i, j);
                 o[(k * n + i) * n + j] = t[k * pk + (size_t)tri(a) + b];
             }
+    API_END
+}
+
+extern "C" gw_status gw_W_copy_pivots(gw_ctx* ctx, const gw_W* W, double* ratio) {
+    if (!ctx || !W || !ratio) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    download(ctx, ratio, W->piv, W->chi0->grid.n_omega);
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
     API_END
 }
 

@@ -1,24 +1,31 @@
-// a3 + a4: spectral weights of chi0 and their Cauchy transform by FFT.
+// a3 + a4: spectral weights of chi0 and their Cauchy transform.
 //
 // For every matrix element (m, n) of the compressed response, the weights
 //   A_j = sum_p 2 w_j(Delta_p) u_pm u_pn      (Eq. chi_by_spectra, spin 2)
-// live only on the band of bins j_lo..j_hi.  The Cauchy integral of
-// Eq. chi_by_spectra on the grid,
-//   chi0_k = sum_j A_j [kap(k-j) - kap(k+j)],  kap(d) = 1/(d dw + i eta),
-// is a Toeplitz part plus a Hankel part.  With L = 2 n_omega both are exact
-// circular products of length L:
-//   chi0 = IFFT( FFT(A) C1 - conj(FFT(A)) C2 )[0..n_omega)
-// where C1 = FFT of kap(d) on d in (-(N-1), N-1) (index d mod L) and
-// C2 = FFT of kap(d) on d in [0, 2N-2] (the Hankel sum is a correlation).
-// Two real elements share one forward complex FFT.  The deposit (a3) is a
+// live only on the band of bins j_lo..j_hi.  The deposit (a3) is a
 // segmented SYRK over the frequency bins, A_j = U_j^T W_j U_j with U_j the
 // pairs of bins j-1 and j and W_j their tent weights, computed by 64 x 64
 // element tiles (U staged through shared memory, each U value reused by 64
-// outputs) and written once as A[bin][element] (packed lower triangle); the
-// FFT kernel reads its two elements' band from there.
+// outputs) and written once per (bin, element): as A[bin][element] (packed
+// lower triangle) on the binary64 path, as TF32 hi/lo operand images for the
+// tensor-core product of kk_tc.cu on the binary32 path.
+//
+// The binary64 path takes the Cauchy integral of Eq. chi_by_spectra on the
+// grid,
+//   chi0_k = sum_j A_j [kap(k-j) - kap(k+j)],  kap(d) = 1/(d dw + i eta),
+// by FFT: a Toeplitz part plus a Hankel part, both exact circular products
+// of length L = 2 n_omega:
+//   chi0 = IFFT( FFT(A) C1 - conj(FFT(A)) C2 )[0..n_omega)
+// where C1 = FFT of kap(d) on d in (-(N-1), N-1) (index d mod L) and
+// C2 = FFT of kap(d) on d in [0, 2N-2] (the Hankel sum is a correlation).
+// Two real elements share one forward complex FFT; the FFT kernel reads its
+// two elements' band from A.
 #include <cmath>
+#include <cstdint>
 
 #include "internal.h"
+#include "kk_layout.cuh"
+#include "tc.cuh"
 
 namespace {
 
@@ -245,10 +252,14 @@ __device__ __forceinline__ void tile_ij(int tt, int& I, int& J) {
 // with weight 2(1 - f_p) and of segment b-1 with weight 2 f_p (tent, spin 2);
 // those pairs are contiguous in the sorted table: [seg[b-1], seg[b+1]).
 // Tile (I, J) of 64 x 64 elements = blockIdx.x, bins [blockIdx.y BC, + BC).
+// With Asplit given (binary32 path), the weights are written instead as
+// TF32 hi/lo operand images for the tensor-core Kramers-Kronig product
+// (kk_layout.cuh).
 template <typename R>
 __global__ void __launch_bounds__(256) k_deposit_syrk(const R* __restrict__ Ut, int n_pair, int n_sub,
                                                       const int* __restrict__ seg, const double* __restrict__ frac,
-                                                      int nb_bins, int BC, long long n_el, R* __restrict__ A) {
+                                                      int nb_bins, int BC, long long n_el, R* __restrict__ A,
+                                                      uint32_t* __restrict__ Asplit, long long n_et) {
     constexpr int T = 64, KC = 32;
     __shared__ R Um[KC][T + 1];     // w_p u_pm for the tile's rows m
     __shared__ R Un[KC][T + 1];     // u_pn for the tile's columns n
@@ -292,7 +303,6 @@ __global__ void __launch_bounds__(256) k_deposit_syrk(const R* __restrict__ Ut, 
                     for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], c[j], acc[i][j]);
             }
         }
-        R* Ab = A + (long long)b * n_el;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int m = m0 + ty + 16 * i;
@@ -300,7 +310,17 @@ __global__ void __launch_bounds__(256) k_deposit_syrk(const R* __restrict__ Ut, 
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int n = n0 + tx + 16 * j;
-                if (n <= m) Ab[(long long)m * (m + 1) / 2 + n] = acc[i][j];
+                if (n > m) continue;
+                const long long e = (long long)m * (m + 1) / 2 + n;
+                if (Asplit) {
+                    uint32_t hi, lo;
+                    tc::split_tf32((float)acc[i][j], hi, lo);
+                    const long long w = kk::weight_word(b, e, n_et);
+                    Asplit[w] = hi;
+                    Asplit[w + kk::TILE_WORDS] = lo;
+                } else {
+                    A[(long long)b * n_el + e] = acc[i][j];
+                }
             }
         }
     }
@@ -308,7 +328,6 @@ __global__ void __launch_bounds__(256) k_deposit_syrk(const R* __restrict__ Ut, 
 
 template <typename C> struct Real;
 template <> struct Real<double2> { typedef double T; static __device__ double2 make(double a, double b) { return make_double2(a, b); } };
-template <> struct Real<float2> { typedef float T; static __device__ float2 make(float a, float b) { return make_float2(a, b); } };
 
 template <typename C>
 __global__ void __launch_bounds__(256) k_chi0_fft(const typename Real<C>::T* __restrict__ A, int n_sub,
@@ -420,7 +439,7 @@ void launch_fft_tables(gw_ctx* ctx, gw_chi0* c) {
 }
 
 template <typename R>
-static void deposit(gw_ctx* ctx, const gw_chi0* c, const R* Ut, R* A, long long n_el) {
+static void deposit(gw_ctx* ctx, const gw_chi0* c, const R* Ut, R* A, long long n_el, uint32_t* Asplit = nullptr) {
     const int n = c->n_sub, band = c->nb_bins + 1;
     const int nt = div_up(n, 64), tiles = nt * (nt + 1) / 2;
     // bins per CTA: about eight CTAs per SM in all
@@ -428,14 +447,13 @@ static void deposit(gw_ctx* ctx, const gw_chi0* c, const R* Ut, R* A, long long 
     const int nbc = div_up(band, BC);
     if (nbc > 65535) gw_throw(GW_ERR_INVALID_ARG, "spectral band too wide for the deposit kernel");
     klaunch(ctx, sizeof(R) == 4 ? "k_deposit_syrk32" : "k_deposit_syrk", k_deposit_syrk<R>, dim3(tiles, nbc), 256, 0,
-            Ut, c->n_pair, n, (const int*)c->seg, (const double*)c->pFrac, c->nb_bins, BC, n_el, A);
+            Ut, c->n_pair, n, (const int*)c->seg, (const double*)c->pFrac, c->nb_bins, BC, n_el, A, Asplit,
+            kk::elem_tiles(n_el));
 }
 
 void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
     const int L = c->L, N = c->grid.n_omega, n = c->n_sub;
-    const bool f32 = c->prec == GW_MIXED;
-    const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
-    size_t smem = 3 * (size_t)fft_buf_len(L) * csz;
+    size_t smem = 3 * (size_t)fft_buf_len(L) * sizeof(double2);
     if (smem > 227 * 1024) gw_throw(GW_ERR_INVALID_ARG, "n_omega too large for the FFT kernel");
     const int ntw = pass_twiddle_count(c->logL);
     int per_sm = std::max(1, (int)((228 * 1024) / (smem + 1024)));
@@ -443,51 +461,62 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
     long long n_grp = (n_el + 1) / 2;
     int grid = (int)std::min<long long>(n_grp, (long long)ctx->num_sms * per_sm);
     const size_t band = (size_t)c->nb_bins + 1;
-    if (f32) {
-        if (!c->Ut32) {        // U^T in binary32 (normally produced directly by the a2 product)
-            c->Ut32 = dalloc<float>(ctx, (size_t)n * c->n_pair);
-            launch_to_f32(ctx, c->Ut, c->Ut32, (long long)n * c->n_pair);
-        }
-        c->tw32 = dalloc<float2>(ctx, L / 2);
-        c->C1_32 = dalloc<float2>(ctx, L);
-        c->C2_32 = dalloc<float2>(ctx, L);
-        launch_to_f32(ctx, (const double*)c->tw, (float*)c->tw32, L);
-        launch_to_f32(ctx, (const double*)c->C1, (float*)c->C1_32, 2LL * L);
-        launch_to_f32(ctx, (const double*)c->C2, (float*)c->C2_32, 2LL * L);
-        float* A = dalloc<float>(ctx, band * n_el);
-        float2* ptw = nullptr;
-        try {
-            ptw = dalloc<float2>(ctx, std::max(ntw, 1));
-            klaunch(ctx, "k_pass_twiddles", k_pass_twiddles<float2>, 1, 256, 0, (const float2*)c->tw32, L, c->logL, ptw);
-            deposit<float>(ctx, c, c->Ut32, A, n_el);
-            c->chi0_32 = dalloc<float2>(ctx, (size_t)N * n_el);
-            allow_max_smem(k_chi0_fft<float2>);
-            klaunch(ctx, "k_chi0_fft32", k_chi0_fft<float2>, grid, 256, smem, (const float*)A, n, c->j_lo, c->nb_bins,
-                    N, c->logL, (const float2*)ptw, (const float2*)c->C1_32, (const float2*)c->C2_32, c->chi0_32);
-        } catch (...) {
-            ctx_free(ctx, A);
-            ctx_free(ctx, ptw);
-            throw;
-        }
+    double* A = dalloc<double>(ctx, band * n_el);
+    double2* ptw = nullptr;
+    try {
+        ptw = dalloc<double2>(ctx, std::max(ntw, 1));
+        klaunch(ctx, "k_pass_twiddles", k_pass_twiddles<double2>, 1, 256, 0, (const double2*)c->tw, L, c->logL, ptw);
+        deposit<double>(ctx, c, c->Ut, A, n_el);
+        c->chi0 = dalloc<double2>(ctx, (size_t)N * n_el);
+        allow_max_smem(k_chi0_fft<double2>);
+        klaunch(ctx, "k_chi0_fft", k_chi0_fft<double2>, grid, 256, smem, (const double*)A, n, c->j_lo, c->nb_bins,
+                N, c->logL, (const double2*)ptw, (const double2*)c->C1, (const double2*)c->C2, c->chi0);
+    } catch (...) {
         ctx_free(ctx, A);
         ctx_free(ctx, ptw);
-    } else {
-        double* A = dalloc<double>(ctx, band * n_el);
-        double2* ptw = nullptr;
+        throw;
+    }
+    ctx_free(ctx, ptw);
+    ctx_free(ctx, A);
+}
+
+// Binary64 spectral weights A64 [band][n_el] of the binary32 path (near-pole
+// policy), deposited from the binary64 U^T.
+void launch_spectral64(gw_ctx* ctx, gw_chi0* c) {
+    const long long n_el = tri(c->n_sub);
+    c->A64 = dalloc<double>(ctx, (size_t)(c->nb_bins + 1) * n_el);
+    deposit<double>(ctx, c, c->Ut, c->A64, n_el);
+}
+
+void launch_chi0_kk32(gw_ctx* ctx, gw_chi0* c) {
+    const int n = c->n_sub, band = c->nb_bins + 1;
+    const long long n_el = (long long)n * (n + 1) / 2;
+    if (!c->Ut32) {            // U^T in binary32 (normally produced directly by the a2 product)
+        c->Ut32 = dalloc<float>(ctx, (size_t)n * c->n_pair);
+        launch_to_f32(ctx, c->Ut, c->Ut32, (long long)n * c->n_pair);
+    }
+    if (ctx->kk_tensor) {
+        const size_t words = kk::weight_words(band, n_el);
+        uint32_t* Asplit = dalloc<uint32_t>(ctx, words);
         try {
-            ptw = dalloc<double2>(ctx, std::max(ntw, 1));
-            klaunch(ctx, "k_pass_twiddles", k_pass_twiddles<double2>, 1, 256, 0, (const double2*)c->tw, L, c->logL, ptw);
-            deposit<double>(ctx, c, c->Ut, A, n_el);
-            c->chi0 = dalloc<double2>(ctx, (size_t)N * n_el);
-            allow_max_smem(k_chi0_fft<double2>);
-            klaunch(ctx, "k_chi0_fft", k_chi0_fft<double2>, grid, 256, smem, (const double*)A, n, c->j_lo, c->nb_bins,
-                    N, c->logL, (const double2*)ptw, (const double2*)c->C1, (const double2*)c->C2, c->chi0);
+            // padding bins of the last chunk and padding elements of the last tile stay zero
+            CUDA_CHECK(cudaMemsetAsync(Asplit, 0, words * sizeof(uint32_t), ctx->stream));
+            deposit<float>(ctx, c, c->Ut32, nullptr, n_el, Asplit);
+            launch_chi0_kk_tc(ctx, c, Asplit);
         } catch (...) {
-            ctx_free(ctx, A);
-            ctx_free(ctx, ptw);
+            ctx_free(ctx, Asplit);
             throw;
         }
-        ctx_free(ctx, ptw);
+        ctx_free(ctx, Asplit);
+    } else {
+        float* A = dalloc<float>(ctx, (size_t)band * n_el);
+        try {
+            deposit<float>(ctx, c, c->Ut32, A, n_el);
+            launch_chi0_kk_fma(ctx, c, A);
+        } catch (...) {
+            ctx_free(ctx, A);
+            throw;
+        }
         ctx_free(ctx, A);
     }
 }

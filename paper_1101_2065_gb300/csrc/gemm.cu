@@ -118,7 +118,12 @@ void gemm_f64(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, double alpha, 
 
 void gemm_f32(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, float alpha, const float* A, long long lda,
               const float* B, long long ldb, float beta, float* C, long long ldc) {
-    if (sgemm_tc(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc)) return;
+    if (!ctx->gemm_simt && sgemm_tc(ctx, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc)) return;
+    gemm_t<float>(ctx, "k_sgemm", ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 1, 0, 0, 0);
+}
+
+void gemm_f32_rn(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, float alpha, const float* A, long long lda,
+                 const float* B, long long ldb, float beta, float* C, long long ldc) {
     gemm_t<float>(ctx, "k_sgemm", ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 1, 0, 0, 0);
 }
 

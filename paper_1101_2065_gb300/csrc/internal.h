@@ -46,9 +46,11 @@ struct gw_ctx {
     int* d_status = nullptr;
     int* h_status = nullptr;
     int num_sms = 0;
-    bool forms_tensor = false;       // GW_OPT_FORMS_TENSOR
     bool forms_simt = false;         // GW_OPT_FORMS_SIMT
     bool syrk_simt = false;          // GW_OPT_SYRK_SIMT
+    bool gemm_simt = false;          // GW_OPT_GEMM_SIMT
+    bool kk_tensor = false;          // GW_OPT_KK_TENSOR
+    int poles_permille = 0;          // GW_OPT_POLES_FP64 (0 = off)
     // optional CUDA-event timing of kernel launches whose name matches prof_filter
     bool prof_on = false;
     std::string prof_filter;
@@ -129,14 +131,14 @@ struct gw_chi0 {
     double* Bsel = nullptr;
     double* Zup = nullptr;           // [n_prod*n_sub]
     double* Ut = nullptr;            // [n_sub*n_pair] U transposed
-    double2* tw = nullptr;           // [L/2] exp(-2 pi i k/L)
+    double2* tw = nullptr;           // [L/2] exp(-2 pi i k/L) (binary64 FFT)
     double2* C1 = nullptr;           // [L] FFT of the Toeplitz kernel
     double2* C2 = nullptr;           // [L] FFT of the Hankel kernel
     double2* chi0 = nullptr;         // [n_omega*n_sub*n_sub], lower triangle valid
     // mixed precision copies
     float* Ut32 = nullptr;
-    float2* tw32 = nullptr; float2* C1_32 = nullptr; float2* C2_32 = nullptr;
-    float2* chi0_32 = nullptr;
+    float2* chi0_32 = nullptr;       // [n_omega][tri(n_sub)] binary32 path
+    double* A64 = nullptr;           // [band][tri(n_sub)] binary64 weights (binary32 path, near-pole policy)
 };
 
 struct gw_W {
@@ -147,6 +149,10 @@ struct gw_W {
     void* linv = nullptr;            // [n_omega][panels][NB][NB] inverses of the unit lower diagonal blocks
     double* piv = nullptr;           // [n_omega] min|d| / max|M|
     double min_pivot_ratio = 0.0;
+    // binary32 path, near-pole policy: frequencies (ascending) whose factorisation
+    // and forms are redone in binary64 where they are consumed
+    std::vector<int> pole_k;
+    int* d_pole = nullptr;
 };
 
 struct gw_sigma {
@@ -185,13 +191,22 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int 
 void basis_rayleigh_scale(gw_ctx* ctx, double* Z, double* Zup, int rows, int n_sub);
 // chi0.cu
 void launch_fft_tables(gw_ctx* ctx, gw_chi0* c);
-void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c);
+void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c);           // binary64: deposit + FFT
+void launch_chi0_kk32(gw_ctx* ctx, gw_chi0* c);          // binary32: deposit + Cauchy sum
+void launch_spectral64(gw_ctx* ctx, gw_chi0* c);         // binary64 weights A64 from c->Ut
+// kk_tc.cu: chi0_32 from the TF32 hi/lo weight images (kk_layout.cuh)
+void launch_chi0_kk_tc(gw_ctx* ctx, gw_chi0* c, const uint32_t* Asplit);
+void launch_chi0_kk_fma(gw_ctx* ctx, gw_chi0* c, const float* A);   // A[band][n_el]
 void launch_spectral_readback(gw_ctx* ctx, const gw_chi0* c, int j0, int nj, double* A);
 void launch_to_f32(gw_ctx* ctx, const double* a, float* b, long long n);
 void launch_to_f64(gw_ctx* ctx, const float* a, double* b, long long n);
 void launch_f64_to_f32_2d(gw_ctx* ctx, const double* a, long long lda, int rows, int cols, float* b);
 void gemm_f32(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, float alpha, const float* A, long long lda,
               const float* B, long long ldb, float beta, float* C, long long ldc);
+// binary32 FMA units only (every addition rounded to nearest): the products whose
+// rounding must carry no common sign (U and q, which chi0 and the forms square)
+void gemm_f32_rn(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, float alpha, const float* A, long long lda,
+                 const float* B, long long ldb, float beta, float* C, long long ldc);
 // tcgen05 3xTF32 tile GEMM; false when the shape is not worth it (caller falls back)
 bool sgemm_tc(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, float alpha, const float* A, long long lda,
               const float* B, long long ldb, float beta, float* C, long long ldc);
@@ -200,6 +215,8 @@ size_t ldlt_linv_bytes(int n, int n_omega, gw_precision prec);
 void launch_ldlt(gw_ctx* ctx, gw_W* W);
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* c);
 void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work);
+// binary32 path: binary64 factorisation and forms at W->pole_k, overwriting those columns of c
+void launch_pole_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout);
 // sigma.cu
 void launch_sigma_grid(gw_ctx* ctx, gw_sigma* s);
 void launch_sigma_c(gw_ctx* ctx, gw_sigma* s);

@@ -25,6 +25,7 @@
 //     cp.async double buffer (k_forms).  The binary32 path with N_sub <= 384
 //     keeps the updates in tensor memory instead and runs them as 3xTF32
 //     products (k_forms_tm).  c_r(s_0) = 0 (odd spectral function).
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -681,7 +682,7 @@ __device__ __forceinline__ void rows_dot(C (&acc)[FR], const C* __restrict__ A, 
 template <typename C, int G, int FT>
 __global__ void __launch_bounds__(320, 1)
     k_forms(const C* __restrict__ fac, const C* __restrict__ linv, int n, int N, const double* __restrict__ Q, int R,
-            int RC, double* __restrict__ c) {
+            int RC, double* __restrict__ c, const int* __restrict__ kmap) {
     typedef typename CT<C>::R T;
     constexpr int NB = Tile<C>::NB, LP = tile_pitch<C>(), FG = G;
     extern __shared__ __align__(16) unsigned char sraw[];
@@ -690,10 +691,13 @@ __global__ void __launch_bounds__(320, 1)
     C* sD = sLi + 2 * NB * NB;                          // [2][NB]
     C* sY = sD + 2 * NB;                                // [n][RC]
     const int tid = threadIdx.x, col = tid % RC, g = tid / RC;
-    const int k = 1 + blockIdx.y, rc0 = blockIdx.x * RC, rc = min(RC, R - rc0);
-    const C* F = fac + (long long)k * tri(n);
+    // factors of frequency k = 1 + blockIdx.y, or (kmap given) of the compact set's entry
+    // blockIdx.y, whose frequency is kmap[blockIdx.y]
+    const int kd = kmap ? (int)blockIdx.y : 1 + (int)blockIdx.y;
+    const int k = kmap ? kmap[blockIdx.y] : kd, rc0 = blockIdx.x * RC, rc = min(RC, R - rc0);
+    const C* F = fac + (long long)kd * tri(n);
     const int nblk = (n + NB - 1) / NB;
-    const C* Lk = linv + (long long)k * nblk * NB * NB;
+    const C* Lk = linv + (long long)kd * nblk * NB * NB;
     load_diag_data<C>(sLi, sD, Lk, F, n, 0, min(NB, n));
     if (n > NB) load_l_tile<C, FT>(sL, F, n, NB, 0, NB);
     cp_async_commit();
@@ -787,7 +791,7 @@ __global__ void __launch_bounds__(320, 1)
         double im = 0.0;
         for (int q = 0; q < FG; ++q) im += red[q * RC + tid];
         c[(long long)(rc0 + tid) * N + k] = -im / M_PI;
-        if (k == 1) c[(long long)(rc0 + tid) * N] = 0.0;
+        if (!kmap && k == 1) c[(long long)(rc0 + tid) * N] = 0.0;
     }
 }
 
@@ -1110,210 +1114,6 @@ __global__ void __launch_bounds__(256, 2) k_forms_tm(const float2* __restrict__ 
     }
 }
 
-// Forms of the binary32 path on the tensor cores: the same resident scheme as
-// k_forms (one CTA per frequency k = 1 + blockIdx.y and chunk of 32
-// right-hand sides, Y [n][33] in shared memory, diagonal blocks by the
-// stored L11^-1), with the update of the rows below each panel as one real
-// TF32 product per 128-row tile (3xTF32, two tensor-memory accumulators):
-//   [Re dY | Im dY] (128 x 64) = [L_re | L_im] (128 x 64) [[y_re, y_im], [-y_im, y_re]]
-// The y_b operand is built once per panel; L row tiles are staged hi/lo in
-// the canonical K-major layout (8 consecutive lanes fill one core matrix with
-// 16-byte stores), the MMAs of a tile are committed to an mbarrier (bounded
-// wait), and the warps read the accumulators back with tcgen05.ld and
-// subtract them from Y.
-constexpr int TCF_RC = 32, TCF_PITCH = 33, TCF_M = 128, TCF_K = 64, TCF_N = 64;
-constexpr int TCF_A_BYTES = TCF_M * TCF_K * 4;      // one 128 x 64 binary32 operand
-constexpr int TCF_B_BYTES = TCF_N * TCF_K * 4;      // one 64 x 64 binary32 operand
-constexpr uint32_t TCF_SBO = (TCF_K / 4) * 128;     // bytes between 8-row groups
-constexpr uint32_t TCF_IDESC = tc::idesc_tf32(TCF_M, TCF_N);
-
-// four consecutive K entries (kq-th quad) of row r, split hi/lo into the two tiles
-__device__ __forceinline__ void stage_quad(unsigned char* hi, unsigned char* lo, int r, int kq, const float (&v)[4]) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) tc::split_tf32(v[q], h[q], l[q]);
-    const uint32_t o = tc::core_off(r, 4 * kq, TCF_K / 4);
-    st_shared_v4(hi + o, h[0], h[1], h[2], h[3]);
-    st_shared_v4(lo + o, l[0], l[1], l[2], l[3]);
-}
-
-// cp.async the raw rows r0 .. r0 + 127 (columns k0 .. k0 + 31) of F into sRaw (zero past n); commits
-__device__ __forceinline__ void prefetch_l_rows(float2* sRaw, const float2* __restrict__ F, int n, int r0, int k0) {
-    for (int t = threadIdx.x; t < TCF_M * 32; t += blockDim.x) {
-        const int r = t >> 5, p = t & 31;
-        float2* d = sRaw + t;
-        if (r0 + r < n) cp_async8(d, F + tri(r0 + r) + k0 + p);
-        else *d = make_float2(0.f, 0.f);
-    }
-    cp_async_commit();
-}
-
-__global__ void __launch_bounds__(256, 1) k_forms_tc(const float2* __restrict__ fac, const float2* __restrict__ linv,
-                                                     int n, int N, const double* __restrict__ Q, int R,
-                                                     double* __restrict__ c, int* status) {
-    constexpr int NB = 32;
-    extern __shared__ __align__(1024) unsigned char sraw_tc[];
-    unsigned char* sAhi = sraw_tc;
-    unsigned char* sAlo = sAhi + TCF_A_BYTES;
-    unsigned char* sBhi = sAlo + TCF_A_BYTES;
-    unsigned char* sBlo = sBhi + TCF_B_BYTES;
-    float2* sRaw = reinterpret_cast<float2*>(sBlo + TCF_B_BYTES);   // [TCF_M][NB] raw L rows of the next tile
-    float2* sLi = sRaw + TCF_M * NB;                                 // [NB][NB]
-    float2* sD = sLi + NB * NB;                                      // [NB]
-    float2* sY = sD + NB;                                            // [n][TCF_PITCH]
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint32_t tbase;
-    __shared__ double red[8][TCF_RC];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int col = tid % TCF_RC, g = tid / TCF_RC;                  // 8 row groups
-    const int k = 1 + blockIdx.y, rc0 = blockIdx.x * TCF_RC, rc = min(TCF_RC, R - rc0);
-    const float2* F = fac + (long long)k * tri(n);
-    const int nblk = (n + NB - 1) / NB;
-    const float2* Lk = linv + (long long)k * nblk * NB * NB;
-    if (warp == 0) tc::tmem_alloc(&tbase, 2 * TCF_N);
-    if (tid == 0) tc::mbar_init(&mbar);
-    {
-        const double* q = Q + rc0 + col;
-        const bool live = col < rc;
-#pragma unroll 4
-        for (int i = g; i < n; i += 8) sY[i * TCF_PITCH + col] = make_float2(live ? (float)q[(long long)i * R] : 0.f, 0.f);
-    }
-    tc::fence_async_smem();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t taddr = tbase, mb = tc::smem_u32(&mbar);
-    uint32_t uses = 0;
-    bool ok = true, raw_pending = false;
-    double2 part = make_double2(0.0, 0.0);
-    for (int blk = 0; blk < nblk && ok; ++blk) {
-        const int k0 = blk * NB, kb = min(NB, n - k0), k1 = k0 + kb;
-        const float2* Li = Lk + (long long)blk * NB * NB;
-        for (int t = tid; t < NB * NB; t += blockDim.x) sLi[t] = Li[t];
-        if (tid < NB) sD[tid] = tid < kb ? F[tri(k0 + tid) + k0 + tid] : make_float2(1.f, 0.f);
-        // y_b = L11^-1 y_b: rows g, g + 8, g + 16, g + 24 of this thread's column
-        float2 y[NB];
-#pragma unroll
-        for (int p = 0; p < NB; ++p) y[p] = p < kb ? sY[(k0 + p) * TCF_PITCH + col] : make_float2(0.f, 0.f);
-        __syncthreads();
-#pragma unroll
-        for (int qq = 0; qq < NB / 8; ++qq) {
-            const int i = g + 8 * qq;
-            float2 v = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int p = 0; p < NB; ++p) v = cfma(sLi[i * NB + p], y[p], v);
-            if (i < kb) {
-                sY[(k0 + i) * TCF_PITCH + col] = v;
-                const float2 w = cdiv(cmul(v, v), sD[i]);
-                part.x += (double)w.x;
-                part.y += (double)w.y;
-            }
-        }
-        __syncthreads();
-        if (k1 >= n) break;
-        // B = [[y_re, y_im], [-y_im, y_re]] as a 64 x 64 K-major operand (rows: output
-        // columns j, Re for j < 32 and Im for j >= 32; K: L_re part then L_im part)
-        for (int t = tid; t < TCF_N * (TCF_K / 4); t += blockDim.x) {
-            const int rr = t & 7, kq = (t >> 3) & 15, rg = t >> 7;
-            const int j = rg * 8 + rr, cc = j & (TCF_RC - 1);
-            const bool im_out = j >= TCF_RC, im_in = kq >= 8;
-            float v[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float2 yy = sY[(k0 + 4 * (kq & 7) + q) * TCF_PITCH + cc];
-                // Re out: (L_re, y_re), (L_im, -y_im); Im out: (L_re, y_im), (L_im, y_re)
-                v[q] = im_out ? (im_in ? yy.x : yy.y) : (im_in ? -yy.y : yy.x);
-            }
-            stage_quad(sBhi, sBlo, j, kq, v);
-        }
-        if (!raw_pending) prefetch_l_rows(sRaw, F, n, k1, k0);
-        raw_pending = false;
-        for (int r0 = k1; r0 < n; r0 += TCF_M) {
-            // A = [L_re | L_im] for rows r0 .. r0 + 127 of panel k0, from the prefetched raw rows
-            cp_async_wait<0>();
-            __syncthreads();
-            for (int t = tid; t < TCF_M * (TCF_K / 4); t += blockDim.x) {
-                const int rr = t & 7, kq = (t >> 3) & 15, rg = t >> 7;
-                const int r = rg * 8 + rr, pb = 4 * (kq & 7);
-                const float2* src = sRaw + r * NB + pb;
-                float v[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] = kq >= 8 ? src[q].y : src[q].x;
-                stage_quad(sAhi, sAlo, r, kq, v);
-            }
-            tc::fence_async_smem();
-            __syncthreads();
-            // the next tile's raw rows (this panel, or the first of the next panel)
-            // stream in while this tile is multiplied and written back
-            if (r0 + TCF_M < n) prefetch_l_rows(sRaw, F, n, r0 + TCF_M, k0);
-            else if (k1 + NB < n) {
-                prefetch_l_rows(sRaw, F, n, k1 + NB, k1);
-                raw_pending = true;
-            }
-            if (tid == 0) {
-                tc::fence_after();
-                const uint32_t ah = tc::smem_u32(sAhi), al = tc::smem_u32(sAlo);
-                const uint32_t bh = tc::smem_u32(sBhi), bl = tc::smem_u32(sBlo);
-#pragma unroll
-                for (int ks = 0; ks < TCF_K / 8; ++ks) {
-                    const uint32_t o = ks * 2 * 128;
-                    const uint32_t first = ks > 0 ? 1u : 0u;
-                    tc::mma_tf32(taddr, tc::smem_desc(ah + o, TCF_SBO), tc::smem_desc(bh + o, TCF_SBO), TCF_IDESC, first);
-                    tc::mma_tf32(taddr + TCF_N, tc::smem_desc(ah + o, TCF_SBO), tc::smem_desc(bl + o, TCF_SBO),
-                                 TCF_IDESC, first);
-                    tc::mma_tf32(taddr + TCF_N, tc::smem_desc(al + o, TCF_SBO), tc::smem_desc(bh + o, TCF_SBO),
-                                 TCF_IDESC, 1u);
-                }
-                tc::commit(mb);
-            }
-            ok = tc::mbar_wait(mb, uses & 1) && ok;
-            ++uses;
-            ok = __syncthreads_and(ok);     // warp-collective tensor-memory loads need a uniform decision
-            tc::fence_after();
-            if (ok) {
-                // warp w: tile rows 32 (w % 4) + lane, complex columns 16 (w / 4) .. + 15
-                const int r = r0 + 32 * (warp & 3) + lane, h = warp >> 2;
-                const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * h;
-                uint32_t re1[16], im1[16], re2[16], im2[16];
-                tc::tmem_ld16(base, re1);
-                tc::tmem_ld16(base + TCF_RC, im1);
-                tc::tmem_ld16(base + TCF_N, re2);
-                tc::tmem_ld16(base + TCF_N + TCF_RC, im2);
-                tc::tmem_wait_ld();
-                if (r < n) {
-                    float2* yr = sY + r * TCF_PITCH + 16 * h;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float2 o = yr[j];
-                        yr[j] = make_float2(o.x - (__uint_as_float(re1[j]) + __uint_as_float(re2[j])),
-                                            o.y - (__uint_as_float(im1[j]) + __uint_as_float(im2[j])));
-                    }
-                }
-            }
-            tc::fence_before();
-            // operand tiles and accumulators are reused by the next tile; a timeout
-            // anywhere stops every thread at the same point
-            ok = __syncthreads_and(ok);
-            if (!ok) break;
-        }
-    }
-    cp_async_wait<0>();
-    if (!ok && tid == 0) atomicOr(status, ST_TIMEOUT);
-    red[g][col] = part.y;
-    __syncthreads();
-    if (ok && tid < rc) {
-        double im = 0.0;
-        for (int q = 0; q < 8; ++q) im += red[q][tid];
-        c[(long long)(rc0 + tid) * N + k] = -im / M_PI;
-        if (k == 1) c[(long long)(rc0 + tid) * N] = 0.0;
-    }
-    tc::fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc::fence_after();
-        tc::tmem_dealloc(taddr, 2 * TCF_N);
-    }
-}
-
 // Batched forward substitution for large n (the right-hand-side chunk no
 // longer fits on chip): Y [nb][n][R] lives in HBM for a batch of nb
 // frequencies k = kbase + z, and every panel takes two launches over the
@@ -1329,7 +1129,7 @@ template <typename C>
 __global__ void __launch_bounds__(256) k_formsb_diag(const C* __restrict__ fac, const C* __restrict__ linv, int n,
                                                      int N, const double* __restrict__ Q, int R, C* __restrict__ Y,
                                                      double* __restrict__ acc, double* __restrict__ c, int k0,
-                                                     int kbase) {
+                                                     int kbase, const int* __restrict__ kmap) {
     typedef typename CT<C>::R T;
     constexpr int NB = Tile<C>::NB, G = 4, RPT = NB / G;     // row groups, rows per thread
     __shared__ C sLi[NB][NB];
@@ -1371,8 +1171,9 @@ __global__ void __launch_bounds__(256) k_formsb_diag(const C* __restrict__ fac, 
         double* a = acc + (long long)z * R + col;
         s += k0 == 0 ? 0.0 : *a;
         if (last) {
-            c[(long long)col * N + k] = -s / M_PI;
-            if (k == 1) c[(long long)col * N] = 0.0;
+            // factors k of the compact set (kmap given) belong to frequency kmap[k]
+            c[(long long)col * N + (kmap ? kmap[k] : k)] = -s / M_PI;
+            if (!kmap && k == 1) c[(long long)col * N] = 0.0;
         } else {
             *a = s;
         }
@@ -1462,6 +1263,46 @@ __global__ void __launch_bounds__(256) k_ldlt_inverse(const double2* __restrict_
     }
 }
 
+// out[i] = chi0_32 of frequency kd[i] (or k1 when kd is null), packed, in binary64
+__global__ void k_gather_c128(const float2* __restrict__ chi0, const int* __restrict__ kd, int k1, int np, long long pk,
+                              double2* __restrict__ out) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)np * pk) return;
+    const int i = (int)(t / pk);
+    const long long e = t % pk;
+    const float2 v = chi0[(long long)(kd ? kd[i] : k1) * pk + e];
+    out[t] = make_double2(v.x, v.y);
+}
+
+// out[i][e] = chi0 of frequency kd[i] (or k1 when kd is null), packed element
+// e, in binary64 by the direct Cauchy sum over the band of the binary64
+// weights A64 [band][n_el] (Eq. chi_by_spectra):
+//   chi0_k[e] = sum_b A64[b][e] [kap(k - j_lo - b) - kap(k + j_lo + b)].
+// One CTA per (element tile of 256, frequency); the CTA's kernel row is
+// tabulated in shared memory first.
+__global__ void __launch_bounds__(256) k_kk_band64(const double* __restrict__ A64, int band, long long n_el, int j_lo,
+                                                   double dw, double eta, const int* __restrict__ kd, int k1,
+                                                   double2* __restrict__ out) {
+    extern __shared__ double2 sk[];
+    const int i = blockIdx.y, k = kd ? kd[i] : k1;
+    for (int b = threadIdx.x; b < band; b += blockDim.x) {
+        const long long j = j_lo + b;
+        const double x1 = (double)(k - j) * dw, x2 = (double)(k + j) * dw, e2 = eta * eta;
+        const double d1 = x1 * x1 + e2, d2 = x2 * x2 + e2;
+        sk[b] = make_double2(x1 / d1 - x2 / d2, -eta / d1 + eta / d2);
+    }
+    __syncthreads();
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < band; ++b) {
+        const double a = A64[(long long)b * n_el + e];
+        re = fma(a, sk[b].x, re);
+        im = fma(a, sk[b].y, im);
+    }
+    out[(long long)i * n_el + e] = make_double2(re, im);
+}
+
 __global__ void k_c64_to_c128(const float2* __restrict__ a, double2* __restrict__ b, long long n) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t < n) b[t] = make_double2(a[t].x, a[t].y);
@@ -1509,13 +1350,16 @@ void launch_ldlt(gw_ctx* ctx, gw_W* W) {
     }
 }
 
+// kmap == nullptr: the factors of frequencies 1 .. N-1 (frequency 0 has c = 0);
+// else the nd factors of a compact set, entry i belonging to frequency kmap[i].
 template <typename C>
 static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, const double* Q, int R,
-                          double* cout, const char* const names[2]) {
+                          double* cout, const char* const names[2], const int* kmap = nullptr, int nd = 0) {
     constexpr int NB = Tile<C>::NB, TT = Tile<C>::T;
+    const int kfirst = kmap ? 0 : 1, kend = kmap ? nd : N;
     // frequencies per batch: Y [nb][n][R] within about 2 GB
     const size_t per = sizeof(C) * (size_t)n * R;
-    const int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)(N - 1), ((size_t)2 << 30) / per));
+    const int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)(kend - kfirst), ((size_t)2 << 30) / per));
     if (nb > 65535 || div_up(R, 64) > 65535) gw_throw(GW_ERR_INVALID_ARG, "forms batch too large");
     C* Y = dalloc<C>(ctx, (size_t)nb * n * R);
     double* acc = nullptr;
@@ -1525,15 +1369,15 @@ static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N
         const size_t sm2 = sizeof(C) * ((size_t)TT * (2 * NB + 1) + (size_t)2 * NB * TT);
         allow_max_smem(k_formsb_update<C, NB>);
         allow_max_smem(k_formsb_update<C, 2 * NB>);
-        for (int kbase = 1; kbase < N; kbase += nb) {
-            const int nbb = std::min(nb, N - kbase);
+        for (int kbase = kfirst; kbase < kend; kbase += nb) {
+            const int nbb = std::min(nb, kend - kbase);
             if constexpr (sizeof(C) == 16) {
                 // binary64: bound by the binary64 arithmetic, not by the traffic of Y, so one
                 // panel per update (fewer launches)
                 for (int k0 = 0; k0 < n; k0 += NB) {
                     const int k1 = std::min(n, k0 + NB);
                     klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R,
-                            Y, acc, cout, k0, kbase);
+                            Y, acc, cout, k0, kbase, kmap);
                     if (k1 == n) break;
                     klaunch(ctx, names[1], k_formsb_update<C, NB>, dim3(div_up(n - k1, TT), div_up(R, TT), nbb), 256,
                             sm1, fac, n, Q, R, Y, k0, k1 - k0, k1, n, kbase);
@@ -1543,12 +1387,12 @@ static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N
                     // panel pair k0 .. k2: diagonal block, second panel's rows, diagonal block, rows below
                     const int k1 = std::min(n, k0 + NB), k2 = std::min(n, k1 + NB);
                     klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R, Y, acc,
-                            cout, k0, kbase);
+                            cout, k0, kbase, kmap);
                     if (k1 == n) break;
                     klaunch(ctx, names[1], k_formsb_update<C, NB>, dim3(div_up(k2 - k1, TT), div_up(R, TT), nbb), 256, sm1,
                             fac, n, Q, R, Y, k0, k1 - k0, k1, k2, kbase);
                     klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R, Y, acc,
-                            cout, k1, kbase);
+                            cout, k1, kbase, kmap);
                     if (k2 == n) break;
                     klaunch(ctx, names[1], k_formsb_update<C, 2 * NB>, dim3(div_up(n - k2, TT), div_up(R, TT), nbb), 256,
                             sm2, fac, n, Q, R, Y, k0, k2 - k0, k2, n, kbase);
@@ -1566,16 +1410,17 @@ static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N
 
 template <typename C>
 static void forms_run(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, const double* Q, int R, double* cout,
-                      const char* name, const char* const bnames[2]) {
+                      const char* name, const char* const bnames[2], const int* kmap = nullptr, int nd = 0) {
     constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, LP = tile_pitch<C>();
-    if (N - 1 > 65535) gw_throw(GW_ERR_INVALID_ARG, "too many frequencies for the forms kernel");
+    const int ny = kmap ? nd : N - 1;
+    if (ny > 65535) gw_throw(GW_ERR_INVALID_ARG, "too many frequencies for the forms kernel");
     const size_t fixed = sizeof(C) * ((size_t)2 * FT * LP + 2 * NB * NB + 2 * NB);
     const size_t budget = 224 * 1024;
     // columns per CTA: at most 320 / FG threads, and Y [n][RC] must fit
     int rc_max = (int)std::min<size_t>(320 / FG, budget > fixed ? (budget - fixed) / (sizeof(C) * (size_t)n) : 0);
     // too few resident right-hand sides per CTA: Y in HBM instead
     if (rc_max < std::min(R, 48)) {
-        forms_batched<C>(ctx, fac, linv, n, N, Q, R, cout, bnames);
+        forms_batched<C>(ctx, fac, linv, n, N, Q, R, cout, bnames, kmap, nd);
         return;
     }
     const int chunks = div_up(R, rc_max);
@@ -1583,27 +1428,7 @@ static void forms_run(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, co
     const size_t smem = fixed + std::max(sizeof(C) * (size_t)n * RC, sizeof(double) * FG * (size_t)RC);
     if (chunks > 65535) gw_throw(GW_ERR_INVALID_ARG, "too many right-hand sides for the forms kernel");
     allow_max_smem(k_forms<C, FG, FT>);
-    klaunch(ctx, name, k_forms<C, FG, FT>, dim3(chunks, N - 1), FG * RC, smem, fac, linv, n, N, Q, R, RC, cout);
-}
-
-// Tensor-core forms (opt-in, GW_OPT_FORMS_TENSOR) when the 32-column chunk of Y
-// fits beside the operand tiles.  Correct, but on the ring it takes 4.4 ms
-// against 3.3 ms for k_forms: one CTA per SM and a serial split -> MMA ->
-// tensor-memory read-back chain per 128-row tile leave the tensor cores
-// idle most of the time; beating the FMA version needs several tiles in
-// flight (warp-specialised producer / MMA / epilogue stages).
-static bool forms_tc(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
-    const gw_chi0* c = W->chi0;
-    const int n = c->n_sub, N = c->grid.n_omega;
-    const size_t smem = 2 * (size_t)TCF_A_BYTES + 2 * (size_t)TCF_B_BYTES +
-                        sizeof(float2) * ((size_t)TCF_M * 32 + 32 * 32 + 32 + (size_t)n * TCF_PITCH);
-    if (smem > 224 * 1024 || n <= 32) return false;
-    const int chunks = div_up(R, TCF_RC);
-    if (chunks > 65535 || N - 1 > 65535) return false;
-    allow_max_smem(k_forms_tc);
-    klaunch(ctx, "k_forms32_tc", k_forms_tc, dim3(chunks, N - 1), 256, smem, (const float2*)W->fac32,
-            (const float2*)W->linv, n, N, Q, R, cout, ctx->d_status);
-    return true;
+    klaunch(ctx, name, k_forms<C, FG, FT>, dim3(chunks, ny), FG * RC, smem, fac, linv, n, N, Q, R, RC, cout, kmap);
 }
 
 // Forms with dY in tensor memory: n <= 384 (three 128-lane tiles of an
@@ -1628,7 +1453,6 @@ static bool forms_tm(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double*
 void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
-    if (c->prec == GW_MIXED && ctx->forms_tensor && forms_tc(ctx, W, Q, R, cout)) return;
     if (c->prec == GW_MIXED && !ctx->forms_simt && forms_tm(ctx, W, Q, R, cout)) return;
     static const char* const b32[2] = {"k_forms32_diag", "k_forms32_update"};
     static const char* const b64[2] = {"k_forms_diag", "k_forms_update"};
@@ -1638,11 +1462,81 @@ void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* co
         forms_run<double2>(ctx, W->fac, (const double2*)W->linv, n, N, Q, R, cout, "k_forms", b64);
 }
 
+// Binary64 factors of np frequencies of the binary32 path's chi0 (kd: device
+// list, or the single frequency k1 when kd is null) into fac [np][tri(n)].
+static void pole_factor(gw_ctx* ctx, const gw_W* W, const int* kd, int k1, int np, double2* fac, void* linv,
+                        double* piv) {
+    static const char* const nm[4] = {"k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk", "k_ldlt_syrk_tc"};
+    const gw_chi0* c = W->chi0;
+    const int n = c->n_sub;
+    const long long pk = tri(n);
+    double2* chi = dalloc<double2>(ctx, (size_t)np * pk);
+    try {
+        if (c->A64) {          // binary64 weights kept by the build: chi0_k in binary64
+            const int band = c->nb_bins + 1;
+            if (div_up(pk, 256) > 0x7fffffff || np > 65535)
+                gw_throw(GW_ERR_INVALID_ARG, "near-pole batch too large");
+            klaunch(ctx, "k_kk_band64", k_kk_band64, dim3(div_up(pk, 256), np), 256, sizeof(double2) * band,
+                    (const double*)c->A64, band, pk, c->j_lo, c->grid.d_omega, c->grid.eta, kd, k1, chi);
+        } else {
+            klaunch(ctx, "k_gather_c128", k_gather_c128, div_up((long long)np * pk, 256), 256, 0,
+                    (const float2*)c->chi0_32, kd, k1, np, pk, chi);
+        }
+        ldlt_steps<double2>(ctx, chi, fac, n, np, (double2*)linv, piv, nm);
+    } catch (...) {
+        ctx_free(ctx, chi);
+        throw;
+    }
+    ctx_free(ctx, chi);
+}
+
+void launch_pole_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
+    static const char* const b64[2] = {"k_forms_diag", "k_forms_update"};
+    const gw_chi0* c = W->chi0;
+    const int n = c->n_sub, N = c->grid.n_omega, np = (int)W->pole_k.size();
+    if (np == 0) return;
+    const long long pk = tri(n);
+    const size_t per = (size_t)pk * 2 * sizeof(double2) + ldlt_linv_bytes(n, 1, GW_FP64) + 2 * sizeof(double);
+    const int nb = (int)std::max<size_t>(1, std::min<size_t>({(size_t)np, ((size_t)4 << 30) / per, (size_t)65535}));
+    double2* fac = dalloc<double2>(ctx, (size_t)nb * pk);
+    void* linv = nullptr;
+    double* piv = nullptr;
+    try {
+        linv = ctx_alloc(ctx, ldlt_linv_bytes(n, nb, GW_FP64));
+        piv = dalloc<double>(ctx, 2 * (size_t)nb);
+        for (int b0 = 0; b0 < np; b0 += nb) {
+            const int m = std::min(nb, np - b0);
+            pole_factor(ctx, W, W->d_pole + b0, 0, m, fac, linv, piv);
+            forms_run<double2>(ctx, fac, (const double2*)linv, n, N, Q, R, cout, "k_forms", b64, W->d_pole + b0, m);
+        }
+    } catch (...) {
+        ctx_free(ctx, fac); ctx_free(ctx, linv); ctx_free(ctx, piv);
+        throw;
+    }
+    ctx_free(ctx, fac); ctx_free(ctx, linv); ctx_free(ctx, piv);
+}
+
 void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work) {
     const gw_chi0* c = W->chi0;
     const long long pk = tri(c->n_sub);
     const double2* F = W->fac ? W->fac + k * pk : work;
-    if (!W->fac) klaunch(ctx, "k_c64_to_c128", k_c64_to_c128, div_up(pk, 256), 256, 0,
-                         (const float2*)(W->fac32 + k * pk), work, pk);
+    if (!W->fac) {
+        if (std::binary_search(W->pole_k.begin(), W->pole_k.end(), k)) {
+            // a frequency the binary32 path refines: its binary64 factors
+            void* linv = ctx_alloc(ctx, ldlt_linv_bytes(c->n_sub, 1, GW_FP64));
+            double* piv = nullptr;
+            try {
+                piv = dalloc<double>(ctx, 2);
+                pole_factor(ctx, W, nullptr, k, 1, work, linv, piv);
+            } catch (...) {
+                ctx_free(ctx, linv); ctx_free(ctx, piv);
+                throw;
+            }
+            ctx_free(ctx, linv); ctx_free(ctx, piv);
+        } else {
+            klaunch(ctx, "k_c64_to_c128", k_c64_to_c128, div_up(pk, 256), 256, 0,
+                    (const float2*)(W->fac32 + k * pk), work, pk);
+        }
+    }
     klaunch(ctx, "k_ldlt_inverse", k_ldlt_inverse, div_up(c->n_sub, 64), 64, 0, F, c->n_sub, out);
 }

@@ -23,9 +23,11 @@ ERRORS = {
 }
 GW_FP64 = 0
 GW_MIXED = 1
-GW_OPT_FORMS_TENSOR = 1
 GW_OPT_FORMS_SIMT = 2
 GW_OPT_SYRK_SIMT = 3
+GW_OPT_GEMM_SIMT = 4
+GW_OPT_KK_TENSOR = 5
+GW_OPT_POLES_FP64 = 6
 
 
 class GWError(RuntimeError):
@@ -51,7 +53,7 @@ class Grid(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n_orb", C.c_int), ("n_occ", C.c_int), ("n_prod", C.c_int), ("n_sub", C.c_int),
                 ("n_pair", C.c_int), ("n_rank", C.c_int), ("n_omega", C.c_int), ("j_lo", C.c_int),
-                ("j_hi", C.c_int), ("precision", C.c_int), ("min_pivot_ratio", C.c_double)]
+                ("j_hi", C.c_int), ("precision", C.c_int), ("min_pivot_ratio", C.c_double), ("n_pole", C.c_int)]
 
 
 def lib_path() -> str:
@@ -97,6 +99,8 @@ def load(path: str | None = None):
         "gw_chi0_copy_spectral": ([P, P, I, I, P], I),
         "gw_chi0_copy": ([P, P, I, I, P], I),
         "gw_W_copy_chi_rpa": ([P, P, P, I, P], I),
+        "gw_W_copy_pivots": ([P, P, P], I),
+        "gw_W_pole_freqs": ([P, P], I),
         "gw_W_copy_full": ([P, P, P, I, P], I),
         "gw_sigma_copy": ([P, P, P, P, P, P], I),
         "gw_sigma_grid": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int)], I),
@@ -169,9 +173,12 @@ class Context:
 
     def set_option(self, option, value):
         """Kernel selection switch of the binary32 path, value 0 or 1 (results agree to binary32 accuracy):
-        GW_OPT_FORMS_TENSOR per-tile tensor-core forms; GW_OPT_FORMS_SIMT FMA-unit forms instead of the
+        GW_OPT_FORMS_SIMT FMA-unit forms instead of the
         default tensor-memory forms; GW_OPT_SYRK_SIMT FMA-unit trailing updates instead of the default
-        tensor-core ones (128 rows and more)."""
+        tensor-core ones (128 rows and more); GW_OPT_GEMM_SIMT binary32 dense products on the FMA units
+        instead of the tensor cores; GW_OPT_KK_TENSOR the binary32 Kramers-Kronig sum on the tensor cores
+        instead of the FMA units; GW_OPT_POLES_FP64 = t (0..1000) refactorises in binary64 the
+        frequencies whose chi^RPA spectral weight is at least t/1000 of its maximum."""
         _check(self, load().gw_ctx_set_option(self.handle, int(option), int(value)))
 
     def profile_get(self, kernel):
@@ -288,6 +295,19 @@ class W(_Handle):
         i = Info()
         _check(self.ctx, load().gw_W_info(self.handle, C.byref(i)))
         return {f: getattr(i, f) for f, _ in Info._fields_}
+
+    def pole_freqs(self):
+        """Frequencies refactorised in binary64 by the near-pole policy (ascending)."""
+        out = np.zeros(self.info()["n_pole"], np.int32)
+        if out.size:
+            _check(self.ctx, load().gw_W_pole_freqs(self.handle, _ptr(out)))
+        return out
+
+    def pivots(self):
+        """min_i |d_i(k)| / max |1 - chi0_k| per frequency k."""
+        out = np.zeros(self.info()["n_omega"])
+        _check(self.ctx, load().gw_W_copy_pivots(self.ctx.handle, self.handle, _ptr(out)))
+        return out
 
     def chi_rpa(self, freqs):
         freqs = np.ascontiguousarray(freqs, np.int32)

@@ -1,11 +1,15 @@
-"""Mixed-precision path (binary32 FFT, factorisation and forms; binary64
-setup, Sigma assembly and quasiparticle root) against the FP64 oracle.
+"""Mixed-precision path (binary32 contractions, Cauchy sum, factorisation
+and forms; binary64 setup, Sigma assembly and quasiparticle root) against
+the FP64 oracle.
 
-Asserted bars: chi0 within relative Frobenius error 1e-5 over the grid and
-quasiparticle energies within 1 meV.  The screened interaction reaches
-about 1e-4 relative error at the frequencies near the RPA poles, where
-kappa(1 - chi0) ~ 300 amplifies binary32 rounding of chi0 and of the
-factorisation; the 1e-5 bar on W is recorded as a strict expected failure.
+Bars: chi0 within relative Frobenius error 1e-5 over the grid, chi^RPA
+(and so W) within 1e-5, quasiparticle energies within 1 meV on the same
+root branch.  The default binary32 path meets the chi^RPA bar at the
+sampled frequencies 1, 100, 400, 1023 of the ring and stays within 2e-5 at
+every frequency (largest near the RPA poles, where 1 - chi0 amplifies
+binary32 rounding); with the near-pole policy (GW_OPT_POLES_FP64) the
+flagged frequencies are refactorised in binary64 and every frequency meets
+1e-5.
 """
 import numpy as np
 import pytest
@@ -28,10 +32,12 @@ def test_chain4_mixed(gwlib, ctx, cfg1, cfg1_oracle):
     try:
         assert h["chi0"].info()["precision"] == gwlib.GW_MIXED
         assert rel(h["chi0"].chi0(0, grid.n_omega), r["chi0"]) < 1e-5
+        # the chain's RPA poles lie beyond its window (kappa larger than the ring's):
+        # without the near-pole policy chi^RPA stays within 4e-5
         ks = [1, 60, 128, 255]
-        assert rel(h["W"].chi_rpa(ks), r["chi_rpa"][ks]) < 3e-4
+        assert rel(h["W"].chi_rpa(ks), r["chi_rpa"][ks]) < 4e-5
         s = h["sigma"].copy()
-        assert rel(s["c"], r["c"]) < 1e-3
+        assert rel(s["c"], r["c"]) < 3e-5
         assert np.abs(e - r["e_qp"]).max() < MEV
         assert np.array_equal(st, r["status"])
     finally:
@@ -45,8 +51,14 @@ def test_ring12_mixed(gwlib, ctx, cfg2, cfg2_oracle):
     try:
         assert rel(h["chi0"].chi0(0, grid.n_omega), r["chi0"]) < 1e-5
         ks = [1, 100, 400, 1023]
-        assert rel(h["W"].chi_rpa(ks), r["chi_rpa"][ks]) < 3e-4
-        assert np.abs(e - r["e_qp"]).max() < MEV
+        assert rel(h["W"].chi_rpa(ks), r["chi_rpa"][ks]) < 1e-5
+        # every 16th frequency: within 2e-5 (the largest errors sit near the RPA poles)
+        kk = list(range(1, grid.n_omega, 16))
+        chi = h["W"].chi_rpa(kk)
+        per = [rel(chi[i], r["chi_rpa"][k]) for i, k in enumerate(kk)]
+        assert max(per) < 2e-5, max(per)
+        assert rel(h["sigma"].copy()["c"], r["c"]) < 2e-5
+        assert np.abs(e - r["e_qp"]).max() < 0.05 * MEV
         assert np.array_equal(st, r["status"])
     finally:
         _free(h)
@@ -54,44 +66,79 @@ def test_ring12_mixed(gwlib, ctx, cfg2, cfg2_oracle):
     h, e, z, st = _mixed(gwlib, ctx, mol, grid)
     try:
         Wg = h["W"].full([100, 400])
-        assert rel(Wg - mol.v, r["W"][1:3] - mol.v) < 3e-4
+        assert rel(Wg - mol.v, r["W"][1:3] - mol.v) < 1e-4
         assert np.abs(e - r["e_qp"]).max() < MEV
         assert np.array_equal(st, r["status"])
     finally:
         _free(h)
 
 
-@pytest.mark.xfail(strict=True, reason="binary32 factorisation and chi0 give ~1e-4 relative error in W near "
-                                       "the RPA poles (kappa ~ 300); the 1e-5 bar needs binary64 there")
-def test_ring12_mixed_W_meets_1e5(gwlib, ctx, cfg2, cfg2_oracle):
-    mol, grid = cfg2
-    r = cfg2_oracle
-    h, *_ = _mixed(gwlib, ctx, mol, grid, Z=r["Z"])
+def _policy_check(gwlib, ctx, mol, grid, r, Z, ks, inside):
+    """Near-pole policy (GW_OPT_POLES_FP64 = 50: spectral weight of chi^RPA
+    at least 5 % of its maximum): the flagged frequencies get chi0 in binary64
+    from binary64 weights and a binary64 factorisation; chi^RPA meets 1e-5 at
+    the sampled frequencies ks and at every flagged frequency, the forms and
+    quasiparticle energies stay within their bars."""
+    ctx.set_option(gwlib.GW_OPT_POLES_FP64, 50)
     try:
-        ks = [1, 100, 400, 1023]
+        h, e, z, st = _mixed(gwlib, ctx, mol, grid, Z=Z)
+    finally:
+        ctx.set_option(gwlib.GW_OPT_POLES_FP64, 0)
+    try:
+        poles = h["W"].pole_freqs()
+        assert h["W"].info()["n_pole"] == poles.size > 0
+        assert np.all(np.diff(poles) > 0) and poles[0] >= 1 and poles[-1] < grid.n_omega
+        assert inside in poles
         assert rel(h["W"].chi_rpa(ks), r["chi_rpa"][ks]) < 1e-5
+        worst = 0.0
+        for i in range(0, poles.size, 64):
+            kk = [int(k) for k in poles[i:i + 64]]
+            chi = h["W"].chi_rpa(kk)
+            worst = max(worst, max(rel(chi[j], r["chi_rpa"][k]) for j, k in enumerate(kk)))
+        assert worst < 1e-5, worst
+        assert rel(h["sigma"].copy()["c"], r["c"]) < 1e-5
+        assert np.abs(e - r["e_qp"]).max() < 0.05 * MEV
+        assert np.array_equal(st, r["status"])
     finally:
         _free(h)
 
 
-def test_ring12_mixed_tensor_core_forms(gwlib, ctx, cfg2, cfg2_oracle):
-    """The opt-in tcgen05 (3xTF32) forms agree with the oracle like the
-    default binary32 forms: c within 1e-3 relative, QP within 1 meV, same
-    root branch."""
+def test_ring12_mixed_W_meets_1e5(gwlib, ctx, cfg2, cfg2_oracle):
     mol, grid = cfg2
     r = cfg2_oracle
-    ctx.set_option(gwlib.GW_OPT_FORMS_TENSOR, 1)
+    # 400 sits in the plasmon band of the ring (~1.6 - 5 Ha)
+    _policy_check(gwlib, ctx, mol, grid, r, r["Z"], [1, 100, 400, 1023], 400)
+
+
+def test_chain4_mixed_W_meets_1e5(gwlib, ctx, cfg1, cfg1_oracle):
+    mol, grid = cfg1
+    _policy_check(gwlib, ctx, mol, grid, cfg1_oracle, None, [1, 60, 128, 255], 128)
+
+
+def test_ring12_kk_tensor_option(gwlib, ctx, cfg2, cfg2_oracle):
+    """GW_OPT_KK_TENSOR: the Cauchy sum as a 3xTF32 tensor-core product gives
+    chi0 within 1e-5 of the oracle (and of the FMA-unit sum to a few 1e-7),
+    quasiparticle energies within 1 meV on the same branch."""
+    mol, grid = cfg2
+    r = cfg2_oracle
+    h, e, z, st = _mixed(gwlib, ctx, mol, grid, Z=r["Z"])
+    try:
+        chi_fma = h["chi0"].chi0(0, grid.n_omega)
+    finally:
+        _free(h)
+    ctx.set_option(gwlib.GW_OPT_KK_TENSOR, 1)
     try:
         h, e, z, st = _mixed(gwlib, ctx, mol, grid, Z=r["Z"])
-        try:
-            s = h["sigma"].copy()
-            assert rel(s["c"], r["c"]) < 1e-3
-            assert np.abs(e - r["e_qp"]).max() < MEV
-            assert np.array_equal(st, r["status"])
-        finally:
-            _free(h)
     finally:
-        ctx.set_option(gwlib.GW_OPT_FORMS_TENSOR, 0)
+        ctx.set_option(gwlib.GW_OPT_KK_TENSOR, 0)
+    try:
+        chi_tc = h["chi0"].chi0(0, grid.n_omega)
+        assert rel(chi_tc, r["chi0"]) < 1e-5
+        assert rel(chi_tc, chi_fma) < 1e-6
+        assert np.abs(e - r["e_qp"]).max() < MEV
+        assert np.array_equal(st, r["status"])
+    finally:
+        _free(h)
 
 
 def test_ring12_forms_tensor_memory_vs_fma(gwlib, ctx, cfg2, cfg2_oracle):
