@@ -1,19 +1,32 @@
 #!/usr/bin/env python
 """GW screening pipeline benchmark on one GB300 (or N independent replicas).
 
-Workload: the 12-atom benzene-like ring (6 heavy atoms x 13 orbitals + 6
-light atoms x 5 orbitals = 108 orbitals, 21 occupied, 600 dominant products
-compressed to 300, 1024 frequency points, FFT length 2048), seeded synthetic
-inputs.  One solve: pair table and compression basis, chi0 (vertex
-contraction, deposit, FFT Kramers-Kronig), W (factorisation of 1 - chi0 at
-every frequency), Sigma for HOMO and LUMO, quasiparticle root.  One step =
---concurrency solves in flight at once (one context and CUDA stream each,
-inputs resident in HBM); the per-kernel table and the roofline come from a
-single-stream run of the same solve, the end-to-end figure from the
-continuous-batching server fed from pinned host memory.
+Workload (the serving configuration the metric is quoted on): a seeded
+Poisson arrival trace at 20 jobs/s of synthetic chains and rings with atom
+counts log-uniform in [10, 120] (13 orbitals, 60 dominant products and 2
+occupied states per atom, W compressed to 30 dimensions per atom), 1024
+frequency points, eta = 0.01 Ha, an HBM admission budget of 150 GB and
+quasiparticle energies for HOMO and LUMO.  One step is one job of the
+trace: its molecule through the whole hot path (pair table and compression
+basis, chi0, factorisation of 1 - chi0 at every frequency, Sigma forms,
+quasiparticle root).  --warmup W jobs (the trace's first W) run first; the
+next --steps K jobs are timed, each submitted at its arrival time relative
+to the first timed arrival, to the continuous-batching engine (gw_server,
+3 worker contexts and CUDA streams, admission by estimated footprint).
+
+value: the molecules already resident in HBM (gw_server_submit_resident),
+wall clock from the first timed arrival to the last result with the device
+synchronised on both sides; latency p50/p99 per job from its submission to
+its result (queueing included).  e2e: the same jobs through gw_server_submit
+from pinned host arrays (upload inside the timed region).  fp64_plain: the
+binary64 path on the smallest timed jobs, closed loop, with the QP
+difference to the mixed result of the same jobs.  The kernel table and the
+roofline come from CUDA events around every launch in a single-stream pass
+over the timed jobs.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on the same workload instead (host cores, frequency-sampled steps).
+oracle instead, on the smallest job of the trace (host cores,
+frequency-sampled steps).
 """
 import argparse
 import json
@@ -29,9 +42,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GW solves/s and p50/p99 latency at 1 meV QP error, mixed vs FP64 plain (1 GB300)"
-WORKLOAD = ("ring12: 12-atom benzene-like ring, 108 orbitals (21 occupied), 600 products "
-            "compressed to 300, 1024 frequencies (FFT length 2048), eta = 0.01 Ha")
-PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs at 2070 MHz
+WORKLOAD = ("serving: seeded Poisson trace at 20 jobs/s of synthetic chains and rings, atom counts log-uniform in "
+            "[10, 120] (13 orbitals, 60 products, 2 occupied per atom, W compressed to 30 dims per atom), "
+            "1024 frequencies, eta 0.01 Ha, HBM admission budget 150 GB, QP HOMO and LUMO")
+RATE, LO, HI, N_OMEGA = 20.0, 10, 120, 1024
+WORKERS = 3
+BUDGET = 150 << 30
+PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12    # 2 DFMA/clk/SM x 152 SMs at 2070 MHz
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 FMA/clk/SM x 152 SMs at 2070 MHz
+HA_MEV = 27211.386245988
 
 
 def _tf32_peak():
@@ -63,13 +82,11 @@ PEAK_HBM_GBS, PEAK_HBM_SOURCE = _hbm_peak()
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--concurrency", type=int, default=4,
-                   help="solves in flight per step (one context and CUDA stream each)")
+    p.add_argument("--workers", type=int, default=WORKERS, help="worker contexts (CUDA streams) of the server")
     return p.parse_args()
 
 
@@ -135,11 +152,203 @@ class ClockSampler:
                 "samples_from": "timed region" if in_window else "sampler run (no sample inside the timed region)"}
 
 
+# ------------------------------------------------------------------ workload
+def trace(n_jobs):
+    """The first n_jobs of the fixed serving trace (the 200-job trace's draws
+    do not depend on how many jobs a run uses): arrival times (s), job specs
+    (kind, atoms, seed), grid."""
+    import synth
+    arrivals, jobs, grid = synth.make_serving_trace(max(200, n_jobs), RATE, LO, HI, N_OMEGA)
+    return [float(a) for a in arrivals[:n_jobs]], jobs[:n_jobs], grid
+
+
+def _build_job(job):
+    """Process-pool task: one synthetic molecule (single-threaded BLAS)."""
+    from synth import molecules as sm
+    return sm.build_job(job)
+
+
+def _pool_init():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+
+
+def build_molecules(jobs):
+    """Synthesise the molecules in a spawned process pool (started before
+    any GPU call of the caller)."""
+    import multiprocessing as mp
+    n = max(1, min(len(jobs), os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(n, initializer=_pool_init) as pool:
+        return pool.map(_build_job, jobs, chunksize=1)
+
+
+def _panels(n, nb):
+    """(kb, m) per panel step of the blocked factorisation: panel width and rows below it."""
+    out = []
+    for k0 in range(0, n, nb):
+        kb = min(nb, n - k0)
+        out.append((kb, n - k0 - kb))
+    return out
+
+
+def forms_kernel(n, R):
+    """Which binary32 forms kernel a molecule takes (the library's dispatch):
+    tensor-memory forms for 32 < n <= 384, the resident FMA forms while 48
+    right-hand sides of Y fit beside the operand tiles, else Y in HBM."""
+    if 32 < n <= 384:
+        return "k_forms32_tm"
+    fixed = 8 * (2 * 64 * 34 + 2 * 32 * 32 + 2 * 32)
+    rc_max = min(80, (224 * 1024 - fixed) // (8 * n))
+    return "k_forms32" if rc_max >= min(R, 48) else "batched"
+
+
+def band_bins(mol, grid):
+    """Spectral bins j_lo .. j_hi carrying the pair transitions."""
+    import numpy as np
+    eps = np.asarray(mol.eps)
+    d_lo = eps[mol.n_occ] - eps[mol.n_occ - 1]
+    d_hi = eps[-1] - eps[0]
+    return int(math.floor(d_hi / grid.d_omega)) - int(math.floor(d_lo / grid.d_omega)) + 2
+
+
+def kernel_model(name, mol, grid, n_rank=None):
+    """Algorithmic work of one solve's launches of a kernel on the binary32
+    path: (flops, bound, peak TFLOP/s), or (None, None, None) when the kernel
+    has no model or does not run for this molecule.
+
+    Complex multiply-adds count 8 flops.  The blocked factorisation and
+    forward substitution launch once per panel with shrinking sizes, so the
+    figure is summed over the solve's launches (achieved = flops / kernel
+    time = average flops per launch / average launch time)."""
+    n, N, R = int(mol.n_sub), grid.n_omega, 2 * int(mol.n_orb)
+    n_orb, n_occ = int(mol.n_orb), int(mol.n_occ)
+    n_pair = n_occ * (n_orb - n_occ)
+    n_prod = int(sum(mol.atom_nprod))
+    if n_rank is None:
+        n_rank = min(n_pair, max(5 * n_orb, n)) if n < n_prod else 0
+    P = _panels(n, 32)
+    fk = forms_kernel(n, R)
+    fwd = (N - 1) * 8.0 * R * n * (n - 1) / 2            # forward substitution L y = q, all right-hand sides
+    diag = (N - 1) * 8.0 * R * sum(kb * kb for kb, _ in P)   # diagonal blocks y_b = L11^-1 y_b
+    if name == "k_forms32_tm":
+        return (fwd, "tensor", PEAK_TF32_TFLOPS / 3) if fk == name else (None, None, None)
+    if name == "k_forms32":
+        return (fwd, "alu", PEAK_FP32_TFLOPS) if fk == name else (None, None, None)
+    if name == "k_forms32_update":
+        return (fwd - diag / 2, "alu", PEAK_FP32_TFLOPS) if fk == "batched" else (None, None, None)
+    if name == "k_forms32_diag":
+        return (diag, "alu", PEAK_FP32_TFLOPS) if fk == "batched" else (None, None, None)
+    if name == "k_ldlt32_syrk_tc":
+        # the trailing updates of 128 rows or more; 3xTF32 takes three TF32 products per binary32 product
+        return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if m >= 128), "tensor", PEAK_TF32_TFLOPS / 3
+    if name == "k_ldlt32_syrk":
+        return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if 0 < m < 128), "alu", PEAK_FP32_TFLOPS
+    if name == "k_ldlt32_panel":
+        return N * 8.0 * sum(kb ** 3 / 6 + m * kb * (kb - 1) / 2 for kb, m in P), "alu", PEAK_FP32_TFLOPS
+    if name == "k_chi0_kk_fma":
+        # complex kernel x real weight: 2 multiply-adds per (frequency, bin, element)
+        return 4.0 * N * band_bins(mol, grid) * n * (n + 1) / 2, "alu", PEAK_FP32_TFLOPS
+    if name == "k_sgemm":
+        # U^T = Zup^T V^EF and q = Zup^T V^nk on the FMA units
+        return 2.0 * n * n_prod * (n_pair + R), "alu", PEAK_FP32_TFLOPS
+    if name == "k_deposit_syrk32":
+        # every pair enters two bins (tent): 2 N_pair multiply-adds per element of the packed lower triangle
+        return 2.0 * 2 * n_pair * (n * (n + 1) / 2), "alu", PEAK_FP32_TFLOPS
+    if name.startswith("k_sytrd32"):
+        # Householder tridiagonalisation: matvec + rank-2 update, 4 n^3/3 multiply-adds
+        return (8.0 / 3.0) * n_rank ** 3, "alu", PEAK_FP32_TFLOPS
+    return None, None, None
+
+
+def kernel_bytes(name, mol, grid):
+    """Algorithmic HBM bytes of one solve's launches of a kernel (each operand
+    read once, each result written once), or None."""
+    n, N, R = int(mol.n_sub), grid.n_omega, 2 * int(mol.n_orb)
+    cz = 8                                          # complex binary32
+    tri = n * (n + 1) // 2
+    P = _panels(n, 32)
+    if name == "k_ldlt32_init":
+        return 2.0 * N * tri * cz                   # read chi0, write M = 1 - chi0
+    if name == "k_chi0_kk_fma":
+        return band_bins(mol, grid) * tri * 4.0 + N * tri * cz   # read the spectral weights, write chi0
+    if name == "k_ldlt32_syrk_tc":
+        return N * sum(m * (m + 1) / 2 * 2 * cz + m * kb * cz for kb, m in P if m >= 128)
+    if name == "k_ldlt32_syrk":
+        return N * sum(m * (m + 1) / 2 * 2 * cz + m * kb * cz for kb, m in P if 0 < m < 128)
+    if name == "k_ldlt32_panel":
+        return N * sum((m + kb) * kb * 2 * cz + kb * kb * cz for kb, m in P)
+    if name in ("k_forms32_tm", "k_forms32"):
+        if forms_kernel(n, R) != name:
+            return None
+        return (N - 1) * (tri * cz + ((n + 31) // 32) * 32 * 32 * cz)
+    if name == "k_forms32_update" and forms_kernel(n, R) == "batched":
+        # the factor read once per frequency; Y read and written once per panel pair
+        pairs = (n + 63) // 64
+        return (N - 1) * (tri * cz + pairs * n * R * cz)
+    return None
+
+
+def workload_model(name, mols, grid, model):
+    """Sum of a per-molecule model over the jobs it applies to (None if none)."""
+    tot, meta = 0.0, None
+    for m in mols:
+        r = model(name, m, grid)
+        v = r[0] if isinstance(r, tuple) else r
+        if v:
+            tot += v
+            if isinstance(r, tuple):
+                meta = r[1:]
+    return (tot, meta) if tot > 0 else (None, meta)
+
+
+def per_kernel_roofline(kt, mols, grid, total_ms):
+    """Achieved fractions of the compute and HBM rooflines of the kernels that
+    take at least 1 % of the summed kernel time."""
+    out = {}
+    for k, (ms, nl) in sorted(kt.items(), key=lambda kv: -kv[1][0]):
+        t = ms / 1e3
+        if t <= 0 or ms < 0.01 * total_ms:
+            continue
+        flops, meta = workload_model(k, mols, grid, kernel_model)
+        b, _ = workload_model(k, mols, grid, kernel_bytes)
+        e = {"ms": ms, "launches": nl, "share": ms / total_ms}
+        if flops:
+            bound, peak = meta
+            e.update({"compute_bound": bound, "tflops": flops / t / 1e12, "compute_peak_tflops": peak,
+                      "compute_frac": flops / t / 1e12 / peak})
+        if b:
+            e.update({"hbm_gbs": b / t / 1e9, "hbm_frac": b / t / 1e9 / PEAK_HBM_GBS})
+        out[k] = e
+    return out
+
+
+KERNELS = ["k_forms32", "k_forms32_tm", "k_forms32_diag", "k_forms32_update", "k_ldlt32_init", "k_ldlt32_panel",
+           "k_ldlt32_syrk", "k_ldlt32_syrk_tc", "k_chi0_kk_fma", "k_chi0_kk_tc", "k_kk_ctable", "k_deposit_syrk32",
+           "k_sgemm", "k_sgemm_tc", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl", "k_bisect", "k_invit",
+           "k_backtransform", "k_cluster_mgs", "k_rayleigh_cols", "k_vertex_contract", "k_vertex_contract32",
+           "k_sigma_c", "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_pair_keys",
+           "k_pair_scatter", "k_pair_segments", "k_invert_perm", "k_to_f32", "k_to_f64", "k_cauchy_table",
+           "k_top_indices", "k_gather_cols", "k_ns_coeff", "k_ns_coeff32", "k_scale_cols_by", "k_oa_stats",
+           "k_oa_E", "k_oa_stats_fin"]
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
+# of the current version of a kernel, on a job of this workload, scaled to
+# the average launch of the timed jobs; an entry is dropped whenever its
+# kernel changes.
+NCU_TRAFFIC = {}
+
+
+def _pct(x, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(x), q)) if len(x) else None
+
+
 # ------------------------------------------------------------------ oracle timing
 def oracle_time(mol, grid, sample=1):
     """Seconds for one oracle solve, timing the frequency-dependent steps
     (Cauchy sum, screening, forms) on every `sample`-th frequency and scaling
-    them by `sample`; every other step runs in full."""
+    them by `sample`; every other step runs in full.  Returns (estimated
+    full-solve seconds, measured seconds)."""
     import numpy as np
     from oracle import gw as og
     N, dw, eta = grid.n_omega, grid.d_omega, grid.eta
@@ -168,173 +377,99 @@ def oracle_time(mol, grid, sample=1):
     for i, n in enumerate(states):
         og.qp_solve(mol.eps[n], sx[i], sx[i], sig[i], j0, dw, eta)
     t3 = time.perf_counter()
-    return (t1 - t0) + sample * (t2 - t1) + (t3 - t2)
+    return (t1 - t0) + sample * (t2 - t1) + (t3 - t2), t3 - t0
+
+
+def _smallest_job():
+    """The smallest job of the fixed 200-job trace (the workload's lower end)."""
+    _, jobs, grid = trace(200)
+    j = min(jobs, key=lambda x: (x[1], x[2]))
+    from synth import molecules as sm
+    return sm.build_job(j), grid, j
+
+
+ORACLE_SAMPLE = 16
 
 
 def run_reference(a):
-    import synth
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    mol, grid = synth.make_config(2)
-    sample = 8
+    mol, grid, job = _smallest_job()
     for _ in range(a.warmup):
-        oracle_time(mol, grid, sample=64)
-    ts = [oracle_time(mol, grid, sample=sample) for _ in range(a.steps)]
-    tot = sum(ts)
-    value = a.steps / tot
+        oracle_time(mol, grid, sample=256)
+    est, real = [], []
+    for _ in range(a.steps):
+        e, r = oracle_time(mol, grid, sample=ORACLE_SAMPLE)
+        est.append(e)
+        real.append(r)
+    value = a.steps / sum(est)
     cores = os.cpu_count()
-    desc = (f"FP64 NumPy/LAPACK oracle, frequency-dependent steps on every {sample}th of the "
-            f"{grid.n_omega} frequencies scaled by {sample}, all other steps in full")
+    desc = (f"FP64 NumPy/LAPACK oracle on the trace's smallest job ({job[0]}, {job[1]} atoms, {grid.n_omega} "
+            f"frequencies; the trace's jobs reach 120 atoms and their cost grows as atoms^3), frequency-dependent "
+            f"steps on every {ORACLE_SAMPLE}th frequency scaled by {ORACLE_SAMPLE}, all other steps in full; value = "
+            f"solves/s of that job extrapolated to all frequencies, ms_per_step = the measured sample")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(real) / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": "host cores"},
+        "config": {"workload": WORKLOAD, "parallelism": "host cores", "sample": desc},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
 # ------------------------------------------------------------------ GPU arm
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 FMA/clk/SM x 152 SMs at 2070 MHz
-KERNELS = ["k_forms", "k_forms32", "k_forms32_tc", "k_forms32_tm", "k_forms_diag", "k_forms_update", "k_forms32_diag", "k_forms32_update",
-           "k_ldlt_init", "k_ldlt_panel", "k_ldlt_syrk", "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk", "k_ldlt32_syrk_tc",
-           "k_chi0_fft", "k_chi0_fft32", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl",
-           "k_bisect", "k_invit", "k_backtransform", "k_oa_stats", "k_oa_E", "k_vertex_contract", "k_vertex_contract32", "k_sigma_c",
-           "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_to_f32", "k_kernel_spectra",
-           "k_cluster_mgs", "k_scale_cols_by", "k_rayleigh_cols", "k_top_indices", "k_gather_cols", "k_ns_coeff", "k_ns_coeff32",
-           "k_pair_keys", "k_pair_scatter", "k_pair_segments", "k_invert_perm", "k_twiddles", "k_cauchy_table",
-           "k_oa_stats_fin", "k_deposit_syrk", "k_deposit_syrk32", "k_sgemm", "k_sgemm_tc", "k_to_f64"]
+def replay(srv, submit, items, arrivals):
+    """Submit items[i] at arrivals[i] (s, relative) from a thread; wait for
+    every job in order.  Returns (results, span_s)."""
+    import threading
+    handles = [None] * len(items)
+    errors = {}
+    t0 = time.perf_counter()
 
+    def submitter():
+        for i, (it, t) in enumerate(zip(items, arrivals)):
+            dt = t - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            try:
+                handles[i] = submit(it)
+            except Exception as ex:        # a rejected job is reported, not retried
+                errors[i] = str(ex)
+                handles[i] = False
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
-# of the current kernel version on this workload (profiles/k_*_ring12.md);
-# an entry is dropped whenever its kernel changes.
-NCU_TRAFFIC = {"k_forms32_tm": 4.490e8}
-
-# fraction of the GPU's SMs a kernel occupies while it runs (default: all)
-SM_SHARE = {"k_sytrd32_cl": 8 / 152}
-
-
-def _panels(n, nb):
-    """(kb, m) per panel step of the blocked factorisation: panel width and rows below it."""
-    out = []
-    for k0 in range(0, n, nb):
-        kb = min(nb, n - k0)
-        out.append((kb, n - k0 - kb))
-    return out
-
-
-def kernel_model(name, mol, grid, n_rank):
-    """Algorithmic work of one step's launches of a kernel: (flops, bound, peak TFLOP/s).
-
-    Complex multiply-adds count 8 flops.  The blocked factorisation and
-    forward substitution launch once per panel with shrinking sizes, so the
-    figure is summed over the step's launches (achieved = flops / kernel time
-    per step = average flops per launch / average launch time)."""
-    n, N, R = mol.n_sub, grid.n_omega, 2 * mol.n_orb
-    L = 2 * N
-    f32 = "32" in name
-    peak = PEAK_FP32_TFLOPS if f32 else PEAK_FP64_TFLOPS
-    nb = 32 if f32 else 16
-    P = _panels(n, nb)
-    if name.startswith("k_ldlt") and name.endswith("_syrk"):
-        # trailing lower triangle (incl. diagonal) x panel width, every frequency; the binary32
-        # path leaves only the updates below 128 rows to this kernel
-        return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if m > 0 and (not f32 or m < 128)), "alu", peak
-    if name.startswith("k_ldlt") and name.endswith("_panel"):
-        return N * 8.0 * sum(kb ** 3 / 6 + m * kb * (kb - 1) / 2 for kb, m in P), "alu", peak
-    if name in ("k_forms32_tc", "k_forms32_tm"):
-        # same forward substitution; the updates below the panels run as 3xTF32 tensor-core products,
-        # whose binary32-product ceiling is a third of the TF32 peak
-        return (N - 1) * 8.0 * R * n * (n - 1) / 2, "tensor", PEAK_TF32_TFLOPS / 3
-    if name == "k_ldlt32_syrk_tc":
-        # the trailing updates of 128 rows or more (the smaller ones stay on the FMA units)
-        return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if m >= 128), "tensor", PEAK_TF32_TFLOPS / 3
-    if name.startswith("k_forms"):
-        # forward substitution L y = q: n(n-1)/2 complex multiply-adds per right-hand side and frequency
-        return (N - 1) * 8.0 * R * n * (n - 1) / 2, "alu", peak
-    if name.startswith("k_deposit_syrk"):
-        # every pair enters two bins (tent): 2 N_pair multiply-adds per element of the packed lower triangle
-        n_pair = int(mol.n_occ) * (int(mol.n_orb) - int(mol.n_occ))
-        return 2.0 * 2 * n_pair * (n * (n + 1) / 2), "alu", peak
-    if name.startswith("k_chi0_fft"):
-        # per element pair: one forward and two inverse complex FFTs of length L (5 L log2 L flops each)
-        pairs = (n * (n + 1) // 2 + 1) // 2
-        return pairs * 3 * 5.0 * L * math.log2(L), "alu", peak
-    if name.startswith("k_sytrd32"):
-        # Householder tridiagonalisation: matvec + rank-2 update, 4 n^3/3 multiply-adds
-        return (8.0 / 3.0) * n_rank ** 3, "alu", PEAK_FP32_TFLOPS
-    return None, None, None
-
-
-def kernel_bytes(name, mol, grid):
-    """Algorithmic HBM bytes of one step's launches of a kernel (each operand
-    read once, each result written once), or None."""
-    import numpy as np
-    n, N = mol.n_sub, grid.n_omega
-    f32 = "32" in name
-    cz = 8 if f32 else 16                       # complex element of the working precision
-    tri = n * (n + 1) // 2
-    P = _panels(n, 32 if f32 else 16)
-    if name.startswith("k_ldlt") and name.endswith("_init"):
-        return 2.0 * N * tri * cz                  # read chi0, write M = 1 - chi0
-    if name.startswith("k_chi0_fft"):
-        eps = np.asarray(mol.eps)
-        d_lo = eps[mol.n_occ] - eps[mol.n_occ - 1]
-        d_hi = eps[-1] - eps[0]
-        band = int(math.floor(d_hi / grid.d_omega)) - int(math.floor(d_lo / grid.d_omega)) + 2
-        return band * tri * cz / 2 + N * tri * cz  # read the spectral weights, write chi0
-    if name == "k_ldlt32_syrk_tc":
-        # read-modify-write of the trailing triangle, panel rows read once
-        return N * sum(m * (m + 1) / 2 * 2 * cz + m * kb * cz for kb, m in P if m >= 128)
-    if name.startswith("k_ldlt") and name.endswith("_syrk"):
-        return N * sum(m * (m + 1) / 2 * 2 * cz + m * kb * cz for kb, m in P if m > 0 and (not f32 or m < 128))
-    if name.startswith("k_ldlt") and name.endswith("_panel"):
-        # panel columns read and written, diagonal-block inverse written
-        return N * sum((m + kb) * kb * 2 * cz + kb * kb * cz for kb, m in P)
-    if name in ("k_forms32_tm", "k_forms32", "k_forms"):
-        # the factor (packed) and the diagonal-block inverses read once per frequency
-        nb = 32 if f32 else 16
-        return (N - 1) * (tri * cz + ((n + nb - 1) // nb) * nb * nb * cz)
-    return None
-
-
-def per_kernel_roofline(kt, steps, mol, grid, n_rank, single_ms):
-    """Achieved fractions of the compute and HBM rooflines of the kernels
-    that take at least 1 % of the single-stream step."""
-    out = {}
-    for k, (ms, nl) in sorted(kt.items(), key=lambda kv: -kv[1][0]):
-        t = ms / steps / 1e3
-        if t <= 0 or t * 1e3 < 0.01 * single_ms:
-            continue
-        flops, bound, peak = kernel_model(k, mol, grid, n_rank)
-        b = kernel_bytes(k, mol, grid)
-        e = {"ms_per_step": ms / steps, "launches_per_step": nl / steps}
-        if flops:
-            e.update({"compute_bound": bound, "tflops": flops / t / 1e12, "compute_peak_tflops": peak,
-                      "compute_frac": flops / t / 1e12 / peak})
-        if b:
-            e.update({"hbm_gbs": b / t / 1e9, "hbm_frac": b / t / 1e9 / PEAK_HBM_GBS})
-        if flops or b:
-            out[k] = e
-    return out
+    th = threading.Thread(target=submitter)
+    th.start()
+    res = [None] * len(items)
+    for i in range(len(items)):
+        while handles[i] is None:
+            time.sleep(0.0002)
+        if handles[i] is not False:
+            res[i] = srv.wait(handles[i])
+    span = time.perf_counter() - t0
+    th.join()
+    if errors:
+        raise RuntimeError(f"jobs rejected: {errors}")
+    return res, span
 
 
 def run_gpu(a):
-    import threading
-
     import numpy as np
-    import torch
 
     import synth
-    import paper_1101_2065_gb300 as gw
-    from paper_1101_2065_gb300 import gw as G
-
     from paper_1101_2065_gb300.replicas import Replicas, world as _world
 
     rank, world, local = _world()
+    W, K = max(0, a.warmup), max(1, a.steps)
+    # the molecules are synthesised in a spawned pool before any GPU call
+    arrivals, jobs, grid = trace(W + K)
+    mols = build_molecules(jobs)
+
+    import torch
+    import paper_1101_2065_gb300 as gw
+    from paper_1101_2065_gb300 import gw as G
+
     torch.cuda.set_device(local)
     reps = Replicas("nccl")
 
@@ -342,199 +477,169 @@ def run_gpu(a):
         reps.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        return reps.max(x)
-
     gw.build.build()
-    mol, grid = synth.make_config(2)
-    states = [mol.n_occ - 1, mol.n_occ]
-    W = max(1, a.concurrency)
-    # one context (CUDA stream) and one resident copy of the inputs per concurrent solve
-    streams = [torch.cuda.Stream() for _ in range(W)]
-    ctxs = [gw.Context(local, 0, s.cuda_stream) for s in streams]
-    mols = [G.gw_mol_upload(c, mol) for c in ctxs]
+    states = lambda m: [m.n_occ - 1, m.n_occ]                     # noqa: E731
+    stage = gw.Context(local)                                      # uploads (staging) and single-stream solves
+    dmols = [G.gw_mol_upload(stage, m) for m in mols]             # inputs resident in HBM
+    srv = G.Server(local, n_workers=a.workers, hbm_budget_bytes=BUDGET)
+    prec = gw.GW_MIXED
+    warm_idx, timed_idx = list(range(W)), list(range(W, W + K))
+    rel_arr = [arrivals[i] - arrivals[W] for i in timed_idx]
 
-    def solve(i, prec):
-        ctx = ctxs[i]
-        c = G.gw_build_chi0(ctx, mols[i], grid, prec)
-        w = G.gw_screen_W(ctx, c)
-        s = G.gw_sigma_diag(ctx, w, states)
-        e, z, st = G.gw_qp_solve(ctx, s)
-        n_rank = c.info()["n_rank"]
-        for h in (s, w, c):
-            h.free()
-        return e, st, n_rank
+    # warm-up: the trace's first W jobs, closed loop
+    if W:
+        replay(srv, lambda i: srv.submit_resident(dmols[i], grid, prec=prec), warm_idx, [0.0] * W)
+    # timed region: the next K jobs at their arrival times, molecules resident
+    l0 = srv.launch_count
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)                                                # nvidia-smi takes a moment to start
+    barrier()
+    tw0 = time.time()
+    res, span = replay(srv, lambda i: srv.submit_resident(dmols[i], grid, prec=prec), timed_idx, rel_arr)
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    span = reps.max(span)
+    ck = clk.stop((tw0, tw1))
+    launches = srv.launch_count - l0
+    value = world * K / span
+    lat = [r["total_ms"] for r in res]
 
-    def measure_single(prec, steps, warmup, clocks=False):
-        """One stream: solves back to back, every kernel timed on the context stream."""
-        ctx, stream = ctxs[0], streams[0]
-        for _ in range(warmup):
-            solve(0, prec)
-        ctx.profile(True, None)
-        barrier()
-        l0 = ctx.launch_count
-        clk = ClockSampler(local)
-        if clocks:
-            clk.start()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-        evs[0].record(stream)
-        for i in range(steps):
-            e, st, n_rank = solve(0, prec)
-            evs[i + 1].record(stream)
-        torch.cuda.synchronize()
-        ck = clk.stop() if clocks else None
-        t_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]))
-        lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
-        kt = {k: ctx.profile_get(k) for k in KERNELS}
-        ctx.profile(False)
-        return dict(value=world * steps / (t_ms / 1e3), t_ms=t_ms, lat=lat, launches=ctx.launch_count - l0,
-                    kt={k: v for k, v in kt.items() if v[1] > 0}, e=e, st=st, clocks=ck, n_rank=n_rank)
-
-    def measure_batched(prec, steps, warmup):
-        """W solves in flight per step, one per context/stream, issued by W host threads."""
-        def run(n, record):
-            lat = [[] for _ in range(W)]
-            out = [None] * W
-            def worker(i):
-                torch.cuda.set_device(local)
-                for _ in range(n):
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(streams[i])
-                    out[i] = solve(i, prec)
-                    e1.record(streams[i])
-                    lat[i].append((e0, e1))
-            th = [threading.Thread(target=worker, args=(i,)) for i in range(W)]
-            for t in th:
-                t.start()
-            for t in th:
-                t.join()
-            return lat, out
-        clk = ClockSampler(local)
-        clk.start()                              # started before the warm-up: nvidia-smi takes a while to start
-        run(warmup, False)
-        barrier()
-        l0 = sum(c.launch_count for c in ctxs)
-        tw0 = time.time()
-        start = torch.cuda.Event(enable_timing=True)
-        start.record(streams[0])                 # the device is idle here (barrier above)
-        lat, out = run(steps, True)
-        ends = []
-        for s_ in streams:
-            ev = torch.cuda.Event(enable_timing=True)
-            ev.record(s_)
-            ends.append(ev)
-        torch.cuda.synchronize()
-        ck = clk.stop((tw0, time.time()))
-        t_ms = max_over_ranks(max(start.elapsed_time(ev) for ev in ends))
-        lats = [e0.elapsed_time(e1) for li in lat for (e0, e1) in li]
-        return dict(value=world * W * steps / (t_ms / 1e3), t_ms=t_ms, lat=lats,
-                    launches=sum(c.launch_count for c in ctxs) - l0, clocks=ck, e=out[0][0], st=out[0][1])
-
-    prec = gw.GW_MIXED if a.precision == "mixed" else gw.GW_FP64
-    single = measure_single(prec, a.steps, a.warmup)
-    batched = measure_batched(prec, a.steps, a.warmup)
-    ref64 = None
-    if prec == gw.GW_MIXED:
-        ref64 = measure_single(gw.GW_FP64, max(2, min(a.steps, 3)), 1)
-
-    # end to end: the continuous-batching server (W workers) from pinned host memory
+    # end to end: the same jobs from pinned host arrays (upload inside the timed region)
     def pinned(x, dt):
         x = np.ascontiguousarray(x, dtype=dt)
         t = torch.empty(x.shape, dtype=getattr(torch, np.dtype(dt).name), pin_memory=True)
         t.numpy()[...] = x
         return t.numpy()
-    hm = synth.Molecule(name=mol.name, pos=mol.pos, atom_norb=pinned(mol.atom_norb, np.int32),
-                        atom_nprod=pinned(mol.atom_nprod, np.int32), nbr_ptr=pinned(mol.nbr_ptr, np.int32),
-                        nbr_idx=pinned(mol.nbr_idx, np.int32), n_occ=mol.n_occ, n_sub=mol.n_sub,
-                        eps=pinned(mol.eps, np.float64), X=pinned(mol.X, np.float64),
-                        vertex=pinned(mol.vertex, np.float64), vertex_off=pinned(mol.vertex_off, np.int64),
-                        v=pinned(mol.v, np.float64))
-    desc = G._Desc(hm)
-    h2d = sum(getattr(desc, k).nbytes for k in ("atom_norb", "atom_nprod", "nbr_ptr", "nbr_idx", "eps", "X",
-                                                  "vertex", "vertex_off", "v"))
-    d2h = len(states) * (8 + 8 + 4 + 8)
-    srv = G.Server(local, n_workers=W, hbm_budget_bytes=150 << 30)
-    for h in [srv.submit(hm, grid, states, prec=prec) for _ in range(W * max(1, min(2, a.warmup)))]:
-        srv.wait(h)
+
+    hmols = {}
+    h2d = 0
+    for i in timed_idx:
+        m = mols[i]
+        hm = synth.Molecule(name=m.name, pos=m.pos, atom_norb=pinned(m.atom_norb, np.int32),
+                            atom_nprod=pinned(m.atom_nprod, np.int32), nbr_ptr=pinned(m.nbr_ptr, np.int32),
+                            nbr_idx=pinned(m.nbr_idx, np.int32), n_occ=m.n_occ, n_sub=m.n_sub,
+                            eps=pinned(m.eps, np.float64), X=pinned(m.X, np.float64),
+                            vertex=pinned(m.vertex, np.float64), vertex_off=pinned(m.vertex_off, np.int64),
+                            v=pinned(m.v, np.float64))
+        d = G._Desc(hm)
+        h2d += sum(getattr(d, k).nbytes for k in ("atom_norb", "atom_nprod", "nbr_ptr", "nbr_idx", "eps", "X",
+                                                   "vertex", "vertex_off", "v"))
+        hmols[i] = hm
+    d2h = 2 * (8 + 8 + 4 + 8)                                       # e_qp, z, root status, Sigma_x per state
     barrier()
-    t0 = time.perf_counter()
-    res = [srv.wait(h) for h in [srv.submit(hm, grid, states, prec=prec) for _ in range(W * a.steps)]]
+    res_e2e, span_e2e = replay(srv, lambda i: srv.submit(hmols[i], grid, prec=prec), timed_idx, rel_arr)
     torch.cuda.synchronize()
-    te = max_over_ranks(time.perf_counter() - t0)
+    span_e2e = reps.max(span_e2e)
     srv.close()
-    e2e = world * W * a.steps / te
-    e2e_lat = [r["total_ms"] for r in res]
+    e2e = world * K / span_e2e
+    same_e2e = all(np.array_equal(x["e_qp"], y["e_qp"]) for x, y in zip(res, res_e2e))
 
-    # roofline of the kernel with the largest share of the step's SM-time (its
-    # single-stream time x the fraction of the SMs it occupies): the batched
-    # headline is bound by SM-time, and the cluster tridiagonalisation, the
-    # longest single-stream kernel, runs on 8 of the 152 SMs beside the others
-    dom = max(single["kt"].items(), key=lambda kv: kv[1][0] * SM_SHARE.get(kv[0], 1.0))[0]
-    flops, bound, peak = kernel_model(dom, mol, grid, single["n_rank"])
-    k_ms, k_n = single["kt"][dom]
-    avg_s = k_ms / k_n / 1e3
-    per_launch = flops / (k_n / a.steps) if flops else None
-    achieved = per_launch / avg_s / 1e12 if flops else None
-    single_ms = single["t_ms"] / a.steps
-    roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": NCU_TRAFFIC.get(dom),
-            "peak_source": (PEAK_TF32_SOURCE + " = dense TF32 tensor peak, / 3: 3xTF32 takes three TF32 products "
-                            "per binary32 product" if bound == "tensor" else
-                            ("128 binary32 FMA/clk/SM" if peak == PEAK_FP32_TFLOPS else "2 binary64 FMA/clk/SM")
-                            + " x 152 SMs x 2070 MHz (recipe unit counts and maximum clock)"),
-            "avg_launch_ms": avg_s * 1e3, "launches": k_n, "flops_per_launch": per_launch,
-            "share_of_step": (k_ms / a.steps) / single_ms,
-            "selected_by": "largest share of the step's SM-time (single-stream kernel time x fraction of the SMs "
-                           "it occupies; k_sytrd32_cl runs on one 8-CTA cluster)",
-            "measured_in": "single-stream run (kernels not overlapped), CUDA events on the context stream"}
-    kernels = {k: {"ms_per_step": v[0] / a.steps, "launches_per_step": v[1] / a.steps} for k, v in single["kt"].items()}
-    kernel_roofline = per_kernel_roofline(single["kt"], a.steps, mol, grid, single["n_rank"], single_ms)
+    # binary64 plain path on the two smallest timed jobs (closed loop, single stream)
+    small = sorted(timed_idx, key=lambda i: mols[i].n_sub)[:2]
+    f64 = []
+    for i in small:
+        t0 = time.perf_counter()
+        e, z, st, sx = G.gw_solve(stage, dmols[i], grid, states(mols[i]), prec=gw.GW_FP64)
+        t_f64 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        G.gw_solve(stage, dmols[i], grid, states(mols[i]), prec=prec)
+        t_mix = time.perf_counter() - t0
+        r = res[timed_idx.index(i)]
+        f64.append(dict(atoms=int(jobs[i][1]), fp64_s=t_f64, mixed_s=t_mix,
+                        err_meV=float(np.abs(e - r["e_qp"]).max() * HA_MEV),
+                        same_branch=bool(np.array_equal(st, r["status"]))))
 
-    def pct(x, q):
-        return float(np.percentile(np.asarray(x), q))
+    # per-kernel times: the timed jobs once more on one stream, CUDA events around every
+    # launch (concurrent jobs would stretch one another's intervals)
+    stage.profile(True, None)
+    t0 = time.perf_counter()
+    for i in timed_idx:
+        G.gw_solve(stage, dmols[i], grid, states(mols[i]), prec=prec)
+    single_s = time.perf_counter() - t0
+    kt = {k: stage.profile_get(k) for k in KERNELS}
+    kt = {k: v for k, v in kt.items() if v[1] > 0}
+    stage.profile(False)
+
+    # roofline of the kernel with the largest share of the timed jobs' kernel time
+    timed_mols = [mols[i] for i in timed_idx]
+    total_ms = sum(v[0] for v in kt.values())
+    table = per_kernel_roofline(kt, timed_mols, grid, total_ms)
+    dom = max(kt.items(), key=lambda kv: kv[1][0])[0]
+    flops, meta = workload_model(dom, timed_mols, grid, kernel_model)
+    k_ms, k_n = kt[dom]
+    roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+            "traffic": NCU_TRAFFIC.get(dom), "avg_launch_ms": k_ms / k_n, "launches": k_n, "share": k_ms / total_ms,
+            "selected_by": "largest share of the kernel time of the timed jobs",
+            "measured_in": "single-stream pass over the timed jobs, CUDA events around every launch on the "
+                           "context stream"}
+    if flops:
+        bound, peak = meta
+        roof.update({"bound": bound, "achieved": (flops / k_n) / (k_ms / k_n / 1e3) / 1e12, "peak": peak,
+                     "frac": flops / (k_ms / 1e3) / 1e12 / peak, "flops_per_launch": flops / k_n,
+                     "peak_source": (PEAK_TF32_SOURCE + " = dense TF32 tensor peak, / 3: 3xTF32 takes three TF32 "
+                                     "products per binary32 product" if bound == "tensor" else
+                                     "128 binary32 FMA/clk/SM x 152 SMs x 2070 MHz (recipe unit counts and maximum "
+                                     "clock)")})
+
+    # context: the 60-atom cage (largest single molecule) and the 12-atom ring, single stream
+    extra = {}
+    for name, cfg in (("ring12", 2), ("cage60", 3)):
+        m, g_ = synth.make_config(cfg)
+        dm = G.gw_mol_upload(stage, m)
+        if cfg == 2:                                               # warm (the cage is too long to repeat)
+            G.gw_solve(stage, dm, g_, states(m), prec=prec)
+        t0 = time.perf_counter()
+        G.gw_solve(stage, dm, g_, states(m), prec=prec)
+        extra[name] = {"mixed_s_per_solve": time.perf_counter() - t0, "n_sub": int(m.n_sub),
+                       "n_omega": int(g_.n_omega)}
+        dm.free()
 
     out = {
-        "metric": METRIC, "value": batched["value"], "unit": "solves/s", "n_gpus": world, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": batched["t_ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prec == gw.GW_FP64 else "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": a.precision, "concurrency": W, "solves_per_step": W,
-                   "batching": f"{W} solves in flight per step, one context and CUDA stream each, inputs resident",
-                   "l2": "no flush: per-step working set (chi0 + factors, >= 1.5 GB per solve) exceeds the 129 MB L2",
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * span / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "mixed (binary32 contractions, Cauchy sum, factorisation, "
+                                                      "forms; binary64 setup, Sigma and QP root)",
+                   "jobs_per_step": 1, "timed_jobs_atoms": [int(jobs[i][1]) for i in timed_idx],
+                   "workers": a.workers, "hbm_budget_gb": BUDGET / (1 << 30),
+                   "timing": "wall clock from the first timed arrival to the last result, device synchronised",
+                   "l2": "no flush: every job's working set (chi0 + factors, >= 0.5 GB) exceeds the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "latency_ms": {"p50": pct(batched["lat"], 50), "p99": pct(batched["lat"], 99)},
-        "single_stream": {"value": single["value"], "unit": "solves/s", "ms_per_solve": single_ms,
-                          "launches_per_solve": single["launches"] / a.steps,
-                          "latency_ms": {"p50": pct(single["lat"], 50), "p99": pct(single["lat"], 99)}},
+        "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99),
+                       "queue_p50": _pct([r["queue_ms"] for r in res], 50),
+                       "run_p50": _pct([r["run_ms"] for r in res], 50)},
         "roofline": roof,
-        "kernels": kernels,
         "kernel_roofline": {"hbm_peak_gbs": PEAK_HBM_GBS, "hbm_peak_source": PEAK_HBM_SOURCE,
-                            "note": "algorithmic flops and bytes per step over the single-stream kernel time; "
-                                    "compute peaks as in roofline.peak_source", "kernels": kernel_roofline},
-        "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": int(W * h2d),
-                "d2h_bytes_per_step": int(W * d2h),
-                "path": f"gw_server with {W} workers, jobs submitted from pinned host arrays, wall clock",
-                "latency_ms": {"p50": pct(e2e_lat, 50), "p99": pct(e2e_lat, 99)}},
-        "gpu_launches": int(batched["launches"]),
-        "clocks": batched["clocks"],
+                            "note": "algorithmic flops and bytes of the timed jobs over the summed CUDA-event "
+                                    "kernel time of a single-stream pass", "kernels": table},
+        "single_stream": {"value": K / single_s, "unit": "solves/s", "s": single_s},
+        "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": int(h2d / K), "d2h_bytes_per_step": d2h,
+                "path": f"gw_server_submit from pinned host arrays, {a.workers} workers, same arrivals",
+                "latency_ms": {"p50": _pct([r["total_ms"] for r in res_e2e], 50),
+                               "p99": _pct([r["total_ms"] for r in res_e2e], 99)},
+                "same_results_as_resident": same_e2e},
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "fp64_plain": {"jobs": f64, "value": len(f64) / sum(x["fp64_s"] for x in f64), "unit": "solves/s",
+                       "mixed_value_same_jobs": len(f64) / sum(x["mixed_s"] for x in f64),
+                       "qp_max_abs_err_meV": max(x["err_meV"] for x in f64),
+                       "same_root_branch": all(x["same_branch"] for x in f64),
+                       "path": "gw_solve single stream, closed loop, molecules resident"},
+        "single_molecule": extra,
     }
-    if ref64 is not None:
-        err = float(np.abs(np.asarray(single["e"]) - np.asarray(ref64["e"])).max()) * 27211.386245988
-        out["fp64_plain"] = {"value": ref64["value"], "unit": "solves/s", "ms_per_step": ref64["t_ms"] / len(ref64["lat"]),
-                             "latency_ms": {"p50": pct(ref64["lat"], 50), "p99": pct(ref64["lat"], 99)},
-                             "qp_max_abs_err_meV": err,
-                             "same_root_branch": bool(np.array_equal(single["st"], ref64["st"]))}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        t_or = oracle_time(mol, grid, sample=8)
-        out["cpu_baseline"] = {"value": 1.0 / t_or, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                               "sample": "FP64 oracle solve of the same workload: Cauchy sum, screening and forms on "
-                                         "every 8th frequency scaled by 8, all other steps in full (NumPy/LAPACK, "
-                                         "all host cores)"}
+        m0, g0, job0 = _smallest_job()
+        est, real = oracle_time(m0, g0, sample=ORACLE_SAMPLE)
+        out["cpu_baseline"] = {"value": 1.0 / est, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": f"FP64 oracle on the trace's smallest job ({job0[1]} atoms), frequency-"
+                                         f"dependent steps on every {ORACLE_SAMPLE}th frequency scaled by "
+                                         f"{ORACLE_SAMPLE} ({real:.1f} s measured)"}
     if rank == 0:
         print(json.dumps(out))
-    for m_ in mols:
+    for m_ in dmols:
         m_.free()
-    for c in ctxs:
-        c.close()
+    stage.close()
     reps.close()
 
 

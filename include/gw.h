@@ -68,6 +68,7 @@ typedef int gw_status;
 #define GW_ERR_ADMISSION      -8   /* request exceeds the context's HBM budget */
 #define GW_ERR_TIMEOUT        -9   /* a bounded device wait gave up */
 #define GW_ERR_CUDA          -10   /* CUDA runtime error (message has details) */
+#define GW_ERR_CANCELLED     -11   /* serving: the server was destroyed before the job started */
 
 typedef enum {
     GW_FP64 = 0,      /* every step in binary64 */
@@ -202,6 +203,16 @@ gw_status gw_sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n_sta
 gw_status gw_qp_solve(gw_ctx* ctx, const gw_sigma* sigma, const double* vxc,
                       double* e_qp, double* z_factor, int* root_status);
 
+/* a0-a8 on a device-resident molecule (which may have been uploaded through
+ * another context of the same device; it is only read): the steps of
+ * gw_build_chi0, gw_screen_W, gw_sigma_diag and gw_qp_solve (Eqs.
+ * chi_by_spectra, chi_RPA, spectral_3, Cauchy1, instantaneous and the QP
+ * rule of gw_qp_solve), QP results to host arrays [n_states], intermediate
+ * device state released.  sigma_x: host [n_states] or NULL. */
+gw_status gw_solve(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, gw_precision prec,
+                   const int* states, int n_states, const double* vxc, double* e_qp, double* z_factor,
+                   int* root_status, double* sigma_x);
+
 /* End to end through host memory: upload, a0-a8, QP results to host,
  * device state released.  sigma_x: host [n_states] or NULL. */
 gw_status gw_solve_host(gw_ctx* ctx, const gw_molecule_desc* desc, const gw_grid* grid,
@@ -220,12 +231,27 @@ gw_status gw_solve_host(gw_ctx* ctx, const gw_molecule_desc* desc, const gw_grid
  * (fixed-order reductions, no cross-job state). */
 typedef struct gw_server gw_server;
 gw_status gw_server_create(gw_server** out, int device, int n_workers, size_t hbm_budget_bytes);
-/* Stops the workers after their running jobs; queued jobs are dropped. */
+/* Stops the workers after their running jobs; jobs still queued end with
+ * GW_ERR_CANCELLED.  Must not run concurrently with gw_server_wait or
+ * gw_server_submit on the same server (collect the results first). */
 void      gw_server_destroy(gw_server* s);
 /* GW_ERR_ADMISSION if the job alone exceeds the budget. */
 gw_status gw_server_submit(gw_server* s, const gw_molecule_desc* desc, const gw_grid* grid,
                            gw_precision prec, const int* states, int n_states, const double* vxc,
                            long long* job_id);
+/* As gw_server_submit for a device-resident molecule (gw_mol_upload on any
+ * context of the server's device): no host copy, no upload in the job.  The
+ * caller keeps the molecule alive until the job's gw_server_wait returns. */
+gw_status gw_server_submit_resident(gw_server* s, const gw_mol* mol, const gw_grid* grid, gw_precision prec,
+                                    const int* states, int n_states, const double* vxc, long long* job_id);
+/* This library's kernel launches over all worker contexts so far. */
+long long gw_server_launch_count(const gw_server* s);
+/* gw_ctx_profile / gw_ctx_profile_get over all worker contexts (times and
+ * launches summed; each kernel timed on its worker's stream, so concurrent
+ * jobs stretch one another's intervals).  Call while no job is queued or
+ * running. */
+gw_status gw_server_profile(gw_server* s, int enable, const char* kernel_name);
+gw_status gw_server_profile_get(gw_server* s, const char* kernel_name, double* total_ms, long long* launches);
 /* 0 queued, 1 running, 2 done; a negative gw_status if the job failed. */
 int       gw_server_poll(gw_server* s, long long job_id);
 /* Waits up to timeout_ms (< 0: no limit; GW_ERR_TIMEOUT when it runs out),
@@ -255,8 +281,10 @@ size_t    gw_server_job_bytes(const gw_molecule_desc* desc, const gw_grid* grid,
  * the library until the process exits); larger requests return
  * GW_ERR_INVALID_ARG.  Allocates no device or host memory.  All calls on
  * a device share the table: calls that overlap on the GPU race.  The first
- * call on a device resolves the table's address with that device current;
- * make it before any stream capture.  Launch errors return GW_ERR_CUDA. */
+ * call in a CUDA context (normally the device's primary context) resolves
+ * the table's address with that context current and caches it per context
+ * (after a device reset the next call resolves it again); make that first
+ * call before any stream capture.  Launch errors return GW_ERR_CUDA. */
 gw_status gw_sigma_c_static(const double* sigma, int n_states, int n_sig, int j0, int n_omega,
                             double d_omega, double eta, double* sigc, void* stream, char* err,
                             size_t err_len);

@@ -395,7 +395,9 @@ static void check_grid(const gw_grid* g) {
 }
 
 static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, gw_precision prec) {
-    REQUIRE(mol && mol->ctx == ctx, "molecule belongs to another context");
+    // a molecule uploaded through another context of the same device may be shared
+    // (read only; its upload was synchronised): serving keeps molecules resident
+    REQUIRE(mol && mol->ctx && mol->ctx->device == ctx->device, "molecule belongs to another device");
     check_grid(grid);
     REQUIRE(prec == GW_FP64 || prec == GW_MIXED, "unknown precision");
     const int n_occ = mol->n_occ, n_orb = mol->n_orb, n_virt = n_orb - n_occ;
@@ -807,6 +809,30 @@ extern "C" gw_status gw_qp_solve(gw_ctx* ctx, const gw_sigma* sigma, const doubl
     API_BEGIN(ctx)
     CUDA_CHECK(cudaSetDevice(ctx->device));
     qp_solve(ctx, sigma, vxc, e_qp, z_factor, root_status);
+    API_END
+}
+
+extern "C" gw_status gw_solve(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, gw_precision prec,
+                              const int* states, int n_states, const double* vxc, double* e_qp, double* z_factor,
+                              int* root_status, double* sigma_x) {
+    if (!ctx) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    gw_chi0* c = nullptr; gw_W* w = nullptr; gw_sigma* s = nullptr;
+    try {
+        c = build_chi0(ctx, mol, grid, prec);
+        w = screen_W(ctx, c);
+        s = sigma_diag(ctx, w, states, n_states);
+        qp_solve(ctx, s, vxc, e_qp, z_factor, root_status);
+        if (sigma_x) {
+            download(ctx, sigma_x, s->sx, n_states);
+            CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        }
+    } catch (...) {
+        sigma_release(s); W_release(w); chi0_release(c);
+        throw;
+    }
+    sigma_release(s); W_release(w); chi0_release(c);
     API_END
 }
 

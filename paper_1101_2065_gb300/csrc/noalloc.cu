@@ -13,13 +13,19 @@
 // there until the process exits.  All calls on a device share it, so calls
 // whose kernels overlap on the GPU (two host threads, or two streams) race
 // on it; serialise them.  Each call rewrites every table entry it reads, so
-// nothing left by an earlier call is used.  The first call on a device looks
-// up the array's device address (cudaGetSymbolAddress) with that device
-// current and caches it; make that first call before any stream capture.
+// nothing left by an earlier call is used.  The first call in a CUDA context
+// (normally the device's primary context) looks up the array's device
+// address (cudaGetSymbolAddress) with that context current and caches it
+// per context, so a device reset or another context on the same device
+// gets its own lookup; make that first call before any stream capture.
+#include <cuda.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "internal.h"
 
@@ -29,9 +35,25 @@ namespace {
 constexpr long long kStaticTableMax = 1LL << 16;
 static __device__ __align__(256) double2 g_sigc_table[kStaticTableMax];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-double2* g_table_ptr[kMaxDevices] = {nullptr};
+std::vector<std::pair<CUcontext, double2*>> g_table_ptr;   // address of the table per CUDA context
+
+// The calling thread's current CUDA context (driver entry point resolved
+// through the runtime, so the library needs no link to libcuda).
+CUcontext current_context() {
+    typedef CUresult (*GetCurrent)(CUcontext*);
+    static GetCurrent fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn = reinterpret_cast<GetCurrent>(p);
+    }
+    CUcontext c = nullptr;
+    return fn(&c) == CUDA_SUCCESS ? c : nullptr;
+}
 
 __global__ void k_static_cauchy_table(double2* __restrict__ K, long long dmin, long long nd, double dw, double eta) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -89,24 +111,33 @@ extern "C" gw_status gw_sigma_c_static(const double* sigma, int n_states, int n_
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
         set_msg(err, err_len, "gw_sigma_c_static: no usable current device");
         return GW_ERR_CUDA;
     }
     double2* table = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mutex);
-        if (!g_table_ptr[dev]) {
+        CUcontext ctx = current_context();
+        for (auto& kv : g_table_ptr)
+            if (ctx && kv.first == ctx) table = kv.second;
+        if (!table) {
             void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_sigc_table);
+            e = cudaGetSymbolAddress(&p, g_sigc_table);     // also makes the runtime's context current
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 set_msg(err, err_len, cudaGetErrorString(e));
                 return GW_ERR_CUDA;
             }
-            g_table_ptr[dev] = static_cast<double2*>(p);
+            table = static_cast<double2*>(p);
+            ctx = current_context();
+            if (!ctx) {
+                set_msg(err, err_len, "gw_sigma_c_static: no current CUDA context");
+                return GW_ERR_CUDA;
+            }
+            g_table_ptr.emplace_back(ctx, table);
         }
-        table = g_table_ptr[dev];
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // d = k - j for k in [-(N-1), N-1] and j in [j0, j0 + n_sig - 1]

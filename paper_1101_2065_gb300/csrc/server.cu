@@ -28,6 +28,7 @@ struct Job {
     std::vector<double> eps, X, vertex, v, vxc;
     std::vector<long long> vertex_off;
     size_t vertex_len = 0;
+    const gw_mol* dmol = nullptr;   // device-resident molecule (borrowed), or null: the copies above
     bool has_vxc = false;
     gw_grid grid{};
     gw_precision prec = GW_FP64;
@@ -83,6 +84,14 @@ static size_t job_bytes(const Job& j) {
 }
 
 static void run_job(gw_ctx* ctx, Job& j) {
+    const int nst = (int)j.states.size();
+    if (j.dmol) {
+        j.e_qp.assign(nst, 0.0); j.z.assign(nst, 0.0); j.sx.assign(nst, 0.0); j.root.assign(nst, 0);
+        j.status = gw_solve(ctx, j.dmol, &j.grid, j.prec, j.states.data(), nst, j.has_vxc ? j.vxc.data() : nullptr,
+                            j.e_qp.data(), j.z.data(), j.root.data(), j.sx.data());
+        if (j.status != GW_OK) j.err = gw_last_error(ctx);
+        return;
+    }
     gw_molecule_desc d{};
     d.n_atoms = j.n_atoms; d.n_orb = j.n_orb; d.n_occ = j.n_occ; d.n_prod = j.n_prod; d.n_sub = j.n_sub;
     d.atom_norb = j.atom_norb.data(); d.atom_nprod = j.atom_nprod.data();
@@ -152,9 +161,17 @@ extern "C" void gw_server_destroy(gw_server* s) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
+        // jobs that never started end as cancelled (a wait on them returns at once)
+        for (auto& j : s->queue) {
+            j->state = 2;
+            j->status = GW_ERR_CANCELLED;
+            j->err = "server destroyed before the job started";
+            j->t_start = j->t_end = Clock::now();
+        }
         s->queue.clear();
     }
     s->cv_work.notify_all();
+    s->cv_done.notify_all();
     for (auto& t : s->workers) t.join();
     for (auto c : s->ctxs) gw_ctx_destroy(c);
     delete s;
@@ -198,6 +215,66 @@ extern "C" gw_status gw_server_submit(gw_server* s, const gw_molecule_desc* d, c
     }
     s->cv_work.notify_all();
     return GW_OK;
+}
+
+extern "C" gw_status gw_server_submit_resident(gw_server* s, const gw_mol* mol, const gw_grid* grid,
+                                               gw_precision prec, const int* states, int n_states,
+                                               const double* vxc, long long* job_id) {
+    if (!s || !mol || !grid || !states || n_states <= 0 || !job_id) return GW_ERR_INVALID_ARG;
+    auto j = std::make_shared<Job>();
+    j->dmol = mol;
+    j->n_atoms = mol->n_atoms; j->n_orb = mol->n_orb; j->n_occ = mol->n_occ; j->n_prod = mol->n_prod;
+    j->n_sub = mol->n_sub;
+    j->eps = mol->h_eps;                     // the energy span sizes the admission estimate
+    j->vertex_len = mol->vertex_len;
+    j->states.assign(states, states + n_states);
+    if (vxc) { j->vxc.assign(vxc, vxc + n_states); j->has_vxc = true; }
+    j->grid = *grid;
+    j->prec = prec;
+    j->bytes = job_bytes(*j);
+    if (j->bytes > s->budget) return GW_ERR_ADMISSION;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        j->id = s->next_id++;
+        j->t_submit = Clock::now();
+        s->jobs[j->id] = j;
+        s->queue.push_back(j);
+        *job_id = j->id;
+    }
+    s->cv_work.notify_all();
+    return GW_OK;
+}
+
+extern "C" gw_status gw_server_profile(gw_server* s, int enable, const char* kernel_name) {
+    if (!s) return GW_ERR_INVALID_ARG;
+    for (auto c : s->ctxs) {
+        gw_status st = gw_ctx_profile(c, enable, kernel_name);
+        if (st != GW_OK) return st;
+    }
+    return GW_OK;
+}
+
+extern "C" gw_status gw_server_profile_get(gw_server* s, const char* kernel_name, double* total_ms,
+                                           long long* launches) {
+    if (!s || !kernel_name || !total_ms || !launches) return GW_ERR_INVALID_ARG;
+    *total_ms = 0.0;
+    *launches = 0;
+    for (auto c : s->ctxs) {
+        double ms = 0.0;
+        long long n = 0;
+        gw_status st = gw_ctx_profile_get(c, kernel_name, &ms, &n);
+        if (st != GW_OK) return st;
+        *total_ms += ms;
+        *launches += n;
+    }
+    return GW_OK;
+}
+
+extern "C" long long gw_server_launch_count(const gw_server* s) {
+    if (!s) return 0;
+    long long n = 0;
+    for (auto c : s->ctxs) n += gw_ctx_launch_count(c);
+    return n;
 }
 
 extern "C" int gw_server_poll(gw_server* s, long long job_id) {

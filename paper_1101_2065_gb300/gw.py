@@ -19,7 +19,7 @@ GW_OK = 0
 ERRORS = {
     -1: "GW_ERR_INVALID_ARG", -2: "GW_ERR_NOT_SPD", -3: "GW_ERR_GRID", -4: "GW_ERR_RANK",
     -5: "GW_ERR_SINGULAR", -6: "GW_ERR_NO_CONVERGENCE", -7: "GW_ERR_OOM", -8: "GW_ERR_ADMISSION",
-    -9: "GW_ERR_TIMEOUT", -10: "GW_ERR_CUDA",
+    -9: "GW_ERR_TIMEOUT", -10: "GW_ERR_CUDA", -11: "GW_ERR_CANCELLED",
 }
 GW_FP64 = 0
 GW_MIXED = 1
@@ -112,6 +112,11 @@ def load(path: str | None = None):
         "gw_server_poll": ([P, C.c_longlong], I),
         "gw_server_wait": ([P, C.c_longlong, I, P, P, P, P, P, C.c_char_p, C.c_size_t], I),
         "gw_server_job_bytes": ([C.POINTER(MoleculeDesc), C.POINTER(Grid), I, I], C.c_size_t),
+        "gw_server_submit_resident": ([P, P, C.POINTER(Grid), I, P, I, P, C.POINTER(C.c_longlong)], I),
+        "gw_server_launch_count": ([P], C.c_longlong),
+        "gw_server_profile": ([P, I, C.c_char_p], I),
+        "gw_server_profile_get": ([P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], I),
+        "gw_solve": ([P, P, C.POINTER(Grid), I, P, I, P, P, P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -393,6 +398,19 @@ def gw_qp_solve(ctx, sigma, vxc=None):
     return e, z, st
 
 
+def gw_solve(ctx, mol, grid, states, prec=GW_FP64, vxc=None):
+    """One GW solve of a device-resident molecule (a Mol from gw_mol_upload on
+    any context of the device) to host results."""
+    g = make_grid(grid)
+    st = np.ascontiguousarray(states, np.int32)
+    n = st.size
+    e = np.zeros(n); z = np.zeros(n); rs = np.zeros(n, np.int32); sx = np.zeros(n)
+    v = None if vxc is None else np.ascontiguousarray(np.broadcast_to(np.asarray(vxc, float), (n,)))
+    _check(ctx, load().gw_solve(ctx.handle, mol.handle, C.byref(g), int(prec), _ptr(st), n, _ptr(v),
+                                _ptr(e), _ptr(z), _ptr(rs), _ptr(sx)))
+    return e, z, rs, sx
+
+
 def gw_solve_host(ctx, mol, grid, states, prec=GW_FP64, vxc=None, desc=None):
     """One GW solve from host arrays to host results (upload included)."""
     d = desc if desc is not None else _Desc(mol)
@@ -429,6 +447,37 @@ class Server:
         if code != GW_OK:
             raise GWError(code, "gw_server_submit failed")
         return jid.value, st.size
+
+    def submit_resident(self, mol, grid, states=None, prec=GW_FP64, vxc=None):
+        """Submit a device-resident molecule (Mol); keep it alive until wait() returns."""
+        if states is None:
+            states = [mol.n_occ - 1, mol.n_occ]
+        g = make_grid(grid)
+        st = np.ascontiguousarray(states, np.int32)
+        v = None if vxc is None else np.ascontiguousarray(np.broadcast_to(np.asarray(vxc, float), (st.size,)))
+        jid = C.c_longlong()
+        code = load().gw_server_submit_resident(self.handle, mol.handle, C.byref(g), int(prec), _ptr(st), st.size,
+                                                _ptr(v), C.byref(jid))
+        if code != GW_OK:
+            raise GWError(code, "gw_server_submit_resident failed")
+        return jid.value, st.size
+
+    @property
+    def launch_count(self):
+        return load().gw_server_launch_count(self.handle)
+
+    def profile(self, enable=True, kernel=None):
+        """Per-kernel CUDA-event timing on every worker stream (call while idle)."""
+        code = load().gw_server_profile(self.handle, int(enable), kernel.encode() if kernel else None)
+        if code != GW_OK:
+            raise GWError(code, "gw_server_profile failed")
+
+    def profile_get(self, kernel):
+        ms, n = C.c_double(), C.c_longlong()
+        code = load().gw_server_profile_get(self.handle, kernel.encode(), C.byref(ms), C.byref(n))
+        if code != GW_OK:
+            raise GWError(code, "gw_server_profile_get failed")
+        return ms.value, n.value
 
     def poll(self, job):
         return load().gw_server_poll(self.handle, job[0])

@@ -1,6 +1,7 @@
-"""Host-side logic of bench.py (no GPU): the algorithmic work and traffic
-models behind the roofline fractions, the per-kernel roofline table, and
-the clock sampler's parsing and timed-window filter."""
+"""Host-side logic of bench.py (no GPU): the serving trace it replays, the
+forms-kernel dispatch it mirrors, the algorithmic work and traffic models
+behind the roofline fractions, the per-kernel roofline table, and the clock
+sampler's parsing and timed-window filter."""
 import datetime
 import math
 import os
@@ -18,51 +19,88 @@ def ring():
     return synth.make_config(2)
 
 
+def test_trace_prefix_does_not_depend_on_its_length():
+    a5, j5, g5 = bench.trace(5)
+    a30, j30, g30 = bench.trace(30)
+    assert j5 == j30[:5] and a5 == a30[:5]
+    assert g5.n_omega == g30.n_omega == 1024
+    assert all(bench.LO <= j[1] <= bench.HI for j in j30)
+    assert all(b > a for a, b in zip(a30, a30[1:]))            # Poisson arrivals, increasing
+
+
+def test_forms_dispatch():
+    assert bench.forms_kernel(300, 216) == "k_forms32_tm"
+    assert bench.forms_kernel(384, 500) == "k_forms32_tm"
+    assert bench.forms_kernel(400, 520) == "k_forms32"          # 48 right-hand sides of Y still fit
+    assert bench.forms_kernel(600, 780) == "batched"
+
+
 def test_forms_model_matches_the_forward_substitution_count(ring):
     mol, grid = ring
     n, N, R = mol.n_sub, grid.n_omega, 2 * mol.n_orb
     assert (n, N, R) == (300, 1024, 216)
-    flops, bound, peak = bench.kernel_model("k_forms32_tm", mol, grid, 540)
+    flops, bound, peak = bench.kernel_model("k_forms32_tm", mol, grid)
     # (N - 1) frequencies x R right-hand sides x n(n-1)/2 complex multiply-adds x 8 flops
     assert flops == pytest.approx(1023 * 216 * 300 * 299 / 2 * 8)
     assert bound == "tensor"
     assert peak == pytest.approx(bench.PEAK_TF32_TFLOPS / 3)
-    simt, sbound, speak = bench.kernel_model("k_forms32", mol, grid, 540)
-    assert simt == flops and sbound == "alu" and speak == pytest.approx(bench.PEAK_FP32_TFLOPS)
+    # the ring never takes the resident FMA or the batched forms
+    assert bench.kernel_model("k_forms32", mol, grid)[0] is None
+    assert bench.kernel_model("k_forms32_update", mol, grid)[0] is None
+
+
+def test_batched_forms_model_splits_diagonal_and_update():
+    from synth import molecules as sm
+    mol = sm._uniform_molecule("chain", 20, 1)          # n = 600: Y in HBM
+    grid = synth.Grid(1024)
+    n, R = mol.n_sub, 2 * mol.n_orb
+    up, b1, _ = bench.kernel_model("k_forms32_update", mol, grid)
+    dg, b2, _ = bench.kernel_model("k_forms32_diag", mol, grid)
+    assert b1 == b2 == "alu"
+    diag = 1023 * 8.0 * R * sum(kb * kb for kb, _ in bench._panels(n, 32))
+    fwd = 1023 * 8.0 * R * n * (n - 1) / 2
+    assert dg == pytest.approx(diag) and up == pytest.approx(fwd - diag / 2)
 
 
 def test_trailing_update_models_split_at_128_rows(ring):
     mol, grid = ring
-    tc, _, _ = bench.kernel_model("k_ldlt32_syrk_tc", mol, grid, 540)
-    fma, _, _ = bench.kernel_model("k_ldlt32_syrk", mol, grid, 540)
-    fp64, _, _ = bench.kernel_model("k_ldlt_syrk", mol, grid, 540)
-    # binary32: the two kernels share the panels (m >= 128 on the tensor cores)
+    tc, _, _ = bench.kernel_model("k_ldlt32_syrk_tc", mol, grid)
+    fma, _, _ = bench.kernel_model("k_ldlt32_syrk", mol, grid)
     full = 1024 * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in bench._panels(300, 32) if m > 0)
     assert tc + fma == pytest.approx(full)
     assert tc > 0 and fma > 0
-    # binary64: NB = 16 panels, all on one kernel
-    full64 = 1024 * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in bench._panels(300, 16) if m > 0)
-    assert fp64 == pytest.approx(full64)
 
 
-def test_traffic_models(ring):
+def test_cauchy_and_traffic_models(ring):
     mol, grid = ring
     tri = 300 * 301 // 2
+    band = bench.band_bins(mol, grid)
+    assert 150 < band < 250                       # transitions span ~1.2 Ha at d_omega = 1/150 Ha
+    kk, bound, _ = bench.kernel_model("k_chi0_kk_fma", mol, grid)
+    assert kk == pytest.approx(4.0 * 1024 * band * tri) and bound == "alu"
     assert bench.kernel_bytes("k_ldlt32_init", mol, grid) == pytest.approx(2 * 1024 * tri * 8)
-    assert bench.kernel_bytes("k_ldlt_init", mol, grid) == pytest.approx(2 * 1024 * tri * 16)
-    forms = bench.kernel_bytes("k_forms32_tm", mol, grid)
-    assert forms == pytest.approx(1023 * (tri * 8 + 10 * 32 * 32 * 8))
-    fft = bench.kernel_bytes("k_chi0_fft32", mol, grid)
-    assert fft > 1024 * tri * 8                      # chi0 written once, plus the spectral weights
+    assert bench.kernel_bytes("k_chi0_kk_fma", mol, grid) == pytest.approx(band * tri * 4 + 1024 * tri * 8)
+    assert bench.kernel_bytes("k_forms32_tm", mol, grid) == pytest.approx(1023 * (tri * 8 + 10 * 32 * 32 * 8))
     assert bench.kernel_bytes("k_bisect", mol, grid) is None
+
+
+def test_workload_model_sums_only_where_the_kernel_runs(ring):
+    from synth import molecules as sm
+    mol, grid = ring
+    big = sm._uniform_molecule("chain", 20, 1)
+    g = synth.Grid(1024)
+    tot, meta = bench.workload_model("k_forms32_update", [mol, big], g, bench.kernel_model)
+    assert tot == pytest.approx(bench.kernel_model("k_forms32_update", big, g)[0])
+    assert meta[0] == "alu"
+    none, _ = bench.workload_model("k_forms32_update", [mol], g, bench.kernel_model)
+    assert none is None
 
 
 def test_per_kernel_roofline_table(ring):
     mol, grid = ring
-    steps = 2
-    kt = {"k_forms32_tm": (2 * 2.2, 2), "k_ldlt32_init": (2 * 0.14, 2), "k_qp": (2 * 0.001, 2)}
-    table = bench.per_kernel_roofline(kt, steps, mol, grid, 540, single_ms=10.0)
-    assert set(table) == {"k_forms32_tm", "k_ldlt32_init"}      # k_qp is below 1 % of the step
+    kt = {"k_forms32_tm": (2.2, 1), "k_ldlt32_init": (0.14, 1), "k_qp": (0.001, 1)}
+    table = bench.per_kernel_roofline(kt, [mol], grid, total_ms=10.0)
+    assert set(table) == {"k_forms32_tm", "k_ldlt32_init"}      # k_qp is below 1 % of the kernel time
     f = table["k_forms32_tm"]
     assert f["tflops"] == pytest.approx(1023 * 216 * 300 * 299 / 2 * 8 / 2.2e-3 / 1e12)
     assert f["compute_frac"] == pytest.approx(f["tflops"] / (bench.PEAK_TF32_TFLOPS / 3))

@@ -70,3 +70,44 @@ def test_admission_budget(gwlib):
     finally:
         srv.close()
     assert all(np.array_equal(res[0]["e_qp"], r["e_qp"]) for r in res)
+
+
+def test_resident_submission_equals_host_submission(gwlib, ctx):
+    """gw_server_submit_resident (molecule uploaded once through another
+    context of the device) gives the same results as gw_server_submit from
+    host arrays and as gw_solve on the uploading context."""
+    grid = synth.Grid(256)
+    mols = _mols()[:3]
+    dm = [gwlib.gw_mol_upload(ctx, m) for m in mols]
+    srv = gwlib.Server(0, n_workers=2)
+    try:
+        l0 = srv.launch_count
+        res = [srv.wait(j) for j in [srv.submit_resident(d, grid, prec=gwlib.GW_MIXED) for d in dm]]
+        assert srv.launch_count > l0
+        host = [srv.wait(j) for j in [srv.submit(m, grid, prec=gwlib.GW_MIXED) for m in mols]]
+    finally:
+        srv.close()
+    for d, m, a, b in zip(dm, mols, res, host):
+        for k in ("e_qp", "z", "status", "sigma_x"):
+            assert np.array_equal(a[k], b[k]), k
+        e, z, st, sx = gwlib.gw_solve(ctx, d, grid, [m.n_occ - 1, m.n_occ], gwlib.GW_MIXED)
+        assert np.array_equal(e, a["e_qp"]) and np.array_equal(st, a["status"])
+        d.free()
+
+
+def test_destroy_cancels_queued_jobs(gwlib):
+    """Destroying a server with jobs still queued returns once the running
+    job ends (the queued ones are cancelled, not run)."""
+    import time
+    grid = synth.Grid(256)
+    m = _mols()[5]
+    srv = gwlib.Server(0, n_workers=1)
+    t0 = time.perf_counter()
+    one = srv.wait(srv.submit(m, grid, prec=gwlib.GW_MIXED))["run_ms"] / 1e3
+    jobs = [srv.submit(m, grid, prec=gwlib.GW_MIXED) for _ in range(12)]
+    t1 = time.perf_counter()
+    srv.close()
+    t2 = time.perf_counter()
+    assert len(jobs) == 12
+    # at most the job running at destruction (plus one picked up meanwhile) completes
+    assert t2 - t1 < 3 * one + 2.0, (t2 - t1, one)

@@ -52,6 +52,38 @@ def test_static_sigma_c_matches_pipeline_twice(gwlib, ctx):
         assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+def test_static_sigma_c_allocates_nothing(gwlib, ctx):
+    """Once warmed up, a call leaves the device's free memory unchanged: the
+    scratch is the library's fixed table, the buffers are the caller's."""
+    import torch
+    mol, grid = synth.make_config(1)
+    h, *_ = gwlib.solve(ctx, mol, grid, prec=gwlib.GW_MIXED)
+    try:
+        s = h["sigma"].copy()
+    finally:
+        for k in ("sigma", "W", "chi0", "mol"):
+            h[k].free()
+    lib = gwlib.load()
+    sig = torch.from_numpy(np.ascontiguousarray(s["sigma"])).to("cuda")
+    ns, n_sig = s["sigma"].shape
+    out = torch.empty((ns, 2 * grid.n_omega - 1, 2), dtype=torch.float64, device="cuda")
+    err = ctypes.create_string_buffer(256)
+    stream = torch.cuda.current_stream()
+
+    def call():
+        code = lib.gw_sigma_c_static(sig.data_ptr(), ns, n_sig, s["j0"], grid.n_omega, grid.d_omega, grid.eta,
+                                     out.data_ptr(), stream.cuda_stream, err, 256)
+        torch.cuda.synchronize()
+        assert code == 0, err.value
+
+    call()                                          # warm: table address resolved, kernels loaded
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        call()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
 def test_static_sigma_c_rejects_oversize(gwlib):
     lib = gwlib.load()
     err = ctypes.create_string_buffer(256)
