@@ -313,6 +313,10 @@ gw_status gw_chi0_copy(gw_ctx* ctx, const gw_chi0* chi0, int k0, int nk, double*
 gw_status gw_W_pole_freqs(const gw_W* W, int* freqs);
 /* min_i |d_i(k)| / max |1 - chi0_k| of the factorisation, [n_omega] */
 gw_status gw_W_copy_pivots(gw_ctx* ctx, const gw_W* W, double* ratio);
+/* chi0_k[m_i, n_i] for every k and the ne host index pairs (m_i, n_i):
+ * complex [n_omega][ne] */
+gw_status gw_chi0_copy_elements(gw_ctx* ctx, const gw_chi0* chi0, const int* m, const int* n, int ne,
+                                double* out);
 /* chi^RPA_k (compressed, complex [nf*n_sub*n_sub]) for the host list freqs */
 gw_status gw_W_copy_chi_rpa(gw_ctx* ctx, const gw_W* W, const int* freqs, int nf, double* out);
 /* W_k = v + Zup chi^RPA_k Zup^T (complex [nf*n_prod*n_prod]) for the host list freqs */

@@ -158,6 +158,22 @@ def deposit_spectral(U, pairs, n_omega):
     return A
 
 
+def spectral_weights_by_bin(U, pairs, bins):
+    """A_j for the bins j in `bins` (Eq. chi_by_spectra with the tent weights
+    of R2), each as one matrix product over the pairs that reach bin j:
+    A_j = U_j^T diag(w_j) U_j, w = 2(1-f) for pairs in bin j and 2f for pairs
+    in bin j-1.  The same sums as deposit_spectral, grouped by bin, for
+    molecules too large for one rank-1 update per pair.  [len(bins), n, n]."""
+    out = np.zeros((len(bins), U.shape[1], U.shape[1]))
+    for i, j in enumerate(bins):
+        lo = pairs["bin"] == j
+        hi = pairs["bin"] == j - 1
+        w = np.concatenate([2.0 * (1.0 - pairs["frac"][lo]), 2.0 * pairs["frac"][hi]])
+        Uj = np.concatenate([U[lo], U[hi]])
+        out[i] = Uj.T @ (w[:, None] * Uj)
+    return out
+
+
 # ------------------------------------------------------------------ a4
 def cauchy_matrix(n_omega, d_omega, eta):
     """K[k, j] = 1/(w_k - s_j + i eta) - 1/(w_k + s_j + i eta) (R3)."""
@@ -173,6 +189,33 @@ def chi0_cauchy(A, d_omega, eta):
     flat = A.reshape(N, -1)
     out = (K.real @ flat) + 1j * (K.imag @ flat)
     return out.reshape(A.shape)
+
+
+def chi0_elements(U, pairs, elems, n_omega, d_omega, eta):
+    """chi0_k[m, n] for k = 0..N-1 and the element list elems [(m, n), ...]
+    straight from the pairs: chi0_k = sum_p 2 u_p u_p^T t_p(k) with the
+    Cauchy kernel of the tent-weighted bins (Eq. chi_by_spectra, R2, R3),
+    t_p(k) = (1-f_p) K[k, j_p] + f_p K[k, j_p + 1].  [N, len(elems)] complex."""
+    k = np.arange(n_omega)[:, None]
+
+    def kern(j):
+        return 1.0 / ((k - j[None, :]) * d_omega + 1j * eta) - 1.0 / ((k + j[None, :]) * d_omega + 1j * eta)
+
+    j = pairs["bin"].astype(np.int64)
+    f = pairs["frac"]
+    t = (1.0 - f)[None, :] * kern(j) + f[None, :] * kern(j + 1)         # [N, N_pair]
+    uu = np.stack([2.0 * U[:, m] * U[:, n] for m, n in elems], axis=1)  # [N_pair, n_elems]
+    return t @ uu
+
+
+def chi0_from_weights(A_band, bins, freqs, d_omega, eta):
+    """chi0_k for the frequencies freqs from the weights of the bins that carry
+    them (Eq. chi_by_spectra): sum_j A_j [1/(w_k - s_j + i eta) - 1/(w_k + s_j + i eta)]."""
+    k = np.asarray(freqs)[:, None]
+    j = np.asarray(bins)[None, :]
+    K = 1.0 / ((k - j) * d_omega + 1j * eta) - 1.0 / ((k + j) * d_omega + 1j * eta)
+    flat = A_band.reshape(len(bins), -1)
+    return ((K.real @ flat) + 1j * (K.imag @ flat)).reshape((len(freqs),) + A_band.shape[1:])
 
 
 # ------------------------------------------------------------------ a5

@@ -985,6 +985,47 @@ extern "C" gw_status gw_chi0_copy(gw_ctx* ctx, const gw_chi0* c, int k0, int nk,
     API_END
 }
 
+namespace {
+// out[k * ne + i] = chi0_k at packed element e[i], binary64 or binary32 storage
+__global__ void k_chi0_elements(const double2* __restrict__ c64, const float2* __restrict__ c32, long long pk, int N,
+                                const long long* __restrict__ e, int ne, double2* __restrict__ out) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)N * ne) return;
+    const int k = (int)(t / ne), i = (int)(t % ne);
+    const long long o = (long long)k * pk + e[i];
+    out[t] = c64 ? c64[o] : make_double2(c32[o].x, c32[o].y);
+}
+}  // namespace
+
+extern "C" gw_status gw_chi0_copy_elements(gw_ctx* ctx, const gw_chi0* c, const int* m, const int* n, int ne,
+                                           double* out) {
+    if (!ctx || !c || !out || ne <= 0 || !m || !n) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    std::vector<long long> he(ne);
+    for (int i = 0; i < ne; ++i) {
+        REQUIRE(m[i] >= 0 && m[i] < c->n_sub && n[i] >= 0 && n[i] < c->n_sub, "element index out of range");
+        const long long a = std::max(m[i], n[i]), b = std::min(m[i], n[i]);
+        he[i] = tri(a) + b;
+    }
+    const int N = c->grid.n_omega;
+    long long* de = nullptr;
+    double2* d = nullptr;
+    try {
+        de = upload(ctx, he.data(), he.size());
+        d = dalloc<double2>(ctx, (size_t)N * ne);
+        klaunch(ctx, "k_chi0_elements", k_chi0_elements, div_up((long long)N * ne, 256), 256, 0,
+                (const double2*)c->chi0, (const float2*)c->chi0_32, tri(c->n_sub), N, (const long long*)de, ne, d);
+        download(ctx, reinterpret_cast<double2*>(out), d, (size_t)N * ne);
+        ctx_finish(ctx, "gw_chi0_copy_elements");
+    } catch (...) {
+        ctx_free(ctx, de); ctx_free(ctx, d);
+        throw;
+    }
+    ctx_free(ctx, de); ctx_free(ctx, d);
+    API_END
+}
+
 extern "C" gw_status gw_W_copy_pivots(gw_ctx* ctx, const gw_W* W, double* ratio) {
     if (!ctx || !W || !ratio) return GW_ERR_INVALID_ARG;
     API_BEGIN(ctx)

@@ -77,6 +77,84 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, T alpha, con
     }
 }
 
+// C = alpha A^T B (+ beta C) in binary32 on the FMA units for A [K][M] and
+// B [K][N] row-major (the layout of U^T = Zup^T V^EF and q = Zup^T V^nk):
+// both operands stream K-major rows, so their tiles are copied to shared
+// memory without transposition.  128 x 128 output tile per CTA, K in steps
+// of 16 staged through two shared-memory buffers (the next step's values
+// are loaded into registers while the current one is multiplied), 8 x 8
+// outputs per thread in four 4 x 4 quadrants so that every shared-memory
+// read is a conflict-free 16-byte vector.  Every addition rounds to nearest.
+constexpr int SG_T = 128, SG_K = 16;
+
+__global__ void __launch_bounds__(256) k_sgemm_tn(int M, int N, int K, float alpha, const float* __restrict__ A,
+                                                  long long lda, const float* __restrict__ B, long long ldb,
+                                                  float beta, float* __restrict__ C, long long ldc) {
+    __shared__ __align__(16) float As[2][SG_K][SG_T];
+    __shared__ __align__(16) float Bs[2][SG_K][SG_T];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int m0 = blockIdx.y * SG_T, n0 = blockIdx.x * SG_T;
+    // loader: thread covers column lc of rows lr, lr + 2, ..., lr + 14 of the K step
+    const int lc = tid % SG_T, lr = tid / SG_T;
+    const bool am = m0 + lc < M, bn = n0 + lc < N;
+    float ra[8], rb[8];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + lr + 2 * u;
+            ra[u] = (am && k < K) ? A[(long long)k * lda + m0 + lc] : 0.f;
+            rb[u] = (bn && k < K) ? B[(long long)k * ldb + n0 + lc] : 0.f;
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            As[buf][lr + 2 * u][lc] = ra[u];
+            Bs[buf][lr + 2 * u][lc] = rb[u];
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    const int nk = (K + SG_K - 1) / SG_K;
+    for (int t = 0; t < nk; ++t) {
+        const int buf = t & 1;
+        if (t + 1 < nk) fetch((t + 1) * SG_K);
+#pragma unroll
+        for (int kk = 0; kk < SG_K; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + 4 * ty]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tx]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + 4 * tx]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (t + 1 < nk) stash(buf ^ 1);      // the other buffer was last read before the previous barrier
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int gm = m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
+        if (gm >= M) continue;
+        float* cr = C + (long long)gm * ldc;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int gn = n0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4);
+            if (gn >= N) continue;
+            cr[gn] = beta == 0.f ? alpha * acc[i][j] : fmaf(alpha, acc[i][j], beta * cr[gn]);
+        }
+    }
+}
+
 template <typename T>
 static void gemm_t(gw_ctx* ctx, const char* name, bool ta, bool tb, int M, int N, int K, T alpha, const T* A,
                    long long lda, const T* B, long long ldb, T beta, T* C, long long ldc, int batch, long long sA,
@@ -124,6 +202,14 @@ void gemm_f32(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, float alpha, c
 
 void gemm_f32_rn(gw_ctx* ctx, bool ta, bool tb, int M, int N, int K, float alpha, const float* A, long long lda,
                  const float* B, long long ldb, float beta, float* C, long long ldc) {
+    if (ta && !tb && M > 0 && N > 0) {
+        const long long gx = (N + SG_T - 1) / SG_T, gy = (M + SG_T - 1) / SG_T;
+        if (gx <= 0x7fffffffLL && gy <= 65535) {
+            klaunch(ctx, "k_sgemm_tn", k_sgemm_tn, dim3((unsigned)gx, (unsigned)gy), 256, 0, M, N, K, alpha, A, lda,
+                    B, ldb, beta, C, ldc);
+            return;
+        }
+    }
     gemm_t<float>(ctx, "k_sgemm", ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 1, 0, 0, 0);
 }
 

@@ -100,6 +100,7 @@ def load(path: str | None = None):
         "gw_chi0_copy": ([P, P, I, I, P], I),
         "gw_W_copy_chi_rpa": ([P, P, P, I, P], I),
         "gw_W_copy_pivots": ([P, P, P], I),
+        "gw_chi0_copy_elements": ([P, P, P, P, I, P], I),
         "gw_W_pole_freqs": ([P, P], I),
         "gw_W_copy_full": ([P, P, P, I, P], I),
         "gw_sigma_copy": ([P, P, P, P, P, P], I),
@@ -285,6 +286,15 @@ class Chi0(_Handle):
         A = np.zeros((nj, n, n))
         _check(self.ctx, load().gw_chi0_copy_spectral(self.ctx.handle, self.handle, j0, nj, _ptr(A)))
         return A
+
+    def chi0_elements(self, elems):
+        """chi0_k[m, n] for every frequency k and the (m, n) pairs: [n_omega, len(elems)]."""
+        m = np.ascontiguousarray([e[0] for e in elems], np.int32)
+        n = np.ascontiguousarray([e[1] for e in elems], np.int32)
+        out = np.zeros((self.info()["n_omega"], m.size), np.complex128)
+        _check(self.ctx, load().gw_chi0_copy_elements(self.ctx.handle, self.handle, _ptr(m), _ptr(n), m.size,
+                                                      _ptr(out)))
+        return out
 
     def chi0(self, k0, nk):
         n = self.info()["n_sub"]

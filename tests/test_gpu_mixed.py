@@ -14,6 +14,8 @@ flagged frequencies are refactorised in binary64 and every frequency meets
 import numpy as np
 import pytest
 
+import synth
+
 from tests.test_gpu_parity import _free, rel
 
 pytestmark = pytest.mark.gpu
@@ -233,3 +235,29 @@ def test_tensor_memory_forms_sizes(gwlib, ctx, atoms):
         ctx.set_option(gwlib.GW_OPT_FORMS_SIMT, 0)
     assert rel(c_tm, c_fma) < 2e-5
     assert np.abs(e - e2).max() < 0.05 * MEV
+
+
+def test_batched_forms_c_level(gwlib, ctx):
+    """N_sub = 480 (16-atom chain): the binary32 path takes the batched forms
+    (Y in HBM, panels in pairs); its c_nk agree with the oracle's and with the
+    binary64 path's (own basis: c is basis invariant) within 1e-4, quasiparticle
+    energies within 1 meV on the same branch."""
+    import oracle
+    from synth import molecules as sm
+    mol = sm._uniform_molecule("chain", 16, sm.SEED_BASE + 7816)
+    assert mol.n_sub == 480
+    grid = synth.Grid(512)
+    r = oracle.solve(mol, grid)
+    out = {}
+    for prec in (gwlib.GW_MIXED, gwlib.GW_FP64):
+        h, e, z, st = gwlib.solve(ctx, mol, grid, prec=prec)
+        try:
+            out[prec] = (h["sigma"].copy()["c"], e, st)
+        finally:
+            _free(h)
+    cm, em, stm = out[gwlib.GW_MIXED]
+    cd, ed, std = out[gwlib.GW_FP64]
+    assert rel(cd, r["c"]) < 1e-9
+    assert rel(cm, r["c"]) < 1e-4 and rel(cm, cd) < 1e-4
+    assert np.abs(em - r["e_qp"]).max() < MEV and np.abs(em - ed).max() < MEV
+    assert np.array_equal(stm, r["status"]) and np.array_equal(std, r["status"])

@@ -377,3 +377,26 @@ def test_z_factor_in_unit_interval(cfg1_oracle):
     for i in range(len(r["states"])):
         if r["status"][i] == 0:
             assert 0.0 < r["z"][i] <= 1.0
+
+
+def test_sampled_frequency_routes_equal_deposit_and_cauchy(cfg1, cfg1_oracle):
+    """The routes the oracle takes for molecules too large for its full grid
+    give the same numbers as the per-pair deposit followed by the O(N^2)
+    Cauchy sum (Eq. chi_by_spectra): weights grouped by bin, chi0 from the
+    band's weights at sampled frequencies, and chi0 elements straight from
+    the pairs' tent-weighted Cauchy kernel."""
+    mol, grid = cfg1
+    r = cfg1_oracle
+    bins = np.arange(int(r["pairs"]["bin"].min()), int(r["pairs"]["bin"].max()) + 2)
+    Ab = gw.spectral_weights_by_bin(r["U"], r["pairs"], bins)
+    assert np.linalg.norm(Ab - r["A"][bins]) <= 1e-13 * np.linalg.norm(r["A"])
+    # every other bin carries no weight
+    outside = np.setdiff1d(np.arange(grid.n_omega), bins)
+    assert np.abs(r["A"][outside]).max() == 0.0
+    ks = [0, 1, 37, 128, 255]
+    c = gw.chi0_from_weights(Ab, bins, ks, grid.d_omega, grid.eta)
+    assert np.linalg.norm(c - r["chi0"][ks]) <= 1e-12 * np.linalg.norm(r["chi0"][ks])
+    elems = [(0, 0), (5, 3), (239, 0), (120, 119), (17, 17)]
+    ce = gw.chi0_elements(r["U"], r["pairs"], elems, grid.n_omega, grid.d_omega, grid.eta)
+    ref = np.stack([r["chi0"][:, m, n] for m, n in elems], axis=1)
+    assert np.linalg.norm(ce - ref) <= 1e-12 * np.linalg.norm(ref)
