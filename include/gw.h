@@ -181,6 +181,16 @@ void      gw_mol_free(gw_mol* mol);
  * lambda_{n_sub} < 1e-12 lambda_max; GW_ERR_NO_CONVERGENCE. */
 gw_status gw_build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid,
                         gw_precision prec, gw_chi0** out);
+/* As gw_build_chi0 with the compression chosen by thresholds (Sec. 7.2)
+ * instead of desc->n_sub: the first N_rank pairs are those with
+ * |E - F| < e_threshold (Ha; Eq. subsetof_vef), and N_sub is the number of
+ * eigenvalues of g = X_r^T v X_r at least lambda_rel times the largest one
+ * (Eq. subspace; lambda_rel in [1e-6, 1): the deciding eigenvalues are
+ * binary32).  gw_chi0_info reports the n_rank and n_sub chosen; every later
+ * step works in that subspace.  GW_ERR_RANK if no pair or no eigenvalue
+ * passes; GW_ERR_INVALID_ARG if the molecule carries its own basis Z. */
+gw_status gw_build_chi0_thr(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, gw_precision prec,
+                            double e_threshold, double lambda_rel, gw_chi0** out);
 /* a5: factorises 1 - chi0_k = L_k D_k L_k^T (complex symmetric) for every
  * k (Eq. chi_RPA).  chi0 stays valid.  GW_ERR_SINGULAR on a zero or
  * non-finite pivot. */

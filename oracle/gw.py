@@ -45,6 +45,10 @@ R9 quasiparticle rule: f(E) = E - E_KS - Sigma_x + vxc - Re Sigma_c(E);
    E1 - 0.5 + i d_omega, i = 0..floor(1/d_omega), take the sign change whose
    midpoint is nearest E1 and bisect (200 halvings or width < 1e-11).
    status 0 = Newton, 1 = bisection, 2 = no root (E1 returned).
+R10 second window (Sec. 4.2): spectral arguments below lam = (N_s - 1) dw_s
+   belong to the small window, the rest to the large one; transitions are
+   deposited on the grid of their window, W's forms split the same way, each
+   window keeps its own broadening 1.5 dw (see solve_two_window).
 """
 from __future__ import annotations
 
@@ -136,6 +140,32 @@ def compression_basis(mol, VEF, method="auto"):
         raise RankError("compression rank below N_sub")
     Z = Xr @ xi[:, idx] / np.sqrt(lam_top)
     return dict(Z=Z, Zup=v @ Z, n_rank=n_rank, lam=lam_top)
+
+
+def compression_threshold(mol, VEF, pairs, e_threshold, lambda_rel):
+    """Threshold-driven compression (Sec. 7.2): the pairs with |E - F| below
+    e_threshold generate the subspace (Eq. subsetof_vef, N_rank of them), and
+    the eigenvectors of g whose eigenvalue is at least lambda_rel times the
+    largest are kept (Eq. subspace, N_sub = N_subrank of them); Z = X xi
+    lambda^-1/2, Zup = v Z (Eq. global-basis-orthogonality)."""
+    v = mol.v
+    n_rank = int(np.count_nonzero(pairs["delta"] < e_threshold))
+    if n_rank < 1:
+        raise RankError("no pair below the energy threshold")
+    Xr = VEF[:n_rank].T
+    g = Xr.T @ v @ Xr
+    lam, xi = np.linalg.eigh(g)
+    keep = np.nonzero(lam >= lambda_rel * lam.max())[0][::-1]          # descending
+    Z = Xr @ xi[:, keep] / np.sqrt(lam[keep])
+    return dict(Z=Z, Zup=v @ Z, n_rank=n_rank, n_sub=keep.size, lam=lam[keep], X=Xr, g=g)
+
+
+def projected_W(mol, X, g, W):
+    """W_projected = P W P^T with P = v X g^-1 X^T, the projector onto the span
+    of the pair vectors X in the Coulomb metric (Eqs. projector0 and
+    proj-scr-inter), for W [..., n_prod, n_prod]."""
+    P = mol.v @ X @ np.linalg.solve(g, X.T)
+    return P @ W @ P.T
 
 
 # ------------------------------------------------------------------ a2, a3
@@ -314,13 +344,22 @@ def sigma_x(mol, Vnk_occ):
 
 
 # ------------------------------------------------------------------ a8
-def qp_solve(e_ks, sig_x, vxc, sig_n, j0, d_omega, eta):
-    """Root of the diagonal quasiparticle equation (R9)."""
-    def F(E):
+def qp_solve(e_ks, sig_x, vxc, sig_n, j0, d_omega, eta, second=None):
+    """Root of the diagonal quasiparticle equation (R9).  ``second`` =
+    (sig_n, j0, d_omega, eta) of the large window adds its Cauchy sum to
+    Re Sigma_c (second window technique, R10); the scan step stays d_omega."""
+    def re_sigma(E):
         re, der = sigma_c_re(sig_n, j0, d_omega, eta, E)
+        if second is not None:
+            r2, d2 = sigma_c_re(second[0], second[1], second[2], second[3], E)
+            re, der = re + r2, der + d2
+        return re, der
+
+    def F(E):
+        re, der = re_sigma(E)
         return E - e_ks - sig_x + vxc - re, 1.0 - der
 
-    re0, der0 = sigma_c_re(sig_n, j0, d_omega, eta, e_ks)
+    re0, der0 = re_sigma(e_ks)
     E1 = e_ks + (sig_x - vxc + re0) / (1.0 - der0)
     E = E1
     ok = False
@@ -363,22 +402,122 @@ def qp_solve(e_ks, sig_x, vxc, sig_n, j0, d_omega, eta):
                 else:
                     b = m
             E, status = 0.5 * (a + b), 1
-    _, der = sigma_c_re(sig_n, j0, d_omega, eta, E)
+    _, der = re_sigma(E)
     return E, 1.0 / (1.0 - der), status
 
 
+# ------------------------------------------------------------------ second window
+# R10 (Sec. 4.2, Eq. win2-for-response): a small window (grid gs, broadening
+# eta_s = 1.5 dw_s) and a large one (grid gl, eta_l = 1.5 dw_l).  Spectral
+# arguments below lam = (N_s - 1) dw_s belong to the small window, the rest
+# to the large one, so no spectral weight is counted twice: transitions with
+# Delta < lam are deposited on the small grid, the others on the large grid
+# (the large window's spectral function truncated below lam); chi0 on the
+# small grid is the sum of both Cauchy integrals, each with its own
+# broadening; chi0 on the large grid takes every transition on the large
+# grid.  W's spectral functions (the forms c_nk) are split the same way
+# (small grid for s2 < lam, large grid for s2 >= lam), each gives its own
+# sigma on its own grid, and Sigma_c is the sum of the two Cauchy sums.
+def window_cut(gs):
+    """lam: spectral arguments s < lam belong to the small window."""
+    return (gs.n_omega - 1) * gs.d_omega
+
+
+def pairs_on_grid(pairs, sel, grid):
+    """The selected sorted pairs with their tent bins on another grid (R2)."""
+    delta = pairs["delta"][sel]
+    x = delta / grid.d_omega
+    j = np.floor(x).astype(np.int64)
+    if np.any(j + 1 > grid.n_omega - 1):
+        raise GridError("transition outside the frequency window")
+    return dict(E=pairs["E"][sel], F=pairs["F"][sel], delta=delta, bin=j, frac=x - j)
+
+
+def chi0_two_window(U, pairs, gs, gl):
+    """chi0 on the small grid by Eq. win2-for-response (R10)."""
+    lam = window_cut(gs)
+    lo = pairs["delta"] < lam
+    A_s = deposit_spectral(U[lo], pairs_on_grid(pairs, lo, gs), gs.n_omega)
+    A_l = deposit_spectral(U[~lo], pairs_on_grid(pairs, ~lo, gl), gl.n_omega)
+    w = np.arange(gs.n_omega)[:, None] * gs.d_omega
+    s = np.arange(gl.n_omega)[None, :] * gl.d_omega
+    K_l = 1.0 / (w - s + 1j * gl.eta) - 1.0 / (w + s + 1j * gl.eta)
+    flat_l = A_l.reshape(gl.n_omega, -1)
+    large = ((K_l.real @ flat_l) + 1j * (K_l.imag @ flat_l)).reshape((gs.n_omega,) + A_l.shape[1:])
+    return chi0_cauchy(A_s, gs.d_omega, gs.eta) + large
+
+
+def split_forms(c_s, c_l, gs, gl):
+    """The forms of the two windows restricted to their own spectral ranges
+    (R10): c_s for s2 < lam, c_l for s2 >= lam."""
+    lam = window_cut(gs)
+    c_s = c_s.copy()
+    c_l = c_l.copy()
+    c_s[..., np.arange(gs.n_omega) * gs.d_omega >= lam] = 0.0
+    c_l[..., np.arange(gl.n_omega) * gl.d_omega < lam] = 0.0
+    return c_s, c_l
+
+
+def sigma_c_two_window(sig_s, j0_s, sig_l, j0_l, gs, gl):
+    """Sigma_c on the small grid's points w_k = k dw_s, |k| < N_s: the small
+    window's Cauchy sum plus the large window's (Eq. Cauchy1 in both, R7, R10)."""
+    small = sigma_c_grid(sig_s, j0_s, gs.d_omega, gs.eta, gs.n_omega)
+    j = j0_l + np.arange(sig_l.shape[1])
+    sgn = np.where(j >= 0, 1.0, -1.0)
+    w = np.arange(-(gs.n_omega - 1), gs.n_omega)[:, None] * gs.d_omega
+    K = 1.0 / (w - j[None, :] * gl.d_omega + 1j * gl.eta * sgn[None, :])
+    return small + gl.d_omega * (sig_l @ K.T)
+
+
+def solve_two_window(mol, gs, gl, states=None, vxc="sigma_x", Z=None):
+    """One GW solve with the second window technique (Sec. 4.2, R10): chi0,
+    W and the forms on both grids, sigma and Sigma_c combined, QP root."""
+    if states is None:
+        states = [mol.n_occ - 1, mol.n_occ]
+    states = list(states)
+    pairs = pair_table(mol.eps, mol.n_occ, gl.d_omega, gl.n_omega)
+    VEF = pair_vertex(mol, pairs)
+    basis = compression_basis(mol, VEF) if Z is None else dict(Z=Z, Zup=mol.v @ Z)
+    Zup = basis["Zup"]
+    U = compress_pairs(VEF, Zup)
+    chi0_s = chi0_two_window(U, pairs, gs, gl)
+    chi0_l = chi0_cauchy(deposit_spectral(U, pairs, gl.n_omega), gl.d_omega, gl.eta)
+    rpa_s, rpa_l = screen(chi0_s), screen(chi0_l)
+    Vnk = state_vertex(mol, states)
+    c_s = sigma_forms(Vnk, Zup, spectral_gamma(rpa_s, np.arange(gs.n_omega)))
+    c_l = sigma_forms(Vnk, Zup, spectral_gamma(rpa_l, np.arange(gl.n_omega)))
+    cs, cl = split_forms(c_s, c_l, gs, gl)
+    sig_s, j0_s = sigma_grid(cs, mol.eps, mol.n_occ, gs.d_omega)
+    sig_l, j0_l = sigma_grid(cl, mol.eps, mol.n_occ, gl.d_omega)
+    sigc = sigma_c_two_window(sig_s, j0_s, sig_l, j0_l, gs, gl)
+    sx = sigma_x(mol, Vnk[:, :mol.n_occ, :])
+    vxc_arr = sx.copy() if isinstance(vxc, str) else np.broadcast_to(np.asarray(vxc, float), sx.shape).copy()
+    e_qp = np.zeros(len(states))
+    zf = np.zeros(len(states))
+    st = np.zeros(len(states), dtype=np.int32)
+    for i, n in enumerate(states):
+        e_qp[i], zf[i], st[i] = qp_solve(mol.eps[n], sx[i], vxc_arr[i], sig_s[i], j0_s, gs.d_omega, gs.eta,
+                                         second=(sig_l[i], j0_l, gl.d_omega, gl.eta))
+    return dict(pairs=pairs, Z=basis["Z"], Zup=Zup, U=U, chi0_s=chi0_s, chi0_l=chi0_l, chi_rpa_s=rpa_s,
+                chi_rpa_l=rpa_l, c_s=c_s, c_l=c_l, sigma_s=sig_s, j0_s=j0_s, sigma_l=sig_l, j0_l=j0_l,
+                sigma_c=sigc, sigma_x=sx, e_qp=e_qp, z=zf, status=st, states=states)
+
+
 # ------------------------------------------------------------------ pipeline
-def solve(mol, grid, states=None, vxc="sigma_x", Z=None, keep_W_freqs=None):
+def solve(mol, grid, states=None, vxc="sigma_x", Z=None, keep_W_freqs=None, thresholds=None):
     """One GW solve: a0..a8.  ``vxc`` is an array, 0, or "sigma_x" (the
     synthetic mean field is taken to contain exchange: vxc_nn = Sigma_x_nn).
-    ``Z`` optionally fixes the compression basis (elementwise parity)."""
+    ``Z`` optionally fixes the compression basis (elementwise parity);
+    ``thresholds`` = (e_threshold, lambda_rel) selects it by Sec. 7.2."""
     N, dw, eta = grid.n_omega, grid.d_omega, grid.eta
     if states is None:
         states = [mol.n_occ - 1, mol.n_occ]
     states = list(states)
     pairs = pair_table(mol.eps, mol.n_occ, dw, N)
     VEF = pair_vertex(mol, pairs)
-    if Z is None:
+    if thresholds is not None:
+        basis = compression_threshold(mol, VEF, pairs, *thresholds)
+    elif Z is None:
         basis = compression_basis(mol, VEF)
     else:
         basis = dict(Z=Z, Zup=mol.v @ Z, n_rank=None, lam=None)

@@ -394,7 +394,15 @@ static void check_grid(const gw_grid* g) {
     REQUIRE(g->eta > 0 && std::isfinite(g->eta), "eta must be positive");
 }
 
-static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, gw_precision prec) {
+// Threshold-driven compression (Sec. 7.2): N_rank = the pairs with
+// |E - F| < e_threshold (Eq. subsetof_vef), N_sub = the eigenvalues of g at
+// least lambda_rel times the largest (Eq. subspace).
+struct Compression {
+    double e_threshold, lambda_rel;
+};
+
+static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, gw_precision prec,
+                           const Compression* cmp = nullptr) {
     // a molecule uploaded through another context of the same device may be shared
     // (read only; its upload was synchronised): serving keeps molecules resident
     REQUIRE(mol && mol->ctx && mol->ctx->device == ctx->device, "molecule belongs to another device");
@@ -418,7 +426,18 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
     c->L = 2 * N;
     c->logL = 0;
     while ((1 << c->logL) < c->L) c->logL++;
-    const int n_prod = mol->n_prod, n_sub = mol->n_sub, n_pair = c->n_pair;
+    const int n_prod = mol->n_prod, n_pair = c->n_pair;
+    int n_sub = mol->n_sub;
+    int nr_thr = 0;
+    if (cmp) {
+        REQUIRE(cmp->e_threshold > 0 && std::isfinite(cmp->e_threshold), "e_threshold must be positive");
+        // the eigenvalues that decide are binary32: a ratio below 1e-6 would not separate g's null space
+        REQUIRE(cmp->lambda_rel >= 1e-6 && cmp->lambda_rel < 1, "lambda_rel must be in [1e-6, 1)");
+        REQUIRE(!mol->Z, "a given basis Z and compression thresholds exclude each other");
+        for (int E = 0; E < n_occ; ++E)
+            for (int F = n_occ; F < n_orb; ++F) nr_thr += (e[F] - e[E] < cmp->e_threshold) ? 1 : 0;
+        if (nr_thr < 1) gw_throw(GW_ERR_RANK, "no pair below e_threshold");
+    }
     double* VEFt = nullptr;
     float* V32 = nullptr;
     double *T1 = nullptr, *g = nullptr, *Bsel = nullptr;
@@ -450,25 +469,36 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
             VEFt = dalloc<double>(ctx, (size_t)n_prod * n_pair);
             launch_vertex_contract(ctx, mol, occ, n_occ, virt, n_virt, rank_of, VEFt, n_pair);
         }
-        // a0: basis
-        c->Zup = dalloc<double>(ctx, (size_t)n_prod * n_sub);
+        // a0: basis (threshold-driven: N_sub is known once the eigenvalues of g are)
+        if (!cmp) c->Zup = dalloc<double>(ctx, (size_t)n_prod * n_sub);
+        auto choose_n_sub = [&](const double* g64, const float* g32_, int nr) {
+            std::vector<float> lam = eigvals32(ctx, g64, g32_, nr);
+            const double top = lam.back();
+            int k = 0;
+            for (float x : lam) k += ((double)x >= cmp->lambda_rel * top) ? 1 : 0;
+            if (!(top > 0) || k < 1) gw_throw(GW_ERR_RANK, "no eigenvalue of g above lambda_rel");
+            n_sub = k;
+            c->n_sub = n_sub;
+            c->Zup = dalloc<double>(ctx, (size_t)n_prod * n_sub);
+        };
         if (mol->Z) {
             c->Z = dalloc<double>(ctx, (size_t)n_prod * n_sub);
             CUDA_CHECK(cudaMemcpyAsync(c->Z, mol->Z, sizeof(double) * n_prod * n_sub, cudaMemcpyDeviceToDevice, ctx->stream));
             gemm_f64(ctx, false, false, n_prod, n_sub, n_prod, 1.0, mol->v, n_prod, c->Z, n_sub, 0.0, c->Zup, n_sub);
-        } else if (n_sub == n_prod) {
+        } else if (!cmp && n_sub == n_prod) {
             CUDA_CHECK(cudaMemcpyAsync(c->Zup, mol->v, sizeof(double) * n_prod * n_prod, cudaMemcpyDeviceToDevice, ctx->stream));
             cholesky_lower(ctx, c->Zup, n_prod);
         } else {
-            const int nr = std::min(n_pair, std::max(5 * n_orb, n_sub));
+            const int nr = cmp ? nr_thr : std::min(n_pair, std::max(5 * n_orb, n_sub));
             c->n_rank = nr;
-            Bsel = dalloc<double>(ctx, (size_t)nr * n_sub);
             if (prec == GW_FP64) {
                 T1 = dalloc<double>(ctx, (size_t)n_prod * nr);
                 g = dalloc<double>(ctx, (size_t)nr * nr);
                 // T1 = v X_r, g = X_r^T v X_r  (X_r = first nr columns of VEFt)
                 gemm_f64(ctx, false, false, n_prod, nr, n_prod, 1.0, mol->v, n_prod, VEFt, n_pair, 0.0, T1, nr);
                 gemm_f64(ctx, true, false, nr, nr, n_prod, 1.0, VEFt, n_pair, T1, nr, 0.0, g, nr);
+                if (cmp) choose_n_sub(g, nullptr, nr);
+                Bsel = dalloc<double>(ctx, (size_t)nr * n_sub);
                 // binary32 start refined to binary64 accuracy
                 eigh_top_scaled(ctx, g, nullptr, nr, n_sub, 6, 1e-13, true, Bsel);
                 gemm_f64(ctx, false, false, n_prod, n_sub, nr, 1.0, T1, nr, Bsel, n_sub, 0.0, c->Zup, n_sub);
@@ -498,6 +528,8 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
                     gemm_f32(ctx, true, false, nr, nr, n_prod, 1.f, X32, nr, T32, nr, 0.f, g32, nr);
                     ctx_free(ctx, v32); v32 = nullptr;
                     ctx_free(ctx, T32); T32 = nullptr;
+                    if (cmp) choose_n_sub(nullptr, g32, nr);
+                    Bsel = dalloc<double>(ctx, (size_t)nr * n_sub);
                     eigh_top_scaled(ctx, nullptr, g32, nr, n_sub, 0, 0.0, false, Bsel);
                     ctx_free(ctx, g32); g32 = nullptr;
                     // Z = X_r B (binary32 product; the scaling below is exact for whatever
@@ -584,6 +616,17 @@ extern "C" gw_status gw_build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid
     API_BEGIN(ctx)
     CUDA_CHECK(cudaSetDevice(ctx->device));
     *out = build_chi0(ctx, mol, grid, prec);
+    API_END
+}
+
+extern "C" gw_status gw_build_chi0_thr(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, gw_precision prec,
+                                       double e_threshold, double lambda_rel, gw_chi0** out) {
+    if (!ctx || !out) return GW_ERR_INVALID_ARG;
+    *out = nullptr;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    const Compression cmp{e_threshold, lambda_rel};
+    *out = build_chi0(ctx, mol, grid, prec, &cmp);
     API_END
 }
 

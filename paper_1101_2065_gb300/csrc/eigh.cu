@@ -709,6 +709,69 @@ void basis_rayleigh_scale(gw_ctx* ctx, double* Z, double* Zup, int rows, int n_s
     ctx_free(ctx, lam);
 }
 
+// All eigenvalues of g (ascending) in binary32: the tridiagonalisation and
+// multisection of eigh_top_scaled without the vectors (threshold-driven
+// choice of the subspace dimension).
+std::vector<float> eigvals32(gw_ctx* ctx, const double* g, const float* g32, int n) {
+    const long long nn = (long long)n * n;
+    float *A32 = nullptr, *d = nullptr, *e = nullptr, *tau = nullptr, *lam32 = nullptr, *vb = nullptr, *pb = nullptr,
+          *pt = nullptr;
+    unsigned int* bar = nullptr;
+    std::vector<float> out(n);
+    auto release = [&]() {
+        for (void* p : {(void*)A32, (void*)d, (void*)e, (void*)tau, (void*)lam32, (void*)vb, (void*)pb, (void*)pt,
+                        (void*)bar})
+            ctx_free(ctx, p);
+    };
+    try {
+        A32 = dalloc<float>(ctx, nn);
+        d = dalloc<float>(ctx, n); e = dalloc<float>(ctx, n); tau = dalloc<float>(ctx, n);
+        lam32 = dalloc<float>(ctx, n);
+        if (g32) CUDA_CHECK(cudaMemcpyAsync(A32, g32, sizeof(float) * nn, cudaMemcpyDeviceToDevice, ctx->stream));
+        else launch_to_f32(ctx, g, A32, nn);
+        const int rows = (n + CL - 1) / CL;
+        const size_t smem_cl = sizeof(float) * ((size_t)rows * n + 5 * (size_t)n);
+        if (smem_cl <= 220 * 1024) {
+            allow_max_smem(k_sytrd32_cl);
+            klaunch(ctx, "k_sytrd32_cl", k_sytrd32_cl, CL, 1024, smem_cl, A32, n, d, e, tau);
+        } else {
+            const size_t smem = 2 * (size_t)n * sizeof(float);
+            if (smem > 200 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for the eigensolver");
+            allow_max_smem(k_sytrd32_grid);
+            const int grid = ctx->num_sms;
+            vb = dalloc<float>(ctx, n); pb = dalloc<float>(ctx, n); pt = dalloc<float>(ctx, grid);
+            bar = dalloc<unsigned int>(ctx, 2);
+            CUDA_CHECK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), ctx->stream));
+            void* args[] = {&A32, (void*)&n, &d, &e, &tau, &vb, &pb, &pt, &bar, &ctx->d_status};
+            prof_begin(ctx, "k_sytrd32_grid");
+            CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)k_sytrd32_grid, dim3(grid), dim3(512), args, smem,
+                                                   ctx->stream));
+            after_launch(ctx, "k_sytrd32_grid");
+        }
+        std::vector<float> hd(n), he(n);
+        CUDA_CHECK(cudaMemcpyAsync(hd.data(), d, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_CHECK(cudaMemcpyAsync(he.data(), e, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        float bnd = 0.f;
+        for (int i = 0; i < n; ++i) {
+            float r = std::fabs(hd[i]) + (i > 0 ? std::fabs(he[i - 1]) : 0.f) + (i + 1 < n ? std::fabs(he[i]) : 0.f);
+            bnd = std::max(bnd, r);
+        }
+        bnd = bnd * 1.01f + 1e-30f;
+        allow_max_smem(k_bisect);
+        if (2 * (size_t)n * sizeof(float) > 200 * 1024) gw_throw(GW_ERR_INVALID_ARG, "rank too large for the bisection");
+        klaunch(ctx, "k_bisect", k_bisect, div_up(n, 8), 256, 2 * (size_t)n * sizeof(float), (const float*)d,
+                (const float*)e, n, bnd, lam32);
+        CUDA_CHECK(cudaMemcpyAsync(out.data(), lam32, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        ctx_finish(ctx, "eigenvalues of g");
+    } catch (...) {
+        release();
+        throw;
+    }
+    release();
+    return out;
+}
+
 void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int n_sub, int oa_iters, double oa_tol,
                      bool vectors_f64, double* B) {
     if (!g && oa_iters > 0) gw_throw(GW_ERR_INVALID_ARG, "eigensolver refinement needs the binary64 matrix");

@@ -189,6 +189,7 @@ void cholesky_lower(gw_ctx* ctx, double* A, int n);          // in place, zeroes
 void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int n_sub, int oa_iters, double oa_tol,
                      bool vectors_f64, double* B);
 void basis_rayleigh_scale(gw_ctx* ctx, double* Z, double* Zup, int rows, int n_sub);
+std::vector<float> eigvals32(gw_ctx* ctx, const double* g, const float* g32, int n);   // ascending
 // chi0.cu
 void launch_fft_tables(gw_ctx* ctx, gw_chi0* c);
 void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c);           // binary64: deposit + FFT

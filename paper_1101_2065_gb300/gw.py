@@ -101,6 +101,7 @@ def load(path: str | None = None):
         "gw_W_copy_chi_rpa": ([P, P, P, I, P], I),
         "gw_W_copy_pivots": ([P, P, P], I),
         "gw_chi0_copy_elements": ([P, P, P, P, I, P], I),
+        "gw_build_chi0_thr": ([P, P, C.POINTER(Grid), I, D, D, pp], I),
         "gw_W_pole_freqs": ([P, P], I),
         "gw_W_copy_full": ([P, P, P, I, P], I),
         "gw_sigma_copy": ([P, P, P, P, P, P], I),
@@ -377,6 +378,17 @@ def gw_build_chi0(ctx, mol, grid, prec=GW_FP64):
     g = make_grid(grid)
     h = C.c_void_p()
     _check(ctx, load().gw_build_chi0(ctx.handle, mol.handle, C.byref(g), int(prec), C.byref(h)))
+    c = Chi0(ctx, h)
+    c.mol, c.n_omega = mol, int(grid.n_omega)
+    return c
+
+
+def gw_build_chi0_thr(ctx, mol, grid, prec=GW_FP64, e_threshold=1.0, lambda_rel=1e-3):
+    """gw_build_chi0 with N_rank and N_sub chosen by the thresholds of Sec. 7.2."""
+    g = make_grid(grid)
+    h = C.c_void_p()
+    _check(ctx, load().gw_build_chi0_thr(ctx.handle, mol.handle, C.byref(g), int(prec), float(e_threshold),
+                                         float(lambda_rel), C.byref(h)))
     c = Chi0(ctx, h)
     c.mol, c.n_omega = mol, int(grid.n_omega)
     return c

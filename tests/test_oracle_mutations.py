@@ -21,6 +21,13 @@ MUTATIONS = [
     ("q = Vnk @ Zup ", "q = Vnk @ Zup * 1.0001 "),
     ("Z = Xr @ xi[:, idx] / np.sqrt(lam_top)", "Z = Xr @ xi[:, idx] / lam_top"),
     ("return np.linalg.solve(I[None] - chi0[ks], chi0[ks])", "return np.linalg.solve(I[None] + chi0[ks], chi0[ks])"),
+    # second window: the large window's transitions with the small broadening; weight counted in both windows
+    ("K_l = 1.0 / (w - s + 1j * gl.eta) - 1.0 / (w + s + 1j * gl.eta)",
+     "K_l = 1.0 / (w - s + 1j * gs.eta) - 1.0 / (w + s + 1j * gs.eta)"),
+    ("A_l = deposit_spectral(U[~lo], pairs_on_grid(pairs, ~lo, gl), gl.n_omega)",
+     "A_l = deposit_spectral(U, pairs_on_grid(pairs, np.ones_like(lo), gl), gl.n_omega)"),
+    # threshold compression: keep the smallest eigenvalues instead of the largest
+    ("keep = np.nonzero(lam >= lambda_rel * lam.max())[0][::-1]", "keep = np.nonzero(lam <= lambda_rel * lam.max())[0]"),
 ]
 
 

@@ -400,3 +400,78 @@ def test_sampled_frequency_routes_equal_deposit_and_cauchy(cfg1, cfg1_oracle):
     ce = gw.chi0_elements(r["U"], r["pairs"], elems, grid.n_omega, grid.d_omega, grid.eta)
     ref = np.stack([r["chi0"][:, m, n] for m, n in elems], axis=1)
     assert np.linalg.norm(ce - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_threshold_compression_pins(cfg1, cfg1_oracle):
+    """Threshold-driven compression (Sec. 7.2) on the chain: thresholds that
+    keep every pair and every nonzero eigenvalue reproduce the uncompressed W
+    exactly; a tighter energy threshold gives N_rank < N_prod pairs whose
+    projector P = v X g^-1 X^T (Eq. projector0) satisfies P^2 = P and fixes the
+    span of v X; N_sub grows as lambda shrinks and N_rank as E_threshold grows;
+    the kept basis is Coulomb-orthonormal."""
+    mol, grid = cfg1
+    r = cfg1_oracle
+    pairs, VEF = r["pairs"], r["VEF"]
+    full = gw.compression_threshold(mol, VEF, pairs, pairs["delta"].max() + 1.0, 1e-10)
+    assert full["n_rank"] == pairs["delta"].size and full["n_sub"] == mol.n_prod
+    ks = [1, 77, 200]
+    U = gw.compress_pairs(VEF, full["Zup"])
+    A = gw.deposit_spectral(U, pairs, grid.n_omega)
+    chi0 = gw.chi0_cauchy(A, grid.d_omega, grid.eta)
+    W = gw.screened_W(mol, full["Zup"], gw.screen(chi0, ks))
+    W_ref = gw.screened_W(mol, r["Zup"], r["chi_rpa"][ks])          # uncompressed (Cholesky basis)
+    assert np.linalg.norm(W - W_ref) <= 1e-10 * np.linalg.norm(W_ref)
+    sub = gw.compression_threshold(mol, VEF, pairs, np.sort(pairs["delta"])[99] + 1e-9, 0.1)
+    assert sub["n_rank"] == 100 and 0 < sub["n_sub"] < 100
+    P = mol.v @ sub["X"] @ np.linalg.solve(sub["g"], sub["X"].T)
+    assert np.linalg.norm(P @ P - P) <= 1e-9 * np.linalg.norm(P)
+    vX = mol.v @ sub["X"]
+    assert np.linalg.norm(P @ vX - vX) <= 1e-9 * np.linalg.norm(vX)
+    Z = sub["Z"]
+    assert np.abs(Z.T @ mol.v @ Z - np.eye(sub["n_sub"])).max() < 1e-10
+    n_by_lam = [gw.compression_threshold(mol, VEF, pairs, 0.9, lam)["n_sub"] for lam in (1e-1, 1e-2, 1e-3, 1e-4)]
+    assert n_by_lam[0] < n_by_lam[1] < n_by_lam[2] < n_by_lam[3] <= mol.n_prod
+    n_by_e = [gw.compression_threshold(mol, VEF, pairs, e, 1e-3)["n_rank"] for e in (0.6, 0.9, 1.4)]
+    assert n_by_e[0] < n_by_e[1] < n_by_e[2]
+
+
+def test_two_window_reduces_to_one_window(cfg1, cfg1_oracle):
+    """Second window technique (Sec. 4.2): with the small window equal to the
+    large one every transition and every form falls in the small window or
+    exactly on the seam, so chi0, Sigma_c and the quasiparticle energies are
+    the one-window results."""
+    mol, grid = cfg1
+    r = cfg1_oracle
+    t = gw.solve_two_window(mol, grid, grid, Z=None)
+    assert np.linalg.norm(t["chi0_s"] - r["chi0"]) <= 1e-13 * np.linalg.norm(r["chi0"])
+    assert np.linalg.norm(t["sigma_c"] - r["sigma_c"]) <= 1e-12 * np.linalg.norm(r["sigma_c"])
+    assert np.abs(t["e_qp"] - r["e_qp"]).max() < 1e-11
+    assert np.array_equal(t["status"], r["status"])
+
+
+def test_two_window_chi0_closed_form_on_nodes():
+    """Eq. win2-for-response with every transition on a node of its window's
+    grid: chi0 on the small grid is the closed form of Sec. 6.1 in which each
+    transition carries the broadening of its window (small below lam, large
+    at or above it), brute-force vertex products."""
+    mol = pins.on_grid(pins.tiny_molecule(n_orb=8, n_occ=4, n_prod=6), DW)
+    gl = synth.Grid(256, DW, 1.5 * DW)
+    gs = synth.Grid(320, DW / 4, 1.5 * DW / 4)
+    lam = gw.window_cut(gs)
+    Zup = np.linalg.cholesky(mol.v)
+    pairs = gw.pair_table(mol.eps, mol.n_occ, gl.d_omega, gl.n_omega)
+    assert np.any(pairs["delta"] < lam) and np.any(pairs["delta"] >= lam)
+    U = gw.compress_pairs(gw.pair_vertex(mol, pairs), Zup)
+    chi = gw.chi0_two_window(U, pairs, gs, gl)
+    ks = np.array([0, 1, 50, 161, 319])
+    w = ks * gs.d_omega
+    Vd = pins.dense_vertex(mol)
+    ref = np.zeros((ks.size, mol.n_sub, mol.n_sub), complex)
+    for E in range(mol.n_occ):
+        for F in range(mol.n_occ, mol.eps.size):
+            u = Zup.T @ pins.brute_vef(mol, E, F, Vd)
+            d = mol.eps[F] - mol.eps[E]
+            eta = gs.eta if d < lam else gl.eta
+            k = 1.0 / (w + 1j * eta - d) - 1.0 / (w + 1j * eta + d)
+            ref += 2.0 * np.outer(u, u)[None] * k[:, None, None]
+    assert np.abs(chi[ks] - ref).max() <= 1e-12 * np.abs(ref).max()
