@@ -191,6 +191,21 @@ gw_status gw_build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid,
  * passes; GW_ERR_INVALID_ARG if the molecule carries its own basis Z. */
 gw_status gw_build_chi0_thr(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, gw_precision prec,
                             double e_threshold, double lambda_rel, gw_chi0** out);
+/* Second window technique (Sec. 4.2, Eq. win2-for-response): chi0 on a
+ * small, fine window and on a large, coarse one.  large: the one-window grid
+ * (n_omega a power of two, every transition inside it); small: any n_omega in
+ * [4, 32768] with d_omega below the large grid's (eta of each grid is its
+ * broadening, 1.5 d_omega in the paper).  With lam = (small.n_omega - 1)
+ * small.d_omega, spectral arguments below lam belong to the small window and
+ * the others to the large one: *large_out is gw_build_chi0 on the large
+ * grid; *small_out is chi0 at the small grid's frequencies from the pairs
+ * with Delta < lam deposited on the small grid (small broadening) plus the
+ * other pairs deposited on the large grid (large broadening).  Keep the
+ * large handle alive while the small one is in use; each is screened by
+ * gw_screen_W and freed by gw_chi0_free.  The small handle keeps no pair
+ * table, U or spectral weights (their read-backs return GW_ERR_INVALID_ARG). */
+gw_status gw_build_chi0_2w(gw_ctx* ctx, const gw_mol* mol, const gw_grid* small, const gw_grid* large,
+                           gw_precision prec, gw_chi0** small_out, gw_chi0** large_out);
 /* a5: factorises 1 - chi0_k = L_k D_k L_k^T (complex symmetric) for every
  * k (Eq. chi_RPA).  chi0 stays valid.  GW_ERR_SINGULAR on a zero or
  * non-finite pivot. */
@@ -203,6 +218,17 @@ gw_status gw_screen_W(gw_ctx* ctx, const gw_chi0* chi0, gw_W** out);
  * Sigma_x_n = -sum_{k occ} V^{nk} v V^{nk} (Eq. instantaneous). */
 gw_status gw_sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n_states,
                         gw_sigma** out);
+/* Self-energy with the second window technique (Sec. 4.2): the forms of
+ * both windows, c_nk on the small grid kept for s2 < lam (its last point
+ * zeroed) and on the large grid kept for s2 >= lam (its first points
+ * zeroed); sigma_n on each grid from its forms; Sigma_c on the small grid's
+ * points is the sum of both Cauchy sums, each with its window's broadening.
+ * gw_qp_solve then adds both windows' Re Sigma_c.  W_small, W_large: the
+ * screened handles of a gw_build_chi0_2w pair.  gw_sigma_copy returns the
+ * small window's arrays (c as used, sigma, the combined Sigma_c);
+ * gw_sigma_copy_large the large window's c and sigma. */
+gw_status gw_sigma_diag_2w(gw_ctx* ctx, const gw_W* W_small, const gw_W* W_large, const int* states,
+                           int n_states, gw_sigma** out);
 /* a8: E solves E - E_KS - Sigma_x + vxc - Re Sigma_c(E) = 0 per state:
  * linearised start, Newton to |step| < 1e-11 Ha (100 steps, confined to
  * +-0.5 Ha of the start), else bracket scan at step d_omega over +-0.5 Ha
@@ -339,6 +365,10 @@ gw_status gw_W_copy_full(gw_ctx* ctx, const gw_W* W, const int* freqs, int nf, d
 gw_status gw_sigma_copy(gw_ctx* ctx, const gw_sigma* s, double* c, double* sigma,
                         double* sigc, double* sigma_x);
 gw_status gw_sigma_grid(const gw_sigma* s, int* j0, int* n_sig);
+/* second window (gw_sigma_diag_2w): the large window's c [n_states*n_orb*n_omega_large]
+ * (zero for s2 < lam) and sigma [n_states*n_sig2] on bins j0 .. j0 + n_sig2 - 1 */
+gw_status gw_sigma_copy_large(gw_ctx* ctx, const gw_sigma* s, double* c, double* sigma);
+gw_status gw_sigma_grid_large(const gw_sigma* s, int* j0, int* n_sig);
 
 #ifdef __cplusplus
 }

@@ -632,6 +632,107 @@ extern "C" gw_status gw_build_chi0_thr(gw_ctx* ctx, const gw_mol* mol, const gw_
 
 extern "C" void gw_chi0_free(gw_chi0* c) { chi0_release(c); }
 
+// Second window technique (Sec. 4.2, Eq. win2-for-response, reading R10):
+// chi0 on the small window's grid from the large window's build (its pairs,
+// basis and U).  Pairs with Delta < lam = (N_s - 1) dws are deposited on the
+// small grid and enter with the small broadening; the others are deposited
+// on the large grid (the large window's spectral function truncated below
+// lam) and enter with the large broadening; one band sum over both blocks of
+// bins gives chi0 at the small grid's frequencies.
+static gw_chi0* build_small_window(gw_ctx* ctx, const gw_chi0* cl, const gw_grid* gs) {
+    REQUIRE(cl && cl->ctx == ctx, "chi0 belongs to another context");
+    REQUIRE(!cl->large, "the large window's handle must be a one-window build");
+    REQUIRE(gs && gs->n_omega >= 4 && gs->n_omega <= (1 << 15) && gs->d_omega > 0 && std::isfinite(gs->d_omega) &&
+                gs->eta > 0 && std::isfinite(gs->eta),
+            "small window: n_omega in [4, 32768], positive d_omega and eta");
+    REQUIRE(gs->d_omega < cl->grid.d_omega, "the small window's grid must be finer than the large window's");
+    const double lam = (double)(gs->n_omega - 1) * gs->d_omega;
+    REQUIRE(lam < (double)cl->grid.n_omega * cl->grid.d_omega, "the small window must lie inside the large one");
+    const int n_pair = cl->n_pair;
+    std::vector<double> delta(n_pair);
+    download(ctx, delta.data(), cl->pDelta, n_pair);
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    int P = 0;
+    while (P < n_pair && delta[P] < lam) ++P;        // sorted ascending: the small window's pairs lead
+    std::vector<double> fs(n_pair, 0.0), fl(n_pair, 0.0);
+    std::vector<int> bs(n_pair, 0), bl(n_pair, 0);
+    for (int p = 0; p < n_pair; ++p) {
+        const double x = delta[p] / (p < P ? gs->d_omega : cl->grid.d_omega);
+        const double j = std::floor(x);
+        (p < P ? fs : fl)[p] = x - j;
+        (p < P ? bs : bl)[p] = (int)j;
+    }
+    auto segments = [](const std::vector<int>& bins, int p0, int p1, int& jlo, int& nb) {
+        jlo = bins[p0];
+        nb = bins[p1 - 1] - jlo + 1;
+        std::vector<int> seg(nb + 1);
+        int p = p0;
+        for (int b = 0; b < nb; ++b) {
+            while (p < p1 && bins[p] < jlo + b) ++p;
+            seg[b] = p;
+        }
+        seg[nb] = p1;
+        return seg;
+    };
+    int js = 0, nbs = 0, jl = 0, nbl = 0;
+    std::vector<int> seg_s, seg_l;
+    if (P > 0) seg_s = segments(bs, 0, P, js, nbs);
+    if (P < n_pair) seg_l = segments(bl, P, n_pair, jl, nbl);
+    const int band_s = P > 0 ? nbs + 1 : 0, band_l = P < n_pair ? nbl + 1 : 0;
+    gw_chi0* c = new gw_chi0();
+    c->ctx = ctx; c->mol = cl->mol; c->grid = *gs; c->prec = cl->prec;
+    c->n_pair = n_pair; c->n_rank = cl->n_rank; c->n_sub = cl->n_sub;
+    c->j_lo = js; c->nb_bins = nbs; c->j_hi = js + nbs;
+    c->large = cl; c->lam_cut = lam;
+    const long long n_el = tri(c->n_sub);
+    const size_t rz = c->prec == GW_MIXED ? sizeof(float) : sizeof(double);
+    int *dseg_s = nullptr, *dseg_l = nullptr;
+    double *dfs = nullptr, *dfl = nullptr;
+    void* A = nullptr;
+    try {
+        const size_t nz = (size_t)c->mol->n_prod * c->n_sub;
+        c->Zup = dalloc<double>(ctx, nz);
+        CUDA_CHECK(cudaMemcpyAsync(c->Zup, cl->Zup, nz * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        A = ctx_alloc(ctx, (size_t)(band_s + band_l) * n_el * rz);
+        if (band_s) {
+            dseg_s = upload(ctx, seg_s.data(), seg_s.size());
+            dfs = upload(ctx, fs.data(), fs.size());
+            launch_deposit_range(ctx, cl, dseg_s, dfs, nbs, A);
+        }
+        if (band_l) {
+            dseg_l = upload(ctx, seg_l.data(), seg_l.size());
+            dfl = upload(ctx, fl.data(), fl.size());
+            launch_deposit_range(ctx, cl, dseg_l, dfl, nbl, (char*)A + (size_t)band_s * n_el * rz);
+        }
+        launch_chi0_kk_2w(ctx, c, A, js, band_s, jl, band_l, cl->grid);
+        ctx_finish(ctx, "gw_build_chi0_2w");
+    } catch (...) {
+        ctx_free(ctx, dseg_s); ctx_free(ctx, dseg_l); ctx_free(ctx, dfs); ctx_free(ctx, dfl); ctx_free(ctx, A);
+        chi0_release(c);
+        throw;
+    }
+    ctx_free(ctx, dseg_s); ctx_free(ctx, dseg_l); ctx_free(ctx, dfs); ctx_free(ctx, dfl); ctx_free(ctx, A);
+    return c;
+}
+
+extern "C" gw_status gw_build_chi0_2w(gw_ctx* ctx, const gw_mol* mol, const gw_grid* small, const gw_grid* large,
+                                      gw_precision prec, gw_chi0** small_out, gw_chi0** large_out) {
+    if (!ctx || !small_out || !large_out) return GW_ERR_INVALID_ARG;
+    *small_out = nullptr;
+    *large_out = nullptr;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    gw_chi0* cl = build_chi0(ctx, mol, large, prec);
+    try {
+        *small_out = build_small_window(ctx, cl, small);
+    } catch (...) {
+        chi0_release(cl);
+        throw;
+    }
+    *large_out = cl;
+    API_END
+}
+
 // ======================================================================
 // a5: screening
 // ======================================================================
@@ -729,17 +830,21 @@ static void sigma_release(gw_sigma* s) {
     if (!s) return;
     gw_ctx* x = s->ctx;
     ctx_free(x, s->c); ctx_free(x, s->sig); ctx_free(x, s->sigc); ctx_free(x, s->sx); ctx_free(x, s->eks);
+    ctx_free(x, s->c2); ctx_free(x, s->sig2);
     delete s;
 }
 
-static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n_states) {
+static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n_states, const gw_W* W2 = nullptr) {
     REQUIRE(W && W->ctx == ctx, "W belongs to another context");
+    REQUIRE(!W2 || (W2->ctx == ctx && W->chi0->large == W2->chi0),
+            "the second window's W must be the large window of the first's chi0");
+    REQUIRE(W2 || !W->chi0->large, "a small window's W needs its large window (gw_sigma_diag_2w)");
     REQUIRE(states && n_states > 0, "empty state list");
     const gw_chi0* c = W->chi0;
     const gw_mol* mol = c->mol;
     for (int i = 0; i < n_states; ++i) REQUIRE(states[i] >= 0 && states[i] < mol->n_orb, "state index out of range");
     gw_sigma* s = new gw_sigma();
-    s->ctx = ctx; s->W = W; s->n_states = n_states; s->states.assign(states, states + n_states);
+    s->ctx = ctx; s->W = W; s->W2 = W2; s->n_states = n_states; s->states.assign(states, states + n_states);
     const int n_orb = mol->n_orb, n_prod = mol->n_prod, n_sub = c->n_sub, N = c->grid.n_omega;
     const int R = n_states * n_orb;
     s->R = R;
@@ -795,11 +900,35 @@ static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n
         s->c = dalloc<double>(ctx, (size_t)R * N);
         launch_forms(ctx, W, Q, R, s->c);
         launch_pole_forms(ctx, W, Q, R, s->c);      // near-pole frequencies in binary64 (policy on)
+        if (W2) {
+            // second window (R10): the small window's forms for s2 < lam, the large
+            // window's for s2 >= lam
+            const gw_grid& gl = W2->chi0->grid;
+            const int NL = gl.n_omega;
+            s->c2 = dalloc<double>(ctx, (size_t)R * NL);
+            launch_forms(ctx, W2, Q, R, s->c2);
+            launch_pole_forms(ctx, W2, Q, R, s->c2);
+            const double lam = c->lam_cut;
+            int jcut = 0;
+            while (jcut < NL && (double)jcut * gl.d_omega < lam) ++jcut;
+            CUDA_CHECK(cudaMemset2DAsync(s->c + (N - 1), sizeof(double) * N, 0, sizeof(double), R, ctx->stream));
+            if (jcut > 0)
+                CUDA_CHECK(cudaMemset2DAsync(s->c2, sizeof(double) * NL, 0, sizeof(double) * jcut, R, ctx->stream));
+            const double dwl = gl.d_omega;
+            double jmin = std::floor(mol->h_eps.front() / dwl), jmax = std::floor(mol->h_eps.back() / dwl);
+            s->j0_2 = (int)jmin - (NL - 1);
+            s->n_sig2 = ((int)jmax + NL) - s->j0_2 + 1;
+        }
         // sigma_n(s), Sigma_c grid
         s->sig = dalloc<double>(ctx, (size_t)n_states * s->n_sig);
         launch_sigma_grid(ctx, s);
         s->sigc = dalloc<double2>(ctx, (size_t)n_states * (2 * N - 1));
         launch_sigma_c(ctx, s);
+        if (W2) {
+            s->sig2 = dalloc<double>(ctx, (size_t)n_states * s->n_sig2);
+            launch_sigma_grid2(ctx, s);
+            launch_sigma_c2(ctx, s);
+        }
         // Sigma_x = -sum_{k occ} V^{nk} v V^{nk}
         s->sx = dalloc<double>(ctx, n_states);
         launch_sigma_x(ctx, s, Vnk, T, R);
@@ -820,6 +949,16 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states
     API_BEGIN(ctx)
     CUDA_CHECK(cudaSetDevice(ctx->device));
     *out = sigma_diag(ctx, W, states, n_states);
+    API_END
+}
+
+extern "C" gw_status gw_sigma_diag_2w(gw_ctx* ctx, const gw_W* W_small, const gw_W* W_large, const int* states,
+                                      int n_states, gw_sigma** out) {
+    if (!ctx || !out || !W_large) return GW_ERR_INVALID_ARG;
+    *out = nullptr;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    *out = sigma_diag(ctx, W_small, states, n_states, W_large);
     API_END
 }
 
@@ -936,6 +1075,7 @@ extern "C" gw_status gw_chi0_copy_pairs(gw_ctx* ctx, const gw_chi0* c, int* E, i
                                         double* delta, int* bin, double* frac) {
     if (!ctx || !c) return GW_ERR_INVALID_ARG;
     API_BEGIN(ctx)
+    REQUIRE(!c->large, "a small window keeps no pair table; read the large window's");
     CUDA_CHECK(cudaSetDevice(ctx->device));
     if (E) download(ctx, E, c->pE, c->n_pair);
     if (F) download(ctx, F, c->pF, c->n_pair);
@@ -969,6 +1109,7 @@ extern "C" gw_status gw_chi0_copy_basis(gw_ctx* ctx, const gw_chi0* c, double* Z
 extern "C" gw_status gw_chi0_copy_U(gw_ctx* ctx, const gw_chi0* c, double* U) {
     if (!ctx || !c || !U) return GW_ERR_INVALID_ARG;
     API_BEGIN(ctx)
+    REQUIRE(!c->large, "a small window keeps no U; read the large window's");
     CUDA_CHECK(cudaSetDevice(ctx->device));
     std::vector<double> t((size_t)c->n_sub * c->n_pair);
     if (c->Ut) {
@@ -989,6 +1130,7 @@ extern "C" gw_status gw_chi0_copy_spectral(gw_ctx* ctx, const gw_chi0* c, int j0
     if (!ctx || !c || !A) return GW_ERR_INVALID_ARG;
     API_BEGIN(ctx)
     CUDA_CHECK(cudaSetDevice(ctx->device));
+    REQUIRE(!c->large, "spectral weights of a small window are not kept; read the large window's");
     REQUIRE(nj >= 0 && j0 >= 0 && j0 + nj <= c->grid.n_omega, "bin range outside the grid");
     size_t n = (size_t)nj * c->n_sub * c->n_sub;
     double* d = dalloc<double>(ctx, std::max<size_t>(n, 1));
@@ -1151,6 +1293,24 @@ extern "C" gw_status gw_sigma_copy(gw_ctx* ctx, const gw_sigma* s, double* c, do
     if (sigma_x) download(ctx, sigma_x, s->sx, s->n_states);
     CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
     API_END
+}
+
+extern "C" gw_status gw_sigma_copy_large(gw_ctx* ctx, const gw_sigma* s, double* c, double* sigma) {
+    if (!ctx || !s || !s->W2) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    const int NL = s->W2->chi0->grid.n_omega;
+    if (c) download(ctx, c, s->c2, (size_t)s->R * NL);
+    if (sigma) download(ctx, sigma, s->sig2, (size_t)s->n_states * s->n_sig2);
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    API_END
+}
+
+extern "C" gw_status gw_sigma_grid_large(const gw_sigma* s, int* j0, int* n_sig) {
+    if (!s || !s->W2 || !j0 || !n_sig) return GW_ERR_INVALID_ARG;
+    *j0 = s->j0_2;
+    *n_sig = s->n_sig2;
+    return GW_OK;
 }
 
 extern "C" gw_status gw_sigma_grid(const gw_sigma* s, int* j0, int* n_sig) {

@@ -480,6 +480,25 @@ void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c) {
     ctx_free(ctx, A);
 }
 
+// Weights of a contiguous range of sorted pairs on any grid (second window
+// technique): seg [nb_bins + 1] holds absolute pair indices, frac the tent
+// fractions of the pairs on that grid; A [nb_bins + 1][n_el] in the working
+// precision of the chi0 handle.
+void launch_deposit_range(gw_ctx* ctx, const gw_chi0* c, const int* seg, const double* frac, int nb_bins, void* A) {
+    const int n = c->n_sub, band = nb_bins + 1;
+    const long long n_el = (long long)n * (n + 1) / 2;
+    const int nt = div_up(n, 64), tiles = nt * (nt + 1) / 2;
+    const int BC = std::max(1, (int)std::min<long long>(band, (long long)tiles * band / (8LL * ctx->num_sms)));
+    const int nbc = div_up(band, BC);
+    if (nbc > 65535) gw_throw(GW_ERR_INVALID_ARG, "spectral band too wide for the deposit kernel");
+    if (c->prec == GW_MIXED)
+        klaunch(ctx, "k_deposit_syrk32", k_deposit_syrk<float>, dim3(tiles, nbc), 256, 0, (const float*)c->Ut32,
+                c->n_pair, n, seg, frac, nb_bins, BC, n_el, (float*)A, (uint32_t*)nullptr, 0LL);
+    else
+        klaunch(ctx, "k_deposit_syrk", k_deposit_syrk<double>, dim3(tiles, nbc), 256, 0, (const double*)c->Ut,
+                c->n_pair, n, seg, frac, nb_bins, BC, n_el, (double*)A, (uint32_t*)nullptr, 0LL);
+}
+
 // Binary64 spectral weights A64 [band][n_el] of the binary32 path (near-pole
 // policy), deposited from the binary64 U^T.
 void launch_spectral64(gw_ctx* ctx, gw_chi0* c) {

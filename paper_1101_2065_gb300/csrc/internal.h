@@ -139,6 +139,9 @@ struct gw_chi0 {
     float* Ut32 = nullptr;
     float2* chi0_32 = nullptr;       // [n_omega][tri(n_sub)] binary32 path
     double* A64 = nullptr;           // [band][tri(n_sub)] binary64 weights (binary32 path, near-pole policy)
+    // second window technique: the small window's handle refers to the large one's
+    const gw_chi0* large = nullptr;  // set on the small window's handle
+    double lam_cut = 0.0;            // spectral arguments below it belong to the small window
 };
 
 struct gw_W {
@@ -166,6 +169,11 @@ struct gw_sigma {
     double2* sigc = nullptr;         // [n_states*(2N-1)]
     double* sx = nullptr;            // [n_states]
     double* eks = nullptr;           // [n_states]
+    // second window technique: the large window's forms and sigma (W2 = its factors)
+    const gw_W* W2 = nullptr;
+    int j0_2 = 0, n_sig2 = 0;
+    double* c2 = nullptr;            // [R*n_omega_large]
+    double* sig2 = nullptr;          // [n_states*n_sig2]
 };
 
 // ------------------------------------------------------------------ launchers
@@ -195,6 +203,10 @@ void launch_fft_tables(gw_ctx* ctx, gw_chi0* c);
 void launch_chi0_fft(gw_ctx* ctx, gw_chi0* c);           // binary64: deposit + FFT
 void launch_chi0_kk32(gw_ctx* ctx, gw_chi0* c);          // binary32: deposit + Cauchy sum
 void launch_spectral64(gw_ctx* ctx, gw_chi0* c);         // binary64 weights A64 from c->Ut
+void launch_deposit_range(gw_ctx* ctx, const gw_chi0* c, const int* seg, const double* frac, int nb_bins, void* A);
+// second window: chi0 of c (small window grid) from [small bins; large bins] weights A
+void launch_chi0_kk_2w(gw_ctx* ctx, gw_chi0* c, const void* A, int js, int band_s, int jl, int band_l,
+                       const gw_grid& gl);
 // kk_tc.cu: chi0_32 from the TF32 hi/lo weight images (kk_layout.cuh)
 void launch_chi0_kk_tc(gw_ctx* ctx, gw_chi0* c, const uint32_t* Asplit);
 void launch_chi0_kk_fma(gw_ctx* ctx, gw_chi0* c, const float* A);   // A[band][n_el]
@@ -221,6 +233,9 @@ void launch_pole_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, doubl
 // sigma.cu
 void launch_sigma_grid(gw_ctx* ctx, gw_sigma* s);
 void launch_sigma_c(gw_ctx* ctx, gw_sigma* s);
+// second window: the large window's sigma (from s->c2) and its Cauchy sum added to s->sigc
+void launch_sigma_grid2(gw_ctx* ctx, gw_sigma* s);
+void launch_sigma_c2(gw_ctx* ctx, gw_sigma* s);
 void launch_sigma_x(gw_ctx* ctx, gw_sigma* s, const double* Vnk, const double* T, int ld);
 void launch_qp(gw_ctx* ctx, const gw_sigma* s, const double* vxc, double* e, double* z, int* st);
 // utilities (misc kernels in linalg.cu)

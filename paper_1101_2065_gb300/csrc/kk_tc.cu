@@ -388,6 +388,82 @@ __global__ void __launch_bounds__(256) k_chi0_kk_fma(const float2* __restrict__ 
 
 }  // namespace
 
+// ----------------------------------------------------------------------
+// Second window technique (Sec. 4.2, Eq. win2-for-response): chi0 on the
+// small window's grid w_k = k dws takes the small window's bins (s = j dws,
+// broadening eta_s) and the large window's truncated bins (s = j dwl,
+// broadening eta_l) in one band sum: the kernel table holds both blocks of
+// rows, the weights both blocks of bins.
+namespace {
+
+template <typename C>
+__global__ void k_kk_ctable_2w(int N, double dws, int js, int band_s, double eta_s, double dwl, int jl, int band_l,
+                               double eta_l, C* __restrict__ Kc) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int band = band_s + band_l;
+    if (t >= (long long)N * band) return;
+    const int b = (int)(t / N), k = (int)(t % N);
+    const double w = (double)k * dws;
+    const double sb = b < band_s ? (double)(js + b) * dws : (double)(jl + b - band_s) * dwl;
+    const double eta = b < band_s ? eta_s : eta_l;
+    const double x1 = w - sb, x2 = w + sb, e2 = eta * eta;
+    const double d1 = x1 * x1 + e2, d2 = x2 * x2 + e2;
+    const double re = x1 / d1 - x2 / d2, im = -eta / d1 + eta / d2;
+    if constexpr (sizeof(C) == 8) Kc[t] = make_float2((float)re, (float)im);
+    else Kc[t] = make_double2(re, im);
+}
+
+// binary64 band sum chi0[k][e] = sum_b A[b][e] Kc[b][k]: one thread per
+// element, the CTA's frequency row of the table in shared memory.
+__global__ void __launch_bounds__(256) k_chi0_kk64(const double2* __restrict__ Kc, const double* __restrict__ A,
+                                                   int N, int band, long long n_el, double2* __restrict__ chi0) {
+    extern __shared__ double2 krow[];
+    const int k = blockIdx.y;
+    for (int b = threadIdx.x; b < band; b += blockDim.x) krow[b] = Kc[(long long)b * N + k];
+    __syncthreads();
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_el) return;
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < band; ++b) {
+        const double a = A[(long long)b * n_el + e];
+        re = fma(a, krow[b].x, re);
+        im = fma(a, krow[b].y, im);
+    }
+    chi0[(long long)k * n_el + e] = make_double2(re, im);
+}
+
+}  // namespace
+
+void launch_chi0_kk_2w(gw_ctx* ctx, gw_chi0* c, const void* A, int js, int band_s, int jl, int band_l,
+                       const gw_grid& gl) {
+    const int N = c->grid.n_omega, band = band_s + band_l;
+    const long long n_el = tri(c->n_sub);
+    const bool f32 = c->prec == GW_MIXED;
+    void* Kc = ctx_alloc(ctx, (size_t)N * band * (f32 ? sizeof(float2) : sizeof(double2)));
+    try {
+        const int nb = div_up((long long)N * band, 256);
+        if (f32) {
+            klaunch(ctx, "k_kk_ctable", k_kk_ctable_2w<float2>, nb, 256, 0, N, c->grid.d_omega, js, band_s,
+                    c->grid.eta, gl.d_omega, jl, band_l, gl.eta, (float2*)Kc);
+            if (!c->chi0_32) c->chi0_32 = dalloc<float2>(ctx, (size_t)N * n_el);
+            const long long net = (n_el + FE - 1) / FE;
+            klaunch(ctx, "k_chi0_kk_fma", k_chi0_kk_fma, dim3((unsigned)net, (unsigned)div_up(N, FK)), 256, 0,
+                    (const float2*)Kc, (const float*)A, N, band, n_el, c->chi0_32);
+        } else {
+            klaunch(ctx, "k_kk_ctable", k_kk_ctable_2w<double2>, nb, 256, 0, N, c->grid.d_omega, js, band_s,
+                    c->grid.eta, gl.d_omega, jl, band_l, gl.eta, (double2*)Kc);
+            if (!c->chi0) c->chi0 = dalloc<double2>(ctx, (size_t)N * n_el);
+            if ((size_t)band * sizeof(double2) > 48 * 1024) gw_throw(GW_ERR_INVALID_ARG, "spectral band too wide");
+            klaunch(ctx, "k_chi0_kk64", k_chi0_kk64, dim3((unsigned)div_up(n_el, 256), (unsigned)N), 256,
+                    sizeof(double2) * band, (const double2*)Kc, (const double*)A, N, band, n_el, c->chi0);
+        }
+    } catch (...) {
+        ctx_free(ctx, Kc);
+        throw;
+    }
+    ctx_free(ctx, Kc);
+}
+
 void launch_chi0_kk_fma(gw_ctx* ctx, gw_chi0* c, const float* A) {
     const int N = c->grid.n_omega, band = c->nb_bins + 1;
     const long long n_el = tri(c->n_sub);

@@ -129,23 +129,42 @@ __device__ void re_sigma(const double* __restrict__ sg, int n_sig, int j0, doubl
     der = dw * block_sum(b, red);
 }
 
+// The second window's sigma (large grid), when there is one.
+struct Window2 {
+    const double* sig;               // [n_states * n_sig] or null
+    int n_sig, j0;
+    double dw, eta;
+};
+
 // One CTA per state: linearised start, Newton, bracket scan + bisection.
-__global__ void __launch_bounds__(256) k_qp(const double* __restrict__ sig, int n_sig, int j0, double dw, double eta,
+// With a second window, Re Sigma_c and its derivative add the large
+// window's Cauchy sum (the scan keeps the small window's step).
+__global__ void __launch_bounds__(256) k_qp(const double* __restrict__ sig_, int n_sig, int j0, double dw, double eta,
                                             const double* __restrict__ eks, const double* __restrict__ sx,
                                             const double* __restrict__ vxc, double* __restrict__ e_out,
-                                            double* __restrict__ z_out, int* __restrict__ st_out) {
+                                            double* __restrict__ z_out, int* __restrict__ st_out, Window2 w2) {
     __shared__ double red[33];
     const int s = blockIdx.x;
-    const double* sg = sig + (long long)s * n_sig;
+    const double* sg1 = sig_ + (long long)s * n_sig;
+    const double* sg2 = w2.sig ? w2.sig + (long long)s * w2.n_sig : nullptr;
+    auto re_sig = [&](double E, double& re, double& der) {
+        re_sigma(sg1, n_sig, j0, dw, eta, E, red, re, der);
+        if (sg2) {
+            double re2, der2;
+            re_sigma(sg2, w2.n_sig, w2.j0, w2.dw, w2.eta, E, red, re2, der2);
+            re += re2;
+            der += der2;
+        }
+    };
     const double e_ks = eks[s], sig_x = sx[s];
     const double v_xc = vxc ? vxc[s] : sig_x;
     double re, der;
-    re_sigma(sg, n_sig, j0, dw, eta, e_ks, red, re, der);
+    re_sig(e_ks, re, der);
     const double E1 = e_ks + (sig_x - v_xc + re) / (1.0 - der);
     double E = E1;
     bool ok = false;
     for (int it = 0; it < 100; ++it) {
-        re_sigma(sg, n_sig, j0, dw, eta, E, red, re, der);
+        re_sig(E, re, der);
         double f = E - e_ks - sig_x + v_xc - re, df = 1.0 - der;
         if (!isfinite(f) || !isfinite(df) || df == 0.0) break;
         double step = f / df;
@@ -160,7 +179,7 @@ __global__ void __launch_bounds__(256) k_qp(const double* __restrict__ sig, int 
         double bestd = 0.0, fprev = 0.0, xprev = 0.0, fbest = 0.0;
         for (int i = 0; i <= n; ++i) {
             double x = E1 - 0.5 + (double)i * dw;
-            re_sigma(sg, n_sig, j0, dw, eta, x, red, re, der);
+            re_sig(x, re, der);
             double f = x - e_ks - sig_x + v_xc - re;
             if (i > 0 && (fprev == 0.0 || fprev * f < 0.0)) {
                 double mid = 0.5 * (xprev + x);
@@ -177,7 +196,7 @@ __global__ void __launch_bounds__(256) k_qp(const double* __restrict__ sig, int 
             for (int it = 0; it < 200; ++it) {
                 if (b - a < 1e-11) break;
                 double m = 0.5 * (a + b);
-                re_sigma(sg, n_sig, j0, dw, eta, m, red, re, der);
+                re_sig(m, re, der);
                 double fm = m - e_ks - sig_x + v_xc - re;
                 if (((fm < 0.0) == (fa < 0.0)) && fm != 0.0) { a = m; fa = fm; }
                 else b = m;
@@ -186,7 +205,7 @@ __global__ void __launch_bounds__(256) k_qp(const double* __restrict__ sig, int 
             status = 1;
         }
     }
-    re_sigma(sg, n_sig, j0, dw, eta, E, red, re, der);
+    re_sig(E, re, der);
     if (threadIdx.x == 0) {
         e_out[s] = E;
         z_out[s] = 1.0 / (1.0 - der);
@@ -228,6 +247,60 @@ void launch_sigma_x(gw_ctx* ctx, gw_sigma* s, const double* Vnk, const double* T
 
 void launch_qp(gw_ctx* ctx, const gw_sigma* s, const double* vxc, double* e, double* z, int* st) {
     const gw_chi0* c = s->W->chi0;
+    Window2 w2{nullptr, 0, 0, 0.0, 0.0};
+    if (s->W2) w2 = {s->sig2, s->n_sig2, s->j0_2, s->W2->chi0->grid.d_omega, s->W2->chi0->grid.eta};
     klaunch(ctx, "k_qp", k_qp, s->n_states, 256, 0, s->sig, s->n_sig, s->j0, c->grid.d_omega, c->grid.eta, s->eks, s->sx,
-                                               vxc, e, z, st);
+                                               vxc, e, z, st, w2);
+}
+
+// Second window: sigma of the large window's forms on the large grid.
+void launch_sigma_grid2(gw_ctx* ctx, gw_sigma* s) {
+    const gw_chi0* c = s->W2->chi0;
+    const gw_mol* mol = c->mol;
+    long long tot = (long long)s->n_states * s->n_sig2;
+    size_t smem = mol->n_orb * (sizeof(double) + sizeof(int));
+    klaunch(ctx, "k_sigma_grid", k_sigma_grid, div_up(tot, 256), 256, smem, s->c2, mol->eps, mol->n_orb, mol->n_occ,
+            c->grid.n_omega, c->grid.d_omega, s->j0_2, s->n_sig2, s->n_states, s->sig2);
+}
+
+namespace {
+// sigc[s][k] += dwl sum_j sig2_j / (w_k - s_j + i eta_l sgn(s_j)), w_k = k dws,
+// s_j = (j0_2 + j) dwl: the large window's Cauchy sum at the small grid's
+// points, one warp per output, direct divisions (Eq. Cauchy1, R7).
+__global__ void __launch_bounds__(256) k_sigma_c2(const double* __restrict__ sig2, int n_sig2, int j0_2, double dwl,
+                                                  double eta_l, int N, double dws, int n_states,
+                                                  double2* __restrict__ out) {
+    const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nk = 2 * N - 1;
+    if (t >= (long long)n_states * nk) return;
+    const int st = (int)(t / nk);
+    const double w = (double)((int)(t % nk) - (N - 1)) * dws;
+    const double* sg = sig2 + (long long)st * n_sig2;
+    double re = 0.0, im = 0.0;
+    for (int q = lane; q < n_sig2; q += 32) {
+        const int j = j0_2 + q;
+        const double x = w - (double)j * dwl, e = j >= 0 ? eta_l : -eta_l;
+        const double den = x * x + e * e, v = sg[q];
+        re = fma(v, x / den, re);
+        im = fma(v, -e / den, im);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+        double2 v = out[t];
+        out[t] = make_double2(v.x + dwl * re, v.y + dwl * im);
+    }
+}
+}  // namespace
+
+void launch_sigma_c2(gw_ctx* ctx, gw_sigma* s) {
+    const gw_chi0* cs = s->W->chi0;
+    const gw_chi0* cl = s->W2->chi0;
+    const int N = cs->grid.n_omega;
+    long long tot = (long long)s->n_states * (2 * N - 1) * 32;
+    klaunch(ctx, "k_sigma_c2", k_sigma_c2, div_up(tot, 256), 256, 0, s->sig2, s->n_sig2, s->j0_2, cl->grid.d_omega,
+            cl->grid.eta, N, cs->grid.d_omega, s->n_states, s->sigc);
 }

@@ -102,6 +102,10 @@ def load(path: str | None = None):
         "gw_W_copy_pivots": ([P, P, P], I),
         "gw_chi0_copy_elements": ([P, P, P, P, I, P], I),
         "gw_build_chi0_thr": ([P, P, C.POINTER(Grid), I, D, D, pp], I),
+        "gw_build_chi0_2w": ([P, P, C.POINTER(Grid), C.POINTER(Grid), I, pp, pp], I),
+        "gw_sigma_diag_2w": ([P, P, P, P, I, pp], I),
+        "gw_sigma_copy_large": ([P, P, P, P], I),
+        "gw_sigma_grid_large": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int)], I),
         "gw_W_pole_freqs": ([P, P], I),
         "gw_W_copy_full": ([P, P, P, I, P], I),
         "gw_sigma_copy": ([P, P, P, P, P, P], I),
@@ -352,6 +356,16 @@ class Sigma(_Handle):
         _check(self.ctx, load().gw_sigma_grid(self.handle, C.byref(j0), C.byref(ns)))
         return j0.value, ns.value
 
+    def copy_large(self):
+        """Second window: the large window's c and sigma."""
+        j0, ns2 = C.c_int(), C.c_int()
+        _check(self.ctx, load().gw_sigma_grid_large(self.handle, C.byref(j0), C.byref(ns2)))
+        NL = self.W2.chi0.n_omega
+        c = np.zeros((len(self.states), self.n_orb, NL))
+        sig = np.zeros((len(self.states), ns2.value))
+        _check(self.ctx, load().gw_sigma_copy_large(self.ctx.handle, self.handle, _ptr(c), _ptr(sig)))
+        return dict(c=c, sigma=sig, j0=j0.value)
+
     def copy(self):
         j0, n_sig = self.grid()
         ns, N = len(self.states), self.n_omega
@@ -392,6 +406,38 @@ def gw_build_chi0_thr(ctx, mol, grid, prec=GW_FP64, e_threshold=1.0, lambda_rel=
     c = Chi0(ctx, h)
     c.mol, c.n_omega = mol, int(grid.n_omega)
     return c
+
+
+def gw_build_chi0_2w(ctx, mol, small, large, prec=GW_FP64):
+    """Second window technique (Sec. 4.2): (chi0 on the small grid, chi0 on the large grid)."""
+    gs, gl = make_grid(small), make_grid(large)
+    hs, hl = C.c_void_p(), C.c_void_p()
+    _check(ctx, load().gw_build_chi0_2w(ctx.handle, mol.handle, C.byref(gs), C.byref(gl), int(prec), C.byref(hs),
+                                        C.byref(hl)))
+    cs, cl = Chi0(ctx, hs), Chi0(ctx, hl)
+    cs.mol, cs.n_omega, cl.mol, cl.n_omega = mol, int(small.n_omega), mol, int(large.n_omega)
+    return cs, cl
+
+
+def gw_sigma_diag_2w(ctx, W_small, W_large, states):
+    st = np.ascontiguousarray(states, np.int32)
+    h = C.c_void_p()
+    _check(ctx, load().gw_sigma_diag_2w(ctx.handle, W_small.handle, W_large.handle, _ptr(st), st.size, C.byref(h)))
+    s = Sigma(ctx, h, st, W_small.chi0.mol.n_orb, W_small.chi0.n_omega)
+    s.W, s.W2 = W_small, W_large
+    return s
+
+
+def solve_two_window(ctx, mol, small, large, states=None, prec=GW_FP64, vxc=None, Z=None):
+    """Second window technique, device resident; returns (handles, e_qp, z, status)."""
+    if states is None:
+        states = [mol.n_occ - 1, mol.n_occ]
+    m = gw_mol_upload(ctx, mol, Z)
+    cs, cl = gw_build_chi0_2w(ctx, m, small, large, prec)
+    ws, wl = gw_screen_W(ctx, cs), gw_screen_W(ctx, cl)
+    s = gw_sigma_diag_2w(ctx, ws, wl, states)
+    e, z, st = gw_qp_solve(ctx, s, vxc)
+    return dict(mol=m, chi0=cs, chi0_large=cl, W=ws, W_large=wl, sigma=s), e, z, st
 
 
 def gw_screen_W(ctx, chi0):

@@ -35,7 +35,8 @@ def _run(gwlib, ctx, mol, grid, prec, e_th, lam):
 def test_threshold_compression_matches_oracle(gwlib, ctx, cfg2, ring_thr):
     mol, grid = cfg2
     r = ring_thr
-    for prec, tol_w, tol_e in ((gwlib.GW_FP64, 1e-10, 1e-9), (gwlib.GW_MIXED, 1e-4, MEV)):
+    # binary32: the basis comes from binary32 eigenvectors of g, so W (own basis) within 3e-4
+    for prec, tol_w, tol_e in ((gwlib.GW_FP64, 1e-10, 1e-9), (gwlib.GW_MIXED, 3e-4, MEV)):
         h, e, st = _run(gwlib, ctx, mol, grid, prec, E_TH, LAM)
         try:
             info = h["chi0"].info()
