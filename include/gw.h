@@ -229,6 +229,23 @@ gw_status gw_sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n_sta
  * gw_sigma_copy_large the large window's c and sigma. */
 gw_status gw_sigma_diag_2w(gw_ctx* ctx, const gw_W* W_small, const gw_W* W_large, const int* states,
                            int n_states, gw_sigma** out);
+/* Self-energy as a matrix over a set of states (Sec. 3, Eqs.
+ * tensorform-self-energy and instantaneous; at most 16 states): Sigma_c,nm
+ * on w_k = k d_omega, |k| < n_omega, from the forms c_nm,k = q_nk^T gamma
+ * q_mk (obtained by polarisation from the quadratic forms of q_nk and
+ * q_nk + q_mk), shifted by E_k and Cauchy-summed as the diagonal;
+ * Sigma_x,nm = -sum_{k occ} V^{nk} v V^{mk}.  The handle is consumed by
+ * gw_dyson_dos and gw_sigma_matrix_copy (not by gw_qp_solve). */
+gw_status gw_sigma_matrix(gw_ctx* ctx, const gw_W* W, const int* states, int n_states, gw_sigma** out);
+/* sigma_c: host complex [S][S][2 n_omega - 1]; sigma_x: host [S][S]; either may be NULL */
+gw_status gw_sigma_matrix_copy(gw_ctx* ctx, const gw_sigma* s, double* sigma_c, double* sigma_x);
+/* Dyson's equation (Eq. tensorform-dyson) on w_k = k d_omega, |k| < n_omega:
+ * G(w)^-1 = (w + i eta - E_n) delta_nm - Sigma_c,nm(w) - Sigma_x,nm + vxc_nm over
+ * the matrix's states (binary64 Gauss-Jordan per frequency), the states
+ * outside the set non-interacting; dos [2 n_omega - 1] = -(1/pi) Im Tr G.
+ * vxc: host [S][S] or NULL (vxc = Sigma_x).  g_diag: host complex
+ * [S][2 n_omega - 1] = G_nn, or NULL. */
+gw_status gw_dyson_dos(gw_ctx* ctx, const gw_sigma* s, const double* vxc, double* dos, double* g_diag);
 /* a8: E solves E - E_KS - Sigma_x + vxc - Re Sigma_c(E) = 0 per state:
  * linearised start, Newton to |step| < 1e-11 Ha (100 steps, confined to
  * +-0.5 Ha of the start), else bracket scan at step d_omega over +-0.5 Ha

@@ -49,6 +49,9 @@ R10 second window (Sec. 4.2): spectral arguments below lam = (N_s - 1) dw_s
    belong to the small window, the rest to the large one; transitions are
    deposited on the grid of their window, W's forms split the same way, each
    window keeps its own broadening 1.5 dw (see solve_two_window).
+R11 Dyson and DOS (Sec. 3): Sigma as a matrix over a set of states; vxc_nm =
+   Sigma_x_nm by default (as R9); states outside the set keep G0; rho(w) =
+   -(1/pi) Im Tr G(w + i eta) on the grid w_k = k d_omega (see solve_dyson).
 """
 from __future__ import annotations
 
@@ -404,6 +407,78 @@ def qp_solve(e_ks, sig_x, vxc, sig_n, j0, d_omega, eta, second=None):
             E, status = 0.5 * (a + b), 1
     _, der = re_sigma(E)
     return E, 1.0 / (1.0 - der), status
+
+
+# ------------------------------------------------------------------ Dyson equation and DOS
+# Sec. 3 (Eqs. tensorform-self-energy, tensorform-dyson, instantaneous): the
+# self-energy as a matrix over a set of states n, m (the Kohn-Sham basis is
+# orthonormal here, S = 1), Dyson's equation at w + i eta and the density of
+# states rho(w) = -(1/pi) Im Tr G(w + i eta).  Reading R11: vxc_nm = Sigma_x_nm
+# by default (as R9); states outside the set keep G0.
+def sigma_forms_matrix(Vnk, Zup, gamma):
+    """c_nm,k(s_j) = q_nk^T gamma_j q_mk for the states n, m of Vnk (Eq.
+    spectral_3 with a != b): [n_states, n_states, n_orb, N]."""
+    q = Vnk @ Zup                                        # [ns, n_orb, n_sub]
+    ns, no, _ = q.shape
+    GQ = np.einsum("jab,mkb->jmka", gamma, q)            # gamma_j q_mk: [N, ns, no, n_sub]
+    return np.einsum("nka,jmka->nmkj", q, GQ)
+
+
+def sigma_x_matrix(mol, Vnk_occ):
+    """Sigma_x_nm = -sum_{k occ} V^{nk} v V^{mk} (Eq. instantaneous, R8)."""
+    return -np.einsum("nka,ab,mkb->nm", Vnk_occ, mol.v, Vnk_occ)
+
+
+def dyson_dos(eps, states, sigc, sx, vxc, d_omega, eta, n_omega):
+    """Dyson's equation (Eq. tensorform-dyson) on w_k = k d_omega, |k| < N:
+    G(w)^-1 = (w + i eta - E) - (Sigma_c(w) + Sigma_x - vxc) on the state set,
+    G0 outside it; rho(w) = -(1/pi) Im Tr G.  sigc [ns, ns, 2N-1]."""
+    w = np.arange(-(n_omega - 1), n_omega) * d_omega
+    st = np.asarray(states)
+    E = eps[st]
+    others = np.setdiff1d(np.arange(eps.size), st)
+    G = np.zeros((w.size, st.size), complex)
+    rho = np.zeros(w.size)
+    for k in range(w.size):
+        A = np.diag(w[k] + 1j * eta - E) - sigc[:, :, k] - (sx - vxc)
+        Gk = np.linalg.inv(A)
+        G[k] = np.diag(Gk)
+        rho[k] = -np.trace(Gk).imag / math.pi
+    rho += -np.sum((1.0 / (w[:, None] + 1j * eta - eps[others][None, :])).imag, axis=1) / math.pi
+    return w, rho, G
+
+
+def solve_dyson(mol, grid, states, Z=None, vxc="sigma_x"):
+    """Self-energy matrix over `states`, Dyson's equation and the DOS (Sec. 3, R11)."""
+    N, dw, eta = grid.n_omega, grid.d_omega, grid.eta
+    pairs = pair_table(mol.eps, mol.n_occ, dw, N)
+    VEF = pair_vertex(mol, pairs)
+    basis = compression_basis(mol, VEF) if Z is None else dict(Z=Z, Zup=mol.v @ Z)
+    Zup = basis["Zup"]
+    U = compress_pairs(VEF, Zup)
+    chi0 = chi0_cauchy(deposit_spectral(U, pairs, N), dw, eta)
+    gamma = spectral_gamma(screen(chi0), np.arange(N))
+    Vnk = state_vertex(mol, states)
+    c = sigma_forms_matrix(Vnk, Zup, gamma)               # [ns, ns, n_orb, N]
+    ns = len(states)
+    sig, j0 = sigma_grid(c.reshape(ns * ns, mol.eps.size, N), mol.eps, mol.n_occ, dw)
+    sigc = sigma_c_grid(sig, j0, dw, eta, N).reshape(ns, ns, -1)
+    sx = sigma_x_matrix(mol, Vnk[:, :mol.n_occ, :])
+    vx = sx.copy() if isinstance(vxc, str) else np.asarray(vxc, float)
+    w, rho, G = dyson_dos(mol.eps, states, sigc, sx, vx, dw, eta, N)
+    return dict(c=c, sigma=sig.reshape(ns, ns, -1), j0=j0, sigma_c=sigc, sigma_x=sx, vxc=vx, omega=w, dos=rho, G=G,
+                Z=basis["Z"], Zup=Zup)
+
+
+def dos_peak(omega, rho, near):
+    """Position of the DOS maximum nearest to `near`: the local maximum of the
+    sampled rho nearest to it, refined by the parabola through it and its two
+    neighbours."""
+    i = np.arange(1, rho.size - 1)
+    peaks = i[(rho[i] >= rho[i - 1]) & (rho[i] > rho[i + 1])]
+    p = peaks[np.argmin(np.abs(omega[peaks] - near))]
+    a, b, c = rho[p - 1], rho[p], rho[p + 1]
+    return omega[p] + 0.5 * (a - c) / (a - 2.0 * b + c) * (omega[1] - omega[0])
 
 
 # ------------------------------------------------------------------ second window

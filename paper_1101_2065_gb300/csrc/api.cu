@@ -830,12 +830,14 @@ static void sigma_release(gw_sigma* s) {
     if (!s) return;
     gw_ctx* x = s->ctx;
     ctx_free(x, s->c); ctx_free(x, s->sig); ctx_free(x, s->sigc); ctx_free(x, s->sx); ctx_free(x, s->eks);
-    ctx_free(x, s->c2); ctx_free(x, s->sig2);
+    ctx_free(x, s->c2); ctx_free(x, s->sig2); ctx_free(x, s->d_states);
     delete s;
 }
 
-static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n_states, const gw_W* W2 = nullptr) {
+static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n_states, const gw_W* W2 = nullptr,
+                            bool matrix = false) {
     REQUIRE(W && W->ctx == ctx, "W belongs to another context");
+    REQUIRE(!matrix || (!W2 && n_states <= dyson_max_states()), "self-energy matrix: one window, at most 16 states");
     REQUIRE(!W2 || (W2->ctx == ctx && W->chi0->large == W2->chi0),
             "the second window's W must be the large window of the first's chi0");
     REQUIRE(W2 || !W->chi0->large, "a small window's W needs its large window (gw_sigma_diag_2w)");
@@ -896,10 +898,30 @@ static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n
             gemm_f64(ctx, true, false, n_sub, R, n_prod, 1.0, c->Zup, n_sub, Vnk, R, 0.0, Q, R);
             gemm_f64(ctx, false, false, n_prod, R, n_prod, 1.0, mol->v, n_prod, Vnk, R, 0.0, T, R);
         }
-        // c_nk(s_j)
-        s->c = dalloc<double>(ctx, (size_t)R * N);
-        launch_forms(ctx, W, Q, R, s->c);
-        launch_pole_forms(ctx, W, Q, R, s->c);      // near-pole frequencies in binary64 (policy on)
+        // c_nk(s_j); for the matrix, the pairs' right-hand sides q_nk (+ q_mk), then
+        // the off-diagonal forms by polarisation
+        double* Qf = Q;
+        int Rf = R;
+        if (matrix) {
+            const int S = n_states, P = S * (S + 1) / 2;
+            Rf = P * n_orb;
+            Qf = dalloc<double>(ctx, (size_t)n_sub * Rf);
+            launch_pair_rhs(ctx, Q, S, n_orb, n_sub, Qf);
+            s->matrix_S = S;
+            s->n_states = P;
+            s->R = Rf;
+            s->d_states = upload(ctx, states, n_states);
+        }
+        s->c = dalloc<double>(ctx, (size_t)Rf * N);
+        try {
+            launch_forms(ctx, W, Qf, Rf, s->c);
+            launch_pole_forms(ctx, W, Qf, Rf, s->c);      // near-pole frequencies in binary64 (policy on)
+        } catch (...) {
+            if (Qf != Q) ctx_free(ctx, Qf);
+            throw;
+        }
+        if (Qf != Q) ctx_free(ctx, Qf);
+        if (matrix) launch_offdiag(ctx, s->c, s->matrix_S, n_orb, N);
         if (W2) {
             // second window (R10): the small window's forms for s2 < lam, the large
             // window's for s2 >= lam
@@ -920,18 +942,19 @@ static gw_sigma* sigma_diag(gw_ctx* ctx, const gw_W* W, const int* states, int n
             s->n_sig2 = ((int)jmax + NL) - s->j0_2 + 1;
         }
         // sigma_n(s), Sigma_c grid
-        s->sig = dalloc<double>(ctx, (size_t)n_states * s->n_sig);
+        s->sig = dalloc<double>(ctx, (size_t)s->n_states * s->n_sig);
         launch_sigma_grid(ctx, s);
-        s->sigc = dalloc<double2>(ctx, (size_t)n_states * (2 * N - 1));
+        s->sigc = dalloc<double2>(ctx, (size_t)s->n_states * (2 * N - 1));
         launch_sigma_c(ctx, s);
         if (W2) {
             s->sig2 = dalloc<double>(ctx, (size_t)n_states * s->n_sig2);
             launch_sigma_grid2(ctx, s);
             launch_sigma_c2(ctx, s);
         }
-        // Sigma_x = -sum_{k occ} V^{nk} v V^{nk}
-        s->sx = dalloc<double>(ctx, n_states);
-        launch_sigma_x(ctx, s, Vnk, T, R);
+        // Sigma_x = -sum_{k occ} V^{nk} v V^{nk} (matrix: V^{nk} v V^{mk})
+        s->sx = dalloc<double>(ctx, s->n_states);
+        if (matrix) launch_sigma_x_pairs(ctx, s, Vnk, T, R);
+        else launch_sigma_x(ctx, s, Vnk, T, R);
         ctx_finish(ctx, "gw_sigma_diag");
         ctx_free(ctx, Es); ctx_free(ctx, Fs); ctx_free(ctx, Vnk); ctx_free(ctx, Q); ctx_free(ctx, T);
     } catch (...) {
@@ -962,6 +985,72 @@ extern "C" gw_status gw_sigma_diag_2w(gw_ctx* ctx, const gw_W* W_small, const gw
     API_END
 }
 
+extern "C" gw_status gw_sigma_matrix(gw_ctx* ctx, const gw_W* W, const int* states, int n_states, gw_sigma** out) {
+    if (!ctx || !out) return GW_ERR_INVALID_ARG;
+    *out = nullptr;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    *out = sigma_diag(ctx, W, states, n_states, nullptr, true);
+    API_END
+}
+
+extern "C" gw_status gw_sigma_matrix_copy(gw_ctx* ctx, const gw_sigma* s, double* sigma_c, double* sigma_x) {
+    if (!ctx || !s || !s->matrix_S) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    const int S = s->matrix_S, P = s->n_states, nk = 2 * s->W->chi0->grid.n_omega - 1;
+    std::vector<double2> sc((size_t)P * nk);
+    std::vector<double> sx(P);
+    download(ctx, sc.data(), s->sigc, sc.size());
+    download(ctx, sx.data(), s->sx, P);
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    for (int n = 0; n < S; ++n)
+        for (int m = 0; m < S; ++m) {
+            const int a = std::min(n, m), b = std::max(n, m);
+            const int p = a * S - a * (a - 1) / 2 + (b - a);
+            if (sigma_c)
+                std::memcpy(reinterpret_cast<double2*>(sigma_c) + ((size_t)n * S + m) * nk, sc.data() + (size_t)p * nk,
+                            sizeof(double2) * nk);
+            if (sigma_x) sigma_x[n * S + m] = sx[p];
+        }
+    API_END
+}
+
+extern "C" gw_status gw_dyson_dos(gw_ctx* ctx, const gw_sigma* s, const double* vxc, double* dos, double* g_diag) {
+    if (!ctx || !s || !s->matrix_S || !dos) return GW_ERR_INVALID_ARG;
+    API_BEGIN(ctx)
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    const int S = s->matrix_S, P = s->n_states, nk = 2 * s->W->chi0->grid.n_omega - 1;
+    // Sigma_x - vxc per pair (vxc NULL: vxc = Sigma_x, the mean field contains exchange)
+    std::vector<double> d(P, 0.0);
+    if (vxc) {
+        std::vector<double> sx(P);
+        download(ctx, sx.data(), s->sx, P);
+        CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        for (int n = 0; n < S; ++n)
+            for (int m = n; m < S; ++m) {
+                const int p = n * S - n * (n - 1) / 2 + (m - n);
+                d[p] = sx[p] - vxc[n * S + m];
+            }
+    }
+    double *dd = nullptr, *ddos = nullptr;
+    double2* dg = nullptr;
+    try {
+        dd = upload(ctx, d.data(), d.size());
+        ddos = dalloc<double>(ctx, nk);
+        if (g_diag) dg = dalloc<double2>(ctx, (size_t)S * nk);
+        launch_dyson(ctx, s, dd, s->d_states, ddos, dg);
+        download(ctx, dos, ddos, nk);
+        if (g_diag) download(ctx, reinterpret_cast<double2*>(g_diag), dg, (size_t)S * nk);
+        ctx_finish(ctx, "gw_dyson_dos");
+    } catch (...) {
+        ctx_free(ctx, dd); ctx_free(ctx, ddos); ctx_free(ctx, dg);
+        throw;
+    }
+    ctx_free(ctx, dd); ctx_free(ctx, ddos); ctx_free(ctx, dg);
+    API_END
+}
+
 extern "C" void gw_sigma_free(gw_sigma* s) { sigma_release(s); }
 
 // ======================================================================
@@ -969,6 +1058,7 @@ extern "C" void gw_sigma_free(gw_sigma* s) { sigma_release(s); }
 // ======================================================================
 static void qp_solve(gw_ctx* ctx, const gw_sigma* s, const double* vxc, double* e, double* z, int* st) {
     REQUIRE(s && s->ctx == ctx, "sigma belongs to another context");
+    REQUIRE(!s->matrix_S, "a self-energy matrix is solved by gw_dyson_dos");
     REQUIRE(e && z && st, "NULL output array");
     const int ns = s->n_states;
     double* dv = nullptr; double* de = nullptr; double* dz = nullptr; int* ds = nullptr;

@@ -174,6 +174,10 @@ struct gw_sigma {
     int j0_2 = 0, n_sig2 = 0;
     double* c2 = nullptr;            // [R*n_omega_large]
     double* sig2 = nullptr;          // [n_states*n_sig2]
+    // self-energy matrix over matrix_S states (Dyson's equation): the rows of
+    // c, sig, sigc and sx are the pairs n <= m, n_states = S(S+1)/2 of them
+    int matrix_S = 0;
+    int* d_states = nullptr;         // [matrix_S]
 };
 
 // ------------------------------------------------------------------ launchers
@@ -230,6 +234,13 @@ void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* c)
 void launch_ldlt_inverse(gw_ctx* ctx, const gw_W* W, int k, double2* out, double2* work);
 // binary32 path: binary64 factorisation and forms at W->pole_k, overwriting those columns of c
 void launch_pole_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout);
+// dyson.cu: self-energy matrix (pairs n <= m) and Dyson's equation
+int dyson_max_states();
+void launch_pair_rhs(gw_ctx* ctx, const double* Q, int S, int n_orb, int n_sub, double* Qp);
+void launch_offdiag(gw_ctx* ctx, double* c, int S, int n_orb, int N);
+void launch_sigma_x_pairs(gw_ctx* ctx, const gw_sigma* s, const double* Vnk, const double* T, int ld);
+void launch_dyson(gw_ctx* ctx, const gw_sigma* s, const double* sx_minus_vxc, const int* states, double* dos,
+                  double2* g);
 // sigma.cu
 void launch_sigma_grid(gw_ctx* ctx, gw_sigma* s);
 void launch_sigma_c(gw_ctx* ctx, gw_sigma* s);

@@ -103,6 +103,9 @@ def load(path: str | None = None):
         "gw_chi0_copy_elements": ([P, P, P, P, I, P], I),
         "gw_build_chi0_thr": ([P, P, C.POINTER(Grid), I, D, D, pp], I),
         "gw_build_chi0_2w": ([P, P, C.POINTER(Grid), C.POINTER(Grid), I, pp, pp], I),
+        "gw_sigma_matrix": ([P, P, P, I, pp], I),
+        "gw_sigma_matrix_copy": ([P, P, P, P], I),
+        "gw_dyson_dos": ([P, P, P, P, P], I),
         "gw_sigma_diag_2w": ([P, P, P, P, I, pp], I),
         "gw_sigma_copy_large": ([P, P, P, P], I),
         "gw_sigma_grid_large": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int)], I),
@@ -367,8 +370,9 @@ class Sigma(_Handle):
         return dict(c=c, sigma=sig, j0=j0.value)
 
     def copy(self):
+        """c, sigma, Sigma_c, Sigma_x rows: one per state, or per pair n <= m of a matrix."""
         j0, n_sig = self.grid()
-        ns, N = len(self.states), self.n_omega
+        ns, N = getattr(self, "rows", len(self.states)), self.n_omega
         c = np.zeros((ns, self.n_orb, N))
         sig = np.zeros((ns, n_sig))
         sigc = np.zeros((ns, 2 * N - 1), np.complex128)
@@ -393,7 +397,7 @@ def gw_build_chi0(ctx, mol, grid, prec=GW_FP64):
     h = C.c_void_p()
     _check(ctx, load().gw_build_chi0(ctx.handle, mol.handle, C.byref(g), int(prec), C.byref(h)))
     c = Chi0(ctx, h)
-    c.mol, c.n_omega = mol, int(grid.n_omega)
+    c.mol, c.n_omega, c.grid_d_omega = mol, int(grid.n_omega), float(grid.d_omega)
     return c
 
 
@@ -404,7 +408,7 @@ def gw_build_chi0_thr(ctx, mol, grid, prec=GW_FP64, e_threshold=1.0, lambda_rel=
     _check(ctx, load().gw_build_chi0_thr(ctx.handle, mol.handle, C.byref(g), int(prec), float(e_threshold),
                                          float(lambda_rel), C.byref(h)))
     c = Chi0(ctx, h)
-    c.mol, c.n_omega = mol, int(grid.n_omega)
+    c.mol, c.n_omega, c.grid_d_omega = mol, int(grid.n_omega), float(grid.d_omega)
     return c
 
 
@@ -415,7 +419,8 @@ def gw_build_chi0_2w(ctx, mol, small, large, prec=GW_FP64):
     _check(ctx, load().gw_build_chi0_2w(ctx.handle, mol.handle, C.byref(gs), C.byref(gl), int(prec), C.byref(hs),
                                         C.byref(hl)))
     cs, cl = Chi0(ctx, hs), Chi0(ctx, hl)
-    cs.mol, cs.n_omega, cl.mol, cl.n_omega = mol, int(small.n_omega), mol, int(large.n_omega)
+    cs.mol, cs.n_omega, cs.grid_d_omega = mol, int(small.n_omega), float(small.d_omega)
+    cl.mol, cl.n_omega, cl.grid_d_omega = mol, int(large.n_omega), float(large.d_omega)
     return cs, cl
 
 
@@ -438,6 +443,47 @@ def solve_two_window(ctx, mol, small, large, states=None, prec=GW_FP64, vxc=None
     s = gw_sigma_diag_2w(ctx, ws, wl, states)
     e, z, st = gw_qp_solve(ctx, s, vxc)
     return dict(mol=m, chi0=cs, chi0_large=cl, W=ws, W_large=wl, sigma=s), e, z, st
+
+
+def gw_sigma_matrix(ctx, W_, states):
+    """Self-energy matrix over `states` (at most 16) for Dyson's equation."""
+    st = np.ascontiguousarray(states, np.int32)
+    h = C.c_void_p()
+    _check(ctx, load().gw_sigma_matrix(ctx.handle, W_.handle, _ptr(st), st.size, C.byref(h)))
+    s = Sigma(ctx, h, st, W_.chi0.mol.n_orb, W_.chi0.n_omega)
+    s.W = W_
+    s.rows = st.size * (st.size + 1) // 2
+    return s
+
+
+def gw_sigma_matrix_copy(ctx, sigma):
+    S, nk = len(sigma.states), 2 * sigma.n_omega - 1
+    sc = np.zeros((S, S, nk), np.complex128)
+    sx = np.zeros((S, S))
+    _check(ctx, load().gw_sigma_matrix_copy(ctx.handle, sigma.handle, _ptr(sc), _ptr(sx)))
+    return sc, sx
+
+
+def gw_dyson_dos(ctx, sigma, vxc=None):
+    """(omega, dos, G_nn) on w_k = k d_omega, |k| < n_omega (Dyson's equation)."""
+    S, N = len(sigma.states), sigma.n_omega
+    dos = np.zeros(2 * N - 1)
+    g = np.zeros((S, 2 * N - 1), np.complex128)
+    v = None if vxc is None else np.ascontiguousarray(vxc, float)
+    _check(ctx, load().gw_dyson_dos(ctx.handle, sigma.handle, _ptr(v), _ptr(dos), _ptr(g)))
+    w = np.arange(-(N - 1), N) * sigma.W.chi0.grid_d_omega
+    return w, dos, g
+
+
+def dos_peak(omega, rho, near):
+    """Position of the DOS maximum nearest to `near` (the sampled local maximum
+    refined by the parabola through its neighbours): HOMO / LUMO read off the
+    density of states."""
+    i = np.arange(1, rho.size - 1)
+    peaks = i[(rho[i] >= rho[i - 1]) & (rho[i] > rho[i + 1])]
+    p = peaks[np.argmin(np.abs(omega[peaks] - near))]
+    a, b, c = rho[p - 1], rho[p], rho[p + 1]
+    return omega[p] + 0.5 * (a - c) / (a - 2.0 * b + c) * (omega[1] - omega[0])
 
 
 def gw_screen_W(ctx, chi0):

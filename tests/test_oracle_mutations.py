@@ -26,6 +26,11 @@ MUTATIONS = [
      "K_l = 1.0 / (w - s + 1j * gs.eta) - 1.0 / (w + s + 1j * gs.eta)"),
     ("A_l = deposit_spectral(U[~lo], pairs_on_grid(pairs, ~lo, gl), gl.n_omega)",
      "A_l = deposit_spectral(U, pairs_on_grid(pairs, np.ones_like(lo), gl), gl.n_omega)"),
+    # Dyson equation: advanced instead of retarded; Sigma added instead of subtracted
+    ("A = np.diag(w[k] + 1j * eta - E) - sigc[:, :, k] - (sx - vxc)",
+     "A = np.diag(w[k] - 1j * eta - E) - sigc[:, :, k] - (sx - vxc)"),
+    ("A = np.diag(w[k] + 1j * eta - E) - sigc[:, :, k] - (sx - vxc)",
+     "A = np.diag(w[k] + 1j * eta - E) + sigc[:, :, k] - (sx - vxc)"),
     # threshold compression: keep the smallest eigenvalues instead of the largest
     ("keep = np.nonzero(lam >= lambda_rel * lam.max())[0][::-1]", "keep = np.nonzero(lam <= lambda_rel * lam.max())[0]"),
 ]

@@ -475,3 +475,39 @@ def test_two_window_chi0_closed_form_on_nodes():
             k = 1.0 / (w + 1j * eta - d) - 1.0 / (w + 1j * eta + d)
             ref += 2.0 * np.outer(u, u)[None] * k[:, None, None]
     assert np.abs(chi[ks] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def _scaled(mol, t):
+    import copy
+    m = copy.deepcopy(mol)
+    m.vertex = mol.vertex * t
+    return m
+
+
+def test_dyson_matrix_and_dos(cfg1, cfg1_oracle):
+    """Self-energy matrix and Dyson's equation (Sec. 3, Eqs. tensorform-dyson,
+    instantaneous): its diagonal is the diagonal self-energy, it is symmetric;
+    with the vertex scaled by 1e-4 (Sigma_c = O(t^4), Sigma_x cancels vxc) the
+    DOS is the non-interacting one, a Lorentzian of width eta at every
+    Kohn-Sham level; with the vertex scaled by 0.1 the peaks of the HOMO and
+    LUMO spectral functions -Im G_nn / pi sit at the roots of the diagonal
+    quasiparticle equation to within 3 % of the GW shift."""
+    mol, grid = cfg1
+    r = cfg1_oracle
+    st = [mol.n_occ - 1, mol.n_occ]
+    d = gw.solve_dyson(mol, grid, st)
+    diag = np.stack([d["sigma_c"][i, i] for i in range(2)])
+    assert np.linalg.norm(diag - r["sigma_c"]) <= 1e-12 * np.linalg.norm(r["sigma_c"])
+    assert np.abs(np.diag(d["sigma_x"]) - r["sigma_x"]).max() <= 1e-12 * np.abs(r["sigma_x"]).max()
+    assert np.abs(d["sigma_c"] - d["sigma_c"].transpose(1, 0, 2)).max() <= 1e-12 * np.abs(d["sigma_c"]).max()
+    weak = _scaled(mol, 1e-4)
+    d0 = gw.solve_dyson(weak, grid, st)
+    w = d0["omega"]
+    free = -np.sum((1.0 / (w[:, None] + 1j * grid.eta - weak.eps[None, :])).imag, axis=1) / math.pi
+    assert np.abs(d0["dos"] - free).max() <= 1e-9 * free.max()
+    mid = _scaled(mol, 0.1)
+    d1 = gw.solve_dyson(mid, grid, st)
+    r1 = gw.solve(mid, grid, states=st)
+    for i, n in enumerate(st):
+        p = gw.dos_peak(d1["omega"], -d1["G"][:, i].imag / math.pi, r1["e_qp"][i])
+        assert abs(p - r1["e_qp"][i]) < 0.03 * abs(r1["e_qp"][i] - mid.eps[n])
