@@ -160,9 +160,14 @@ gw_status gw_ctx_profile_get(gw_ctx* ctx, const char* kernel_name, double* total
  * poles of W, are factorised again in binary64 (from the binary32 chi0_k)
  * where they are consumed: their quadratic forms in gw_sigma_diag and the
  * read-back of chi^RPA and W.  gw_W_info reports how many (n_pole).
+ * GW_OPT_BARRIER_POLLS (value >= 0, default 0 = about a second): how many
+ * times a CTA of the whole-GPU tridiagonalisation (compression ranks above
+ * about 645) polls a grid barrier before it gives up, flags GW_ERR_TIMEOUT
+ * and returns; the call then fails with GW_ERR_TIMEOUT and the context stays
+ * usable.  A small value exercises that path (tests).
  * GW_ERR_INVALID_ARG for an unknown option or value. */
 enum { GW_OPT_FORMS_SIMT = 2, GW_OPT_SYRK_SIMT = 3, GW_OPT_GEMM_SIMT = 4,
-       GW_OPT_KK_TENSOR = 5, GW_OPT_POLES_FP64 = 6 };
+       GW_OPT_KK_TENSOR = 5, GW_OPT_POLES_FP64 = 6, GW_OPT_BARRIER_POLLS = 7 };
 gw_status gw_ctx_set_option(gw_ctx* ctx, int option, int value);
 
 /* ---------------------------------------------------------------- molecule */
@@ -246,7 +251,10 @@ gw_status gw_sigma_matrix_copy(gw_ctx* ctx, const gw_sigma* s, double* sigma_c, 
  * vxc: host [S][S] or NULL (vxc = Sigma_x).  g_diag: host complex
  * [S][2 n_omega - 1] = G_nn, or NULL. */
 gw_status gw_dyson_dos(gw_ctx* ctx, const gw_sigma* s, const double* vxc, double* dos, double* g_diag);
-/* a8: E solves E - E_KS - Sigma_x + vxc - Re Sigma_c(E) = 0 per state:
+/* a8 (Sec. 2: the quasiparticle equation with the exchange-correlation
+ * potential of the mean field removed, the diagonal approximation of
+ * Dyson's equation Eq. tensorform-dyson):
+ * E solves E - E_KS - Sigma_x + vxc - Re Sigma_c(E) = 0 per state:
  * linearised start, Newton to |step| < 1e-11 Ha (100 steps, confined to
  * +-0.5 Ha of the start), else bracket scan at step d_omega over +-0.5 Ha
  * and bisection.  vxc: host [n_states] or NULL for vxc = Sigma_x (the

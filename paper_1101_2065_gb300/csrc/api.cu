@@ -270,6 +270,10 @@ extern "C" gw_status gw_ctx_set_option(gw_ctx* ctx, int option, int value) {
         ctx->poles_permille = value;
         return GW_OK;
     }
+    if (option == GW_OPT_BARRIER_POLLS && value >= 0) {
+        ctx->barrier_polls = value;
+        return GW_OK;
+    }
     ctx->err = "gw_ctx_set_option: unknown option or value";
     return GW_ERR_INVALID_ARG;
 }

@@ -187,7 +187,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024)
 // Same reduction on the whole GPU for ranks too large for the cluster:
 // cooperative launch, matrix in global memory (L2), three grid barriers per
 // Householder step.
-__device__ bool grid_barrier(unsigned int* bar, int* status, int* s_flag) {
+__device__ bool grid_barrier(unsigned int* bar, int* status, int* s_flag, unsigned long long poll_limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned int* vgen = bar + 1;
@@ -202,7 +202,7 @@ __device__ bool grid_barrier(unsigned int* bar, int* status, int* s_flag) {
         } else {
             unsigned long long polls = 0;
             while (*vgen == gen) {
-                if (++polls > (1ull << 25)) { atomicOr(status, ST_TIMEOUT); ok = 0; break; }
+                if (++polls > poll_limit) { atomicOr(status, ST_TIMEOUT); ok = 0; break; }
                 __nanosleep(32);
             }
         }
@@ -216,7 +216,8 @@ __device__ bool grid_barrier(unsigned int* bar, int* status, int* s_flag) {
 __global__ void __launch_bounds__(512) k_sytrd32_grid(float* __restrict__ A, int n, float* __restrict__ d,
                                                       float* __restrict__ e, float* __restrict__ tau,
                                                       float* __restrict__ vbuf, float* __restrict__ pbuf,
-                                                      float* __restrict__ part, unsigned int* bar, int* status) {
+                                                      float* __restrict__ part, unsigned int* bar, int* status,
+                                                      unsigned long long poll_limit) {
     extern __shared__ float sm[];
     float* sv = sm;          // v
     float* sw = sm + n;      // w
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(512) k_sytrd32_grid(float* __restrict__ A, int
                 rowk[j] = sv[j];
             }
         }
-        if (!grid_barrier(bar, status, &s_flag)) return;
+        if (!grid_barrier(bar, status, &s_flag, poll_limit)) return;
         const float t = tau[k];
         for (int j = tid; j < m; j += blockDim.x) sv[j] = vbuf[j];
         __syncthreads();
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(512) k_sytrd32_grid(float* __restrict__ A, int
         }
         pv = block_sum1024(pv, red);
         if (tid == 0) part[blockIdx.x] = pv;
-        if (!grid_barrier(bar, status, &s_flag)) return;
+        if (!grid_barrier(bar, status, &s_flag, poll_limit)) return;
         float tot = 0.f;
         for (int b = 0; b < (int)gridDim.x; ++b) tot += part[b];
         const float K = 0.5f * t * tot;
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(512) k_sytrd32_grid(float* __restrict__ A, int
             const float vi = sv[i], wi = sw[i];
             for (int j = lane; j < m; j += 32) ri[j] -= vi * sw[j] + wi * sv[j];
         }
-        if (!grid_barrier(bar, status, &s_flag)) return;
+        if (!grid_barrier(bar, status, &s_flag, poll_limit)) return;
     }
     if (blockIdx.x == 0 && tid == 0) {
         if (n >= 2) {
@@ -742,11 +743,14 @@ std::vector<float> eigvals32(gw_ctx* ctx, const double* g, const float* g32, int
             vb = dalloc<float>(ctx, n); pb = dalloc<float>(ctx, n); pt = dalloc<float>(ctx, grid);
             bar = dalloc<unsigned int>(ctx, 2);
             CUDA_CHECK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), ctx->stream));
-            void* args[] = {&A32, (void*)&n, &d, &e, &tau, &vb, &pb, &pt, &bar, &ctx->d_status};
+            // bounded grid barriers: a CTA gives up after poll_limit polls (about a second by default)
+            unsigned long long poll_limit = ctx->barrier_polls ? (unsigned long long)ctx->barrier_polls : (1ull << 25);
+            void* args[] = {&A32, (void*)&n, &d, &e, &tau, &vb, &pb, &pt, &bar, &ctx->d_status, &poll_limit};
             prof_begin(ctx, "k_sytrd32_grid");
             CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)k_sytrd32_grid, dim3(grid), dim3(512), args, smem,
                                                    ctx->stream));
             after_launch(ctx, "k_sytrd32_grid");
+            ctx_finish(ctx, "tridiagonalisation");     // a timed-out barrier stops here, before T is used
         }
         std::vector<float> hd(n), he(n);
         CUDA_CHECK(cudaMemcpyAsync(hd.data(), d, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
@@ -816,11 +820,14 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int 
             pt = dalloc<float>(ctx, grid);
             bar = dalloc<unsigned int>(ctx, 2);
             CUDA_CHECK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), ctx->stream));
-            void* args[] = {&A32, (void*)&n, &d, &e, &tau, &vb, &pb, &pt, &bar, &ctx->d_status};
+            // bounded grid barriers: a CTA gives up after poll_limit polls (about a second by default)
+            unsigned long long poll_limit = ctx->barrier_polls ? (unsigned long long)ctx->barrier_polls : (1ull << 25);
+            void* args[] = {&A32, (void*)&n, &d, &e, &tau, &vb, &pb, &pt, &bar, &ctx->d_status, &poll_limit};
             prof_begin(ctx, "k_sytrd32_grid");
             CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)k_sytrd32_grid, dim3(grid), dim3(512), args, smem,
                                                    ctx->stream));
             after_launch(ctx, "k_sytrd32_grid");
+            ctx_finish(ctx, "tridiagonalisation");     // a timed-out barrier stops here, before T is used
         }
         // Gershgorin bound of T (host needs d, e: small copy)
         std::vector<float> hd(n), he(n);

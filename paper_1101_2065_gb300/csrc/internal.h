@@ -51,6 +51,7 @@ struct gw_ctx {
     bool gemm_simt = false;          // GW_OPT_GEMM_SIMT
     bool kk_tensor = false;          // GW_OPT_KK_TENSOR
     int poles_permille = 0;          // GW_OPT_POLES_FP64 (0 = off)
+    int barrier_polls = 0;           // GW_OPT_BARRIER_POLLS (0 = default limit)
     // optional CUDA-event timing of kernel launches whose name matches prof_filter
     bool prof_on = false;
     std::string prof_filter;

@@ -28,6 +28,7 @@ GW_OPT_SYRK_SIMT = 3
 GW_OPT_GEMM_SIMT = 4
 GW_OPT_KK_TENSOR = 5
 GW_OPT_POLES_FP64 = 6
+GW_OPT_BARRIER_POLLS = 7
 
 
 class GWError(RuntimeError):
