@@ -514,10 +514,10 @@ static gw_chi0* build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid, 
                 Bsel = nullptr;
             } else {
                 // mixed: g only feeds the binary32 eigensolver, so it is formed in
-                // binary32; the basis Z = X_r B, Zup = v Z is formed in binary64
-                // from the kept (re-orthonormalised) vectors and scaled by the
-                // binary64 Rayleigh quotients Z_j^T v Z_j, so Z^T v Z has a unit
-                // diagonal to binary64 accuracy (no binary64 refinement)
+                // binary32; the basis Z = X_r B and Zup = v Z are binary32 products
+                // of the kept (re-orthonormalised) vectors, scaled by the binary64
+                // quotients Z_j^T Zup_j, so that Z^T Zup has a unit diagonal (Z^T v Z
+                // with the binary64 v one to binary32 accuracy; no binary64 refinement)
                 float* v32 = dalloc<float>(ctx, (size_t)n_prod * n_prod);
                 float* X32 = dalloc<float>(ctx, (size_t)n_prod * nr);
                 float* T32 = dalloc<float>(ctx, (size_t)n_prod * nr);

@@ -185,8 +185,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024)
 }
 
 // Same reduction on the whole GPU for ranks too large for the cluster:
-// cooperative launch, matrix in global memory (L2), three grid barriers per
-// Householder step.
+// cooperative launch, matrix in global memory (L2), one grid barrier per
+// Householder step (k_sytrd32_grid below).
 __device__ bool grid_barrier(unsigned int* bar, int* status, int* s_flag, unsigned long long poll_limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -213,81 +213,139 @@ __device__ bool grid_barrier(unsigned int* bar, int* status, int* s_flag, unsign
     return *s_flag != 0;
 }
 
+// Householder vector of the row r[0 .. mm) held in shared memory (all
+// threads of the CTA): v = r - alpha e_0, tau = 2 / v^T v, alpha = -sign(r_0)
+// |r|; returns alpha (or r_0 when |r| = 0) in *e_out and tau in *tau_out.
+__device__ void house_row(float* r, int mm, float* red, float* e_out, float* tau_out) {
+    float pp = 0.f;
+    for (int j = threadIdx.x; j < mm; j += blockDim.x) pp += r[j] * r[j];
+    const float sig = block_sum1024(pp, red);
+    if (threadIdx.x == 0) {
+        const float x0 = r[0];
+        const float alpha = sig > 0.f ? -copysignf(sqrtf(sig), x0) : 0.f;
+        const float v0 = x0 - alpha;
+        const float vtv = sig - x0 * x0 + v0 * v0;
+        r[0] = v0;
+        *e_out = sig > 0.f ? alpha : x0;
+        *tau_out = vtv > 0.f ? 2.f / vtv : 0.f;
+    }
+    __syncthreads();
+}
+
+// Step k: trailing block rows/columns k+1 .. n-1 (m = n - k - 1), v_k and
+// w_k in shared memory (sv, sw), identical in every CTA.  Every CTA forms
+// the updated row k+1 of A - v w^T - w v^T and its Householder vector
+// v_{k+1} redundantly (no barrier needed for it); then each warp updates its
+// rows i >= k+2 in one pass and, in the same pass, takes the dot products of
+// the updated rows with v_{k+1} (p_{k+1} = tau A_{k+1} v_{k+1}); one grid
+// barrier publishes p_{k+1} and the partial sums of v^T p, after which every
+// CTA forms w_{k+1} = p - (tau v^T p / 2) v.  The trailing matrix is read
+// and written once per step, with one grid barrier.  CTA 0 writes the
+// reflector v_k into row k of A (every CTA read that row in the step
+// before), and d, e, tau.
 __global__ void __launch_bounds__(512) k_sytrd32_grid(float* __restrict__ A, int n, float* __restrict__ d,
                                                       float* __restrict__ e, float* __restrict__ tau,
                                                       float* __restrict__ vbuf, float* __restrict__ pbuf,
                                                       float* __restrict__ part, unsigned int* bar, int* status,
                                                       unsigned long long poll_limit) {
     extern __shared__ float sm[];
-    float* sv = sm;          // v
-    float* sw = sm + n;      // w
+    float* sv = sm;              // v_k   (entries k+1 .. n-1)
+    float* sw = sm + n;          // w_k
+    float* sr = sm + 2 * n;      // updated row k+1, then v_{k+1}
     __shared__ float red[33];
     __shared__ int s_flag;
+    __shared__ float s_e, s_tau;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int gwarp = blockIdx.x * nw + warp, nwarps = gridDim.x * nw;
-    for (int k = 0; k + 2 < n; ++k) {
-        const int m = n - k - 1;
-        if (blockIdx.x == 0) {
-            float* rowk = A + (long long)k * n + k + 1;
-            float pp = 0.f;
-            for (int j = tid; j < m; j += blockDim.x) {
-                float x = rowk[j];
-                sv[j] = x;
-                pp += x * x;
-            }
-            float sig = block_sum1024(pp, red);
-            if (tid == 0) {
-                float x0 = sv[0];
-                float alpha = sig > 0.f ? -copysignf(sqrtf(sig), x0) : 0.f;
-                float v0 = x0 - alpha;
-                float vtv = sig - x0 * x0 + v0 * v0;
-                sv[0] = v0;
-                d[k] = A[(long long)k * n + k];
-                e[k] = sig > 0.f ? alpha : x0;
-                tau[k] = vtv > 0.f ? 2.f / vtv : 0.f;
-            }
-            __syncthreads();
-            for (int j = tid; j < m; j += blockDim.x) {
-                vbuf[j] = sv[j];
-                rowk[j] = sv[j];
-            }
+    (void)vbuf;
+    if (n < 3) {
+        if (blockIdx.x == 0 && tid == 0) {
+            for (int i = 0; i < n; ++i) { d[i] = A[(long long)i * n + i]; tau[i] = 0.f; }
+            if (n == 2) e[0] = A[(long long)n + 0];
         }
-        if (!grid_barrier(bar, status, &s_flag, poll_limit)) return;
-        const float t = tau[k];
-        for (int j = tid; j < m; j += blockDim.x) sv[j] = vbuf[j];
+        return;
+    }
+    // step 0: v_0 from row 0, p_0 = tau A v_0 over rows 1 .. n-1
+    {
+        const int m = n - 1;
+        for (int j = tid; j < m; j += blockDim.x) sr[j] = A[1 + j];
         __syncthreads();
+        house_row(sr, m, red, &s_e, &s_tau);
+        if (blockIdx.x == 0 && tid == 0) { d[0] = A[0]; e[0] = s_e; tau[0] = s_tau; }
+        for (int j = tid; j < m; j += blockDim.x) sv[j] = sr[j];
+        __syncthreads();
+        const float t = s_tau;
         float pv = 0.f;
         for (int i = gwarp; i < m; i += nwarps) {
-            const float* ri = A + (long long)(k + 1 + i) * n + k + 1;
+            const float* ri = A + (long long)(1 + i) * n + 1;
             float acc = 0.f;
             for (int j = lane; j < m; j += 32) acc += ri[j] * sv[j];
             acc = warp_sum(acc) * t;
-            if (lane == 0) {
-                pbuf[i] = acc;
-                pv += acc * sv[i];
-            }
+            if (lane == 0) { pbuf[i] = acc; pv += acc * sv[i]; }          // parity 0
         }
         pv = block_sum1024(pv, red);
         if (tid == 0) part[blockIdx.x] = pv;
         if (!grid_barrier(bar, status, &s_flag, poll_limit)) return;
         float tot = 0.f;
-        for (int b = 0; b < (int)gridDim.x; ++b) tot += part[b];
+        for (int q = 0; q < (int)gridDim.x; ++q) tot += part[q];
         const float K = 0.5f * t * tot;
         for (int j = tid; j < m; j += blockDim.x) sw[j] = pbuf[j] - K * sv[j];
         __syncthreads();
-        for (int i = gwarp; i < m; i += nwarps) {
-            float* ri = A + (long long)(k + 1 + i) * n + k + 1;
-            const float vi = sv[i], wi = sw[i];
-            for (int j = lane; j < m; j += 32) ri[j] -= vi * sw[j] + wi * sv[j];
-        }
-        if (!grid_barrier(bar, status, &s_flag, poll_limit)) return;
     }
-    if (blockIdx.x == 0 && tid == 0) {
-        if (n >= 2) {
-            d[n - 2] = A[(long long)(n - 2) * n + n - 2];
-            e[n - 2] = A[(long long)(n - 1) * n + n - 2];
-            tau[n - 2] = 0.f;
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;                 // v_k, w_k cover rows k+1 .. n-1
+        // reflector v_k into row k (all CTAs read row k during the previous step)
+        if (blockIdx.x == 0)
+            for (int j = tid; j < m; j += blockDim.x) A[(long long)k * n + k + 1 + j] = sv[j];
+        // updated row k+1 (local row 0 of the trailing block), redundantly in every CTA
+        const float* r1 = A + (long long)(k + 1) * n + k + 1;
+        const float v0 = sv[0], w0 = sw[0];
+        for (int j = tid; j < m; j += blockDim.x) sr[j] = r1[j] - v0 * sw[j] - w0 * sv[j];
+        __syncthreads();
+        const bool last = k + 3 >= n;            // row k+1 = n-2: no further reflector
+        if (blockIdx.x == 0 && tid == 0) d[k + 1] = sr[0];
+        float t1 = 0.f;
+        if (!last) {
+            house_row(sr + 1, m - 1, red, &s_e, &s_tau);           // v_{k+1} in sr[1 .. m)
+            if (blockIdx.x == 0 && tid == 0) { e[k + 1] = s_e; tau[k + 1] = s_tau; }
+            t1 = s_tau;
+        } else if (blockIdx.x == 0 && tid == 0) {
+            e[k + 1] = sr[1];
+            tau[k + 1] = 0.f;
         }
+        // fused pass over rows i = k+2 .. n-1 (local 1 .. m-1): A -= v w^T + w v^T on columns
+        // k+2 .. n-1, and the dot product of the updated row with v_{k+1}
+        const float* vn = sr + 1;                // v_{k+1}, local column j - 1
+        float* pb = pbuf + (long long)((k + 1) & 1) * n;                  // p_{k+1}: parity k+1
+        float* pt = part + (long long)((k + 1) & 1) * gridDim.x;
+        float pv = 0.f;
+        for (int i = 1 + gwarp; i < m; i += nwarps) {
+            float* ri = A + (long long)(k + 1 + i) * n + k + 2;
+            const float vi = sv[i], wi = sw[i];
+            float acc = 0.f;
+            for (int j = lane; j < m - 1; j += 32) {
+                const float a = ri[j] - vi * sw[1 + j] - wi * sv[1 + j];
+                ri[j] = a;
+                acc += a * vn[j];
+            }
+            acc = warp_sum(acc) * t1;
+            if (lane == 0) { pb[i - 1] = acc; pv += acc * vn[i - 1]; }
+        }
+        if (last) break;
+        pv = block_sum1024(pv, red);
+        if (tid == 0) pt[blockIdx.x] = pv;
+        if (!grid_barrier(bar, status, &s_flag, poll_limit)) return;
+        float tot = 0.f;
+        for (int q = 0; q < (int)gridDim.x; ++q) tot += pt[q];
+        const float K = 0.5f * t1 * tot;
+        for (int j = tid; j < m - 1; j += blockDim.x) sw[j] = pb[j] - K * vn[j];
+        __syncthreads();
+        for (int j = tid; j < m - 1; j += blockDim.x) sv[j] = vn[j];
+        __syncthreads();
+    }
+    // the last diagonal entry: row n-1 was updated by the last pass (its owner warp)
+    if (!grid_barrier(bar, status, &s_flag, poll_limit)) return;
+    if (blockIdx.x == 0 && tid == 0) {
         d[n - 1] = A[(long long)(n - 1) * n + n - 1];
         tau[n - 1] = 0.f;
     }
@@ -389,14 +447,14 @@ constexpr int IT = 8;
 
 template <typename R>
 __global__ void __launch_bounds__(IT) k_invit(const float* __restrict__ d, const float* __restrict__ e,
-                                              const float* __restrict__ lam, int n, double tiny,
+                                              const float* __restrict__ lam, int n, int i0, double tiny,
                                               float* __restrict__ Y, R* __restrict__ gws) {
     extern __shared__ __align__(16) unsigned char swraw[];
     R* swd = reinterpret_cast<R*>(swraw);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int li = blockIdx.x * blockDim.x + threadIdx.x, i = i0 + li;      // eigenvalues i0 .. n-1
     if (i >= n) return;
     const long long per = 5LL * n + (n + sizeof(R) - 1) / sizeof(R);   // R words per eigenvalue in gws
-    R* base = gws ? gws + (long long)i * per : swd + (long long)threadIdx.x * 5 * n;
+    R* base = gws ? gws + (long long)li * per : swd + (long long)threadIdx.x * 5 * n;
     R* du = base;
     R* du1 = du + n;
     R* du2 = du1 + n;
@@ -521,6 +579,49 @@ __global__ void __launch_bounds__(256) k_backtransform(const float* __restrict__
         }
     }
     for (int j = lane; j < n; j += 32) X[(long long)j * n + i] = (double)y[j];
+}
+
+// Blocked back-transformation for large n (compact WY form): the reflectors
+// k0 .. k0 + nb - 1 give Q_b = H_k0 ... H_k0+nb-1 = I - V T V^T, V the
+// reflectors as columns (v_k stored in row k of A from column k + 1), T upper
+// triangular (T_ii = tau_i, T_{0:i,i} = -tau_i T_{0:i,0:i} V_{:,0:i}^T v_i).
+// Y <- Q_b Y for the blocks from last to first, each as binary32 products
+// W = V^T Y, W = T W, Y -= V W: the same arithmetic as one reflector at a
+// time, with every reflector read once per block instead of once per vector.
+// Vt [nb][m]: Vt[r][j] = v_{k0+r}[k0 + 1 + j] (zero where j < r), m = n - k0 - 1
+__global__ void k_wy_vt(const float* __restrict__ A, int n, int k0, int nb, float* __restrict__ Vt) {
+    const int m = n - k0 - 1;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nb * m) return;
+    const int r = (int)(t / m), j = (int)(t % m);
+    Vt[t] = j >= r ? A[(long long)(k0 + r) * n + k0 + 1 + j] : 0.f;
+}
+
+// T from G = V^T V (nb x nb) and tau (one CTA, column by column)
+__global__ void k_wy_t(const float* __restrict__ G, const float* __restrict__ tau, int k0, int nb,
+                       float* __restrict__ T) {
+    const int r = threadIdx.x;
+    for (int t = r; t < nb * nb; t += blockDim.x) T[t] = 0.f;
+    __syncthreads();
+    for (int i = 0; i < nb; ++i) {
+        const float ti = tau[k0 + i];
+        float acc = 0.f;
+        if (r < i) {
+            for (int q = r; q < i; ++q) acc += T[r * nb + q] * G[q * nb + i];
+        }
+        __syncthreads();
+        if (r < i) T[r * nb + i] = -ti * acc;
+        if (r == i) T[i * nb + i] = ti;
+        __syncthreads();
+    }
+}
+
+// X[j][i0 + q] = Y[q][j] (binary64), q < nv
+__global__ void k_wy_out(const float* __restrict__ Y, int n, int i0, int nv, double* __restrict__ X) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nv * n) return;
+    const int j = (int)(t / nv), q = (int)(t % nv);
+    X[(long long)j * n + i0 + q] = (double)Y[(long long)q * n + j];
 }
 
 // ------------------------------------------------------------------ 5
@@ -736,11 +837,11 @@ std::vector<float> eigvals32(gw_ctx* ctx, const double* g, const float* g32, int
             allow_max_smem(k_sytrd32_cl);
             klaunch(ctx, "k_sytrd32_cl", k_sytrd32_cl, CL, 1024, smem_cl, A32, n, d, e, tau);
         } else {
-            const size_t smem = 2 * (size_t)n * sizeof(float);
+            const size_t smem = 3 * (size_t)n * sizeof(float);
             if (smem > 200 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for the eigensolver");
             allow_max_smem(k_sytrd32_grid);
             const int grid = ctx->num_sms;
-            vb = dalloc<float>(ctx, n); pb = dalloc<float>(ctx, n); pt = dalloc<float>(ctx, grid);
+            vb = dalloc<float>(ctx, n); pb = dalloc<float>(ctx, 2 * (size_t)n); pt = dalloc<float>(ctx, 2 * (size_t)grid);
             bar = dalloc<unsigned int>(ctx, 2);
             CUDA_CHECK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), ctx->stream));
             // bounded grid barriers: a CTA gives up after poll_limit polls (about a second by default)
@@ -808,7 +909,7 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int 
             allow_max_smem(k_sytrd32_cl);
             klaunch(ctx, "k_sytrd32_cl", k_sytrd32_cl, CL, 1024, smem_cl, A32, n, d, e, tau);
         } else {
-            const size_t smem = 2 * (size_t)n * sizeof(float);
+            const size_t smem = 3 * (size_t)n * sizeof(float);
             if (smem > 200 * 1024) gw_throw(GW_ERR_INVALID_ARG, "compression rank too large for the eigensolver");
             allow_max_smem(k_sytrd32_grid);
             int per_sm = 0;
@@ -816,8 +917,8 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int 
             if (per_sm < 1) gw_throw(GW_ERR_CUDA, "tridiagonalisation kernel cannot be resident");
             const int grid = ctx->num_sms;          // one CTA per SM, co-resident (cooperative launch)
             vb = dalloc<float>(ctx, n);
-            pb = dalloc<float>(ctx, n);
-            pt = dalloc<float>(ctx, grid);
+            pb = dalloc<float>(ctx, 2 * (size_t)n);          // two parities
+            pt = dalloc<float>(ctx, 2 * (size_t)grid);
             bar = dalloc<unsigned int>(ctx, 2);
             CUDA_CHECK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), ctx->stream));
             // bounded grid barriers: a CTA gives up after poll_limit polls (about a second by default)
@@ -844,6 +945,21 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int 
         if (2 * (size_t)n * sizeof(float) > 200 * 1024) gw_throw(GW_ERR_INVALID_ARG, "rank too large for the bisection");
         klaunch(ctx, "k_bisect", k_bisect, div_up(n, 8), 256, 2 * (size_t)n * sizeof(float), (const float*)d,
                 (const float*)e, n, bnd, lam32);
+        // cluster tolerance: eigenvalue gaps below which inverse iteration cannot keep
+        // the vectors orthogonal in its working precision
+        const float cl_tol = (vectors_f64 ? 1e-6f : 1e-4f) * bnd;
+        // the vectors needed: every one for the binary64 refinement, else the top
+        // n_sub and the rest of a cluster that the cut runs through (the kept
+        // vectors of that cluster are orthogonalised against its discarded ones);
+        // the others stay zero
+        int i0 = 0;
+        if (oa_iters == 0) {
+            std::vector<float> hl(n);
+            CUDA_CHECK(cudaMemcpyAsync(hl.data(), lam32, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+            CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+            i0 = n - n_sub;
+            while (i0 > 0 && hl[i0] - hl[i0 - 1] < cl_tol) --i0;
+        }
         // binary64 vectors when they are refined to binary64 accuracy afterwards
         auto invit = [&](auto zero) {
             typedef decltype(zero) R;
@@ -855,23 +971,22 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int 
                     1, std::min(std::min((size_t)IT, (200 * 1024) / per_thread), (size_t)div_up(n, ctx->num_sms)));
                 const size_t smem_it = per_thread * it_threads + 16;
                 allow_max_smem(k_invit<R>);
-                klaunch(ctx, "k_invit", k_invit<R>, div_up(n, it_threads), it_threads, smem_it, (const float*)d,
-                        (const float*)e, (const float*)lam32, n, tiny, Y, (R*)nullptr);
+                klaunch(ctx, "k_invit", k_invit<R>, div_up(n - i0, it_threads), it_threads, smem_it, (const float*)d,
+                        (const float*)e, (const float*)lam32, n, i0, tiny, Y, (R*)nullptr);
             } else {
                 const size_t per = 5 * (size_t)n + (n + sizeof(R) - 1) / sizeof(R);
-                gws = ctx_alloc(ctx, (size_t)n * per * sizeof(R));
-                klaunch(ctx, "k_invit", k_invit<R>, div_up(n, IT), IT, 0, (const float*)d, (const float*)e,
-                        (const float*)lam32, n, tiny, Y, (R*)gws);
+                gws = ctx_alloc(ctx, (size_t)(n - i0) * per * sizeof(R));
+                klaunch(ctx, "k_invit", k_invit<R>, div_up(n - i0, IT), IT, 0, (const float*)d, (const float*)e,
+                        (const float*)lam32, n, i0, tiny, Y, (R*)gws);
             }
         };
+        if (i0 > 0) CUDA_CHECK(cudaMemsetAsync(Y, 0, sizeof(float) * (size_t)i0 * n, ctx->stream));
         if (vectors_f64) invit(0.0);
         else invit(0.0f);
-        // clusters: eigenvalue gaps below which inverse iteration cannot keep
-        // the vectors orthogonal in its working precision
-        // (the refinement of the binary64 path works on every vector; without
-        // it only the kept top n_sub matter)
-        klaunch(ctx, "k_cluster_mgs", k_cluster_mgs, n, 256, 0, (const float*)lam32, n,
-                (vectors_f64 ? 1e-6f : 1e-4f) * bnd, oa_iters > 0 ? n : n_sub, Y);
+        // clusters (the refinement of the binary64 path works on every vector;
+        // without it only the clusters that hold kept vectors matter)
+        klaunch(ctx, "k_cluster_mgs", k_cluster_mgs, n, 256, 0, (const float*)lam32, n, cl_tol,
+                oa_iters > 0 ? n : n_sub, Y);
         // two warps per CTA: the vectors spread over all SMs
         const int bt_warps = (int)std::max<size_t>(1, std::min<size_t>(2, (200 * 1024) / ((size_t)n * sizeof(float))));
         const size_t smem_bt = (size_t)bt_warps * n * sizeof(float);
@@ -883,7 +998,38 @@ void eigh_top_scaled(gw_ctx* ctx, const double* g, const float* g32, int n, int 
         if (n <= 32 * 8) backtransform(k_backtransform<8>);
         else if (n <= 32 * 16) backtransform(k_backtransform<16>);
         else if (n <= 32 * 24) backtransform(k_backtransform<24>);
-        else backtransform(k_backtransform<0>);
+        else {
+            // compact WY blocks of WYB reflectors, binary32 products (Y rows i0 .. n-1 in place)
+            constexpr int WYB = 64;
+            const int nv = n - i0;
+            float* Yv = Y + (size_t)i0 * n;
+            float* Vt = dalloc<float>(ctx, (size_t)WYB * n);
+            float* Gm = nullptr; float* Tm = nullptr; float* Wm = nullptr; float* W2 = nullptr;
+            try {
+                Gm = dalloc<float>(ctx, WYB * WYB);
+                Tm = dalloc<float>(ctx, WYB * WYB);
+                Wm = dalloc<float>(ctx, (size_t)WYB * nv);
+                W2 = dalloc<float>(ctx, (size_t)WYB * nv);
+                const int nref = n - 2;                         // reflectors 0 .. n-3
+                for (int k0 = ((nref - 1) / WYB) * WYB; k0 >= 0; k0 -= WYB) {
+                    const int nb = std::min(WYB, nref - k0), m = n - k0 - 1;
+                    klaunch(ctx, "k_backtransform", k_wy_vt, div_up((long long)nb * m, 256), 256, 0,
+                            (const float*)A32, n, k0, nb, Vt);
+                    gemm_f32(ctx, false, true, nb, nb, m, 1.f, Vt, m, Vt, m, 0.f, Gm, nb);        // G = V^T V
+                    klaunch(ctx, "k_backtransform", k_wy_t, 1, 64, 0, (const float*)Gm, (const float*)tau, k0, nb,
+                            Tm);
+                    gemm_f32(ctx, false, true, nb, nv, m, 1.f, Vt, m, Yv + k0 + 1, n, 0.f, Wm, nv);  // W = V^T Y
+                    gemm_f32(ctx, false, false, nb, nv, nb, 1.f, Tm, nb, Wm, nv, 0.f, W2, nv);      // W = T W
+                    gemm_f32(ctx, true, false, nv, m, nb, -1.f, W2, nv, Vt, m, 1.f, Yv + k0 + 1, n); // Y -= V W
+                }
+                klaunch(ctx, "k_backtransform", k_wy_out, div_up((long long)nv * n, 256), 256, 0, (const float*)Yv,
+                        n, i0, nv, X);
+            } catch (...) {
+                ctx_free(ctx, Vt); ctx_free(ctx, Gm); ctx_free(ctx, Tm); ctx_free(ctx, Wm); ctx_free(ctx, W2);
+                throw;
+            }
+            ctx_free(ctx, Vt); ctx_free(ctx, Gm); ctx_free(ctx, Tm); ctx_free(ctx, Wm); ctx_free(ctx, W2);
+        }
         // binary64 refinement
         if (oa_iters > 0) {
             X2 = dalloc<double>(ctx, nn); R = dalloc<double>(ctx, nn); S = dalloc<double>(ctx, nn);
