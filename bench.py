@@ -191,6 +191,17 @@ def _panels(n, nb):
     return out
 
 
+def _form_pairs(n, nb=32):
+    """Panel pairs of the batched forward substitution: (first panel width,
+    second panel width, rows below the pair) per pair."""
+    out = []
+    for k0 in range(0, n, 2 * nb):
+        k1 = min(n, k0 + nb)
+        k2 = min(n, k1 + nb)
+        out.append((k1 - k0, k2 - k1, n - k2))
+    return out
+
+
 def forms_kernel(n, R):
     """Which binary32 forms kernel a molecule takes (the library's dispatch):
     tensor-memory forms for 32 < n <= 384, the resident FMA forms while 48
@@ -234,8 +245,21 @@ def kernel_model(name, mol, grid, n_rank=None):
         return (fwd, "tensor", PEAK_TF32_TFLOPS / 3) if fk == name else (None, None, None)
     if name == "k_forms32":
         return (fwd, "alu", PEAK_FP32_TFLOPS) if fk == name else (None, None, None)
-    if name == "k_forms32_update":
-        return (fwd - diag / 2, "alu", PEAK_FP32_TFLOPS) if fk == "batched" else (None, None, None)
+    if name in ("k_forms32_update", "k_forms32_update_tc"):
+        if fk != "batched":
+            return None, None, None
+        # per pair: the first panel's update of the second panel's rows (binary32 FMA), then the
+        # update of the rows below the pair by both panels (tensor cores from 64 rows on)
+        fma = tcf = 0.0
+        for b1, b2, m in _form_pairs(n):
+            fma += 8.0 * R * b2 * b1
+            if m >= 64:
+                tcf += 8.0 * R * m * (b1 + b2)
+            else:
+                fma += 8.0 * R * m * (b1 + b2)
+        if name == "k_forms32_update":
+            return (N - 1) * fma, "alu", PEAK_FP32_TFLOPS
+        return ((N - 1) * tcf, "tensor", PEAK_TF32_TFLOPS / 3) if tcf > 0 else (None, None, None)
     if name == "k_forms32_diag":
         return (diag, "alu", PEAK_FP32_TFLOPS) if fk == "batched" else (None, None, None)
     if name == "k_ldlt32_syrk_tc":
@@ -281,10 +305,17 @@ def kernel_bytes(name, mol, grid):
         if forms_kernel(n, R) != name:
             return None
         return (N - 1) * (tri * cz + ((n + 31) // 32) * 32 * 32 * cz)
-    if name == "k_forms32_update" and forms_kernel(n, R) == "batched":
-        # the factor read once per frequency; Y read and written once per panel pair
-        pairs = (n + 63) // 64
-        return (N - 1) * (tri * cz + pairs * n * R * cz)
+    if name in ("k_forms32_update", "k_forms32_update_tc") and forms_kernel(n, R) == "batched":
+        # per pair and frequency: the updated rows of Y read and written once, their
+        # rows of the factor's panel columns and the pair's rows of Y read once
+        tc_ = name.endswith("_tc")
+        b = 0.0
+        for b1, b2, m in _form_pairs(n):
+            if not tc_:
+                b += b2 * R * 2 * cz + b2 * b1 * cz + b1 * R * cz
+            if (m >= 64) == tc_ and m > 0:
+                b += m * R * 2 * cz + m * (b1 + b2) * cz + (b1 + b2) * R * cz
+        return (N - 1) * b if b > 0 else None
     return None
 
 
@@ -322,8 +353,8 @@ def per_kernel_roofline(kt, mols, grid, total_ms):
     return out
 
 
-KERNELS = ["k_forms32", "k_forms32_tm", "k_forms32_diag", "k_forms32_update", "k_ldlt32_init", "k_ldlt32_panel",
-           "k_ldlt32_syrk", "k_ldlt32_syrk_tc", "k_chi0_kk_fma", "k_chi0_kk_tc", "k_kk_ctable", "k_deposit_syrk32",
+KERNELS = ["k_forms32", "k_forms32_tm", "k_forms32_diag", "k_forms32_update", "k_forms32_update_tc",
+           "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk", "k_ldlt32_syrk_tc", "k_chi0_kk_fma", "k_chi0_kk_tc", "k_kk_ctable", "k_deposit_syrk32",
            "k_sgemm", "k_sgemm_tc", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl", "k_bisect", "k_invit",
            "k_backtransform", "k_cluster_mgs", "k_rayleigh_cols", "k_vertex_contract", "k_vertex_contract32",
            "k_sigma_c", "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_pair_keys",

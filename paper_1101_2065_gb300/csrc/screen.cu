@@ -1240,6 +1240,207 @@ __global__ void __launch_bounds__(256) k_formsb_update(const C* __restrict__ fac
     }
 }
 
+// The same update for a panel pair on the tensor cores (binary32 path):
+// Y[r][q] -= sum_p L[r][p] y[p][q] over the pair's 64 complex columns p is
+// one real TF32 product with the complex entries interleaved along K
+// (K = 128, 3xTF32 as in k_ldlt_syrk_tc):
+//   A[r][2p] = Re L[r][p], A[r][2p+1] = Im L[r][p]
+//   B[q][2p] = Re y[p][q], B[q][2p+1] = -Im y[p][q]; B[32+q][2p] = Im y, B[32+q][2p+1] = Re y
+// so that accumulator columns q and 32 + q hold Re and Im of (L y)[r][q].
+// One CTA per (frequency, 128-row block, run of column tiles of 32
+// right-hand sides) stages its rows of L once (hi and lo, 128 KB) and walks
+// the run: the MMAs of tile t + 1 run while tile t is read back and
+// subtracted from Y.  Each thread owns one row and 16 consecutive
+// right-hand sides of a tile (128 contiguous bytes of Y), so the
+// read-modify-write needs no transpose.
+constexpr int FU_KC = 64, FU_KR = 2 * FU_KC, FU_NC = 32, FU_N = 2 * FU_NC;
+constexpr int FU_A_BYTES = 128 * FU_KR * 4;             // 128 x 128 binary32 (hi or lo)
+constexpr int FU_B_BYTES = FU_N * FU_KR * 4;            // 64 x 128 binary32 (hi or lo)
+constexpr uint32_t FU_SBO = (FU_KR / 4) * 128;
+constexpr uint32_t FU_IDESC = tc::idesc_tf32(128, FU_N);
+constexpr size_t FU_SMEM = 2 * (size_t)FU_A_BYTES + 2 * (size_t)FU_B_BYTES;
+constexpr uint32_t FU_TMEM = 4 * FU_N;                  // two sets of (hi x hi, cross terms)
+
+// this thread's raw B entries of column tile c0: y[2 kq][q] and y[2 kq + 1][q]
+__device__ __forceinline__ void fu_load_b(float2 (&yb)[4][2], const float2* __restrict__ Yk, int R, int kk0, int kw,
+                                          int c0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int idx = threadIdx.x + 256 * j, q = idx & 31, p = 2 * (idx >> 5), col = c0 + q;
+        yb[j][0] = (col < R && p < kw) ? Yk[(long long)(kk0 + p) * R + col] : make_float2(0.f, 0.f);
+        yb[j][1] = (col < R && p + 1 < kw) ? Yk[(long long)(kk0 + p + 1) * R + col] : make_float2(0.f, 0.f);
+    }
+}
+
+__device__ __forceinline__ void fu_store_b(const float2 (&yb)[4][2], unsigned char* bh, unsigned char* bl) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int idx = threadIdx.x + 256 * j, q = idx & 31, kq = idx >> 5;
+        const float2 y0 = yb[j][0], y1 = yb[j][1];
+        st_shared_quad(bh, bl, tc::core_off(q, 4 * kq, FU_KR / 4), y0.x, -y0.y, y1.x, -y1.y);
+        st_shared_quad(bh, bl, tc::core_off(FU_NC + q, 4 * kq, FU_KR / 4), y0.y, y0.x, y1.y, y1.x);
+    }
+}
+
+// the current values of this thread's 16 entries (row r, columns cb ..): Y, or q before the first update
+template <bool VEC>
+__device__ __forceinline__ void fu_load_c(float2 (&cv)[16], const float2* __restrict__ Yk, const double* __restrict__ Q,
+                                          int R, int r, int r_hi, int cb, bool first) {
+    if (r >= r_hi) return;
+    const long long o = (long long)r * R + cb;
+    if (VEC && cb + 16 <= R) {
+        if (first) {
+#pragma unroll
+            for (int t = 0; t < 16; t += 2) {
+                const double2 qq = *reinterpret_cast<const double2*>(Q + o + t);
+                cv[t] = make_float2((float)qq.x, 0.f);
+                cv[t + 1] = make_float2((float)qq.y, 0.f);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 16; t += 2) {
+                const float4 v = *reinterpret_cast<const float4*>(Yk + o + t);
+                cv[t] = make_float2(v.x, v.y);
+                cv[t + 1] = make_float2(v.z, v.w);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+            cv[t] = cb + t < R ? (first ? make_float2((float)Q[o + t], 0.f) : Yk[o + t]) : make_float2(0.f, 0.f);
+    }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(256, 1) k_formsb_update_tc(const float2* __restrict__ fac, int n,
+                                                             const double* __restrict__ Q, int R,
+                                                             float2* __restrict__ Y, int kk0, int kw, int r_lo,
+                                                             int r_hi, int kbase, int tiles_per_cta, int* status) {
+    extern __shared__ __align__(128) unsigned char sraw_fu[];
+    unsigned char* sAh = sraw_fu;
+    unsigned char* sAl = sAh + FU_A_BYTES;
+    unsigned char* sBh = sAl + FU_A_BYTES;
+    unsigned char* sBl = sBh + FU_B_BYTES;
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int z = blockIdx.z, k = kbase + z;
+    const float2* F = fac + (long long)k * tri(n);
+    float2* Yk = Y + (long long)z * n * R;
+    const int r0 = r_lo + 128 * blockIdx.x;
+    const int t_all = (R + FU_NC - 1) / FU_NC, J0 = blockIdx.y * tiles_per_cta;
+    const int nt = min(t_all, J0 + tiles_per_cta) - J0;
+    if (nt <= 0) return;                                  // uniform over the CTA
+    const bool first = kk0 == 0;
+    // this thread's read-back entries: row r, right-hand sides 16 h .. 16 h + 15 of a tile
+    const int r = r0 + 32 * (warp & 3) + lane, h = warp >> 2;
+    if (warp == 0) tc::tmem_alloc(&tbase, FU_TMEM);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0]);
+        tc::mbar_init(&mbar[1]);
+    }
+    float2 yb[4][2], cvA[16], cvB[16];
+    fu_load_b(yb, Yk, R, kk0, kw, FU_NC * J0);
+    fu_load_c<VEC>(cvA, Yk, Q, R, r, r_hi, FU_NC * J0 + 16 * h, first);
+    // A operand: rows r0 .. r0 + 127 of the panel pair, staged once
+#pragma unroll 4
+    for (int j = 0; j < 16; ++j) {
+        const int idx = tid + 256 * j, rr = idx & 7, kq = (idx >> 3) & 31, rg = idx >> 8;
+        const int ra = r0 + 8 * rg + rr, p = 2 * kq;
+        float2 a = make_float2(0.f, 0.f), b = a;
+        if (ra < r_hi) {
+            const float2* src = F + tri(ra) + kk0 + p;
+            if (p < kw) a = src[0];
+            if (p + 1 < kw) b = src[1];
+        }
+        st_shared_quad(sAh, sAl, tc::core_off(8 * rg + rr, 4 * kq, FU_KR / 4), a.x, a.y, b.x, b.y);
+    }
+    fu_store_b(yb, sBh, sBl);
+    if (nt > 1) fu_load_b(yb, Yk, R, kk0, kw, FU_NC * (J0 + 1));
+    tc::fence_async_smem();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t taddr = tbase;
+    const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+    auto issue = [&](int t) {                             // one thread: the 48 MMAs of local tile t
+        tc::fence_after();
+        const uint32_t d = taddr + (uint32_t)(2 * FU_N * (t & 1));
+#pragma unroll
+        for (int ks = 0; ks < FU_KR / 8; ++ks) {
+            const uint32_t o = ks * 256, acc = ks > 0 ? 1u : 0u;
+            tc::mma_tf32(d, tc::smem_desc(ah + o, FU_SBO), tc::smem_desc(bh + o, FU_SBO), FU_IDESC, acc);
+            tc::mma_tf32(d + FU_N, tc::smem_desc(ah + o, FU_SBO), tc::smem_desc(bl + o, FU_SBO), FU_IDESC, acc);
+            tc::mma_tf32(d + FU_N, tc::smem_desc(al + o, FU_SBO), tc::smem_desc(bh + o, FU_SBO), FU_IDESC, 1u);
+        }
+        tc::commit(tc::smem_u32(&mbar[t & 1]));
+    };
+    if (tid == 0) issue(0);
+    bool ok = true;
+    int t = 0;
+    // local tile t: wait for its MMAs, stage and issue tile t + 1 (the B buffer is free), then
+    // read back tile t from register set cur while tile t + 1's entries load into nxt
+    auto step = [&](float2 (&cur)[16], float2 (&nxt)[16]) -> bool {
+        if (t + 1 < nt) fu_load_c<VEC>(nxt, Yk, Q, R, r, r_hi, FU_NC * (J0 + t + 1) + 16 * h, first);
+        ok = tc::mbar_wait(tc::smem_u32(&mbar[t & 1]), (t >> 1) & 1) && ok;
+        ok = __syncthreads_and(ok);
+        if (!ok) return false;
+        if (t + 1 < nt) {
+            fu_store_b(yb, sBh, sBl);
+            if (t + 2 < nt) fu_load_b(yb, Yk, R, kk0, kw, FU_NC * (J0 + t + 2));
+            tc::fence_async_smem();
+            __syncthreads();
+            if (tid == 0) issue(t + 1);
+        }
+        tc::fence_after();
+        const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(2 * FU_N * (t & 1) + 16 * h);
+        uint32_t re[16], im[16], re2[16], im2[16];
+        tc::tmem_ld16(base, re);
+        tc::tmem_ld16(base + FU_NC, im);
+        tc::tmem_ld16(base + FU_N, re2);
+        tc::tmem_ld16(base + FU_N + FU_NC, im2);
+        tc::tmem_wait_ld();
+        tc::fence_before();
+        const int cb = FU_NC * (J0 + t) + 16 * h;
+        if (r < r_hi) {
+            float2 out[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                out[q] = make_float2(cur[q].x - (__uint_as_float(re[q]) + __uint_as_float(re2[q])),
+                                     cur[q].y - (__uint_as_float(im[q]) + __uint_as_float(im2[q])));
+            float2* dst = Yk + (long long)r * R + cb;
+            if (VEC && cb + 16 <= R) {
+#pragma unroll
+                for (int q = 0; q < 16; q += 2)
+                    *reinterpret_cast<float4*>(dst + q) = make_float4(out[q].x, out[q].y, out[q + 1].x, out[q + 1].y);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (cb + q < R) dst[q] = out[q];
+            }
+        }
+        return true;
+    };
+    while (t < nt) {
+        if (!step(cvA, cvB) || ++t >= nt) break;
+        if (!step(cvB, cvA)) break;
+        ++t;
+    }
+    if (!ok) {
+        // stopped at local tile t: tiles 0 .. t were issued; their MMAs finish before the columns are freed
+        if (tid == 0) atomicOr(status, ST_TIMEOUT);
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int cnt = t >= s2 ? (t - s2) / 2 + 1 : 0;
+            if (cnt > 0) tc::mbar_wait(tc::smem_u32(&mbar[s2]), (cnt - 1) & 1);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(taddr, FU_TMEM);
+    }
+}
+
 // out = M_k^-1 - 1 = chi^RPA_k from the factors (test read-back): column
 // col = blockIdx.x * blockDim.x + threadIdx.x of X solves L D L^T x = e_col.
 __global__ void __launch_bounds__(256) k_ldlt_inverse(const double2* __restrict__ F, int n, double2* __restrict__ X) {
@@ -1354,7 +1555,7 @@ void launch_ldlt(gw_ctx* ctx, gw_W* W) {
 // else the nd factors of a compact set, entry i belonging to frequency kmap[i].
 template <typename C>
 static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, const double* Q, int R,
-                          double* cout, const char* const names[2], const int* kmap = nullptr, int nd = 0) {
+                          double* cout, const char* const names[3], const int* kmap = nullptr, int nd = 0) {
     constexpr int NB = Tile<C>::NB, TT = Tile<C>::T;
     const int kfirst = kmap ? 0 : 1, kend = kmap ? nd : N;
     // frequencies per batch: Y [nb][n][R] within about 2 GB
@@ -1394,6 +1595,22 @@ static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N
                     klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R, Y, acc,
                             cout, k1, kbase, kmap);
                     if (k2 == n) break;
+                    if (!ctx->forms_simt && n - k2 >= 64) {
+                        // the rows below the pair on the tensor cores; runs of column tiles
+                        // so that about two CTAs per SM are in flight
+                        const int gx = div_up(n - k2, 128), t_all = div_up(R, FU_NC);
+                        const int want = div_up(2 * ctx->num_sms, gx * nbb);
+                        const int tpc = div_up(t_all, std::max(1, std::min(t_all, want)));
+                        const dim3 grid(gx, div_up(t_all, tpc), nbb);
+                        auto run = [&](auto kern) {
+                            allow_max_smem(kern);
+                            klaunch(ctx, names[2], kern, grid, 256, FU_SMEM, (const float2*)fac, n, Q, R, (float2*)Y,
+                                    k0, k2 - k0, k2, n, kbase, tpc, ctx->d_status);
+                        };
+                        if (R % 2 == 0) run(k_formsb_update_tc<true>);
+                        else run(k_formsb_update_tc<false>);
+                        continue;
+                    }
                     klaunch(ctx, names[1], k_formsb_update<C, 2 * NB>, dim3(div_up(n - k2, TT), div_up(R, TT), nbb), 256,
                             sm2, fac, n, Q, R, Y, k0, k2 - k0, k2, n, kbase);
                 }
@@ -1410,7 +1627,7 @@ static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N
 
 template <typename C>
 static void forms_run(gw_ctx* ctx, const C* fac, const C* linv, int n, int N, const double* Q, int R, double* cout,
-                      const char* name, const char* const bnames[2], const int* kmap = nullptr, int nd = 0) {
+                      const char* name, const char* const bnames[3], const int* kmap = nullptr, int nd = 0) {
     constexpr int NB = Tile<C>::NB, FT = Tile<C>::FT, LP = tile_pitch<C>();
     const int ny = kmap ? nd : N - 1;
     if (ny > 65535) gw_throw(GW_ERR_INVALID_ARG, "too many frequencies for the forms kernel");
@@ -1454,8 +1671,8 @@ void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* co
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
     if (c->prec == GW_MIXED && !ctx->forms_simt && forms_tm(ctx, W, Q, R, cout)) return;
-    static const char* const b32[2] = {"k_forms32_diag", "k_forms32_update"};
-    static const char* const b64[2] = {"k_forms_diag", "k_forms_update"};
+    static const char* const b32[3] = {"k_forms32_diag", "k_forms32_update", "k_forms32_update_tc"};
+    static const char* const b64[3] = {"k_forms_diag", "k_forms_update", "k_forms_update_tc"};
     if (c->prec == GW_MIXED)
         forms_run<float2>(ctx, W->fac32, (const float2*)W->linv, n, N, Q, R, cout, "k_forms32", b32);
     else
@@ -1491,7 +1708,7 @@ static void pole_factor(gw_ctx* ctx, const gw_W* W, const int* kd, int k1, int n
 }
 
 void launch_pole_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
-    static const char* const b64[2] = {"k_forms_diag", "k_forms_update"};
+    static const char* const b64[3] = {"k_forms_diag", "k_forms_update", "k_forms_update_tc"};
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega, np = (int)W->pole_k.size();
     if (np == 0) return;

@@ -239,9 +239,11 @@ def test_tensor_memory_forms_sizes(gwlib, ctx, atoms):
 
 def test_batched_forms_c_level(gwlib, ctx):
     """N_sub = 480 (16-atom chain): the binary32 path takes the batched forms
-    (Y in HBM, panels in pairs); its c_nk agree with the oracle's and with the
-    binary64 path's (own basis: c is basis invariant) within 1e-4, quasiparticle
-    energies within 1 meV on the same branch."""
+    (Y in HBM, panels in pairs, the rows below a pair updated on the tensor
+    cores); its c_nk agree with the oracle's and with the binary64 path's (own
+    basis: c is basis invariant) within 1e-4, quasiparticle energies within 1
+    meV on the same branch; the FMA-unit update (GW_OPT_FORMS_SIMT) gives the
+    same c to 2e-5."""
     import oracle
     from synth import molecules as sm
     mol = sm._uniform_molecule("chain", 16, sm.SEED_BASE + 7816)
@@ -255,12 +257,26 @@ def test_batched_forms_c_level(gwlib, ctx):
             out[prec] = (h["sigma"].copy()["c"], e, st)
         finally:
             _free(h)
+    # the rows below each panel pair updated on the FMA units instead of the tensor cores
+    ctx.set_option(gwlib.GW_OPT_FORMS_SIMT, 1)
+    try:
+        h, e, z, st = gwlib.solve(ctx, mol, grid, prec=gwlib.GW_MIXED)
+        try:
+            out["fma"] = (h["sigma"].copy()["c"], e, st)
+        finally:
+            _free(h)
+    finally:
+        ctx.set_option(gwlib.GW_OPT_FORMS_SIMT, 0)
     cm, em, stm = out[gwlib.GW_MIXED]
     cd, ed, std = out[gwlib.GW_FP64]
+    cf, ef, stf = out["fma"]
     assert rel(cd, r["c"]) < 1e-9
     assert rel(cm, r["c"]) < 1e-4 and rel(cm, cd) < 1e-4
+    assert rel(cf, r["c"]) < 1e-4
+    print("batched forms: tensor vs FMA c", rel(cm, cf), "QP", np.abs(em - ef).max() / MEV, "meV")
+    assert rel(cm, cf) < 2e-5 and np.abs(em - ef).max() < 0.05 * MEV
     assert np.abs(em - r["e_qp"]).max() < MEV and np.abs(em - ed).max() < MEV
-    assert np.array_equal(stm, r["status"]) and np.array_equal(std, r["status"])
+    assert np.array_equal(stm, r["status"]) and np.array_equal(std, r["status"]) and np.array_equal(stf, stm)
 
 
 def test_large_rank_eigensolver_mixed_vs_fp64(gwlib, ctx):
