@@ -8,7 +8,8 @@
  *   gw_build_chi0  spectral function of chi0 in the dominant-product basis
  *                  (Eq. chi_by_spectra, closed form of Sec. 6.1), compressed
  *                  (Eqs. subsetof_vef, projector0, subspace, subspace_chi0),
- *                  and its Cauchy (Kramers-Kronig) transform by FFT.
+ *                  and its Cauchy (Kramers-Kronig) transform (binary64: by
+ *                  FFT; binary32: direct sum over the transition band).
  *   gw_screen_W    chi^RPA = (1 - chi0)^-1 chi0 per frequency (Eq. chi_RPA),
  *                  W = v + Zup chi^RPA Zup^T.
  *   gw_sigma_diag  diagonal GW self-energy from the spectral convolution of
@@ -72,8 +73,11 @@ typedef int gw_status;
 
 typedef enum {
     GW_FP64 = 0,      /* every step in binary64 */
-    GW_MIXED = 1      /* binary32 contractions, FFTs and factorisations, binary64 setup
-                         and quasiparticle root; error stated against GW_FP64 */
+    GW_MIXED = 1      /* binary32 contractions, Cauchy sum, factorisation and forms
+                         (3xTF32 tensor-core products where the tensor cores'
+                         accumulation bias stays below the tolerance, binary32 FMA
+                         elsewhere), binary64 setup, Sigma and quasiparticle root;
+                         error stated against GW_FP64 */
 } gw_precision;
 
 typedef struct gw_ctx gw_ctx;       /* device, stream, HBM accounting */
@@ -182,8 +186,9 @@ void      gw_mol_free(gw_mol* mol);
 /* a0-a4: pair table, vertex products V^{EF}_mu = X_aE V^mu_ab X_bF
  * (Sec. 6.1), compression basis (Eqs. projector0, subspace,
  * global-basis-orthogonality) unless desc->Z was given, u_p = Zup^T V^p
- * (Eq. subspace_chi0), tent deposit of A_j and chi0_k by the FFT form of the
- * Cauchy integral (Eq. chi_by_spectra).  Errors: GW_ERR_GRID if
+ * (Eq. subspace_chi0), tent deposit of A_j and chi0_k by the Cauchy integral
+ * (Eq. chi_by_spectra; binary64: exact FFT form, binary32: direct sum over
+ * the bins that carry weight).  Errors: GW_ERR_GRID if
  * max Delta/d_omega + 1 > n_omega - 1; GW_ERR_NOT_SPD; GW_ERR_RANK if
  * lambda_{n_sub} < 1e-12 lambda_max; GW_ERR_NO_CONVERGENCE. */
 gw_status gw_build_chi0(gw_ctx* ctx, const gw_mol* mol, const gw_grid* grid,

@@ -6,9 +6,14 @@ serve: replays a seeded Poisson arrival trace of molecules of uneven size
        closed-loop on a sample of the same jobs and compares the
        quasiparticle energies.
 batch: submits a whole batch of uneven molecules at once.
+one:   solves one synthetic chain or ring (13 orbitals, 60 products and 2
+       occupied states per atom, 50 % compression) on one context stream,
+       --repeat times, and reports the time per solve (a fixed case for
+       profiling a kernel).
 
 Usage: python -m paper_1101_2065_gb300.serve serve --jobs 60 --rate 10 --lo 4 --hi 16
        python -m paper_1101_2065_gb300.serve batch
+       python -m paper_1101_2065_gb300.serve one --kind chain --atoms 24 --n-omega 512
 Prints one JSON line.
 """
 import argparse
@@ -102,9 +107,33 @@ def fp64_compare(mols, grid, mixed_results, sample, workers=1, budget=0):
             "same_root_branch": same}
 
 
+def solve_one(kind, atoms, n_omega, fp64=False, repeat=1):
+    """Time gw_solve on one resident synthetic molecule (single stream)."""
+    mol = sm._uniform_molecule(kind, atoms, sm.SEED_BASE + 9000 + atoms)
+    grid = synth.Grid(n_omega)
+    prec = gw.GW_FP64 if fp64 else gw.GW_MIXED
+    times = []
+    with gw.Context(0) as ctx:
+        m = gw.gw_mol_upload(ctx, mol)
+        try:
+            for _ in range(max(1, repeat)):
+                t0 = time.perf_counter()
+                e, z, st, sx = gw.gw_solve(ctx, m, grid, [mol.n_occ - 1, mol.n_occ], prec=prec)
+                times.append(time.perf_counter() - t0)
+        finally:
+            m.free()
+    return {"mode": "one", "molecule": f"{kind}{atoms}", "n_sub": int(mol.n_sub), "n_omega": n_omega,
+            "precision": "fp64" if fp64 else "mixed", "s_per_solve": times,
+            "e_qp_ha": [float(x) for x in e], "root_status": [int(x) for x in st]}
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("mode", choices=["serve", "batch"])
+    p.add_argument("mode", choices=["serve", "batch", "one"])
+    p.add_argument("--kind", choices=["chain", "ring"], default="chain")
+    p.add_argument("--atoms", type=int, default=24)
+    p.add_argument("--fp64", action="store_true", help="one: the binary64 path instead of the mixed one")
+    p.add_argument("--repeat", type=int, default=1)
     p.add_argument("--jobs", type=int, default=60)
     p.add_argument("--rate", type=float, default=20.0)
     p.add_argument("--lo", type=int, default=10)
@@ -116,6 +145,9 @@ def main(argv=None):
     a = p.parse_args(argv)
     gw.load() if os.path.exists(gw.lib_path()) else gw._build.build()
     budget = int(a.budget_gb * (1 << 30))
+    if a.mode == "one":
+        print(json.dumps(solve_one(a.kind, a.atoms, a.n_omega or 1024, a.fp64, a.repeat)))
+        return
     if a.mode == "serve":
         arrivals, jobs, grid = synth.make_serving_trace(a.jobs, a.rate, a.lo, a.hi, a.n_omega or 1024)
         mols = [synth.molecules.build_job(j) for j in jobs]
