@@ -383,6 +383,7 @@ constexpr int ST_A_BYTES = 128 * 64 * 4;            // 128 x 64 binary32 (hi or 
 constexpr int ST_B_BYTES = ST_N * 64 * 4;           // 64 x 64 binary32 (hi or lo)
 constexpr uint32_t ST_SBO = (64 / 4) * 128;
 constexpr uint32_t ST_IDESC = tc::idesc_tf32(128, ST_N);
+constexpr uint32_t ST_IDESC2 = tc::idesc_tf32(128, 2 * ST_N);     // A_hi x [B_hi; B_lo]
 constexpr size_t ST_SMEM = 2 * (size_t)ST_A_BYTES + 4 * (size_t)ST_B_BYTES + 8 * 32 * ST_XP * sizeof(float2);
 
 __host__ __device__ inline int st_row_tiles(int nj, int I) { return nj < 4 * I + 4 ? nj : 4 * I + 4; }
@@ -496,13 +497,14 @@ __global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fa
             if (tid == 0) {
                 tc::fence_after();
                 const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl);
-                const uint32_t b0 = tc::smem_u32(bh), b1 = tc::smem_u32(bl);
+                const uint32_t b0 = tc::smem_u32(bh);
                 const uint32_t d = taddr + (uint32_t)(2 * ST_N * (J & 1));
 #pragma unroll
+                // B lo follows B hi (rows ST_N .. 2 ST_N - 1 of one operand), the cross-term
+                // accumulator follows the hi x hi one: A_hi x [B_hi; B_lo] is one N = 2 ST_N product
                 for (int ks = 0; ks < 8; ++ks) {
                     const uint32_t o = ks * 256, acc = ks > 0 ? 1u : 0u;
-                    tc::mma_tf32(d, tc::smem_desc(ah + o, ST_SBO), tc::smem_desc(b0 + o, ST_SBO), ST_IDESC, acc);
-                    tc::mma_tf32(d + ST_N, tc::smem_desc(ah + o, ST_SBO), tc::smem_desc(b1 + o, ST_SBO), ST_IDESC, acc);
+                    tc::mma_tf32(d, tc::smem_desc(ah + o, ST_SBO), tc::smem_desc(b0 + o, ST_SBO), ST_IDESC2, acc);
                     tc::mma_tf32(d + ST_N, tc::smem_desc(al + o, ST_SBO), tc::smem_desc(b0 + o, ST_SBO), ST_IDESC, 1u);
                 }
                 tc::commit(tc::smem_u32(&mbar[J & 1]));
@@ -1258,6 +1260,7 @@ constexpr int FU_A_BYTES = 128 * FU_KR * 4;             // 128 x 128 binary32 (h
 constexpr int FU_B_BYTES = FU_N * FU_KR * 4;            // 64 x 128 binary32 (hi or lo)
 constexpr uint32_t FU_SBO = (FU_KR / 4) * 128;
 constexpr uint32_t FU_IDESC = tc::idesc_tf32(128, FU_N);
+constexpr uint32_t FU_IDESC2 = tc::idesc_tf32(128, 2 * FU_N);     // A_hi x [B_hi; B_lo]
 constexpr size_t FU_SMEM = 2 * (size_t)FU_A_BYTES + 2 * (size_t)FU_B_BYTES;
 constexpr uint32_t FU_TMEM = 4 * FU_N;                  // two sets of (hi x hi, cross terms)
 
@@ -1365,11 +1368,13 @@ __global__ void __launch_bounds__(256, 1) k_formsb_update_tc(const float2* __res
     auto issue = [&](int t) {                             // one thread: the 48 MMAs of local tile t
         tc::fence_after();
         const uint32_t d = taddr + (uint32_t)(2 * FU_N * (t & 1));
+        // B lo follows B hi in shared memory (rows FU_N .. 2 FU_N - 1 of one operand) and the
+        // cross-term accumulator follows the hi x hi one in tensor memory, so A_hi x [B_hi; B_lo]
+        // is one N = 2 FU_N product: A_hi is read once per K step for both terms
 #pragma unroll
         for (int ks = 0; ks < FU_KR / 8; ++ks) {
             const uint32_t o = ks * 256, acc = ks > 0 ? 1u : 0u;
-            tc::mma_tf32(d, tc::smem_desc(ah + o, FU_SBO), tc::smem_desc(bh + o, FU_SBO), FU_IDESC, acc);
-            tc::mma_tf32(d + FU_N, tc::smem_desc(ah + o, FU_SBO), tc::smem_desc(bl + o, FU_SBO), FU_IDESC, acc);
+            tc::mma_tf32(d, tc::smem_desc(ah + o, FU_SBO), tc::smem_desc(bh + o, FU_SBO), FU_IDESC2, acc);
             tc::mma_tf32(d + FU_N, tc::smem_desc(al + o, FU_SBO), tc::smem_desc(bh + o, FU_SBO), FU_IDESC, 1u);
         }
         tc::commit(tc::smem_u32(&mbar[t & 1]));

@@ -38,6 +38,31 @@ def test_alone_equals_in_mix(gwlib, prec_name):
             assert np.array_equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("prec_name", ["GW_MIXED", "GW_FP64"])
+def test_alone_equals_in_mix_large_paths(gwlib, prec_name):
+    """The same with molecules that take the large-size code paths while
+    other jobs run beside them: the 16-atom chain (N_sub 480: batched forms
+    with the tensor-core panel-pair update on the binary32 path; N_rank 1040:
+    the cooperative grid-wide tridiagonalisation and the blocked
+    back-transformation), the 13-atom chain (N_sub 390, N_rank 845) and the
+    11-atom ring (N_sub 330: tensor-memory forms; N_rank 715)."""
+    prec = getattr(gwlib, prec_name)
+    grid = synth.Grid(256)
+    spec = [("chain", 16), ("ring", 11), ("chain", 13), ("chain", 5)]
+    mols = [sm._uniform_molecule(k, n, synth.molecules.SEED_BASE + 7100 + i) for i, (k, n) in enumerate(spec)]
+    assert [m.n_sub for m in mols[:3]] == [480, 330, 390]
+    srv = gwlib.Server(0, n_workers=3, hbm_budget_bytes=40 << 30)
+    try:
+        alone = [srv.wait(srv.submit(m, grid, prec=prec)) for m in mols]
+        jobs = [srv.submit(m, grid, prec=prec) for m in mols]
+        mixed = [srv.wait(j) for j in jobs]
+    finally:
+        srv.close()
+    for a, b in zip(alone, mixed):
+        for k in ("e_qp", "z", "status", "sigma_x"):
+            assert np.array_equal(a[k], b[k]), k
+
+
 def test_matches_direct_call(gwlib, ctx):
     grid = synth.Grid(256)
     m = _mols()[1]
