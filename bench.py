@@ -191,14 +191,13 @@ def _panels(n, nb):
     return out
 
 
-def _form_pairs(n, nb=32):
-    """Panel pairs of the batched forward substitution: (first panel width,
-    second panel width, rows below the pair) per pair."""
+def _form_blocks(n, nb=32, bm=128):
+    """Blocks of the left-looking batched forward substitution: (i0, i1, panel
+    widths) per block of bm rows."""
     out = []
-    for k0 in range(0, n, 2 * nb):
-        k1 = min(n, k0 + nb)
-        k2 = min(n, k1 + nb)
-        out.append((k1 - k0, k2 - k1, n - k2))
+    for i0 in range(0, n, bm):
+        i1 = min(n, i0 + bm)
+        out.append((i0, i1, [min(nb, i1 - k0) for k0 in range(i0, i1, nb)]))
     return out
 
 
@@ -245,18 +244,18 @@ def kernel_model(name, mol, grid, n_rank=None):
         return (fwd, "tensor", PEAK_TF32_TFLOPS / 3) if fk == name else (None, None, None)
     if name == "k_forms32":
         return (fwd, "alu", PEAK_FP32_TFLOPS) if fk == name else (None, None, None)
-    if name in ("k_forms32_update", "k_forms32_update_tc"):
+    if name in ("k_forms32_update", "k_forms32_gemm_tc"):
         if fk != "batched":
             return None, None, None
-        # per pair: the first panel's update of the second panel's rows (binary32 FMA), then the
-        # update of the rows below the pair by both panels (tensor cores from 64 rows on)
+        # per block of 128 rows: the product of all rows above it (tensor cores), then the
+        # updates inside the block by its first three panels (binary32 FMA)
         fma = tcf = 0.0
-        for b1, b2, m in _form_pairs(n):
-            fma += 8.0 * R * b2 * b1
-            if m >= 64:
-                tcf += 8.0 * R * m * (b1 + b2)
-            else:
-                fma += 8.0 * R * m * (b1 + b2)
+        for i0, i1, widths in _form_blocks(n):
+            tcf += 8.0 * R * (i1 - i0) * i0
+            k0 = i0
+            for kb in widths:
+                fma += 8.0 * R * (i1 - k0 - kb) * kb
+                k0 += kb
         if name == "k_forms32_update":
             return (N - 1) * fma, "alu", PEAK_FP32_TFLOPS
         return ((N - 1) * tcf, "tensor", PEAK_TF32_TFLOPS / 3) if tcf > 0 else (None, None, None)
@@ -305,16 +304,22 @@ def kernel_bytes(name, mol, grid):
         if forms_kernel(n, R) != name:
             return None
         return (N - 1) * (tri * cz + ((n + 31) // 32) * 32 * 32 * cz)
-    if name in ("k_forms32_update", "k_forms32_update_tc") and forms_kernel(n, R) == "batched":
-        # per pair and frequency: the updated rows of Y read and written once, their
-        # rows of the factor's panel columns and the pair's rows of Y read once
-        tc_ = name.endswith("_tc")
+    if name in ("k_forms32_update", "k_forms32_gemm_tc") and forms_kernel(n, R) == "batched":
         b = 0.0
-        for b1, b2, m in _form_pairs(n):
-            if not tc_:
-                b += b2 * R * 2 * cz + b2 * b1 * cz + b1 * R * cz
-            if (m >= 64) == tc_ and m > 0:
-                b += m * R * 2 * cz + m * (b1 + b2) * cz + (b1 + b2) * R * cz
+        for i0, i1, widths in _form_blocks(n):
+            m = i1 - i0
+            if name == "k_forms32_gemm_tc":
+                if i0 > 0:
+                    # the rows of Y above the block and the block's rows of L read once, the
+                    # block's rows of q (binary64) read and of Y written once
+                    b += i0 * R * cz + m * i0 * cz + m * R * 8 + m * R * cz
+            else:
+                k0 = i0
+                for kb in widths:
+                    rows = i1 - k0 - kb
+                    if rows > 0:
+                        b += rows * R * 2 * cz + rows * kb * cz + kb * R * cz
+                    k0 += kb
         return (N - 1) * b if b > 0 else None
     return None
 
@@ -353,7 +358,7 @@ def per_kernel_roofline(kt, mols, grid, total_ms):
     return out
 
 
-KERNELS = ["k_forms32", "k_forms32_tm", "k_forms32_diag", "k_forms32_update", "k_forms32_update_tc",
+KERNELS = ["k_forms32", "k_forms32_tm", "k_forms32_diag", "k_forms32_update", "k_forms32_gemm_tc",
            "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk", "k_ldlt32_syrk_tc", "k_chi0_kk_fma", "k_chi0_kk_tc", "k_kk_ctable", "k_deposit_syrk32",
            "k_sgemm", "k_sgemm_tc", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl", "k_bisect", "k_invit",
            "k_backtransform", "k_cluster_mgs", "k_rayleigh_cols", "k_vertex_contract", "k_vertex_contract32",

@@ -1242,207 +1242,196 @@ __global__ void __launch_bounds__(256) k_formsb_update(const C* __restrict__ fac
     }
 }
 
-// The same update for a panel pair on the tensor cores (binary32 path):
-// Y[r][q] -= sum_p L[r][p] y[p][q] over the pair's 64 complex columns p is
-// one real TF32 product with the complex entries interleaved along K
-// (K = 128, 3xTF32 as in k_ldlt_syrk_tc):
-//   A[r][2p] = Re L[r][p], A[r][2p+1] = Im L[r][p]
-//   B[q][2p] = Re y[p][q], B[q][2p+1] = -Im y[p][q]; B[32+q][2p] = Im y, B[32+q][2p+1] = Re y
-// so that accumulator columns q and 32 + q hold Re and Im of (L y)[r][q].
-// One CTA per (frequency, 128-row block, run of column tiles of 32
-// right-hand sides) stages its rows of L once (hi and lo, 128 KB) and walks
-// the run: the MMAs of tile t + 1 run while tile t is read back and
-// subtracted from Y.  Each thread owns one row and 16 consecutive
-// right-hand sides of a tile (128 contiguous bytes of Y), so the
-// read-modify-write needs no transpose.
-constexpr int FU_KC = 64, FU_KR = 2 * FU_KC, FU_NC = 32, FU_N = 2 * FU_NC;
-constexpr int FU_A_BYTES = 128 * FU_KR * 4;             // 128 x 128 binary32 (hi or lo)
-constexpr int FU_B_BYTES = FU_N * FU_KR * 4;            // 64 x 128 binary32 (hi or lo)
-constexpr uint32_t FU_SBO = (FU_KR / 4) * 128;
-constexpr uint32_t FU_IDESC = tc::idesc_tf32(128, FU_N);
-constexpr uint32_t FU_IDESC2 = tc::idesc_tf32(128, 2 * FU_N);     // A_hi x [B_hi; B_lo]
-constexpr size_t FU_SMEM = 2 * (size_t)FU_A_BYTES + 2 * (size_t)FU_B_BYTES;
-constexpr uint32_t FU_TMEM = 4 * FU_N;                  // two sets of (hi x hi, cross terms)
+// Left-looking form of the batched forward substitution (binary32 path):
+// block I of 128 rows (rows i0 .. i1) first takes the product of every row
+// above it at once,
+//   Y[i0:i1, :] = q[i0:i1, :] - L[i0:i1, 0:i0] Y[0:i0, :],
+// as one real TF32 product per 128-row block and tile of 128 right-hand
+// sides, with the complex entries interleaved along K (3xTF32: A_hi B_hi
+// into one tensor-memory accumulator, A_hi B_lo + A_lo B_hi into a second;
+// M = 128, N = 256 = Re and Im of 128 right-hand sides, K = 8 per MMA).  The
+// K loop runs over chunks of 16 columns of L in two shared-memory buffers
+// (hi and lo of the block's L rows and of the chunk's rows of Y, 96 KB
+// each): eight producer warps load a chunk two chunks ahead, split it and
+// store it in the canonical K-major layout, then arrive on the buffer's
+// `full` barrier; a ninth warp issues the chunk's 12 MMAs once it is full
+// and commits their completion to the buffer's `empty` barrier.  The
+// accumulators stay in tensor memory (all 512 columns) for the whole K loop
+// and each block of Y is written once.  The four 32-row panels of the block
+// then take the diagonal-block solves and the small updates inside the
+// block (k_formsb_diag, k_formsb_update).  Y is read once per block below
+// it instead of read and written once per panel pair.  One CTA per (tile of
+// right-hand sides, frequency); the tiles of one frequency are neighbours
+// in the grid and share L through L2.
+constexpr int FG_KC = 16, FG_KR = 2 * FG_KC, FG_NC = 128, FG_N = 2 * FG_NC;
+constexpr int FG_A_BYTES = 128 * FG_KR * 4;             // 128 x 32 binary32 (hi or lo): 16 KB
+constexpr int FG_B_BYTES = FG_N * FG_KR * 4;            // 256 x 32 binary32 (hi or lo): 32 KB
+constexpr int FG_STAGE = 2 * FG_A_BYTES + 2 * FG_B_BYTES;
+constexpr uint32_t FG_SBO = (FG_KR / 4) * 128;
+constexpr uint32_t FG_IDESC = tc::idesc_tf32(128, FG_N);
+constexpr size_t FG_SMEM = 2 * (size_t)FG_STAGE;
+constexpr uint32_t FG_TMEM = 2 * FG_N;                  // hi x hi and cross terms: all 512 columns
 
-// this thread's raw B entries of column tile c0: y[2 kq][q] and y[2 kq + 1][q]
-__device__ __forceinline__ void fu_load_b(float2 (&yb)[4][2], const float2* __restrict__ Yk, int R, int kk0, int kw,
-                                          int c0) {
+// this thread's raw entries of chunk kk (columns kk .. kk + 15 of L rows i0 ..,
+// rows kk .. kk + 15 of Y): 4 quads of A, 4 quads of B (two complex each)
+__device__ __forceinline__ void fg_load(float2 (&av)[4][2], float2 (&bv)[4][2], const float2* __restrict__ F,
+                                        const float2* __restrict__ Yk, int R, int i0, int i1, int kk, int c0) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int idx = threadIdx.x + 256 * j, q = idx & 31, p = 2 * (idx >> 5), col = c0 + q;
-        yb[j][0] = (col < R && p < kw) ? Yk[(long long)(kk0 + p) * R + col] : make_float2(0.f, 0.f);
-        yb[j][1] = (col < R && p + 1 < kw) ? Yk[(long long)(kk0 + p + 1) * R + col] : make_float2(0.f, 0.f);
-    }
-}
-
-__device__ __forceinline__ void fu_store_b(const float2 (&yb)[4][2], unsigned char* bh, unsigned char* bl) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int idx = threadIdx.x + 256 * j, q = idx & 31, kq = idx >> 5;
-        const float2 y0 = yb[j][0], y1 = yb[j][1];
-        st_shared_quad(bh, bl, tc::core_off(q, 4 * kq, FU_KR / 4), y0.x, -y0.y, y1.x, -y1.y);
-        st_shared_quad(bh, bl, tc::core_off(FU_NC + q, 4 * kq, FU_KR / 4), y0.y, y0.x, y1.y, y1.x);
-    }
-}
-
-// the current values of this thread's 16 entries (row r, columns cb ..): Y, or q before the first update
-template <bool VEC>
-__device__ __forceinline__ void fu_load_c(float2 (&cv)[16], const float2* __restrict__ Yk, const double* __restrict__ Q,
-                                          int R, int r, int r_hi, int cb, bool first) {
-    if (r >= r_hi) return;
-    const long long o = (long long)r * R + cb;
-    if (VEC && cb + 16 <= R) {
-        if (first) {
-#pragma unroll
-            for (int t = 0; t < 16; t += 2) {
-                const double2 qq = *reinterpret_cast<const double2*>(Q + o + t);
-                cv[t] = make_float2((float)qq.x, 0.f);
-                cv[t + 1] = make_float2((float)qq.y, 0.f);
-            }
+        const int idx = threadIdx.x + 256 * j, rr = idx & 7, kq = (idx >> 3) & 7, rg = idx >> 6;
+        const int ra = i0 + 8 * rg + rr;
+        if (ra < i1) {
+            const float2* src = F + tri(ra) + kk + 2 * kq;
+            av[j][0] = src[0];
+            av[j][1] = src[1];
         } else {
-#pragma unroll
-            for (int t = 0; t < 16; t += 2) {
-                const float4 v = *reinterpret_cast<const float4*>(Yk + o + t);
-                cv[t] = make_float2(v.x, v.y);
-                cv[t + 1] = make_float2(v.z, v.w);
-            }
+            av[j][0] = av[j][1] = make_float2(0.f, 0.f);
         }
-    } else {
+    }
 #pragma unroll
-        for (int t = 0; t < 16; ++t)
-            cv[t] = cb + t < R ? (first ? make_float2((float)Q[o + t], 0.f) : Yk[o + t]) : make_float2(0.f, 0.f);
+    for (int j = 0; j < 4; ++j) {
+        const int idx = threadIdx.x + 256 * j, q = idx & 127, kq = idx >> 7, col = c0 + q;
+        if (col < R) {
+            bv[j][0] = Yk[(long long)(kk + 2 * kq) * R + col];
+            bv[j][1] = Yk[(long long)(kk + 2 * kq + 1) * R + col];
+        } else {
+            bv[j][0] = bv[j][1] = make_float2(0.f, 0.f);
+        }
     }
 }
 
-template <bool VEC>
-__global__ void __launch_bounds__(256, 1) k_formsb_update_tc(const float2* __restrict__ fac, int n,
-                                                             const double* __restrict__ Q, int R,
-                                                             float2* __restrict__ Y, int kk0, int kw, int r_lo,
-                                                             int r_hi, int kbase, int tiles_per_cta, int* status) {
-    extern __shared__ __align__(128) unsigned char sraw_fu[];
-    unsigned char* sAh = sraw_fu;
-    unsigned char* sAl = sAh + FU_A_BYTES;
-    unsigned char* sBh = sAl + FU_A_BYTES;
-    unsigned char* sBl = sBh + FU_B_BYTES;
-    __shared__ __align__(8) uint64_t mbar[2];
+__device__ __forceinline__ void fg_store(const float2 (&av)[4][2], const float2 (&bv)[4][2], unsigned char* st) {
+    unsigned char* ah = st;
+    unsigned char* al = ah + FG_A_BYTES;
+    unsigned char* bh = al + FG_A_BYTES;
+    unsigned char* bl = bh + FG_B_BYTES;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int idx = threadIdx.x + 256 * j, rr = idx & 7, kq = (idx >> 3) & 7, rg = idx >> 6;
+        st_shared_quad(ah, al, tc::core_off(8 * rg + rr, 4 * kq, FG_KR / 4), av[j][0].x, av[j][0].y, av[j][1].x,
+                       av[j][1].y);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int idx = threadIdx.x + 256 * j, q = idx & 127, kq = idx >> 7;
+        const float2 y0 = bv[j][0], y1 = bv[j][1];
+        st_shared_quad(bh, bl, tc::core_off(q, 4 * kq, FG_KR / 4), y0.x, -y0.y, y1.x, -y1.y);
+        st_shared_quad(bh, bl, tc::core_off(FG_NC + q, 4 * kq, FG_KR / 4), y0.y, y0.x, y1.y, y1.x);
+    }
+}
+
+__global__ void __launch_bounds__(288, 1) k_formsb_gemm_tc(const float2* __restrict__ fac, int n,
+                                                           const double* __restrict__ Q, int R,
+                                                           float2* __restrict__ Y, int i0, int i1, int kbase,
+                                                           int* status) {
+    extern __shared__ __align__(128) unsigned char sraw_fg[];
+    __shared__ __align__(8) uint64_t full[2], empty[2], done;
     __shared__ uint32_t tbase;
+    __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int z = blockIdx.z, k = kbase + z;
+    const int z = blockIdx.y, k = kbase + z, c0 = FG_NC * blockIdx.x;
     const float2* F = fac + (long long)k * tri(n);
     float2* Yk = Y + (long long)z * n * R;
-    const int r0 = r_lo + 128 * blockIdx.x;
-    const int t_all = (R + FU_NC - 1) / FU_NC, J0 = blockIdx.y * tiles_per_cta;
-    const int nt = min(t_all, J0 + tiles_per_cta) - J0;
-    if (nt <= 0) return;                                  // uniform over the CTA
-    const bool first = kk0 == 0;
-    // this thread's read-back entries: row r, right-hand sides 16 h .. 16 h + 15 of a tile
-    const int r = r0 + 32 * (warp & 3) + lane, h = warp >> 2;
-    if (warp == 0) tc::tmem_alloc(&tbase, FU_TMEM);
+    const int nk = i0 / FG_KC;                            // i0 is a multiple of 128
+    if (warp == 0) tc::tmem_alloc(&tbase, FG_TMEM);
     if (tid == 0) {
-        tc::mbar_init(&mbar[0]);
-        tc::mbar_init(&mbar[1]);
+        tc::mbar_init_n(&full[0], 256);
+        tc::mbar_init_n(&full[1], 256);
+        tc::mbar_init(&empty[0]);
+        tc::mbar_init(&empty[1]);
+        tc::mbar_init(&done);
+        s_abort = 0;
     }
-    float2 yb[4][2], cvA[16], cvB[16];
-    fu_load_b(yb, Yk, R, kk0, kw, FU_NC * J0);
-    fu_load_c<VEC>(cvA, Yk, Q, R, r, r_hi, FU_NC * J0 + 16 * h, first);
-    // A operand: rows r0 .. r0 + 127 of the panel pair, staged once
-#pragma unroll 4
-    for (int j = 0; j < 16; ++j) {
-        const int idx = tid + 256 * j, rr = idx & 7, kq = (idx >> 3) & 31, rg = idx >> 8;
-        const int ra = r0 + 8 * rg + rr, p = 2 * kq;
-        float2 a = make_float2(0.f, 0.f), b = a;
-        if (ra < r_hi) {
-            const float2* src = F + tri(ra) + kk0 + p;
-            if (p < kw) a = src[0];
-            if (p + 1 < kw) b = src[1];
-        }
-        st_shared_quad(sAh, sAl, tc::core_off(8 * rg + rr, 4 * kq, FU_KR / 4), a.x, a.y, b.x, b.y);
-    }
-    fu_store_b(yb, sBh, sBl);
-    if (nt > 1) fu_load_b(yb, Yk, R, kk0, kw, FU_NC * (J0 + 1));
-    tc::fence_async_smem();
     __syncthreads();
     tc::fence_after();
     const uint32_t taddr = tbase;
-    const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
-    auto issue = [&](int t) {                             // one thread: the 48 MMAs of local tile t
-        tc::fence_after();
-        const uint32_t d = taddr + (uint32_t)(2 * FU_N * (t & 1));
-        // B lo follows B hi in shared memory (rows FU_N .. 2 FU_N - 1 of one operand) and the
-        // cross-term accumulator follows the hi x hi one in tensor memory, so A_hi x [B_hi; B_lo]
-        // is one N = 2 FU_N product: A_hi is read once per K step for both terms
-#pragma unroll
-        for (int ks = 0; ks < FU_KR / 8; ++ks) {
-            const uint32_t o = ks * 256, acc = ks > 0 ? 1u : 0u;
-            tc::mma_tf32(d, tc::smem_desc(ah + o, FU_SBO), tc::smem_desc(bh + o, FU_SBO), FU_IDESC2, acc);
-            tc::mma_tf32(d + FU_N, tc::smem_desc(al + o, FU_SBO), tc::smem_desc(bh + o, FU_SBO), FU_IDESC, 1u);
-        }
-        tc::commit(tc::smem_u32(&mbar[t & 1]));
-    };
-    if (tid == 0) issue(0);
-    bool ok = true;
-    int t = 0;
-    // local tile t: wait for its MMAs, stage and issue tile t + 1 (the B buffer is free), then
-    // read back tile t from register set cur while tile t + 1's entries load into nxt
-    auto step = [&](float2 (&cur)[16], float2 (&nxt)[16]) -> bool {
-        if (t + 1 < nt) fu_load_c<VEC>(nxt, Yk, Q, R, r, r_hi, FU_NC * (J0 + t + 1) + 16 * h, first);
-        ok = tc::mbar_wait(tc::smem_u32(&mbar[t & 1]), (t >> 1) & 1) && ok;
-        ok = __syncthreads_and(ok);
-        if (!ok) return false;
-        if (t + 1 < nt) {
-            fu_store_b(yb, sBh, sBl);
-            if (t + 2 < nt) fu_load_b(yb, Yk, R, kk0, kw, FU_NC * (J0 + t + 2));
+    volatile int* abort = &s_abort;
+    int issued = 0;                                       // chunks whose MMAs the issuing lane committed
+    if (warp < 8) {
+        // producers: chunk kc into buffer kc % 2 once the MMAs of chunk kc - 2 have released
+        // it (chunk c's raw entries in register set c % 2, loaded two chunks ahead)
+        float2 av0[4][2], bv0[4][2], av1[4][2], bv1[4][2];
+        fg_load(av0, bv0, F, Yk, R, i0, i1, 0, c0);
+        if (nk > 1) fg_load(av1, bv1, F, Yk, R, i0, i1, FG_KC, c0);
+        int kc = 0;
+        auto step = [&](float2 (&av)[4][2], float2 (&bv)[4][2]) -> bool {
+            const int s = kc & 1;
+            if (kc >= 2 && !tc::mbar_wait_abort(tc::smem_u32(&empty[s]), ((kc - 2) >> 1) & 1, abort)) return false;
+            fg_store(av, bv, sraw_fg + s * FG_STAGE);
+            if (kc + 2 < nk) fg_load(av, bv, F, Yk, R, i0, i1, FG_KC * (kc + 2), c0);
             tc::fence_async_smem();
-            __syncthreads();
-            if (tid == 0) issue(t + 1);
+            tc::mbar_arrive(tc::smem_u32(&full[s]));
+            return true;
+        };
+        while (kc < nk) {
+            if (!step(av0, bv0) || ++kc >= nk) break;
+            if (!step(av1, bv1)) break;
+            ++kc;
         }
-        tc::fence_after();
-        const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(2 * FU_N * (t & 1) + 16 * h);
-        uint32_t re[16], im[16], re2[16], im2[16];
-        tc::tmem_ld16(base, re);
-        tc::tmem_ld16(base + FU_NC, im);
-        tc::tmem_ld16(base + FU_N, re2);
-        tc::tmem_ld16(base + FU_N + FU_NC, im2);
-        tc::tmem_wait_ld();
-        tc::fence_before();
-        const int cb = FU_NC * (J0 + t) + 16 * h;
-        if (r < r_hi) {
-            float2 out[16];
+    } else if (lane == 0) {
+        // the MMA lane: chunk kc once its buffer is full, completion to empty[kc % 2]
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc & 1;
+            if (!tc::mbar_wait_abort(tc::smem_u32(&full[s]), (kc >> 1) & 1, abort)) break;
+            tc::fence_after();
+            const uint32_t st = tc::smem_u32(sraw_fg + s * FG_STAGE);
+            const uint32_t ah = st, al = st + FG_A_BYTES, bh = st + 2 * FG_A_BYTES, bl = bh + FG_B_BYTES;
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
-                out[q] = make_float2(cur[q].x - (__uint_as_float(re[q]) + __uint_as_float(re2[q])),
-                                     cur[q].y - (__uint_as_float(im[q]) + __uint_as_float(im2[q])));
-            float2* dst = Yk + (long long)r * R + cb;
-            if (VEC && cb + 16 <= R) {
+            for (int ks = 0; ks < FG_KR / 8; ++ks) {
+                const uint32_t o = ks * 256, acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                tc::mma_tf32(taddr, tc::smem_desc(ah + o, FG_SBO), tc::smem_desc(bh + o, FG_SBO), FG_IDESC, acc);
+                tc::mma_tf32(taddr + FG_N, tc::smem_desc(ah + o, FG_SBO), tc::smem_desc(bl + o, FG_SBO), FG_IDESC,
+                             acc);
+                tc::mma_tf32(taddr + FG_N, tc::smem_desc(al + o, FG_SBO), tc::smem_desc(bh + o, FG_SBO), FG_IDESC,
+                             1u);
+            }
+            tc::commit(tc::smem_u32(&empty[s]));
+            issued = kc + 1;
+        }
+        if (issued == nk) tc::commit(tc::smem_u32(&done));
+    }
+    // epilogue (producer warps): Y rows i0 .. i1 = q - product; warp w reads lanes
+    // 32 (w % 4) .. (rows) and right-hand sides 64 (w / 4) .. + 63 of the tile, 16 at a time
+    if (warp < 8) {
+        bool ok = tc::mbar_wait_abort(tc::smem_u32(&done), 0, abort);
+        ok = __all_sync(0xffffffffu, ok);                // tcgen05.ld below is warp-collective
+        if (ok) {
+            tc::fence_after();
+            const int r = i0 + 32 * (warp & 3) + lane, h = warp >> 2;
+            const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * h);
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {
+                uint32_t re[16], im[16], re2[16], im2[16];
+                tc::tmem_ld16(base + 16 * j, re);
+                tc::tmem_ld16(base + FG_NC + 16 * j, im);
+                tc::tmem_ld16(base + FG_N + 16 * j, re2);
+                tc::tmem_ld16(base + FG_N + FG_NC + 16 * j, im2);
+                tc::tmem_wait_ld();
+                if (r < i1) {
+                    const int cb = c0 + 64 * h + 16 * j;
+                    const long long o = (long long)r * R + cb;
 #pragma unroll
-                for (int q = 0; q < 16; q += 2)
-                    *reinterpret_cast<float4*>(dst + q) = make_float4(out[q].x, out[q].y, out[q + 1].x, out[q + 1].y);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (cb + q < R) dst[q] = out[q];
+                    for (int q = 0; q < 16; ++q)
+                        if (cb + q < R)
+                            Yk[o + q] = make_float2(
+                                (float)Q[o + q] - (__uint_as_float(re[q]) + __uint_as_float(re2[q])),
+                                -(__uint_as_float(im[q]) + __uint_as_float(im2[q])));
+                }
             }
         }
-        return true;
-    };
-    while (t < nt) {
-        if (!step(cvA, cvB) || ++t >= nt) break;
-        if (!step(cvB, cvA)) break;
-        ++t;
     }
-    if (!ok) {
-        // stopped at local tile t: tiles 0 .. t were issued; their MMAs finish before the columns are freed
+    __syncthreads();
+    if (*abort) {
+        // a wait ran out: the MMAs committed so far finish before the columns are freed
         if (tid == 0) atomicOr(status, ST_TIMEOUT);
-        for (int s2 = 0; s2 < 2; ++s2) {
-            const int cnt = t >= s2 ? (t - s2) / 2 + 1 : 0;
-            if (cnt > 0) tc::mbar_wait(tc::smem_u32(&mbar[s2]), (cnt - 1) & 1);
-        }
+        if (warp == 8 && lane == 0 && issued > 0)
+            tc::mbar_wait(tc::smem_u32(&empty[(issued - 1) & 1]), ((issued - 1) >> 1) & 1);
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 0) {
         tc::fence_after();
-        tc::tmem_dealloc(taddr, FU_TMEM);
+        tc::tmem_dealloc(taddr, FG_TMEM);
     }
 }
 
@@ -1588,6 +1577,24 @@ static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N
                     klaunch(ctx, names[1], k_formsb_update<C, NB>, dim3(div_up(n - k1, TT), div_up(R, TT), nbb), 256,
                             sm1, fac, n, Q, R, Y, k0, k1 - k0, k1, n, kbase);
                 }
+            } else if (!ctx->forms_simt) {
+                // left-looking in blocks of 128 rows: the product of all rows above the block on
+                // the tensor cores, then the block's four panels
+                allow_max_smem(k_formsb_gemm_tc);
+                for (int i0 = 0; i0 < n; i0 += 128) {
+                    const int i1 = std::min(n, i0 + 128);
+                    if (i0 > 0)
+                        klaunch(ctx, names[2], k_formsb_gemm_tc, dim3(div_up(R, FG_NC), nbb), 288, FG_SMEM,
+                                (const float2*)fac, n, Q, R, (float2*)Y, i0, i1, kbase, ctx->d_status);
+                    for (int k0 = i0; k0 < i1; k0 += NB) {
+                        const int k1 = std::min(i1, k0 + NB);
+                        klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q,
+                                R, Y, acc, cout, k0, kbase, kmap);
+                        if (k1 == i1) break;
+                        klaunch(ctx, names[1], k_formsb_update<C, NB>, dim3(div_up(i1 - k1, TT), div_up(R, TT), nbb),
+                                256, sm1, fac, n, Q, R, Y, k0, k1 - k0, k1, i1, kbase);
+                    }
+                }
             } else {
                 for (int k0 = 0; k0 < n; k0 += 2 * NB) {
                     // panel pair k0 .. k2: diagonal block, second panel's rows, diagonal block, rows below
@@ -1600,22 +1607,6 @@ static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N
                     klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q, R, Y, acc,
                             cout, k1, kbase, kmap);
                     if (k2 == n) break;
-                    if (!ctx->forms_simt && n - k2 >= 64) {
-                        // the rows below the pair on the tensor cores; runs of column tiles
-                        // so that about two CTAs per SM are in flight
-                        const int gx = div_up(n - k2, 128), t_all = div_up(R, FU_NC);
-                        const int want = div_up(2 * ctx->num_sms, gx * nbb);
-                        const int tpc = div_up(t_all, std::max(1, std::min(t_all, want)));
-                        const dim3 grid(gx, div_up(t_all, tpc), nbb);
-                        auto run = [&](auto kern) {
-                            allow_max_smem(kern);
-                            klaunch(ctx, names[2], kern, grid, 256, FU_SMEM, (const float2*)fac, n, Q, R, (float2*)Y,
-                                    k0, k2 - k0, k2, n, kbase, tpc, ctx->d_status);
-                        };
-                        if (R % 2 == 0) run(k_formsb_update_tc<true>);
-                        else run(k_formsb_update_tc<false>);
-                        continue;
-                    }
                     klaunch(ctx, names[1], k_formsb_update<C, 2 * NB>, dim3(div_up(n - k2, TT), div_up(R, TT), nbb), 256,
                             sm2, fac, n, Q, R, Y, k0, k2 - k0, k2, n, kbase);
                 }
@@ -1676,8 +1667,8 @@ void launch_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* co
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega;
     if (c->prec == GW_MIXED && !ctx->forms_simt && forms_tm(ctx, W, Q, R, cout)) return;
-    static const char* const b32[3] = {"k_forms32_diag", "k_forms32_update", "k_forms32_update_tc"};
-    static const char* const b64[3] = {"k_forms_diag", "k_forms_update", "k_forms_update_tc"};
+    static const char* const b32[3] = {"k_forms32_diag", "k_forms32_update", "k_forms32_gemm_tc"};
+    static const char* const b64[3] = {"k_forms_diag", "k_forms_update", "k_forms_gemm_tc"};
     if (c->prec == GW_MIXED)
         forms_run<float2>(ctx, W->fac32, (const float2*)W->linv, n, N, Q, R, cout, "k_forms32", b32);
     else
@@ -1713,7 +1704,7 @@ static void pole_factor(gw_ctx* ctx, const gw_W* W, const int* kd, int k1, int n
 }
 
 void launch_pole_forms(gw_ctx* ctx, const gw_W* W, const double* Q, int R, double* cout) {
-    static const char* const b64[3] = {"k_forms_diag", "k_forms_update", "k_forms_update_tc"};
+    static const char* const b64[3] = {"k_forms_diag", "k_forms_update", "k_forms_gemm_tc"};
     const gw_chi0* c = W->chi0;
     const int n = c->n_sub, N = c->grid.n_omega, np = (int)W->pole_k.size();
     if (np == 0) return;

@@ -86,6 +86,29 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
 }
 
+// mbarrier expecting `count` arrivals per phase
+__device__ __forceinline__ void mbar_init_n(uint64_t* mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// bounded wait that also gives up once *abort is set (checked every 256
+// polls); sets *abort itself when the limit runs out; false if it gave up
+__device__ __forceinline__ bool mbar_wait_abort(uint32_t mbar, uint32_t parity, volatile int* abort) {
+    for (long it = 0; it < (1L << 24); ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, P;\n}" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        if ((it & 255) == 255 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
 // bounded wait for the given parity of an mbarrier; false on timeout
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     for (long it = 0; it < (1L << 24); ++it) {
