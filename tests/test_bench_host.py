@@ -56,10 +56,15 @@ def test_batched_forms_model_splits_diagonal_and_update():
     n, R = mol.n_sub, 2 * mol.n_orb
     up, b1, _ = bench.kernel_model("k_forms32_update", mol, grid)
     dg, b2, _ = bench.kernel_model("k_forms32_diag", mol, grid)
-    assert b1 == b2 == "alu"
-    diag = 1023 * 8.0 * R * sum(kb * kb for kb, _ in bench._panels(n, 32))
-    fwd = 1023 * 8.0 * R * n * (n - 1) / 2
-    assert dg == pytest.approx(diag) and up == pytest.approx(fwd - diag / 2)
+    gm, b3, _ = bench.kernel_model("k_forms32_gemm_tc", mol, grid)
+    assert b1 == b2 == "alu" and b3 == "tensor"
+    P = bench._panels(n, 32)
+    diag = 1023 * 8.0 * R * sum(kb * kb for kb, _ in P)
+    # every entry of L strictly below the diagonal blocks once: the product of the rows above a
+    # 128-row block (tensor cores) plus the updates inside the block (FMA units)
+    off = 1023 * 8.0 * R * (n * (n - 1) / 2 - sum(kb * (kb - 1) / 2 for kb, _ in P))
+    assert dg == pytest.approx(diag) and up + gm == pytest.approx(off)
+    assert gm == pytest.approx(1023 * 8.0 * R * sum((min(n, i0 + 128) - i0) * i0 for i0 in range(0, n, 128)))
 
 
 def test_trailing_update_models_split_at_128_rows(ring):
