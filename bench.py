@@ -367,11 +367,21 @@ KERNELS = ["k_forms32", "k_forms32_tm", "k_forms32_diag", "k_forms32_update", "k
            "k_top_indices", "k_gather_cols", "k_ns_coeff", "k_ns_coeff32", "k_scale_cols_by", "k_oa_stats",
            "k_oa_E", "k_oa_stats_fin"]
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
-# of the current version of a kernel, on a job of this workload, scaled to
-# the average launch of the timed jobs; an entry is dropped whenever its
-# kernel changes.
-NCU_TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the
+# current version of a kernel (a 24-atom chain of this workload's family,
+# 512 frequencies: the full-size jobs are too large to capture), divided by
+# the algorithmic bytes of the captured launch; the bench scales it to the
+# average launch of the timed jobs.  An entry is dropped whenever its kernel
+# changes.
+NCU_TRAFFIC = {
+    # third trailing update (k0 = 64, 624 rows, 512 frequencies): 922.2 MB read + 752.4 MB written
+    "k_ldlt32_syrk_tc": {"ratio": 1674.6e6 / (512 * (624 * 625 / 2 * 16 + 624 * 32 * 8)),
+                         "capture": "k_ldlt_syrk_tc, chain24 N_omega 512, launch 3"},
+    # block i0 = 256 (rows 256..383, 511 frequencies): 803.1 MB read + 299.5 MB written; q (binary64)
+    # is shared by the frequencies and stays in L2
+    "k_forms32_gemm_tc": {"ratio": 1102.6e6 / (511 * (256 * 624 * 8 + 128 * 256 * 8 + 128 * 624 * 8 * 2)),
+                          "capture": "k_formsb_gemm_tc, chain24 N_omega 512, launch 2"},
+}
 
 
 def _pct(x, q):
@@ -604,8 +614,16 @@ def run_gpu(a):
     dom = max(kt.items(), key=lambda kv: kv[1][0])[0]
     flops, meta = workload_model(dom, timed_mols, grid, kernel_model)
     k_ms, k_n = kt[dom]
+    traffic, traffic_src = None, None
+    if dom in NCU_TRAFFIC:
+        b_alg, _ = workload_model(dom, timed_mols, grid, kernel_bytes)
+        if b_alg:
+            traffic = NCU_TRAFFIC[dom]["ratio"] * b_alg / k_n
+            traffic_src = ("ncu " + NCU_TRAFFIC[dom]["capture"] + ": DRAM bytes / algorithmic bytes = "
+                           f"{NCU_TRAFFIC[dom]['ratio']:.3f}, times the algorithmic bytes per launch of the timed jobs")
     roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-            "traffic": NCU_TRAFFIC.get(dom), "avg_launch_ms": k_ms / k_n, "launches": k_n, "share": k_ms / total_ms,
+            "traffic": traffic, "traffic_source": traffic_src, "avg_launch_ms": k_ms / k_n, "launches": k_n,
+            "share": k_ms / total_ms,
             "selected_by": "largest share of the kernel time of the timed jobs",
             "measured_in": "single-stream pass over the timed jobs, CUDA events around every launch on the "
                            "context stream"}
