@@ -323,7 +323,22 @@ __global__ void __launch_bounds__(512) k_sytrd32_grid(float* __restrict__ A, int
             float* ri = A + (long long)(k + 1 + i) * n + k + 2;
             const float vi = sv[i], wi = sw[i];
             float acc = 0.f;
-            for (int j = lane; j < m - 1; j += 32) {
+            int j = lane;
+            // eight loads of the row in flight per lane (the pass is bound by their latency);
+            // each lane still accumulates its columns in ascending order
+            for (; j + 32 * 7 < m - 1; j += 32 * 8) {
+                float a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = ri[j + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int jj = j + 32 * u;
+                    a[u] = a[u] - vi * sw[1 + jj] - wi * sv[1 + jj];
+                    ri[jj] = a[u];
+                    acc += a[u] * vn[jj];
+                }
+            }
+            for (; j < m - 1; j += 32) {
                 const float a = ri[j] - vi * sw[1 + j] - wi * sv[1 + j];
                 ri[j] = a;
                 acc += a * vn[j];

@@ -6,6 +6,10 @@ serve: replays a seeded Poisson arrival trace of molecules of uneven size
        closed-loop on a sample of the same jobs and compares the
        quasiparticle energies.
 batch: submits a whole batch of uneven molecules at once.
+sweep: replays the same jobs at several arrival rates and reports, per rate,
+       throughput and latency, and the highest rate the engine sustains
+       (completion rate at least 95 % of the offered rate and the p50 queueing
+       time below the p50 run time).
 one:   solves one synthetic chain or ring (13 orbitals, 60 products and 2
        occupied states per atom, 50 % compression) on one context stream,
        --repeat times, and reports the time per solve (a fixed case for
@@ -13,6 +17,7 @@ one:   solves one synthetic chain or ring (13 orbitals, 60 products and 2
 
 Usage: python -m paper_1101_2065_gb300.serve serve --jobs 60 --rate 10 --lo 4 --hi 16
        python -m paper_1101_2065_gb300.serve batch
+       python -m paper_1101_2065_gb300.serve sweep --jobs 24 --rates 0.5,1,2,4
        python -m paper_1101_2065_gb300.serve one --kind chain --atoms 24 --n-omega 512
 Prints one JSON line.
 """
@@ -107,6 +112,27 @@ def fp64_compare(mols, grid, mixed_results, sample, workers=1, budget=0):
             "same_root_branch": same}
 
 
+def rate_sweep(rates, n_jobs, lo, hi, n_omega, workers, budget):
+    """The same n_jobs molecules (the trace's first jobs: the size draws do not
+    depend on the rate) submitted at Poisson arrivals of each offered rate."""
+    out = {"mode": "sweep", "precision": "mixed", "jobs": n_jobs, "n_omega": n_omega, "workers": workers,
+           "hbm_budget_gb": budget / (1 << 30), "rates": []}
+    mols = None
+    for r in rates:
+        arrivals, jobs, grid = synth.make_serving_trace(n_jobs, r, lo, hi, n_omega)
+        if mols is None:
+            mols = [synth.molecules.build_job(j) for j in jobs]
+            out["atoms"] = [int(m.n_atoms) for m in mols]
+        res, span, errors = run_jobs(mols, grid, list(arrivals), gw.GW_MIXED, workers, budget)
+        sm_ = summarize(res, span, mols, errors)
+        sm_["offered_rate_per_s"] = r
+        out["rates"].append(sm_)
+    ok = [x for x in out["rates"] if x["completed"] == n_jobs and x["solves_per_s"] >= 0.95 * x["offered_rate_per_s"]
+          and x["queue_ms"]["p50"] <= x["run_ms"]["p50"]]
+    out["sustainable_rate_per_s"] = max((x["offered_rate_per_s"] for x in ok), default=None)
+    return out
+
+
 def solve_one(kind, atoms, n_omega, fp64=False, repeat=1):
     """Time gw_solve on one resident synthetic molecule (single stream)."""
     mol = sm._uniform_molecule(kind, atoms, sm.SEED_BASE + 9000 + atoms)
@@ -129,7 +155,8 @@ def solve_one(kind, atoms, n_omega, fp64=False, repeat=1):
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("mode", choices=["serve", "batch", "one"])
+    p.add_argument("mode", choices=["serve", "batch", "one", "sweep"])
+    p.add_argument("--rates", default="0.5,1,2,4", help="sweep: offered arrival rates (jobs/s)")
     p.add_argument("--kind", choices=["chain", "ring"], default="chain")
     p.add_argument("--atoms", type=int, default=24)
     p.add_argument("--fp64", action="store_true", help="one: the binary64 path instead of the mixed one")
@@ -147,6 +174,10 @@ def main(argv=None):
     budget = int(a.budget_gb * (1 << 30))
     if a.mode == "one":
         print(json.dumps(solve_one(a.kind, a.atoms, a.n_omega or 1024, a.fp64, a.repeat)))
+        return
+    if a.mode == "sweep":
+        rates = [float(x) for x in a.rates.split(",") if x]
+        print(json.dumps(rate_sweep(rates, a.jobs, a.lo, a.hi, a.n_omega or 1024, a.workers, budget)))
         return
     if a.mode == "serve":
         arrivals, jobs, grid = synth.make_serving_trace(a.jobs, a.rate, a.lo, a.hi, a.n_omega or 1024)
