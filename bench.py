@@ -358,8 +358,56 @@ def per_kernel_roofline(kt, mols, grid, total_ms):
     return out
 
 
+def roofline_of(dom, kt, timed_mols, grid, total_ms):
+    """Roofline of kernel `dom` from its summed CUDA-event time kt[dom] =
+    (ms, launches) over the timed jobs: compute and HBM fractions of the
+    algorithmic work, and the binding roof (HBM when the arithmetic intensity
+    lies below the ridge point of the compute peak and the HBM peak)."""
+    flops, meta = workload_model(dom, timed_mols, grid, kernel_model)
+    k_ms, k_n = kt[dom]
+    traffic, traffic_src = None, None
+    if dom in NCU_TRAFFIC:
+        b_alg, _ = workload_model(dom, timed_mols, grid, kernel_bytes)
+        if b_alg:
+            traffic = NCU_TRAFFIC[dom]["ratio"] * b_alg / k_n
+            traffic_src = ("ncu " + NCU_TRAFFIC[dom]["capture"] + ": DRAM bytes / algorithmic bytes = "
+                           f"{NCU_TRAFFIC[dom]['ratio']:.3f}, times the algorithmic bytes per launch of the timed jobs")
+    roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+            "traffic": traffic, "traffic_source": traffic_src, "avg_launch_ms": k_ms / k_n, "launches": k_n,
+            "share": k_ms / total_ms,
+            "selected_by": "largest share of the kernel time of the timed jobs",
+            "measured_in": "single-stream pass over the timed jobs, CUDA events around every launch on the "
+                           "context stream"}
+    if flops:
+        bound, peak = meta
+        t = k_ms / 1e3
+        b_alg, _ = workload_model(dom, timed_mols, grid, kernel_bytes)
+        cpeak_src = (PEAK_TF32_SOURCE + " = dense TF32 tensor peak, / 3: 3xTF32 takes three TF32 products per "
+                     "binary32 product" if bound == "tensor" else
+                     "128 binary32 FMA/clk/SM x 152 SMs x 2070 MHz (recipe unit counts and maximum clock)")
+        roof.update({"compute_bound": bound, "compute_tflops": flops / t / 1e12, "compute_peak_tflops": peak,
+                     "compute_frac": flops / t / 1e12 / peak, "flops_per_launch": flops / k_n,
+                     "compute_peak_source": cpeak_src})
+        # the binding roof: HBM when the kernel's arithmetic intensity (algorithmic flops per
+        # algorithmic byte) lies below the ridge point peak flops / peak bandwidth
+        ridge = peak * 1e12 / (PEAK_HBM_GBS * 1e9)
+        intensity = flops / b_alg if b_alg else None
+        roof.update({"intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge})
+        if intensity is not None and intensity < ridge:
+            roof.update({"bound": "hbm", "achieved": b_alg / t / 1e9, "peak": PEAK_HBM_GBS, "unit": "GB/s",
+                         "frac": b_alg / t / 1e9 / PEAK_HBM_GBS, "bytes_per_launch": b_alg / k_n,
+                         "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json)"
+                         if PEAK_HBM_SOURCE == "measured" else "fallback 6.8 TB/s"})
+        else:
+            roof.update({"bound": bound, "achieved": flops / t / 1e12, "peak": peak,
+                         "frac": flops / t / 1e12 / peak, "peak_source": cpeak_src})
+
+    return roof
+
+
 KERNELS = ["k_forms32", "k_forms32_tm", "k_forms32_diag", "k_forms32_update", "k_forms32_gemm_tc",
-           "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk", "k_ldlt32_syrk_tc", "k_chi0_kk_fma", "k_chi0_kk_tc", "k_kk_ctable", "k_deposit_syrk32",
+           "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk", "k_ldlt32_syrk_tc", "k_chi0_kk_fma", "k_chi0_kk_tc",
+           "k_kk_ctable", "k_deposit_syrk32",
            "k_sgemm", "k_sgemm_tc", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl", "k_bisect", "k_invit",
            "k_backtransform", "k_cluster_mgs", "k_rayleigh_cols", "k_vertex_contract", "k_vertex_contract32",
            "k_sigma_c", "k_sigma_grid", "k_qp", "k_sigma_x", "k_chol_panel", "k_pair_rank", "k_pair_keys",
@@ -612,29 +660,7 @@ def run_gpu(a):
     total_ms = sum(v[0] for v in kt.values())
     table = per_kernel_roofline(kt, timed_mols, grid, total_ms)
     dom = max(kt.items(), key=lambda kv: kv[1][0])[0]
-    flops, meta = workload_model(dom, timed_mols, grid, kernel_model)
-    k_ms, k_n = kt[dom]
-    traffic, traffic_src = None, None
-    if dom in NCU_TRAFFIC:
-        b_alg, _ = workload_model(dom, timed_mols, grid, kernel_bytes)
-        if b_alg:
-            traffic = NCU_TRAFFIC[dom]["ratio"] * b_alg / k_n
-            traffic_src = ("ncu " + NCU_TRAFFIC[dom]["capture"] + ": DRAM bytes / algorithmic bytes = "
-                           f"{NCU_TRAFFIC[dom]['ratio']:.3f}, times the algorithmic bytes per launch of the timed jobs")
-    roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-            "traffic": traffic, "traffic_source": traffic_src, "avg_launch_ms": k_ms / k_n, "launches": k_n,
-            "share": k_ms / total_ms,
-            "selected_by": "largest share of the kernel time of the timed jobs",
-            "measured_in": "single-stream pass over the timed jobs, CUDA events around every launch on the "
-                           "context stream"}
-    if flops:
-        bound, peak = meta
-        roof.update({"bound": bound, "achieved": (flops / k_n) / (k_ms / k_n / 1e3) / 1e12, "peak": peak,
-                     "frac": flops / (k_ms / 1e3) / 1e12 / peak, "flops_per_launch": flops / k_n,
-                     "peak_source": (PEAK_TF32_SOURCE + " = dense TF32 tensor peak, / 3: 3xTF32 takes three TF32 "
-                                     "products per binary32 product" if bound == "tensor" else
-                                     "128 binary32 FMA/clk/SM x 152 SMs x 2070 MHz (recipe unit counts and maximum "
-                                     "clock)")})
+    roof = roofline_of(dom, kt, timed_mols, grid, total_ms)
 
     # context: the 60-atom cage (largest single molecule) and the 12-atom ring, single stream
     extra = {}

@@ -154,3 +154,23 @@ def test_clock_sampler_without_window_samples():
     assert r["samples"] == 1 and r["samples_from"].startswith("sampler run")
     assert r["reasons"] == ["sw_power_cap"]
     assert math.isclose(r["sm_mhz"], 1980)
+
+
+def test_roofline_picks_the_binding_roof():
+    """The trailing update (16 flops per byte, below the ridge point of the
+    3xTF32 ceiling and the HBM bandwidth) is reported against HBM; the forms
+    block product (about 90 flops per byte) against the tensor ceiling."""
+    from synth import molecules as sm
+    mol = sm._uniform_molecule("chain", 40, 1)           # n = 1200: batched forms, tensor-core updates
+    grid = synth.Grid(1024)
+    kt = {"k_ldlt32_syrk_tc": (100.0, 10), "k_forms32_gemm_tc": (50.0, 5)}
+    r = bench.roofline_of("k_ldlt32_syrk_tc", kt, [mol], grid, 150.0)
+    assert r["intensity_flop_per_byte"] < r["ridge_flop_per_byte"]
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == bench.PEAK_HBM_GBS
+    b, _ = bench.workload_model("k_ldlt32_syrk_tc", [mol], grid, bench.kernel_bytes)
+    assert r["achieved"] == pytest.approx(b / 0.1 / 1e9) and r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["compute_frac"] == pytest.approx(r["compute_tflops"] / r["compute_peak_tflops"])
+    g = bench.roofline_of("k_forms32_gemm_tc", kt, [mol], grid, 150.0)
+    assert g["intensity_flop_per_byte"] > g["ridge_flop_per_byte"]
+    assert g["bound"] == "tensor" and g["unit"] == "TFLOP/s"
+    assert g["share"] == pytest.approx(50.0 / 150.0)
