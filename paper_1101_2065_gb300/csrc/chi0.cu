@@ -255,19 +255,31 @@ __device__ __forceinline__ void tile_ij(int tt, int& I, int& J) {
 // With Asplit given (binary32 path), the weights are written instead as
 // TF32 hi/lo operand images for the tensor-core Kramers-Kronig product
 // (kk_layout.cuh).
+// four consecutive entries of a 16-byte aligned shared-memory row
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+    const double2 q0 = *reinterpret_cast<const double2*>(p), q1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_deposit_syrk(const R* __restrict__ Ut, int n_pair, int n_sub,
                                                       const int* __restrict__ seg, const double* __restrict__ frac,
                                                       int nb_bins, int BC, long long n_el, R* __restrict__ A,
                                                       uint32_t* __restrict__ Asplit, long long n_et) {
-    constexpr int T = 64, KC = 32;
-    __shared__ R Um[KC][T + 1];     // w_p u_pm for the tile's rows m
-    __shared__ R Un[KC][T + 1];     // u_pn for the tile's columns n
+    constexpr int T = 64, KC = 32, TP = T + 4;     // row pitch: 16-byte aligned rows
+    __shared__ __align__(16) R Um[KC][TP];         // w_p u_pm for the tile's rows m
+    __shared__ __align__(16) R Un[KC][TP];         // u_pn for the tile's columns n
     int I, J;
     tile_ij(blockIdx.x, I, J);
     const int m0 = I * T, n0 = J * T;
     const int band = nb_bins + 1;
     const int b0 = blockIdx.y * BC, b1 = min(b0 + BC, band);
+    // each thread: rows m0 + 4 ty .. + 3, columns n0 + 4 tx .. + 3 (four consecutive entries of
+    // a staged row per vector load)
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     for (int b = b0; b < b1; ++b) {
         const int lo = seg[b > 0 ? b - 1 : 0], mid = seg[b], hi = seg[b < nb_bins ? b + 1 : nb_bins];
@@ -293,10 +305,8 @@ __global__ void __launch_bounds__(256) k_deposit_syrk(const R* __restrict__ Ut, 
             const int kc = min(KC, hi - p0);
             for (int k = 0; k < kc; ++k) {
                 R a[4], c[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = Um[k][ty + 16 * i];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) c[j] = Un[k][tx + 16 * j];
+                load4(&Um[k][4 * ty], a);
+                load4(&Un[k][4 * tx], c);
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -305,11 +315,11 @@ __global__ void __launch_bounds__(256) k_deposit_syrk(const R* __restrict__ Ut, 
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int m = m0 + ty + 16 * i;
+            const int m = m0 + 4 * ty + i;
             if (m >= n_sub) continue;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int n = n0 + tx + 16 * j;
+                const int n = n0 + 4 * tx + j;
                 if (n > m) continue;
                 const long long e = (long long)m * (m + 1) / 2 + n;
                 if (Asplit) {
