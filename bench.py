@@ -244,11 +244,11 @@ def kernel_model(name, mol, grid, n_rank=None):
         return (fwd, "tensor", PEAK_TF32_TFLOPS / 3) if fk == name else (None, None, None)
     if name == "k_forms32":
         return (fwd, "alu", PEAK_FP32_TFLOPS) if fk == name else (None, None, None)
-    if name in ("k_forms32_update", "k_forms32_gemm_tc"):
+    if name in ("k_forms32_block", "k_forms32_gemm_tc"):
         if fk != "batched":
             return None, None, None
-        # per block of 128 rows: the product of all rows above it (tensor cores), then the
-        # updates inside the block by its first three panels (binary32 FMA)
+        # per block of 128 rows: the product of all rows above it (tensor cores), then, in one
+        # launch, the block's diagonal solves and the updates inside the block (binary32 FMA)
         fma = tcf = 0.0
         for i0, i1, widths in _form_blocks(n):
             tcf += 8.0 * R * (i1 - i0) * i0
@@ -256,11 +256,10 @@ def kernel_model(name, mol, grid, n_rank=None):
             for kb in widths:
                 fma += 8.0 * R * (i1 - k0 - kb) * kb
                 k0 += kb
-        if name == "k_forms32_update":
-            return (N - 1) * fma, "alu", PEAK_FP32_TFLOPS
+        if name == "k_forms32_block":
+            return (N - 1) * fma + diag, "alu", PEAK_FP32_TFLOPS
         return ((N - 1) * tcf, "tensor", PEAK_TF32_TFLOPS / 3) if tcf > 0 else (None, None, None)
-    if name == "k_forms32_diag":
-        return (diag, "alu", PEAK_FP32_TFLOPS) if fk == "batched" else (None, None, None)
+
     if name == "k_ldlt32_syrk_tc":
         # the trailing updates of 128 rows or more; 3xTF32 takes three TF32 products per binary32 product
         return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if m >= 128), "tensor", PEAK_TF32_TFLOPS / 3
@@ -304,7 +303,7 @@ def kernel_bytes(name, mol, grid):
         if forms_kernel(n, R) != name:
             return None
         return (N - 1) * (tri * cz + ((n + 31) // 32) * 32 * 32 * cz)
-    if name in ("k_forms32_update", "k_forms32_gemm_tc") and forms_kernel(n, R) == "batched":
+    if name in ("k_forms32_block", "k_forms32_gemm_tc") and forms_kernel(n, R) == "batched":
         b = 0.0
         for i0, i1, widths in _form_blocks(n):
             m = i1 - i0
@@ -314,12 +313,9 @@ def kernel_bytes(name, mol, grid):
                     # block's rows of q (binary64) read and of Y written once
                     b += i0 * R * cz + m * i0 * cz + m * R * 8 + m * R * cz
             else:
-                k0 = i0
-                for kb in widths:
-                    rows = i1 - k0 - kb
-                    if rows > 0:
-                        b += rows * R * 2 * cz + rows * kb * cz + kb * R * cz
-                    k0 += kb
+                # the block of Y read and written once, the block's lower triangle of L and its
+                # four diagonal-block inverses read once
+                b += m * R * 2 * cz + m * (m + 1) / 2 * cz + len(widths) * 32 * 32 * cz
         return (N - 1) * b if b > 0 else None
     return None
 
@@ -405,7 +401,7 @@ def roofline_of(dom, kt, timed_mols, grid, total_ms):
     return roof
 
 
-KERNELS = ["k_forms32", "k_forms32_tm", "k_forms32_diag", "k_forms32_update", "k_forms32_gemm_tc",
+KERNELS = ["k_forms32", "k_forms32_tm", "k_forms32_diag", "k_forms32_update", "k_forms32_gemm_tc", "k_forms32_block",
            "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk", "k_ldlt32_syrk_tc", "k_chi0_kk_fma", "k_chi0_kk_tc",
            "k_kk_ctable", "k_deposit_syrk32",
            "k_sgemm", "k_sgemm_tc", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl", "k_bisect", "k_invit",

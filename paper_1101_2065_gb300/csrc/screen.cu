@@ -1182,6 +1182,116 @@ __global__ void __launch_bounds__(256) k_formsb_diag(const C* __restrict__ fac, 
     }
 }
 
+// The four panels of one 128-row block of the left-looking substitution in
+// one launch (binary32): the block's rows of Y for 64 right-hand sides stay
+// in shared memory while each panel takes its diagonal solve y_b = L11^-1 y_b
+// (with its y^2/d sums) and updates the block's later rows,
+// Y[r] -= L[r][panel] y_b.  The arithmetic of every entry is that of
+// k_formsb_diag and k_formsb_update (same operations in the same order); Y
+// is read and written once per block instead of once per panel step, and
+// one launch replaces seven.  Rows before the first block come from q; the
+// last block of the matrix writes c and no Y.
+constexpr size_t BK_SMEM = sizeof(float2) * (128 * 64 + 96 * 33);
+
+__global__ void __launch_bounds__(256) k_formsb_block(const float2* __restrict__ fac, const float2* __restrict__ linv,
+                                                      int n, int N, const double* __restrict__ Q, int R,
+                                                      float2* __restrict__ Y, double* __restrict__ acc,
+                                                      double* __restrict__ c, int i0, int kbase,
+                                                      const int* __restrict__ kmap) {
+    constexpr int NB = 32, G = 4, RPT = NB / G, RC = 64, LP = NB + 1;
+    extern __shared__ __align__(16) unsigned char sraw_bk[];
+    float2* Ys = reinterpret_cast<float2*>(sraw_bk);                 // [128][RC]
+    float2* sL = Ys + 128 * RC;                                       // [96][LP]: later rows x panel columns
+    __shared__ float2 sLi[NB][NB];
+    __shared__ float2 sD[NB];
+    __shared__ double red[G][RC];
+    __shared__ double sacc[RC];
+    const int tid = threadIdx.x, cl = tid % RC, g = tid / RC;
+    const int z = blockIdx.y, k = kbase + z, col = blockIdx.x * RC + cl;
+    const bool live = col < R;
+    const float2* F = fac + (long long)k * tri(n);
+    float2* Yk = Y + (long long)z * n * R;
+    const int i1 = min(n, i0 + 128), nblk = (n + NB - 1) / NB;
+    // the block's rows of Y (q before any update)
+    for (int t = tid; t < 128 * RC; t += blockDim.x) {
+        const int rr = t / RC, cc = t % RC, r = i0 + rr, cg = blockIdx.x * RC + cc;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < i1 && cg < R) {
+            const long long o = (long long)r * R + cg;
+            v = i0 == 0 ? make_float2((float)Q[o], 0.f) : Yk[o];
+        }
+        Ys[t] = v;
+    }
+    if (g == 0) sacc[cl] = (i0 == 0 || !live) ? 0.0 : acc[(long long)z * R + col];
+    for (int k0 = i0; k0 < i1; k0 += NB) {
+        const int kb = min(NB, n - k0), k1 = k0 + kb, nl = i1 - k1;
+        const bool last = k1 == n;
+        const float2* Li = linv + ((long long)k * nblk + k0 / NB) * NB * NB;
+        __syncthreads();                          // previous panel's update done
+        for (int t = tid; t < NB * NB; t += blockDim.x) sLi[t / NB][t % NB] = Li[t];
+        if (tid < NB) sD[tid] = tid < kb ? F[tri(k0 + tid) + k0 + tid] : make_float2(1.f, 0.f);
+        for (int t = tid; t < nl * NB; t += blockDim.x) {
+            const int rr = t / NB, p = t % NB;
+            sL[rr * LP + p] = p < kb ? F[tri(k1 + rr) + k0 + p] : make_float2(0.f, 0.f);
+        }
+        float2 y[NB];
+#pragma unroll
+        for (int p = 0; p < NB; ++p)
+            y[p] = (live && p < kb) ? Ys[(k0 - i0 + p) * RC + cl] : make_float2(0.f, 0.f);
+        __syncthreads();                          // every panel row read before any is rewritten
+        // diagonal block: rows g + G q of the panel
+        float2 part = make_float2(0.f, 0.f);
+        float2 vq[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int i = g + G * q;
+            float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int p = 0; p < NB; ++p) v = cfma(sLi[i][p], y[p], v);
+            vq[q] = v;
+            if (live && i < kb) part = cadd(part, cdiv(cmul(v, v), sD[i]));
+        }
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int i = g + G * q;
+            if (i < kb) Ys[(k0 - i0 + i) * RC + cl] = vq[q];
+        }
+        red[g][cl] = (double)part.y;
+        __syncthreads();
+        if (g == 0 && live) {
+            double sum = red[0][cl] + red[1][cl] + red[2][cl] + red[3][cl];
+            sum += k0 == 0 ? 0.0 : sacc[cl];
+            if (last) {
+                c[(long long)col * N + (kmap ? kmap[k] : k)] = -sum / M_PI;
+                if (!kmap && k == 1) c[(long long)col * N] = 0.0;
+            }
+            sacc[cl] = sum;
+        }
+        // the block's later rows: Y[r] -= sum_p L[r][k0 + p] y_b[p], rows g + G q' of them
+        // (the solved panel column in registers)
+        if (nl > 0) {
+#pragma unroll
+            for (int p = 0; p < NB; ++p) y[p] = p < kb ? Ys[(k0 - i0 + p) * RC + cl] : make_float2(0.f, 0.f);
+        }
+        for (int rr = g; rr < nl; rr += G) {
+            float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int p = 0; p < NB; ++p) a = cfma(sL[rr * LP + p], y[p], a);
+            float2* dst = &Ys[(k1 - i0 + rr) * RC + cl];
+            *dst = csub(*dst, a);
+        }
+    }
+    __syncthreads();
+    if (i1 < n) {
+        // Y of the block for the later block products, and the running sums
+        for (int t = tid; t < (i1 - i0) * RC; t += blockDim.x) {
+            const int rr = t / RC, cc = t % RC, cg = blockIdx.x * RC + cc;
+            if (cg < R) Yk[(long long)(i0 + rr) * R + cg] = Ys[t];
+        }
+        if (g == 0 && live) acc[(long long)z * R + col] = sacc[cl];
+    }
+}
+
 // Y[r_lo, r_hi) -= L[r_lo.., kk0 .. kk0 + kw) y[kk0 .. kk0 + kw) for one
 // T x T tile (rows, right-hand sides) of frequency kbase + blockIdx.z; KW >=
 // kw is the compile-time panel width (one panel, or two panels at once so
@@ -1581,19 +1691,15 @@ static void forms_batched(gw_ctx* ctx, const C* fac, const C* linv, int n, int N
                 // left-looking in blocks of 128 rows: the product of all rows above the block on
                 // the tensor cores, then the block's four panels
                 allow_max_smem(k_formsb_gemm_tc);
+                allow_max_smem(k_formsb_block);
                 for (int i0 = 0; i0 < n; i0 += 128) {
                     const int i1 = std::min(n, i0 + 128);
                     if (i0 > 0)
                         klaunch(ctx, names[2], k_formsb_gemm_tc, dim3(div_up(R, FG_NC), nbb), 288, FG_SMEM,
                                 (const float2*)fac, n, Q, R, (float2*)Y, i0, i1, kbase, ctx->d_status);
-                    for (int k0 = i0; k0 < i1; k0 += NB) {
-                        const int k1 = std::min(i1, k0 + NB);
-                        klaunch(ctx, names[0], k_formsb_diag<C>, dim3(div_up(R, 64), nbb), 256, 0, fac, linv, n, N, Q,
-                                R, Y, acc, cout, k0, kbase, kmap);
-                        if (k1 == i1) break;
-                        klaunch(ctx, names[1], k_formsb_update<C, NB>, dim3(div_up(i1 - k1, TT), div_up(R, TT), nbb),
-                                256, sm1, fac, n, Q, R, Y, k0, k1 - k0, k1, i1, kbase);
-                    }
+                    klaunch(ctx, "k_forms32_block", k_formsb_block, dim3(div_up(R, 64), nbb), 256, BK_SMEM,
+                            (const float2*)fac, (const float2*)linv, n, N, Q, R, (float2*)Y, acc, cout, i0, kbase,
+                            kmap);
                 }
             } else {
                 for (int k0 = 0; k0 < n; k0 += 2 * NB) {

@@ -54,16 +54,17 @@ def test_batched_forms_model_splits_diagonal_and_update():
     mol = sm._uniform_molecule("chain", 20, 1)          # n = 600: Y in HBM
     grid = synth.Grid(1024)
     n, R = mol.n_sub, 2 * mol.n_orb
-    up, b1, _ = bench.kernel_model("k_forms32_update", mol, grid)
-    dg, b2, _ = bench.kernel_model("k_forms32_diag", mol, grid)
+    bk, b1, _ = bench.kernel_model("k_forms32_block", mol, grid)
     gm, b3, _ = bench.kernel_model("k_forms32_gemm_tc", mol, grid)
-    assert b1 == b2 == "alu" and b3 == "tensor"
+    assert b1 == "alu" and b3 == "tensor"
     P = bench._panels(n, 32)
     diag = 1023 * 8.0 * R * sum(kb * kb for kb, _ in P)
     # every entry of L strictly below the diagonal blocks once: the product of the rows above a
-    # 128-row block (tensor cores) plus the updates inside the block (FMA units)
+    # 128-row block (tensor cores) plus the updates inside the block (FMA units, with the
+    # diagonal-block solves in the same launch)
     off = 1023 * 8.0 * R * (n * (n - 1) / 2 - sum(kb * (kb - 1) / 2 for kb, _ in P))
-    assert dg == pytest.approx(diag) and up + gm == pytest.approx(off)
+    assert bk + gm == pytest.approx(off + diag)
+    assert bench.kernel_model("k_forms32_diag", mol, grid)[0] is None
     assert gm == pytest.approx(1023 * 8.0 * R * sum((min(n, i0 + 128) - i0) * i0 for i0 in range(0, n, 128)))
 
 
@@ -94,10 +95,10 @@ def test_workload_model_sums_only_where_the_kernel_runs(ring):
     mol, grid = ring
     big = sm._uniform_molecule("chain", 20, 1)
     g = synth.Grid(1024)
-    tot, meta = bench.workload_model("k_forms32_update", [mol, big], g, bench.kernel_model)
-    assert tot == pytest.approx(bench.kernel_model("k_forms32_update", big, g)[0])
+    tot, meta = bench.workload_model("k_forms32_block", [mol, big], g, bench.kernel_model)
+    assert tot == pytest.approx(bench.kernel_model("k_forms32_block", big, g)[0])
     assert meta[0] == "alu"
-    none, _ = bench.workload_model("k_forms32_update", [mol], g, bench.kernel_model)
+    none, _ = bench.workload_model("k_forms32_block", [mol], g, bench.kernel_model)
     assert none is None
 
 
