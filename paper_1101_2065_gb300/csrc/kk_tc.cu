@@ -309,10 +309,29 @@ __global__ void k_kk_ctable(int N, int j_lo, int band, double dw, double eta, fl
     Kc[t] = make_float2((float)(x1 / d1 - x2 / d2), (float)(-eta / d1 + eta / d2));
 }
 
+// asynchronous copies into shared memory: `bytes` of src (0 = zero fill) into a dst slot of `size`
+__device__ __forceinline__ void cp_async_z8(void* dst, const void* src, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_z16(void* dst, const void* src, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_z4(void* dst, const void* src, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+
+constexpr size_t KKF_SMEM = 2 * (sizeof(float2) * FB * FK + sizeof(float) * FB * FE);
+
+// The chunks of FB bins go through two shared-memory buffers: chunk c + 1 is
+// copied asynchronously while chunk c is summed.
 __global__ void __launch_bounds__(256) k_chi0_kk_fma(const float2* __restrict__ Kc, const float* __restrict__ A,
                                                      int N, int band, long long n_el, float2* __restrict__ chi0) {
-    __shared__ __align__(16) float2 sK[FB][FK];      // [bin][frequency]
-    __shared__ __align__(16) float sA[FB][FE];       // [bin][element]
+    extern __shared__ __align__(16) unsigned char sraw_kf[];
+    float2 (*sK)[FB][FK] = reinterpret_cast<float2 (*)[FB][FK]>(sraw_kf);                       // [2][bin][frequency]
+    float (*sA)[FB][FE] = reinterpret_cast<float (*)[FB][FE]>(sraw_kf + 2 * sizeof(float2) * FB * FK);  // [2][bin][element]
     const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
     const int k0 = blockIdx.y * FK;
     const long long e0 = (long long)blockIdx.x * FE;
@@ -322,28 +341,39 @@ __global__ void __launch_bounds__(256) k_chi0_kk_fma(const float2* __restrict__ 
 #pragma unroll
         for (int i = 0; i < 4; ++i) tr[f][i] = ti[f][i] = 0.f;
     const bool vec = (n_el % 4 == 0);
-    for (int b0 = 0; b0 < band; b0 += FB) {
-        __syncthreads();
+    const int nch = (band + FB - 1) / FB;
+    auto stage = [&](int ch, int buf) {
+        const int b0 = ch * FB;
         for (int t = tid; t < FB * FK; t += 256) {
             const int f = t % FK, bb = t / FK, k = k0 + f, b = b0 + bb;
-            sK[bb][f] = (k < N && b < band) ? Kc[(long long)b * N + k] : make_float2(0.f, 0.f);
+            const bool in = k < N && b < band;
+            cp_async_z8(&sK[buf][bb][f], in ? (const void*)(Kc + (long long)b * N + k) : (const void*)Kc, in ? 8 : 0);
         }
         for (int t = tid; t < FB * FE / 4; t += 256) {
             const int bb = t / (FE / 4), q = t % (FE / 4), b = b0 + bb;
             const long long e = e0 + 4 * q;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (b < band) {
-                const float* row = A + (long long)b * n_el;
-                if (vec && e + 3 < n_el) {
-                    v = *reinterpret_cast<const float4*>(row + e);
-                } else {
-                    if (e < n_el) v.x = row[e];
-                    if (e + 1 < n_el) v.y = row[e + 1];
-                    if (e + 2 < n_el) v.z = row[e + 2];
-                    if (e + 3 < n_el) v.w = row[e + 3];
+            const float* row = A + (long long)(b < band ? b : 0) * n_el;
+            if (vec) {
+                const int nb = (b < band && e < n_el) ? 16 : 0;       // n_el % 4 == 0: whole quads
+                cp_async_z16(&sA[buf][bb][4 * q], nb ? (const void*)(row + e) : (const void*)A, nb);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool in = b < band && e + u < n_el;
+                    cp_async_z4(&sA[buf][bb][4 * q + u], in ? (const void*)(row + e + u) : (const void*)A, in ? 4 : 0);
                 }
             }
-            *reinterpret_cast<float4*>(&sA[bb][4 * q]) = v;
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    stage(0, 0);
+    for (int ch = 0; ch < nch; ++ch) {
+        const int buf = ch & 1;
+        if (ch + 1 < nch) {
+            stage(ch + 1, buf ^ 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncthreads();
         float pr[8][4], pi[8][4];
@@ -353,15 +383,21 @@ __global__ void __launch_bounds__(256) k_chi0_kk_fma(const float2* __restrict__ 
             for (int i = 0; i < 4; ++i) pr[f][i] = pi[f][i] = 0.f;
 #pragma unroll 4
         for (int bb = 0; bb < FB; ++bb) {
-            const float4 a = *reinterpret_cast<const float4*>(&sA[bb][4 * tx]);
+            const float4 a = *reinterpret_cast<const float4*>(&sA[buf][bb][4 * tx]);
             const float av[4] = {a.x, a.y, a.z, a.w};
+            const float4* kp = reinterpret_cast<const float4*>(&sK[buf][bb][8 * ty]);
 #pragma unroll
-            for (int f = 0; f < 8; ++f) {
-                const float2 kv = sK[bb][8 * ty + f];
+            for (int f2 = 0; f2 < 4; ++f2) {
+                const float4 kk2 = kp[f2];                            // frequencies 2 f2, 2 f2 + 1
+                const float2 kvs[2] = {make_float2(kk2.x, kk2.y), make_float2(kk2.z, kk2.w)};
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    pr[f][i] = fmaf(kv.x, av[i], pr[f][i]);
-                    pi[f][i] = fmaf(kv.y, av[i], pi[f][i]);
+                for (int h = 0; h < 2; ++h) {
+                    const int f = 2 * f2 + h;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        pr[f][i] = fmaf(kvs[h].x, av[i], pr[f][i]);
+                        pi[f][i] = fmaf(kvs[h].y, av[i], pi[f][i]);
+                    }
                 }
             }
         }
@@ -372,6 +408,7 @@ __global__ void __launch_bounds__(256) k_chi0_kk_fma(const float2* __restrict__ 
                 tr[f][i] += pr[f][i];
                 ti[f][i] += pi[f][i];
             }
+        __syncthreads();                              // buffer buf is refilled by the next iteration's copies
     }
 #pragma unroll
     for (int f = 0; f < 8; ++f) {
@@ -447,7 +484,8 @@ void launch_chi0_kk_2w(gw_ctx* ctx, gw_chi0* c, const void* A, int js, int band_
                     c->grid.eta, gl.d_omega, jl, band_l, gl.eta, (float2*)Kc);
             if (!c->chi0_32) c->chi0_32 = dalloc<float2>(ctx, (size_t)N * n_el);
             const long long net = (n_el + FE - 1) / FE;
-            klaunch(ctx, "k_chi0_kk_fma", k_chi0_kk_fma, dim3((unsigned)net, (unsigned)div_up(N, FK)), 256, 0,
+            allow_max_smem(k_chi0_kk_fma);
+            klaunch(ctx, "k_chi0_kk_fma", k_chi0_kk_fma, dim3((unsigned)net, (unsigned)div_up(N, FK)), 256, KKF_SMEM,
                     (const float2*)Kc, (const float*)A, N, band, n_el, c->chi0_32);
         } else {
             klaunch(ctx, "k_kk_ctable", k_kk_ctable_2w<double2>, nb, 256, 0, N, c->grid.d_omega, js, band_s,
@@ -475,7 +513,8 @@ void launch_chi0_kk_fma(gw_ctx* ctx, gw_chi0* c, const float* A) {
         const long long net = (n_el + FE - 1) / FE;
         if (net > 0x7fffffffLL) gw_throw(GW_ERR_INVALID_ARG, "too many matrix elements for the Kramers-Kronig kernel");
         dim3 grid((unsigned)net, (unsigned)div_up(N, FK));
-        klaunch(ctx, "k_chi0_kk_fma", k_chi0_kk_fma, grid, 256, 0, (const float2*)Kc, A, N, band, n_el, c->chi0_32);
+        allow_max_smem(k_chi0_kk_fma);
+        klaunch(ctx, "k_chi0_kk_fma", k_chi0_kk_fma, grid, 256, KKF_SMEM, (const float2*)Kc, A, N, band, n_el, c->chi0_32);
     } catch (...) {
         ctx_free(ctx, Kc);
         throw;
