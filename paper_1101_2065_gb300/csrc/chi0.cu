@@ -265,14 +265,36 @@ __device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
     v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
 }
 
+// asynchronous copy of one R from global (bytes = 0: zero fill) into shared memory
+__device__ __forceinline__ void cp_async_r(float* dst, const float* src, bool in) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(in ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_r(double* dst, const double* src, bool in) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(in ? 8 : 0) : "memory");
+}
+
+constexpr int DEP_T = 64, DEP_KC = 32, DEP_TP = DEP_T + 4;   // row pitch: 16-byte aligned rows
+template <typename R> constexpr size_t dep_smem() { return sizeof(R) * 2 * (2 * DEP_KC * DEP_TP + DEP_KC); }
+
+// Segmented SYRK of the spectral weights: bin b of a CTA's range takes the
+// pairs of bins b - 1 and b (contiguous in the sorted pair order, [lo, hi))
+// with their tent weights.  Chunks of 32 pairs are copied asynchronously
+// (cp.async) into two buffers, the next chunk (possibly of the next bin) in
+// flight while the current one is summed; the weight multiplies the staged
+// row value in the inner loop (the same product as weighting it before
+// staging).
 template <typename R>
 __global__ void __launch_bounds__(256) k_deposit_syrk(const R* __restrict__ Ut, int n_pair, int n_sub,
                                                       const int* __restrict__ seg, const double* __restrict__ frac,
                                                       int nb_bins, int BC, long long n_el, R* __restrict__ A,
                                                       uint32_t* __restrict__ Asplit, long long n_et) {
-    constexpr int T = 64, KC = 32, TP = T + 4;     // row pitch: 16-byte aligned rows
-    __shared__ __align__(16) R Um[KC][TP];         // w_p u_pm for the tile's rows m
-    __shared__ __align__(16) R Un[KC][TP];         // u_pn for the tile's columns n
+    constexpr int T = DEP_T, KC = DEP_KC, TP = DEP_TP;
+    extern __shared__ __align__(16) unsigned char sraw_dep[];
+    R (*Um)[KC][TP] = reinterpret_cast<R (*)[KC][TP]>(sraw_dep);                 // [2][pair][row m]: u_pm
+    R (*Un)[KC][TP] = Um + 2;                                                   // [2][pair][column n]: u_pn
+    R (*sW)[KC] = reinterpret_cast<R (*)[KC]>(Un + 2);                          // [2][pair]: tent weight
     int I, J;
     tile_ij(blockIdx.x, I, J);
     const int m0 = I * T, n0 = J * T;
@@ -281,37 +303,70 @@ __global__ void __launch_bounds__(256) k_deposit_syrk(const R* __restrict__ Ut, 
     // each thread: rows m0 + 4 ty .. + 3, columns n0 + 4 tx .. + 3 (four consecutive entries of
     // a staged row per vector load)
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+    auto bin_lo = [&](int b) { return seg[b > 0 ? b - 1 : 0]; };
+    auto bin_hi = [&](int b) { return seg[b < nb_bins ? b + 1 : nb_bins]; };
+    // the chunk after (b, p0) in the CTA's sequence, skipping bins without pairs; b = b1: none
+    auto next_chunk = [&](int& b, int& p0) {
+        if (p0 + KC < bin_hi(b)) { p0 += KC; return; }
+        for (++b; b < b1; ++b)
+            if (bin_lo(b) < bin_hi(b)) { p0 = bin_lo(b); return; }
+    };
+    auto stage = [&](int b, int p0, int buf) {
+        const int mid = seg[b], hi = bin_hi(b);
+        for (int t = tid; t < KC * T; t += blockDim.x) {
+            const int r = t / KC, k = t % KC, p = p0 + k;
+            const bool inp = p < hi;
+            cp_async_r(&Um[buf][k][r], Ut + (inp && m0 + r < n_sub ? (long long)(m0 + r) * n_pair + p : 0),
+                       inp && m0 + r < n_sub);
+            cp_async_r(&Un[buf][k][r], Ut + (inp && n0 + r < n_sub ? (long long)(n0 + r) * n_pair + p : 0),
+                       inp && n0 + r < n_sub);
+        }
+        if (tid < KC) {
+            const int p = p0 + tid;
+            sW[buf][tid] = p < hi ? R(p < mid ? 2.0 * frac[p] : 2.0 * (1.0 - frac[p])) : R(0);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    // first chunk of the range
+    int sb = b0, sp = 0;
+    while (sb < b1 && bin_lo(sb) >= bin_hi(sb)) ++sb;
+    if (sb < b1) {
+        sp = bin_lo(sb);
+        stage(sb, sp, 0);
+    }
+    int buf = 0;
     for (int b = b0; b < b1; ++b) {
-        const int lo = seg[b > 0 ? b - 1 : 0], mid = seg[b], hi = seg[b < nb_bins ? b + 1 : nb_bins];
+        const int lo = bin_lo(b), hi = bin_hi(b);
         R acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = R(0);
         for (int p0 = lo; p0 < hi; p0 += KC) {
-            __syncthreads();
-            for (int t = tid; t < KC * T; t += blockDim.x) {
-                const int r = t / KC, k = t % KC, p = p0 + k;
-                R um = R(0), un = R(0);
-                if (p < hi) {
-                    const R w = R(p < mid ? 2.0 * frac[p] : 2.0 * (1.0 - frac[p]));
-                    if (m0 + r < n_sub) um = w * Ut[(long long)(m0 + r) * n_pair + p];
-                    if (n0 + r < n_sub) un = Ut[(long long)(n0 + r) * n_pair + p];
-                }
-                Um[k][r] = um;
-                Un[k][r] = un;
+            // this chunk (b, p0) is in buffer buf; stage the one after it
+            next_chunk(sb, sp);
+            if (sb < b1) {
+                stage(sb, sp, buf ^ 1);
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             }
             __syncthreads();
             const int kc = min(KC, hi - p0);
             for (int k = 0; k < kc; ++k) {
                 R a[4], c[4];
-                load4(&Um[k][4 * ty], a);
-                load4(&Un[k][4 * tx], c);
+                load4(&Um[buf][k][4 * ty], a);
+                load4(&Un[buf][k][4 * tx], c);
+                const R w = sW[buf][k];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = w * a[i];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], c[j], acc[i][j]);
             }
+            __syncthreads();                          // buffer buf is refilled two chunks later
+            buf ^= 1;
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -323,11 +378,11 @@ __global__ void __launch_bounds__(256) k_deposit_syrk(const R* __restrict__ Ut, 
                 if (n > m) continue;
                 const long long e = (long long)m * (m + 1) / 2 + n;
                 if (Asplit) {
-                    uint32_t hi, lo;
-                    tc::split_tf32((float)acc[i][j], hi, lo);
+                    uint32_t hi_, lo_;
+                    tc::split_tf32((float)acc[i][j], hi_, lo_);
                     const long long w = kk::weight_word(b, e, n_et);
-                    Asplit[w] = hi;
-                    Asplit[w + kk::TILE_WORDS] = lo;
+                    Asplit[w] = hi_;
+                    Asplit[w + kk::TILE_WORDS] = lo_;
                 } else {
                     A[(long long)b * n_el + e] = acc[i][j];
                 }
@@ -456,8 +511,9 @@ static void deposit(gw_ctx* ctx, const gw_chi0* c, const R* Ut, R* A, long long 
     const int BC = std::max(1, (int)std::min<long long>(band, (long long)tiles * band / (8LL * ctx->num_sms)));
     const int nbc = div_up(band, BC);
     if (nbc > 65535) gw_throw(GW_ERR_INVALID_ARG, "spectral band too wide for the deposit kernel");
-    klaunch(ctx, sizeof(R) == 4 ? "k_deposit_syrk32" : "k_deposit_syrk", k_deposit_syrk<R>, dim3(tiles, nbc), 256, 0,
-            Ut, c->n_pair, n, (const int*)c->seg, (const double*)c->pFrac, c->nb_bins, BC, n_el, A, Asplit,
+    allow_max_smem(k_deposit_syrk<R>);
+    klaunch(ctx, sizeof(R) == 4 ? "k_deposit_syrk32" : "k_deposit_syrk", k_deposit_syrk<R>, dim3(tiles, nbc), 256,
+            dep_smem<R>(), Ut, c->n_pair, n, (const int*)c->seg, (const double*)c->pFrac, c->nb_bins, BC, n_el, A, Asplit,
             kk::elem_tiles(n_el));
 }
 
@@ -501,12 +557,17 @@ void launch_deposit_range(gw_ctx* ctx, const gw_chi0* c, const int* seg, const d
     const int BC = std::max(1, (int)std::min<long long>(band, (long long)tiles * band / (8LL * ctx->num_sms)));
     const int nbc = div_up(band, BC);
     if (nbc > 65535) gw_throw(GW_ERR_INVALID_ARG, "spectral band too wide for the deposit kernel");
-    if (c->prec == GW_MIXED)
-        klaunch(ctx, "k_deposit_syrk32", k_deposit_syrk<float>, dim3(tiles, nbc), 256, 0, (const float*)c->Ut32,
-                c->n_pair, n, seg, frac, nb_bins, BC, n_el, (float*)A, (uint32_t*)nullptr, 0LL);
-    else
-        klaunch(ctx, "k_deposit_syrk", k_deposit_syrk<double>, dim3(tiles, nbc), 256, 0, (const double*)c->Ut,
-                c->n_pair, n, seg, frac, nb_bins, BC, n_el, (double*)A, (uint32_t*)nullptr, 0LL);
+    if (c->prec == GW_MIXED) {
+        allow_max_smem(k_deposit_syrk<float>);
+        klaunch(ctx, "k_deposit_syrk32", k_deposit_syrk<float>, dim3(tiles, nbc), 256, dep_smem<float>(),
+                (const float*)c->Ut32, c->n_pair, n, seg, frac, nb_bins, BC, n_el, (float*)A, (uint32_t*)nullptr,
+                0LL);
+    } else {
+        allow_max_smem(k_deposit_syrk<double>);
+        klaunch(ctx, "k_deposit_syrk", k_deposit_syrk<double>, dim3(tiles, nbc), 256, dep_smem<double>(),
+                (const double*)c->Ut, c->n_pair, n, seg, frac, nb_bins, BC, n_el, (double*)A, (uint32_t*)nullptr,
+                0LL);
+    }
 }
 
 // Binary64 spectral weights A64 [band][n_el] of the binary32 path (near-pole
