@@ -300,7 +300,22 @@ __global__ void __launch_bounds__(512) k_sytrd32_grid(float* __restrict__ A, int
         // updated row k+1 (local row 0 of the trailing block), redundantly in every CTA
         const float* r1 = A + (long long)(k + 1) * n + k + 1;
         const float v0 = sv[0], w0 = sw[0];
-        for (int j = tid; j < m; j += blockDim.x) sr[j] = r1[j] - v0 * sw[j] - w0 * sv[j];
+        {
+            // up to eight loads of the row in flight per thread
+            const int stride = blockDim.x;
+            int j = tid;
+            for (; j + 7 * stride < m; j += 8 * stride) {
+                float a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = r1[j + u * stride];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int jj = j + u * stride;
+                    sr[jj] = a[u] - v0 * sw[jj] - w0 * sv[jj];
+                }
+            }
+            for (; j < m; j += stride) sr[j] = r1[j] - v0 * sw[j] - w0 * sv[j];
+        }
         __syncthreads();
         const bool last = k + 3 >= n;            // row k+1 = n-2: no further reflector
         if (blockIdx.x == 0 && tid == 0) d[k + 1] = sr[0];
@@ -353,7 +368,18 @@ __global__ void __launch_bounds__(512) k_sytrd32_grid(float* __restrict__ A, int
         float tot = 0.f;
         for (int q = 0; q < (int)gridDim.x; ++q) tot += pt[q];
         const float K = 0.5f * t1 * tot;
-        for (int j = tid; j < m - 1; j += blockDim.x) sw[j] = pb[j] - K * vn[j];
+        {
+            const int stride = blockDim.x;
+            int j = tid;
+            for (; j + 7 * stride < m - 1; j += 8 * stride) {
+                float a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = pb[j + u * stride];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sw[j + u * stride] = a[u] - K * vn[j + u * stride];
+            }
+            for (; j < m - 1; j += stride) sw[j] = pb[j] - K * vn[j];
+        }
         __syncthreads();
         for (int j = tid; j < m - 1; j += blockDim.x) sv[j] = vn[j];
         __syncthreads();
