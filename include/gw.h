@@ -143,9 +143,10 @@ gw_status gw_ctx_profile_get(gw_ctx* ctx, const char* kernel_name, double* total
  * counterpart).
  * GW_OPT_FORMS_SIMT (value 0 or 1, default 0): for 32 < N_sub <= 384 the
  * binary32 path by default keeps the forward substitution's updates in
- * tensor memory (3xTF32 products), and for larger N_sub it updates the rows
- * below each pair of 32-column panels on the tensor cores (3xTF32); 1 runs
- * both on the FMA units instead.
+ * tensor memory (3xTF32 products), and for larger N_sub it runs the
+ * forward substitution left-looking by blocks of 128 rows, the product of
+ * all rows above a block on the tensor cores (3xTF32); 1 runs both on the
+ * FMA units instead (right-looking, by pairs of 32-column panels).
  * GW_OPT_SYRK_SIMT (value 0 or 1, default 0): the binary32 factorisation
  * runs its trailing updates of 128 or more rows as 3xTF32 tensor-core
  * products by default; 1 keeps them on the FMA units.
