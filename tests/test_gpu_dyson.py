@@ -48,3 +48,36 @@ def test_dyson_dos_against_oracle(gwlib, ctx, cfg, request):
         finally:
             for h in (s, w, c, m):
                 h.free()
+
+
+@pytest.mark.parametrize("prec_name", ["GW_MIXED", "GW_FP64"])
+def test_matrix_diagonal_equals_diagonal_sigma_on_the_batched_path(gwlib, ctx, prec_name):
+    """15-atom chain (195 orbitals, N_sub 450 > 384: the batched forms, on the
+    binary32 path the left-looking tensor-core block product) with three states:
+    the matrix path solves for 6 x 195 = 1170 right-hand sides and the diagonal
+    path for 3 x 195 = 585 (an odd count, so the last column tile is ragged).
+    Every right-hand side is solved on its own, so the diagonal of Sigma_c,nm
+    and Sigma_x,nm equals the diagonal self-energy of the same states."""
+    from paper_1101_2065_gb300 import gw as G
+    from synth import molecules as sm
+    prec = getattr(gwlib, prec_name)
+    mol = sm._uniform_molecule("chain", 15, sm.SEED_BASE + 7915)
+    assert mol.n_sub == 450 and mol.eps.size == 195
+    grid = synth.Grid(256)
+    st = [mol.n_occ - 2, mol.n_occ - 1, mol.n_occ]
+    m = G.gw_mol_upload(ctx, mol)
+    c = G.gw_build_chi0(ctx, m, grid, prec)
+    w = G.gw_screen_W(ctx, c)
+    try:
+        sm_ = G.gw_sigma_matrix(ctx, w, st)
+        sd = G.gw_sigma_diag(ctx, w, st)
+        try:
+            sc, sx = G.gw_sigma_matrix_copy(ctx, sm_)
+            d = sd.copy()
+            for i in range(len(st)):
+                assert np.abs(sc[i, i] - d["sigma_c"][i]).max() <= 1e-12 * np.abs(d["sigma_c"][i]).max()
+                assert abs(sx[i, i] - d["sigma_x"][i]) <= 1e-12 * abs(d["sigma_x"][i])
+        finally:
+            sm_.free(); sd.free()
+    finally:
+        w.free(); c.free(); m.free()
