@@ -10,7 +10,8 @@
 // 32 of op(A) and op(B) into shared memory, split into hi/lo parts and laid
 // out in the canonical K-major core-matrix layout without swizzle (8 rows x
 // 16 bytes per core matrix; 128 bytes between core matrices along K, 1024
-// between 8-row groups).  Thread 0 issues the 12 MMAs of a chunk
+// between 8-row groups), four consecutive K values of a row per 16-byte
+// store.  Thread 0 issues the 12 MMAs of a chunk
 // (4 steps of K = 8, three products each) and commits them to the chunk's
 // mbarrier; two stages alternate, so the loads of chunk c + 1 overlap the
 // MMAs of chunk c.  The accumulators (128 lanes x 128 columns of binary32
@@ -34,6 +35,15 @@ constexpr uint32_t IDESC = tc::idesc_tf32(TM, TN);
 constexpr uint32_t SBO = (KC / 4) * 128;          // bytes between 8-row groups of a 128 x 32 tile
 
 __device__ __forceinline__ uint32_t tile_off(int r, int k) { return tc::core_off(r, k, KC / 4); }
+
+// four consecutive K values of one row, split into hi and lo, as one 16-byte store each
+__device__ __forceinline__ void store_quad(unsigned char* hi, unsigned char* lo, const float (&v)[4]) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tc::split_tf32(v[i], h[i], l[i]);
+    *reinterpret_cast<uint4*>(hi) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo) = make_uint4(l[0], l[1], l[2], l[3]);
+}
 
 // C = alpha op(A) op(B) + beta C; op(A) is M x K, op(B) is K x N, all row-major.
 // blockIdx.x = tile row (M), blockIdx.y = tile column (N): CTAs that run
@@ -62,38 +72,32 @@ __global__ void __launch_bounds__(256, 1) k_sgemm_tc(int M, int N, int K, float 
     for (int c = 0; c < nchunk; ++c) {
         const int s = c % NSTAGE, k0 = c * KC;
         unsigned char* st = sm + s * STAGE_BYTES;
-        // stage op(A)[m0 .. +128)[k0 .. +32) and op(B)^T[n0 .. +128)[k0 .. +32):
-        // each thread loads its 16 + 16 values first (all loads in flight at
-        // once), then splits and stores them
-        constexpr int PER = TM * KC / 256;
-        float va[PER], vb[PER];
+        // stage op(A)[m0 .. +128)[k0 .. +32) and op(B)^T[n0 .. +128)[k0 .. +32) by quads of
+        // four consecutive K of one row (lanes 0-7: rows 8 rg .. 8 rg + 7 of one quad, so
+        // the 16-byte stores of a warp fill 512 contiguous bytes): each thread loads its
+        // 4 + 4 quads first (all loads in flight at once), then splits and stores them
+        float va[4][4], vb[4][4];
 #pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int t = tid + 256 * u;
-            int r, k;
-            if (TA) { k = t / TM; r = t % TM; } else { r = t / KC; k = t % KC; }
-            const int gm = m0 + r, gk = k0 + k;
-            va[u] = (gm < M && gk < K) ? (TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : 0.f;
-            if (TB) { r = t / KC; k = t % KC; } else { k = t / TN; r = t % TN; }
-            const int gn = n0 + r, gk2 = k0 + k;
-            vb[u] = (gn < N && gk2 < K) ? (TB ? B[(long long)gn * ldb + gk2] : B[(long long)gk2 * ldb + gn]) : 0.f;
+        for (int u = 0; u < 4; ++u) {
+            const int idx = tid + 256 * u, rr = idx & 7, kq = (idx >> 3) & 7, rg = idx >> 6;
+            const int r = 8 * rg + rr, gk = k0 + 4 * kq;
+            const int gm = m0 + r, gn = n0 + r;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const bool ka = gm < M && gk + i < K, kb = gn < N && gk + i < K;
+                va[u][i] = ka ? (TA ? A[(long long)(gk + i) * lda + gm] : A[(long long)gm * lda + gk + i]) : 0.f;
+                vb[u][i] = kb ? (TB ? B[(long long)gn * ldb + gk + i] : B[(long long)(gk + i) * ldb + gn]) : 0.f;
+            }
         }
         if (c >= NSTAGE) {           // the MMAs that read this stage two chunks ago are done
             ok = tc::mbar_wait(tc::smem_u32(&mbar[s]), (uses[s] - 1) & 1) && ok;
         }
 #pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int t = tid + 256 * u;
-            int r, k;
-            uint32_t hi, lo;
-            if (TA) { k = t / TM; r = t % TM; } else { r = t / KC; k = t % KC; }
-            tc::split_tf32(va[u], hi, lo);
-            *reinterpret_cast<uint32_t*>(st + tile_off(r, k)) = hi;
-            *reinterpret_cast<uint32_t*>(st + TILE_BYTES + tile_off(r, k)) = lo;
-            if (TB) { r = t / KC; k = t % KC; } else { k = t / TN; r = t % TN; }
-            tc::split_tf32(vb[u], hi, lo);
-            *reinterpret_cast<uint32_t*>(st + 2 * TILE_BYTES + tile_off(r, k)) = hi;
-            *reinterpret_cast<uint32_t*>(st + 3 * TILE_BYTES + tile_off(r, k)) = lo;
+        for (int u = 0; u < 4; ++u) {
+            const int idx = tid + 256 * u, rr = idx & 7, kq = (idx >> 3) & 7, rg = idx >> 6;
+            const uint32_t o = tile_off(8 * rg + rr, 4 * kq);
+            store_quad(st + o, st + TILE_BYTES + o, va[u]);
+            store_quad(st + 2 * TILE_BYTES + o, st + 3 * TILE_BYTES + o, vb[u]);
         }
         tc::fence_async_smem();
         __syncthreads();
