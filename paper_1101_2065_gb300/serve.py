@@ -127,10 +127,17 @@ def rate_sweep(rates, n_jobs, lo, hi, n_omega, workers, budget):
         sm_ = summarize(res, span, mols, errors)
         sm_["offered_rate_per_s"] = r
         out["rates"].append(sm_)
-    ok = [x for x in out["rates"] if x["completed"] == n_jobs and x["solves_per_s"] >= 0.95 * x["offered_rate_per_s"]
-          and x["queue_ms"]["p50"] <= x["run_ms"]["p50"]]
-    out["sustainable_rate_per_s"] = max((x["offered_rate_per_s"] for x in ok), default=None)
+    out["sustainable_rate_per_s"] = sustainable_rate(out["rates"], n_jobs)
     return out
+
+
+def sustainable_rate(per_rate, n_jobs):
+    """The highest offered rate at which every job completed, the completion
+    rate kept up with at least 95 % of the offered rate and the p50 queueing
+    time stayed below the p50 run time (None if no rate qualifies)."""
+    ok = [x for x in per_rate if x["completed"] == n_jobs and x["solves_per_s"] >= 0.95 * x["offered_rate_per_s"]
+          and x["queue_ms"]["p50"] <= x["run_ms"]["p50"]]
+    return max((x["offered_rate_per_s"] for x in ok), default=None)
 
 
 def solve_one(kind, atoms, n_omega, fp64=False, repeat=1):

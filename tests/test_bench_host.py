@@ -175,3 +175,19 @@ def test_roofline_picks_the_binding_roof():
     assert g["intensity_flop_per_byte"] > g["ridge_flop_per_byte"]
     assert g["bound"] == "tensor" and g["unit"] == "TFLOP/s"
     assert g["share"] == pytest.approx(50.0 / 150.0)
+
+
+def test_sustainable_rate_rule():
+    """serve.py sweep: the highest offered rate that every job completes at,
+    with throughput keeping up and queueing below the run time."""
+    from paper_1101_2065_gb300.serve import sustainable_rate
+
+    def row(rate, done, sps, q50, r50):
+        return {"offered_rate_per_s": rate, "completed": done, "solves_per_s": sps,
+                "queue_ms": {"p50": q50}, "run_ms": {"p50": r50}}
+    rows = [row(0.25, 24, 0.34, 0.04, 488.0), row(0.5, 24, 0.63, 0.03, 512.0), row(1.0, 24, 1.06, 0.04, 728.0),
+            row(2.0, 24, 1.18, 3407.0, 772.0)]
+    assert sustainable_rate(rows, 24) == 1.0
+    rows[2] = row(1.0, 23, 1.06, 0.04, 728.0)            # a job failed at 1/s
+    assert sustainable_rate(rows, 24) == 0.5
+    assert sustainable_rate([row(4.0, 24, 1.2, 9000.0, 800.0)], 24) is None
