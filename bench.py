@@ -201,6 +201,33 @@ def _form_blocks(n, nb=32, bm=128):
     return out
 
 
+def ldlt_updates(n, nb=32):
+    """The binary32 factorisation's trailing-update launches, as the library
+    issues them: (kernel, rows, columns updated per row at most, panel width).
+    With 128 rows or more left after the next panel, two panels share one pass
+    (the first panel's update of the next panel's columns, then both updates
+    of the rest in k_ldlt32_syrk_tc2); otherwise one panel per launch, on the
+    tensor cores from 128 rows, else on the FMA units."""
+    out, k0 = [], 0
+    while k0 < n:
+        m = n - min(n, k0 + nb)
+        if m == 0:
+            break
+        if m >= 128 and m - nb >= 128:
+            out.append(("k_ldlt32_syrk_tc", m, nb, nb))
+            out.append(("k_ldlt32_syrk_tc2", m - nb, m - nb, 2 * nb))
+            k0 += 2 * nb
+            continue
+        out.append(("k_ldlt32_syrk_tc" if m >= 128 else "k_ldlt32_syrk", m, m, nb))
+        k0 += nb
+    return out
+
+
+def _update_entries(m, w):
+    """Entries (r, c) of an m-row trailing triangle with c among its first w columns."""
+    return m * (m + 1) / 2 if w >= m else w * m - w * (w - 1) / 2
+
+
 def forms_kernel(n, R):
     """Which binary32 forms kernel a molecule takes (the library's dispatch):
     tensor-memory forms for 32 < n <= 384, the resident FMA forms while 48
@@ -260,11 +287,12 @@ def kernel_model(name, mol, grid, n_rank=None):
             return (N - 1) * fma + diag, "alu", PEAK_FP32_TFLOPS
         return ((N - 1) * tcf, "tensor", PEAK_TF32_TFLOPS / 3) if tcf > 0 else (None, None, None)
 
-    if name == "k_ldlt32_syrk_tc":
-        # the trailing updates of 128 rows or more; 3xTF32 takes three TF32 products per binary32 product
-        return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if m >= 128), "tensor", PEAK_TF32_TFLOPS / 3
-    if name == "k_ldlt32_syrk":
-        return N * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in P if 0 < m < 128), "alu", PEAK_FP32_TFLOPS
+    if name in ("k_ldlt32_syrk_tc", "k_ldlt32_syrk_tc2", "k_ldlt32_syrk"):
+        # entries updated x panel width; 3xTF32 takes three TF32 products per binary32 product
+        f = N * 8.0 * sum(_update_entries(m, w) * kb for k, m, w, kb in ldlt_updates(n) if k == name)
+        if f == 0:
+            return None, None, None
+        return (f, "alu", PEAK_FP32_TFLOPS) if name == "k_ldlt32_syrk" else (f, "tensor", PEAK_TF32_TFLOPS / 3)
     if name == "k_ldlt32_panel":
         return N * 8.0 * sum(kb ** 3 / 6 + m * kb * (kb - 1) / 2 for kb, m in P), "alu", PEAK_FP32_TFLOPS
     if name == "k_chi0_kk_fma":
@@ -293,10 +321,10 @@ def kernel_bytes(name, mol, grid):
         return 2.0 * N * tri * cz                   # read chi0, write M = 1 - chi0
     if name == "k_chi0_kk_fma":
         return band_bins(mol, grid) * tri * 4.0 + N * tri * cz   # read the spectral weights, write chi0
-    if name == "k_ldlt32_syrk_tc":
-        return N * sum(m * (m + 1) / 2 * 2 * cz + m * kb * cz for kb, m in P if m >= 128)
-    if name == "k_ldlt32_syrk":
-        return N * sum(m * (m + 1) / 2 * 2 * cz + m * kb * cz for kb, m in P if 0 < m < 128)
+    if name in ("k_ldlt32_syrk_tc", "k_ldlt32_syrk_tc2", "k_ldlt32_syrk"):
+        # the updated entries read and written once, the panel rows read once
+        b = N * sum(_update_entries(m, w) * 2 * cz + m * kb * cz for k, m, w, kb in ldlt_updates(n) if k == name)
+        return b if b > 0 else None
     if name == "k_ldlt32_panel":
         return N * sum((m + kb) * kb * 2 * cz + kb * kb * cz for kb, m in P)
     if name in ("k_forms32_tm", "k_forms32"):
@@ -402,7 +430,8 @@ def roofline_of(dom, kt, timed_mols, grid, total_ms):
 
 
 KERNELS = ["k_forms32", "k_forms32_tm", "k_forms32_diag", "k_forms32_update", "k_forms32_gemm_tc", "k_forms32_block",
-           "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk", "k_ldlt32_syrk_tc", "k_chi0_kk_fma", "k_chi0_kk_tc",
+           "k_ldlt32_init", "k_ldlt32_panel", "k_ldlt32_syrk", "k_ldlt32_syrk_tc", "k_ldlt32_syrk_tc2",
+           "k_chi0_kk_fma", "k_chi0_kk_tc",
            "k_kk_ctable", "k_deposit_syrk32",
            "k_sgemm", "k_sgemm_tc", "k_dgemm", "k_sytrd32_grid", "k_sytrd32_cl", "k_bisect", "k_invit",
            "k_backtransform", "k_cluster_mgs", "k_rayleigh_cols", "k_vertex_contract", "k_vertex_contract32",
@@ -418,9 +447,6 @@ KERNELS = ["k_forms32", "k_forms32_tm", "k_forms32_diag", "k_forms32_update", "k
 # average launch of the timed jobs.  An entry is dropped whenever its kernel
 # changes.
 NCU_TRAFFIC = {
-    # third trailing update (k0 = 64, 624 rows, 512 frequencies): 922.2 MB read + 752.4 MB written
-    "k_ldlt32_syrk_tc": {"ratio": 1674.6e6 / (512 * (624 * 625 / 2 * 16 + 624 * 32 * 8)),
-                         "capture": "k_ldlt_syrk_tc, chain24 N_omega 512, launch 3"},
     # block i0 = 256 (rows 256..383, 511 frequencies): 803.1 MB read + 299.5 MB written; q (binary64)
     # is shared by the frequencies and stays in L2
     "k_forms32_gemm_tc": {"ratio": 1102.6e6 / (511 * (256 * 624 * 8 + 128 * 256 * 8 + 128 * 624 * 8 * 2)),

@@ -430,7 +430,8 @@ __device__ __forceinline__ void st_load_c(float2 (&cv)[4][4], const float2* __re
     }
 }
 
-__global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fac, int n, int k0, int* status) {
+__global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fac, int n, int k0, int nj_max,
+                                                         int* status) {
     extern __shared__ __align__(128) unsigned char sraw_st[];
     unsigned char* sAh = sraw_st;
     unsigned char* sAl = sAh + ST_A_BYTES;
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fa
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float2* A = fac + (long long)blockIdx.y * tri(n);
     const int k1 = k0 + 32, m = n - k1, nj = (m + ST_NC - 1) / ST_NC, I = blockIdx.x;
-    const int r0 = k1 + 128 * I, ntile = st_row_tiles(nj, I);
+    const int r0 = k1 + 128 * I, ntile = min(st_row_tiles(nj, I), nj_max);
     // this warp's read-back block: rows rw .. rw + 31, complex columns 16 h .. + 15 of a tile
     const int rw = r0 + 32 * (warp & 3), h = warp >> 2;
     if (warp == 0) tc::tmem_alloc(&tbase, 4 * ST_N);
@@ -571,6 +572,189 @@ __global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fa
     if (warp == 0) {
         tc::fence_after();
         tc::tmem_dealloc(taddr, 4 * ST_N);
+    }
+}
+
+// The trailing update of two consecutive panels in one pass (binary32): with
+// panel p0 = [g0, g0 + 32) factored, its update restricted to the columns of
+// panel p1 = [g0 + 32, g0 + 64) (k_ldlt_syrk_tc with one column tile) and
+// p1 factored, the rest of the trailing matrix takes
+//   M[r][c] <- (M[r][c] - u0[r][c]) - u1[r][c],  g0 + 64 <= c <= r,
+// u_j the 3xTF32 product of panel j, each in its own tensor-memory
+// accumulators and subtracted in that order: the same operations, in the same
+// order, as two k_ldlt_syrk_tc launches, with the packed triangle read and
+// written once instead of twice.  One CTA per frequency and 128-row block:
+// both panels' rows staged once (128 KB), one B buffer holding both panels'
+// w for a column tile of 32 (64 KB), two accumulator sets of 256 columns, and
+// the per-warp read-back turn-around of k_ldlt_syrk_tc.
+constexpr size_t ST2_SMEM = 4 * (size_t)ST_A_BYTES + 4 * (size_t)ST_B_BYTES + 8 * 32 * ST_XP * sizeof(float2);
+
+__global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc2(float2* __restrict__ fac, int n, int g0, int* status) {
+    extern __shared__ __align__(128) unsigned char sraw_s2[];
+    unsigned char* sA = sraw_s2;                                       // [panel][hi, lo][ST_A_BYTES]
+    unsigned char* sB = sA + 4 * ST_A_BYTES;                           // [panel][hi, lo][ST_B_BYTES]
+    float2* sX = reinterpret_cast<float2*>(sB + 4 * ST_B_BYTES);       // [8 warps][32][ST_XP]
+    __shared__ float2 dd[64];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float2* A = fac + (long long)blockIdx.y * tri(n);
+    const int k2 = g0 + 64, m = n - k2, nj = (m + ST_NC - 1) / ST_NC, I = blockIdx.x;
+    const int r0 = k2 + 128 * I, ntile = st_row_tiles(nj, I);
+    const int rw = r0 + 32 * (warp & 3), h = warp >> 2;
+    if (warp == 0) tc::tmem_alloc(&tbase, 8 * ST_N);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0]);
+        tc::mbar_init(&mbar[1]);
+    }
+    if (tid < 64) dd[tid] = A[tri(g0 + tid) + g0 + tid];
+    float2 wr0[2][2], wr1[2][2], cs0[4][4], cs1[4][4], cs2[4][4];
+    st_load_b(wr0, A, n, g0, k2);
+    st_load_b(wr1, A, n, g0 + 32, k2);
+    st_load_c(cs0, A, n, rw, k2 + 16 * h);
+    if (ntile > 1) st_load_c(cs1, A, n, rw, k2 + ST_NC + 16 * h);
+    // A operands: rows r0 .. r0 + 127 of both panels, staged once
+#pragma unroll 4
+    for (int j = 0; j < 16; ++j) {
+        const int pj = j >> 3, idx = tid + 256 * (j & 7), rr = idx & 7, kq = (idx >> 3) & 15, rg = idx >> 7;
+        const int ra = r0 + 8 * rg + rr;
+        float2 a = make_float2(0.f, 0.f), b = a;
+        if (ra < n) {
+            const float2* src = A + tri(ra) + g0 + 32 * pj + 2 * kq;
+            a = src[0];
+            b = src[1];
+        }
+        unsigned char* ah = sA + 2 * pj * ST_A_BYTES;
+        st_shared_quad(ah, ah + ST_A_BYTES, tc::core_off(8 * rg + rr, 4 * kq, 16), a.x, a.y, b.x, b.y);
+    }
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t taddr = tbase;
+    bool ok = true;
+    float2* X = sX + warp * 32 * ST_XP;
+    int J = 0;
+    auto stage_b = [&](const float2 (&wr)[2][2], int pj) {
+        unsigned char* bh = sB + 2 * pj * ST_B_BYTES;
+        unsigned char* bl = bh + ST_B_BYTES;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int idx = tid + 256 * j, rr = idx & 7, kq = (idx >> 3) & 15, rg = idx >> 7, q = 8 * rg + rr;
+            const float2 w0 = cmul(wr[j][0], dd[32 * pj + 2 * kq]), w1 = cmul(wr[j][1], dd[32 * pj + 2 * kq + 1]);
+            st_shared_quad(bh, bl, tc::core_off(q, 4 * kq, 16), w0.x, -w0.y, w1.x, -w1.y);
+            st_shared_quad(bh, bl, tc::core_off(ST_NC + q, 4 * kq, 16), w0.y, w0.x, w1.y, w1.x);
+        }
+    };
+    // this warp's 16 columns of one panel's product: per 8 columns, hi x hi + cross terms
+    auto to_x = [&](uint32_t base) {
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            uint32_t re[8], im[8], re2[8], im2[8];
+            tc::tmem_ld8(base + 8 * hh, re);
+            tc::tmem_ld8(base + ST_NC + 8 * hh, im);
+            tc::tmem_ld8(base + ST_N + 8 * hh, re2);
+            tc::tmem_ld8(base + ST_N + ST_NC + 8 * hh, im2);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                X[lane * ST_XP + 8 * hh + j] = make_float2(__uint_as_float(re[j]) + __uint_as_float(re2[j]),
+                                                           __uint_as_float(im[j]) + __uint_as_float(im2[j]));
+        }
+    };
+    // step J: wait for tile J - 1's MMAs (the B buffer is free, its accumulators ready), stage
+    // and multiply tile J, read back tile J - 1 from register set `cp`, load tile J + 1 into `cnx`
+    auto step = [&](float2 (&cp)[4][4], float2 (&cnx)[4][4]) -> bool {
+        if (J >= 1) {
+            if (J + 1 < ntile) st_load_c(cnx, A, n, rw, k2 + ST_NC * (J + 1) + 16 * h);
+            ok = tc::mbar_wait(tc::smem_u32(&mbar[(J - 1) & 1]), ((J - 1) >> 1) & 1) && ok;
+            ok = __syncthreads_and(ok);
+            if (!ok) return false;
+        }
+        if (J < ntile) {
+            stage_b(wr0, 0);
+            stage_b(wr1, 1);
+            if (J + 1 < ntile) {
+                st_load_b(wr0, A, n, g0, k2 + ST_NC * (J + 1));
+                st_load_b(wr1, A, n, g0 + 32, k2 + ST_NC * (J + 1));
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after();
+#pragma unroll
+                for (int pj = 0; pj < 2; ++pj) {
+                    const uint32_t ah = tc::smem_u32(sA + 2 * pj * ST_A_BYTES), al = ah + ST_A_BYTES;
+                    const uint32_t b0 = tc::smem_u32(sB + 2 * pj * ST_B_BYTES);
+                    const uint32_t d = taddr + (uint32_t)(4 * ST_N * (J & 1) + 2 * ST_N * pj);
+#pragma unroll
+                    for (int ks = 0; ks < 8; ++ks) {
+                        const uint32_t o = ks * 256, acc = ks > 0 ? 1u : 0u;
+                        tc::mma_tf32(d, tc::smem_desc(ah + o, ST_SBO), tc::smem_desc(b0 + o, ST_SBO), ST_IDESC2, acc);
+                        tc::mma_tf32(d + ST_N, tc::smem_desc(al + o, ST_SBO), tc::smem_desc(b0 + o, ST_SBO), ST_IDESC,
+                                     1u);
+                    }
+                }
+                tc::commit(tc::smem_u32(&mbar[J & 1]));
+            }
+        }
+        if (J >= 1) {
+            // tile J - 1: M - u0, then - u1, through the turn-around
+            const int Jp = J - 1, cb = k2 + ST_NC * Jp + 16 * h;
+            tc::fence_after();
+            const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(4 * ST_N * (Jp & 1) + 16 * h);
+            to_x(base);
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int rl = (lane >> 2) + 8 * i;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float2 x = X[rl * ST_XP + 4 * (lane & 3) + t];
+                    cp[i][t] = make_float2(cp[i][t].x - x.x, cp[i][t].y - x.y);
+                }
+            }
+            __syncwarp();
+            to_x(base + 2 * ST_N);
+            tc::fence_before();
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int rl = (lane >> 2) + 8 * i, r = rw + rl;
+                if (r < n) {
+                    float2* row = A + tri(r);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int cl = 4 * (lane & 3) + t, cc = cb + cl;
+                        if (cc <= r) {
+                            const float2 x = X[rl * ST_XP + cl];
+                            row[cc] = make_float2(cp[i][t].x - x.x, cp[i][t].y - x.y);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        return true;
+    };
+    while (J <= ntile) {
+        if (!step(cs2, cs1) || ++J > ntile) break;
+        if (!step(cs0, cs2) || ++J > ntile) break;
+        if (!step(cs1, cs0)) break;
+        ++J;
+    }
+    if (!ok) {
+        // the loop ended at tile J: tiles 0 .. J - 1 were issued; their MMAs finish before the columns are freed
+        if (tid == 0) atomicOr(status, ST_TIMEOUT);
+        const int issued = min(J, ntile);
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int cnt = (issued - s2 + 1) / 2;
+            if (cnt > 0) tc::mbar_wait(tc::smem_u32(&mbar[s2]), (cnt - 1) & 1);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(taddr, 8 * ST_N);
     }
 }
 
@@ -1628,8 +1812,21 @@ static void ldlt_steps(gw_ctx* ctx, const C* chi0, C* fac, int n, int N, C* linv
             // binary32: trailing updates with at least one full 128-row block on the tensor cores
             if (!ctx->syrk_simt && m >= 128 && N <= 65535) {
                 allow_max_smem(k_ldlt_syrk_tc);
+                if (m - NB >= 128) {
+                    // two panels per pass over the trailing matrix: the next panel's columns
+                    // first, that panel factored, then both updates of the rest in one launch
+                    klaunch(ctx, names[3], k_ldlt_syrk_tc, dim3(div_up(m, 128), N), 256, ST_SMEM, (float2*)fac, n,
+                            k0, 1, ctx->d_status);
+                    klaunch(ctx, names[1], k_ldlt_panel<C>, N, 256, 0, fac, n, N, k0 + NB, linv, piv,
+                            ctx->d_status);
+                    allow_max_smem(k_ldlt_syrk_tc2);
+                    klaunch(ctx, "k_ldlt32_syrk_tc2", k_ldlt_syrk_tc2, dim3(div_up(m - NB, 128), N), 256, ST2_SMEM,
+                            (float2*)fac, n, k0, ctx->d_status);
+                    k0 += NB;
+                    continue;
+                }
                 klaunch(ctx, names[3], k_ldlt_syrk_tc, dim3(div_up(m, 128), N), 256, ST_SMEM, (float2*)fac, n, k0,
-                        ctx->d_status);
+                        1 << 30, ctx->d_status);
                 continue;
             }
         }

@@ -69,12 +69,25 @@ def test_batched_forms_model_splits_diagonal_and_update():
 
 
 def test_trailing_update_models_split_at_128_rows(ring):
+    """Every entry of every panel's trailing triangle once, whichever launch
+    updates it: strips of the next panel's columns and the paired updates
+    (k_ldlt32_syrk_tc, k_ldlt32_syrk_tc2) while 128 rows remain after the next
+    panel, single-panel launches below that."""
     mol, grid = ring
     tc, _, _ = bench.kernel_model("k_ldlt32_syrk_tc", mol, grid)
+    tc2, _, _ = bench.kernel_model("k_ldlt32_syrk_tc2", mol, grid)
     fma, _, _ = bench.kernel_model("k_ldlt32_syrk", mol, grid)
     full = 1024 * 8.0 * sum(m * (m + 1) / 2 * kb for kb, m in bench._panels(300, 32) if m > 0)
-    assert tc + fma == pytest.approx(full)
-    assert tc > 0 and fma > 0
+    assert tc + tc2 + fma == pytest.approx(full)
+    assert tc > 0 and tc2 > 0 and fma > 0
+    # n = 300: panels at 0, 64 paired (268 and 204 rows below them), 128 and 160 alone (140, 108 rows)
+    ups = bench.ldlt_updates(300)
+    assert [(k[9:], m) for k, m, _, _ in ups] == [("syrk_tc", 268), ("syrk_tc2", 236), ("syrk_tc", 204),
+                                                   ("syrk_tc2", 172), ("syrk_tc", 140)] + \
+        [("syrk", 300 - 32 * j) for j in range(6, 10)]
+    # bytes: a paired pass reads and writes its triangle once for two panels
+    b2 = bench.kernel_bytes("k_ldlt32_syrk_tc2", mol, grid)
+    assert b2 == pytest.approx(1024 * ((236 * 237 / 2 + 172 * 173 / 2) * 16 + (236 + 172) * 64 * 8))
 
 
 def test_cauchy_and_traffic_models(ring):
