@@ -10,7 +10,11 @@
 //     update M22 -= L21 D L21^T: k_ldlt_syrk (one CTA per frequency and
 //     64 x 64 tile, FMA units) or, on the binary32 path for 128 rows and
 //     more, k_ldlt_syrk_tc (one CTA per frequency and 128-row block, 3xTF32
-//     on the tensor cores).  The steps are small one by one, but N of them
+//     on the tensor cores).  While 128 rows remain after the next panel, the
+//     binary32 path takes two panels per pass over the trailing matrix: the
+//     first panel's update of the next panel's columns, that panel, then
+//     k_ldlt_syrk_tc2 for both updates of the rest, with the rounding of two
+//     separate passes.  The steps are small one by one, but N of them
 //     side by side fill the GPU.  chi^RPA_k = M_k^-1 chi0_k = M_k^-1 - 1
 //     (Eq. chi_RPA) is never formed on the hot path: the forms only need
 //     M_k^-1.
