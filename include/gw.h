@@ -149,7 +149,9 @@ gw_status gw_ctx_profile_get(gw_ctx* ctx, const char* kernel_name, double* total
  * FMA units instead (right-looking, by pairs of 32-column panels).
  * GW_OPT_SYRK_SIMT (value 0 or 1, default 0): the binary32 factorisation
  * runs its trailing updates of 128 or more rows as 3xTF32 tensor-core
- * products by default; 1 keeps them on the FMA units.
+ * products by default, two 32-column panels per pass over the trailing
+ * matrix while 128 rows remain after the second (the same factors as one
+ * pass per panel); 1 keeps them on the FMA units.
  * GW_OPT_GEMM_SIMT (value 0 or 1, default 0): the binary32 path's dense
  * products (g, U, Z, Zup, q) run as 3xTF32 tensor-core products by default;
  * 1 runs them on the binary32 FMA units (round to nearest throughout).
