@@ -31,8 +31,26 @@ MUTATIONS = [
      "A = np.diag(w[k] - 1j * eta - E) - sigc[:, :, k] - (sx - vxc)"),
     ("A = np.diag(w[k] + 1j * eta - E) - sigc[:, :, k] - (sx - vxc)",
      "A = np.diag(w[k] + 1j * eta - E) + sigc[:, :, k] - (sx - vxc)"),
-    # threshold compression: keep the smallest eigenvalues instead of the largest
+    # threshold compression: keep the smallest eigenvalues instead of the largest; lambda^-1 for lambda^-1/2
     ("keep = np.nonzero(lam >= lambda_rel * lam.max())[0][::-1]", "keep = np.nonzero(lam <= lambda_rel * lam.max())[0]"),
+    ("Z = Xr @ xi[:, keep] / np.sqrt(lam[keep])", "Z = Xr @ xi[:, keep] / lam[keep]"),
+    # gamma = -(1/pi) Im chi^RPA without its sign; W = v - Zup chi^RPA Zup^T; P W P for P W P^T
+    ("g = -chi_rpa.imag / math.pi", "g = chi_rpa.imag / math.pi"),
+    ("return mol.v[None] + Zup[None] @ chi_rpa @ Zup.T[None]", "return mol.v[None] - Zup[None] @ chi_rpa @ Zup.T[None]"),
+    ("return P @ W @ P.T", "return P @ W @ P"),
+    # occupied states: the tent's second node on the wrong side; Sigma_c with +i eta for s < 0 too
+    ("np.add.at(sig[n], i + 1 - jp - j0, f * ck)", "np.add.at(sig[n], i - jp - j0, f * ck)"),
+    ("sgn = np.where(j >= 0, 1.0, -1.0)", "sgn = np.ones(j.size)"),
+    # sampled-frequency routes: the odd part added; tent weights of a bin swapped
+    ("K = 1.0 / ((k - j) * d_omega + 1j * eta) - 1.0 / ((k + j) * d_omega + 1j * eta)\n    flat = A_band",
+     "K = 1.0 / ((k - j) * d_omega + 1j * eta) + 1.0 / ((k + j) * d_omega + 1j * eta)\n    flat = A_band"),
+    ('w = np.concatenate([2.0 * (1.0 - pairs["frac"][lo]), 2.0 * pairs["frac"][hi]])',
+     'w = np.concatenate([2.0 * pairs["frac"][lo], 2.0 * (1.0 - pairs["frac"][hi])])'),
+    # DOS = +(1/pi) Im Tr G; second window: the seam one node further out
+    ("rho[k] = -np.trace(Gk).imag / math.pi", "rho[k] = np.trace(Gk).imag / math.pi"),
+    ("return (gs.n_omega - 1) * gs.d_omega", "return gs.n_omega * gs.d_omega"),
+    # renormalisation factor 1 / (1 + dSigma/dE)
+    ("return E, 1.0 / (1.0 - der), status", "return E, 1.0 / (1.0 + der), status"),
 ]
 
 

@@ -435,6 +435,29 @@ def test_threshold_compression_pins(cfg1, cfg1_oracle):
     assert n_by_e[0] < n_by_e[1] < n_by_e[2]
 
 
+def test_projected_W_keeps_the_screened_part(cfg1, cfg1_oracle):
+    """Eqs. projector0 and proj-scr-inter with N_rank = 100 < N_prod pair
+    vectors X: the compressed basis Zup = v Z lies in the span of v X, so the
+    projection P (.) P^T, P = v X g^-1 X^T, leaves the screened part
+    W - v = Zup chi^RPA Zup^T of the compressed W unchanged, and on the span
+    the projected bare interaction is v itself: X^T (P v P^T) X = X^T v X = g."""
+    mol, grid = cfg1
+    r = cfg1_oracle
+    pairs, VEF = r["pairs"], r["VEF"]
+    sub = gw.compression_threshold(mol, VEF, pairs, np.sort(pairs["delta"])[99] + 1e-9, 0.1)
+    X, g, Zup = sub["X"], sub["g"], sub["Zup"]
+    ks = [1, 90, 200]
+    U = gw.compress_pairs(VEF, Zup)
+    chi0 = gw.chi0_cauchy(gw.deposit_spectral(U, pairs, grid.n_omega), grid.d_omega, grid.eta)
+    Ws = gw.screened_W(mol, Zup, gw.screen(chi0, ks)) - mol.v[None]
+    assert np.linalg.norm(Ws) > 0.0
+    Wp = gw.projected_W(mol, X, g, Ws)
+    assert np.linalg.norm(Wp - Ws) <= 1e-8 * np.linalg.norm(Ws)
+    Pv = gw.projected_W(mol, X, g, mol.v)
+    assert np.linalg.norm(Pv - Pv.T) <= 1e-9 * np.linalg.norm(Pv)
+    assert np.linalg.norm(X.T @ Pv @ X - g) <= 1e-8 * np.linalg.norm(g)
+
+
 def test_two_window_reduces_to_one_window(cfg1, cfg1_oracle):
     """Second window technique (Sec. 4.2): with the small window equal to the
     large one every transition and every form falls in the small window or
@@ -447,6 +470,24 @@ def test_two_window_reduces_to_one_window(cfg1, cfg1_oracle):
     assert np.linalg.norm(t["sigma_c"] - r["sigma_c"]) <= 1e-12 * np.linalg.norm(r["sigma_c"])
     assert np.abs(t["e_qp"] - r["e_qp"]).max() < 1e-11
     assert np.array_equal(t["status"], r["status"])
+
+
+def _two_window_closed_form(mol, Zup, gs, gl, lam, ks):
+    """chi0_k on the small grid from the transitions one by one (Sec. 6.1
+    closed form, brute-force vertex products), each transition with the
+    broadening of the window its energy falls in: small below lam, large at
+    or above it."""
+    w = ks * gs.d_omega
+    Vd = pins.dense_vertex(mol)
+    ref = np.zeros((ks.size, mol.n_sub, mol.n_sub), complex)
+    for E in range(mol.n_occ):
+        for F in range(mol.n_occ, mol.eps.size):
+            u = Zup.T @ pins.brute_vef(mol, E, F, Vd)
+            d = mol.eps[F] - mol.eps[E]
+            eta = gs.eta if d < lam else gl.eta
+            k = 1.0 / (w + 1j * eta - d) - 1.0 / (w + 1j * eta + d)
+            ref += 2.0 * np.outer(u, u)[None] * k[:, None, None]
+    return ref
 
 
 def test_two_window_chi0_closed_form_on_nodes():
@@ -464,16 +505,32 @@ def test_two_window_chi0_closed_form_on_nodes():
     U = gw.compress_pairs(gw.pair_vertex(mol, pairs), Zup)
     chi = gw.chi0_two_window(U, pairs, gs, gl)
     ks = np.array([0, 1, 50, 161, 319])
-    w = ks * gs.d_omega
-    Vd = pins.dense_vertex(mol)
-    ref = np.zeros((ks.size, mol.n_sub, mol.n_sub), complex)
-    for E in range(mol.n_occ):
-        for F in range(mol.n_occ, mol.eps.size):
-            u = Zup.T @ pins.brute_vef(mol, E, F, Vd)
-            d = mol.eps[F] - mol.eps[E]
-            eta = gs.eta if d < lam else gl.eta
-            k = 1.0 / (w + 1j * eta - d) - 1.0 / (w + 1j * eta + d)
-            ref += 2.0 * np.outer(u, u)[None] * k[:, None, None]
+    ref = _two_window_closed_form(mol, Zup, gs, gl, lam, ks)
+    assert np.abs(chi[ks] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_two_window_seam_transition():
+    """Eq. win2-for-response at the seam: the small window holds the spectral
+    arguments below its last node (N_s - 1) dw_s, where a tent still has both
+    of its nodes on the small grid.  A transition exactly on that node
+    belongs to the large window (one at 80 dw_l here, with N_s = 321 and
+    dw_s = dw_l / 4), and chi0 on the small grid is the closed form with it
+    carrying the large broadening; the others, on nodes of both grids, split
+    at that energy."""
+    mol = pins.tiny_molecule(n_orb=8, n_occ=4, n_prod=6)
+    mol.eps = np.array([-96, -80, -64, -40, 4, 16, 30, 60], float) * DW     # 16 - (-64) = 80
+    gl = synth.Grid(256, DW, 1.5 * DW)
+    gs = synth.Grid(321, DW / 4, 1.5 * DW / 4)
+    seam = (gs.n_omega - 1) * gs.d_omega
+    assert seam == 80 * DW
+    Zup = np.linalg.cholesky(mol.v)
+    pairs = gw.pair_table(mol.eps, mol.n_occ, gl.d_omega, gl.n_omega)
+    assert np.count_nonzero(pairs["delta"] == seam) == 1
+    assert np.any(pairs["delta"] < seam) and np.any(pairs["delta"] > seam)
+    U = gw.compress_pairs(gw.pair_vertex(mol, pairs), Zup)
+    chi = gw.chi0_two_window(U, pairs, gs, gl)
+    ks = np.array([0, 3, 160, 320])
+    ref = _two_window_closed_form(mol, Zup, gs, gl, seam, ks)
     assert np.abs(chi[ks] - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
