@@ -1,9 +1,11 @@
 """Plant mistakes in a copy of the oracle (on the CPU) and check that the
-pins catch each one."""
+pins catch each one.  The copies run side by side (one pytest process each,
+two BLAS threads apiece) so that the suite stays a few minutes long."""
 import os
 import shutil
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -51,18 +53,44 @@ MUTATIONS = [
     ("return (gs.n_omega - 1) * gs.d_omega", "return gs.n_omega * gs.d_omega"),
     # renormalisation factor 1 / (1 + dSigma/dE)
     ("return E, 1.0 / (1.0 - der), status", "return E, 1.0 / (1.0 + der), status"),
+    # virtual states: the tent's second node on the wrong side
+    ("np.add.at(sig[n], i + 1 + jp - j0, f * ck)", "np.add.at(sig[n], i + jp - j0, f * ck)"),
+    # second window: the small window's broadening in the large window's Cauchy sum for Sigma_c and the QP root
+    ("K = 1.0 / (w - j[None, :] * gl.d_omega + 1j * gl.eta * sgn[None, :])",
+     "K = 1.0 / (w - j[None, :] * gl.d_omega + 1j * gs.eta * sgn[None, :])"),
+    ("second=(sig_l[i], j0_l, gl.d_omega, gl.eta))", "second=(sig_l[i], j0_l, gl.d_omega, gs.eta))"),
 ]
 
 
-@pytest.mark.parametrize("old,new", MUTATIONS)
-def test_pins_catch_planted_mistake(tmp_path, old, new):
-    for d in ("synth", "oracle", "tests"):
-        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+def _run_pins_on_mutant(base, idx):
+    """pytest's exit status on the pins with mutation idx planted in a copy
+    of the oracle, or None if the text to replace is not in the oracle."""
+    old, new = MUTATIONS[idx]
+    d = base / f"m{idx}"
+    for sub in ("synth", "oracle", "tests"):
+        shutil.copytree(os.path.join(ROOT, sub), d / sub,
                         ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
-    shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path)
-    src = (tmp_path / "oracle" / "gw.py").read_text()
-    assert old in src
-    (tmp_path / "oracle" / "gw.py").write_text(src.replace(old, new, 1))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), d)
+    src = (d / "oracle" / "gw.py").read_text()
+    if old not in src:
+        return None
+    (d / "oracle" / "gw.py").write_text(src.replace(old, new, 1))
+    env = dict(os.environ, OMP_NUM_THREADS="2", OPENBLAS_NUM_THREADS="2", MKL_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
-                        "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True)
-    assert r.returncode != 0, "planted mistake went unnoticed"
+                        "-p", "no:cacheprovider"], cwd=d, capture_output=True, text=True, env=env)
+    return r.returncode
+
+
+@pytest.fixture(scope="module")
+def pin_outcomes(tmp_path_factory):
+    base = tmp_path_factory.mktemp("mutants")
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(lambda i: _run_pins_on_mutant(base, i), range(len(MUTATIONS))))
+
+
+@pytest.mark.parametrize("idx", range(len(MUTATIONS)), ids=[m[1][:60] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(pin_outcomes, idx):
+    rc = pin_outcomes[idx]
+    assert rc is not None, "the text to replace is not in the oracle"
+    assert rc != 0, "planted mistake went unnoticed"

@@ -300,6 +300,27 @@ def test_two_level_sigma_c_analytic():
     assert 1.5 < errs[0] / errs[1] < 2.6, errs
 
 
+def test_sigma_tent_keeps_zeroth_and_first_moments(cfg1, cfg1_oracle):
+    """Eq. spectral_3 on the grid: each form c_nk is shifted to E_k + s2
+    (virtual k) or E_k - s2 (occupied k) and spread over the two nearest
+    nodes with linear (tent) weights, which keep the total weight and the
+    mean position exactly:  sum_j sigma_j = sum_k sum_j' c_nk(s_j') and
+    sum_j s_j sigma_j = sum_k sum_j' (E_k +- s_j') c_nk(s_j')."""
+    mol, grid = cfg1
+    r = cfg1_oracle
+    dw = grid.d_omega
+    c, sig, j0 = r["c"], r["sigma"], r["j0"]
+    s_sig = (j0 + np.arange(sig.shape[1])) * dw
+    s2 = np.arange(c.shape[2]) * dw
+    assert np.any(np.abs(mol.eps / dw - np.rint(mol.eps / dw)) > 0.1)      # off-grid energies
+    for n in range(sig.shape[0]):
+        w0 = c[n].sum()
+        sign = np.where(np.arange(mol.eps.size) >= mol.n_occ, 1.0, -1.0)
+        w1 = np.sum((mol.eps[:, None] + sign[:, None] * s2[None, :]) * c[n])
+        assert sig[n].sum() == pytest.approx(w0, rel=1e-12)
+        assert np.sum(s_sig * sig[n]) == pytest.approx(w1, rel=1e-11, abs=1e-12 * np.abs(c[n]).sum())
+
+
 def test_sigma_signs(cfg1_oracle):
     r = cfg1_oracle
     assert r["sigma"].min() >= 0.0
@@ -467,6 +488,7 @@ def test_two_window_reduces_to_one_window(cfg1, cfg1_oracle):
     r = cfg1_oracle
     t = gw.solve_two_window(mol, grid, grid, Z=None)
     assert np.linalg.norm(t["chi0_s"] - r["chi0"]) <= 1e-13 * np.linalg.norm(r["chi0"])
+    assert np.array_equal(t["sigma_x"], r["sigma_x"])
     assert np.linalg.norm(t["sigma_c"] - r["sigma_c"]) <= 1e-12 * np.linalg.norm(r["sigma_c"])
     assert np.abs(t["e_qp"] - r["e_qp"]).max() < 1e-11
     assert np.array_equal(t["status"], r["status"])
@@ -488,6 +510,25 @@ def _two_window_closed_form(mol, Zup, gs, gl, lam, ks):
             k = 1.0 / (w + 1j * eta - d) - 1.0 / (w + 1j * eta + d)
             ref += 2.0 * np.outer(u, u)[None] * k[:, None, None]
     return ref
+
+
+def test_two_window_with_an_empty_small_window(cfg1, cfg1_oracle):
+    """Eq. win2-for-response with a small window of two nodes (lam = dw, no
+    transition below it, and the forms vanish at s2 = 0): all the spectral
+    weight is in the large window, so chi0 on the large grid, Sigma_c at the
+    nodes the two grids share and the quasiparticle energies are those of
+    the one-window route on the large grid, whatever the small window's
+    broadening (each window keeps its own)."""
+    mol, grid = cfg1
+    r = cfg1_oracle
+    gs = synth.Grid(2, grid.d_omega, 0.25 * grid.eta)       # nodes shared, broadening not
+    t = gw.solve_two_window(mol, gs, grid, Z=None)
+    assert not np.any(t["pairs"]["delta"] < gw.window_cut(gs))
+    assert np.linalg.norm(t["chi0_l"] - r["chi0"]) <= 1e-13 * np.linalg.norm(r["chi0"])
+    N = grid.n_omega
+    assert np.abs(t["sigma_c"] - r["sigma_c"][:, N - 2:N + 1]).max() <= 1e-12 * np.abs(r["sigma_c"]).max()
+    assert np.abs(t["e_qp"] - r["e_qp"]).max() < 1e-11
+    assert np.array_equal(t["status"], r["status"])
 
 
 def test_two_window_chi0_closed_form_on_nodes():
