@@ -53,6 +53,9 @@ MUTATIONS = [
     ("return (gs.n_omega - 1) * gs.d_omega", "return gs.n_omega * gs.d_omega"),
     # renormalisation factor 1 / (1 + dSigma/dE)
     ("return E, 1.0 / (1.0 - der), status", "return E, 1.0 / (1.0 + der), status"),
+    # uncompressed basis: L^-1 for L^-T
+    ("Z = sla.solve_triangular(L, np.eye(n_prod), lower=True).T   # L^{-T}",
+     "Z = sla.solve_triangular(L, np.eye(n_prod), lower=True)   # L^{-T}"),
     # virtual states: the tent's second node on the wrong side
     ("np.add.at(sig[n], i + 1 + jp - j0, f * ck)", "np.add.at(sig[n], i + jp - j0, f * ck)"),
     # second window: the small window's broadening in the large window's Cauchy sum for Sigma_c and the QP root

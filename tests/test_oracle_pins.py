@@ -184,6 +184,12 @@ def test_compression_orthonormal_and_projector():
     # Z spans Xr xi: Z^T v Xr reproduces g's top eigen-block
     M = Z.T @ mol.v @ Xr
     assert np.allclose(np.sort(np.linalg.eigvalsh(M @ M.T))[::-1], lam, rtol=1e-10)
+    # uncompressed (N_sub = N_prod): the Cholesky route gives the same two conditions
+    full = pins.tiny_molecule(n_orb=8, n_occ=3, n_prod=8, atoms=2, seed=5)
+    c = gw.compression_basis(full, gw.pair_vertex(full, gw.pair_table(full.eps, full.n_occ, grid.d_omega,
+                                                                       grid.n_omega)))
+    assert np.abs(c["Z"].T @ full.v @ c["Z"] - np.eye(8)).max() < 1e-12
+    assert np.abs(c["Zup"] - full.v @ c["Z"]).max() < 1e-12
 
 
 def _W_direct(mol, chi0_full_k):
