@@ -333,7 +333,11 @@ int       gw_server_poll(gw_server* s, long long job_id);
 gw_status gw_server_wait(gw_server* s, long long job_id, int timeout_ms, double* e_qp,
                          double* z_factor, int* root_status, double* sigma_x, double* times_ms,
                          char* err, size_t err_len);
-/* Estimated device footprint of a job (bytes), as used for admission. */
+/* Estimated device footprint of a job (bytes), the figure gw_server_submit
+ * compares with the budget: the molecule plus the largest phase (basis
+ * construction, chi0 with the spectral weights of the band spanned by
+ * desc->eps, or the factors and forms of the screening), plus one eighth and
+ * 64 MiB of slack.  Host-only; 0 for a NULL or incomplete desc or grid. */
 size_t    gw_server_job_bytes(const gw_molecule_desc* desc, const gw_grid* grid, gw_precision prec,
                               int n_states);
 

@@ -324,9 +324,10 @@ extern "C" gw_status gw_server_wait(gw_server* s, long long job_id, int timeout_
 
 extern "C" size_t gw_server_job_bytes(const gw_molecule_desc* d, const gw_grid* grid, gw_precision prec,
                                       int n_states) {
-    if (!d || !grid || !d->vertex_off) return 0;
+    if (!d || !grid || !d->vertex_off || !d->eps || d->n_orb <= 0 || n_states < 0) return 0;
     Job j;
     j.n_orb = d->n_orb; j.n_occ = d->n_occ; j.n_prod = d->n_prod; j.n_sub = d->n_sub;
+    j.eps.assign(d->eps, d->eps + d->n_orb);     // the energy span sizes the spectral band, as at submission
     j.grid = *grid; j.prec = prec;
     j.vertex_len = (size_t)d->vertex_off[d->n_prod];
     j.states.resize(n_states);
