@@ -50,6 +50,9 @@ namespace {
 using namespace kk;
 constexpr int STAGE_BYTES = 2 * OPER_WORDS * 4;   // kernel matrix + weights (64 KB)
 constexpr int NSTAGE = 2;
+// all 512 tensor-memory columns: a second CTA of the kernel never fits beside the first (228 KB per SM)
+static_assert(NSTAGE * STAGE_BYTES <= 227 * 1024 - 1024 && 2 * NSTAGE * STAGE_BYTES > 228 * 1024,
+              "tensor-core Cauchy sum: one CTA per SM");
 constexpr uint32_t IDESC = tc::idesc_tf32(TM, TN);
 constexpr uint32_t SBO = (KC / 4) * 128;      // bytes between 8-row groups
 constexpr int OUT_LD = 266;                   // words per staged output row (128 complex + padding)

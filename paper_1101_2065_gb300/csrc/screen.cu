@@ -389,6 +389,9 @@ constexpr uint32_t ST_SBO = (64 / 4) * 128;
 constexpr uint32_t ST_IDESC = tc::idesc_tf32(128, ST_N);
 constexpr uint32_t ST_IDESC2 = tc::idesc_tf32(128, 2 * ST_N);     // A_hi x [B_hi; B_lo]
 constexpr size_t ST_SMEM = 2 * (size_t)ST_A_BYTES + 4 * (size_t)ST_B_BYTES + 8 * 32 * ST_XP * sizeof(float2);
+// per-block dynamic shared memory ceiling (227 KB), 1 KB kept for the static arrays
+constexpr size_t SMEM_DYN_MAX = 227 * 1024 - 1024, SMEM_PER_SM = 228 * 1024;
+static_assert(ST_SMEM <= SMEM_DYN_MAX, "trailing update: shared memory");
 
 __host__ __device__ inline int st_row_tiles(int nj, int I) { return nj < 4 * I + 4 ? nj : 4 * I + 4; }
 
@@ -592,6 +595,9 @@ __global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc(float2* __restrict__ fa
 // w for a column tile of 32 (64 KB), two accumulator sets of 256 columns, and
 // the per-warp read-back turn-around of k_ldlt_syrk_tc.
 constexpr size_t ST2_SMEM = 4 * (size_t)ST_A_BYTES + 4 * (size_t)ST_B_BYTES + 8 * 32 * ST_XP * sizeof(float2);
+static_assert(ST2_SMEM <= SMEM_DYN_MAX, "paired trailing update: shared memory");
+// all 512 tensor-memory columns: a second CTA of the kernel never fits beside the first
+static_assert(8 * ST_N == 512 && 2 * ST2_SMEM > SMEM_PER_SM, "paired trailing update: one CTA per SM");
 
 __global__ void __launch_bounds__(256, 1) k_ldlt_syrk_tc2(float2* __restrict__ fac, int n, int g0, int* status) {
     extern __shared__ __align__(128) unsigned char sraw_s2[];
@@ -1569,6 +1575,8 @@ constexpr uint32_t FG_SBO = (FG_KR / 4) * 128;
 constexpr uint32_t FG_IDESC = tc::idesc_tf32(128, FG_N);
 constexpr size_t FG_SMEM = 2 * (size_t)FG_STAGE;
 constexpr uint32_t FG_TMEM = 2 * FG_N;                  // hi x hi and cross terms: all 512 columns
+static_assert(FG_SMEM <= SMEM_DYN_MAX, "forms product: shared memory");
+static_assert(FG_TMEM == 512 && 2 * FG_SMEM > SMEM_PER_SM, "forms product: one CTA per SM");
 
 // this thread's raw entries of chunk kk (columns kk .. kk + 15 of L rows i0 ..,
 // rows kk .. kk + 15 of Y): 4 quads of A, 4 quads of B (two complex each)
